@@ -1,0 +1,256 @@
+"""CPU FP64 oracle for the page-wise linear algebra and FE assembly path.
+
+TEST INFRASTRUCTURE ONLY: the test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` are the only callers.  The library package
+never imports this module, and this module never imports the library.
+
+The arithmetic lives in ``vla_oracle.c`` (plain C, explicit loops, FP64);
+this file only compiles it with gcc (once, next to the source) and marshals
+numpy arrays through ctypes.  Each wrapper names the paper passage its C
+function follows.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "vla_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_d = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_i = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_i64 = C.c_int64
+
+
+def build(force: bool = False) -> str:
+    """Compile ``vla_oracle.c`` into ``liboracle.so`` (gcc, -O2, portable flags)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(build())
+        vp = C.c_void_p
+        lib.orc_amtam.argtypes = [_i64, C.c_int, C.c_int, C.c_int, _d, _d, _d]
+        lib.orc_astam.argtypes = [_i64, C.c_int, C.c_int, _d, _d, _d]
+        lib.orc_avtam.argtypes = [_i64, C.c_int, C.c_int, _d, _d, _d]
+        lib.orc_amdet.argtypes = [_i64, C.c_int, _d, _d]
+        lib.orc_aminv.argtypes = [_i64, C.c_int, _d, _d, vp]
+        lib.orc_aminv.restype = _i64
+        lib.orc_vectors.argtypes = [C.c_int, _i64, C.c_int, _i, _d, _d]
+        lib.orc_volumes.argtypes = [C.c_int, _i64, C.c_int, _i, _d, _d, vp]
+        lib.orc_simplex_normals.argtypes = [C.c_int, _i64, C.c_int, _i, _d, _d]
+        lib.orc_element_pages.argtypes = [C.c_int, C.c_int, _i64, C.c_int, _i, _d, C.c_int, C.c_double, C.c_double,
+                                          _d, _d, _d, _d]
+        lib.orc_csr_pattern.argtypes = [_i64, _i64, C.c_int, _i, vp, vp]
+        lib.orc_csr_pattern.restype = _i64
+        lib.orc_csr_scatter.argtypes = [_i64, C.c_int, _i, _d, _i, _i, _d]
+        lib.orc_csr_scatter.restype = C.c_int
+        lib.orc_assemble.argtypes = [C.c_int, C.c_int, _i64, _i64, C.c_int, _i, _d, C.c_int, C.c_double, C.c_double,
+                                     _i, _i, _d, _d, _d, vp, vp]
+        lib.orc_assemble.restype = C.c_int
+        lib.orc_boundary.argtypes = [C.c_int, _i64, _i64, C.c_int, _i, _d, _i64, _i, _d, _d]
+        lib.orc_boundary.restype = _i64
+        lib.orc_count_facets.argtypes = [C.c_int, _i64, C.c_int, _i, C.POINTER(_i64), C.POINTER(_i64)]
+        lib.orc_count_facets.restype = C.c_int
+        _lib = lib
+        return lib
+
+
+def _f64(x):
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _i32(x):
+    return np.ascontiguousarray(x, dtype=np.int32)
+
+
+# --------------------------------------------------------------------------
+# page primitives (Section 2.4).  Page arrays are numpy (N, cols, rows) C
+# arrays, i.e. column-major pages with the page index slowest.
+# --------------------------------------------------------------------------
+
+def amtam(A, B):
+    """C_k = A_k^T B_k.  A: (N, m, p) = N pages p x m; B: (N, n, p); C: (N, n, m)."""
+    A, B = _f64(A), _f64(B)
+    N, m, p = A.shape
+    n = B.shape[1]
+    Cm = np.empty((N, n, m))
+    _load().orc_amtam(N, p, m, n, A, B, Cm)
+    return Cm
+
+
+def astam(s, A):
+    """C_k = s_k A_k."""
+    s, A = _f64(s), _f64(A)
+    N, n, m = A.shape
+    out = np.empty_like(A)
+    _load().orc_astam(N, m, n, s, A, out)
+    return out
+
+
+def avtam(v, A):
+    """y_k = v_k^T A_k.  v: (N, p); A: (N, n, p) = pages p x n; y: (N, n)."""
+    v, A = _f64(v), _f64(A)
+    N, n, p = A.shape
+    y = np.empty((N, n))
+    _load().orc_avtam(N, p, n, v, A, y)
+    return y
+
+
+def amdet(A):
+    A = _f64(A)
+    N, n, _ = A.shape
+    out = np.empty(N)
+    _load().orc_amdet(N, n, A, out)
+    return out
+
+
+def aminv(A):
+    """Returns (Ainv, det, n_singular)."""
+    A = _f64(A)
+    N, n, _ = A.shape
+    inv = np.empty_like(A)
+    det = np.empty(N)
+    ns = _load().orc_aminv(N, n, A, inv, det.ctypes.data_as(C.c_void_p))
+    return inv, det, int(ns)
+
+
+# --------------------------------------------------------------------------
+# geometry and FE assembly (Sections 3.1, 3.2, 3.5)
+# --------------------------------------------------------------------------
+
+def vectors(dim, elems, coords):
+    """vectors3D pages: (ne, dim, dim) with [k, j, :] = x_{e_k[j]} - x_{e_k[dim]}."""
+    elems, coords = _i32(elems), _f64(coords)
+    ne, nlb = elems.shape
+    V = np.empty((ne, dim, dim))
+    _load().orc_vectors(dim, ne, nlb, elems, coords, V)
+    return V
+
+
+def volumes(dim, elems, coords):
+    """Returns (vol = |det|/dim!, signed det)."""
+    elems, coords = _i32(elems), _f64(coords)
+    ne, nlb = elems.shape
+    vol, det = np.empty(ne), np.empty(ne)
+    _load().orc_volumes(dim, ne, nlb, elems, coords, vol, det.ctypes.data_as(C.c_void_p))
+    return vol, det
+
+
+def simplex_normals(dim, elems, coords):
+    """Unnormalised facet normals (V^{-T} normalsRef): (ne, dim+1, dim); [k, j] is column j."""
+    elems, coords = _i32(elems), _f64(coords)
+    ne, nlb = elems.shape
+    out = np.empty((ne, dim + 1, dim))
+    _load().orc_simplex_normals(dim, ne, nlb, elems, coords, out)
+    return out
+
+
+def element_pages(dim, order, elems, coords, ca=1.0, cb=0.0, ckind=0):
+    """Returns (K3D, M3D, vol, coef); pages as (ne, nlb, nlb) with [k, q, p] = P_k(p, q).
+    Coefficient at the element's vertex centroid: ckind 0: a + b|x|^2; 1: a exp(b sum x)."""
+    elems, coords = _i32(elems), _f64(coords)
+    ne, nlb = elems.shape
+    K = np.empty((ne, nlb, nlb))
+    M = np.empty((ne, nlb, nlb))
+    vol, coef = np.empty(ne), np.empty(ne)
+    _load().orc_element_pages(dim, order, ne, nlb, elems, coords, ckind, ca, cb, K, M, vol, coef)
+    return K, M, vol, coef
+
+
+def csr_pattern(nn, elems):
+    """Sorted-unique (row, col) pattern of all element pairs: (row_ptr, col_idx)."""
+    elems = _i32(elems)
+    ne, nlb = elems.shape
+    lib = _load()
+    nnz = lib.orc_csr_pattern(nn, ne, nlb, elems, None, None)
+    if nnz < 0:
+        raise MemoryError("oracle pattern")
+    rp = np.zeros(nn + 1, dtype=np.int32)
+    ci = np.zeros(max(nnz, 1), dtype=np.int32)
+    lib.orc_csr_pattern(nn, ne, nlb, elems, rp.ctypes.data_as(C.c_void_p), ci.ctypes.data_as(C.c_void_p))
+    return rp, ci[:nnz]
+
+
+def csr_scatter(elems, pages, row_ptr, col_idx):
+    elems = _i32(elems)
+    ne, nlb = elems.shape
+    vals = np.zeros(len(col_idx))
+    rc = _load().orc_csr_scatter(ne, nlb, elems, _f64(pages), _i32(row_ptr), _i32(col_idx) if len(col_idx) else
+                                 np.zeros(1, np.int32), vals if len(vals) else np.zeros(1))
+    if rc != 0:
+        raise ValueError("pair missing from pattern")
+    return vals
+
+
+def assemble(dim, order, nn, elems, coords, ca=1.0, cb=0.0, pattern=None, want_pages=False, ckind=0):
+    """K and M in CSR (values FP64) plus volumes.  Returns a dict with
+    row_ptr, col_idx, K, M, vol and (optionally) K3D, M3D."""
+    elems, coords = _i32(elems), _f64(coords)
+    ne, nlb = elems.shape
+    rp, ci = pattern if pattern is not None else csr_pattern(nn, elems)
+    nnz = len(ci)
+    Kv, Mv, vol = np.zeros(max(nnz, 1)), np.zeros(max(nnz, 1)), np.zeros(max(ne, 1))
+    K3D = M3D = None
+    vp = None
+    if want_pages:
+        K3D = np.empty((ne, nlb, nlb))
+        M3D = np.empty((ne, nlb, nlb))
+    lib = _load()
+    rc = lib.orc_assemble(dim, order, nn, ne, nlb, elems, coords, ckind, ca, cb, _i32(rp),
+                          _i32(ci) if nnz else np.zeros(1, np.int32), Kv, Mv, vol,
+                          K3D.ctypes.data_as(C.c_void_p) if want_pages else vp,
+                          M3D.ctypes.data_as(C.c_void_p) if want_pages else vp)
+    if rc != 0:
+        raise ValueError("oracle assembly failed")
+    out = {"row_ptr": rp, "col_idx": ci, "K": Kv[:nnz], "M": Mv[:nnz], "vol": vol[:ne]}
+    if want_pages:
+        out["K3D"], out["M3D"] = K3D, M3D
+    return out
+
+
+def boundary(dim, nn, elems, coords, faces):
+    """Outward unit normals (nfb, dim) and facet measures (nfb,).  Returns
+    (normals, areas, n_missing_owner)."""
+    elems, coords, faces = _i32(elems), _f64(coords), _i32(faces)
+    ne, nlb = elems.shape
+    nfb = faces.shape[0]
+    nrm = np.empty((max(nfb, 1), dim))
+    ar = np.empty(max(nfb, 1))
+    miss = _load().orc_boundary(dim, nn, ne, nlb, elems, coords, nfb, faces if nfb else np.zeros((1, dim), np.int32),
+                                nrm, ar)
+    return nrm[:nfb], ar[:nfb], int(miss)
+
+
+def count_facets(dim, elems):
+    """(number of distinct facets, number of boundary facets)."""
+    elems = _i32(elems)
+    ne, nlb = elems.shape
+    a, b = _i64(0), _i64(0)
+    if _load().orc_count_facets(dim, ne, nlb, elems, C.byref(a), C.byref(b)) != 0:
+        raise MemoryError("oracle facets")
+    return int(a.value), int(b.value)
+
+
+def to_dense(nn, row_ptr, col_idx, vals):
+    """Dense nn x nn matrix of a CSR triple (test helper)."""
+    D = np.zeros((nn, nn))
+    for r in range(nn):
+        for q in range(row_ptr[r], row_ptr[r + 1]):
+            D[r, col_idx[q]] += vals[q]
+    return D
