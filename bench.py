@@ -1,0 +1,349 @@
+"""Benchmark: P1 tetrahedral stiffness + mass assembly into CSR on the unit cube.
+
+Workload (default): 64^3 cubes x 6 Kuhn tetrahedra = 1,572,864 tets, 274,625
+nodes, 4,018,753 CSR nonzeros, interior nodes jittered by U(-0.1h, 0.1h)
+(seed 0), coefficient c(x) = 1 + |x|^2 at the element centroid, mixed
+precision (FP32 element matrices, compensated determinant and CSR sums, FP64
+outputs), plus outward unit normals and areas of the 49,152 boundary
+triangles.  One step = vla_assemble (K, M, volumes) + vla_boundary on a
+resident mesh.
+
+  value   elements/s over all ranks, inputs resident in HBM, CUDA events
+          around each step, L2 flushed (512 MiB write) before every step.
+  e2e     the same metric host to host through the public API: pinned host
+          coords/elems/faces -> device, mesh build (CSR pattern + tiles),
+          assembly, boundary, CSR + values + volumes + normals -> pinned host.
+  roofline  the assembly kernel against the measured HBM copy bandwidth, with
+          the algorithmic bytes per element of the method (elements 16 B,
+          coordinates 24 nn/ne B, element-to-nonzero map 64 B, K and M values
+          16 nnz/ne B, volume 8 B).
+  cpu_baseline  the FP64 oracle (plain C, one thread) on the same mesh.
+
+Multi-GPU (torchrun): every rank assembles its own copy of the workload on its
+own GPU (independent problems, no collective on the data path); the reported
+time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return PEAKS_FALLBACK, "fallback"
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    for f in ("vla_assemble.cu", "vla_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2404_16039_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_from_profile(kernel_hash):
+    p = os.path.join(ROOT, "profiles", "assemble_p1tet64_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != kernel_hash:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        return dist, dist.get_rank(), ws, local
+    return None, 0, 1, 0
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def _max_over_ranks(dist, x):
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _alg_bytes_per_el(ne, nn, nnz):
+    return 16.0 + 24.0 * nn / ne + 64.0 + 16.0 * nnz / ne + 8.0
+
+
+def cpu_baseline(m, seconds=10.0):
+    """The oracle as it stands (single thread) on the same mesh; pattern built once."""
+    import oracle
+    pat = oracle.csr_pattern(m.nn, m.elems)
+    t0 = time.perf_counter()
+    reps = 0
+    while True:
+        oracle.assemble(3, 1, m.nn, m.elems, m.coords, 1.0, 1.0, pattern=pat)
+        oracle.boundary(3, m.nn, m.elems, m.coords, m.faces)
+        reps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return {"value": m.ne / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} full passes of the oracle assembly (K, M, volumes, CSR scatter) plus boundary "
+                      f"facets on the same {m.ne}-tet mesh, CSR pattern precomputed, 1 host thread"}
+
+
+def run_reference(args):
+    dist, rank, ws, _ = _dist()
+    if rank != 0:
+        return 0
+    import meshgen
+    m = meshgen.kuhn_cube(args.n, jitter=0.1, seed=0)
+    import oracle
+    pat = oracle.csr_pattern(m.nn, m.elems)
+    per_step = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.assemble(3, 1, m.nn, m.elems, m.coords, 1.0, 1.0, pattern=pat)
+        oracle.boundary(3, m.nn, m.elems, m.coords, m.faces)
+        if i >= args.warmup:
+            per_step.append(time.perf_counter() - t0)
+    dt = sum(per_step) / len(per_step)
+    val = m.ne / dt
+    line = {"metric": "elements/sec for P1 tet K+M to CSR", "value": val, "unit": "elements/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": _config(m, "fp64 oracle"),
+            "cpu_baseline": {"value": val, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step one full oracle pass over the {m.ne}-tet mesh, 1 host thread"},
+            "e2e": {"value": val, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(m, precision):
+    return {"workload": f"P1 tet K+M -> CSR + boundary normals/areas, unit cube {m.n}^3 cubes x 6 Kuhn tets "
+                        f"({m.ne} tets, {m.nn} nodes), interior jitter U(-0.1h,0.1h) seed 0, c(x)=1+|x|^2 "
+                        f"at the centroid",
+            "ne": m.ne, "nn": m.nn, "nfb": m.nfb, "precision": precision,
+            "l2": "flushed before every timed step (512 MiB write)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="vla", choices=["vla", "reference"])
+    ap.add_argument("--n", type=int, default=64, help="cubes per side")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import meshgen
+    import paper_2404_16039_gb300 as vla
+
+    dist, rank, ws, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = vla.PREC_MIXED if args.precision == "mixed" else vla.PREC_FP64
+    m = meshgen.kuhn_cube(args.n, jitter=0.1, seed=0)
+    coords = torch.from_numpy(m.coords).to(dev)
+    elems = torch.from_numpy(m.elems).to(dev)
+    faces = torch.from_numpy(m.faces).to(dev)
+    gm = vla.Mesh(coords, elems, faces)
+    K = torch.empty(gm.nnz, dtype=torch.float64, device=dev)
+    M = torch.empty(gm.nnz, dtype=torch.float64, device=dev)
+    vol = torch.empty(gm.ne, dtype=torch.float64, device=dev)
+    nrm = torch.empty((gm.nfb, 3), dtype=torch.float64, device=dev)
+    ar = torch.empty(gm.nfb, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        gm.assemble(1.0, 1.0, precision=prec, K=K, M=M, vol=vol)
+        gm.boundary(precision=prec, normals=nrm, areas=ar)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    _barrier(dist)
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.zero_()
+        e0, e1, e2 = ev[i]
+        e0.record(stream)
+        gm.assemble(1.0, 1.0, precision=prec, K=K, M=M, vol=vol)
+        e1.record(stream)
+        gm.boundary(precision=prec, normals=nrm, areas=ar)
+        e2.record(stream)
+    torch.cuda.synchronize()
+    _barrier(dist)
+    clocks = sampler.stop()
+    step_ms = [a.elapsed_time(c) for a, b, c in ev]
+    asm_ms = [a.elapsed_time(b) for a, b, c in ev]
+    ms = _max_over_ranks(dist, sum(step_ms) / len(step_ms))
+    asm = sum(asm_ms) / len(asm_ms)
+    value = ws * gm.ne / (ms * 1e-3)
+
+    # end to end through the public API with pinned host buffers
+    hc = torch.from_numpy(m.coords).pin_memory()
+    he = torch.from_numpy(m.elems).pin_memory()
+    hf = torch.from_numpy(m.faces).pin_memory()
+    out_host = {
+        "K": torch.empty(gm.nnz, dtype=torch.float64).pin_memory(),
+        "M": torch.empty(gm.nnz, dtype=torch.float64).pin_memory(),
+        "vol": torch.empty(gm.ne, dtype=torch.float64).pin_memory(),
+        "nrm": torch.empty((gm.nfb, 3), dtype=torch.float64).pin_memory(),
+        "ar": torch.empty(gm.nfb, dtype=torch.float64).pin_memory(),
+        "rp": torch.empty(gm.nn + 1, dtype=torch.int32).pin_memory(),
+        "ci": torch.empty(gm.nnz, dtype=torch.int32).pin_memory(),
+    }
+    h2d = hc.numel() * 8 + he.numel() * 4 + hf.numel() * 4
+    d2h = sum(t.numel() * t.element_size() for t in out_host.values())
+
+    def e2e_step():
+        dc = hc.to(dev, non_blocking=True)
+        de = he.to(dev, non_blocking=True)
+        df = hf.to(dev, non_blocking=True)
+        g2 = vla.Mesh(dc, de, df)
+        o = g2.assemble(1.0, 1.0, precision=prec)
+        n2, a2 = g2.boundary(precision=prec)
+        rp, ci = g2.csr()
+        out_host["K"].copy_(o["K"], non_blocking=True)
+        out_host["M"].copy_(o["M"], non_blocking=True)
+        out_host["vol"].copy_(o["vol"], non_blocking=True)
+        out_host["nrm"].copy_(n2, non_blocking=True)
+        out_host["ar"].copy_(a2, non_blocking=True)
+        out_host["rp"].copy_(rp, non_blocking=True)
+        out_host["ci"].copy_(ci, non_blocking=True)
+        torch.cuda.synchronize()
+        g2.close()
+
+    e2e_step()
+    _barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = _max_over_ranks(dist, (time.perf_counter() - t0) / args.e2e_steps)
+    e2e = {"value": ws * gm.ne / e2e_s, "unit": "elements/s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
+           "includes": "H2D of coords/elems/faces, mesh build (CSR pattern, tiles), assembly, boundary, "
+                       "D2H of row_ptr/col_idx/K/M/vol/normals/areas"}
+
+    peaks, src = _peaks()
+    bpe = _alg_bytes_per_el(gm.ne, gm.nn, gm.nnz)
+    achieved = bpe * gm.ne / (asm * 1e-3) / 1e9
+    khash = _src_hash()
+    roof = {"bound": "hbm", "kernel": "k_assemble<3,1,%s>" % ("mixed" if prec else "fp64"),
+            "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "peak_source": src,
+            "traffic": _traffic_from_profile(khash) if prec == vla.PREC_MIXED else None,
+            "alg_bytes_per_element": bpe, "kernel_ms": asm, "kernel_source_hash": khash}
+
+    line = {"metric": "elements/sec for P1 tet K+M to CSR", "value": value, "unit": "elements/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if prec == vla.PREC_MIXED else "f64", "data": "synthetic",
+            "config": _config(m, "mixed: f32 element matrices, float-float det and CSR sums, f64 outputs"
+                              if prec else "fp64"),
+            "e2e": e2e, "roofline": roof, "gpu_launches": 2 * args.steps, "clocks": clocks,
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99))}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(m, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    gm.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,204 @@
+/*
+ * vla.h -- C ABI of libvla: page-wise tiny-matrix algebra and P1/P2 simplex
+ * stiffness/mass assembly into CSR on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: "On a vectorized basic linear algebra package for prototyping codes
+ * in MATLAB", arXiv:2404.16039.  Each entry point names the passage that
+ * defines the operation it computes.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Status: every call returns vla_status.  0 is success, > 0 a warning, < 0
+ *    an error.  No call aborts, traps or throws across the ABI.  The message
+ *    of the most recent failure on the calling host thread is available from
+ *    vla_last_error().
+ *  - Memory: unless a parameter says "host", every array pointer is a DEVICE
+ *    pointer owned by the caller, on the current CUDA device.  The library
+ *    never frees caller memory.  Handles (vla_mesh) own the device memory they
+ *    allocate and release it in their destroy call.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  Work is enqueued on it; calls return without waiting
+ *    unless stated otherwise.  Outputs are valid once the stream reaches them.
+ *  - Indices are 0-based int32.  Counts above 2^31-1 are rejected with
+ *    VLA_ERR_INVALID_ARG.
+ *  - Page arrays (the paper's "am"/"av"/"as" arrays, Section 2.4) hold N small
+ *    matrices.  VLA_LAYOUT_PAGE: an n x m x N array in column-major order, so
+ *    entry (r, c) of page k is at k*n*m + r + c*n (each page contiguous, the
+ *    MATLAB layout).  VLA_LAYOUT_SOA: entry (r, c) of page k is at
+ *    (r + c*n)*N + k (page index fastest).  Vectors are n x N (page layout:
+ *    k*n + r; SoA: r*N + k); scalars are N contiguous values.
+ *  - Mesh arrays (Section 3, "coords" and "elems"): coords is dim x nn FP64
+ *    column-major (node i's coordinates contiguous: coords[i*dim + d]);
+ *    elems is nlb x ne int32 column-major (element k's nodes contiguous:
+ *    elems[k*nlb + j]), nlb = dim+1 for P1 and (dim+1)(dim+2)/2 for P2.  P2
+ *    local numbering: vertices first, then mid-edge nodes in the order
+ *    2-D (1,2),(2,3),(1,3); 3-D (1,2),(2,3),(1,3),(1,4),(2,4),(3,4)
+ *    (1-based local vertices).
+ */
+#ifndef VLA_H
+#define VLA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t vla_status;
+
+enum {
+    VLA_OK = 0,
+    VLA_WARN_SINGULAR = 1,     /* some pages/elements had det == 0 (IEEE inf/nan in their outputs) */
+    VLA_ERR_INVALID_ARG = -1,  /* bad size, null pointer, unsupported shape or flag */
+    VLA_ERR_INDEX_OOB = -2,    /* an element or facet references a node outside [0, nn) */
+    VLA_ERR_OOM = -3,          /* device allocation failed */
+    VLA_ERR_CUDA = -4,         /* a CUDA runtime call failed (message has the CUDA error) */
+    VLA_ERR_TIMEOUT = -5,      /* a bounded wait expired */
+    VLA_ERR_BUDGET = -6,       /* request exceeds the configured memory budget */
+    VLA_ERR_DEGENERATE = -7,   /* an element repeats a node, or a facet has no owning element */
+    VLA_ERR_UNSUPPORTED = -8   /* mesh outside the implemented limits (row length, element count) */
+};
+
+enum { VLA_F32 = 0, VLA_F64 = 1 };                      /* dtype */
+enum { VLA_LAYOUT_PAGE = 0, VLA_LAYOUT_SOA = 1 };        /* page-array layout */
+enum { VLA_P1 = 1, VLA_P2 = 2 };                         /* element order */
+enum { VLA_PREC_FP64 = 0, VLA_PREC_MIXED = 1 };          /* assembly precision */
+enum { VLA_COEFF_POLY = 0, VLA_COEFF_EXP = 1 };          /* coefficient kind */
+
+/* Library version, 100*major + minor. */
+int32_t vla_version(void);
+
+/* Copies the last error message of the calling thread into buf (NUL
+ * terminated, truncated to len).  Returns the full message length. */
+size_t vla_last_error(char *buf, size_t len);
+
+/* ------------------------------------------------------------------------ */
+/* Page primitives (Section 2.4, "A vectorization library")                  */
+/* dtype: VLA_F32 or VLA_F64 (all arrays of the call share it).  Shapes      */
+/* p, m, n in {2, 3}.  N >= 0; N == 0 is a no-op.  Arrays must not overlap.  */
+/* ------------------------------------------------------------------------ */
+
+/* amtam: C_k = A_k^T B_k for every page k.  A: p x m x N, B: p x n x N,
+ * C: m x n x N.  (Section 2.4 lists amtam as the product of one page array
+ * with the transpose of another and identifies it with
+ * pagemtimes(amx,'transpose',ama,'none'); its use amtam(dphi3D,dphi3D) in the
+ * P1 stiffness listing of Section 3.5 fixes the reading transpose(A)*B.) */
+vla_status vla_amtam(int32_t dtype, int32_t layout, int64_t N, int32_t p, int32_t m, int32_t n, const void *A,
+                     const void *B, void *C, void *stream);
+
+/* astam: C_k = s_k A_k (page-wise scalar multiplication Id (x) pi, Section
+ * 2.2 and the astam example of Section 2.4).  s: N scalars, A and C m x n x N. */
+vla_status vla_astam(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t n, const void *s, const void *A,
+                     void *C, void *stream);
+
+/* avtam: y_k = v_k^T A_k (row vector times page, Section 2.4).  v: p x N,
+ * A: p x n x N, y: n x N. */
+vla_status vla_avtam(int32_t dtype, int32_t layout, int64_t N, int32_t p, int32_t n, const void *v, const void *A,
+                     void *y, void *stream);
+
+/* amdet: det_k = det(A_k), signed (page-wise determinant det_W of Section
+ * 2.3; the signed value -25/64 * 6 of the Section 3.2 example).  A: n x n x N,
+ * det: N values. */
+vla_status vla_amdet(int32_t dtype, int32_t layout, int64_t N, int32_t n, const void *A, void *det, void *stream);
+
+/* aminv: Ainv_k = A_k^{-1} (page-wise inverse of Section 2.3, pageinv) and,
+ * if det != NULL, det_k.  The paper defines the inverse only where det != 0;
+ * a page with det == 0 gets IEEE inf/nan entries and is counted.
+ * n_singular: NULL, or a DEVICE int64 that receives the number of singular
+ * pages (overwritten, not accumulated).  Returns VLA_OK; singular pages are
+ * reported through n_singular only (the count lives on the device). */
+vla_status vla_aminv(int32_t dtype, int32_t layout, int64_t N, int32_t n, const void *A, void *Ainv, void *det,
+                     int64_t *n_singular, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Meshes and assembly (Sections 3.1-3.5)                                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct vla_mesh vla_mesh;
+
+typedef struct {
+    int32_t dim, order, nlb;
+    int64_t nn, ne, nfb, nnz;
+    int32_t max_row_len;     /* longest CSR row */
+    int32_t n_tiles;         /* row tiles of the assembly kernel */
+    int64_t device_bytes;    /* device memory held by the handle */
+    int64_t tile_elems;      /* element computations per assembly (sum over tiles; >= ne) */
+    int64_t n_codes;         /* contribution codes streamed per assembly (including padding) */
+} vla_mesh_info_t;
+
+/* Ingests a simplicial mesh and builds, on the device, everything the
+ * assembly needs: the CSR pattern of sparse(X3D(:),Y3D(:),.,nn,nn) of
+ * Section 3.5 (every (elems(k,i), elems(k,j)) pair, duplicates merged,
+ * explicit zeros kept, columns ascending), node->element incidence, the row
+ * tiles of the assembly kernel and the owner of every boundary facet.
+ *   dim 2 or 3; order VLA_P1 or VLA_P2; nn, ne >= 1.
+ *   coords: dim x nn FP64 (device); elems: nlb x ne int32 (device).
+ *   faces:  dim x nfb int32 (device) boundary facets given by vertex nodes
+ *           (triangles in 3-D, edges in 2-D), any orientation; NULL if nfb 0.
+ * Validation: node indices outside [0, nn) -> VLA_ERR_INDEX_OOB; an element
+ * that repeats a node, or a facet no element owns -> VLA_ERR_DEGENERATE; a CSR
+ * row longer than 255 entries or ne >= 2^27 -> VLA_ERR_UNSUPPORTED.
+ * Synchronises `stream` (the build sizes depend on device results).  The
+ * handle keeps its own copies of coords/elems/faces; the caller's arrays may
+ * be freed afterwards. */
+vla_status vla_mesh_create(int32_t dim, int32_t order, int64_t nn, int64_t ne, const double *coords,
+                           const int32_t *elems, int64_t nfb, const int32_t *faces, void *stream, vla_mesh **out);
+
+/* Fills *info (host struct). */
+vla_status vla_mesh_info(const vla_mesh *mesh, vla_mesh_info_t *info);
+
+/* Copies the CSR pattern to caller buffers (device): row_ptr nn+1 int32,
+ * col_idx nnz int32.  Either may be NULL. */
+vla_status vla_mesh_csr(const vla_mesh *mesh, int32_t *row_ptr, int32_t *col_idx, void *stream);
+
+/* Assembles K and M (Section 3.5 stiffness and mass listings) into the
+ * mesh's CSR pattern:
+ *   K_ij = sum_k c_k int_{T_k} grad phi_i . grad phi_j,
+ *   M_ij = sum_k c_k int_{T_k} phi_i phi_j,
+ * where c_k is the coefficient evaluated at the vertex centroid x_c of T_k:
+ *   VLA_COEFF_POLY: c = ca + cb |x_c|^2;  VLA_COEFF_EXP: c = ca exp(cb sum_d x_c,d).
+ * P1 integrals are exact; P2 stiffness uses the 4-point rule (exact for the
+ * quadratic integrand of affine elements) and P2 mass the exact reference
+ * mass matrix.  Outputs (device, FP64, any may be NULL):
+ *   K_vals, M_vals: nnz values in the mesh's CSR order;
+ *   vol: ne element measures |det V_k| / dim! (Section 3.2 volume script);
+ *   K_pages, M_pages: the element matrices K3D, M3D as nlb x nlb x ne
+ *   column-major pages (second output of the Section 3.5 listings).
+ * precision: VLA_PREC_FP64 computes everything in FP64.  VLA_PREC_MIXED
+ *   forms element matrices in FP32 from coordinates stored as float pairs;
+ *   the edge vectors are exact to float rounding, the 2x2 cofactors use
+ *   Kahan's FMA determinant, det uses a compensated dot product, and every CSR
+ *   value is a compensated (float-float) sum converted to FP64 once.
+ * If n_singular != NULL (device int64), it receives the number of elements
+ * with det == 0.  Deterministic: the same inputs give bit-identical outputs. */
+vla_status vla_assemble(const vla_mesh *mesh, int32_t coeff_kind, double ca, double cb, int32_t precision,
+                        double *K_vals, double *M_vals, double *vol, double *K_pages, double *M_pages,
+                        int64_t *n_singular, void *stream);
+
+/* Boundary facets (Section 3.2 normals of boundary faces; the areas used by
+ * the surface integrals of Section 3.4): for facet f with vertex nodes
+ * (x1, x2[, x3]) the normal n = (x2-x1) x (x3-x1) (3-D) or the edge vector
+ * rotated by -90 degrees (2-D), oriented away from the remaining vertex of
+ * the owning element, normalised to unit length; areas[f] = |n|/2 (3-D) or
+ * the edge length (2-D).  normals: dim x nfb FP64 (facet f at f*dim + d),
+ * areas: nfb FP64 (device).  precision as in vla_assemble. */
+vla_status vla_boundary(const vla_mesh *mesh, int32_t precision, double *normals, double *areas, void *stream);
+
+/* Unnormalised outer normals of all element facets,
+ * normals3D_k = (vectors3D_k)^{-T} normalsRef (Section 3.2, with the normal
+ * transform X = A^{-T} of Section 2.3).  vectors3D_k holds x_j - x_last as
+ * columns; normalsRef columns are -e_1..-e_dim and (1,..,1); column j is the
+ * normal of the facet opposite local vertex j.  normals: dim x (dim+1) x ne
+ * FP64 column-major pages (device). FP64 arithmetic. */
+vla_status vla_simplex_normals(const vla_mesh *mesh, double *normals, void *stream);
+
+/* Releases the handle and its device memory (stream-ordered on the stream
+ * the mesh was created with, which is synchronised first).  NULL is a no-op. */
+vla_status vla_mesh_destroy(vla_mesh *mesh);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VLA_H */

@@ -1,0 +1,291 @@
+"""Python binding of libvla (GB300 page-wise linear algebra and FE assembly).
+
+Argument marshalling only: every computation happens in the CUDA kernels of
+``libvla.so`` behind the C ABI declared in ``include/vla.h``.  PyTorch
+supplies device memory and the current CUDA stream.  There is no CPU path:
+if the shared library is missing or fails to load, every call raises.
+
+Shapes (torch tensors on the current CUDA device, C-contiguous):
+  page layout  (N, cols, rows)  -- page k is a column-major rows x cols matrix,
+                                   exactly the paper's n x m x N array;
+  SoA layout   (cols, rows, N)  -- entry (r, c) of page k at [c, r, k].
+  mesh coords  (nn, dim) float64, elems (ne, nlb) int32, faces (nfb, dim) int32.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import torch
+
+__all__ = [
+    "VlaError", "lib", "version", "amtam", "astam", "avtam", "amdet", "aminv", "Mesh",
+    "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP",
+]
+
+F32, F64 = 0, 1
+LAYOUT_PAGE, LAYOUT_SOA = 0, 1
+PREC_FP64, PREC_MIXED = 0, 1
+COEFF_POLY, COEFF_EXP = 0, 1
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvla.so")
+_lock = threading.Lock()
+_lib = None
+
+
+class VlaError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"vla status {status}: {message}")
+        self.status = status
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("order", C.c_int32), ("nlb", C.c_int32),
+                ("nn", C.c_int64), ("ne", C.c_int64), ("nfb", C.c_int64), ("nnz", C.c_int64),
+                ("max_row_len", C.c_int32), ("n_tiles", C.c_int32), ("device_bytes", C.c_int64),
+                ("tile_elems", C.c_int64), ("n_codes", C.c_int64)]
+
+
+def lib():
+    """The loaded libvla.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                              "(python paper_2404_16039_gb300/build.py)")
+        L = C.CDLL(LIB_PATH)
+        vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        L.vla_version.restype = i32
+        L.vla_last_error.argtypes = [C.c_char_p, C.c_size_t]
+        L.vla_last_error.restype = C.c_size_t
+        L.vla_amtam.argtypes = [i32, i32, i64, i32, i32, i32, vp, vp, vp, vp]
+        L.vla_astam.argtypes = [i32, i32, i64, i32, i32, vp, vp, vp, vp]
+        L.vla_avtam.argtypes = [i32, i32, i64, i32, i32, vp, vp, vp, vp]
+        L.vla_amdet.argtypes = [i32, i32, i64, i32, vp, vp, vp]
+        L.vla_aminv.argtypes = [i32, i32, i64, i32, vp, vp, vp, vp, vp]
+        L.vla_mesh_create.argtypes = [i32, i32, i64, i64, vp, vp, i64, vp, vp, C.POINTER(vp)]
+        L.vla_mesh_info.argtypes = [vp, C.POINTER(MeshInfo)]
+        L.vla_mesh_csr.argtypes = [vp, vp, vp, vp]
+        L.vla_assemble.argtypes = [vp, i32, dbl, dbl, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.vla_boundary.argtypes = [vp, i32, vp, vp, vp]
+        L.vla_simplex_normals.argtypes = [vp, vp, vp]
+        L.vla_mesh_destroy.argtypes = [vp]
+        for name in ("vla_amtam", "vla_astam", "vla_avtam", "vla_amdet", "vla_aminv", "vla_mesh_create",
+                     "vla_mesh_info", "vla_mesh_csr", "vla_assemble", "vla_boundary", "vla_simplex_normals",
+                     "vla_mesh_destroy"):
+            getattr(L, name).restype = i32
+        _lib = L
+        return L
+
+
+def _check(st: int):
+    if st < 0:
+        buf = C.create_string_buffer(1024)
+        lib().vla_last_error(buf, 1024)
+        raise VlaError(st, buf.value.decode(errors="replace"))
+    return st
+
+
+def version() -> int:
+    return lib().vla_version()
+
+
+def _p(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t):
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise TypeError("page arrays must be float32 or float64")
+
+
+def _req(t, dtype=None):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return t
+
+
+def _page_dims(A, layout):
+    # returns (N, rows, cols)
+    if layout == LAYOUT_PAGE:
+        N, cols, rows = A.shape
+    else:
+        cols, rows, N = A.shape
+    return N, rows, cols
+
+
+def _new_pages(N, rows, cols, layout, like):
+    shape = (N, cols, rows) if layout == LAYOUT_PAGE else (cols, rows, N)
+    return torch.empty(shape, dtype=like.dtype, device=like.device)
+
+
+def _new_vec(N, n, layout, like):
+    shape = (N, n) if layout == LAYOUT_PAGE else (n, N)
+    return torch.empty(shape, dtype=like.dtype, device=like.device)
+
+
+# ---------------------------------------------------------------------------
+# page primitives
+# ---------------------------------------------------------------------------
+
+def amtam(A, B, out=None, layout=LAYOUT_PAGE, stream=None):
+    """C_k = A_k^T B_k (amtam).  A: p x m pages, B: p x n pages -> m x n pages."""
+    _req(A), _req(B)
+    N, p, m = _page_dims(A, layout)
+    N2, p2, n = _page_dims(B, layout)
+    if N2 != N or p2 != p or A.dtype != B.dtype:
+        raise ValueError("amtam: page counts, row counts and dtypes must match")
+    out = _new_pages(N, m, n, layout, A) if out is None else _req(out, A.dtype)
+    _check(lib().vla_amtam(_dtype_code(A), layout, N, p, m, n, _p(A), _p(B), _p(out), _stream(stream)))
+    return out
+
+
+def astam(s, A, out=None, layout=LAYOUT_PAGE, stream=None):
+    """C_k = s_k A_k (astam)."""
+    _req(s, A.dtype), _req(A)
+    N, m, n = _page_dims(A, layout)
+    if s.numel() != N:
+        raise ValueError("astam: one scalar per page")
+    out = _new_pages(N, m, n, layout, A) if out is None else _req(out, A.dtype)
+    _check(lib().vla_astam(_dtype_code(A), layout, N, m, n, _p(s), _p(A), _p(out), _stream(stream)))
+    return out
+
+
+def avtam(v, A, out=None, layout=LAYOUT_PAGE, stream=None):
+    """y_k = v_k^T A_k (avtam).  v: (N, p) page layout or (p, N) SoA."""
+    _req(v, A.dtype), _req(A)
+    N, p, n = _page_dims(A, layout)
+    if v.numel() != N * p:
+        raise ValueError("avtam: v must hold p values per page")
+    out = _new_vec(N, n, layout, A) if out is None else _req(out, A.dtype)
+    _check(lib().vla_avtam(_dtype_code(A), layout, N, p, n, _p(v), _p(A), _p(out), _stream(stream)))
+    return out
+
+
+def amdet(A, out=None, layout=LAYOUT_PAGE, stream=None):
+    """Signed page determinants (amdet)."""
+    _req(A)
+    N, n, n2 = _page_dims(A, layout)
+    if n != n2:
+        raise ValueError("amdet: square pages required")
+    out = torch.empty(N, dtype=A.dtype, device=A.device) if out is None else _req(out, A.dtype)
+    _check(lib().vla_amdet(_dtype_code(A), layout, N, n, _p(A), _p(out), _stream(stream)))
+    return out
+
+
+def aminv(A, out=None, det=None, want_det=True, count_singular=True, layout=LAYOUT_PAGE, stream=None):
+    """Page inverses (aminv).  Returns (Ainv, det or None, n_singular device tensor or None)."""
+    _req(A)
+    N, n, n2 = _page_dims(A, layout)
+    if n != n2:
+        raise ValueError("aminv: square pages required")
+    out = torch.empty_like(A) if out is None else _req(out, A.dtype)
+    if want_det and det is None:
+        det = torch.empty(N, dtype=A.dtype, device=A.device)
+    ns = torch.zeros(1, dtype=torch.int64, device=A.device) if count_singular else None
+    _check(lib().vla_aminv(_dtype_code(A), layout, N, n, _p(A), _p(out), _p(det) if want_det else None, _p(ns),
+                           _stream(stream)))
+    return out, (det if want_det else None), ns
+
+
+# ---------------------------------------------------------------------------
+# meshes
+# ---------------------------------------------------------------------------
+
+class Mesh:
+    """A mesh resident on the device with its CSR pattern and assembly tiles
+    (vla_mesh_create).  ``coords`` (nn, dim) float64 and ``elems`` (ne, nlb)
+    int32 are CUDA tensors; ``faces`` (nfb, dim) int32 or None."""
+
+    def __init__(self, coords, elems, faces=None, order=1, stream=None):
+        _req(coords, torch.float64), _req(elems, torch.int32)
+        if faces is not None:
+            _req(faces, torch.int32)
+        nn, dim = coords.shape
+        ne = elems.shape[0]
+        nfb = 0 if faces is None else faces.shape[0]
+        h = C.c_void_p()
+        _check(lib().vla_mesh_create(dim, order, nn, ne, _p(coords), _p(elems), nfb, _p(faces), _stream(stream),
+                                     C.byref(h)))
+        self._h = h
+        info = MeshInfo()
+        _check(lib().vla_mesh_info(h, C.byref(info)))
+        self.dim, self.order, self.nlb = info.dim, info.order, info.nlb
+        self.nn, self.ne, self.nfb, self.nnz = info.nn, info.ne, info.nfb, info.nnz
+        self.max_row_len, self.n_tiles, self.device_bytes = info.max_row_len, info.n_tiles, info.device_bytes
+        self.tile_elems, self.n_codes = info.tile_elems, info.n_codes
+        self.device = coords.device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vla_mesh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def csr(self, stream=None):
+        rp = torch.empty(self.nn + 1, dtype=torch.int32, device=self.device)
+        ci = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=self.device)
+        _check(lib().vla_mesh_csr(self._h, _p(rp), _p(ci), _stream(stream)))
+        return rp, ci[: self.nnz]
+
+    def assemble(self, ca=1.0, cb=0.0, kind=COEFF_POLY, precision=PREC_MIXED, K=None, M=None, vol=None,
+                 want_K=True, want_M=True, want_vol=True, pages=False, count_singular=False, stream=None):
+        """K and M values in CSR order (FP64), element volumes and optionally the
+        element pages (ne, nlb, nlb).  Returns a dict of tensors."""
+        dev = self.device
+        f64 = torch.float64
+        if want_K and K is None:
+            K = torch.empty(self.nnz, dtype=f64, device=dev)
+        if want_M and M is None:
+            M = torch.empty(self.nnz, dtype=f64, device=dev)
+        if want_vol and vol is None:
+            vol = torch.empty(self.ne, dtype=f64, device=dev)
+        Kp = torch.empty((self.ne, self.nlb, self.nlb), dtype=f64, device=dev) if pages else None
+        Mp = torch.empty((self.ne, self.nlb, self.nlb), dtype=f64, device=dev) if pages else None
+        ns = torch.zeros(1, dtype=torch.int64, device=dev) if count_singular else None
+        _check(lib().vla_assemble(self._h, kind, float(ca), float(cb), precision,
+                                  _p(K) if want_K else None, _p(M) if want_M else None,
+                                  _p(vol) if want_vol else None, _p(Kp), _p(Mp), _p(ns), _stream(stream)))
+        out = {"K": K if want_K else None, "M": M if want_M else None, "vol": vol if want_vol else None}
+        if pages:
+            out["K3D"], out["M3D"] = Kp, Mp
+        if count_singular:
+            out["n_singular"] = ns
+        return out
+
+    def boundary(self, precision=PREC_MIXED, normals=None, areas=None, stream=None):
+        """Outward unit normals (nfb, dim) and facet measures (nfb,)."""
+        dev = self.device
+        if normals is None:
+            normals = torch.empty((max(self.nfb, 1), self.dim), dtype=torch.float64, device=dev)[: self.nfb]
+        if areas is None:
+            areas = torch.empty(max(self.nfb, 1), dtype=torch.float64, device=dev)[: self.nfb]
+        _check(lib().vla_boundary(self._h, precision, _p(normals), _p(areas), _stream(stream)))
+        return normals, areas
+
+    def simplex_normals(self, stream=None):
+        """Unnormalised facet normals of every element: (ne, dim+1, dim), [k, j] = column j."""
+        out = torch.empty((self.ne, self.dim + 1, self.dim), dtype=torch.float64, device=self.device)
+        _check(lib().vla_simplex_normals(self._h, _p(out), _stream(stream)))
+        return out

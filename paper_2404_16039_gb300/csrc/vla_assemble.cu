@@ -1,0 +1,932 @@
+// vla_assemble.cu -- P1/P2 simplex stiffness and mass assembly into CSR
+// (Section 3.5 stiffness/mass listings and their sparse() scatter), boundary
+// facet normals and areas, and all-facet normals (Section 3.2).
+//
+// One CTA per row tile (built in vla_mesh.cu):
+//   phase 0  the tile's vertex coordinates -> shared memory;
+//   phase 1  every element touching the tile's rows: Jacobian, determinant,
+//            cofactors, coefficient at the centroid, element matrix K_k and
+//            mass scale -> shared memory (owned elements also write volume
+//            and, on request, the K3D/M3D pages);
+//   phase 2  every nonzero of the tile sums its contribution list (ascending
+//            element id) from shared memory and writes its FP64 value once.
+// No atomics, no global gathers in the hot loop; the order of every sum is
+// fixed by the mesh, so results are bit-reproducible.
+//
+// Geometry (Sections 3.1-3.2): vectors3D V = [x_0 - x_d, ..., x_{d-1} - x_d];
+// the cofactor vectors C_j (rows of adj V) give grad lambda_j = C_j / det V
+// for j < d and C_d = -sum_j C_j.  P1: K_k(a,b) = c_k (C_a.C_b) / (d! |det V|),
+// M_k = c_k |det V| / d! * (1 + delta_ab) / ((d+1)(d+2)).  P2: the same
+// cofactor products weighted by reference tensors from the 4-point rule.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <type_traits>
+
+#include "vla_internal.cuh"
+
+namespace vla {
+namespace {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// P2 reference tables (built on the host once per device)
+// ---------------------------------------------------------------------------
+struct P2Tab {
+    // stiffness: K_pq = sc * sum_t coef[u][t] * Cd[st[u][t]], u = packed (p<=q)
+    unsigned char nterm[55];
+    unsigned char st[55][4];
+    float coef_f[55][4];
+    double coef_d[55][4];
+    float mhat_f[55];
+    double mhat_d[55];
+};
+__constant__ P2Tab c_p2[2];   // [0] = 2-D (6 nodes), [1] = 3-D (10 nodes)
+
+int packed_index(int p, int q, int n) {  // p <= q
+    return p * n - p * (p - 1) / 2 + (q - p);
+}
+
+void p2_edges(int dim, int e, int &a, int &b) {
+    static const int E2[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+    static const int E3[6][2] = {{0, 1}, {1, 2}, {0, 2}, {0, 3}, {1, 3}, {2, 3}};
+    a = dim == 2 ? E2[e][0] : E3[e][0];
+    b = dim == 2 ? E2[e][1] : E3[e][1];
+}
+
+// d(phi_p)/d(lambda_s) at barycentric point lam
+double p2_dphi(int dim, int p, int s, const double *lam) {
+    if (p <= dim) return (s == p) ? 4.0 * lam[p] - 1.0 : 0.0;
+    int a, b;
+    p2_edges(dim, p - dim - 1, a, b);
+    if (s == a) return 4.0 * lam[b];
+    if (s == b) return 4.0 * lam[a];
+    return 0.0;
+}
+
+double p2_phi(int dim, int p, const double *lam) {
+    if (p <= dim) return lam[p] * (2.0 * lam[p] - 1.0);
+    int a, b;
+    p2_edges(dim, p - dim - 1, a, b);
+    return 4.0 * lam[a] * lam[b];
+}
+
+void build_p2_table(int dim, P2Tab &T) {
+    const int n = dim == 2 ? 6 : 10, nv = dim + 1;
+    // stiffness rule: 4 points, weights normalised to sum 1
+    std::vector<std::vector<double>> pts;
+    std::vector<double> wts;
+    if (dim == 3) {
+        const double a = 0.5854101966249685, b = 0.1381966011250105;
+        for (int i = 0; i < 4; ++i) {
+            std::vector<double> l(4, b);
+            l[i] = a;
+            pts.push_back(l);
+            wts.push_back(0.25);
+        }
+    } else {
+        pts.push_back({1.0 / 3, 1.0 / 3, 1.0 / 3});
+        wts.push_back(-27.0 / 48.0);
+        for (int i = 0; i < 3; ++i) {
+            std::vector<double> l(3, 0.2);
+            l[i] = 0.6;
+            pts.push_back(l);
+            wts.push_back(25.0 / 48.0);
+        }
+    }
+    std::memset(&T, 0, sizeof(T));
+    for (int p = 0; p < n; ++p)
+        for (int q = p; q < n; ++q) {
+            int u = packed_index(p, q, n);
+            double acc[16] = {0};
+            for (int s = 0; s < nv; ++s)
+                for (int t = 0; t < nv; ++t)
+                    for (size_t g = 0; g < pts.size(); ++g)
+                        acc[std::min(s, t) * nv + std::max(s, t)] +=
+                            wts[g] * p2_dphi(dim, p, s, pts[g].data()) * p2_dphi(dim, q, t, pts[g].data());
+            int nt = 0;
+            for (int s = 0; s < nv; ++s)
+                for (int t = s; t < nv; ++t) {
+                    double v = acc[s * nv + t];
+                    if (std::fabs(v) < 1e-14) continue;
+                    T.st[u][nt] = (unsigned char)packed_index(s, t, nv);
+                    T.coef_d[u][nt] = v;
+                    T.coef_f[u][nt] = (float)v;
+                    ++nt;
+                }
+            T.nterm[u] = (unsigned char)nt;
+        }
+    // mass: collapsed Gauss-Legendre product rule (4 points per direction),
+    // exact for the quartic integrand; normalised by the reference measure
+    const double gx[4] = {-0.8611363115940526, -0.3399810435848563, 0.3399810435848563, 0.8611363115940526};
+    const double gw[4] = {0.3478548451374538, 0.6521451548625461, 0.6521451548625461, 0.3478548451374538};
+    double M[10][10] = {{0}};
+    double refvol = dim == 2 ? 0.5 : 1.0 / 6.0;
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j)
+            for (int k = 0; k < (dim == 3 ? 4 : 1); ++k) {
+                double a = 0.5 * (gx[i] + 1), b = 0.5 * (gx[j] + 1), c = 0.5 * (gx[k] + 1);
+                double xi[3], w;
+                if (dim == 2) {
+                    xi[0] = a;
+                    xi[1] = b * (1 - a);
+                    w = 0.25 * gw[i] * gw[j] * (1 - a);
+                } else {
+                    xi[0] = a;
+                    xi[1] = b * (1 - a);
+                    xi[2] = c * (1 - a) * (1 - b);
+                    w = 0.125 * gw[i] * gw[j] * gw[k] * (1 - a) * (1 - a) * (1 - b);
+                }
+                double lam[4];
+                double sum = 0;
+                for (int d = 0; d < dim; ++d) {
+                    lam[d] = xi[d];
+                    sum += xi[d];
+                }
+                lam[dim] = 1 - sum;
+                for (int p = 0; p < n; ++p)
+                    for (int q = 0; q < n; ++q) M[p][q] += w * p2_phi(dim, p, lam) * p2_phi(dim, q, lam);
+            }
+    for (int p = 0; p < n; ++p)
+        for (int q = p; q < n; ++q) {
+            int u = packed_index(p, q, n);
+            T.mhat_d[u] = M[p][q] / refvol;
+            T.mhat_f[u] = (float)T.mhat_d[u];
+        }
+}
+
+std::mutex g_tab_mu;
+bool g_tab_done[64] = {false};
+
+vla_status ensure_p2_tables() {
+    int dev = 0;
+    VLA_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(VLA_ERR_INVALID_ARG, "device ordinal %d not supported", dev);
+    std::lock_guard<std::mutex> lk(g_tab_mu);
+    if (g_tab_done[dev]) return VLA_OK;
+    P2Tab t[2];
+    build_p2_table(2, t[0]);
+    build_p2_table(3, t[1]);
+    VLA_CUDA(cudaMemcpyToSymbol(c_p2, t, sizeof(t)));
+    g_tab_done[dev] = true;
+    return VLA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// element geometry
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Geo {
+    T C[4][3];   // cofactor vectors (C_d = -sum)
+    T det;       // signed det V (rounded)
+    T xc[3];     // vertex centroid
+};
+
+// exact difference a - b = s + e (TwoSum with a negated operand)
+__device__ __forceinline__ void two_diff(float a, float b, float &s, float &e) { two_sum(a, -b, s, e); }
+
+// Mixed precision, 3-D.  V = Vh + Vl is the edge vector as a normalised
+// float pair (Vh = fl(V), |Vl| <= ulp(Vh)/2), built error-free from the
+// coordinate pairs; det V =
+// det(Vh) (evaluated with an error-free cross product and a compensated dot
+// product) + sum_j Vl_j . C_j (first-order correction; the remainder is
+// O(|Vl|^2) ~ 2^-48 relative).
+__device__ __forceinline__ void geo_mixed3(const float4 *__restrict__ sh, const float4 *__restrict__ sl, ushort4 v,
+                                           Geo<float> &g) {
+    const float4 h3 = sh[v.w], l3 = sl[v.w];
+    float Vh[3][3], Vl[3][3];
+    const unsigned short vi[3] = {v.x, v.y, v.z};
+    float hs[3] = {h3.x, h3.y, h3.z};
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float4 hj = sh[vi[j]], lj = sl[vi[j]];
+        const float hjc[3] = {hj.x, hj.y, hj.z}, ljc[3] = {lj.x, lj.y, lj.z}, h3c[3] = {h3.x, h3.y, h3.z},
+                    l3c[3] = {l3.x, l3.y, l3.z};
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float s, e;
+            two_diff(hjc[c], h3c[c], s, e);
+            // renormalise so that |Vl| <= ulp(Vh)/2 even far from the origin,
+            // where the lo parts are not small next to the edge length
+            two_sum(s, __fadd_rn(e, __fsub_rn(ljc[c], l3c[c])), Vh[j][c], Vl[j][c]);
+        }
+        hs[0] += hj.x;
+        hs[1] += hj.y;
+        hs[2] += hj.z;
+    }
+    // C0 = Vh1 x Vh2 in float-float (exact products, one rounding in t)
+    float s0[3], t0[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+        float p1, e1, p2, e2, s, es;
+        two_prod(Vh[1][c1], Vh[2][c2], p1, e1);
+        two_prod(Vh[1][c2], Vh[2][c1], p2, e2);
+        two_sum(p1, -p2, s, es);
+        s0[c] = s;
+        t0[c] = __fadd_rn(es, __fsub_rn(e1, e2));
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+        g.C[0][c] = __fadd_rn(s0[c], t0[c]);
+        g.C[1][c] = det2_kahan(Vh[2][c1], Vh[2][c2], Vh[0][c1], Vh[0][c2]);  // Vh2 x Vh0
+        g.C[2][c] = det2_kahan(Vh[0][c1], Vh[0][c2], Vh[1][c1], Vh[1][c2]);  // Vh0 x Vh1
+        g.C[3][c] = -((g.C[0][c] + g.C[1][c]) + g.C[2][c]);
+    }
+    // det(Vh) = Vh0 . (s0 + t0), compensated
+    float P, E;
+    two_prod(Vh[0][0], s0[0], P, E);
+    float err = __fmaf_rn(Vh[0][0], t0[0], E);
+#pragma unroll
+    for (int c = 1; c < 3; ++c) {
+        float p, e, q;
+        two_prod(Vh[0][c], s0[c], p, e);
+        two_sum(P, p, P, q);
+        err = __fadd_rn(err, __fadd_rn(q, __fmaf_rn(Vh[0][c], t0[c], e)));
+    }
+    // first-order correction from Vl
+    float corr = 0.f;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) corr = __fmaf_rn(Vl[j][c], g.C[j][c], corr);
+    g.det = __fadd_rn(P, __fadd_rn(err, corr));
+    g.xc[0] = hs[0] * 0.25f;
+    g.xc[1] = hs[1] * 0.25f;
+    g.xc[2] = hs[2] * 0.25f;
+}
+
+// Mixed precision, 2-D.  C0 = (V1y, -V1x), C1 = (-V0y, V0x) (rows of adj V).
+__device__ __forceinline__ void geo_mixed2(const float4 *__restrict__ sh, const float4 *__restrict__ sl, ushort4 v,
+                                           Geo<float> &g) {
+    const float4 h2 = sh[v.z], l2 = sl[v.z];
+    float Vh[2][2], Vl[2][2];
+    const unsigned short vi[2] = {v.x, v.y};
+    float hs[2] = {h2.x, h2.y};
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        const float4 hj = sh[vi[j]], lj = sl[vi[j]];
+        float s, e;
+        two_diff(hj.x, h2.x, s, e);
+        two_sum(s, __fadd_rn(e, __fsub_rn(lj.x, l2.x)), Vh[j][0], Vl[j][0]);
+        two_diff(hj.y, h2.y, s, e);
+        two_sum(s, __fadd_rn(e, __fsub_rn(lj.y, l2.y)), Vh[j][1], Vl[j][1]);
+        hs[0] += hj.x;
+        hs[1] += hj.y;
+    }
+    g.C[0][0] = Vh[1][1];
+    g.C[0][1] = -Vh[1][0];
+    g.C[1][0] = -Vh[0][1];
+    g.C[1][1] = Vh[0][0];
+    g.C[2][0] = -(g.C[0][0] + g.C[1][0]);
+    g.C[2][1] = -(g.C[0][1] + g.C[1][1]);
+    g.C[0][2] = g.C[1][2] = g.C[2][2] = g.C[3][0] = g.C[3][1] = g.C[3][2] = 0.f;
+    float p1, e1, p2, e2, s, es;
+    two_prod(Vh[0][0], Vh[1][1], p1, e1);
+    two_prod(Vh[0][1], Vh[1][0], p2, e2);
+    two_sum(p1, -p2, s, es);
+    float corr = 0.f;
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) corr = __fmaf_rn(Vl[j][c], g.C[j][c], corr);
+    g.det = __fadd_rn(s, __fadd_rn(__fadd_rn(es, __fsub_rn(e1, e2)), corr));
+    g.xc[0] = hs[0] * (1.0f / 3.0f);
+    g.xc[1] = hs[1] * (1.0f / 3.0f);
+    g.xc[2] = 0.f;
+}
+
+// FP64, 3-D and 2-D (coordinates as double4 in shared memory).
+template <int DIM>
+__device__ __forceinline__ void geo_f64(const double4 *__restrict__ sx, ushort4 v, Geo<double> &g) {
+    const unsigned short vi[4] = {v.x, v.y, v.z, v.w};
+    const double4 xl = sx[vi[DIM]];
+    double V[3][3];
+    double cs[3] = {xl.x, xl.y, xl.z};
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+        const double4 xj = sx[vi[j]];
+        V[j][0] = xj.x - xl.x;
+        V[j][1] = xj.y - xl.y;
+        V[j][2] = xj.z - xl.z;
+        cs[0] += xj.x;
+        cs[1] += xj.y;
+        cs[2] += xj.z;
+    }
+    if (DIM == 3) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+            g.C[0][c] = V[1][c1] * V[2][c2] - V[1][c2] * V[2][c1];
+            g.C[1][c] = V[2][c1] * V[0][c2] - V[2][c2] * V[0][c1];
+            g.C[2][c] = V[0][c1] * V[1][c2] - V[0][c2] * V[1][c1];
+            g.C[3][c] = -((g.C[0][c] + g.C[1][c]) + g.C[2][c]);
+        }
+        g.det = V[0][0] * g.C[0][0] + V[0][1] * g.C[0][1] + V[0][2] * g.C[0][2];
+        g.xc[0] = cs[0] * 0.25;
+        g.xc[1] = cs[1] * 0.25;
+        g.xc[2] = cs[2] * 0.25;
+    } else {
+        g.C[0][0] = V[1][1];
+        g.C[0][1] = -V[1][0];
+        g.C[1][0] = -V[0][1];
+        g.C[1][1] = V[0][0];
+        g.C[2][0] = -(g.C[0][0] + g.C[1][0]);
+        g.C[2][1] = -(g.C[0][1] + g.C[1][1]);
+        g.C[0][2] = g.C[1][2] = g.C[2][2] = g.C[3][0] = g.C[3][1] = g.C[3][2] = 0.0;
+        g.det = V[0][0] * V[1][1] - V[0][1] * V[1][0];
+        g.xc[0] = cs[0] / 3.0;
+        g.xc[1] = cs[1] / 3.0;
+        g.xc[2] = 0.0;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T coeff(int kind, T ca, T cb, const T *xc, int dim) {
+    if (kind == VLA_COEFF_EXP) {
+        T s = xc[0] + xc[1] + (dim == 3 ? xc[2] : T(0));
+        if constexpr (sizeof(T) == 4) return ca * expf(cb * s);
+        else return ca * exp(cb * s);
+    }
+    T r2 = xc[0] * xc[0] + xc[1] * xc[1] + (dim == 3 ? xc[2] * xc[2] : T(0));
+    return ca + cb * r2;
+}
+
+template <typename T>
+__device__ __forceinline__ T dot3(const T *a, const T *b) {
+    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+// Mixed precision fast path: edge vectors rounded once to float, Kahan 2x2
+// cofactors, plain dot for det.  The det error is below ~8u perm(|V|); if
+// |det| < perm(|V|)/32 (a flat or sliver element) the exact float-pair path
+// recomputes the geometry.
+__device__ __forceinline__ void geo_mixed3_fast(const float4 *__restrict__ sh, const float4 *__restrict__ sl,
+                                                ushort4 v, Geo<float> &g) {
+    const float4 h3 = sh[v.w], l3 = sl[v.w];
+    const unsigned short vi[3] = {v.x, v.y, v.z};
+    float V[3][3];
+    float sx = h3.x, sy = h3.y, sz = h3.z;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const float4 hj = sh[vi[j]], lj = sl[vi[j]];
+        V[j][0] = __fadd_rn(__fsub_rn(hj.x, h3.x), __fsub_rn(lj.x, l3.x));
+        V[j][1] = __fadd_rn(__fsub_rn(hj.y, h3.y), __fsub_rn(lj.y, l3.y));
+        V[j][2] = __fadd_rn(__fsub_rn(hj.z, h3.z), __fsub_rn(lj.z, l3.z));
+        sx += hj.x;
+        sy += hj.y;
+        sz += hj.z;
+    }
+    float perm = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+        g.C[0][c] = det2_kahan(V[1][c1], V[1][c2], V[2][c1], V[2][c2]);
+        g.C[1][c] = det2_kahan(V[2][c1], V[2][c2], V[0][c1], V[0][c2]);
+        g.C[2][c] = det2_kahan(V[0][c1], V[0][c2], V[1][c1], V[1][c2]);
+        g.C[3][c] = -((g.C[0][c] + g.C[1][c]) + g.C[2][c]);
+        perm = fmaf(fabsf(V[0][c]), fabsf(V[1][c1] * V[2][c2]) + fabsf(V[1][c2] * V[2][c1]), perm);
+    }
+    g.det = fmaf(V[0][0], g.C[0][0], fmaf(V[0][1], g.C[0][1], V[0][2] * g.C[0][2]));
+    g.xc[0] = sx * 0.25f;
+    g.xc[1] = sy * 0.25f;
+    g.xc[2] = sz * 0.25f;
+    if (fabsf(g.det) < 0.03125f * perm) geo_mixed3(sh, sl, v, g);
+}
+
+__device__ __forceinline__ void geo_mixed2_fast(const float4 *__restrict__ sh, const float4 *__restrict__ sl,
+                                                ushort4 v, Geo<float> &g) {
+    const float4 h2 = sh[v.z], l2 = sl[v.z];
+    const float4 h0 = sh[v.x], l0 = sl[v.x], h1 = sh[v.y], l1 = sl[v.y];
+    const float V00 = __fadd_rn(__fsub_rn(h0.x, h2.x), __fsub_rn(l0.x, l2.x));
+    const float V01 = __fadd_rn(__fsub_rn(h0.y, h2.y), __fsub_rn(l0.y, l2.y));
+    const float V10 = __fadd_rn(__fsub_rn(h1.x, h2.x), __fsub_rn(l1.x, l2.x));
+    const float V11 = __fadd_rn(__fsub_rn(h1.y, h2.y), __fsub_rn(l1.y, l2.y));
+    g.C[0][0] = V11;
+    g.C[0][1] = -V10;
+    g.C[1][0] = -V01;
+    g.C[1][1] = V00;
+    g.C[2][0] = -(V11 - V01);
+    g.C[2][1] = -(V00 - V10);
+    g.C[0][2] = g.C[1][2] = g.C[2][2] = g.C[3][0] = g.C[3][1] = g.C[3][2] = 0.f;
+    g.det = det2_kahan(V00, V01, V10, V11);
+    g.xc[0] = (h0.x + h1.x + h2.x) * (1.0f / 3.0f);
+    g.xc[1] = (h0.y + h1.y + h2.y) * (1.0f / 3.0f);
+    g.xc[2] = 0.f;
+    if (fabsf(g.det) < 0.03125f * (fabsf(V00 * V11) + fabsf(V01 * V10))) geo_mixed2(sh, sl, v, g);
+}
+
+// ---------------------------------------------------------------------------
+// compile-time configuration
+// ---------------------------------------------------------------------------
+template <int DIM, int ORDER, bool MIX>
+struct Cfg {
+    static constexpr int NV = DIM + 1;
+    static constexpr int NLB = ORDER == 1 ? DIM + 1 : (DIM + 1) * (DIM + 2) / 2;
+    static constexpr int NU = NLB * (NLB + 1) / 2;            // packed upper triangle
+    static constexpr int RS = (NU + 1 + 3) / 4 * 4;            // record: NU entries, mass scale, padding
+    static constexpr int UB = ORDER == 1 ? 4 : 8;              // code = element << UB | entry
+    using T = typename std::conditional<MIX, float, double>::type;
+    using CT = typename std::conditional<ORDER == 1, uint16_t, uint32_t>::type;
+    static constexpr double DFACT = DIM == 3 ? 6.0 : 2.0;      // dim!
+    static constexpr double MOFF = 1.0 / ((DIM + 1) * (DIM + 2));   // P1 off-diagonal mass / (c |T|)
+};
+
+struct AsmArgs {
+    const vla::TileHdr *tiles;
+    const int32_t *tile_nodes;
+    const ushort4 *tile_elem;
+    const int32_t *tile_own;
+    const int2 *tile_nzpos;
+    const int2 *tile_chunks;
+    const void *codes;
+    const float4 *xh, *xl;
+    const double *coords;
+    int kind;
+    double ca, cb;
+    double *K, *M, *vol, *Kp, *Mp;
+    unsigned long long *n_sing;
+    int *err;
+    int spin_limit;
+};
+
+__host__ __device__ constexpr int padq(int x, int q) { return (x + q - 1) / q * q; }
+
+template <int DIM, int ORDER, bool MIX>
+__global__ void __launch_bounds__(kThreads) k_assemble(AsmArgs A) {
+    using C = Cfg<DIM, ORDER, MIX>;
+    using T = typename C::T;
+    using CT = typename C::CT;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    const vla::TileHdr h = A.tiles[blockIdx.x];
+
+    // shared layout (16-byte aligned segments)
+    const int b_ids = 4 * padq(h.n_nodes, kTilePadNodes);
+    const int b_rec = 8 * padq(h.n_elems, kTilePadElems);
+    const int b_gid = 4 * padq(h.n_own, kTilePadOwn);
+    const int b_chk = 8 * padq(h.n_chunks, kTilePadChunks);
+    const int b_nz = 8 * padq(h.n_nz, kTilePadNz);
+    const int b_cod = (int)sizeof(CT) * h.n_codes;
+    int32_t *s_ids = reinterpret_cast<int32_t *>(smem);
+    ushort4 *s_rec = reinterpret_cast<ushort4 *>(smem + b_ids);
+    int32_t *s_gid = reinterpret_cast<int32_t *>(smem + b_ids + b_rec);
+    int2 *s_chk = reinterpret_cast<int2 *>(smem + b_ids + b_rec + b_gid);
+    int2 *s_nz = reinterpret_cast<int2 *>(smem + b_ids + b_rec + b_gid + b_chk);
+    CT *s_cod = reinterpret_cast<CT *>(smem + b_ids + b_rec + b_gid + b_chk + b_nz);
+    unsigned char *p_xyz = smem + b_ids + b_rec + b_gid + b_chk + b_nz + padq(b_cod, 16);
+    float4 *s_h = reinterpret_cast<float4 *>(p_xyz);
+    float4 *s_l = s_h + h.n_nodes;
+    double4 *s_x = reinterpret_cast<double4 *>(p_xyz);
+    T *s_k = reinterpret_cast<T *>(p_xyz + 32 * h.n_nodes);
+    T *s_mhat = s_k + (size_t)(h.n_elems + 1) * C::RS;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_async_smem();
+        mbar_expect_tx(&bar[0], (uint32_t)(b_ids + b_rec + b_gid));
+        if (b_ids) bulk_g2s(s_ids, A.tile_nodes + h.node_off, (uint32_t)b_ids, &bar[0]);
+        if (b_rec) bulk_g2s(s_rec, A.tile_elem + h.elem_off, (uint32_t)b_rec, &bar[0]);
+        if (b_gid) bulk_g2s(s_gid, A.tile_own + h.own_off, (uint32_t)b_gid, &bar[0]);
+        mbar_expect_tx(&bar[1], (uint32_t)(b_chk + b_nz + b_cod));
+        if (b_chk) bulk_g2s(s_chk, A.tile_chunks + h.chunk_off, (uint32_t)b_chk, &bar[1]);
+        if (b_nz) bulk_g2s(s_nz, A.tile_nzpos + h.nz_off, (uint32_t)b_nz, &bar[1]);
+        if (b_cod) bulk_g2s(s_cod, reinterpret_cast<const CT *>(A.codes) + h.code_off, (uint32_t)b_cod, &bar[1]);
+    }
+    if constexpr (ORDER == 2) {
+        for (int u = threadIdx.x; u < C::NU; u += kThreads)
+            s_mhat[u] = MIX ? (T)c_p2[DIM - 2].mhat_f[u] : (T)c_p2[DIM - 2].mhat_d[u];
+    }
+    __syncthreads();
+    // bounded wait; on expiry every thread leaves after the copies in flight land
+    auto bail = [&]() {
+        if (threadIdx.x == 0) {
+            atomicOr(A.err, 1);
+            mbar_wait_bounded(&bar[0], 0, 1 << 24);
+            mbar_wait_bounded(&bar[1], 0, 1 << 24);
+        }
+    };
+    if (__syncthreads_or(!mbar_wait_bounded(&bar[0], 0, A.spin_limit))) {
+        bail();
+        return;
+    }
+
+    // phase 0: vertex coordinates of the tile
+    for (int i = threadIdx.x; i < h.n_nodes; i += kThreads) {
+        const int32_t g = s_ids[i];
+        if constexpr (MIX) {
+            s_h[i] = A.xh[g];
+            s_l[i] = A.xl[g];
+        } else {
+            double4 x;
+            x.x = A.coords[(int64_t)g * DIM];
+            x.y = A.coords[(int64_t)g * DIM + 1];
+            x.z = DIM == 3 ? A.coords[(int64_t)g * DIM + 2] : 0.0;
+            x.w = 0.0;
+            s_x[i] = x;
+        }
+    }
+    __syncthreads();
+
+    // phase 1: element records (index n_elems is the zero record used by padding)
+    const T ca = (T)A.ca, cb = (T)A.cb;
+    unsigned long long sing = 0;
+    for (int e = threadIdx.x; e <= h.n_elems; e += kThreads) {
+        // P1 records are built in registers and stored as vectors; P2 records
+        // (up to 56 values) are written straight to shared memory
+        T *dst = s_k + (size_t)e * C::RS;
+        T rec[ORDER == 1 ? C::RS : 1];
+        if constexpr (ORDER == 1) {
+#pragma unroll
+            for (int u = 0; u < C::RS; ++u) rec[u] = T(0);
+        }
+        if (e < h.n_elems) {
+            const ushort4 v = s_rec[e];
+            Geo<T> g;
+            if constexpr (MIX) {
+                if constexpr (DIM == 3) geo_mixed3_fast(s_h, s_l, v, g);
+                else geo_mixed2_fast(s_h, s_l, v, g);
+            } else {
+                geo_f64<DIM>(s_x, v, g);
+            }
+            const T c = coeff<T>(A.kind, ca, cb, g.xc, DIM);
+            const T adet = g.det < T(0) ? -g.det : g.det;
+            const T sc = c / (T(C::DFACT) * adet);          // K(a,b) = sc * C_a . C_b
+            T mscale;
+            if constexpr (ORDER == 1) {
+#pragma unroll
+                for (int a = 0; a < C::NV; ++a)
+#pragma unroll
+                    for (int b = a; b < C::NV; ++b) rec[a * C::NLB - a * (a - 1) / 2 + (b - a)] = sc * dot3<T>(g.C[a], g.C[b]);
+                mscale = c * adet * T(C::MOFF / C::DFACT);       // off-diagonal mass entry
+                rec[C::NU] = mscale;
+            } else {
+                T cd[10];
+#pragma unroll
+                for (int s = 0; s < C::NV; ++s)
+#pragma unroll
+                    for (int q = s; q < C::NV; ++q) cd[s * C::NV - s * (s - 1) / 2 + (q - s)] = dot3<T>(g.C[s], g.C[q]);
+                const P2Tab &tb = c_p2[DIM - 2];
+                for (int u = 0; u < C::NU; ++u) {
+                    T acc = 0;
+                    const int nt = tb.nterm[u];
+                    for (int q = 0; q < nt; ++q) {
+                        const T cf = MIX ? (T)tb.coef_f[u][q] : (T)tb.coef_d[u][q];
+                        acc += cf * cd[tb.st[u][q]];
+                    }
+                    dst[u] = sc * acc;
+                }
+                mscale = c * adet * T(1.0 / C::DFACT);           // c |T|; entries scale the reference mass
+                dst[C::NU] = mscale;
+            }
+            if (e < h.n_own) {
+                const int64_t k = s_gid[e];
+                if (g.det == T(0)) ++sing;
+                if (A.vol) {
+                    if constexpr (MIX) A.vol[k] = f32_to_f64(adet * (float)(1.0 / C::DFACT));
+                    else A.vol[k] = adet / C::DFACT;
+                }
+                if (A.Kp || A.Mp) {
+                    for (int a = 0; a < C::NLB; ++a)
+                        for (int b = 0; b < C::NLB; ++b) {
+                            const int p = a < b ? a : b, q = a < b ? b : a;
+                            const int u = p * C::NLB - p * (p - 1) / 2 + (q - p);
+                            const int64_t pos = k * C::NLB * C::NLB + a + (int64_t)b * C::NLB;
+                            T kv, mv;
+                            if constexpr (ORDER == 1) {
+                                kv = rec[u];
+                                mv = mscale * (a == b ? T(2) : T(1));
+                            } else {
+                                kv = dst[u];
+                                mv = mscale * (MIX ? (T)c_p2[DIM - 2].mhat_f[u] : (T)c_p2[DIM - 2].mhat_d[u]);
+                            }
+                            if constexpr (MIX) {
+                                if (A.Kp) A.Kp[pos] = f32_to_f64(kv);
+                                if (A.Mp) A.Mp[pos] = f32_to_f64(mv);
+                            } else {
+                                if (A.Kp) A.Kp[pos] = kv;
+                                if (A.Mp) A.Mp[pos] = mv;
+                            }
+                        }
+                }
+            }
+        } else if constexpr (ORDER == 2) {
+            for (int u = 0; u < C::RS; ++u) dst[u] = T(0);
+        }
+        if constexpr (ORDER == 1) {
+            if constexpr (MIX) {
+#pragma unroll
+                for (int u = 0; u < C::RS; u += 4)
+                    *reinterpret_cast<float4 *>(dst + u) = make_float4(rec[u], rec[u + 1], rec[u + 2], rec[u + 3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < C::RS; u += 2)
+                    *reinterpret_cast<double2 *>(dst + u) = make_double2(rec[u], rec[u + 1]);
+            }
+        }
+    }
+    if (A.n_sing && sing) atomicAdd(A.n_sing, sing);
+    __syncthreads();
+    if (__syncthreads_or(!mbar_wait_bounded(&bar[1], 0, A.spin_limit))) {
+        bail();
+        return;
+    }
+    if (!A.K && !A.M) return;
+
+    // phase 2: pairs {i, j} (and diagonals), 32 per warp-chunk, contributions in
+    // ascending element order, two interleaved compensated accumulators
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int n_up_chunks = (h.n_up + 31) >> 5;
+    constexpr uint32_t UMASK = (1u << C::UB) - 1;
+    for (int c = warp; c < h.n_chunks; c += kThreads / 32) {
+        const bool diag = c >= n_up_chunks;
+        int q = diag ? h.n_up + (c - n_up_chunks) * 32 + lane : c * 32 + lane;
+        if (q >= (diag ? h.n_nz : h.n_up)) q = -1;
+        const int2 ch = s_chk[c];
+        const CT *cp = s_cod + ch.x + lane;
+        if constexpr (MIX) {
+            ffacc k0, k1, m0, m1;
+            k0.zero();
+            k1.zero();
+            m0.zero();
+            m1.zero();
+            int tt = 0;
+            for (; tt + 1 < ch.y; tt += 2) {
+                const uint32_t c0 = cp[tt * 32], c1 = cp[(tt + 1) * 32];
+                const float *r0 = s_k + (c0 >> C::UB) * C::RS, *r1 = s_k + (c1 >> C::UB) * C::RS;
+                const float kv0 = r0[c0 & UMASK], kv1 = r1[c1 & UMASK];
+                float mv0 = r0[C::NU], mv1 = r1[C::NU];
+                if constexpr (ORDER == 2) {
+                    mv0 *= s_mhat[c0 & UMASK];
+                    mv1 *= s_mhat[c1 & UMASK];
+                }
+                k0.add(kv0);
+                k1.add(kv1);
+                m0.add(mv0);
+                m1.add(mv1);
+            }
+            if (tt < ch.y) {
+                const uint32_t c0 = cp[tt * 32];
+                const float *r0 = s_k + (c0 >> C::UB) * C::RS;
+                float mv0 = r0[C::NU];
+                if constexpr (ORDER == 2) mv0 *= s_mhat[c0 & UMASK];
+                k0.add(r0[c0 & UMASK]);
+                m0.add(mv0);
+            }
+            if (q >= 0) {
+                k0.add(k1.hi);
+                k0.add(k1.lo);
+                m0.add(m1.hi);
+                m0.add(m1.lo);
+                k0.norm();
+                m0.norm();
+                if (ORDER == 1 && diag) {   // P1 diagonal mass entries are twice the off-diagonal scale
+                    m0.hi *= 2.f;
+                    m0.lo *= 2.f;
+                }
+                const int2 pos = s_nz[q];
+                const double kd = ff_to_f64(k0.hi, k0.lo), md = ff_to_f64(m0.hi, m0.lo);
+                if (A.K) {
+                    A.K[pos.x] = kd;
+                    if (pos.y != pos.x) A.K[pos.y] = kd;
+                }
+                if (A.M) {
+                    A.M[pos.x] = md;
+                    if (pos.y != pos.x) A.M[pos.y] = md;
+                }
+            }
+        } else {
+            double ks = 0.0, ms = 0.0;
+            for (int tt = 0; tt < ch.y; ++tt) {
+                const uint32_t c0 = cp[tt * 32];
+                const double *r0 = s_k + (c0 >> C::UB) * C::RS;
+                ks += r0[c0 & UMASK];
+                if constexpr (ORDER == 2) ms += r0[C::NU] * s_mhat[c0 & UMASK];
+                else ms += r0[C::NU];
+            }
+            if (q >= 0) {
+                if (ORDER == 1 && diag) ms *= 2.0;
+                const int2 pos = s_nz[q];
+                if (A.K) {
+                    A.K[pos.x] = ks;
+                    if (pos.y != pos.x) A.K[pos.y] = ks;
+                }
+                if (A.M) {
+                    A.M[pos.x] = ms;
+                    if (pos.y != pos.x) A.M[pos.y] = ms;
+                }
+            }
+        }
+    }
+}
+
+template <int DIM, int ORDER, bool MIX>
+size_t asm_smem(const vla_mesh *m) {
+    using C = Cfg<DIM, ORDER, MIX>;
+    return m->tile_stage_bytes + 64 + (size_t)m->max_tile_nodes * 32 +
+           ((size_t)m->max_tile_elems + 1) * C::RS * sizeof(typename C::T) + (size_t)C::NU * sizeof(typename C::T);
+}
+
+template <int DIM, int ORDER, bool MIX>
+vla_status launch_assemble(const vla_mesh *m, const AsmArgs &a, cudaStream_t st) {
+    const size_t smem = asm_smem<DIM, ORDER, MIX>(m);
+    int dev = 0, maxsm = 0;
+    VLA_CUDA(cudaGetDevice(&dev));
+    VLA_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (smem > (size_t)maxsm - 64)
+        return fail(VLA_ERR_UNSUPPORTED, "assembly tile needs %zu bytes of shared memory (limit %d)", smem, maxsm);
+    VLA_CUDA(cudaFuncSetAttribute(k_assemble<DIM, ORDER, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_assemble<DIM, ORDER, MIX><<<m->n_tiles, kThreads, smem, st>>>(a);
+    VLA_CUDA(cudaGetLastError());
+    return VLA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// boundary facets
+// ---------------------------------------------------------------------------
+__global__ void k_boundary_f64(int64_t nfb, int dim, const double *__restrict__ x, const int32_t *__restrict__ faces,
+                               const int32_t *__restrict__ opp, double *__restrict__ nrm, double *__restrict__ area) {
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nfb; f += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = faces[f * dim], b = faces[f * dim + 1];
+        const int32_t o = opp[f];
+        double n[3] = {0, 0, 0}, meas;
+        const double *x1 = x + (int64_t)a * dim, *x2 = x + (int64_t)b * dim, *xo = x + (int64_t)o * dim;
+        if (dim == 3) {
+            const double *x3 = x + (int64_t)faces[f * dim + 2] * dim;
+            double u[3], w[3];
+            for (int d = 0; d < 3; ++d) {
+                u[d] = x2[d] - x1[d];
+                w[d] = x3[d] - x1[d];
+            }
+            n[0] = u[1] * w[2] - u[2] * w[1];
+            n[1] = u[2] * w[0] - u[0] * w[2];
+            n[2] = u[0] * w[1] - u[1] * w[0];
+        } else {
+            n[0] = x2[1] - x1[1];
+            n[1] = -(x2[0] - x1[0]);
+        }
+        const double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        meas = dim == 3 ? 0.5 * len : len;
+        double side = 0;
+        for (int d = 0; d < dim; ++d) side += n[d] * (xo[d] - x1[d]);
+        const double sg = side > 0 ? -1.0 : 1.0;
+        for (int d = 0; d < dim; ++d) nrm[f * dim + d] = sg * n[d] / len;
+        area[f] = meas;
+    }
+}
+
+__global__ void k_boundary_mixed(int64_t nfb, int dim, const float4 *__restrict__ xh, const float4 *__restrict__ xl,
+                                 const int32_t *__restrict__ faces, const int32_t *__restrict__ opp,
+                                 double *__restrict__ nrm, double *__restrict__ area) {
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nfb; f += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t ia = faces[f * dim], ib = faces[f * dim + 1], io = opp[f];
+        const float4 ha = xh[ia], la = xl[ia], hb = xh[ib], lb = xl[ib], ho = xh[io], lo = xl[io];
+        auto dif = [](float h1, float l1, float h0, float l0) {
+            return __fadd_rn(__fsub_rn(h1, h0), __fsub_rn(l1, l0));
+        };
+        float u[3] = {dif(hb.x, lb.x, ha.x, la.x), dif(hb.y, lb.y, ha.y, la.y), dif(hb.z, lb.z, ha.z, la.z)};
+        float r[3] = {dif(ho.x, lo.x, ha.x, la.x), dif(ho.y, lo.y, ha.y, la.y), dif(ho.z, lo.z, ha.z, la.z)};
+        float n[3];
+        if (dim == 3) {
+            const int32_t ic = faces[f * dim + 2];
+            const float4 hc = xh[ic], lc = xl[ic];
+            float w[3] = {dif(hc.x, lc.x, ha.x, la.x), dif(hc.y, lc.y, ha.y, la.y), dif(hc.z, lc.z, ha.z, la.z)};
+            n[0] = det2_kahan(u[1], u[2], w[1], w[2]);
+            n[1] = det2_kahan(u[2], u[0], w[2], w[0]);
+            n[2] = det2_kahan(u[0], u[1], w[0], w[1]);
+        } else {
+            n[0] = u[1];
+            n[1] = -u[0];
+            n[2] = 0.f;
+        }
+        const float len = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        const float side = n[0] * r[0] + n[1] * r[1] + n[2] * r[2];
+        const float inv = (side > 0.f ? -1.f : 1.f) / len;
+        for (int d = 0; d < dim; ++d) nrm[f * dim + d] = f32_to_f64(n[d] * inv);
+        area[f] = f32_to_f64(dim == 3 ? 0.5f * len : len);
+    }
+}
+
+// all-facet normals V^{-T} normalsRef = -grad lambda_j = -C_j / det (FP64)
+__global__ void k_simplex_normals(int64_t ne, int dim, int nlb, const double *__restrict__ x,
+                                  const int32_t *__restrict__ elems, double *__restrict__ out) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += (int64_t)gridDim.x * blockDim.x) {
+        double V[3][3] = {{0}}, Cf[4][3] = {{0}}, det;
+        const int32_t last = elems[k * nlb + dim];
+        for (int j = 0; j < dim; ++j) {
+            const int32_t vj = elems[k * nlb + j];
+            for (int d = 0; d < dim; ++d) V[j][d] = x[(int64_t)vj * dim + d] - x[(int64_t)last * dim + d];
+        }
+        if (dim == 3) {
+            for (int c = 0; c < 3; ++c) {
+                const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
+                Cf[0][c] = V[1][c1] * V[2][c2] - V[1][c2] * V[2][c1];
+                Cf[1][c] = V[2][c1] * V[0][c2] - V[2][c2] * V[0][c1];
+                Cf[2][c] = V[0][c1] * V[1][c2] - V[0][c2] * V[1][c1];
+            }
+            det = V[0][0] * Cf[0][0] + V[0][1] * Cf[0][1] + V[0][2] * Cf[0][2];
+        } else {
+            Cf[0][0] = V[1][1];
+            Cf[0][1] = -V[1][0];
+            Cf[1][0] = -V[0][1];
+            Cf[1][1] = V[0][0];
+            det = V[0][0] * V[1][1] - V[0][1] * V[1][0];
+        }
+        const double r = 1.0 / det;
+        for (int d = 0; d < dim; ++d) {
+            double s = 0;
+            for (int j = 0; j < dim; ++j) {
+                const double g = Cf[j][d] * r;       // grad lambda_j
+                out[k * dim * (dim + 1) + d + j * dim] = -g;
+                s += g;
+            }
+            out[k * dim * (dim + 1) + d + dim * dim] = s;  // -grad lambda_dim
+        }
+    }
+}
+
+}  // namespace
+}  // namespace vla
+
+using namespace vla;
+
+extern "C" vla_status vla_assemble(const vla_mesh *m, int32_t kind, double ca, double cb, int32_t precision,
+                                   double *K_vals, double *M_vals, double *vol, double *K_pages, double *M_pages,
+                                   int64_t *n_singular, void *stream) {
+    if (!m) return fail(VLA_ERR_INVALID_ARG, "null mesh");
+    if (kind != VLA_COEFF_POLY && kind != VLA_COEFF_EXP) return fail(VLA_ERR_INVALID_ARG, "unknown coefficient kind");
+    if (precision != VLA_PREC_FP64 && precision != VLA_PREC_MIXED)
+        return fail(VLA_ERR_INVALID_ARG, "precision must be VLA_PREC_FP64 or VLA_PREC_MIXED");
+    if (!std::isfinite(ca) || !std::isfinite(cb)) return fail(VLA_ERR_INVALID_ARG, "non-finite coefficient");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (m->order == 2) {
+        vla_status s = ensure_p2_tables();
+        if (s) return s;
+    }
+    unsigned long long *ns = reinterpret_cast<unsigned long long *>(n_singular);
+    if (ns) VLA_CUDA(cudaMemsetAsync(ns, 0, sizeof(unsigned long long), st));
+    AsmArgs a;
+    a.tiles = m->tiles;
+    a.tile_nodes = m->tile_nodes;
+    a.tile_elem = m->tile_elem;
+    a.tile_own = m->tile_own;
+    a.tile_nzpos = m->tile_nzpos;
+    a.tile_chunks = m->tile_chunks;
+    a.codes = m->tile_codes;
+    a.xh = m->xh;
+    a.xl = m->xl;
+    a.coords = m->coords;
+    a.kind = kind;
+    a.ca = ca;
+    a.cb = cb;
+    a.K = K_vals;
+    a.M = M_vals;
+    a.vol = vol;
+    a.Kp = K_pages;
+    a.Mp = M_pages;
+    a.n_sing = ns;
+    a.err = m->d_err;
+    a.spin_limit = m->spin_limit;
+    const bool mix = precision == VLA_PREC_MIXED;
+    const int key = (m->dim == 3 ? 4 : 0) + (m->order == 2 ? 2 : 0) + (mix ? 1 : 0);
+    switch (key) {
+    case 0: return launch_assemble<2, 1, false>(m, a, st);
+    case 1: return launch_assemble<2, 1, true>(m, a, st);
+    case 2: return launch_assemble<2, 2, false>(m, a, st);
+    case 3: return launch_assemble<2, 2, true>(m, a, st);
+    case 4: return launch_assemble<3, 1, false>(m, a, st);
+    case 5: return launch_assemble<3, 1, true>(m, a, st);
+    case 6: return launch_assemble<3, 2, false>(m, a, st);
+    default: return launch_assemble<3, 2, true>(m, a, st);
+    }
+}
+
+extern "C" vla_status vla_boundary(const vla_mesh *m, int32_t precision, double *normals, double *areas,
+                                   void *stream) {
+    if (!m) return fail(VLA_ERR_INVALID_ARG, "null mesh");
+    if (precision != VLA_PREC_FP64 && precision != VLA_PREC_MIXED)
+        return fail(VLA_ERR_INVALID_ARG, "precision must be VLA_PREC_FP64 or VLA_PREC_MIXED");
+    if (m->nfb == 0) return VLA_OK;
+    if (!normals || !areas) return fail(VLA_ERR_INVALID_ARG, "null output");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int g = grid_for(m->nfb, 256, 152 * 16);
+    if (precision == VLA_PREC_FP64)
+        k_boundary_f64<<<g, 256, 0, st>>>(m->nfb, m->dim, m->coords, m->faces, m->face_opp, normals, areas);
+    else
+        k_boundary_mixed<<<g, 256, 0, st>>>(m->nfb, m->dim, m->xh, m->xl, m->faces, m->face_opp, normals, areas);
+    VLA_CUDA(cudaGetLastError());
+    return VLA_OK;
+}
+
+extern "C" vla_status vla_simplex_normals(const vla_mesh *m, double *normals, void *stream) {
+    if (!m) return fail(VLA_ERR_INVALID_ARG, "null mesh");
+    if (!normals) return fail(VLA_ERR_INVALID_ARG, "null output");
+    cudaStream_t st = (cudaStream_t)stream;
+    k_simplex_normals<<<grid_for(m->ne, 256, 152 * 16), 256, 0, st>>>(m->ne, m->dim, m->nlb, m->coords, m->elems,
+                                                                     normals);
+    VLA_CUDA(cudaGetLastError());
+    return VLA_OK;
+}

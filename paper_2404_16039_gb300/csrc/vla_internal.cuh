@@ -1,0 +1,244 @@
+// vla_internal.cuh -- shared internals of libvla (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/vla.h"
+
+namespace vla {
+
+// ---------------------------------------------------------------------------
+// error reporting (thread-local last message, see vla_last_error)
+// ---------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+vla_status fail(vla_status st, const char *fmt, ...);
+vla_status cuda_fail(cudaError_t e, const char *what);
+
+#define VLA_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return ::vla::cuda_fail(e_, #call);  \
+    } while (0)
+
+inline int grid_for(int64_t n, int block, int64_t cap = 152 * 64) {
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+// ---------------------------------------------------------------------------
+// float-float helpers (error-free transformations, round-to-nearest)
+// ---------------------------------------------------------------------------
+
+// s + e == a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// p + e == a * b exactly (FMA-based TwoProduct).
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// a*d - b*c with at most ~1.5 ulp error (Kahan's FMA algorithm).
+__device__ __forceinline__ float det2_kahan(float a, float b, float c, float d) {
+    float w = __fmul_rn(b, c);
+    float e = __fmaf_rn(-b, c, w);
+    float f = __fmaf_rn(a, d, -w);
+    return __fadd_rn(f, e);
+}
+
+// compensated accumulator: value = hi + lo
+struct ffacc {
+    float hi, lo;
+    __device__ __forceinline__ void zero() { hi = 0.f; lo = 0.f; }
+    __device__ __forceinline__ void add(float x) {
+        float s, e;
+        two_sum(hi, x, s, e);
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    // normalise so that |lo| <= ulp(hi)/2
+    __device__ __forceinline__ void norm() {
+        float s, e;
+        two_sum(hi, lo, s, e);
+        hi = s;
+        lo = e;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// FP32 -> FP64 conversions with integer instructions only.  The FP64 and
+// conversion pipes of the GB300 SM run at a small fraction of the FP32 rate,
+// so the mixed-precision kernels build the IEEE-754 binary64 bit patterns
+// directly.
+// ---------------------------------------------------------------------------
+
+// exact conversion of any float (normal, subnormal, zero, inf, nan)
+__device__ __forceinline__ unsigned long long f32_to_f64_bits(float x) {
+    uint32_t u = __float_as_uint(x);
+    unsigned long long s = (unsigned long long)(u >> 31) << 63;
+    uint32_t e = (u >> 23) & 0xffu;
+    uint32_t m = u & 0x7fffffu;
+    if (e == 0xffu) return s | 0x7ff0000000000000ull | ((unsigned long long)m << 29);
+    if (e == 0) {
+        if (m == 0) return s;
+        int p = 31 - __clz(m);                         // leading one of the subnormal mantissa, 0..22
+        unsigned long long mant = ((unsigned long long)m << (52 - p)) & 0xfffffffffffffull;
+        unsigned long long ex = (unsigned long long)(p - 149 + 1023);
+        return s | (ex << 52) | mant;
+    }
+    return s | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+}
+
+__device__ __forceinline__ double f32_to_f64(float x) { return __longlong_as_double((long long)f32_to_f64_bits(x)); }
+
+// hi + lo as a double, for a normalised pair (|lo| <= ulp_f32(hi)/2), with an
+// error below one double ulp (lo bits below the double's precision are
+// truncated).  Integer-only except in the rare case where lo would move the
+// result below hi's binade.
+__device__ __forceinline__ double ff_to_f64(float hi, float lo) {
+    unsigned long long hb = f32_to_f64_bits(hi);
+    uint32_t lu = __float_as_uint(lo);
+    if ((lu & 0x7fffffffu) == 0u || ((hb >> 52) & 0x7ffull) == 0x7ffull) return __longlong_as_double((long long)hb);
+    if (hi == 0.0f) return f32_to_f64(lo);
+    uint32_t le = (lu >> 23) & 0xffu;
+    uint32_t lm = lu & 0x7fffffu;
+    int elo;                                            // |lo| = lm' * 2^(elo - 23)
+    if (le == 0) {
+        elo = -126;
+    } else {
+        elo = (int)le - 127;
+        lm |= 0x800000u;
+    }
+    int ehi = (int)((hb >> 52) & 0x7ffull) - 1023;      // hi's exponent as a double
+    int shift = elo - ehi + 29;                         // lo in units of 2^(ehi-52)
+    unsigned long long delta;
+    if (shift >= 0) {
+        if (shift > 5) return __longlong_as_double((long long)hb) + f32_to_f64(lo);  // not normalised
+        delta = (unsigned long long)lm << shift;
+    } else {
+        delta = (shift <= -32) ? 0ull : ((unsigned long long)lm >> (-shift));
+    }
+    bool same = ((lu >> 31) == (uint32_t)(hb >> 63));
+    unsigned long long mant = hb & 0xfffffffffffffull;
+    if (same) return __longlong_as_double((long long)(hb + delta));   // low 29 bits of hb are zero: no carry
+    if (mant < delta) return __longlong_as_double((long long)hb) + f32_to_f64(lo);  // crosses the binade
+    return __longlong_as_double((long long)(hb - delta));
+}
+
+// ---------------------------------------------------------------------------
+// PTX wrappers: mbarrier + 1-D bulk TMA (cp.async.bulk), sm_90+
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\t"
+        "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(smem_u32(bar)),
+        "r"(bytes)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// bounded wait on an mbarrier phase; false if the limit expired
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int limit) {
+    for (int i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// mesh handle
+// ---------------------------------------------------------------------------
+
+// Per-tile header produced by the mesh build.  Every per-tile segment starts
+// on a 16-byte boundary and its byte size is padded to a multiple of 16, so
+// the assembly kernel can stage it into shared memory with one bulk copy.
+struct TileHdr {
+    int32_t node_off, n_nodes;    // tile_nodes: vertex node ids (int32)
+    int32_t elem_off, n_elems;    // tile_elem: local vertex indices (ushort4); owned elements first
+    int32_t own_off, n_own;       // tile_own: global ids of the owned elements (int32)
+    int32_t nz_off, n_nz;         // tile_nzpos: (p_ij, p_ji) CSR positions (int2); upper pairs, then diagonals
+    int32_t n_up;                 // number of off-diagonal pairs {i, j}
+    int32_t chunk_off, n_chunks;  // tile_chunks: (code offset in the tile's segment, width) per 32 pairs
+    int32_t code_off, n_codes;    // tile_codes segment (in codes; multiple of 32)
+    int32_t rank_begin, n_rows;   // rows of the tile: ranks [rank_begin, rank_begin + n_rows) of the order
+    int32_t pad;
+};
+
+constexpr int kTilePadNodes = 4, kTilePadElems = 2, kTilePadOwn = 4, kTilePadNz = 2, kTilePadChunks = 2;
+
+}  // namespace vla
+
+struct vla_mesh {
+    int32_t dim, order, nlb;
+    int64_t nn, ne, nfb, nnz;
+    int32_t max_row_len;
+    int32_t n_tiles;
+    int32_t max_tile_nodes, max_tile_elems, max_tile_nz;
+    int32_t tile_budget;
+    int64_t n_codes;
+    int64_t tile_elems_total;     // sum over tiles of their element counts (recompute factor * ne)
+    size_t tile_stage_bytes;      // largest per-tile staged segment set (ids, records, owned, chunks, pairs, codes)
+    int32_t spin_limit;           // bounded waits on bulk copies
+    int32_t *d_err;               // device error word (bit 0: a bounded wait expired)
+    int64_t device_bytes;
+    cudaStream_t stream;
+
+    double *coords;        // nn x dim
+    int32_t *elems;        // ne x nlb
+    int32_t *faces;        // nfb x dim
+    int32_t *face_opp;     // nfb: remaining vertex of the owning element
+    float4 *xh, *xl;       // float pair split of coords (w = 0)
+    int32_t *row_ptr, *col_idx;
+    int32_t *n2e_ptr, *n2e;
+
+    vla::TileHdr *tiles;
+    int32_t *tile_nodes;   // global node ids per tile
+    ushort4 *tile_elem;    // local vertex indices per tile element
+    int32_t *tile_own;     // global ids of owned elements
+    int2 *tile_nzpos;      // (p_ij, p_ji) CSR positions of each tile pair
+    int2 *tile_chunks;     // (code offset within the tile segment, width) per 32-pair chunk
+    void *tile_codes;      // uint16 (P1) or uint32 (P2) contribution codes, chunk-interleaved
+
+    std::vector<void *> allocs;  // every device allocation owned by the handle
+};

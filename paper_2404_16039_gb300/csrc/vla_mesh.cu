@@ -1,0 +1,1128 @@
+// vla_mesh.cu -- mesh ingest on the device: validation, node->element
+// incidence, the CSR pattern of sparse(X3D(:),Y3D(:),.,nn,nn) (Section 3.5),
+// boundary-facet owners, the float-pair split of the coordinates, and the row
+// tiles used by the assembly kernel.
+//
+// Row tiles.  Assembly is a gather problem: CSR entry (i,j) sums the
+// (i,j) entries of every element containing nodes i and j.  The assembly
+// kernel gives each CTA a set of rows that are close in space (nodes sorted
+// by the Morton code of their cell), recomputes in shared memory the element
+// matrices of every element touching those rows, and sums them per nonzero
+// from shared memory.  The build below produces, per tile: its vertex nodes,
+// its elements (local vertex indices), the elements it owns (writes volume and
+// pages for), the global CSR position of each of its nonzeros, and for every
+// nonzero the list of (local element, a, b) contribution codes in ascending
+// element order, laid out 32 nonzeros at a time so that lane l of a warp reads
+// code t of nonzero l from consecutive addresses.  The summation order of
+// every CSR entry is therefore fixed by the mesh alone (ascending element id),
+// which makes assembly bit-reproducible.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+
+#include "vla_internal.cuh"
+
+namespace vla {
+namespace {
+
+constexpr int kMaxRow = 255;   // CSR row length limit (slot fits a byte)
+constexpr int kScanItems = 8;  // items per thread of the block scan
+constexpr int kScanThreads = 256;
+
+// ---------------------------------------------------------------------------
+// device-wide exclusive scan of int32 or int64 values into int64
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long warp_incl_scan(long long v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// block-wide exclusive scan of one value per thread; returns the block total in *total
+__device__ long long block_excl_scan(long long v, long long *total) {
+    __shared__ long long warp_sums[32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    long long inc = warp_incl_scan(v);
+    if (lane == 31) warp_sums[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        long long s = lane < nw ? warp_sums[lane] : 0;
+        long long si = warp_incl_scan(s);
+        if (lane < nw) warp_sums[lane] = si - s;
+        if (lane == nw - 1) warp_sums[31] = si;
+    }
+    __syncthreads();
+    long long res = inc - v + warp_sums[wid];
+    long long tot = warp_sums[31];
+    __syncthreads();
+    if (total) *total = tot;
+    return res;
+}
+
+template <typename TI>
+__global__ void k_scan_blocks(int64_t n, const TI *__restrict__ in, long long *__restrict__ out,
+                              long long *__restrict__ block_sums) {
+    const int64_t base = (int64_t)blockIdx.x * kScanThreads * kScanItems + (int64_t)threadIdx.x * kScanItems;
+    long long vals[kScanItems];
+    long long s = 0;
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        int64_t i = base + q;
+        vals[q] = (i < n) ? (long long)in[i] : 0;
+        s += vals[q];
+    }
+    long long tot;
+    long long pre = block_excl_scan(s, &tot);
+#pragma unroll
+    for (int q = 0; q < kScanItems; ++q) {
+        int64_t i = base + q;
+        if (i < n) out[i] = pre;
+        pre += vals[q];
+    }
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_add(int64_t n, long long *__restrict__ out, const long long *__restrict__ block_pre) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] += block_pre[i / (kScanThreads * kScanItems)];
+}
+
+// out[i] = sum_{j<i} in[j] for i in [0, n]; returns the total on the host.
+template <typename TI>
+vla_status excl_scan(const TI *in, int64_t n, long long *out, cudaStream_t st, long long *total_host) {
+    const int64_t per = (int64_t)kScanThreads * kScanItems;
+    int64_t nb = (n + per - 1) / per;
+    if (nb < 1) nb = 1;
+    long long *bs = nullptr, *bsp = nullptr;
+    VLA_CUDA(cudaMallocAsync(&bs, sizeof(long long) * (nb + 1), st));
+    VLA_CUDA(cudaMallocAsync(&bsp, sizeof(long long) * (nb + 1), st));
+    k_scan_blocks<TI><<<(int)nb, kScanThreads, 0, st>>>(n, in, out, bs);
+    VLA_CUDA(cudaGetLastError());
+    long long tot = 0;
+    if (nb > 1) {
+        vla_status s = excl_scan<long long>(bs, nb, bsp, st, &tot);
+        if (s) return s;
+        k_scan_add<<<grid_for(n, 256, 1 << 30), 256, 0, st>>>(n, out, bsp);
+        VLA_CUDA(cudaGetLastError());
+    } else {
+        VLA_CUDA(cudaMemcpyAsync(&tot, bs, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        VLA_CUDA(cudaStreamSynchronize(st));
+    }
+    // out[n] = total
+    VLA_CUDA(cudaMemcpyAsync(out + n, &tot, sizeof(long long), cudaMemcpyHostToDevice, st));
+    VLA_CUDA(cudaStreamSynchronize(st));
+    VLA_CUDA(cudaFreeAsync(bs, st));
+    VLA_CUDA(cudaFreeAsync(bsp, st));
+    if (total_host) *total_host = tot;
+    return VLA_OK;
+}
+
+__global__ void k_i64_to_i32(int64_t n, const long long *__restrict__ in, int32_t *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (int32_t)in[i];
+}
+
+// ---------------------------------------------------------------------------
+// validation and incidence
+// ---------------------------------------------------------------------------
+enum { ERR_OOB = 1, ERR_DUP = 2, ERR_ROWLEN = 4, ERR_FACE_OOB = 8, ERR_FACE_OWNER = 16 };
+
+__global__ void k_validate_count(int64_t ne, int nlb, int64_t nn, const int32_t *__restrict__ elems,
+                                 int32_t *__restrict__ cnt, int *__restrict__ err, long long *__restrict__ bad) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v[10];
+        bool ok = true;
+        for (int j = 0; j < nlb; ++j) {
+            v[j] = elems[k * nlb + j];
+            if (v[j] < 0 || v[j] >= nn) ok = false;
+        }
+        if (!ok) {
+            atomicOr(err, ERR_OOB);
+            atomicMin(bad, (long long)k);
+            continue;
+        }
+        for (int j = 0; j < nlb; ++j)
+            for (int q = 0; q < j; ++q)
+                if (v[q] == v[j]) ok = false;
+        if (!ok) {
+            atomicOr(err, ERR_DUP);
+            atomicMin(bad, (long long)k);
+            continue;
+        }
+        for (int j = 0; j < nlb; ++j) atomicAdd(&cnt[v[j]], 1);
+    }
+}
+
+__global__ void k_fill_n2e(int64_t ne, int nlb, const int32_t *__restrict__ elems, int32_t *__restrict__ cursor,
+                           int32_t *__restrict__ n2e) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += (int64_t)gridDim.x * blockDim.x)
+        for (int j = 0; j < nlb; ++j) {
+            int32_t pos = atomicAdd(&cursor[elems[k * nlb + j]], 1);
+            n2e[pos] = (int32_t)((k << 4) | j);
+        }
+}
+
+// insertion sort of every node's incidence list (ascending element id)
+__global__ void k_sort_segments(int64_t n, const int32_t *__restrict__ ptr, int32_t *__restrict__ v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t b = ptr[i], e = ptr[i + 1];
+        for (int32_t p = b + 1; p < e; ++p) {
+            int32_t x = v[p];
+            int32_t q = p - 1;
+            while (q >= b && v[q] > x) {
+                v[q + 1] = v[q];
+                --q;
+            }
+            v[q + 1] = x;
+        }
+    }
+}
+
+// sorted-unique neighbour set of node i, built in scratch (capacity nlb * deg(i))
+__global__ void k_row_count(int64_t nn, int nlb, const int32_t *__restrict__ elems,
+                            const int32_t *__restrict__ n2e_ptr, const int32_t *__restrict__ n2e,
+                            int32_t *__restrict__ scratch, int32_t *__restrict__ rowlen, int *__restrict__ err) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t b = n2e_ptr[i], e = n2e_ptr[i + 1];
+        int32_t *u = scratch + (int64_t)nlb * b;
+        int n = 0;
+        for (int32_t t = b; t < e; ++t) {
+            int64_t k = (int64_t)(n2e[t] >> 4);
+            for (int q = 0; q < nlb; ++q) {
+                int32_t c = elems[k * nlb + q];
+                int lo = 0, hi = n;  // first position with u[pos] >= c
+                while (lo < hi) {
+                    int mid = (lo + hi) >> 1;
+                    if (u[mid] < c) lo = mid + 1;
+                    else hi = mid;
+                }
+                if (lo < n && u[lo] == c) continue;
+                for (int s = n; s > lo; --s) u[s] = u[s - 1];
+                u[lo] = c;
+                ++n;
+            }
+        }
+        rowlen[i] = n;
+        if (n > kMaxRow) atomicOr(err, ERR_ROWLEN);
+    }
+}
+
+__global__ void k_row_fill(int64_t nn, int nlb, const int32_t *__restrict__ n2e_ptr,
+                           const int32_t *__restrict__ scratch, const int32_t *__restrict__ row_ptr,
+                           int32_t *__restrict__ col_idx) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t *u = scratch + (int64_t)nlb * n2e_ptr[i];
+        int32_t b = row_ptr[i], e = row_ptr[i + 1];
+        for (int32_t p = b; p < e; ++p) col_idx[p] = u[p - b];
+    }
+}
+
+// owner element and remaining vertex of each boundary facet
+__global__ void k_face_owner(int64_t nfb, int dim, int nlb, int64_t nn, const int32_t *__restrict__ faces,
+                             const int32_t *__restrict__ elems, const int32_t *__restrict__ n2e_ptr,
+                             const int32_t *__restrict__ n2e, int32_t *__restrict__ opp, int *__restrict__ err) {
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nfb; f += (int64_t)gridDim.x * blockDim.x) {
+        int32_t fn[3] = {0, 0, 0};
+        bool ok = true;
+        for (int q = 0; q < dim; ++q) {
+            fn[q] = faces[f * dim + q];
+            if (fn[q] < 0 || fn[q] >= nn) ok = false;
+        }
+        if (!ok) {
+            atomicOr(err, ERR_FACE_OOB);
+            opp[f] = -1;
+            continue;
+        }
+        int32_t found = -1;
+        for (int32_t t = n2e_ptr[fn[0]]; t < n2e_ptr[fn[0] + 1] && found < 0; ++t) {
+            int64_t k = (int64_t)(n2e[t] >> 4);
+            int hits = 0;
+            int32_t rest = -1;
+            for (int j = 0; j <= dim; ++j) {
+                int32_t v = elems[k * nlb + j];
+                bool in = false;
+                for (int q = 0; q < dim; ++q) in |= (v == fn[q]);
+                if (in) ++hits;
+                else rest = v;
+            }
+            if (hits == dim) found = rest;
+        }
+        opp[f] = found;
+        if (found < 0) atomicOr(err, ERR_FACE_OWNER);
+    }
+}
+
+// float pair split: x = hi + lo with hi = fl32(x), lo = fl32(x - hi)
+__global__ void k_split_coords(int64_t nn, int dim, const double *__restrict__ x, float4 *__restrict__ xh,
+                               float4 *__restrict__ xl) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
+        float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+        for (int d = 0; d < dim; ++d) {
+            double v = x[i * dim + d];
+            h[d] = (float)v;
+            l[d] = (float)(v - (double)h[d]);
+        }
+        xh[i] = make_float4(h[0], h[1], h[2], 0.f);
+        xl[i] = make_float4(l[0], l[1], l[2], 0.f);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// spatial ordering of the rows
+// ---------------------------------------------------------------------------
+__global__ void k_bbox_partial(int64_t nn, int dim, const double *__restrict__ x, double *__restrict__ part) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x)
+        for (int d = 0; d < dim; ++d) {
+            double v = x[i * dim + d];
+            lo[d] = fmin(lo[d], v);
+            hi[d] = fmax(hi[d], v);
+        }
+    __shared__ double s[6][256];
+    for (int d = 0; d < 3; ++d) {
+        s[d][threadIdx.x] = lo[d];
+        s[3 + d][threadIdx.x] = hi[d];
+    }
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int d = 0; d < 3; ++d) {
+                s[d][threadIdx.x] = fmin(s[d][threadIdx.x], s[d][threadIdx.x + o]);
+                s[3 + d][threadIdx.x] = fmax(s[3 + d][threadIdx.x], s[3 + d][threadIdx.x + o]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int d = 0; d < 6; ++d) part[blockIdx.x * 6 + d] = s[d][0];
+}
+
+__device__ __forceinline__ uint32_t spread3(uint32_t v) {  // 10 bits -> every third bit
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+__device__ __forceinline__ uint32_t spread2(uint32_t v) {  // 16 bits -> every second bit
+    v &= 0xffffu;
+    v = (v | (v << 8)) & 0x00ff00ffu;
+    v = (v | (v << 4)) & 0x0f0f0f0fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+__global__ void k_cell_keys(int64_t nn, int dim, int bits, const double *__restrict__ x,
+                            const double *__restrict__ bb, int32_t *__restrict__ key) {
+    const uint32_t G = 1u << bits;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t q[3] = {0, 0, 0};
+        for (int d = 0; d < dim; ++d) {
+            double ext = bb[3 + d] - bb[d];
+            double t = ext > 0 ? (x[i * dim + d] - bb[d]) / ext : 0.0;
+            int64_t c = (int64_t)(t * G);
+            if (c < 0) c = 0;
+            if (c >= (int64_t)G) c = G - 1;
+            q[d] = (uint32_t)c;
+        }
+        key[i] = (int32_t)(dim == 3 ? (spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2))
+                                    : (spread2(q[0]) | (spread2(q[1]) << 1)));
+    }
+}
+
+__global__ void k_hist(int64_t n, const int32_t *__restrict__ key, int32_t *__restrict__ h) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&h[key[i]], 1);
+}
+
+__global__ void k_bucket_scatter(int64_t n, const int32_t *__restrict__ key, int32_t *__restrict__ cursor,
+                                 int32_t *__restrict__ perm) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        perm[atomicAdd(&cursor[key[i]], 1)] = (int32_t)i;
+}
+
+// tile = consecutive ranks whose incidence-weight prefix falls in [t*B, (t+1)*B)
+__global__ void k_rank_weights(int64_t nn, const int32_t *__restrict__ perm, const int32_t *__restrict__ cnt,
+                               int32_t *__restrict__ w) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nn; r += (int64_t)gridDim.x * blockDim.x)
+        w[r] = cnt[perm[r]] + 1;
+}
+
+__global__ void k_tile_flags(int64_t nn, int64_t B, const long long *__restrict__ pre, int32_t *__restrict__ flag) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nn; r += (int64_t)gridDim.x * blockDim.x)
+        flag[r] = (r == 0 || pre[r - 1] / B != pre[r] / B) ? 1 : 0;
+}
+
+__global__ void k_tile_assign(int64_t nn, const int32_t *__restrict__ flag, const long long *__restrict__ fpre,
+                              const int32_t *__restrict__ perm, int32_t *__restrict__ tile_begin,
+                              int32_t *__restrict__ node_tile) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nn; r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t t = (int32_t)(fpre[r] + flag[r] - 1);
+        if (flag[r]) tile_begin[t] = (int32_t)r;
+        node_tile[perm[r]] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-tile sets (one CTA per tile)
+// ---------------------------------------------------------------------------
+__device__ void bitonic_sort(int32_t *a, int n /* power of two */) {
+    for (int k = 2; k <= n; k <<= 1)
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                int l = i ^ j;
+                if (l > i) {
+                    bool up = ((i & k) == 0);
+                    int32_t x = a[i], y = a[l];
+                    if ((x > y) == up) {
+                        a[i] = y;
+                        a[l] = x;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+}
+
+// compacts the sorted array a[0..n) to its distinct values in place; returns the count
+__device__ int unique_sorted(int32_t *a, int n, int32_t *tmp) {
+    long long base = 0;
+    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
+        int i = c0 + threadIdx.x;
+        int keep = (i < n && (i == 0 || a[i] != a[i - 1])) ? 1 : 0;
+        long long tot;
+        long long pos = block_excl_scan(keep, &tot);
+        if (keep) tmp[base + pos] = a[i];
+        base += tot;
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < base; i += blockDim.x) a[i] = tmp[i];
+    __syncthreads();
+    return (int)base;
+}
+
+struct TileCounts {
+    int32_t n_nodes, n_elems, n_own, n_up, n_diag, n_rows, rank_begin, pad;
+};
+
+__device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int32_t x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] < x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Pass A: distinct elements (owned first, each group ascending) and vertex
+// nodes of every tile, plus counts.  An element is owned by the tile holding
+// the row of its first vertex.
+__global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e, int cap_n,
+                            const int32_t *__restrict__ tile_begin, const int32_t *__restrict__ perm,
+                            const int32_t *__restrict__ n2e_ptr, const int32_t *__restrict__ n2e,
+                            const int32_t *__restrict__ elems, const int32_t *__restrict__ row_ptr,
+                            const int32_t *__restrict__ col_idx, const int32_t *__restrict__ node_tile,
+                            int32_t *__restrict__ sc_elems, int32_t *__restrict__ sc_nodes,
+                            TileCounts *__restrict__ counts, int *__restrict__ err) {
+    extern __shared__ int32_t sm[];
+    const int t = blockIdx.x;
+    if (t >= n_tiles) return;
+    int32_t *ce = sm;                 // cap_e (power of two)
+    int32_t *cn = sm + cap_e;         // cap_n (power of two)
+    int32_t *tmp = cn + cap_n;        // max(cap_e, cap_n)
+    const int rb = tile_begin[t];
+    const int re = (t + 1 < n_tiles) ? tile_begin[t + 1] : (int)nn;
+    __shared__ int s_ne;
+    if (threadIdx.x == 0) s_ne = 0;
+    __syncthreads();
+    for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
+        int32_t i = perm[r];
+        int32_t b = n2e_ptr[i], e = n2e_ptr[i + 1];
+        int pos = atomicAdd(&s_ne, e - b);
+        for (int32_t q = b; q < e; ++q)
+            if (pos + (q - b) < cap_e) ce[pos + (q - b)] = n2e[q] >> 4;
+    }
+    __syncthreads();
+    const int ncand = s_ne;
+    if (ncand > cap_e) {
+        if (threadIdx.x == 0) atomicOr(err, 32);
+        return;
+    }
+    for (int i = ncand + threadIdx.x; i < cap_e; i += blockDim.x) ce[i] = 0x7fffffff;
+    __syncthreads();
+    bitonic_sort(ce, cap_e);
+    const int n_el = unique_sorted(ce, ncand, tmp);
+    // owned elements first (stable partition)
+    long long obase = 0, hbase = 0, n_own = 0;
+    {
+        long long own = 0;
+        for (int i = threadIdx.x; i < n_el; i += blockDim.x) own += (node_tile[elems[(int64_t)ce[i] * nlb]] == t);
+        block_excl_scan(own, &n_own);
+    }
+    for (int c0 = 0; c0 < n_el; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        int own = 0, halo = 0;
+        if (i < n_el) {
+            own = node_tile[elems[(int64_t)ce[i] * nlb]] == t;
+            halo = !own;
+        }
+        long long tot_o, tot_h;
+        long long po = block_excl_scan(own, &tot_o);
+        long long ph = block_excl_scan(halo, &tot_h);
+        if (own) tmp[obase + po] = ce[i];
+        if (halo) tmp[n_own + hbase + ph] = ce[i];
+        obase += tot_o;
+        hbase += tot_h;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n_el; i += blockDim.x) sc_elems[(int64_t)t * cap_e + i] = tmp[i];
+    // vertex nodes of those elements
+    const int nv = dim + 1;
+    const int nnc = n_el * nv;
+    if (nnc > cap_n) {
+        if (threadIdx.x == 0) atomicOr(err, 32);
+        return;
+    }
+    for (int i = threadIdx.x; i < cap_n; i += blockDim.x)
+        cn[i] = (i < nnc) ? elems[(int64_t)ce[i / nv] * nlb + (i % nv)] : 0x7fffffff;
+    __syncthreads();
+    bitonic_sort(cn, cap_n);
+    const int n_nd = unique_sorted(cn, nnc, tmp);
+    for (int i = threadIdx.x; i < n_nd; i += blockDim.x) sc_nodes[(int64_t)t * cap_n + i] = cn[i];
+    // upper pairs {i, j > i} and diagonals of the tile's rows
+    long long up = 0, dg = 0;
+    for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
+        const int32_t i = perm[r];
+        const int32_t b = row_ptr[i], len = row_ptr[i + 1] - b;
+        if (len == 0) continue;
+        const int ds = lower_bound_i32(col_idx + b, len, i);
+        up += len - ds - 1;
+        dg += 1;
+    }
+    long long tot_up, tot_dg;
+    block_excl_scan(up, &tot_up);
+    block_excl_scan(dg, &tot_dg);
+    if (threadIdx.x == 0) {
+        TileCounts c;
+        c.n_nodes = n_nd;
+        c.n_elems = n_el;
+        c.n_own = (int32_t)n_own;
+        c.n_up = (int32_t)tot_up;
+        c.n_diag = (int32_t)tot_dg;
+        c.n_rows = re - rb;
+        c.rank_begin = rb;
+        c.pad = 0;
+        counts[t] = c;
+    }
+}
+
+// local index of global element k in a tile's element list (owned block then halo block)
+__device__ __forceinline__ int tile_local_elem(const int32_t *te, int n_own, int n_el, int32_t k) {
+    int p = lower_bound_i32(te, n_own, k);
+    if (p < n_own && te[p] == k) return p;
+    return n_own + lower_bound_i32(te + n_own, n_el - n_own, k);
+}
+
+// Pass B: node lists, element records, owned ids, pair positions and the
+// contribution count of every pair.
+__global__ void k_tile_fill(int n_tiles, int dim, int nlb, int cap_e, int cap_n, const TileHdr *__restrict__ hdr,
+                            const int32_t *__restrict__ perm, const int32_t *__restrict__ n2e_ptr,
+                            const int32_t *__restrict__ n2e, const int32_t *__restrict__ elems,
+                            const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+                            const int32_t *__restrict__ sc_elems, const int32_t *__restrict__ sc_nodes,
+                            int32_t *__restrict__ tile_nodes, ushort4 *__restrict__ tile_elem,
+                            int32_t *__restrict__ tile_own, int2 *__restrict__ tile_nzpos,
+                            int32_t *__restrict__ nz_count, int2 *__restrict__ row_info) {
+    const int t = blockIdx.x;
+    if (t >= n_tiles) return;
+    const TileHdr h = hdr[t];
+    const int32_t *te = sc_elems + (int64_t)t * cap_e;
+    const int32_t *tn = sc_nodes + (int64_t)t * cap_n;
+    for (int i = threadIdx.x; i < h.n_nodes; i += blockDim.x) tile_nodes[h.node_off + i] = tn[i];
+    for (int e = threadIdx.x; e < h.n_elems; e += blockDim.x) {
+        const int64_t k = te[e];
+        unsigned short v[4] = {0, 0, 0, 0};
+        for (int j = 0; j <= dim; ++j) v[j] = (unsigned short)lower_bound_i32(tn, h.n_nodes, elems[k * nlb + j]);
+        tile_elem[h.elem_off + e] = make_ushort4(v[0], v[1], v[2], v[3]);
+        if (e < h.n_own) tile_own[h.own_off + e] = (int32_t)k;
+    }
+    // per-row base of its upper pairs and index of its diagonal (rank order)
+    long long ubase = 0, dbase = 0;
+    for (int c0 = 0; c0 < h.n_rows; c0 += blockDim.x) {
+        const int rr = c0 + threadIdx.x;
+        long long up = 0, hasd = 0;
+        int32_t i = -1, b = 0, len = 0, ds = 0;
+        if (rr < h.n_rows) {
+            i = perm[h.rank_begin + rr];
+            b = row_ptr[i];
+            len = row_ptr[i + 1] - b;
+            if (len > 0) {
+                ds = lower_bound_i32(col_idx + b, len, i);
+                up = len - ds - 1;
+                hasd = 1;
+            }
+        }
+        long long tot_u, tot_d;
+        const long long pu = block_excl_scan(up, &tot_u);
+        const long long pd = block_excl_scan(hasd, &tot_d);
+        if (rr < h.n_rows) {
+            const int32_t qu = (int32_t)(ubase + pu);
+            const int32_t qd = hasd ? h.n_up + (int32_t)(dbase + pd) : -1;
+            for (int s = ds + 1; s < len; ++s) {
+                const int32_t j = col_idx[b + s];
+                const int32_t bj = row_ptr[j], lj = row_ptr[j + 1] - bj;
+                const int32_t pji = bj + lower_bound_i32(col_idx + bj, lj, i);
+                tile_nzpos[h.nz_off + qu + (s - ds - 1)] = make_int2(b + s, pji);
+                nz_count[h.nz_off + qu + (s - ds - 1)] = 0;
+            }
+            if (hasd) {
+                tile_nzpos[h.nz_off + qd] = make_int2(b + ds, b + ds);
+                nz_count[h.nz_off + qd] = 0;
+            }
+            row_info[h.rank_begin + rr] = make_int2(qu, qd);
+        }
+        ubase += tot_u;
+        dbase += tot_d;
+    }
+    __syncthreads();
+    // contribution counts: one thread per row, every pair it owns is private to it
+    for (int rr = threadIdx.x; rr < h.n_rows; rr += blockDim.x) {
+        const int32_t i = perm[h.rank_begin + rr];
+        const int32_t b = row_ptr[i], len = row_ptr[i + 1] - b;
+        if (len == 0) continue;
+        const int2 ri = row_info[h.rank_begin + rr];
+        const int ds = lower_bound_i32(col_idx + b, len, i);
+        for (int32_t q = n2e_ptr[i]; q < n2e_ptr[i + 1]; ++q) {
+            const int64_t k = n2e[q] >> 4;
+            for (int bb = 0; bb < nlb; ++bb) {
+                const int32_t c = elems[k * nlb + bb];
+                if (c < i) continue;
+                const int32_t qq = (c == i) ? ri.y : ri.x + lower_bound_i32(col_idx + b, len, c) - ds - 1;
+                nz_count[h.nz_off + qq] += 1;
+            }
+        }
+    }
+}
+
+// chunk widths (largest contribution count of 32 consecutive pairs) and the
+// tile-relative code offset of every chunk
+__global__ void k_chunk_table(int n_tiles, const TileHdr *__restrict__ hdr, const int32_t *__restrict__ nz_count,
+                              int2 *__restrict__ chunks, int32_t *__restrict__ tile_codes_n) {
+    const int t = blockIdx.x;
+    if (t >= n_tiles) return;
+    const TileHdr h = hdr[t];
+    const int n_up_chunks = (h.n_up + 31) / 32;
+    __shared__ int32_t w[1024];
+    for (int c = threadIdx.x; c < h.n_chunks; c += blockDim.x) {
+        int q0, q1;
+        if (c < n_up_chunks) {
+            q0 = c * 32;
+            q1 = min(q0 + 32, h.n_up);
+        } else {
+            q0 = h.n_up + (c - n_up_chunks) * 32;
+            q1 = min(q0 + 32, h.n_nz);
+        }
+        int wd = 0;
+        for (int q = q0; q < q1; ++q) wd = max(wd, nz_count[h.nz_off + q]);
+        if (c < 1024) w[c] = wd;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int32_t off = 0;
+        for (int c = 0; c < h.n_chunks && c < 1024; ++c) {
+            chunks[h.chunk_off + c] = make_int2(off, w[c]);
+            off += 32 * w[c];
+        }
+        tile_codes_n[t] = off;
+    }
+}
+
+// Pass C: contribution codes (local element, packed (a,b) entry), ascending
+// element order per pair; padding slots point at the tile's zero element.
+template <typename CT, int UBITS>
+__global__ void k_tile_codes(int n_tiles, int nv, int nlb, int cap_e, const TileHdr *__restrict__ hdr,
+                             const int32_t *__restrict__ perm, const int32_t *__restrict__ n2e_ptr,
+                             const int32_t *__restrict__ n2e, const int32_t *__restrict__ elems,
+                             const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
+                             const int32_t *__restrict__ sc_elems, const int2 *__restrict__ row_info,
+                             const int2 *__restrict__ chunks, int32_t *__restrict__ fill, CT *__restrict__ codes) {
+    const int t = blockIdx.x;
+    if (t >= n_tiles) return;
+    const TileHdr h = hdr[t];
+    const int32_t *te = sc_elems + (int64_t)t * cap_e;
+    const int n_up_chunks = (h.n_up + 31) / 32;
+    const CT dummy = (CT)((uint32_t)h.n_elems << UBITS);
+    for (int i = threadIdx.x; i < h.n_codes; i += blockDim.x) codes[(int64_t)h.code_off + i] = dummy;
+    __syncthreads();
+    for (int rr = threadIdx.x; rr < h.n_rows; rr += blockDim.x) {
+        const int32_t i = perm[h.rank_begin + rr];
+        const int32_t b = row_ptr[i], len = row_ptr[i + 1] - b;
+        if (len == 0) continue;
+        const int2 ri = row_info[h.rank_begin + rr];
+        const int ds = lower_bound_i32(col_idx + b, len, i);
+        for (int32_t q = n2e_ptr[i]; q < n2e_ptr[i + 1]; ++q) {
+            const int64_t k = n2e[q] >> 4;
+            const int a = n2e[q] & 15;
+            const int el = tile_local_elem(te, h.n_own, h.n_elems, (int32_t)k);
+            for (int bb = 0; bb < nlb; ++bb) {
+                const int32_t c = elems[k * nlb + bb];
+                if (c < i) continue;
+                const int32_t qq = (c == i) ? ri.y : ri.x + lower_bound_i32(col_idx + b, len, c) - ds - 1;
+                int chunk, lane;
+                if (qq < h.n_up) {
+                    chunk = qq >> 5;
+                    lane = qq & 31;
+                } else {
+                    chunk = n_up_chunks + ((qq - h.n_up) >> 5);
+                    lane = (qq - h.n_up) & 31;
+                }
+                const int tt = fill[h.nz_off + qq]++;
+                const int2 ch = chunks[h.chunk_off + chunk];
+                const int p = a < bb ? a : bb, r = a < bb ? bb : a;
+                const uint32_t u = (uint32_t)(p * nlb - p * (p - 1) / 2 + (r - p));
+                codes[(int64_t)h.code_off + ch.x + tt * 32 + lane] = (CT)(((uint32_t)el << UBITS) | u);
+            }
+        }
+    }
+}
+
+int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+template <typename T>
+vla_status dalloc(vla_mesh *m, T **p, size_t count, cudaStream_t st) {
+    size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+    cudaError_t e = cudaMallocAsync((void **)p, bytes, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(VLA_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    }
+    m->allocs.push_back((void *)*p);
+    m->device_bytes += (int64_t)bytes;
+    return VLA_OK;
+}
+
+struct Scratch {  // temporary device buffers freed at the end of the build
+    std::vector<void *> bufs;
+    cudaStream_t st;
+    template <typename T>
+    vla_status get(T **p, size_t count) {
+        size_t bytes = sizeof(T) * (count > 0 ? count : 1);
+        cudaError_t e = cudaMallocAsync((void **)p, bytes, st);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(VLA_ERR_OOM, "device scratch allocation of %zu bytes failed", bytes);
+        }
+        bufs.push_back((void *)*p);
+        return VLA_OK;
+    }
+    ~Scratch() {
+        for (void *b : bufs) cudaFreeAsync(b, st);
+    }
+};
+
+#define TRY(x)                    \
+    do {                          \
+        vla_status s_ = (x);      \
+        if (s_ != VLA_OK) return s_; \
+    } while (0)
+
+// incidence budget of a tile (sum over its rows of 1 + incident elements)
+int tile_budget(int dim, int order) {
+    if (order == 1) return dim == 3 ? 1600 : 2048;
+    return dim == 3 ? 384 : 1024;
+}
+
+vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const int32_t *faces) {
+    cudaStream_t st = m->stream;
+    const int dim = m->dim, nlb = m->nlb;
+    const int64_t nn = m->nn, ne = m->ne, nfb = m->nfb;
+    Scratch S;
+    S.st = st;
+    const int TB = 256;
+
+    TRY(dalloc(m, &m->coords, nn * dim, st));
+    TRY(dalloc(m, &m->elems, ne * nlb, st));
+    VLA_CUDA(cudaMemcpyAsync(m->coords, coords, sizeof(double) * nn * dim, cudaMemcpyDeviceToDevice, st));
+    VLA_CUDA(cudaMemcpyAsync(m->elems, elems, sizeof(int32_t) * ne * nlb, cudaMemcpyDeviceToDevice, st));
+    if (nfb > 0) {
+        TRY(dalloc(m, &m->faces, nfb * dim, st));
+        TRY(dalloc(m, &m->face_opp, nfb, st));
+        VLA_CUDA(cudaMemcpyAsync(m->faces, faces, sizeof(int32_t) * nfb * dim, cudaMemcpyDeviceToDevice, st));
+    }
+
+    // ---- validation + incidence counts
+    int *d_err;
+    long long *d_bad;
+    int32_t *cnt;
+    TRY(S.get(&d_err, 1));
+    TRY(S.get(&d_bad, 1));
+    TRY(S.get(&cnt, nn));
+    VLA_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+    const long long big = 0x7fffffffffffffffll;
+    VLA_CUDA(cudaMemcpyAsync(d_bad, &big, sizeof(long long), cudaMemcpyHostToDevice, st));
+    VLA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nn, st));
+    k_validate_count<<<grid_for(ne, TB), TB, 0, st>>>(ne, nlb, nn, m->elems, cnt, d_err, d_bad);
+    VLA_CUDA(cudaGetLastError());
+    int h_err = 0;
+    long long h_bad = 0;
+    VLA_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VLA_CUDA(cudaMemcpyAsync(&h_bad, d_bad, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    VLA_CUDA(cudaStreamSynchronize(st));
+    if (h_err & ERR_OOB) return fail(VLA_ERR_INDEX_OOB, "element %lld references a node outside [0, %lld)", h_bad, (long long)nn);
+    if (h_err & ERR_DUP) return fail(VLA_ERR_DEGENERATE, "element %lld repeats a node", h_bad);
+
+    // ---- node -> element incidence (sorted by element)
+    long long *pre;
+    TRY(S.get(&pre, nn + 1));
+    long long n2e_total = 0;
+    TRY(excl_scan<int32_t>(cnt, nn, pre, st, &n2e_total));
+    TRY(dalloc(m, &m->n2e_ptr, nn + 1, st));
+    TRY(dalloc(m, &m->n2e, n2e_total, st));
+    k_i64_to_i32<<<grid_for(nn + 1, TB, 1 << 30), TB, 0, st>>>(nn + 1, pre, m->n2e_ptr);
+    int32_t *cursor;
+    TRY(S.get(&cursor, nn + 1));
+    VLA_CUDA(cudaMemcpyAsync(cursor, m->n2e_ptr, sizeof(int32_t) * (nn + 1), cudaMemcpyDeviceToDevice, st));
+    k_fill_n2e<<<grid_for(ne, TB), TB, 0, st>>>(ne, nlb, m->elems, cursor, m->n2e);
+    k_sort_segments<<<grid_for(nn, 128), 128, 0, st>>>(nn, m->n2e_ptr, m->n2e);
+    VLA_CUDA(cudaGetLastError());
+
+    // ---- CSR pattern
+    int32_t *scratch, *rowlen;
+    TRY(S.get(&scratch, (size_t)n2e_total * nlb));
+    TRY(S.get(&rowlen, nn));
+    k_row_count<<<grid_for(nn, 128), 128, 0, st>>>(nn, nlb, m->elems, m->n2e_ptr, m->n2e, scratch, rowlen, d_err);
+    VLA_CUDA(cudaGetLastError());
+    long long nnz = 0;
+    TRY(excl_scan<int32_t>(rowlen, nn, pre, st, &nnz));
+    VLA_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VLA_CUDA(cudaStreamSynchronize(st));
+    if (h_err & ERR_ROWLEN) return fail(VLA_ERR_UNSUPPORTED, "a CSR row has more than %d entries", kMaxRow);
+    if (nnz > 0x7fffffffll) return fail(VLA_ERR_UNSUPPORTED, "nnz %lld exceeds int32", nnz);
+    m->nnz = nnz;
+    TRY(dalloc(m, &m->row_ptr, nn + 1, st));
+    TRY(dalloc(m, &m->col_idx, nnz, st));
+    k_i64_to_i32<<<grid_for(nn + 1, TB, 1 << 30), TB, 0, st>>>(nn + 1, pre, m->row_ptr);
+    k_row_fill<<<grid_for(nn, TB), TB, 0, st>>>(nn, nlb, m->n2e_ptr, scratch, m->row_ptr, m->col_idx);
+    VLA_CUDA(cudaGetLastError());
+
+    // ---- boundary facet owners
+    if (nfb > 0) {
+        k_face_owner<<<grid_for(nfb, TB), TB, 0, st>>>(nfb, dim, nlb, nn, m->faces, m->elems, m->n2e_ptr, m->n2e,
+                                                        m->face_opp, d_err);
+        VLA_CUDA(cudaGetLastError());
+        VLA_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        VLA_CUDA(cudaStreamSynchronize(st));
+        if (h_err & ERR_FACE_OOB) return fail(VLA_ERR_INDEX_OOB, "a boundary facet references a node outside [0, %lld)", (long long)nn);
+        if (h_err & ERR_FACE_OWNER) return fail(VLA_ERR_DEGENERATE, "a boundary facet is not a facet of any element");
+    }
+
+    // ---- float pair coordinates
+    TRY(dalloc(m, &m->xh, nn, st));
+    TRY(dalloc(m, &m->xl, nn, st));
+    k_split_coords<<<grid_for(nn, TB), TB, 0, st>>>(nn, dim, m->coords, m->xh, m->xl);
+    VLA_CUDA(cudaGetLastError());
+
+    // ---- spatial order of the rows (Morton code of the cell, then node id)
+    const int nbb = 256;
+    double *bbp, *bbf;
+    TRY(S.get(&bbp, nbb * 6));
+    TRY(S.get(&bbf, 6));
+    k_bbox_partial<<<nbb, 256, 0, st>>>(nn, dim, m->coords, bbp);
+    VLA_CUDA(cudaGetLastError());
+    double hbb[nbb * 6];
+    VLA_CUDA(cudaMemcpyAsync(hbb, bbp, sizeof(hbb), cudaMemcpyDeviceToHost, st));
+    VLA_CUDA(cudaStreamSynchronize(st));
+    double bb[6] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300};
+    for (int b = 0; b < nbb; ++b)
+        for (int d = 0; d < 3; ++d) {
+            bb[d] = std::min(bb[d], hbb[b * 6 + d]);
+            bb[3 + d] = std::max(bb[3 + d], hbb[b * 6 + 3 + d]);
+        }
+    VLA_CUDA(cudaMemcpyAsync(bbf, bb, sizeof(bb), cudaMemcpyHostToDevice, st));
+    int bits = 1;
+    {
+        double cells = (double)nn / 8.0;
+        while (bits < (dim == 3 ? 7 : 10) && std::pow(2.0, (double)(bits * dim)) < cells) ++bits;
+    }
+    const int64_t nkeys = (int64_t)1 << (bits * dim);
+    int32_t *key, *hist, *perm;
+    long long *hpre;
+    TRY(S.get(&key, nn));
+    TRY(S.get(&hist, nkeys));
+    TRY(S.get(&hpre, nkeys + 1));
+    TRY(S.get(&perm, nn));
+    k_cell_keys<<<grid_for(nn, TB), TB, 0, st>>>(nn, dim, bits, m->coords, bbf, key);
+    VLA_CUDA(cudaMemsetAsync(hist, 0, sizeof(int32_t) * nkeys, st));
+    k_hist<<<grid_for(nn, TB), TB, 0, st>>>(nn, key, hist);
+    VLA_CUDA(cudaGetLastError());
+    TRY(excl_scan<int32_t>(hist, nkeys, hpre, st, nullptr));
+    int32_t *bptr;
+    TRY(S.get(&bptr, nkeys + 1));
+    k_i64_to_i32<<<grid_for(nkeys + 1, TB, 1 << 30), TB, 0, st>>>(nkeys + 1, hpre, bptr);
+    int32_t *bcur;
+    TRY(S.get(&bcur, nkeys + 1));
+    VLA_CUDA(cudaMemcpyAsync(bcur, bptr, sizeof(int32_t) * (nkeys + 1), cudaMemcpyDeviceToDevice, st));
+    k_bucket_scatter<<<grid_for(nn, TB), TB, 0, st>>>(nn, key, bcur, perm);
+    k_sort_segments<<<grid_for(nkeys, 128), 128, 0, st>>>(nkeys, bptr, perm);
+    VLA_CUDA(cudaGetLastError());
+
+    // ---- tiles: consecutive ranks, incidence-weight budget B
+    int B = tile_budget(dim, m->order);
+    if (const char *tb = getenv("VLA_TILE_BUDGET")) B = std::max(64, atoi(tb));   // tuning override
+    m->tile_budget = B;
+    int32_t *w, *flag, *tile_begin, *node_tile;
+    long long *fpre;
+    TRY(S.get(&w, nn));
+    TRY(S.get(&flag, nn));
+    TRY(S.get(&fpre, nn + 1));
+    TRY(S.get(&node_tile, nn));
+    k_rank_weights<<<grid_for(nn, TB), TB, 0, st>>>(nn, perm, cnt, w);
+    TRY(excl_scan<int32_t>(w, nn, pre, st, nullptr));
+    k_tile_flags<<<grid_for(nn, TB), TB, 0, st>>>(nn, B, pre, flag);
+    long long n_tiles = 0;
+    TRY(excl_scan<int32_t>(flag, nn, fpre, st, &n_tiles));
+    TRY(S.get(&tile_begin, n_tiles + 1));
+    k_tile_assign<<<grid_for(nn, TB), TB, 0, st>>>(nn, flag, fpre, perm, tile_begin, node_tile);
+    VLA_CUDA(cudaGetLastError());
+    m->n_tiles = (int32_t)n_tiles;
+
+    // max incidence of a single node bounds the tile's candidate count: B + max weight
+    std::vector<int32_t> hcnt(nn);
+    VLA_CUDA(cudaMemcpyAsync(hcnt.data(), cnt, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, st));
+    VLA_CUDA(cudaStreamSynchronize(st));
+    int wmax = 0;
+    for (int64_t i = 0; i < nn; ++i) wmax = std::max(wmax, hcnt[i] + 1);
+    if (wmax > B) return fail(VLA_ERR_UNSUPPORTED, "a node belongs to %d elements (tile budget %d)", wmax - 1, B);
+    const int cap_e = next_pow2(B + wmax);
+    const int cap_n = next_pow2((dim + 1) * (B + wmax));
+    int32_t *sc_elems, *sc_nodes;
+    TileCounts *tcnt;
+    TRY(S.get(&sc_elems, (size_t)n_tiles * cap_e));
+    TRY(S.get(&sc_nodes, (size_t)n_tiles * cap_n));
+    TRY(S.get(&tcnt, n_tiles));
+    const size_t smemA = sizeof(int32_t) * (cap_e + cap_n + std::max(cap_e, cap_n));
+    VLA_CUDA(cudaFuncSetAttribute(k_tile_sets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemA));
+    k_tile_sets<<<(int)n_tiles, 256, smemA, st>>>((int)n_tiles, nn, dim, nlb, cap_e, cap_n, tile_begin, perm,
+                                                   m->n2e_ptr, m->n2e, m->elems, m->row_ptr, m->col_idx, node_tile,
+                                                   sc_elems, sc_nodes, tcnt, d_err);
+    VLA_CUDA(cudaGetLastError());
+    std::vector<TileCounts> hc(n_tiles);
+    VLA_CUDA(cudaMemcpyAsync(hc.data(), tcnt, sizeof(TileCounts) * n_tiles, cudaMemcpyDeviceToHost, st));
+    VLA_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VLA_CUDA(cudaStreamSynchronize(st));
+    if (h_err & 32) return fail(VLA_ERR_UNSUPPORTED, "tile candidate capacity exceeded");
+
+    // tile offsets (host scan over a few thousand tiles); every segment padded for bulk copies
+    auto pad = [](int64_t x, int64_t q) { return (x + q - 1) / q * q; };
+    std::vector<TileHdr> hh(n_tiles);
+    int64_t o_node = 0, o_elem = 0, o_own = 0, o_nz = 0, o_chunk = 0, n_own_total = 0, nz_total = 0;
+    m->max_tile_nodes = m->max_tile_elems = m->max_tile_nz = 0;
+    m->tile_elems_total = 0;
+    for (int64_t t = 0; t < n_tiles; ++t) {
+        TileHdr &h = hh[t];
+        std::memset(&h, 0, sizeof(h));
+        const TileCounts &c = hc[t];
+        h.node_off = (int32_t)o_node;
+        h.n_nodes = c.n_nodes;
+        h.elem_off = (int32_t)o_elem;
+        h.n_elems = c.n_elems;
+        h.own_off = (int32_t)o_own;
+        h.n_own = c.n_own;
+        h.nz_off = (int32_t)o_nz;
+        h.n_nz = c.n_up + c.n_diag;
+        h.n_up = c.n_up;
+        h.chunk_off = (int32_t)o_chunk;
+        h.n_chunks = (c.n_up + 31) / 32 + (c.n_diag + 31) / 32;
+        h.rank_begin = c.rank_begin;
+        h.n_rows = c.n_rows;
+        o_node += pad(c.n_nodes, kTilePadNodes);
+        o_elem += pad(c.n_elems, kTilePadElems);
+        o_own += pad(c.n_own, kTilePadOwn);
+        o_nz += pad(h.n_nz, kTilePadNz);
+        o_chunk += pad(h.n_chunks, kTilePadChunks);
+        n_own_total += c.n_own;
+        nz_total += 2LL * c.n_up + c.n_diag;
+        m->tile_elems_total += c.n_elems;
+        m->max_tile_nodes = std::max(m->max_tile_nodes, c.n_nodes);
+        m->max_tile_elems = std::max(m->max_tile_elems, c.n_elems);
+        m->max_tile_nz = std::max(m->max_tile_nz, h.n_nz);
+        if (h.n_chunks > 1024) return fail(VLA_ERR_UNSUPPORTED, "tile has more than 1024 chunks");
+    }
+    if (n_own_total != ne) return fail(VLA_ERR_CUDA, "internal: tiles own %lld of %lld elements", (long long)n_own_total, (long long)ne);
+    if (nz_total != nnz) return fail(VLA_ERR_CUDA, "internal: tiles cover %lld of %lld nonzeros", (long long)nz_total, nnz);
+    if (m->max_tile_elems >= 0xffff || m->max_tile_nodes > 0xffff)
+        return fail(VLA_ERR_UNSUPPORTED, "tile exceeds 65534 elements or 65535 nodes");
+    if (m->order == 1 && m->max_tile_elems >= 4095)
+        return fail(VLA_ERR_UNSUPPORTED, "P1 tile has %d elements (limit 4094)", m->max_tile_elems);
+    TRY(dalloc(m, &m->tiles, n_tiles, st));
+    VLA_CUDA(cudaMemcpyAsync(m->tiles, hh.data(), sizeof(TileHdr) * n_tiles, cudaMemcpyHostToDevice, st));
+    // +16 bytes of slack: bulk copies round sizes up to 16 bytes
+    TRY(dalloc(m, &m->tile_nodes, o_node + 4, st));
+    TRY(dalloc(m, &m->tile_elem, o_elem + 2, st));
+    TRY(dalloc(m, &m->tile_own, o_own + 4, st));
+    TRY(dalloc(m, &m->tile_nzpos, o_nz + 2, st));
+    TRY(dalloc(m, &m->tile_chunks, o_chunk + 2, st));
+    VLA_CUDA(cudaMemsetAsync(m->tile_nodes, 0, sizeof(int32_t) * (o_node + 4), st));
+    VLA_CUDA(cudaMemsetAsync(m->tile_elem, 0, sizeof(ushort4) * (o_elem + 2), st));
+    VLA_CUDA(cudaMemsetAsync(m->tile_own, 0, sizeof(int32_t) * (o_own + 4), st));
+    VLA_CUDA(cudaMemsetAsync(m->tile_nzpos, 0, sizeof(int2) * (o_nz + 2), st));
+    VLA_CUDA(cudaMemsetAsync(m->tile_chunks, 0, sizeof(int2) * (o_chunk + 2), st));
+    int32_t *nz_count, *tile_ncodes;
+    int2 *row_info;
+    TRY(S.get(&nz_count, o_nz + 2));
+    TRY(S.get(&row_info, nn));
+    TRY(S.get(&tile_ncodes, n_tiles));
+    k_tile_fill<<<(int)n_tiles, 256, 0, st>>>((int)n_tiles, dim, nlb, cap_e, cap_n, m->tiles, perm, m->n2e_ptr,
+                                              m->n2e, m->elems, m->row_ptr, m->col_idx, sc_elems, sc_nodes,
+                                              m->tile_nodes, m->tile_elem, m->tile_own, m->tile_nzpos, nz_count,
+                                              row_info);
+    k_chunk_table<<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, m->tiles, nz_count, m->tile_chunks, tile_ncodes);
+    VLA_CUDA(cudaGetLastError());
+    std::vector<int32_t> hnc(n_tiles);
+    VLA_CUDA(cudaMemcpyAsync(hnc.data(), tile_ncodes, sizeof(int32_t) * n_tiles, cudaMemcpyDeviceToHost, st));
+    VLA_CUDA(cudaStreamSynchronize(st));
+    int64_t o_code = 0;
+    const size_t code_bytes = (m->order == 1) ? 2 : 4;
+    size_t stage_max = 0;
+    for (int64_t t = 0; t < n_tiles; ++t) {
+        hh[t].code_off = (int32_t)o_code;
+        hh[t].n_codes = hnc[t];
+        o_code += hnc[t];
+        if (o_code > 0x7fffffffll) return fail(VLA_ERR_UNSUPPORTED, "too many contribution codes");
+        const TileHdr &h = hh[t];
+        size_t stage = 4 * pad(h.n_nodes, kTilePadNodes) + 8 * pad(h.n_elems, kTilePadElems) +
+                       4 * pad(h.n_own, kTilePadOwn) + 8 * pad(h.n_chunks, kTilePadChunks) +
+                       8 * pad(h.n_nz, kTilePadNz) + code_bytes * h.n_codes;
+        stage_max = std::max(stage_max, stage);
+    }
+    m->tile_stage_bytes = stage_max;
+    m->n_codes = o_code;
+    VLA_CUDA(cudaMemcpyAsync(m->tiles, hh.data(), sizeof(TileHdr) * n_tiles, cudaMemcpyHostToDevice, st));
+    int32_t *fill;
+    TRY(S.get(&fill, o_nz + 2));
+    VLA_CUDA(cudaMemsetAsync(fill, 0, sizeof(int32_t) * (o_nz + 2), st));
+    if (m->order == 1) {
+        uint16_t *codes;
+        TRY(dalloc(m, &codes, o_code + 64, st));
+        k_tile_codes<uint16_t, 4><<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, m->tiles, perm,
+                                                                 m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
+                                                                 m->col_idx, sc_elems, row_info, m->tile_chunks,
+                                                                 fill, codes);
+        m->tile_codes = codes;
+    } else {
+        uint32_t *codes;
+        TRY(dalloc(m, &codes, o_code + 64, st));
+        k_tile_codes<uint32_t, 8><<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, m->tiles, perm,
+                                                                 m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
+                                                                 m->col_idx, sc_elems, row_info, m->tile_chunks,
+                                                                 fill, codes);
+        m->tile_codes = codes;
+    }
+    VLA_CUDA(cudaGetLastError());
+    TRY(dalloc(m, &m->d_err, 1, st));
+    VLA_CUDA(cudaMemsetAsync(m->d_err, 0, sizeof(int32_t), st));
+    m->spin_limit = 1 << 22;
+    if (const char *sl = getenv("VLA_DEBUG_SPIN_LIMIT")) m->spin_limit = atoi(sl);
+    // max row length (host, from row_ptr)
+    std::vector<int32_t> hrp(nn + 1);
+    VLA_CUDA(cudaMemcpyAsync(hrp.data(), m->row_ptr, sizeof(int32_t) * (nn + 1), cudaMemcpyDeviceToHost, st));
+    VLA_CUDA(cudaStreamSynchronize(st));
+    int mr = 0;
+    for (int64_t i = 0; i < nn; ++i) mr = std::max(mr, hrp[i + 1] - hrp[i]);
+    m->max_row_len = mr;
+    return VLA_OK;
+}
+
+}  // namespace
+
+vla_status mesh_build(vla_mesh *m, const double *coords, const int32_t *elems, const int32_t *faces) {
+    return build(m, coords, elems, faces);
+}
+
+}  // namespace vla
+
+using namespace vla;
+
+extern "C" vla_status vla_mesh_create(int32_t dim, int32_t order, int64_t nn, int64_t ne, const double *coords,
+                                      const int32_t *elems, int64_t nfb, const int32_t *faces, void *stream,
+                                      vla_mesh **out) {
+    if (!out) return fail(VLA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return fail(VLA_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (order != VLA_P1 && order != VLA_P2) return fail(VLA_ERR_INVALID_ARG, "order must be VLA_P1 or VLA_P2");
+    if (nn < 1 || ne < 1 || nfb < 0) return fail(VLA_ERR_INVALID_ARG, "need nn >= 1, ne >= 1, nfb >= 0");
+    if (nn > 0x7fffffffll || nfb > 0x7fffffffll) return fail(VLA_ERR_INVALID_ARG, "counts must fit int32");
+    if (ne >= ((int64_t)1 << 27)) return fail(VLA_ERR_UNSUPPORTED, "ne must be below 2^27");
+    if (!coords || !elems || (nfb > 0 && !faces)) return fail(VLA_ERR_INVALID_ARG, "null mesh array");
+    vla_mesh *m = new (std::nothrow) vla_mesh();
+    if (!m) return fail(VLA_ERR_OOM, "host allocation failed");
+    m->dim = dim;
+    m->order = order;
+    m->nlb = order == VLA_P1 ? dim + 1 : (dim + 1) * (dim + 2) / 2;
+    m->nn = nn;
+    m->ne = ne;
+    m->nfb = nfb;
+    m->stream = (cudaStream_t)stream;
+    vla_status s = mesh_build(m, coords, elems, faces);
+    if (s != VLA_OK) {
+        char keep[512];
+        vla_last_error(keep, sizeof(keep));
+        vla_mesh_destroy(m);
+        set_error("%s", keep);
+        return s;
+    }
+    cudaError_t e = cudaStreamSynchronize(m->stream);
+    if (e != cudaSuccess) {
+        vla_mesh_destroy(m);
+        return cuda_fail(e, "mesh build");
+    }
+    *out = m;
+    return VLA_OK;
+}
+
+extern "C" vla_status vla_mesh_destroy(vla_mesh *m) {
+    if (!m) return VLA_OK;
+    cudaStreamSynchronize(m->stream);
+    for (void *p : m->allocs) cudaFreeAsync(p, m->stream);
+    cudaStreamSynchronize(m->stream);
+    delete m;
+    return VLA_OK;
+}
+
+extern "C" vla_status vla_mesh_info(const vla_mesh *m, vla_mesh_info_t *info) {
+    if (!m || !info) return fail(VLA_ERR_INVALID_ARG, "null argument");
+    info->dim = m->dim;
+    info->order = m->order;
+    info->nlb = m->nlb;
+    info->nn = m->nn;
+    info->ne = m->ne;
+    info->nfb = m->nfb;
+    info->nnz = m->nnz;
+    info->max_row_len = m->max_row_len;
+    info->n_tiles = m->n_tiles;
+    info->device_bytes = m->device_bytes;
+    info->tile_elems = m->tile_elems_total;
+    info->n_codes = m->n_codes;
+    return VLA_OK;
+}
+
+extern "C" vla_status vla_mesh_csr(const vla_mesh *m, int32_t *row_ptr, int32_t *col_idx, void *stream) {
+    if (!m) return fail(VLA_ERR_INVALID_ARG, "null mesh");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (row_ptr)
+        VLA_CUDA(cudaMemcpyAsync(row_ptr, m->row_ptr, sizeof(int32_t) * (m->nn + 1), cudaMemcpyDeviceToDevice, st));
+    if (col_idx && m->nnz > 0)
+        VLA_CUDA(cudaMemcpyAsync(col_idx, m->col_idx, sizeof(int32_t) * m->nnz, cudaMemcpyDeviceToDevice, st));
+    return VLA_OK;
+}
