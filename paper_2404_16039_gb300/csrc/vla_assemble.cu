@@ -444,16 +444,77 @@ struct AsmArgs {
     const void *codes;
     const float4 *xh, *xl;
     const double *coords;
+    int n_tiles;
     int kind;
     double ca, cb;
+    float caf, cbf;
     double *K, *M, *vol, *Kp, *Mp;
     unsigned long long *n_sing;
     int *err;
     int spin_limit;
+    int stage_bytes;       // bytes of one input stage (segments + coordinates), 16-byte multiple
 };
 
 __host__ __device__ constexpr int padq(int x, int q) { return (x + q - 1) / q * q; }
 
+// byte offsets of the staged segments of one tile inside a stage
+struct StageMap {
+    int ids, rec, gid, chk, nz, cod, xyz, end;
+};
+template <typename CT>
+__device__ __forceinline__ StageMap stage_map(const vla::TileHdr &h) {
+    StageMap m;
+    m.ids = 0;
+    m.rec = m.ids + 4 * padq(h.n_nodes, kTilePadNodes);
+    m.gid = m.rec + 8 * padq(h.n_elems, kTilePadElems);
+    m.chk = m.gid + 4 * padq(h.n_own, kTilePadOwn);
+    m.nz = m.chk + 8 * padq(h.n_chunks, kTilePadChunks);
+    m.cod = m.nz + 8 * padq(h.n_nz, kTilePadNz);
+    m.xyz = m.cod + padq((int)sizeof(CT) * h.n_codes, 16);
+    m.end = m.xyz + 32 * h.n_nodes;
+    return m;
+}
+
+// packed f32x2 arithmetic (sm_100+): the K and M sums of a pair advance together
+__device__ __forceinline__ unsigned long long pk(float a, float b) {
+    unsigned long long d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(a), "f"(b));
+    return d;
+}
+__device__ __forceinline__ void upk(unsigned long long d, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(d));
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// (hi, lo) += x, error-free on both lanes (TwoSum)
+__device__ __forceinline__ void ff2_add(unsigned long long &hi, unsigned long long &lo, unsigned long long x) {
+    const unsigned long long s = add2(hi, x);
+    const unsigned long long bb = sub2(s, hi);
+    const unsigned long long e = add2(sub2(hi, sub2(s, bb)), sub2(x, bb));
+    hi = s;
+    lo = add2(lo, e);
+}
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Persistent CTA: tiles blockIdx.x, +gridDim.x, ...  Two input stages: while
+// tile j is computed from stage j&1, the bulk copies of tile j+2 and the
+// coordinate gathers (cp.async) of tile j+1 are in flight.
 template <int DIM, int ORDER, bool MIX>
 __global__ void __launch_bounds__(kThreads) k_assemble(AsmArgs A) {
     using C = Cfg<DIM, ORDER, MIX>;
@@ -461,89 +522,111 @@ __global__ void __launch_bounds__(kThreads) k_assemble(AsmArgs A) {
     using CT = typename C::CT;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
-    const vla::TileHdr h = A.tiles[blockIdx.x];
+    __shared__ int next_chunk[2];   // dynamic chunk counters, one per tile parity
+    if (threadIdx.x == 0) {
+        next_chunk[0] = kThreads / 32;
+        next_chunk[1] = kThreads / 32;
+    }
+    auto stage = [&](int st_) { return smem + (size_t)st_ * A.stage_bytes; };
+    T *s_k = reinterpret_cast<T *>(smem + 2 * (size_t)A.stage_bytes);
+    __shared__ T mhat[ORDER == 2 ? C::NU : 1];
+    if constexpr (ORDER == 2) {
+        for (int u = threadIdx.x; u < C::NU; u += kThreads)
+            mhat[u] = MIX ? (T)c_p2[DIM - 2].mhat_f[u] : (T)c_p2[DIM - 2].mhat_d[u];
+    }
+    const int G = gridDim.x;
+    int issued0 = 0, issued1 = 0;   // thread 0: loads issued per stage
 
-    // shared layout (16-byte aligned segments)
-    const int b_ids = 4 * padq(h.n_nodes, kTilePadNodes);
-    const int b_rec = 8 * padq(h.n_elems, kTilePadElems);
-    const int b_gid = 4 * padq(h.n_own, kTilePadOwn);
-    const int b_chk = 8 * padq(h.n_chunks, kTilePadChunks);
-    const int b_nz = 8 * padq(h.n_nz, kTilePadNz);
-    const int b_cod = (int)sizeof(CT) * h.n_codes;
-    int32_t *s_ids = reinterpret_cast<int32_t *>(smem);
-    ushort4 *s_rec = reinterpret_cast<ushort4 *>(smem + b_ids);
-    int32_t *s_gid = reinterpret_cast<int32_t *>(smem + b_ids + b_rec);
-    int2 *s_chk = reinterpret_cast<int2 *>(smem + b_ids + b_rec + b_gid);
-    int2 *s_nz = reinterpret_cast<int2 *>(smem + b_ids + b_rec + b_gid + b_chk);
-    CT *s_cod = reinterpret_cast<CT *>(smem + b_ids + b_rec + b_gid + b_chk + b_nz);
-    unsigned char *p_xyz = smem + b_ids + b_rec + b_gid + b_chk + b_nz + padq(b_cod, 16);
-    float4 *s_h = reinterpret_cast<float4 *>(p_xyz);
-    float4 *s_l = s_h + h.n_nodes;
-    double4 *s_x = reinterpret_cast<double4 *>(p_xyz);
-    T *s_k = reinterpret_cast<T *>(p_xyz + 32 * h.n_nodes);
-    T *s_mhat = s_k + (size_t)(h.n_elems + 1) * C::RS;
+    auto issue = [&](int t, int s) {   // thread 0 only
+        const vla::TileHdr h = A.tiles[t];
+        const StageMap mp = stage_map<CT>(h);
+        unsigned char *b = stage(s);
+        mbar_expect_tx(&bar[s], (uint32_t)mp.xyz);
+        if (mp.rec > mp.ids) bulk_g2s(b + mp.ids, A.tile_nodes + h.node_off, (uint32_t)(mp.rec - mp.ids), &bar[s]);
+        if (mp.gid > mp.rec) bulk_g2s(b + mp.rec, A.tile_elem + h.elem_off, (uint32_t)(mp.gid - mp.rec), &bar[s]);
+        if (mp.chk > mp.gid) bulk_g2s(b + mp.gid, A.tile_own + h.own_off, (uint32_t)(mp.chk - mp.gid), &bar[s]);
+        if (mp.nz > mp.chk) bulk_g2s(b + mp.chk, A.tile_chunks + h.chunk_off, (uint32_t)(mp.nz - mp.chk), &bar[s]);
+        if (mp.cod > mp.nz) bulk_g2s(b + mp.nz, A.tile_nzpos + h.nz_off, (uint32_t)(mp.cod - mp.nz), &bar[s]);
+        if (mp.xyz > mp.cod)
+            bulk_g2s(b + mp.cod, reinterpret_cast<const CT *>(A.codes) + h.code_off, (uint32_t)(mp.xyz - mp.cod), &bar[s]);
+        if (s) ++issued1;
+        else ++issued0;
+    };
+    // coordinate gathers of tile t into stage s (all threads, asynchronous)
+    auto gather = [&](int t, int s) {
+        const vla::TileHdr h = A.tiles[t];
+        const StageMap mp = stage_map<CT>(h);
+        const int32_t *ids = reinterpret_cast<const int32_t *>(stage(s) + mp.ids);
+        unsigned char *xyz = stage(s) + mp.xyz;
+        for (int i = threadIdx.x; i < h.n_nodes; i += kThreads) {
+            const int32_t g = ids[i];
+            if constexpr (MIX) {
+                cp_async16(xyz + 16 * i, A.xh + g);
+                cp_async16(xyz + 16 * (h.n_nodes + i), A.xl + g);
+            } else {
+                double *dst = reinterpret_cast<double *>(xyz + 32 * i);
+#pragma unroll
+                for (int d = 0; d < DIM; ++d) cp_async8(dst + d, A.coords + (int64_t)g * DIM + d);
+                if (DIM == 2) dst[2] = 0.0;
+            }
+        }
+        cp_async_commit();
+    };
+    auto bail = [&]() {   // a bounded wait expired: record it, let copies in flight land, leave
+        if (threadIdx.x == 0) {
+            atomicOr(A.err, 1);
+            if (issued0) mbar_wait_bounded(&bar[0], (uint32_t)((issued0 - 1) & 1), 1 << 24);
+            if (issued1) mbar_wait_bounded(&bar[1], (uint32_t)((issued1 - 1) & 1), 1 << 24);
+        }
+        cp_async_wait_all();
+    };
 
+    const int t0 = blockIdx.x;
+    if (t0 >= A.n_tiles) return;
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_async_smem();
-        mbar_expect_tx(&bar[0], (uint32_t)(b_ids + b_rec + b_gid));
-        if (b_ids) bulk_g2s(s_ids, A.tile_nodes + h.node_off, (uint32_t)b_ids, &bar[0]);
-        if (b_rec) bulk_g2s(s_rec, A.tile_elem + h.elem_off, (uint32_t)b_rec, &bar[0]);
-        if (b_gid) bulk_g2s(s_gid, A.tile_own + h.own_off, (uint32_t)b_gid, &bar[0]);
-        mbar_expect_tx(&bar[1], (uint32_t)(b_chk + b_nz + b_cod));
-        if (b_chk) bulk_g2s(s_chk, A.tile_chunks + h.chunk_off, (uint32_t)b_chk, &bar[1]);
-        if (b_nz) bulk_g2s(s_nz, A.tile_nzpos + h.nz_off, (uint32_t)b_nz, &bar[1]);
-        if (b_cod) bulk_g2s(s_cod, reinterpret_cast<const CT *>(A.codes) + h.code_off, (uint32_t)b_cod, &bar[1]);
-    }
-    if constexpr (ORDER == 2) {
-        for (int u = threadIdx.x; u < C::NU; u += kThreads)
-            s_mhat[u] = MIX ? (T)c_p2[DIM - 2].mhat_f[u] : (T)c_p2[DIM - 2].mhat_d[u];
+        issue(t0, 0);
+        if (t0 + G < A.n_tiles) issue(t0 + G, 1);
     }
     __syncthreads();
-    // bounded wait; on expiry every thread leaves after the copies in flight land
-    auto bail = [&]() {
-        if (threadIdx.x == 0) {
-            atomicOr(A.err, 1);
-            mbar_wait_bounded(&bar[0], 0, 1 << 24);
-            mbar_wait_bounded(&bar[1], 0, 1 << 24);
-        }
-    };
     if (__syncthreads_or(!mbar_wait_bounded(&bar[0], 0, A.spin_limit))) {
         bail();
         return;
     }
+    gather(t0, 0);
 
-    // phase 0: vertex coordinates of the tile
-    for (int i = threadIdx.x; i < h.n_nodes; i += kThreads) {
-        const int32_t g = s_ids[i];
-        if constexpr (MIX) {
-            s_h[i] = A.xh[g];
-            s_l[i] = A.xl[g];
-        } else {
-            double4 x;
-            x.x = A.coords[(int64_t)g * DIM];
-            x.y = A.coords[(int64_t)g * DIM + 1];
-            x.z = DIM == 3 ? A.coords[(int64_t)g * DIM + 2] : 0.0;
-            x.w = 0.0;
-            s_x[i] = x;
-        }
-    }
-    __syncthreads();
-
-    // phase 1: element records (index n_elems is the zero record used by padding)
-    const T ca = (T)A.ca, cb = (T)A.cb;
+    const T ca = MIX ? (T)A.caf : (T)A.ca, cb = MIX ? (T)A.cbf : (T)A.cb;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr uint32_t UMASK = (1u << C::UB) - 1;
     unsigned long long sing = 0;
-    for (int e = threadIdx.x; e <= h.n_elems; e += kThreads) {
-        // P1 records are built in registers and stored as vectors; P2 records
-        // (up to 56 values) are written straight to shared memory
-        T *dst = s_k + (size_t)e * C::RS;
-        T rec[ORDER == 1 ? C::RS : 1];
-        if constexpr (ORDER == 1) {
-#pragma unroll
-            for (int u = 0; u < C::RS; ++u) rec[u] = T(0);
-        }
-        if (e < h.n_elems) {
+
+    for (int j = 0;; ++j) {
+        const int t = t0 + j * G;
+        if (t >= A.n_tiles) break;
+        const int s = j & 1;
+        const vla::TileHdr h = A.tiles[t];
+        const StageMap mp = stage_map<CT>(h);
+        unsigned char *b = stage(s);
+        const ushort4 *s_rec = reinterpret_cast<const ushort4 *>(b + mp.rec);
+        const int32_t *s_gid = reinterpret_cast<const int32_t *>(b + mp.gid);
+        const int2 *s_chk = reinterpret_cast<const int2 *>(b + mp.chk);
+        const int2 *s_nz = reinterpret_cast<const int2 *>(b + mp.nz);
+        const CT *s_cod = reinterpret_cast<const CT *>(b + mp.cod);
+        const float4 *s_h = reinterpret_cast<const float4 *>(b + mp.xyz);
+        const float4 *s_l = s_h + h.n_nodes;
+        const double4 *s_x = reinterpret_cast<const double4 *>(b + mp.xyz);
+        cp_async_wait_all();   // this thread's coordinate copies of tile t
+        __syncthreads();       // everyone's
+
+        // phase 1: element records (index n_elems is the zero record used by padding)
+        for (int e = threadIdx.x; e <= h.n_elems; e += kThreads) {
+            T *dst = s_k + (size_t)e * C::RS;
+            if (e == h.n_elems) {
+                for (int u = 0; u < C::RS; ++u) dst[u] = T(0);
+                continue;
+            }
             const ushort4 v = s_rec[e];
             Geo<T> g;
             if constexpr (MIX) {
@@ -554,21 +637,35 @@ __global__ void __launch_bounds__(kThreads) k_assemble(AsmArgs A) {
             }
             const T c = coeff<T>(A.kind, ca, cb, g.xc, DIM);
             const T adet = g.det < T(0) ? -g.det : g.det;
-            const T sc = c / (T(C::DFACT) * adet);          // K(a,b) = sc * C_a . C_b
+            T sc;
+            if constexpr (MIX) sc = c * __frcp_rn(T(C::DFACT) * adet);   // K(a,b) = sc * C_a . C_b
+            else sc = c / (T(C::DFACT) * adet);
             T mscale;
             if constexpr (ORDER == 1) {
+                T rec[C::RS];
+#pragma unroll
+                for (int u = 0; u < C::RS; ++u) rec[u] = T(0);
 #pragma unroll
                 for (int a = 0; a < C::NV; ++a)
 #pragma unroll
-                    for (int b = a; b < C::NV; ++b) rec[a * C::NLB - a * (a - 1) / 2 + (b - a)] = sc * dot3<T>(g.C[a], g.C[b]);
+                    for (int q = a; q < C::NV; ++q) rec[a * C::NLB - a * (a - 1) / 2 + (q - a)] = sc * dot3<T>(g.C[a], g.C[q]);
                 mscale = c * adet * T(C::MOFF / C::DFACT);       // off-diagonal mass entry
                 rec[C::NU] = mscale;
+                if constexpr (MIX) {
+#pragma unroll
+                    for (int u = 0; u < C::RS; u += 4)
+                        *reinterpret_cast<float4 *>(dst + u) = make_float4(rec[u], rec[u + 1], rec[u + 2], rec[u + 3]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < C::RS; u += 2)
+                        *reinterpret_cast<double2 *>(dst + u) = make_double2(rec[u], rec[u + 1]);
+                }
             } else {
                 T cd[10];
 #pragma unroll
-                for (int s = 0; s < C::NV; ++s)
+                for (int a = 0; a < C::NV; ++a)
 #pragma unroll
-                    for (int q = s; q < C::NV; ++q) cd[s * C::NV - s * (s - 1) / 2 + (q - s)] = dot3<T>(g.C[s], g.C[q]);
+                    for (int q = a; q < C::NV; ++q) cd[a * C::NV - a * (a - 1) / 2 + (q - a)] = dot3<T>(g.C[a], g.C[q]);
                 const P2Tab &tb = c_p2[DIM - 2];
                 for (int u = 0; u < C::NU; ++u) {
                     T acc = 0;
@@ -591,18 +688,14 @@ __global__ void __launch_bounds__(kThreads) k_assemble(AsmArgs A) {
                 }
                 if (A.Kp || A.Mp) {
                     for (int a = 0; a < C::NLB; ++a)
-                        for (int b = 0; b < C::NLB; ++b) {
-                            const int p = a < b ? a : b, q = a < b ? b : a;
-                            const int u = p * C::NLB - p * (p - 1) / 2 + (q - p);
-                            const int64_t pos = k * C::NLB * C::NLB + a + (int64_t)b * C::NLB;
-                            T kv, mv;
-                            if constexpr (ORDER == 1) {
-                                kv = rec[u];
-                                mv = mscale * (a == b ? T(2) : T(1));
-                            } else {
-                                kv = dst[u];
-                                mv = mscale * (MIX ? (T)c_p2[DIM - 2].mhat_f[u] : (T)c_p2[DIM - 2].mhat_d[u]);
-                            }
+                        for (int q = 0; q < C::NLB; ++q) {
+                            const int p0 = a < q ? a : q, p1 = a < q ? q : a;
+                            const int u = p0 * C::NLB - p0 * (p0 - 1) / 2 + (p1 - p0);
+                            const int64_t pos = k * C::NLB * C::NLB + a + (int64_t)q * C::NLB;
+                            const T kv = dst[u];
+                            T mv;
+                            if constexpr (ORDER == 1) mv = mscale * (a == q ? T(2) : T(1));
+                            else mv = mscale * mhat[u];
                             if constexpr (MIX) {
                                 if (A.Kp) A.Kp[pos] = f32_to_f64(kv);
                                 if (A.Mp) A.Mp[pos] = f32_to_f64(mv);
@@ -613,133 +706,135 @@ __global__ void __launch_bounds__(kThreads) k_assemble(AsmArgs A) {
                         }
                 }
             }
-        } else if constexpr (ORDER == 2) {
-            for (int u = 0; u < C::RS; ++u) dst[u] = T(0);
         }
-        if constexpr (ORDER == 1) {
-            if constexpr (MIX) {
-#pragma unroll
-                for (int u = 0; u < C::RS; u += 4)
-                    *reinterpret_cast<float4 *>(dst + u) = make_float4(rec[u], rec[u + 1], rec[u + 2], rec[u + 3]);
-            } else {
-#pragma unroll
-                for (int u = 0; u < C::RS; u += 2)
-                    *reinterpret_cast<double2 *>(dst + u) = make_double2(rec[u], rec[u + 1]);
+        // prefetch: coordinates of the next tile (its bulk copies were issued two tiles ago)
+        const int tn = t + G;
+        if (tn < A.n_tiles) {
+            if (__syncthreads_or(!mbar_wait_bounded(&bar[s ^ 1], (uint32_t)(((j + 1) >> 1) & 1), A.spin_limit))) {
+                bail();
+                return;
+            }
+            gather(tn, s ^ 1);
+        } else {
+            __syncthreads();
+        }
+
+        // phase 2: pairs sorted by contribution count, 32 per warp-chunk,
+        // contributions in ascending element order
+        if (A.K || A.M) {
+            // chunks are handed out dynamically: they are sorted by width, so a
+            // static round-robin would give the first warps all the long ones
+            for (int c = warp;;) {
+                if (c >= h.n_chunks) break;
+                const int q = c * 32 + lane;
+                const int2 ch = s_chk[c];
+                const CT *cp = s_cod + ch.x + lane;
+                if constexpr (MIX) {
+                    unsigned long long h0 = 0ull, l0 = 0ull, h1 = 0ull, l1 = 0ull;   // (K, M) pairs, 2 chains
+                    int tt = 0;
+                    for (; tt + 1 < ch.y; tt += 2) {
+                        const uint32_t c0 = cp[tt * 32], c1 = cp[(tt + 1) * 32];
+                        const float *r0 = s_k + (c0 >> C::UB) * C::RS, *r1 = s_k + (c1 >> C::UB) * C::RS;
+                        float m0 = r0[C::NU], m1 = r1[C::NU];
+                        if constexpr (ORDER == 2) {
+                            m0 *= mhat[c0 & UMASK];
+                            m1 *= mhat[c1 & UMASK];
+                        }
+                        ff2_add(h0, l0, pk(r0[c0 & UMASK], m0));
+                        ff2_add(h1, l1, pk(r1[c1 & UMASK], m1));
+                    }
+                    if (tt < ch.y) {
+                        const uint32_t c0 = cp[tt * 32];
+                        const float *r0 = s_k + (c0 >> C::UB) * C::RS;
+                        float m0 = r0[C::NU];
+                        if constexpr (ORDER == 2) m0 *= mhat[c0 & UMASK];
+                        ff2_add(h0, l0, pk(r0[c0 & UMASK], m0));
+                    }
+                    if (q < h.n_nz) {
+                        ff2_add(h0, l0, h1);
+                        ff2_add(h0, l0, l1);
+                        // renormalise both sums at once: (hi, lo) <- TwoSum(hi, lo)
+                        const unsigned long long s2 = add2(h0, l0);
+                        const unsigned long long bb = sub2(s2, h0);
+                        const unsigned long long e2 = add2(sub2(h0, sub2(s2, bb)), sub2(l0, bb));
+                        float khi, mhi, klo, mlo;
+                        upk(s2, khi, mhi);
+                        upk(e2, klo, mlo);
+                        const int2 pos = s_nz[q];
+                        if (ORDER == 1 && pos.x == pos.y) {   // P1 diagonal mass: twice the off-diagonal scale
+                            mhi *= 2.f;
+                            mlo *= 2.f;
+                        }
+                        const double kd = ff_to_f64(khi, klo), md = ff_to_f64(mhi, mlo);
+                        if (A.K) {
+                            A.K[pos.x] = kd;
+                            if (pos.y != pos.x) A.K[pos.y] = kd;
+                        }
+                        if (A.M) {
+                            A.M[pos.x] = md;
+                            if (pos.y != pos.x) A.M[pos.y] = md;
+                        }
+                    }
+                } else {
+                    double ks = 0.0, ms = 0.0;
+                    for (int tt = 0; tt < ch.y; ++tt) {
+                        const uint32_t c0 = cp[tt * 32];
+                        const double *r0 = s_k + (c0 >> C::UB) * C::RS;
+                        ks += r0[c0 & UMASK];
+                        if constexpr (ORDER == 2) ms += r0[C::NU] * mhat[c0 & UMASK];
+                        else ms += r0[C::NU];
+                    }
+                    if (q < h.n_nz) {
+                        const int2 pos = s_nz[q];
+                        if (ORDER == 1 && pos.x == pos.y) ms *= 2.0;
+                        if (A.K) {
+                            A.K[pos.x] = ks;
+                            if (pos.y != pos.x) A.K[pos.y] = ks;
+                        }
+                        if (A.M) {
+                            A.M[pos.x] = ms;
+                            if (pos.y != pos.x) A.M[pos.y] = ms;
+                        }
+                    }
+                }
+                int nc = 0;
+                if (lane == 0) nc = atomicAdd(&next_chunk[j & 1], 1);
+                c = __shfl_sync(0xffffffffu, nc, 0);
             }
         }
+        if (threadIdx.x == 0) next_chunk[(j + 1) & 1] = kThreads / 32;   // reset for the next tile
+        __syncthreads();   // stage s and the element records are free
+        if (threadIdx.x == 0 && t + 2 * G < A.n_tiles) issue(t + 2 * G, s);
     }
     if (A.n_sing && sing) atomicAdd(A.n_sing, sing);
-    __syncthreads();
-    if (__syncthreads_or(!mbar_wait_bounded(&bar[1], 0, A.spin_limit))) {
-        bail();
-        return;
-    }
-    if (!A.K && !A.M) return;
-
-    // phase 2: pairs {i, j} (and diagonals), 32 per warp-chunk, contributions in
-    // ascending element order, two interleaved compensated accumulators
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int n_up_chunks = (h.n_up + 31) >> 5;
-    constexpr uint32_t UMASK = (1u << C::UB) - 1;
-    for (int c = warp; c < h.n_chunks; c += kThreads / 32) {
-        const bool diag = c >= n_up_chunks;
-        int q = diag ? h.n_up + (c - n_up_chunks) * 32 + lane : c * 32 + lane;
-        if (q >= (diag ? h.n_nz : h.n_up)) q = -1;
-        const int2 ch = s_chk[c];
-        const CT *cp = s_cod + ch.x + lane;
-        if constexpr (MIX) {
-            ffacc k0, k1, m0, m1;
-            k0.zero();
-            k1.zero();
-            m0.zero();
-            m1.zero();
-            int tt = 0;
-            for (; tt + 1 < ch.y; tt += 2) {
-                const uint32_t c0 = cp[tt * 32], c1 = cp[(tt + 1) * 32];
-                const float *r0 = s_k + (c0 >> C::UB) * C::RS, *r1 = s_k + (c1 >> C::UB) * C::RS;
-                const float kv0 = r0[c0 & UMASK], kv1 = r1[c1 & UMASK];
-                float mv0 = r0[C::NU], mv1 = r1[C::NU];
-                if constexpr (ORDER == 2) {
-                    mv0 *= s_mhat[c0 & UMASK];
-                    mv1 *= s_mhat[c1 & UMASK];
-                }
-                k0.add(kv0);
-                k1.add(kv1);
-                m0.add(mv0);
-                m1.add(mv1);
-            }
-            if (tt < ch.y) {
-                const uint32_t c0 = cp[tt * 32];
-                const float *r0 = s_k + (c0 >> C::UB) * C::RS;
-                float mv0 = r0[C::NU];
-                if constexpr (ORDER == 2) mv0 *= s_mhat[c0 & UMASK];
-                k0.add(r0[c0 & UMASK]);
-                m0.add(mv0);
-            }
-            if (q >= 0) {
-                k0.add(k1.hi);
-                k0.add(k1.lo);
-                m0.add(m1.hi);
-                m0.add(m1.lo);
-                k0.norm();
-                m0.norm();
-                if (ORDER == 1 && diag) {   // P1 diagonal mass entries are twice the off-diagonal scale
-                    m0.hi *= 2.f;
-                    m0.lo *= 2.f;
-                }
-                const int2 pos = s_nz[q];
-                const double kd = ff_to_f64(k0.hi, k0.lo), md = ff_to_f64(m0.hi, m0.lo);
-                if (A.K) {
-                    A.K[pos.x] = kd;
-                    if (pos.y != pos.x) A.K[pos.y] = kd;
-                }
-                if (A.M) {
-                    A.M[pos.x] = md;
-                    if (pos.y != pos.x) A.M[pos.y] = md;
-                }
-            }
-        } else {
-            double ks = 0.0, ms = 0.0;
-            for (int tt = 0; tt < ch.y; ++tt) {
-                const uint32_t c0 = cp[tt * 32];
-                const double *r0 = s_k + (c0 >> C::UB) * C::RS;
-                ks += r0[c0 & UMASK];
-                if constexpr (ORDER == 2) ms += r0[C::NU] * s_mhat[c0 & UMASK];
-                else ms += r0[C::NU];
-            }
-            if (q >= 0) {
-                if (ORDER == 1 && diag) ms *= 2.0;
-                const int2 pos = s_nz[q];
-                if (A.K) {
-                    A.K[pos.x] = ks;
-                    if (pos.y != pos.x) A.K[pos.y] = ks;
-                }
-                if (A.M) {
-                    A.M[pos.x] = ms;
-                    if (pos.y != pos.x) A.M[pos.y] = ms;
-                }
-            }
-        }
-    }
 }
 
 template <int DIM, int ORDER, bool MIX>
-size_t asm_smem(const vla_mesh *m) {
+size_t asm_smem(const vla_mesh *m, int &stage_bytes) {
     using C = Cfg<DIM, ORDER, MIX>;
-    return m->tile_stage_bytes + 64 + (size_t)m->max_tile_nodes * 32 +
-           ((size_t)m->max_tile_elems + 1) * C::RS * sizeof(typename C::T) + (size_t)C::NU * sizeof(typename C::T);
+    stage_bytes = (int)((m->tile_stage_bytes + 32 * (size_t)m->max_tile_nodes + 16 + 15) / 16 * 16);
+    return 2 * (size_t)stage_bytes + ((size_t)m->max_tile_elems + 1) * C::RS * sizeof(typename C::T);
 }
 
 template <int DIM, int ORDER, bool MIX>
-vla_status launch_assemble(const vla_mesh *m, const AsmArgs &a, cudaStream_t st) {
-    const size_t smem = asm_smem<DIM, ORDER, MIX>(m);
-    int dev = 0, maxsm = 0;
+vla_status launch_assemble(const vla_mesh *m, AsmArgs a, cudaStream_t st) {
+    int stage_bytes = 0;
+    const size_t smem = asm_smem<DIM, ORDER, MIX>(m, stage_bytes);
+    a.stage_bytes = stage_bytes;
+    int dev = 0, maxsm = 0, nsm = 0;
     VLA_CUDA(cudaGetDevice(&dev));
     VLA_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (smem > (size_t)maxsm - 64)
+    VLA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    if (smem + 1024 > (size_t)maxsm)
         return fail(VLA_ERR_UNSUPPORTED, "assembly tile needs %zu bytes of shared memory (limit %d)", smem, maxsm);
-    VLA_CUDA(cudaFuncSetAttribute(k_assemble<DIM, ORDER, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_assemble<DIM, ORDER, MIX><<<m->n_tiles, kThreads, smem, st>>>(a);
+    auto kern = k_assemble<DIM, ORDER, MIX>;
+    VLA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    VLA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int grid = nsm * per_sm;
+    if (grid > m->n_tiles) grid = m->n_tiles;
+    kern<<<grid, kThreads, smem, st>>>(a);
     VLA_CUDA(cudaGetLastError());
     return VLA_OK;
 }
@@ -890,6 +985,10 @@ extern "C" vla_status vla_assemble(const vla_mesh *m, int32_t kind, double ca, d
     a.n_sing = ns;
     a.err = m->d_err;
     a.spin_limit = m->spin_limit;
+    a.n_tiles = m->n_tiles;
+    a.caf = (float)ca;
+    a.cbf = (float)cb;
+    a.stage_bytes = 0;
     const bool mix = precision == VLA_PREC_MIXED;
     const int key = (m->dim == 3 ? 4 : 0) + (m->order == 2 ? 2 : 0) + (mix ? 1 : 0);
     switch (key) {

@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/vla.h"
+#include "vla.h"
 
 namespace vla {
 
@@ -102,38 +102,36 @@ __device__ __forceinline__ unsigned long long f32_to_f64_bits(float x) {
 
 __device__ __forceinline__ double f32_to_f64(float x) { return __longlong_as_double((long long)f32_to_f64_bits(x)); }
 
-// hi + lo as a double, for a normalised pair (|lo| <= ulp_f32(hi)/2), with an
-// error below one double ulp (lo bits below the double's precision are
-// truncated).  Integer-only except in the rare case where lo would move the
-// result below hi's binade.
+// hi + lo as a double, for a normalised float pair (|lo| <= ulp_f32(hi)/2),
+// with integer instructions only and no data-dependent branches.  The 24-bit
+// significand of hi is widened to 53 bits and lo is added in units of the
+// result's last place (its bits below that are truncated, an error under one
+// double ulp); one left shift renormalises the rare case where lo pulls the
+// value below hi's binade.  Zero, subnormal-float lo and inf/nan hi are exact.
 __device__ __forceinline__ double ff_to_f64(float hi, float lo) {
-    unsigned long long hb = f32_to_f64_bits(hi);
-    uint32_t lu = __float_as_uint(lo);
-    if ((lu & 0x7fffffffu) == 0u || ((hb >> 52) & 0x7ffull) == 0x7ffull) return __longlong_as_double((long long)hb);
-    if (hi == 0.0f) return f32_to_f64(lo);
-    uint32_t le = (lu >> 23) & 0xffu;
-    uint32_t lm = lu & 0x7fffffu;
-    int elo;                                            // |lo| = lm' * 2^(elo - 23)
-    if (le == 0) {
-        elo = -126;
-    } else {
-        elo = (int)le - 127;
-        lm |= 0x800000u;
-    }
-    int ehi = (int)((hb >> 52) & 0x7ffull) - 1023;      // hi's exponent as a double
-    int shift = elo - ehi + 29;                         // lo in units of 2^(ehi-52)
-    unsigned long long delta;
-    if (shift >= 0) {
-        if (shift > 5) return __longlong_as_double((long long)hb) + f32_to_f64(lo);  // not normalised
-        delta = (unsigned long long)lm << shift;
-    } else {
-        delta = (shift <= -32) ? 0ull : ((unsigned long long)lm >> (-shift));
-    }
-    bool same = ((lu >> 31) == (uint32_t)(hb >> 63));
-    unsigned long long mant = hb & 0xfffffffffffffull;
-    if (same) return __longlong_as_double((long long)(hb + delta));   // low 29 bits of hb are zero: no carry
-    if (mant < delta) return __longlong_as_double((long long)hb) + f32_to_f64(lo);  // crosses the binade
-    return __longlong_as_double((long long)(hb - delta));
+    const uint32_t hu = __float_as_uint(hi), lu = __float_as_uint(lo);
+    const uint32_t he = (hu >> 23) & 0xffu, le = (lu >> 23) & 0xffu;
+    if (((hu | lu) << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)(hu >> 31) << 63));
+    // the rare cases go through the exact (FP64) path: hi zero/subnormal/inf/nan
+    if (he == 0u || he == 0xffu) return f32_to_f64(hi) + f32_to_f64(lo);
+    // significand of hi with 29 extra bits: M in [2^52, 2^53)
+    const long long Mh = (long long)((0x800000u | (hu & 0x7fffffu))) << 29;
+    // lo's significand and its shift into units of 2^(E_hi - 52)
+    const uint32_t lm = (le == 0u) ? (lu & 0x7fffffu) : (0x800000u | (lu & 0x7fffffu));
+    const int sh = (int)(le == 0u ? 1u : le) - (int)he + 29;      // <= 5 for a normalised pair
+    const long long d = sh >= 0 ? ((long long)lm << (sh > 40 ? 40 : sh)) : (sh <= -32 ? 0ll : (long long)(lm >> -sh));
+    const bool same = (lu >> 31) == (hu >> 31);
+    long long M = same ? Mh + d : Mh - d;
+    int E = (int)he + 896;                                          // biased double exponent of hi
+    const int low = M < (1ll << 52) ? 1 : 0;                        // at most one bit lost
+    M <<= low;
+    E -= low;
+    const int up = M >= (1ll << 53) ? 1 : 0;                        // impossible for normalised pairs
+    M >>= up;
+    E += up;
+    const unsigned long long bits = ((unsigned long long)(hu >> 31) << 63) | ((unsigned long long)E << 52) |
+                                    ((unsigned long long)M & 0xfffffffffffffull);
+    return __longlong_as_double((long long)bits);
 }
 
 // ---------------------------------------------------------------------------

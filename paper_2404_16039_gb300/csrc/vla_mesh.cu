@@ -611,26 +611,50 @@ __global__ void k_tile_fill(int n_tiles, int dim, int nlb, int cap_e, int cap_n,
     }
 }
 
-// chunk widths (largest contribution count of 32 consecutive pairs) and the
-// tile-relative code offset of every chunk
+// Orders every tile's pairs by contribution count (descending, stable), so
+// that the 32 pairs of a chunk need nearly the same number of iterations, then
+// writes the chunk table (tile-relative code offset, width) and the permuted
+// pair positions.  order[nz_off + q] = new index of row-major pair q.
 __global__ void k_chunk_table(int n_tiles, const TileHdr *__restrict__ hdr, const int32_t *__restrict__ nz_count,
-                              int2 *__restrict__ chunks, int32_t *__restrict__ tile_codes_n) {
+                              const int2 *__restrict__ nzpos_rowmajor, int2 *__restrict__ nzpos,
+                              int32_t *__restrict__ order, int2 *__restrict__ chunks,
+                              int32_t *__restrict__ tile_codes_n) {
     const int t = blockIdx.x;
     if (t >= n_tiles) return;
     const TileHdr h = hdr[t];
-    const int n_up_chunks = (h.n_up + 31) / 32;
+    constexpr int kMaxCount = 512;
+    __shared__ int32_t hist[kMaxCount + 1];
     __shared__ int32_t w[1024];
-    for (int c = threadIdx.x; c < h.n_chunks; c += blockDim.x) {
-        int q0, q1;
-        if (c < n_up_chunks) {
-            q0 = c * 32;
-            q1 = min(q0 + 32, h.n_up);
-        } else {
-            q0 = h.n_up + (c - n_up_chunks) * 32;
-            q1 = min(q0 + 32, h.n_nz);
+    for (int i = threadIdx.x; i <= kMaxCount; i += blockDim.x) hist[i] = 0;
+    __syncthreads();
+    for (int q = threadIdx.x; q < h.n_nz; q += blockDim.x) atomicAdd(&hist[min(nz_count[h.nz_off + q], kMaxCount)], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {   // descending counts: start offset of each count value
+        int32_t run = 0;
+        for (int c = kMaxCount; c >= 0; --c) {
+            const int32_t n = hist[c];
+            hist[c] = run;
+            run += n;
         }
+    }
+    __syncthreads();
+    // stable placement: one thread walks the pairs in row-major order
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < h.n_nz; ++q) {
+            const int c = min(nz_count[h.nz_off + q], kMaxCount);
+            const int32_t nq = hist[c]++;
+            order[h.nz_off + q] = nq;
+            nzpos[h.nz_off + nq] = nzpos_rowmajor[h.nz_off + q];
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < h.n_chunks; c += blockDim.x) {
+        const int q0 = c * 32, q1 = min(q0 + 32, h.n_nz);
         int wd = 0;
-        for (int q = q0; q < q1; ++q) wd = max(wd, nz_count[h.nz_off + q]);
+        for (int q = 0; q < h.n_nz; ++q) {
+            const int nq = order[h.nz_off + q];
+            if (nq >= q0 && nq < q1) wd = max(wd, nz_count[h.nz_off + q]);
+        }
         if (c < 1024) w[c] = wd;
     }
     __syncthreads();
@@ -652,12 +676,12 @@ __global__ void k_tile_codes(int n_tiles, int nv, int nlb, int cap_e, const Tile
                              const int32_t *__restrict__ n2e, const int32_t *__restrict__ elems,
                              const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
                              const int32_t *__restrict__ sc_elems, const int2 *__restrict__ row_info,
-                             const int2 *__restrict__ chunks, int32_t *__restrict__ fill, CT *__restrict__ codes) {
+                             const int32_t *__restrict__ order, const int2 *__restrict__ chunks,
+                             int32_t *__restrict__ fill, CT *__restrict__ codes) {
     const int t = blockIdx.x;
     if (t >= n_tiles) return;
     const TileHdr h = hdr[t];
     const int32_t *te = sc_elems + (int64_t)t * cap_e;
-    const int n_up_chunks = (h.n_up + 31) / 32;
     const CT dummy = (CT)((uint32_t)h.n_elems << UBITS);
     for (int i = threadIdx.x; i < h.n_codes; i += blockDim.x) codes[(int64_t)h.code_off + i] = dummy;
     __syncthreads();
@@ -675,14 +699,8 @@ __global__ void k_tile_codes(int n_tiles, int nv, int nlb, int cap_e, const Tile
                 const int32_t c = elems[k * nlb + bb];
                 if (c < i) continue;
                 const int32_t qq = (c == i) ? ri.y : ri.x + lower_bound_i32(col_idx + b, len, c) - ds - 1;
-                int chunk, lane;
-                if (qq < h.n_up) {
-                    chunk = qq >> 5;
-                    lane = qq & 31;
-                } else {
-                    chunk = n_up_chunks + ((qq - h.n_up) >> 5);
-                    lane = (qq - h.n_up) & 31;
-                }
+                const int nq = order[h.nz_off + qq];
+                const int chunk = nq >> 5, lane = nq & 31;
                 const int tt = fill[h.nz_off + qq]++;
                 const int2 ch = chunks[h.chunk_off + chunk];
                 const int p = a < bb ? a : bb, r = a < bb ? bb : a;
@@ -739,7 +757,7 @@ struct Scratch {  // temporary device buffers freed at the end of the build
 
 // incidence budget of a tile (sum over its rows of 1 + incident elements)
 int tile_budget(int dim, int order) {
-    if (order == 1) return dim == 3 ? 1600 : 2048;
+    if (order == 1) return dim == 3 ? 800 : 2048;
     return dim == 3 ? 384 : 1024;
 }
 
@@ -943,7 +961,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         h.n_nz = c.n_up + c.n_diag;
         h.n_up = c.n_up;
         h.chunk_off = (int32_t)o_chunk;
-        h.n_chunks = (c.n_up + 31) / 32 + (c.n_diag + 31) / 32;
+        h.n_chunks = (c.n_up + c.n_diag + 31) / 32;
         h.rank_begin = c.rank_begin;
         h.n_rows = c.n_rows;
         o_node += pad(c.n_nodes, kTilePadNodes);
@@ -978,16 +996,19 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     VLA_CUDA(cudaMemsetAsync(m->tile_own, 0, sizeof(int32_t) * (o_own + 4), st));
     VLA_CUDA(cudaMemsetAsync(m->tile_nzpos, 0, sizeof(int2) * (o_nz + 2), st));
     VLA_CUDA(cudaMemsetAsync(m->tile_chunks, 0, sizeof(int2) * (o_chunk + 2), st));
-    int32_t *nz_count, *tile_ncodes;
-    int2 *row_info;
+    int32_t *nz_count, *tile_ncodes, *nz_order;
+    int2 *row_info, *nzpos_rm;
     TRY(S.get(&nz_count, o_nz + 2));
+    TRY(S.get(&nz_order, o_nz + 2));
+    TRY(S.get(&nzpos_rm, o_nz + 2));
     TRY(S.get(&row_info, nn));
     TRY(S.get(&tile_ncodes, n_tiles));
     k_tile_fill<<<(int)n_tiles, 256, 0, st>>>((int)n_tiles, dim, nlb, cap_e, cap_n, m->tiles, perm, m->n2e_ptr,
                                               m->n2e, m->elems, m->row_ptr, m->col_idx, sc_elems, sc_nodes,
-                                              m->tile_nodes, m->tile_elem, m->tile_own, m->tile_nzpos, nz_count,
+                                              m->tile_nodes, m->tile_elem, m->tile_own, nzpos_rm, nz_count,
                                               row_info);
-    k_chunk_table<<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, m->tiles, nz_count, m->tile_chunks, tile_ncodes);
+    k_chunk_table<<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, m->tiles, nz_count, nzpos_rm, m->tile_nzpos, nz_order,
+                                                m->tile_chunks, tile_ncodes);
     VLA_CUDA(cudaGetLastError());
     std::vector<int32_t> hnc(n_tiles);
     VLA_CUDA(cudaMemcpyAsync(hnc.data(), tile_ncodes, sizeof(int32_t) * n_tiles, cudaMemcpyDeviceToHost, st));
@@ -1017,16 +1038,16 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         TRY(dalloc(m, &codes, o_code + 64, st));
         k_tile_codes<uint16_t, 4><<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, m->tiles, perm,
                                                                  m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
-                                                                 m->col_idx, sc_elems, row_info, m->tile_chunks,
-                                                                 fill, codes);
+                                                                 m->col_idx, sc_elems, row_info, nz_order,
+                                                                 m->tile_chunks, fill, codes);
         m->tile_codes = codes;
     } else {
         uint32_t *codes;
         TRY(dalloc(m, &codes, o_code + 64, st));
         k_tile_codes<uint32_t, 8><<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, m->tiles, perm,
                                                                  m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
-                                                                 m->col_idx, sc_elems, row_info, m->tile_chunks,
-                                                                 fill, codes);
+                                                                 m->col_idx, sc_elems, row_info, nz_order,
+                                                                 m->tile_chunks, fill, codes);
         m->tile_codes = codes;
     }
     VLA_CUDA(cudaGetLastError());
