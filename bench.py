@@ -202,6 +202,58 @@ def _config(m, precision):
             "l2": "flushed before every timed step (512 MiB write)"}
 
 
+def run_pages(args):
+    """Page-primitive sweep (amtam, astam, avtam, amdet, aminv): N pages of n x n,
+    FP32/FP64, page-major layout, inputs generated on the device; GB/s of each
+    call (bytes the operation must move / CUDA-event time, L2 flushed)."""
+    import torch
+    import paper_2404_16039_gb300 as vla
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peaks, src = _peaks()
+    rows = []
+    for N in [int(x) for x in args.pages_n.split(",")]:
+        for dt, sz in ((torch.float32, 4), (torch.float64, 8)):
+            for n in (2, 3):
+                g = torch.Generator(device="cuda").manual_seed(0)
+                A = torch.randn((N, n, n), generator=g, dtype=dt, device=dev)
+                A[:, list(range(n)), list(range(n))] += 3.0
+                B = torch.randn((N, n, n), generator=g, dtype=dt, device=dev)
+                s_ = torch.empty(N, dtype=dt, device=dev).uniform_(0.5, 2.0, generator=g)
+                v = torch.randn((N, n), generator=g, dtype=dt, device=dev)
+                out = torch.empty_like(A)
+                det = torch.empty(N, dtype=dt, device=dev)
+                y = torch.empty((N, n), dtype=dt, device=dev)
+                ops = {
+                    "amtam": (lambda: vla.amtam(A, B, out=out), 3 * n * n * sz),
+                    "astam": (lambda: vla.astam(s_, A, out=out), (2 * n * n + 1) * sz),
+                    "avtam": (lambda: vla.avtam(v, A, out=y), (n * n + 2 * n) * sz),
+                    "amdet": (lambda: vla.amdet(A, out=det), (n * n + 1) * sz),
+                    "aminv": (lambda: vla.aminv(A, out=out, det=det, count_singular=False), (2 * n * n + 1) * sz),
+                }
+                for name, (fn, bpp) in ops.items():
+                    for _ in range(3):
+                        fn()
+                    ts = []
+                    for _ in range(args.steps):
+                        flush.zero_()
+                        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        a.record()
+                        fn()
+                        b.record()
+                        torch.cuda.synchronize()
+                        ts.append(a.elapsed_time(b))
+                    ms = float(np.median(ts))
+                    gbs = N * bpp / (ms * 1e-3) / 1e9
+                    rows.append({"op": name, "n": n, "dtype": "f32" if sz == 4 else "f64", "N": N, "ms": ms,
+                                 "GBps": gbs, "frac_hbm": gbs / peaks["hbm_gbs"]})
+                del A, B, out, det, y, s_, v
+                torch.cuda.empty_cache()
+    print(json.dumps({"workload": "page primitives, page-major layout", "peak_hbm_gbs": peaks["hbm_gbs"],
+                      "peak_source": src, "results": rows}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -213,9 +265,13 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="p1tet", choices=["p1tet", "pages"])
+    ap.add_argument("--pages-n", default="100000000")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "pages":
+        return run_pages(args)
 
     import torch
     import meshgen
