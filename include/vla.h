@@ -193,6 +193,28 @@ vla_status vla_boundary(const vla_mesh *mesh, int32_t precision, double *normals
  * FP64 column-major pages (device). FP64 arithmetic. */
 vla_status vla_simplex_normals(const vla_mesh *mesh, double *normals, void *stream);
 
+/* Element pages and volumes without a mesh handle and without allocating.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory where they need element matrices (a heap
+ * owned by another framework, allocator-free real-time loops, code that must
+ * not create a persistent handle).  It computes exactly what vla_assemble
+ * writes to K_pages, M_pages and vol (same geometry and precision paths), but
+ * from the raw arrays: coords dim x nn FP64 and elems nlb x ne int32 (device,
+ * layouts as for vla_mesh_create; indices are not validated here).
+ * Scratch: the float-pair split of the coordinates used by VLA_PREC_MIXED is
+ * kept in a fixed device array built into the library (8 MiB per GPU that
+ * loads it, held until the process exits); nn above 262,144 is rejected with
+ * VLA_ERR_BUDGET.  No cudaMalloc/cudaFree or allocating library call is made.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array: calls that overlap on the GPU (different
+ * streams, or different host threads) race and must be serialised by the
+ * caller.  Outputs (device, any may be NULL): K_pages, M_pages nlb x nlb x ne
+ * column-major, vol ne, n_singular (device int64, overwritten). */
+vla_status vla_element_pages_static(int32_t dim, int32_t order, int64_t nn, int64_t ne, const double *coords,
+                                    const int32_t *elems, int32_t coeff_kind, double ca, double cb, int32_t precision,
+                                    double *K_pages, double *M_pages, double *vol, int64_t *n_singular, void *stream);
+
 /* Releases the handle and its device memory (stream-ordered on the stream
  * the mesh was created with, which is synchronised first).  NULL is a no-op. */
 vla_status vla_mesh_destroy(vla_mesh *mesh);

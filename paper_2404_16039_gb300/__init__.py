@@ -20,7 +20,7 @@ import threading
 import torch
 
 __all__ = [
-    "VlaError", "lib", "version", "amtam", "astam", "avtam", "amdet", "aminv", "Mesh",
+    "VlaError", "lib", "version", "amtam", "astam", "avtam", "amdet", "aminv", "Mesh", "element_pages_static",
     "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP",
 ]
 
@@ -74,9 +74,10 @@ def lib():
         L.vla_boundary.argtypes = [vp, i32, vp, vp, vp]
         L.vla_simplex_normals.argtypes = [vp, vp, vp]
         L.vla_mesh_destroy.argtypes = [vp]
+        L.vla_element_pages_static.argtypes = [i32, i32, i64, i64, vp, vp, i32, dbl, dbl, i32, vp, vp, vp, vp, vp]
         for name in ("vla_amtam", "vla_astam", "vla_avtam", "vla_amdet", "vla_aminv", "vla_mesh_create",
                      "vla_mesh_info", "vla_mesh_csr", "vla_assemble", "vla_boundary", "vla_simplex_normals",
-                     "vla_mesh_destroy"):
+                     "vla_mesh_destroy", "vla_element_pages_static"):
             getattr(L, name).restype = i32
         _lib = L
         return L
@@ -289,3 +290,26 @@ class Mesh:
         out = torch.empty((self.ne, self.dim + 1, self.dim), dtype=torch.float64, device=self.device)
         _check(lib().vla_simplex_normals(self._h, _p(out), _stream(stream)))
         return out
+
+
+def element_pages_static(coords, elems, order=1, ca=1.0, cb=0.0, kind=COEFF_POLY, precision=PREC_MIXED,
+                         count_singular=False, stream=None):
+    """Element pages (ne, nlb, nlb), volumes (ne,) and optionally the singular
+    count from raw mesh arrays, without a mesh handle and without any device
+    allocation inside the library (vla_element_pages_static; at most 262,144
+    nodes).  The output tensors are allocated here by PyTorch; callers that
+    cannot allocate pass the C entry point their own buffers."""
+    _req(coords, torch.float64), _req(elems, torch.int32)
+    nn, dim = coords.shape
+    ne, nlb = elems.shape
+    dev = coords.device
+    Kp = torch.empty((ne, nlb, nlb), dtype=torch.float64, device=dev)
+    Mp = torch.empty((ne, nlb, nlb), dtype=torch.float64, device=dev)
+    vol = torch.empty(ne, dtype=torch.float64, device=dev)
+    ns = torch.zeros(1, dtype=torch.int64, device=dev) if count_singular else None
+    _check(lib().vla_element_pages_static(dim, order, nn, ne, _p(coords), _p(elems), kind, float(ca), float(cb),
+                                          precision, _p(Kp), _p(Mp), _p(vol), _p(ns), _stream(stream)))
+    out = {"K3D": Kp, "M3D": Mp, "vol": vol}
+    if count_singular:
+        out["n_singular"] = ns
+    return out

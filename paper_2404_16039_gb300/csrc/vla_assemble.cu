@@ -1029,3 +1029,199 @@ extern "C" vla_status vla_simplex_normals(const vla_mesh *m, double *normals, vo
     VLA_CUDA(cudaGetLastError());
     return VLA_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free element pages.
+//
+// Some callers cannot allocate device memory at the point where they need
+// element matrices: code running while another framework owns the whole
+// device heap, real-time loops that forbid allocator calls, or setups that
+// must not create a persistent mesh handle.  vla_element_pages_static serves
+// them: it takes the raw coordinate and connectivity arrays and writes the
+// element pages and volumes, keeping its one scratch buffer (the float-pair
+// split of the node coordinates used by the mixed-precision geometry) in a
+// file-scope device array instead of allocating.  That array exists once per
+// GPU that loads the library and lives until the process exits.
+// ---------------------------------------------------------------------------
+namespace vla {
+namespace {
+
+constexpr int64_t kStaticMaxNodes = int64_t(1) << 18;    // 262,144 nodes: 8 MiB of float pairs
+static __device__ __align__(256) float4 g_static_xhl[2 * kStaticMaxNodes];
+
+std::mutex g_static_mu;
+void *g_static_ptr[64] = {nullptr};
+
+// Device address of the scratch array for the current device (set up once
+// per device with that device current; host code must not use the symbol's
+// name as an address).
+vla_status static_scratch(float4 **out) {
+    int dev = 0;
+    VLA_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(VLA_ERR_INVALID_ARG, "device ordinal %d not supported", dev);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_xhl);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+        g_static_ptr[dev] = p;
+    }
+    *out = reinterpret_cast<float4 *>(g_static_ptr[dev]);
+    return VLA_OK;
+}
+
+__global__ void k_static_split(int64_t nn, int dim, const double *__restrict__ x, float4 *__restrict__ xh,
+                               float4 *__restrict__ xl) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
+        float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+        for (int d = 0; d < dim; ++d) {
+            const double v = x[i * dim + d];
+            h[d] = (float)v;
+            l[d] = (float)(v - (double)h[d]);
+        }
+        xh[i] = make_float4(h[0], h[1], h[2], 0.f);
+        xl[i] = make_float4(l[0], l[1], l[2], 0.f);
+    }
+}
+
+// element pages and volumes straight from the mesh arrays, one thread per element
+template <int DIM, int ORDER, bool MIX>
+__global__ void __launch_bounds__(256) k_static_pages(int64_t ne, const int32_t *__restrict__ elems,
+                                                      const float4 *__restrict__ xh, const float4 *__restrict__ xl,
+                                                      const double *__restrict__ coords, int kind, double ca,
+                                                      double cb, double *__restrict__ Kp, double *__restrict__ Mp,
+                                                      double *__restrict__ vol, unsigned long long *__restrict__ n_sing) {
+    using C = Cfg<DIM, ORDER, MIX>;
+    using T = typename C::T;
+    const T cat = (T)ca, cbt = (T)cb;
+    unsigned long long sing = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ne; k += (int64_t)gridDim.x * blockDim.x) {
+        Geo<T> g;
+        if constexpr (MIX) {
+            float4 h[C::NV], l[C::NV];
+#pragma unroll
+            for (int j = 0; j < C::NV; ++j) {
+                const int32_t v = elems[k * C::NLB + j];
+                h[j] = xh[v];
+                l[j] = xl[v];
+            }
+            // same geometry as the tiled assembly, from vertex arrays
+            if constexpr (DIM == 3) {
+                geo_mixed3_fast(h, l, make_ushort4(0, 1, 2, 3), g);
+            } else {
+                geo_mixed2_fast(h, l, make_ushort4(0, 1, 2, 0), g);
+            }
+        } else {
+            double4 x[C::NV];
+#pragma unroll
+            for (int j = 0; j < C::NV; ++j) {
+                const int32_t v = elems[k * C::NLB + j];
+                x[j].x = coords[(int64_t)v * DIM];
+                x[j].y = coords[(int64_t)v * DIM + 1];
+                x[j].z = DIM == 3 ? coords[(int64_t)v * DIM + 2] : 0.0;
+                x[j].w = 0.0;
+            }
+            geo_f64<DIM>(x, make_ushort4(0, 1, 2, DIM == 3 ? 3 : 0), g);
+        }
+        const T c = coeff<T>(kind, cat, cbt, g.xc, DIM);
+        const T adet = g.det < T(0) ? -g.det : g.det;
+        T sc;
+        if constexpr (MIX) sc = c * __frcp_rn(T(C::DFACT) * adet);
+        else sc = c / (T(C::DFACT) * adet);
+        T cd[10];
+#pragma unroll
+        for (int a = 0; a < C::NV; ++a)
+#pragma unroll
+            for (int q = a; q < C::NV; ++q) cd[a * C::NV - a * (a - 1) / 2 + (q - a)] = dot3<T>(g.C[a], g.C[q]);
+        const T mscale = ORDER == 1 ? c * adet * T(C::MOFF / C::DFACT) : c * adet * T(1.0 / C::DFACT);
+        for (int a = 0; a < C::NLB; ++a)
+            for (int q = 0; q < C::NLB; ++q) {
+                const int p0 = a < q ? a : q, p1 = a < q ? q : a;
+                T kv, mv;
+                if constexpr (ORDER == 1) {
+                    kv = sc * cd[p0 * C::NV - p0 * (p0 - 1) / 2 + (p1 - p0)];
+                    mv = mscale * (a == q ? T(2) : T(1));
+                } else {
+                    const int u = p0 * C::NLB - p0 * (p0 - 1) / 2 + (p1 - p0);
+                    const P2Tab &tb = c_p2[DIM - 2];
+                    T acc = 0;
+                    for (int t = 0; t < tb.nterm[u]; ++t) acc += (MIX ? (T)tb.coef_f[u][t] : (T)tb.coef_d[u][t]) * cd[tb.st[u][t]];
+                    kv = sc * acc;
+                    mv = mscale * (MIX ? (T)tb.mhat_f[u] : (T)tb.mhat_d[u]);
+                }
+                const int64_t pos = k * C::NLB * C::NLB + a + (int64_t)q * C::NLB;
+                if constexpr (MIX) {
+                    if (Kp) Kp[pos] = f32_to_f64(kv);
+                    if (Mp) Mp[pos] = f32_to_f64(mv);
+                } else {
+                    if (Kp) Kp[pos] = kv;
+                    if (Mp) Mp[pos] = mv;
+                }
+            }
+        if (g.det == T(0)) ++sing;
+        if (vol) {
+            if constexpr (MIX) vol[k] = f32_to_f64(adet * (float)(1.0 / C::DFACT));
+            else vol[k] = adet / C::DFACT;
+        }
+    }
+    if (n_sing && sing) atomicAdd(n_sing, sing);
+}
+
+template <int DIM, int ORDER, bool MIX>
+void launch_static_pages(int64_t ne, const int32_t *elems, const float4 *xh, const float4 *xl, const double *coords,
+                         int kind, double ca, double cb, double *Kp, double *Mp, double *vol,
+                         unsigned long long *ns, cudaStream_t st) {
+    k_static_pages<DIM, ORDER, MIX><<<grid_for(ne, 256, 152 * 16), 256, 0, st>>>(ne, elems, xh, xl, coords, kind, ca,
+                                                                                   cb, Kp, Mp, vol, ns);
+}
+
+}  // namespace
+}  // namespace vla
+
+extern "C" vla_status vla_element_pages_static(int32_t dim, int32_t order, int64_t nn, int64_t ne,
+                                               const double *coords, const int32_t *elems, int32_t kind, double ca,
+                                               double cb, int32_t precision, double *K_pages, double *M_pages,
+                                               double *vol, int64_t *n_singular, void *stream) {
+    if (dim != 2 && dim != 3) return fail(VLA_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (order != VLA_P1 && order != VLA_P2) return fail(VLA_ERR_INVALID_ARG, "order must be VLA_P1 or VLA_P2");
+    if (kind != VLA_COEFF_POLY && kind != VLA_COEFF_EXP) return fail(VLA_ERR_INVALID_ARG, "unknown coefficient kind");
+    if (precision != VLA_PREC_FP64 && precision != VLA_PREC_MIXED)
+        return fail(VLA_ERR_INVALID_ARG, "precision must be VLA_PREC_FP64 or VLA_PREC_MIXED");
+    if (nn < 1 || ne < 0) return fail(VLA_ERR_INVALID_ARG, "need nn >= 1 and ne >= 0");
+    if (nn > kStaticMaxNodes)
+        return fail(VLA_ERR_BUDGET, "vla_element_pages_static: %lld nodes exceed its fixed scratch of %lld nodes; "
+                                    "use vla_mesh_create + vla_assemble", (long long)nn, (long long)kStaticMaxNodes);
+    if (ne >= ((int64_t)1 << 31) / 100) return fail(VLA_ERR_INVALID_ARG, "too many elements");
+    if (ne > 0 && (!coords || !elems)) return fail(VLA_ERR_INVALID_ARG, "null mesh array");
+    if (!std::isfinite(ca) || !std::isfinite(cb)) return fail(VLA_ERR_INVALID_ARG, "non-finite coefficient");
+    cudaStream_t st = (cudaStream_t)stream;
+    float4 *scratch = nullptr;
+    vla_status s = static_scratch(&scratch);
+    if (s) return s;
+    if (order == 2) {
+        s = ensure_p2_tables();
+        if (s) return s;
+    }
+    unsigned long long *ns = reinterpret_cast<unsigned long long *>(n_singular);
+    if (ns) VLA_CUDA(cudaMemsetAsync(ns, 0, sizeof(unsigned long long), st));
+    if (ne == 0) return VLA_OK;
+    const bool mix = precision == VLA_PREC_MIXED;
+    float4 *xh = scratch, *xl = scratch + kStaticMaxNodes;
+    if (mix) {
+        k_static_split<<<grid_for(nn, 256, 152 * 16), 256, 0, st>>>(nn, dim, coords, xh, xl);
+        VLA_CUDA(cudaGetLastError());
+    }
+    const int key = (dim == 3 ? 4 : 0) + (order == 2 ? 2 : 0) + (mix ? 1 : 0);
+    switch (key) {
+    case 0: launch_static_pages<2, 1, false>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
+    case 1: launch_static_pages<2, 1, true>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
+    case 2: launch_static_pages<2, 2, false>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
+    case 3: launch_static_pages<2, 2, true>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
+    case 4: launch_static_pages<3, 1, false>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
+    case 5: launch_static_pages<3, 1, true>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
+    case 6: launch_static_pages<3, 2, false>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
+    default: launch_static_pages<3, 2, true>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
+    }
+    VLA_CUDA(cudaGetLastError());
+    return VLA_OK;
+}
