@@ -383,11 +383,14 @@ __device__ __forceinline__ void geo_mixed3_fast(const float4 *__restrict__ sh, c
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const int c1 = (c + 1) % 3, c2 = (c + 2) % 3;
-        g.C[0][c] = det2_kahan(V[1][c1], V[1][c2], V[2][c1], V[2][c2]);
-        g.C[1][c] = det2_kahan(V[2][c1], V[2][c2], V[0][c1], V[0][c2]);
-        g.C[2][c] = det2_kahan(V[0][c1], V[0][c2], V[1][c1], V[1][c2]);
+        // fast path: one FMA per cofactor; the exact path below takes over
+        // whenever cancellation could matter (|det| small against perm(|V|))
+        const float p12 = V[1][c2] * V[2][c1], p20 = V[2][c2] * V[0][c1], p01 = V[0][c2] * V[1][c1];
+        g.C[0][c] = fmaf(V[1][c1], V[2][c2], -p12);
+        g.C[1][c] = fmaf(V[2][c1], V[0][c2], -p20);
+        g.C[2][c] = fmaf(V[0][c1], V[1][c2], -p01);
         g.C[3][c] = -((g.C[0][c] + g.C[1][c]) + g.C[2][c]);
-        perm = fmaf(fabsf(V[0][c]), fabsf(V[1][c1] * V[2][c2]) + fabsf(V[1][c2] * V[2][c1]), perm);
+        perm = fmaf(fabsf(V[0][c]), fabsf(V[1][c1] * V[2][c2]) + fabsf(p12), perm);
     }
     g.det = fmaf(V[0][0], g.C[0][0], fmaf(V[0][1], g.C[0][1], V[0][2] * g.C[0][2]));
     g.xc[0] = sx * 0.25f;
@@ -523,6 +526,8 @@ __global__ void __launch_bounds__(kThreads) k_assemble(AsmArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int next_chunk[2];   // dynamic chunk counters, one per tile parity
+    __shared__ vla::TileHdr s_hdr[2];   // header and segment map of the tile in each stage
+    __shared__ StageMap s_map[2];
     if (threadIdx.x == 0) {
         next_chunk[0] = kThreads / 32;
         next_chunk[1] = kThreads / 32;
@@ -540,6 +545,8 @@ __global__ void __launch_bounds__(kThreads) k_assemble(AsmArgs A) {
     auto issue = [&](int t, int s) {   // thread 0 only
         const vla::TileHdr h = A.tiles[t];
         const StageMap mp = stage_map<CT>(h);
+        s_hdr[s] = h;
+        s_map[s] = mp;
         unsigned char *b = stage(s);
         mbar_expect_tx(&bar[s], (uint32_t)mp.xyz);
         if (mp.rec > mp.ids) bulk_g2s(b + mp.ids, A.tile_nodes + h.node_off, (uint32_t)(mp.rec - mp.ids), &bar[s]);
@@ -554,8 +561,8 @@ __global__ void __launch_bounds__(kThreads) k_assemble(AsmArgs A) {
     };
     // coordinate gathers of tile t into stage s (all threads, asynchronous)
     auto gather = [&](int t, int s) {
-        const vla::TileHdr h = A.tiles[t];
-        const StageMap mp = stage_map<CT>(h);
+        const vla::TileHdr &h = s_hdr[s];
+        const StageMap &mp = s_map[s];
         const int32_t *ids = reinterpret_cast<const int32_t *>(stage(s) + mp.ids);
         unsigned char *xyz = stage(s) + mp.xyz;
         for (int i = threadIdx.x; i < h.n_nodes; i += kThreads) {
@@ -606,8 +613,8 @@ __global__ void __launch_bounds__(kThreads) k_assemble(AsmArgs A) {
         const int t = t0 + j * G;
         if (t >= A.n_tiles) break;
         const int s = j & 1;
-        const vla::TileHdr h = A.tiles[t];
-        const StageMap mp = stage_map<CT>(h);
+        const vla::TileHdr h = s_hdr[s];
+        const StageMap mp = s_map[s];
         unsigned char *b = stage(s);
         const ushort4 *s_rec = reinterpret_cast<const ushort4 *>(b + mp.rec);
         const int32_t *s_gid = reinterpret_cast<const int32_t *>(b + mp.gid);

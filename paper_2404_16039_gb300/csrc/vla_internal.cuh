@@ -102,37 +102,22 @@ __device__ __forceinline__ unsigned long long f32_to_f64_bits(float x) {
 
 __device__ __forceinline__ double f32_to_f64(float x) { return __longlong_as_double((long long)f32_to_f64_bits(x)); }
 
-// hi + lo as a double, for a normalised float pair (|lo| <= ulp_f32(hi)/2),
-// with integer instructions only and no data-dependent branches.  The 24-bit
-// significand of hi is widened to 53 bits and lo is added in units of the
-// result's last place (its bits below that are truncated, an error under one
-// double ulp); one left shift renormalises the rare case where lo pulls the
-// value below hi's binade.  Zero, subnormal-float lo and inf/nan hi are exact.
-__device__ __forceinline__ double ff_to_f64(float hi, float lo) {
-    const uint32_t hu = __float_as_uint(hi), lu = __float_as_uint(lo);
-    const uint32_t he = (hu >> 23) & 0xffu, le = (lu >> 23) & 0xffu;
-    if (((hu | lu) << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)(hu >> 31) << 63));
-    // the rare cases go through the exact (FP64) path: hi zero/subnormal/inf/nan
-    if (he == 0u || he == 0xffu) return f32_to_f64(hi) + f32_to_f64(lo);
-    // significand of hi with 29 extra bits: M in [2^52, 2^53)
-    const long long Mh = (long long)((0x800000u | (hu & 0x7fffffu))) << 29;
-    // lo's significand and its shift into units of 2^(E_hi - 52)
-    const uint32_t lm = (le == 0u) ? (lu & 0x7fffffu) : (0x800000u | (lu & 0x7fffffu));
-    const int sh = (int)(le == 0u ? 1u : le) - (int)he + 29;      // <= 5 for a normalised pair
-    const long long d = sh >= 0 ? ((long long)lm << (sh > 40 ? 40 : sh)) : (sh <= -32 ? 0ll : (long long)(lm >> -sh));
-    const bool same = (lu >> 31) == (hu >> 31);
-    long long M = same ? Mh + d : Mh - d;
-    int E = (int)he + 896;                                          // biased double exponent of hi
-    const int low = M < (1ll << 52) ? 1 : 0;                        // at most one bit lost
-    M <<= low;
-    E -= low;
-    const int up = M >= (1ll << 53) ? 1 : 0;                        // impossible for normalised pairs
-    M >>= up;
-    E += up;
-    const unsigned long long bits = ((unsigned long long)(hu >> 31) << 63) | ((unsigned long long)E << 52) |
-                                    ((unsigned long long)M & 0xfffffffffffffull);
-    return __longlong_as_double((long long)bits);
+// float -> double by integer widening of the bit pattern: exact for normal
+// numbers and zeros; subnormal floats, inf and nan take the general path.
+__device__ __forceinline__ double f32_to_f64_w(float x) {
+    const uint32_t u = __float_as_uint(x);
+    const uint32_t a = u & 0x7fffffffu;
+    const uint32_t e = a >> 23;
+    if (e == 0xffu || (e == 0u && a != 0u)) return f32_to_f64(x);
+    const unsigned long long mag = a ? (((unsigned long long)a << 29) + (896ull << 52)) : 0ull;
+    return __longlong_as_double((long long)(((unsigned long long)(u >> 31) << 63) | mag));
 }
+
+// hi + lo of a float pair as the correctly rounded double: both parts are
+// widened exactly with integer instructions and added once in FP64 (one
+// instruction on the otherwise idle FP64 pipe instead of a ~45-instruction
+// integer significand construction).
+__device__ __forceinline__ double ff_to_f64(float hi, float lo) { return f32_to_f64_w(hi) + f32_to_f64_w(lo); }
 
 // ---------------------------------------------------------------------------
 // PTX wrappers: mbarrier + 1-D bulk TMA (cp.async.bulk), sm_90+
