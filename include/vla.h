@@ -219,6 +219,115 @@ vla_status vla_element_pages_static(int32_t dim, int32_t order, int64_t nn, int6
  * the mesh was created with, which is synchronised first).  NULL is a no-op. */
 vla_status vla_mesh_destroy(vla_mesh *mesh);
 
+/* Reads and clears the mesh's device error word, synchronising `stream`:
+ * VLA_ERR_TIMEOUT if a bounded wait of a kernel on this mesh expired since
+ * the last check (its outputs are then incomplete), else VLA_OK.  Kernels
+ * never spin without a limit; an expired wait ends the kernel early and is
+ * reported here rather than by a fault. */
+vla_status vla_mesh_check(vla_mesh *mesh, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Batched assembly (Section 3.5 assembly over many meshes at once)          */
+/* ------------------------------------------------------------------------ */
+/* The paper assembles one mesh per call; a batch runs the same computation
+ * as vla_assemble for many meshes of any element type (triangles or
+ * tetrahedra, P1 or P2) in ONE persistent kernel launch: the row tiles of all
+ * meshes form one work list, and each CTA streams tiles of whatever mesh
+ * comes next.  Every mesh's outputs are bit-identical to vla_assemble on that
+ * mesh alone (the summation order of every value depends only on the mesh). */
+
+typedef struct vla_batch vla_batch;
+
+typedef struct {
+    const vla_mesh *mesh;      /* the mesh (handle from vla_mesh_create) */
+    int32_t coeff_kind;        /* as in vla_assemble */
+    int32_t reserved;          /* 0 */
+    double ca, cb;
+    double *K_vals, *M_vals;   /* nnz FP64 each (device), or NULL */
+    double *vol;               /* ne FP64 (device), or NULL */
+    double *K_pages, *M_pages; /* nlb x nlb x ne FP64 (device), or NULL */
+} vla_batch_job_t;
+
+typedef struct {
+    int32_t count;             /* jobs */
+    int32_t n_work;            /* row tiles over all jobs (work items of the launch) */
+    int32_t grid;              /* persistent CTAs of the launch */
+    int32_t ctas_per_sm;       /* tuned residency (0 = occupancy limit) */
+    int64_t smem_bytes;        /* dynamic shared memory per CTA */
+    int64_t elements;          /* sum of ne */
+    int64_t tile_elems;        /* element computations per launch (>= elements) */
+    int32_t graph;             /* 1 if runs replay a captured CUDA graph */
+    int32_t reserved;
+} vla_batch_info_t;
+
+#define VLA_BATCH_GRAPH 1      /* capture the launch into a CUDA graph at creation */
+
+/* Builds the job table and work list of a batch on the device.
+ *   jobs: host array of count >= 1 jobs (copied; meshes must outlive the batch).
+ *   precision: VLA_PREC_FP64 or VLA_PREC_MIXED, for every job.
+ *   n_singular: device int64[count] receiving, per job, the number of
+ *     elements with det == 0 (reset by every run), or NULL.
+ *   flags: 0 or VLA_BATCH_GRAPH (the reset and the kernel are captured once
+ *     into a CUDA graph; each run is one graph launch).
+ * Synchronises `stream`.  Errors: VLA_ERR_INVALID_ARG, VLA_ERR_OOM,
+ * VLA_ERR_UNSUPPORTED (a tile larger than shared memory), VLA_ERR_CUDA. */
+vla_status vla_batch_create(const vla_batch_job_t *jobs, int32_t count, int32_t precision, int64_t *n_singular,
+                            int32_t flags, void *stream, vla_batch **out);
+
+/* Replaces job `index`'s coefficient and output pointers (same mesh), stream
+ * ordered: runs enqueued on `stream` afterwards see the new job. */
+vla_status vla_batch_set_job(vla_batch *batch, int32_t index, const vla_batch_job_t *job, void *stream);
+
+/* Enqueues one assembly of every job on `stream` (one persistent launch, or
+ * one graph launch with VLA_BATCH_GRAPH). */
+vla_status vla_batch_run(vla_batch *batch, void *stream);
+
+/* Fills *info (host struct). */
+vla_status vla_batch_info(const vla_batch *batch, vla_batch_info_t *info);
+
+/* As vla_mesh_check, for the batch's own error word. */
+vla_status vla_batch_check(vla_batch *batch, void *stream);
+
+/* Frees the batch.  No run of it may still be in flight. */
+vla_status vla_batch_destroy(vla_batch *batch);
+
+/* One-shot batch: create, run once and free, all stream-ordered on `stream`
+ * (no host synchronisation); the error word is not kept. */
+vla_status vla_batch_assemble(const vla_batch_job_t *jobs, int32_t count, int32_t precision, int64_t *n_singular,
+                              void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Autotuning of the tile and warp mapping                                   */
+/* ------------------------------------------------------------------------ */
+/* The assembly maps elements to row tiles (the incidence budget bounds the
+ * rows x incident elements of one tile, which sets the element records and
+ * contribution lists a CTA holds in shared memory) and tiles to persistent
+ * CTAs of 8 warps, each warp taking 32-pair chunks of a tile.  The tuner
+ * times candidate budgets and CTA residencies on a sample mesh and keeps the
+ * fastest for the element type and precision, process-wide: meshes built
+ * afterwards use the tuned budget, and assemblies and batches the tuned
+ * residency.  Results do not depend on either choice. */
+
+typedef struct {
+    int32_t tile_budget;       /* incidence budget of a row tile (0 = library default) */
+    int32_t ctas_per_sm;       /* resident CTAs per SM (0 = occupancy limit) */
+    double us;                 /* median time of one assembly of the sample mesh, microseconds (tuner output) */
+} vla_tune_t;
+
+/* Times vla_assemble (precision as given, coefficient 1 + |x|^2, K, M and vol
+ * outputs, an L2 flush before every timed run) on the sample mesh for each
+ * candidate budget (0.5x to 1.5x the default) and then each residency (1, 2,
+ * 3, 4 and the occupancy limit) at the best budget, `reps` timed runs each
+ * (median), stores the winner and returns it in *best.  coords/elems as for
+ * vla_mesh_create.  Allocates scratch; synchronises `stream`. */
+vla_status vla_autotune(int32_t dim, int32_t order, int32_t precision, int64_t nn, int64_t ne, const double *coords,
+                        const int32_t *elems, int32_t reps, void *stream, vla_tune_t *best);
+
+/* Reads or sets the stored parameters for an element type and precision
+ * (us is ignored by vla_tune_set and 0 from vla_tune_get). */
+vla_status vla_tune_get(int32_t dim, int32_t order, int32_t precision, vla_tune_t *out);
+vla_status vla_tune_set(int32_t dim, int32_t order, int32_t precision, const vla_tune_t *in);
+
 #ifdef __cplusplus
 }
 #endif

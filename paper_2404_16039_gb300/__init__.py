@@ -21,7 +21,7 @@ import torch
 
 __all__ = [
     "VlaError", "lib", "version", "amtam", "astam", "avtam", "amdet", "aminv", "Mesh", "element_pages_static",
-    "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP",
+    "Batch", "batch_assemble", "autotune", "tune_get", "tune_set", "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP",
 ]
 
 F32, F64 = 0, 1
@@ -46,6 +46,25 @@ class MeshInfo(C.Structure):
                 ("nn", C.c_int64), ("ne", C.c_int64), ("nfb", C.c_int64), ("nnz", C.c_int64),
                 ("max_row_len", C.c_int32), ("n_tiles", C.c_int32), ("device_bytes", C.c_int64),
                 ("tile_elems", C.c_int64), ("n_codes", C.c_int64)]
+
+
+class BatchJob(C.Structure):
+    _fields_ = [("mesh", C.c_void_p), ("coeff_kind", C.c_int32), ("reserved", C.c_int32),
+                ("ca", C.c_double), ("cb", C.c_double), ("K_vals", C.c_void_p), ("M_vals", C.c_void_p),
+                ("vol", C.c_void_p), ("K_pages", C.c_void_p), ("M_pages", C.c_void_p)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("count", C.c_int32), ("n_work", C.c_int32), ("grid", C.c_int32), ("ctas_per_sm", C.c_int32),
+                ("smem_bytes", C.c_int64), ("elements", C.c_int64), ("tile_elems", C.c_int64),
+                ("graph", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Tune(C.Structure):
+    _fields_ = [("tile_budget", C.c_int32), ("ctas_per_sm", C.c_int32), ("us", C.c_double)]
+
+
+BATCH_GRAPH = 1
 
 
 def lib():
@@ -75,9 +94,22 @@ def lib():
         L.vla_simplex_normals.argtypes = [vp, vp, vp]
         L.vla_mesh_destroy.argtypes = [vp]
         L.vla_element_pages_static.argtypes = [i32, i32, i64, i64, vp, vp, i32, dbl, dbl, i32, vp, vp, vp, vp, vp]
+        L.vla_mesh_check.argtypes = [vp, vp]
+        L.vla_batch_create.argtypes = [C.POINTER(BatchJob), i32, i32, vp, i32, vp, C.POINTER(vp)]
+        L.vla_batch_set_job.argtypes = [vp, i32, C.POINTER(BatchJob), vp]
+        L.vla_batch_run.argtypes = [vp, vp]
+        L.vla_batch_info.argtypes = [vp, C.POINTER(BatchInfo)]
+        L.vla_batch_check.argtypes = [vp, vp]
+        L.vla_batch_destroy.argtypes = [vp]
+        L.vla_batch_assemble.argtypes = [C.POINTER(BatchJob), i32, i32, vp, vp]
+        L.vla_autotune.argtypes = [i32, i32, i32, i64, i64, vp, vp, i32, vp, C.POINTER(Tune)]
+        L.vla_tune_get.argtypes = [i32, i32, i32, C.POINTER(Tune)]
+        L.vla_tune_set.argtypes = [i32, i32, i32, C.POINTER(Tune)]
         for name in ("vla_amtam", "vla_astam", "vla_avtam", "vla_amdet", "vla_aminv", "vla_mesh_create",
                      "vla_mesh_info", "vla_mesh_csr", "vla_assemble", "vla_boundary", "vla_simplex_normals",
-                     "vla_mesh_destroy", "vla_element_pages_static"):
+                     "vla_mesh_destroy", "vla_element_pages_static", "vla_mesh_check", "vla_batch_create",
+                     "vla_batch_set_job", "vla_batch_run", "vla_batch_info", "vla_batch_check", "vla_batch_destroy",
+                     "vla_batch_assemble", "vla_autotune", "vla_tune_get", "vla_tune_set"):
             getattr(L, name).restype = i32
         _lib = L
         return L
@@ -285,6 +317,20 @@ class Mesh:
         _check(lib().vla_boundary(self._h, precision, _p(normals), _p(areas), _stream(stream)))
         return normals, areas
 
+    def check(self, stream=None):
+        """Raises VlaError (VLA_ERR_TIMEOUT) if a bounded wait of a kernel on
+        this mesh expired since the last check (vla_mesh_check)."""
+        _check(lib().vla_mesh_check(self._h, _stream(stream)))
+
+    def outputs(self, want_K=True, want_M=True, want_vol=True, pages=False):
+        """Fresh output tensors for one assembly of this mesh."""
+        dev, f64 = self.device, torch.float64
+        return {"K": torch.empty(self.nnz, dtype=f64, device=dev) if want_K else None,
+                "M": torch.empty(self.nnz, dtype=f64, device=dev) if want_M else None,
+                "vol": torch.empty(self.ne, dtype=f64, device=dev) if want_vol else None,
+                "K3D": torch.empty((self.ne, self.nlb, self.nlb), dtype=f64, device=dev) if pages else None,
+                "M3D": torch.empty((self.ne, self.nlb, self.nlb), dtype=f64, device=dev) if pages else None}
+
     def simplex_normals(self, stream=None):
         """Unnormalised facet normals of every element: (ne, dim+1, dim), [k, j] = column j."""
         out = torch.empty((self.ne, self.dim + 1, self.dim), dtype=torch.float64, device=self.device)
@@ -313,3 +359,92 @@ def element_pages_static(coords, elems, order=1, ca=1.0, cb=0.0, kind=COEFF_POLY
     if count_singular:
         out["n_singular"] = ns
     return out
+
+
+# ---------------------------------------------------------------------------
+# batches and tuning
+# ---------------------------------------------------------------------------
+
+def _job(mesh, out, kind, ca, cb):
+    return BatchJob(mesh._h, kind, 0, float(ca), float(cb), _p(out.get("K")), _p(out.get("M")),
+                    _p(out.get("vol")), _p(out.get("K3D")), _p(out.get("M3D")))
+
+
+class Batch:
+    """Many meshes assembled by one persistent launch (vla_batch_create).
+
+    ``jobs`` is a list of (mesh, outputs, kind, ca, cb) where outputs is a
+    dict with optional keys K, M, vol, K3D, M3D (tensors, e.g. from
+    Mesh.outputs()).  With ``graph`` the launch is captured into a CUDA graph.
+    ``n_singular`` (int64 tensor, one entry per job) is filled by each run."""
+
+    def __init__(self, jobs, precision=PREC_MIXED, graph=False, count_singular=False, stream=None):
+        if not jobs:
+            raise ValueError("a batch needs at least one job")
+        self.meshes = [j[0] for j in jobs]
+        self.outs = [j[1] for j in jobs]
+        arr = (BatchJob * len(jobs))(*[_job(m, o, k, a, b) for (m, o, k, a, b) in jobs])
+        dev = self.meshes[0].device
+        self.n_singular = torch.zeros(len(jobs), dtype=torch.int64, device=dev) if count_singular else None
+        h = C.c_void_p()
+        _check(lib().vla_batch_create(arr, len(jobs), precision, _p(self.n_singular),
+                                      BATCH_GRAPH if graph else 0, _stream(stream), C.byref(h)))
+        self._h = h
+        info = BatchInfo()
+        _check(lib().vla_batch_info(h, C.byref(info)))
+        self.count, self.n_work, self.grid = info.count, info.n_work, info.grid
+        self.ctas_per_sm, self.smem_bytes = info.ctas_per_sm, info.smem_bytes
+        self.elements, self.tile_elems, self.graph = info.elements, info.tile_elems, bool(info.graph)
+
+    def set_job(self, index, out, kind=COEFF_POLY, ca=1.0, cb=0.0, stream=None):
+        job = _job(self.meshes[index], out, kind, ca, cb)
+        _check(lib().vla_batch_set_job(self._h, index, C.byref(job), _stream(stream)))
+        self.outs[index] = out
+
+    def run(self, stream=None):
+        _check(lib().vla_batch_run(self._h, _stream(stream)))
+        return self.outs
+
+    def check(self, stream=None):
+        _check(lib().vla_batch_check(self._h, _stream(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vla_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_assemble(jobs, precision=PREC_MIXED, n_singular=None, stream=None):
+    """One-shot batch (vla_batch_assemble): jobs as for Batch; stream-ordered."""
+    arr = (BatchJob * len(jobs))(*[_job(m, o, k, a, b) for (m, o, k, a, b) in jobs])
+    _check(lib().vla_batch_assemble(arr, len(jobs), precision, _p(n_singular), _stream(stream)))
+    return [j[1] for j in jobs]
+
+
+def autotune(coords, elems, order=1, precision=PREC_MIXED, reps=5, stream=None):
+    """Times candidate tile budgets and CTA residencies on this sample mesh,
+    stores the fastest for its element type and precision, and returns
+    (tile_budget, ctas_per_sm, microseconds)."""
+    _req(coords, torch.float64), _req(elems, torch.int32)
+    nn, dim = coords.shape
+    t = Tune()
+    _check(lib().vla_autotune(dim, order, precision, nn, elems.shape[0], _p(coords), _p(elems), reps,
+                              _stream(stream), C.byref(t)))
+    return t.tile_budget, t.ctas_per_sm, t.us
+
+
+def tune_get(dim, order, precision=PREC_MIXED):
+    t = Tune()
+    _check(lib().vla_tune_get(dim, order, precision, C.byref(t)))
+    return t.tile_budget, t.ctas_per_sm
+
+
+def tune_set(dim, order, precision=PREC_MIXED, tile_budget=0, ctas_per_sm=0):
+    t = Tune(tile_budget, ctas_per_sm, 0.0)
+    _check(lib().vla_tune_set(dim, order, precision, C.byref(t)))

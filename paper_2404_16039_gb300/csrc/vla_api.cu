@@ -2,6 +2,7 @@
 // device error word polled after bounded waits.
 #include <cstdarg>
 #include <cstring>
+#include <mutex>
 
 #include "vla_internal.cuh"
 
@@ -30,6 +31,27 @@ vla_status fail(vla_status st, const char *fmt, ...) {
 
 vla_status cuda_fail(cudaError_t e, const char *what) {
     return fail(VLA_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+static std::mutex g_tune_mu;
+static int g_budget[4] = {0, 0, 0, 0};
+static int g_ctas[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+
+int tuned_budget(int type) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return (type >= 0 && type < 4) ? g_budget[type] : 0;
+}
+
+int tuned_ctas(int type, bool mix) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    return (type >= 0 && type < 4) ? g_ctas[type][mix ? 1 : 0] : 0;
+}
+
+void set_tuned(int type, bool mix, int budget, int ctas) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (type < 0 || type >= 4) return;
+    g_budget[type] = budget;
+    g_ctas[type][mix ? 1 : 0] = ctas;
 }
 
 }  // namespace vla

@@ -18,6 +18,7 @@
 // for j < d and C_d = -sum_j C_j.  P1: K_k(a,b) = c_k (C_a.C_b) / (d! |det V|),
 // M_k = c_k |det V| / d! * (1 + delta_ab) / ((d+1)(d+2)).  P2: the same
 // cofactor products weighted by reference tensors from the 4-point rule.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -437,7 +438,11 @@ struct Cfg {
     static constexpr double MOFF = 1.0 / ((DIM + 1) * (DIM + 2));   // P1 off-diagonal mass / (c |T|)
 };
 
-struct AsmArgs {
+// One mesh of an assembly launch: its tile streams, coordinates, coefficient
+// and outputs.  A single-mesh launch passes it as a kernel parameter; a
+// batched launch keeps a table of them in device memory and bulk-copies the
+// one a tile belongs to into shared memory together with the tile.
+struct MeshJob {
     const vla::TileHdr *tiles;
     const int32_t *tile_nodes;
     const ushort4 *tile_elem;
@@ -447,25 +452,48 @@ struct AsmArgs {
     const void *codes;
     const float4 *xh, *xl;
     const double *coords;
-    int n_tiles;
-    int kind;
-    double ca, cb;
-    float caf, cbf;
     double *K, *M, *vol, *Kp, *Mp;
     unsigned long long *n_sing;
-    int *err;
+    double ca, cb;
+    float caf, cbf;
+    int32_t kind;
+    int32_t type;          // element type index (dim - 2) * 2 + (order - 1)
+    int32_t n_tiles;
+    int32_t work_base;     // first work item of the mesh in a batched launch
+    int64_t pad;
+};
+static_assert(sizeof(MeshJob) == 176, "MeshJob is bulk-copied in 16-byte units");
+static_assert(sizeof(vla::TileHdr) == 64, "TileHdr is fetched in 16-byte units");
+
+// One tile of a batched launch: its header, the absolute sources of its six
+// staged segments (vertex ids, element records, owned ids, chunk table, pair
+// positions, codes) and the job of its mesh.
+struct WorkItem {
+    vla::TileHdr h;
+    const void *src[6];
+    const MeshJob *job;
+    int32_t type, job_index;
+};
+static_assert(sizeof(WorkItem) == 128, "WorkItem is fetched in 16-byte units");
+
+struct LaunchArgs {
+    MeshJob one;              // single-mesh launch: the mesh
+    const WorkItem *work;     // batched launch: the work items
+    int n_work;               // tiles of the mesh, or work items of the batch
+    int *err;                 // device error word (bit 0: a bounded wait expired)
     int spin_limit;
-    int stage_bytes;       // bytes of one input stage (segments + coordinates), 16-byte multiple
+    int stage_bytes;          // bytes of one input stage (segments + coordinates), 16-byte multiple
 };
 
 __host__ __device__ constexpr int padq(int x, int q) { return (x + q - 1) / q * q; }
+__host__ __device__ constexpr int type_index(int dim, int order) { return (dim - 2) * 2 + (order - 1); }
+__host__ __device__ constexpr int code_bytes(int type) { return (type & 1) ? 4 : 2; }   // P2 uint32, P1 uint16
 
 // byte offsets of the staged segments of one tile inside a stage
 struct StageMap {
     int ids, rec, gid, chk, nz, cod, xyz, end;
 };
-template <typename CT>
-__device__ __forceinline__ StageMap stage_map(const vla::TileHdr &h) {
+__device__ __forceinline__ StageMap stage_map(const vla::TileHdr &h, int cbytes) {
     StageMap m;
     m.ids = 0;
     m.rec = m.ids + 4 * padq(h.n_nodes, kTilePadNodes);
@@ -473,7 +501,7 @@ __device__ __forceinline__ StageMap stage_map(const vla::TileHdr &h) {
     m.chk = m.gid + 4 * padq(h.n_own, kTilePadOwn);
     m.nz = m.chk + 8 * padq(h.n_chunks, kTilePadChunks);
     m.cod = m.nz + 8 * padq(h.n_nz, kTilePadNz);
-    m.xyz = m.cod + padq((int)sizeof(CT) * h.n_codes, 16);
+    m.xyz = m.cod + padq(cbytes * h.n_codes, 16);
     m.end = m.xyz + 32 * h.n_nodes;
     return m;
 }
@@ -514,67 +542,335 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_but1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Persistent CTA: tiles blockIdx.x, +gridDim.x, ...  Two input stages: while
-// tile j is computed from stage j&1, the bulk copies of tile j+2 and the
-// coordinate gathers (cp.async) of tile j+1 are in flight.
+// Phase 1 of a tile: one thread per tile element computes the packed upper
+// triangle of K_k and the mass scale into the record area (index n_elems is
+// the zero record that padding codes point at), and writes the outputs of
+// the elements the tile owns (vol, optional pages, singular count).
 template <int DIM, int ORDER, bool MIX>
-__global__ void __launch_bounds__(kThreads) k_assemble(AsmArgs A) {
+__device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileHdr &h, const unsigned char *b,
+                                              const StageMap &mp, typename Cfg<DIM, ORDER, MIX>::T *s_k,
+                                              const typename Cfg<DIM, ORDER, MIX>::T *mhat) {
     using C = Cfg<DIM, ORDER, MIX>;
     using T = typename C::T;
+    const ushort4 *s_rec = reinterpret_cast<const ushort4 *>(b + mp.rec);
+    const int32_t *s_gid = reinterpret_cast<const int32_t *>(b + mp.gid);
+    const float4 *s_h = reinterpret_cast<const float4 *>(b + mp.xyz);
+    const float4 *s_l = s_h + h.n_nodes;
+    const double4 *s_x = reinterpret_cast<const double4 *>(b + mp.xyz);
+    const T ca = MIX ? (T)J.caf : (T)J.ca, cb = MIX ? (T)J.cbf : (T)J.cb;
+    for (int e = threadIdx.x; e <= h.n_elems; e += kThreads) {
+        T *dst = s_k + (size_t)e * C::RS;
+        if (e == h.n_elems) {
+            for (int u = 0; u < C::RS; ++u) dst[u] = T(0);
+            continue;
+        }
+        const ushort4 v = s_rec[e];
+        Geo<T> g;
+        if constexpr (MIX) {
+            if constexpr (DIM == 3) geo_mixed3_fast(s_h, s_l, v, g);
+            else geo_mixed2_fast(s_h, s_l, v, g);
+        } else {
+            geo_f64<DIM>(s_x, v, g);
+        }
+        const T c = coeff<T>(J.kind, ca, cb, g.xc, DIM);
+        const T adet = g.det < T(0) ? -g.det : g.det;
+        T sc;
+        if constexpr (MIX) sc = c * __frcp_rn(T(C::DFACT) * adet);   // K(a,b) = sc * C_a . C_b
+        else sc = c / (T(C::DFACT) * adet);
+        T mscale;
+        if constexpr (ORDER == 1) {
+            T rec[C::RS];
+#pragma unroll
+            for (int u = 0; u < C::RS; ++u) rec[u] = T(0);
+#pragma unroll
+            for (int a = 0; a < C::NV; ++a)
+#pragma unroll
+                for (int q = a; q < C::NV; ++q) rec[a * C::NLB - a * (a - 1) / 2 + (q - a)] = sc * dot3<T>(g.C[a], g.C[q]);
+            mscale = c * adet * T(C::MOFF / C::DFACT);       // off-diagonal mass entry
+            rec[C::NU] = mscale;
+            if constexpr (MIX) {
+#pragma unroll
+                for (int u = 0; u < C::RS; u += 4)
+                    *reinterpret_cast<float4 *>(dst + u) = make_float4(rec[u], rec[u + 1], rec[u + 2], rec[u + 3]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < C::RS; u += 2)
+                    *reinterpret_cast<double2 *>(dst + u) = make_double2(rec[u], rec[u + 1]);
+            }
+        } else {
+            T cd[10];
+#pragma unroll
+            for (int a = 0; a < C::NV; ++a)
+#pragma unroll
+                for (int q = a; q < C::NV; ++q) cd[a * C::NV - a * (a - 1) / 2 + (q - a)] = dot3<T>(g.C[a], g.C[q]);
+            const P2Tab &tb = c_p2[DIM - 2];
+            for (int u = 0; u < C::NU; ++u) {
+                T acc = 0;
+                const int nt = tb.nterm[u];
+                for (int q = 0; q < nt; ++q) {
+                    const T cf = MIX ? (T)tb.coef_f[u][q] : (T)tb.coef_d[u][q];
+                    acc += cf * cd[tb.st[u][q]];
+                }
+                dst[u] = sc * acc;
+            }
+            mscale = c * adet * T(1.0 / C::DFACT);           // c |T|; entries scale the reference mass
+            dst[C::NU] = mscale;
+        }
+        if (e < h.n_own) {
+            const int64_t k = s_gid[e];
+            if (g.det == T(0) && J.n_sing) atomicAdd(J.n_sing, 1ull);
+            if (J.vol) {
+                if constexpr (MIX) J.vol[k] = f32_to_f64(adet * (float)(1.0 / C::DFACT));
+                else J.vol[k] = adet / C::DFACT;
+            }
+            if (J.Kp || J.Mp) {
+                for (int a = 0; a < C::NLB; ++a)
+                    for (int q = 0; q < C::NLB; ++q) {
+                        const int p0 = a < q ? a : q, p1 = a < q ? q : a;
+                        const int u = p0 * C::NLB - p0 * (p0 - 1) / 2 + (p1 - p0);
+                        const int64_t pos = k * C::NLB * C::NLB + a + (int64_t)q * C::NLB;
+                        const T kv = dst[u];
+                        T mv;
+                        if constexpr (ORDER == 1) mv = mscale * (a == q ? T(2) : T(1));
+                        else mv = mscale * mhat[u];
+                        if constexpr (MIX) {
+                            if (J.Kp) J.Kp[pos] = f32_to_f64(kv);
+                            if (J.Mp) J.Mp[pos] = f32_to_f64(mv);
+                        } else {
+                            if (J.Kp) J.Kp[pos] = kv;
+                            if (J.Mp) J.Mp[pos] = mv;
+                        }
+                    }
+            }
+        }
+    }
+}
+
+// Phase 2 of a tile: the pairs {i, j} of its rows, sorted by contribution
+// count and cut into 32-pair chunks handed to warps dynamically (a static
+// round-robin would give the first warps all the long ones); each lane sums
+// its pair's contributions in ascending element order and writes p_ij and
+// p_ji once.
+template <int DIM, int ORDER, bool MIX>
+__device__ __forceinline__ void tile_pairs(double *__restrict__ K, double *__restrict__ M, const vla::TileHdr &h,
+                                           const unsigned char *b, const StageMap &mp,
+                                           const typename Cfg<DIM, ORDER, MIX>::T *s_k,
+                                           const typename Cfg<DIM, ORDER, MIX>::T *mhat, int *next_chunk) {
+    using C = Cfg<DIM, ORDER, MIX>;
     using CT = typename C::CT;
+    constexpr uint32_t UMASK = (1u << C::UB) - 1;
+    const int2 *s_chk = reinterpret_cast<const int2 *>(b + mp.chk);
+    const int2 *s_nz = reinterpret_cast<const int2 *>(b + mp.nz);
+    const CT *s_cod = reinterpret_cast<const CT *>(b + mp.cod);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = warp;;) {
+        if (c >= h.n_chunks) break;
+        const int q = c * 32 + lane;
+        const int2 ch = s_chk[c];
+        const CT *cp = s_cod + ch.x + lane;
+        if constexpr (MIX) {
+            unsigned long long h0 = 0ull, l0 = 0ull, h1 = 0ull, l1 = 0ull;   // (K, M) pairs, 2 chains
+            int tt = 0;
+            for (; tt + 1 < ch.y; tt += 2) {
+                const uint32_t c0 = cp[tt * 32], c1 = cp[(tt + 1) * 32];
+                const float *r0 = s_k + (c0 >> C::UB) * C::RS, *r1 = s_k + (c1 >> C::UB) * C::RS;
+                float m0 = r0[C::NU], m1 = r1[C::NU];
+                if constexpr (ORDER == 2) {
+                    m0 *= mhat[c0 & UMASK];
+                    m1 *= mhat[c1 & UMASK];
+                }
+                ff2_add(h0, l0, pk(r0[c0 & UMASK], m0));
+                ff2_add(h1, l1, pk(r1[c1 & UMASK], m1));
+            }
+            if (tt < ch.y) {
+                const uint32_t c0 = cp[tt * 32];
+                const float *r0 = s_k + (c0 >> C::UB) * C::RS;
+                float m0 = r0[C::NU];
+                if constexpr (ORDER == 2) m0 *= mhat[c0 & UMASK];
+                ff2_add(h0, l0, pk(r0[c0 & UMASK], m0));
+            }
+            if (q < h.n_nz) {
+                ff2_add(h0, l0, h1);
+                ff2_add(h0, l0, l1);
+                // renormalise both sums at once: (hi, lo) <- TwoSum(hi, lo)
+                const unsigned long long s2 = add2(h0, l0);
+                const unsigned long long bb = sub2(s2, h0);
+                const unsigned long long e2 = add2(sub2(h0, sub2(s2, bb)), sub2(l0, bb));
+                float khi, mhi, klo, mlo;
+                upk(s2, khi, mhi);
+                upk(e2, klo, mlo);
+                const int2 pos = s_nz[q];
+                if (ORDER == 1 && pos.x == pos.y) {   // P1 diagonal mass: twice the off-diagonal scale
+                    mhi *= 2.f;
+                    mlo *= 2.f;
+                }
+                const double kd = ff_to_f64(khi, klo), md = ff_to_f64(mhi, mlo);
+                if (K) {
+                    K[pos.x] = kd;
+                    if (pos.y != pos.x) K[pos.y] = kd;
+                }
+                if (M) {
+                    M[pos.x] = md;
+                    if (pos.y != pos.x) M[pos.y] = md;
+                }
+            }
+        } else {
+            double ks = 0.0, ms = 0.0;
+            for (int tt = 0; tt < ch.y; ++tt) {
+                const uint32_t c0 = cp[tt * 32];
+                const double *r0 = s_k + (c0 >> C::UB) * C::RS;
+                ks += r0[c0 & UMASK];
+                if constexpr (ORDER == 2) ms += r0[C::NU] * mhat[c0 & UMASK];
+                else ms += r0[C::NU];
+            }
+            if (q < h.n_nz) {
+                const int2 pos = s_nz[q];
+                if (ORDER == 1 && pos.x == pos.y) ms *= 2.0;
+                if (K) {
+                    K[pos.x] = ks;
+                    if (pos.y != pos.x) K[pos.y] = ks;
+                }
+                if (M) {
+                    M[pos.x] = ms;
+                    if (pos.y != pos.x) M[pos.y] = ms;
+                }
+            }
+        }
+        int nc = 0;
+        if (lane == 0) nc = atomicAdd(next_chunk, 1);
+        c = __shfl_sync(0xffffffffu, nc, 0);
+    }
+}
+
+// Calls f(DIM, ORDER) (as integral constants) for element type `ty`, which
+// must be one of the types in the bit set TYPES; a single-type set needs no
+// test at run time.
+template <int TYPES, typename F>
+__device__ __forceinline__ void by_type(int ty, F &&f) {
+    using I2 = std::integral_constant<int, 2>;
+    using I3 = std::integral_constant<int, 3>;
+    using O1 = std::integral_constant<int, 1>;
+    using O2 = std::integral_constant<int, 2>;
+    if constexpr ((TYPES & 4) != 0)
+        if (TYPES == 4 || ty == 2) {
+            f(I3(), O1());
+            return;
+        }
+    if constexpr ((TYPES & 8) != 0)
+        if (TYPES == 8 || ty == 3) {
+            f(I3(), O2());
+            return;
+        }
+    if constexpr ((TYPES & 1) != 0)
+        if (TYPES == 1 || ty == 0) {
+            f(I2(), O1());
+            return;
+        }
+    if constexpr ((TYPES & 2) != 0)
+        if (TYPES == 2 || ty == 1) f(I2(), O2());
+}
+
+constexpr int single_type(int types) { return types == 1 ? 0 : types == 2 ? 1 : types == 4 ? 2 : 3; }
+
+// Persistent CTA over work items blockIdx.x, +gridDim.x, ...: the tiles of
+// one mesh (BATCH false, one element type) or the tiles of many meshes of
+// any of the element types in TYPES (BATCH true).  Two input stages: while
+// tile j is computed from stage j&1, the bulk copies of tile j+2 (and, in a
+// batch, the job of its mesh) and the coordinate gathers (cp.async) of tile
+// j+1 are in flight, and the header of tile j+2 is being fetched.
+template <bool MIX, int TYPES, bool BATCH>
+__global__ void __launch_bounds__(kThreads) k_assemble(const LaunchArgs A) {
+    using T = typename std::conditional<MIX, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
-    __shared__ int next_chunk[2];   // dynamic chunk counters, one per tile parity
-    __shared__ vla::TileHdr s_hdr[2];   // header and segment map of the tile in each stage
+    __shared__ int next_chunk[2];                   // dynamic chunk counters, one per tile parity
+    __shared__ __align__(16) WorkItem s_item[3];    // the tiles of the two stages, and the next one
+    __shared__ __align__(16) MeshJob s_job[BATCH ? 2 : 1];
     __shared__ StageMap s_map[2];
+    __shared__ T mhat[(TYPES & 10) ? 76 : 1];        // P2 reference mass: triangles at 0, tetrahedra at 21
     if (threadIdx.x == 0) {
         next_chunk[0] = kThreads / 32;
         next_chunk[1] = kThreads / 32;
     }
+    if constexpr ((TYPES & 2) != 0)
+        for (int u = threadIdx.x; u < 21; u += kThreads) mhat[u] = MIX ? (T)c_p2[0].mhat_f[u] : (T)c_p2[0].mhat_d[u];
+    if constexpr ((TYPES & 8) != 0)
+        for (int u = threadIdx.x; u < 55; u += kThreads)
+            mhat[21 + u] = MIX ? (T)c_p2[1].mhat_f[u] : (T)c_p2[1].mhat_d[u];
     auto stage = [&](int st_) { return smem + (size_t)st_ * A.stage_bytes; };
     T *s_k = reinterpret_cast<T *>(smem + 2 * (size_t)A.stage_bytes);
-    __shared__ T mhat[ORDER == 2 ? C::NU : 1];
-    if constexpr (ORDER == 2) {
-        for (int u = threadIdx.x; u < C::NU; u += kThreads)
-            mhat[u] = MIX ? (T)c_p2[DIM - 2].mhat_f[u] : (T)c_p2[DIM - 2].mhat_d[u];
-    }
-    const int G = gridDim.x;
+    const int G = gridDim.x, n = A.n_work;
     int issued0 = 0, issued1 = 0;   // thread 0: loads issued per stage
 
-    auto issue = [&](int t, int s) {   // thread 0 only
-        const vla::TileHdr h = A.tiles[t];
-        const StageMap mp = stage_map<CT>(h);
-        s_hdr[s] = h;
+    auto type_of = [&](int s) { return BATCH ? s_item[s].type : single_type(TYPES); };
+    auto job_of = [&](int s) -> const MeshJob & {
+        if constexpr (BATCH) return s_job[s];
+        else return A.one;
+    };
+    auto fetch = [&](int w, int slot) {   // thread 0: work item w into s_item[slot], synchronously
+        if constexpr (BATCH) s_item[slot] = A.work[w];
+        else s_item[slot].h = A.one.tiles[w];
+    };
+    auto prefetch = [&](int w) {   // work item w into s_item[2], asynchronously (one cp.async group)
+        unsigned char *d = reinterpret_cast<unsigned char *>(&s_item[2]);
+        if constexpr (BATCH) {
+            if (threadIdx.x < 8) cp_async16(d + 16 * threadIdx.x, reinterpret_cast<const unsigned char *>(A.work + w) + 16 * threadIdx.x);
+        } else {
+            if (threadIdx.x < 4) cp_async16(d + 16 * threadIdx.x, reinterpret_cast<const unsigned char *>(A.one.tiles + w) + 16 * threadIdx.x);
+        }
+        cp_async_commit();
+    };
+    auto issue = [&](int s) {   // thread 0: bulk copies of the tile in s_item[s] into stage s
+        const vla::TileHdr &h = s_item[s].h;
+        const int cb = code_bytes(type_of(s));
+        const StageMap mp = stage_map(h, cb);
         s_map[s] = mp;
         unsigned char *b = stage(s);
-        mbar_expect_tx(&bar[s], (uint32_t)mp.xyz);
-        if (mp.rec > mp.ids) bulk_g2s(b + mp.ids, A.tile_nodes + h.node_off, (uint32_t)(mp.rec - mp.ids), &bar[s]);
-        if (mp.gid > mp.rec) bulk_g2s(b + mp.rec, A.tile_elem + h.elem_off, (uint32_t)(mp.gid - mp.rec), &bar[s]);
-        if (mp.chk > mp.gid) bulk_g2s(b + mp.gid, A.tile_own + h.own_off, (uint32_t)(mp.chk - mp.gid), &bar[s]);
-        if (mp.nz > mp.chk) bulk_g2s(b + mp.chk, A.tile_chunks + h.chunk_off, (uint32_t)(mp.nz - mp.chk), &bar[s]);
-        if (mp.cod > mp.nz) bulk_g2s(b + mp.nz, A.tile_nzpos + h.nz_off, (uint32_t)(mp.cod - mp.nz), &bar[s]);
-        if (mp.xyz > mp.cod)
-            bulk_g2s(b + mp.cod, reinterpret_cast<const CT *>(A.codes) + h.code_off, (uint32_t)(mp.xyz - mp.cod), &bar[s]);
+        const void *src[6];
+        if constexpr (BATCH) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) src[i] = s_item[s].src[i];
+        } else {
+            src[0] = A.one.tile_nodes + h.node_off;
+            src[1] = A.one.tile_elem + h.elem_off;
+            src[2] = A.one.tile_own + h.own_off;
+            src[3] = A.one.tile_chunks + h.chunk_off;
+            src[4] = A.one.tile_nzpos + h.nz_off;
+            src[5] = reinterpret_cast<const unsigned char *>(A.one.codes) + (size_t)cb * h.code_off;
+        }
+        mbar_expect_tx(&bar[s], (uint32_t)mp.xyz + (BATCH ? (uint32_t)sizeof(MeshJob) : 0u));
+        if constexpr (BATCH) bulk_g2s(&s_job[s], s_item[s].job, (uint32_t)sizeof(MeshJob), &bar[s]);
+        const int off[7] = {mp.ids, mp.rec, mp.gid, mp.chk, mp.nz, mp.cod, mp.xyz};
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            if (off[i + 1] > off[i]) bulk_g2s(b + off[i], src[i], (uint32_t)(off[i + 1] - off[i]), &bar[s]);
         if (s) ++issued1;
         else ++issued0;
     };
-    // coordinate gathers of tile t into stage s (all threads, asynchronous)
-    auto gather = [&](int t, int s) {
-        const vla::TileHdr &h = s_hdr[s];
+    // coordinate gathers of the tile of stage s (all threads, asynchronous)
+    auto gather = [&](int s) {
+        const vla::TileHdr &h = s_item[s].h;
         const StageMap &mp = s_map[s];
+        const MeshJob &J = job_of(s);
         const int32_t *ids = reinterpret_cast<const int32_t *>(stage(s) + mp.ids);
         unsigned char *xyz = stage(s) + mp.xyz;
-        for (int i = threadIdx.x; i < h.n_nodes; i += kThreads) {
-            const int32_t g = ids[i];
-            if constexpr (MIX) {
-                cp_async16(xyz + 16 * i, A.xh + g);
-                cp_async16(xyz + 16 * (h.n_nodes + i), A.xl + g);
-            } else {
+        if constexpr (MIX) {
+            const float4 *xh = J.xh, *xl = J.xl;
+            for (int i = threadIdx.x; i < h.n_nodes; i += kThreads) {
+                const int32_t g = ids[i];
+                cp_async16(xyz + 16 * i, xh + g);
+                cp_async16(xyz + 16 * (h.n_nodes + i), xl + g);
+            }
+        } else {
+            const double *x = J.coords;
+            const int dim = 2 + (type_of(s) >> 1);
+            for (int i = threadIdx.x; i < h.n_nodes; i += kThreads) {
+                const int32_t g = ids[i];
                 double *dst = reinterpret_cast<double *>(xyz + 32 * i);
-#pragma unroll
-                for (int d = 0; d < DIM; ++d) cp_async8(dst + d, A.coords + (int64_t)g * DIM + d);
-                if (DIM == 2) dst[2] = 0.0;
+                for (int d = 0; d < dim; ++d) cp_async8(dst + d, x + (int64_t)g * dim + d);
+                if (dim == 2) dst[2] = 0.0;
             }
         }
         cp_async_commit();
@@ -589,261 +885,157 @@ __global__ void __launch_bounds__(kThreads) k_assemble(AsmArgs A) {
     };
 
     const int t0 = blockIdx.x;
-    if (t0 >= A.n_tiles) return;
+    if (t0 >= n) return;
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         fence_async_smem();
-        issue(t0, 0);
-        if (t0 + G < A.n_tiles) issue(t0 + G, 1);
+        fetch(t0, 0);
+        issue(0);
+        if (t0 + G < n) {
+            fetch(t0 + G, 1);
+            issue(1);
+        }
     }
     __syncthreads();
     if (__syncthreads_or(!mbar_wait_bounded(&bar[0], 0, A.spin_limit))) {
         bail();
         return;
     }
-    gather(t0, 0);
-
-    const T ca = MIX ? (T)A.caf : (T)A.ca, cb = MIX ? (T)A.cbf : (T)A.cb;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr uint32_t UMASK = (1u << C::UB) - 1;
-    unsigned long long sing = 0;
+    gather(0);
 
     for (int j = 0;; ++j) {
         const int t = t0 + j * G;
-        if (t >= A.n_tiles) break;
+        if (t >= n) break;
         const int s = j & 1;
-        const vla::TileHdr h = s_hdr[s];
-        const StageMap mp = s_map[s];
-        unsigned char *b = stage(s);
-        const ushort4 *s_rec = reinterpret_cast<const ushort4 *>(b + mp.rec);
-        const int32_t *s_gid = reinterpret_cast<const int32_t *>(b + mp.gid);
-        const int2 *s_chk = reinterpret_cast<const int2 *>(b + mp.chk);
-        const int2 *s_nz = reinterpret_cast<const int2 *>(b + mp.nz);
-        const CT *s_cod = reinterpret_cast<const CT *>(b + mp.cod);
-        const float4 *s_h = reinterpret_cast<const float4 *>(b + mp.xyz);
-        const float4 *s_l = s_h + h.n_nodes;
-        const double4 *s_x = reinterpret_cast<const double4 *>(b + mp.xyz);
         cp_async_wait_all();   // this thread's coordinate copies of tile t
         __syncthreads();       // everyone's
+        const bool more = t + 2 * G < n;
+        if (more) prefetch(t + 2 * G);
+        const vla::TileHdr h = s_item[s].h;
+        const StageMap mp = s_map[s];
+        const unsigned char *b = stage(s);
+        const int ty = type_of(s);
 
-        // phase 1: element records (index n_elems is the zero record used by padding)
-        for (int e = threadIdx.x; e <= h.n_elems; e += kThreads) {
-            T *dst = s_k + (size_t)e * C::RS;
-            if (e == h.n_elems) {
-                for (int u = 0; u < C::RS; ++u) dst[u] = T(0);
-                continue;
-            }
-            const ushort4 v = s_rec[e];
-            Geo<T> g;
-            if constexpr (MIX) {
-                if constexpr (DIM == 3) geo_mixed3_fast(s_h, s_l, v, g);
-                else geo_mixed2_fast(s_h, s_l, v, g);
-            } else {
-                geo_f64<DIM>(s_x, v, g);
-            }
-            const T c = coeff<T>(A.kind, ca, cb, g.xc, DIM);
-            const T adet = g.det < T(0) ? -g.det : g.det;
-            T sc;
-            if constexpr (MIX) sc = c * __frcp_rn(T(C::DFACT) * adet);   // K(a,b) = sc * C_a . C_b
-            else sc = c / (T(C::DFACT) * adet);
-            T mscale;
-            if constexpr (ORDER == 1) {
-                T rec[C::RS];
-#pragma unroll
-                for (int u = 0; u < C::RS; ++u) rec[u] = T(0);
-#pragma unroll
-                for (int a = 0; a < C::NV; ++a)
-#pragma unroll
-                    for (int q = a; q < C::NV; ++q) rec[a * C::NLB - a * (a - 1) / 2 + (q - a)] = sc * dot3<T>(g.C[a], g.C[q]);
-                mscale = c * adet * T(C::MOFF / C::DFACT);       // off-diagonal mass entry
-                rec[C::NU] = mscale;
-                if constexpr (MIX) {
-#pragma unroll
-                    for (int u = 0; u < C::RS; u += 4)
-                        *reinterpret_cast<float4 *>(dst + u) = make_float4(rec[u], rec[u + 1], rec[u + 2], rec[u + 3]);
-                } else {
-#pragma unroll
-                    for (int u = 0; u < C::RS; u += 2)
-                        *reinterpret_cast<double2 *>(dst + u) = make_double2(rec[u], rec[u + 1]);
-                }
-            } else {
-                T cd[10];
-#pragma unroll
-                for (int a = 0; a < C::NV; ++a)
-#pragma unroll
-                    for (int q = a; q < C::NV; ++q) cd[a * C::NV - a * (a - 1) / 2 + (q - a)] = dot3<T>(g.C[a], g.C[q]);
-                const P2Tab &tb = c_p2[DIM - 2];
-                for (int u = 0; u < C::NU; ++u) {
-                    T acc = 0;
-                    const int nt = tb.nterm[u];
-                    for (int q = 0; q < nt; ++q) {
-                        const T cf = MIX ? (T)tb.coef_f[u][q] : (T)tb.coef_d[u][q];
-                        acc += cf * cd[tb.st[u][q]];
-                    }
-                    dst[u] = sc * acc;
-                }
-                mscale = c * adet * T(1.0 / C::DFACT);           // c |T|; entries scale the reference mass
-                dst[C::NU] = mscale;
-            }
-            if (e < h.n_own) {
-                const int64_t k = s_gid[e];
-                if (g.det == T(0)) ++sing;
-                if (A.vol) {
-                    if constexpr (MIX) A.vol[k] = f32_to_f64(adet * (float)(1.0 / C::DFACT));
-                    else A.vol[k] = adet / C::DFACT;
-                }
-                if (A.Kp || A.Mp) {
-                    for (int a = 0; a < C::NLB; ++a)
-                        for (int q = 0; q < C::NLB; ++q) {
-                            const int p0 = a < q ? a : q, p1 = a < q ? q : a;
-                            const int u = p0 * C::NLB - p0 * (p0 - 1) / 2 + (p1 - p0);
-                            const int64_t pos = k * C::NLB * C::NLB + a + (int64_t)q * C::NLB;
-                            const T kv = dst[u];
-                            T mv;
-                            if constexpr (ORDER == 1) mv = mscale * (a == q ? T(2) : T(1));
-                            else mv = mscale * mhat[u];
-                            if constexpr (MIX) {
-                                if (A.Kp) A.Kp[pos] = f32_to_f64(kv);
-                                if (A.Mp) A.Mp[pos] = f32_to_f64(mv);
-                            } else {
-                                if (A.Kp) A.Kp[pos] = kv;
-                                if (A.Mp) A.Mp[pos] = mv;
-                            }
-                        }
-                }
-            }
-        }
+        by_type<TYPES>(ty, [&](auto D, auto O) {
+            constexpr int DIM = decltype(D)::value, ORDER = decltype(O)::value;
+            tile_elements<DIM, ORDER, MIX>(job_of(s), h, b, mp, s_k, mhat + (DIM == 3 ? 21 : 0));
+        });
         // prefetch: coordinates of the next tile (its bulk copies were issued two tiles ago)
-        const int tn = t + G;
-        if (tn < A.n_tiles) {
+        if (t + G < n) {
             if (__syncthreads_or(!mbar_wait_bounded(&bar[s ^ 1], (uint32_t)(((j + 1) >> 1) & 1), A.spin_limit))) {
                 bail();
                 return;
             }
-            gather(tn, s ^ 1);
+            gather(s ^ 1);
         } else {
             __syncthreads();
         }
-
-        // phase 2: pairs sorted by contribution count, 32 per warp-chunk,
-        // contributions in ascending element order
-        if (A.K || A.M) {
-            // chunks are handed out dynamically: they are sorted by width, so a
-            // static round-robin would give the first warps all the long ones
-            for (int c = warp;;) {
-                if (c >= h.n_chunks) break;
-                const int q = c * 32 + lane;
-                const int2 ch = s_chk[c];
-                const CT *cp = s_cod + ch.x + lane;
-                if constexpr (MIX) {
-                    unsigned long long h0 = 0ull, l0 = 0ull, h1 = 0ull, l1 = 0ull;   // (K, M) pairs, 2 chains
-                    int tt = 0;
-                    for (; tt + 1 < ch.y; tt += 2) {
-                        const uint32_t c0 = cp[tt * 32], c1 = cp[(tt + 1) * 32];
-                        const float *r0 = s_k + (c0 >> C::UB) * C::RS, *r1 = s_k + (c1 >> C::UB) * C::RS;
-                        float m0 = r0[C::NU], m1 = r1[C::NU];
-                        if constexpr (ORDER == 2) {
-                            m0 *= mhat[c0 & UMASK];
-                            m1 *= mhat[c1 & UMASK];
-                        }
-                        ff2_add(h0, l0, pk(r0[c0 & UMASK], m0));
-                        ff2_add(h1, l1, pk(r1[c1 & UMASK], m1));
-                    }
-                    if (tt < ch.y) {
-                        const uint32_t c0 = cp[tt * 32];
-                        const float *r0 = s_k + (c0 >> C::UB) * C::RS;
-                        float m0 = r0[C::NU];
-                        if constexpr (ORDER == 2) m0 *= mhat[c0 & UMASK];
-                        ff2_add(h0, l0, pk(r0[c0 & UMASK], m0));
-                    }
-                    if (q < h.n_nz) {
-                        ff2_add(h0, l0, h1);
-                        ff2_add(h0, l0, l1);
-                        // renormalise both sums at once: (hi, lo) <- TwoSum(hi, lo)
-                        const unsigned long long s2 = add2(h0, l0);
-                        const unsigned long long bb = sub2(s2, h0);
-                        const unsigned long long e2 = add2(sub2(h0, sub2(s2, bb)), sub2(l0, bb));
-                        float khi, mhi, klo, mlo;
-                        upk(s2, khi, mhi);
-                        upk(e2, klo, mlo);
-                        const int2 pos = s_nz[q];
-                        if (ORDER == 1 && pos.x == pos.y) {   // P1 diagonal mass: twice the off-diagonal scale
-                            mhi *= 2.f;
-                            mlo *= 2.f;
-                        }
-                        const double kd = ff_to_f64(khi, klo), md = ff_to_f64(mhi, mlo);
-                        if (A.K) {
-                            A.K[pos.x] = kd;
-                            if (pos.y != pos.x) A.K[pos.y] = kd;
-                        }
-                        if (A.M) {
-                            A.M[pos.x] = md;
-                            if (pos.y != pos.x) A.M[pos.y] = md;
-                        }
-                    }
-                } else {
-                    double ks = 0.0, ms = 0.0;
-                    for (int tt = 0; tt < ch.y; ++tt) {
-                        const uint32_t c0 = cp[tt * 32];
-                        const double *r0 = s_k + (c0 >> C::UB) * C::RS;
-                        ks += r0[c0 & UMASK];
-                        if constexpr (ORDER == 2) ms += r0[C::NU] * mhat[c0 & UMASK];
-                        else ms += r0[C::NU];
-                    }
-                    if (q < h.n_nz) {
-                        const int2 pos = s_nz[q];
-                        if (ORDER == 1 && pos.x == pos.y) ms *= 2.0;
-                        if (A.K) {
-                            A.K[pos.x] = ks;
-                            if (pos.y != pos.x) A.K[pos.y] = ks;
-                        }
-                        if (A.M) {
-                            A.M[pos.x] = ms;
-                            if (pos.y != pos.x) A.M[pos.y] = ms;
-                        }
-                    }
-                }
-                int nc = 0;
-                if (lane == 0) nc = atomicAdd(&next_chunk[j & 1], 1);
-                c = __shfl_sync(0xffffffffu, nc, 0);
-            }
+        const MeshJob &J = job_of(s);
+        if (J.K || J.M) {
+            by_type<TYPES>(ty, [&](auto D, auto O) {
+                constexpr int DIM = decltype(D)::value, ORDER = decltype(O)::value;
+                tile_pairs<DIM, ORDER, MIX>(J.K, J.M, h, b, mp, s_k, mhat + (DIM == 3 ? 21 : 0), &next_chunk[j & 1]);
+            });
         }
         if (threadIdx.x == 0) next_chunk[(j + 1) & 1] = kThreads / 32;   // reset for the next tile
-        __syncthreads();   // stage s and the element records are free
-        if (threadIdx.x == 0 && t + 2 * G < A.n_tiles) issue(t + 2 * G, s);
+        if (more) cp_async_wait_but1();   // the header fetch (the gather group may still be in flight)
+        __syncthreads();   // stage s, its job and the element records are free; the next header has landed
+        if (threadIdx.x == 0 && more) {
+            s_item[s] = s_item[2];
+            issue(s);
+        }
     }
-    if (A.n_sing && sing) atomicAdd(A.n_sing, sing);
 }
 
-template <int DIM, int ORDER, bool MIX>
-size_t asm_smem(const vla_mesh *m, int &stage_bytes) {
-    using C = Cfg<DIM, ORDER, MIX>;
-    stage_bytes = (int)((m->tile_stage_bytes + 32 * (size_t)m->max_tile_nodes + 16 + 15) / 16 * 16);
-    return 2 * (size_t)stage_bytes + ((size_t)m->max_tile_elems + 1) * C::RS * sizeof(typename C::T);
+// stage and record-area sizes of a mesh under a launch of precision MIX
+inline int mesh_stage_bytes(const vla_mesh *m) {
+    return (int)((m->tile_stage_bytes + 32 * (size_t)m->max_tile_nodes + 16 + 15) / 16 * 16);
+}
+inline size_t mesh_record_bytes(const vla_mesh *m, bool mix) {
+    const int nlb = m->nlb, nu = nlb * (nlb + 1) / 2, rs = (nu + 1 + 3) / 4 * 4;
+    return ((size_t)m->max_tile_elems + 1) * rs * (mix ? 4 : 8);
 }
 
-template <int DIM, int ORDER, bool MIX>
-vla_status launch_assemble(const vla_mesh *m, AsmArgs a, cudaStream_t st) {
-    int stage_bytes = 0;
-    const size_t smem = asm_smem<DIM, ORDER, MIX>(m, stage_bytes);
-    a.stage_bytes = stage_bytes;
+// Launch shape of an assembly kernel: grid = SMs x resident CTAs (capped by
+// the tuned residency and by the work items).  The kernel's dynamic shared
+// memory limit is raised to the device maximum once per device, so launches
+// (and graphs) of any size up to it stay valid.
+template <bool MIX, int TYPES, bool BATCH>
+vla_status kernel_shape(size_t smem, int ctas_per_sm, int n_work, int *grid) {
+    static std::mutex mu;
+    static bool ready[64] = {};
     int dev = 0, maxsm = 0, nsm = 0;
     VLA_CUDA(cudaGetDevice(&dev));
     VLA_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     VLA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    if (smem + 1024 > (size_t)maxsm)
-        return fail(VLA_ERR_UNSUPPORTED, "assembly tile needs %zu bytes of shared memory (limit %d)", smem, maxsm);
-    auto kern = k_assemble<DIM, ORDER, MIX>;
-    VLA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    auto kern = k_assemble<MIX, TYPES, BATCH>;
+    cudaFuncAttributes fa;
+    VLA_CUDA(cudaFuncGetAttributes(&fa, kern));
+    if (smem + fa.sharedSizeBytes > (size_t)maxsm)
+        return fail(VLA_ERR_UNSUPPORTED, "assembly tile needs %zu bytes of shared memory (limit %d)",
+                    smem + fa.sharedSizeBytes, maxsm);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (dev < 0 || dev >= 64 || !ready[dev]) {
+            VLA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          maxsm - (int)fa.sharedSizeBytes));
+            if (dev >= 0 && dev < 64) ready[dev] = true;
+        }
+    }
     int per_sm = 0;
     VLA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
     if (per_sm < 1) per_sm = 1;
-    int grid = nsm * per_sm;
-    if (grid > m->n_tiles) grid = m->n_tiles;
-    kern<<<grid, kThreads, smem, st>>>(a);
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    int g = nsm * per_sm;
+    if (g > n_work) g = n_work;
+    *grid = g;
+    return VLA_OK;
+}
+
+template <bool MIX, int TYPES, bool BATCH>
+vla_status launch_kernel(const LaunchArgs &a, size_t smem, int grid, cudaStream_t st) {
+    if (grid < 1) return VLA_OK;
+    k_assemble<MIX, TYPES, BATCH><<<grid, kThreads, smem, st>>>(a);
     VLA_CUDA(cudaGetLastError());
     return VLA_OK;
+}
+
+template <bool MIX, int TYPES>
+vla_status launch_single(const LaunchArgs &a, size_t smem, int ctas_per_sm, cudaStream_t st) {
+    int grid = 0;
+    TRY(kernel_shape<MIX, TYPES, false>(smem, ctas_per_sm, a.n_work, &grid));
+    return launch_kernel<MIX, TYPES, false>(a, smem, grid, st);
+}
+
+MeshJob make_job(const vla_mesh *m, int kind, double ca, double cb, double *K, double *M, double *vol, double *Kp,
+                 double *Mp, unsigned long long *ns) {
+    MeshJob j;
+    memset(&j, 0, sizeof(j));
+    j.tiles = m->tiles;
+    j.tile_nodes = m->tile_nodes;
+    j.tile_elem = m->tile_elem;
+    j.tile_own = m->tile_own;
+    j.tile_nzpos = m->tile_nzpos;
+    j.tile_chunks = m->tile_chunks;
+    j.codes = m->tile_codes;
+    j.xh = m->xh;
+    j.xl = m->xl;
+    j.coords = m->coords;
+    j.K = K;
+    j.M = M;
+    j.vol = vol;
+    j.Kp = Kp;
+    j.Mp = Mp;
+    j.n_sing = ns;
+    j.ca = ca;
+    j.cb = cb;
+    j.caf = (float)ca;
+    j.cbf = (float)cb;
+    j.kind = kind;
+    j.type = type_index(m->dim, m->order);
+    j.n_tiles = m->n_tiles;
+    return j;
 }
 
 // ---------------------------------------------------------------------------
@@ -950,6 +1142,41 @@ __global__ void k_simplex_normals(int64_t ne, int dim, int nlb, const double *__
     }
 }
 
+// ---------------------------------------------------------------------------
+// batched launches
+// ---------------------------------------------------------------------------
+// work item w of a batch: the tile w - work_base of the last job whose
+// work_base <= w, with the absolute sources of its staged segments
+__global__ void k_fill_work(const MeshJob *__restrict__ jobs, int count, int n_work, WorkItem *__restrict__ work) {
+    for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += gridDim.x * blockDim.x) {
+        int lo = 0, hi = count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].work_base <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        const MeshJob &J = jobs[lo];
+        WorkItem it;
+        it.h = J.tiles[w - J.work_base];
+        it.src[0] = J.tile_nodes + it.h.node_off;
+        it.src[1] = J.tile_elem + it.h.elem_off;
+        it.src[2] = J.tile_own + it.h.own_off;
+        it.src[3] = J.tile_chunks + it.h.chunk_off;
+        it.src[4] = J.tile_nzpos + it.h.nz_off;
+        it.src[5] = reinterpret_cast<const unsigned char *>(J.codes) + (size_t)code_bytes(J.type) * it.h.code_off;
+        it.job = jobs + lo;
+        it.type = J.type;
+        it.job_index = lo;
+        work[w] = it;
+    }
+}
+
+// replaces one job's coefficient and outputs, in stream order
+__global__ void k_set_job(MeshJob *dst, MeshJob j) {
+    j.work_base = dst->work_base;
+    *dst = j;
+}
+
 }  // namespace
 }  // namespace vla
 
@@ -970,44 +1197,273 @@ extern "C" vla_status vla_assemble(const vla_mesh *m, int32_t kind, double ca, d
     }
     unsigned long long *ns = reinterpret_cast<unsigned long long *>(n_singular);
     if (ns) VLA_CUDA(cudaMemsetAsync(ns, 0, sizeof(unsigned long long), st));
-    AsmArgs a;
-    a.tiles = m->tiles;
-    a.tile_nodes = m->tile_nodes;
-    a.tile_elem = m->tile_elem;
-    a.tile_own = m->tile_own;
-    a.tile_nzpos = m->tile_nzpos;
-    a.tile_chunks = m->tile_chunks;
-    a.codes = m->tile_codes;
-    a.xh = m->xh;
-    a.xl = m->xl;
-    a.coords = m->coords;
-    a.kind = kind;
-    a.ca = ca;
-    a.cb = cb;
-    a.K = K_vals;
-    a.M = M_vals;
-    a.vol = vol;
-    a.Kp = K_pages;
-    a.Mp = M_pages;
-    a.n_sing = ns;
+    const bool mix = precision == VLA_PREC_MIXED;
+    LaunchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.one = make_job(m, kind, ca, cb, K_vals, M_vals, vol, K_pages, M_pages, ns);
+    a.n_work = m->n_tiles;
     a.err = m->d_err;
     a.spin_limit = m->spin_limit;
-    a.n_tiles = m->n_tiles;
-    a.caf = (float)ca;
-    a.cbf = (float)cb;
-    a.stage_bytes = 0;
-    const bool mix = precision == VLA_PREC_MIXED;
-    const int key = (m->dim == 3 ? 4 : 0) + (m->order == 2 ? 2 : 0) + (mix ? 1 : 0);
-    switch (key) {
-    case 0: return launch_assemble<2, 1, false>(m, a, st);
-    case 1: return launch_assemble<2, 1, true>(m, a, st);
-    case 2: return launch_assemble<2, 2, false>(m, a, st);
-    case 3: return launch_assemble<2, 2, true>(m, a, st);
-    case 4: return launch_assemble<3, 1, false>(m, a, st);
-    case 5: return launch_assemble<3, 1, true>(m, a, st);
-    case 6: return launch_assemble<3, 2, false>(m, a, st);
-    default: return launch_assemble<3, 2, true>(m, a, st);
+    a.stage_bytes = mesh_stage_bytes(m);
+    const size_t smem = 2 * (size_t)a.stage_bytes + mesh_record_bytes(m, mix);
+    const int ty = type_index(m->dim, m->order);
+    const int cps = tuned_ctas(ty, mix);
+    switch (ty * 2 + (mix ? 1 : 0)) {
+    case 0: return launch_single<false, 1>(a, smem, cps, st);
+    case 1: return launch_single<true, 1>(a, smem, cps, st);
+    case 2: return launch_single<false, 2>(a, smem, cps, st);
+    case 3: return launch_single<true, 2>(a, smem, cps, st);
+    case 4: return launch_single<false, 4>(a, smem, cps, st);
+    case 5: return launch_single<true, 4>(a, smem, cps, st);
+    case 6: return launch_single<false, 8>(a, smem, cps, st);
+    default: return launch_single<true, 8>(a, smem, cps, st);
     }
+}
+
+// ---------------------------------------------------------------------------
+// batched assembly: many meshes of any element type in one persistent launch
+// ---------------------------------------------------------------------------
+struct vla_batch {
+    int32_t count = 0, precision = 0, flags = 0;
+    int32_t n_work = 0, grid = 0, ctas_per_sm = 0, stage_bytes = 0, spin_limit = 0;
+    size_t smem = 0;
+    bool async_mem = false;               // memory is stream-ordered on `stream` (one-shot batches)
+    cudaStream_t stream = nullptr;        // creation stream
+    void *block = nullptr;                // d_jobs | d_work | d_err
+    MeshJob *d_jobs = nullptr;
+    WorkItem *d_work = nullptr;
+    int *d_err = nullptr;
+    unsigned long long *n_sing = nullptr;  // caller's per-job singular counts (device), or NULL
+    std::vector<MeshJob> h_jobs;
+    std::vector<const vla_mesh *> meshes;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void batch_release(vla_batch *b) {
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->block) {
+        if (b->async_mem) cudaFreeAsync(b->block, b->stream);
+        else cudaFree(b->block);
+    }
+    delete b;
+}
+
+vla_status check_job(const vla_batch_job_t &j) {
+    if (!j.mesh) return fail(VLA_ERR_INVALID_ARG, "batch job without a mesh");
+    if (j.coeff_kind != VLA_COEFF_POLY && j.coeff_kind != VLA_COEFF_EXP)
+        return fail(VLA_ERR_INVALID_ARG, "unknown coefficient kind");
+    if (!std::isfinite(j.ca) || !std::isfinite(j.cb)) return fail(VLA_ERR_INVALID_ARG, "non-finite coefficient");
+    return VLA_OK;
+}
+
+// memset of the singular counts, then the persistent kernel (what a graph captures)
+vla_status batch_enqueue(vla_batch *b, cudaStream_t st) {
+    if (b->n_sing) VLA_CUDA(cudaMemsetAsync(b->n_sing, 0, sizeof(unsigned long long) * b->count, st));
+    LaunchArgs a;
+    memset(&a, 0, sizeof(a));
+    a.work = b->d_work;
+    a.n_work = b->n_work;
+    a.err = b->d_err;
+    a.spin_limit = b->spin_limit;
+    a.stage_bytes = b->stage_bytes;
+    if (b->precision == VLA_PREC_MIXED) return launch_kernel<true, 15, true>(a, b->smem, b->grid, st);
+    return launch_kernel<false, 15, true>(a, b->smem, b->grid, st);
+}
+
+vla_status batch_build(const vla_batch_job_t *jobs, int32_t count, int32_t precision, int64_t *n_singular,
+                       int32_t flags, cudaStream_t st, bool async_mem, vla_batch **out) {
+    if (!out) return fail(VLA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!jobs || count < 1) return fail(VLA_ERR_INVALID_ARG, "need count >= 1 jobs");
+    if (precision != VLA_PREC_FP64 && precision != VLA_PREC_MIXED)
+        return fail(VLA_ERR_INVALID_ARG, "precision must be VLA_PREC_FP64 or VLA_PREC_MIXED");
+    if (flags & ~VLA_BATCH_GRAPH) return fail(VLA_ERR_INVALID_ARG, "unknown batch flags");
+    if (async_mem && (flags & VLA_BATCH_GRAPH)) return fail(VLA_ERR_INVALID_ARG, "a one-shot batch has no graph");
+    const bool mix = precision == VLA_PREC_MIXED;
+    int64_t n_work = 0;
+    int stage_bytes = 0;
+    size_t rec_bytes = 0;
+    bool p2 = false;
+    int64_t te[4] = {0, 0, 0, 0};   // tile elements per type: the dominant type picks the residency
+    for (int i = 0; i < count; ++i) {
+        TRY(check_job(jobs[i]));
+        const vla_mesh *m = jobs[i].mesh;
+        n_work += m->n_tiles;
+        stage_bytes = std::max(stage_bytes, mesh_stage_bytes(m));
+        rec_bytes = std::max(rec_bytes, mesh_record_bytes(m, mix));
+        p2 = p2 || m->order == 2;
+        te[type_index(m->dim, m->order)] += m->tile_elems_total;
+    }
+    if (n_work > 0x7fffffffll) return fail(VLA_ERR_UNSUPPORTED, "more than 2^31-1 tiles in one batch");
+    if (p2) TRY(ensure_p2_tables());
+    const size_t smem = 2 * (size_t)stage_bytes + rec_bytes;
+    int dom = 0;
+    for (int t = 1; t < 4; ++t)
+        if (te[t] > te[dom]) dom = t;
+    const int cps = tuned_ctas(dom, mix);
+    int grid = 0;
+    if (mix) TRY(kernel_shape<true, 15, true>(smem, cps, (int)n_work, &grid));
+    else TRY(kernel_shape<false, 15, true>(smem, cps, (int)n_work, &grid));
+    vla_batch *b = new (std::nothrow) vla_batch();
+    if (!b) return fail(VLA_ERR_OOM, "host allocation failed");
+    b->count = count;
+    b->precision = precision;
+    b->flags = flags;
+    b->n_work = (int32_t)n_work;
+    b->stage_bytes = stage_bytes;
+    b->smem = smem;
+    b->grid = grid;
+    b->async_mem = async_mem;
+    b->stream = st;
+    b->spin_limit = jobs[0].mesh->spin_limit;
+    b->n_sing = reinterpret_cast<unsigned long long *>(n_singular);
+    b->ctas_per_sm = cps;
+    b->h_jobs.resize(count);
+    b->meshes.resize(count);
+    int32_t base = 0;
+    for (int i = 0; i < count; ++i) {
+        const vla_batch_job_t &j = jobs[i];
+        b->meshes[i] = j.mesh;
+        b->h_jobs[i] = make_job(j.mesh, j.coeff_kind, j.ca, j.cb, j.K_vals, j.M_vals, j.vol, j.K_pages, j.M_pages,
+                                b->n_sing ? b->n_sing + i : nullptr);
+        b->h_jobs[i].work_base = base;
+        base += j.mesh->n_tiles;
+    }
+    const size_t jb = (sizeof(MeshJob) * count + 255) / 256 * 256;
+    const size_t wb = (sizeof(WorkItem) * (size_t)n_work + 255) / 256 * 256;
+    cudaError_t e = async_mem ? cudaMallocAsync(&b->block, jb + wb + 256, st) : cudaMalloc(&b->block, jb + wb + 256);
+    if (e != cudaSuccess) {
+        b->block = nullptr;
+        batch_release(b);
+        return e == cudaErrorMemoryAllocation ? fail(VLA_ERR_OOM, "batch tables: out of device memory")
+                                              : cuda_fail(e, "batch tables");
+    }
+    b->d_jobs = reinterpret_cast<MeshJob *>(b->block);
+    b->d_work = reinterpret_cast<WorkItem *>(reinterpret_cast<unsigned char *>(b->block) + jb);
+    b->d_err = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(b->block) + jb + wb);
+    vla_status s = VLA_OK;
+    auto ck = [&](cudaError_t ce, const char *what) {
+        if (ce != cudaSuccess && s == VLA_OK) s = cuda_fail(ce, what);
+    };
+    ck(cudaMemcpyAsync(b->d_jobs, b->h_jobs.data(), sizeof(MeshJob) * count, cudaMemcpyHostToDevice, st), "batch jobs");
+    ck(cudaMemsetAsync(b->d_err, 0, sizeof(int), st), "batch error word");
+    if (s == VLA_OK) {
+        k_fill_work<<<grid_for(n_work, 256), 256, 0, st>>>(b->d_jobs, count, (int)n_work, b->d_work);
+        ck(cudaGetLastError(), "batch work list");
+    }
+    // the job table is copied from pageable host memory: finish before the vector can go away
+    if (s == VLA_OK && !async_mem) ck(cudaStreamSynchronize(st), "batch build");
+    if (s == VLA_OK && (flags & VLA_BATCH_GRAPH)) {
+        cudaStream_t cs = nullptr;
+        ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
+        if (s == VLA_OK) {
+            // kernel attributes and the grid were settled above, outside the capture
+            ck(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal), "begin capture");
+            if (s == VLA_OK) {
+                vla_status es = batch_enqueue(b, cs);
+                cudaGraph_t g = nullptr;
+                cudaError_t ee = cudaStreamEndCapture(cs, &g);
+                if (es != VLA_OK && s == VLA_OK) s = es;
+                ck(ee, "end capture");
+                b->graph = g;
+                if (s == VLA_OK) ck(cudaGraphInstantiate(&b->exec, b->graph, 0), "graph instantiate");
+            }
+            cudaStreamDestroy(cs);
+        }
+    }
+    if (s != VLA_OK) {
+        batch_release(b);
+        return s;
+    }
+    *out = b;
+    return VLA_OK;
+}
+
+}  // namespace
+
+extern "C" vla_status vla_batch_create(const vla_batch_job_t *jobs, int32_t count, int32_t precision,
+                                       int64_t *n_singular, int32_t flags, void *stream, vla_batch **out) {
+    return batch_build(jobs, count, precision, n_singular, flags, (cudaStream_t)stream, false, out);
+}
+
+extern "C" vla_status vla_batch_set_job(vla_batch *b, int32_t index, const vla_batch_job_t *job, void *stream) {
+    if (!b || !job) return fail(VLA_ERR_INVALID_ARG, "null batch or job");
+    if (index < 0 || index >= b->count) return fail(VLA_ERR_INVALID_ARG, "job index %d outside [0, %d)", index, b->count);
+    TRY(check_job(*job));
+    if (job->mesh != b->meshes[index]) return fail(VLA_ERR_INVALID_ARG, "a batch job keeps its mesh");
+    MeshJob j = make_job(job->mesh, job->coeff_kind, job->ca, job->cb, job->K_vals, job->M_vals, job->vol,
+                         job->K_pages, job->M_pages, b->n_sing ? b->n_sing + index : nullptr);
+    j.work_base = b->h_jobs[index].work_base;
+    b->h_jobs[index] = j;
+    k_set_job<<<1, 1, 0, (cudaStream_t)stream>>>(b->d_jobs + index, j);
+    VLA_CUDA(cudaGetLastError());
+    return VLA_OK;
+}
+
+extern "C" vla_status vla_batch_run(vla_batch *b, void *stream) {
+    if (!b) return fail(VLA_ERR_INVALID_ARG, "null batch");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (b->exec) {
+        VLA_CUDA(cudaGraphLaunch(b->exec, st));
+        return VLA_OK;
+    }
+    return batch_enqueue(b, st);
+}
+
+extern "C" vla_status vla_batch_info(const vla_batch *b, vla_batch_info_t *info) {
+    if (!b || !info) return fail(VLA_ERR_INVALID_ARG, "null batch or info");
+    memset(info, 0, sizeof(*info));
+    info->count = b->count;
+    info->n_work = b->n_work;
+    info->grid = b->grid;
+    info->ctas_per_sm = b->ctas_per_sm;
+    info->smem_bytes = (int64_t)b->smem;
+    info->graph = b->exec != nullptr;
+    for (const vla_mesh *m : b->meshes) {
+        info->elements += m->ne;
+        info->tile_elems += m->tile_elems_total;
+    }
+    return VLA_OK;
+}
+
+extern "C" vla_status vla_batch_check(vla_batch *b, void *stream) {
+    if (!b) return fail(VLA_ERR_INVALID_ARG, "null batch");
+    int h = 0;
+    VLA_CUDA(cudaMemcpyAsync(&h, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    VLA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (h) {
+        VLA_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), (cudaStream_t)stream));
+        return fail(VLA_ERR_TIMEOUT, "a bounded wait of the batched assembly expired (error word %d)", h);
+    }
+    return VLA_OK;
+}
+
+extern "C" vla_status vla_batch_destroy(vla_batch *b) {
+    if (!b) return VLA_OK;
+    batch_release(b);
+    return VLA_OK;
+}
+
+extern "C" vla_status vla_batch_assemble(const vla_batch_job_t *jobs, int32_t count, int32_t precision,
+                                         int64_t *n_singular, void *stream) {
+    vla_batch *b = nullptr;
+    cudaStream_t st = (cudaStream_t)stream;
+    TRY(batch_build(jobs, count, precision, n_singular, 0, st, true, &b));
+    vla_status s = batch_enqueue(b, st);
+    // stream-ordered free of the tables after the launch; the host side goes
+    // once the stream has passed the copy of the job table
+    if (b->block) cudaFreeAsync(b->block, st);
+    b->block = nullptr;
+    if (cudaLaunchHostFunc(st, [](void *p) { delete static_cast<vla_batch *>(p); }, b) != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        delete b;
+    }
+    return s;
 }
 
 extern "C" vla_status vla_boundary(const vla_mesh *m, int32_t precision, double *normals, double *areas,
@@ -1230,5 +1686,155 @@ extern "C" vla_status vla_element_pages_static(int32_t dim, int32_t order, int64
     default: launch_static_pages<3, 2, true>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
     }
     VLA_CUDA(cudaGetLastError());
+    return VLA_OK;
+}
+
+// ---------------------------------------------------------------------------
+// autotuner
+// ---------------------------------------------------------------------------
+namespace {
+
+int default_budget(int dim, int order) {   // the mesh builder's defaults
+    if (order == 1) return dim == 3 ? 800 : 2048;
+    return dim == 3 ? 384 : 1024;
+}
+
+struct TuneScratch {
+    double *K = nullptr, *M = nullptr, *vol = nullptr;
+    void *flush = nullptr;
+    size_t flush_bytes = 0;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~TuneScratch() {
+        cudaFree(K);
+        cudaFree(M);
+        cudaFree(vol);
+        cudaFree(flush);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
+// median microseconds of `reps` assemblies (L2 flushed before each)
+vla_status time_assembly(const vla_mesh *m, int precision, int reps, TuneScratch &S, cudaStream_t st, double *us) {
+    std::vector<float> t;
+    for (int r = -2; r < reps; ++r) {
+        if (S.flush) VLA_CUDA(cudaMemsetAsync(S.flush, r & 0xff, S.flush_bytes, st));
+        VLA_CUDA(cudaEventRecord(S.e0, st));
+        TRY(vla_assemble(m, VLA_COEFF_POLY, 1.0, 1.0, precision, S.K, S.M, S.vol, nullptr, nullptr, nullptr, st));
+        VLA_CUDA(cudaEventRecord(S.e1, st));
+        VLA_CUDA(cudaEventSynchronize(S.e1));
+        float ms = 0.f;
+        VLA_CUDA(cudaEventElapsedTime(&ms, S.e0, S.e1));
+        if (r >= 0) t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    *us = 1000.0 * t[t.size() / 2];
+    return VLA_OK;
+}
+
+}  // namespace
+
+extern "C" vla_status vla_autotune(int32_t dim, int32_t order, int32_t precision, int64_t nn, int64_t ne,
+                                   const double *coords, const int32_t *elems, int32_t reps, void *stream,
+                                   vla_tune_t *best) {
+    if (!best) return fail(VLA_ERR_INVALID_ARG, "best is NULL");
+    if (dim != 2 && dim != 3) return fail(VLA_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (order != VLA_P1 && order != VLA_P2) return fail(VLA_ERR_INVALID_ARG, "order must be VLA_P1 or VLA_P2");
+    if (precision != VLA_PREC_FP64 && precision != VLA_PREC_MIXED)
+        return fail(VLA_ERR_INVALID_ARG, "precision must be VLA_PREC_FP64 or VLA_PREC_MIXED");
+    if (reps < 1 || reps > 1000) return fail(VLA_ERR_INVALID_ARG, "reps must be in [1, 1000]");
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool mix = precision == VLA_PREC_MIXED;
+    const int ty = type_index(dim, order);
+    const int b0 = default_budget(dim, order);
+    const int prev_budget = tuned_budget(ty), prev_ctas = tuned_ctas(ty, mix);
+    TuneScratch S;
+    VLA_CUDA(cudaEventCreate(&S.e0));
+    VLA_CUDA(cudaEventCreate(&S.e1));
+    int dev = 0, l2 = 0;
+    VLA_CUDA(cudaGetDevice(&dev));
+    VLA_CUDA(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    S.flush_bytes = 2 * (size_t)l2;
+    if (cudaMalloc(&S.flush, S.flush_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        S.flush = nullptr;   // time warm instead
+    }
+    vla_tune_t win{0, 0, 1e300};
+    bool have = false;
+    // 1) tile budget at the occupancy-limited residency
+    const double scale[5] = {0.5, 0.75, 1.0, 1.25, 1.5};
+    for (double f : scale) {
+        const int B = std::max(64, (int)(b0 * f));
+        vla_mesh *m = nullptr;
+        TRY(mesh_create_budget(dim, order, nn, ne, coords, elems, 0, nullptr, st, B, &m));
+        vla_status s = VLA_OK;
+        if (!S.K) {
+            if (cudaMalloc(&S.K, 8 * (size_t)m->nnz) != cudaSuccess || cudaMalloc(&S.M, 8 * (size_t)m->nnz) != cudaSuccess ||
+                cudaMalloc(&S.vol, 8 * (size_t)ne) != cudaSuccess) {
+                cudaGetLastError();
+                s = fail(VLA_ERR_OOM, "autotune outputs: out of device memory");
+            }
+        }
+        double us = 0;
+        if (s == VLA_OK) {
+            set_tuned(ty, mix, prev_budget, 0);
+            s = time_assembly(m, precision, reps, S, st, &us);
+        }
+        vla_mesh_destroy(m);
+        if (s == VLA_ERR_UNSUPPORTED) continue;   // tile beyond shared memory
+        if (s != VLA_OK) {
+            set_tuned(ty, mix, prev_budget, prev_ctas);
+            return s;
+        }
+        if (us < win.us) {
+            win = vla_tune_t{B, 0, us};
+            have = true;
+        }
+    }
+    if (!have) {
+        set_tuned(ty, mix, prev_budget, prev_ctas);
+        return fail(VLA_ERR_UNSUPPORTED, "no candidate tile fits in shared memory");
+    }
+    // 2) residency at the best budget
+    vla_mesh *m = nullptr;
+    TRY(mesh_create_budget(dim, order, nn, ne, coords, elems, 0, nullptr, st, win.tile_budget, &m));
+    for (int c = 1; c <= 4; ++c) {
+        set_tuned(ty, mix, prev_budget, c);
+        double us = 0;
+        vla_status s = time_assembly(m, precision, reps, S, st, &us);
+        if (s != VLA_OK) {
+            vla_mesh_destroy(m);
+            set_tuned(ty, mix, prev_budget, prev_ctas);
+            return s;
+        }
+        if (us < win.us) win = vla_tune_t{win.tile_budget, c, us};
+    }
+    vla_mesh_destroy(m);
+    set_tuned(ty, mix, win.tile_budget, win.ctas_per_sm);
+    *best = win;
+    return VLA_OK;
+}
+
+extern "C" vla_status vla_tune_get(int32_t dim, int32_t order, int32_t precision, vla_tune_t *out) {
+    if (!out) return fail(VLA_ERR_INVALID_ARG, "out is NULL");
+    if ((dim != 2 && dim != 3) || (order != VLA_P1 && order != VLA_P2) ||
+        (precision != VLA_PREC_FP64 && precision != VLA_PREC_MIXED))
+        return fail(VLA_ERR_INVALID_ARG, "unknown element type or precision");
+    const int ty = type_index(dim, order);
+    out->tile_budget = tuned_budget(ty);
+    out->ctas_per_sm = tuned_ctas(ty, precision == VLA_PREC_MIXED);
+    out->us = 0.0;
+    return VLA_OK;
+}
+
+extern "C" vla_status vla_tune_set(int32_t dim, int32_t order, int32_t precision, const vla_tune_t *in) {
+    if (!in) return fail(VLA_ERR_INVALID_ARG, "in is NULL");
+    if ((dim != 2 && dim != 3) || (order != VLA_P1 && order != VLA_P2) ||
+        (precision != VLA_PREC_FP64 && precision != VLA_PREC_MIXED))
+        return fail(VLA_ERR_INVALID_ARG, "unknown element type or precision");
+    if (in->tile_budget < 0 || in->tile_budget > (1 << 16) || in->ctas_per_sm < 0 || in->ctas_per_sm > 32)
+        return fail(VLA_ERR_INVALID_ARG, "tile_budget must be in [0, 65536] and ctas_per_sm in [0, 32]");
+    if (in->tile_budget > 0 && in->tile_budget < 64) return fail(VLA_ERR_INVALID_ARG, "tile_budget below 64");
+    set_tuned(type_index(dim, order), precision == VLA_PREC_MIXED, in->tile_budget, in->ctas_per_sm);
     return VLA_OK;
 }

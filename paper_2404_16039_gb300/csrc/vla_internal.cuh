@@ -19,6 +19,26 @@ void set_error(const char *fmt, ...);
 vla_status fail(vla_status st, const char *fmt, ...);
 vla_status cuda_fail(cudaError_t e, const char *what);
 
+// Launch parameters chosen by the autotuner (process-wide, all devices), per
+// element type (dim - 2) * 2 + (order - 1): the incidence budget of a row
+// tile used when a mesh is built, and the resident CTAs per SM of the
+// assembly launch per precision.  0 means the library default.
+int tuned_budget(int type);
+int tuned_ctas(int type, bool mix);
+void set_tuned(int type, bool mix, int budget, int ctas);
+
+// vla_mesh_create with an explicit tile budget (0: tuned or default)
+vla_status mesh_create_budget(int32_t dim, int32_t order, int64_t nn, int64_t ne, const double *coords,
+                              const int32_t *elems, int64_t nfb, const int32_t *faces, void *stream, int budget,
+                              vla_mesh **out);
+
+// returns the status of a library call that failed
+#define TRY(...)                      \
+    do {                              \
+        vla_status s_ = (__VA_ARGS__); \
+        if (s_ != VLA_OK) return s_;  \
+    } while (0)
+
 #define VLA_CUDA(call)                                              \
     do {                                                            \
         cudaError_t e_ = (call);                                    \

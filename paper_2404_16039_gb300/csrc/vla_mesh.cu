@@ -749,11 +749,6 @@ struct Scratch {  // temporary device buffers freed at the end of the build
     }
 };
 
-#define TRY(x)                    \
-    do {                          \
-        vla_status s_ = (x);      \
-        if (s_ != VLA_OK) return s_; \
-    } while (0)
 
 // incidence budget of a tile (sum over its rows of 1 + incident elements)
 int tile_budget(int dim, int order) {
@@ -896,8 +891,11 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     VLA_CUDA(cudaGetLastError());
 
     // ---- tiles: consecutive ranks, incidence-weight budget B
-    int B = tile_budget(dim, m->order);
-    if (const char *tb = getenv("VLA_TILE_BUDGET")) B = std::max(64, atoi(tb));   // tuning override
+    // budget: the caller's (autotuner candidates), else the tuned one, else the default;
+    // VLA_TILE_BUDGET overrides all three (experiments)
+    int B = m->tile_budget > 0 ? m->tile_budget : tuned_budget((dim - 2) * 2 + (m->order - 1));
+    if (B <= 0) B = tile_budget(dim, m->order);
+    if (const char *tb = getenv("VLA_TILE_BUDGET")) B = std::max(64, atoi(tb));
     m->tile_budget = B;
     int32_t *w, *flag, *tile_begin, *node_tile;
     long long *fpre;
@@ -1075,9 +1073,10 @@ vla_status mesh_build(vla_mesh *m, const double *coords, const int32_t *elems, c
 
 using namespace vla;
 
-extern "C" vla_status vla_mesh_create(int32_t dim, int32_t order, int64_t nn, int64_t ne, const double *coords,
-                                      const int32_t *elems, int64_t nfb, const int32_t *faces, void *stream,
-                                      vla_mesh **out) {
+namespace vla {
+vla_status mesh_create_budget(int32_t dim, int32_t order, int64_t nn, int64_t ne, const double *coords,
+                              const int32_t *elems, int64_t nfb, const int32_t *faces, void *stream, int budget,
+                              vla_mesh **out) {
     if (!out) return fail(VLA_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (dim != 2 && dim != 3) return fail(VLA_ERR_INVALID_ARG, "dim must be 2 or 3");
@@ -1095,6 +1094,7 @@ extern "C" vla_status vla_mesh_create(int32_t dim, int32_t order, int64_t nn, in
     m->ne = ne;
     m->nfb = nfb;
     m->stream = (cudaStream_t)stream;
+    m->tile_budget = budget;
     vla_status s = mesh_build(m, coords, elems, faces);
     if (s != VLA_OK) {
         char keep[512];
@@ -1111,6 +1111,13 @@ extern "C" vla_status vla_mesh_create(int32_t dim, int32_t order, int64_t nn, in
     *out = m;
     return VLA_OK;
 }
+}  // namespace vla
+
+extern "C" vla_status vla_mesh_create(int32_t dim, int32_t order, int64_t nn, int64_t ne, const double *coords,
+                                      const int32_t *elems, int64_t nfb, const int32_t *faces, void *stream,
+                                      vla_mesh **out) {
+    return vla::mesh_create_budget(dim, order, nn, ne, coords, elems, nfb, faces, stream, 0, out);
+}
 
 extern "C" vla_status vla_mesh_destroy(vla_mesh *m) {
     if (!m) return VLA_OK;
@@ -1118,6 +1125,20 @@ extern "C" vla_status vla_mesh_destroy(vla_mesh *m) {
     for (void *p : m->allocs) cudaFreeAsync(p, m->stream);
     cudaStreamSynchronize(m->stream);
     delete m;
+    return VLA_OK;
+}
+
+extern "C" vla_status vla_mesh_check(vla_mesh *m, void *stream) {
+    if (!m) return fail(VLA_ERR_INVALID_ARG, "null mesh");
+    cudaStream_t st = (cudaStream_t)stream;
+    int h = 0;
+    VLA_CUDA(cudaMemcpyAsync(&h, m->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VLA_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        VLA_CUDA(cudaMemsetAsync(m->d_err, 0, sizeof(int), st));
+        VLA_CUDA(cudaStreamSynchronize(st));
+        return fail(VLA_ERR_TIMEOUT, "a bounded wait of a kernel on this mesh expired (error word %d)", h);
+    }
     return VLA_OK;
 }
 

@@ -1,0 +1,212 @@
+"""GPU: batched assembly of many meshes in one persistent launch, the
+autotuner, and the device error word of bounded waits.
+
+Every batch job must be bit-identical to vla_assemble on its mesh alone (the
+summation order of each CSR value and page entry depends only on the mesh),
+and the single-mesh path is itself checked against the FP64 oracle in
+test_gpu_parity.py; small jobs are also compared with the oracle directly.
+"""
+import numpy as np
+import pytest
+import torch
+
+import meshgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL_MIX = 1e-5
+
+
+@pytest.fixture(scope="module")
+def vla():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2404_16039_gb300 as v
+    v.lib()
+    return v
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _gpu_mesh(vla, m):
+    return vla.Mesh(_dev(m.coords), _dev(m.elems), _dev(m.faces) if m.nfb else None, order=m.order)
+
+
+def _rel_fro(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+# a mix of every element type and of tile counts from 1 to many
+MIX_SPECS = [(2, 1, 3), (3, 2, 2), (3, 1, 9), (2, 2, 11), (3, 1, 1), (2, 1, 40), (3, 2, 4), (2, 2, 2),
+             (3, 1, 14), (2, 1, 7), (3, 2, 1), (2, 2, 23)]
+
+
+def _mix(vla, specs, seed0=0):
+    meshes, gms = [], []
+    for q, (dim, order, n) in enumerate(specs):
+        m = meshgen.make_mesh(dim, n, order=order, jitter=0.1, seed=seed0 + q)
+        meshes.append(m)
+        gms.append(_gpu_mesh(vla, m))
+    return meshes, gms
+
+
+def _coeffs(q):
+    return (0 if q % 3 else 1), 0.5 + 0.25 * (q % 5), 0.1 * (q % 4)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("graph", [False, True])
+def test_batch_bit_identical_to_single(vla, precision, graph):
+    meshes, gms = _mix(vla, MIX_SPECS)
+    jobs = []
+    for q, gm in enumerate(gms):
+        kind, ca, cb = _coeffs(q)
+        jobs.append((gm, gm.outputs(pages=(q % 4 == 1)), kind, ca, cb))
+    b = vla.Batch(jobs, precision=precision, graph=graph, count_singular=True)
+    assert b.count == len(jobs) and b.graph == graph
+    assert b.n_work == sum(gm.n_tiles for gm in gms)
+    assert b.elements == sum(m.ne for m in meshes)
+    for rep in range(2):   # a second run (graph replay) gives the same bits
+        b.run()
+        torch.cuda.synchronize()
+        for q, gm in enumerate(gms):
+            kind, ca, cb = _coeffs(q)
+            ref = gm.assemble(ca, cb, kind=kind, precision=precision, pages=(q % 4 == 1))
+            got = b.outs[q]
+            for key in ("K", "M", "vol") + (("K3D", "M3D") if q % 4 == 1 else ()):
+                assert torch.equal(got[key], ref[key]), (q, key, rep)
+    assert int(b.n_singular.abs().sum().item()) == 0
+    b.check()
+    b.close()
+
+
+def test_batch_against_oracle(vla):
+    specs = [(2, 1, 6), (2, 2, 5), (3, 1, 4), (3, 2, 2)]
+    meshes, gms = _mix(vla, specs, seed0=40)
+    for precision, tol in ((0, None), (1, TOL_MIX)):
+        jobs = [(gm, gm.outputs(pages=True), 0, 1.0, 1.0) for gm in gms]
+        vla.Batch(jobs, precision=precision).run()
+        torch.cuda.synchronize()
+        for (m, (_, out, *_)) in zip(meshes, jobs):
+            ref = oracle.assemble(m.dim, m.order, m.nn, m.elems, m.coords, 1.0, 1.0, want_pages=True)
+            for key, rk in (("K", "K"), ("M", "M"), ("vol", "vol"), ("K3D", "K3D"), ("M3D", "M3D")):
+                got = out[key].cpu().numpy()
+                if tol is None:
+                    scale = np.abs(ref[rk]).max()
+                    assert np.abs(got - ref[rk]).max() <= TOL64 * scale, key
+                else:
+                    assert _rel_fro(got, ref[rk]) <= tol, key
+
+
+def test_batch_set_job_and_one_shot(vla):
+    meshes, gms = _mix(vla, MIX_SPECS[:6], seed0=7)
+    jobs = [(gm, gm.outputs(), 0, 1.0, 0.0) for gm in gms]
+    b = vla.Batch(jobs, precision=1, graph=True)
+    b.run()
+    # new coefficient and new outputs for job 2, same mesh, stream ordered
+    fresh = gms[2].outputs()
+    b.set_job(2, fresh, kind=0, ca=1.7, cb=0.6)
+    b.run()
+    torch.cuda.synchronize()
+    ref = gms[2].assemble(1.7, 0.6, precision=1)
+    assert torch.equal(fresh["K"], ref["K"]) and torch.equal(fresh["M"], ref["M"])
+    ref0 = gms[0].assemble(1.0, 0.0, precision=1)
+    assert torch.equal(b.outs[0]["K"], ref0["K"])
+    # one-shot batch (stream-ordered tables)
+    outs = vla.batch_assemble([(gm, gm.outputs(), 1, 1.0, 0.5) for gm in gms], precision=1)
+    torch.cuda.synchronize()
+    for gm, o in zip(gms, outs):
+        r = gm.assemble(1.0, 0.5, kind=1, precision=1)
+        assert torch.equal(o["K"], r["K"]) and torch.equal(o["vol"], r["vol"])
+    with pytest.raises(vla.VlaError):
+        b.set_job(0, gms[0].outputs(), kind=7)   # unknown coefficient kind
+    b.close()
+
+
+def test_batch_singular_counts_per_job(vla):
+    coords = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0], [0, 0, 1]], dtype=np.float64)
+    flat = vla.Mesh(_dev(coords), _dev(np.array([[0, 1, 2, 4], [0, 1, 2, 3]], dtype=np.int32)))
+    good = _gpu_mesh(vla, meshgen.kuhn_cube(2, seed=1))
+    b = vla.Batch([(good, good.outputs(), 0, 1.0, 0.0), (flat, flat.outputs(), 0, 1.0, 0.0)],
+                  precision=0, count_singular=True)
+    b.run()
+    torch.cuda.synchronize()
+    assert b.n_singular.cpu().tolist() == [0, 1]
+    b.run()   # counts are reset by every run
+    torch.cuda.synchronize()
+    assert b.n_singular.cpu().tolist() == [0, 1]
+
+
+def test_batch_uneven_config_scaled(vla):
+    # the uneven mix of the batched workload (2-D/3-D x P1/P2, log-uniform sizes),
+    # 32 meshes of 1e3..1e5 elements: every job bit-identical to its single assembly
+    specs = meshgen.batch_specs(32, lo=1e3, hi=1e5, seed=3)
+    gms = [_gpu_mesh(vla, meshgen.make_mesh(s["dim"], s["n"], order=s["order"], seed=s["seed"])) for s in specs]
+    jobs = [(gm, gm.outputs(), 0, 1.0, 1.0) for gm in gms]
+    b = vla.Batch(jobs, precision=1, graph=True)
+    b.run()
+    torch.cuda.synchronize()
+    for gm, (_, out, *_) in zip(gms, jobs):
+        ref = gm.assemble(1.0, 1.0, precision=1)
+        assert torch.equal(out["K"], ref["K"]) and torch.equal(out["M"], ref["M"])
+    b.check()
+
+
+def test_tile_budget_does_not_change_results(vla):
+    m = meshgen.kuhn_cube(10, seed=2)
+    ref = None
+    try:
+        for budget in (64, 200, 800, 1200):
+            vla.tune_set(3, 1, 1, tile_budget=budget, ctas_per_sm=1 + budget % 3)
+            gm = _gpu_mesh(vla, m)
+            out = gm.assemble(1.0, 1.0, precision=1)
+            if ref is None:
+                ref = out
+                n_tiles = gm.n_tiles
+            else:
+                assert torch.equal(out["K"], ref["K"]) and torch.equal(out["M"], ref["M"])
+                assert torch.equal(out["vol"], ref["vol"])
+        assert gm.n_tiles < n_tiles
+    finally:
+        vla.tune_set(3, 1, 1, tile_budget=0, ctas_per_sm=0)
+
+
+def test_autotune_picks_a_candidate(vla):
+    m = meshgen.kuhn_cube(16, seed=0)
+    try:
+        budget, ctas, us = vla.autotune(_dev(m.coords), _dev(m.elems), order=1, precision=1, reps=3)
+        assert budget in (400, 600, 800, 1000, 1200)
+        assert ctas in (0, 1, 2, 3, 4)
+        assert us > 0
+        assert vla.tune_get(3, 1, 1) == (budget, ctas)
+        gm = _gpu_mesh(vla, m)   # built with the tuned budget
+        out = gm.assemble(1.0, 1.0, precision=1)
+        ref = oracle.assemble(3, 1, m.nn, m.elems, m.coords, 1.0, 1.0)
+        assert _rel_fro(out["K"].cpu().numpy(), ref["K"]) <= TOL_MIX
+    finally:
+        vla.tune_set(3, 1, 1, tile_budget=0, ctas_per_sm=0)
+
+
+def test_bounded_wait_expiry_is_reported(vla, monkeypatch):
+    # a mesh whose kernels may not wait at all: the first wait on a bulk copy
+    # runs out, the kernel records it in the error word and returns; the host
+    # reads VLA_ERR_TIMEOUT and the context stays usable
+    m = meshgen.kuhn_cube(6, seed=5)
+    monkeypatch.setenv("VLA_DEBUG_SPIN_LIMIT", "0")
+    gm = _gpu_mesh(vla, m)
+    monkeypatch.delenv("VLA_DEBUG_SPIN_LIMIT")
+    gm.assemble(1.0, 0.0, precision=1)
+    with pytest.raises(vla.VlaError) as e:
+        gm.check()
+    assert e.value.status == -5
+    gm.check()   # cleared
+    good = _gpu_mesh(vla, m)
+    out = good.assemble(1.0, 0.0, precision=1)
+    good.check()
+    ref = oracle.assemble(3, 1, m.nn, m.elems, m.coords, 1.0, 0.0)
+    assert _rel_fro(out["K"].cpu().numpy(), ref["K"]) <= TOL_MIX
