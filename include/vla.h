@@ -50,6 +50,7 @@ typedef int32_t vla_status;
 enum {
     VLA_OK = 0,
     VLA_WARN_SINGULAR = 1,     /* some pages/elements had det == 0 (IEEE inf/nan in their outputs) */
+    VLA_PENDING = 2,           /* a server request is not finished yet (vla_server_poll) */
     VLA_ERR_INVALID_ARG = -1,  /* bad size, null pointer, unsupported shape or flag */
     VLA_ERR_INDEX_OOB = -2,    /* an element or facet references a node outside [0, nn) */
     VLA_ERR_OOM = -3,          /* device allocation failed */
@@ -327,6 +328,86 @@ vla_status vla_autotune(int32_t dim, int32_t order, int32_t precision, int64_t n
  * (us is ignored by vla_tune_set and 0 from vla_tune_get). */
 vla_status vla_tune_get(int32_t dim, int32_t order, int32_t precision, vla_tune_t *out);
 vla_status vla_tune_set(int32_t dim, int32_t order, int32_t precision, const vla_tune_t *in);
+
+/* ------------------------------------------------------------------------ */
+/* Assembly server: continuous batching over a device-memory budget          */
+/* ------------------------------------------------------------------------ */
+/* The paper has no server; this is the serving form of its assembly.  A
+ * request carries a mesh (arrays plus a client key) and a coefficient and
+ * returns K, M (in the mesh's CSR pattern) and vol, computed exactly as
+ * vla_assemble computes them (bit-identical whatever else runs at the same
+ * time).  Requests are admitted in arrival order while the memory they need
+ * (the mesh handle, estimated until built, and the outputs) fits the budget;
+ * idle resident meshes are evicted least recently used first to make room,
+ * and a request that could never fit fails with VLA_ERR_BUDGET.  Ingest
+ * threads build admitted meshes on their own streams while earlier requests
+ * assemble; each scheduling step assembles every request whose mesh is ready
+ * in ONE batched persistent launch, so requests that arrive while a launch
+ * runs join the next one.  All calls are thread-safe. */
+
+typedef struct vla_server vla_server;
+
+typedef struct {
+    int64_t hbm_budget_bytes;  /* device bytes the server may hold (meshes + outputs) */
+    int32_t precision;         /* VLA_PREC_MIXED or VLA_PREC_FP64 for every request */
+    int32_t ingest_workers;    /* host threads building meshes (0 = 4) */
+    int32_t max_batch;         /* requests per launch at most (0 = no limit) */
+    int32_t max_inflight;      /* admitted, unfinished requests at most (0 = no limit) */
+} vla_server_config_t;
+
+typedef struct {
+    int64_t key;               /* >= 0: mesh identity; a request whose key names a mesh the
+                                  server holds reuses it (the arrays are then not read).
+                                  -1: a private mesh. */
+    int32_t dim, order;
+    int64_t nn, ne, nfb;
+    const double *coords;      /* host or device; layouts as vla_mesh_create; read by the */
+    const int32_t *elems;      /* ingest, so valid until the request is finished */
+    const int32_t *faces;      /* or NULL (nfb 0) */
+    int32_t keep_resident;     /* keep the mesh on the device under its key afterwards */
+    int32_t coeff_kind;        /* as in vla_assemble */
+    double ca, cb;
+} vla_request_t;
+
+typedef struct {
+    int32_t status;            /* VLA_OK or the request's error */
+    int32_t new_mesh;          /* 1 if this request built its mesh */
+    int32_t batch_size;        /* requests in the launch that computed it */
+    int32_t reserved;
+    int64_t batch_id;
+    int64_t nn, ne, nnz;
+    const double *K_vals, *M_vals, *vol;   /* device; valid until vla_server_release */
+    const int32_t *row_ptr, *col_idx;      /* device CSR pattern of the mesh; same lifetime */
+    double t_submit, t_admit, t_ready, t_start, t_done;   /* CLOCK_MONOTONIC seconds */
+} vla_result_t;
+
+typedef struct {
+    int64_t budget_bytes, used_bytes, peak_bytes;
+    int64_t n_done, n_failed, n_batches, n_ingested, n_reused, n_evicted, n_resident, n_queued, max_batch;
+    double mean_batch;         /* requests per launch */
+    double assembly_busy_s;    /* time with a launch in flight */
+} vla_server_stats_t;
+
+/* Starts the scheduler and ingest threads on the current device. */
+vla_status vla_server_create(const vla_server_config_t *cfg, vla_server **out);
+
+/* Queues a request; *ticket identifies it.  Never blocks on the GPU. */
+vla_status vla_server_submit(vla_server *server, const vla_request_t *req, int64_t *ticket);
+
+/* Waits up to timeout_s seconds (0: no wait) for the request: VLA_PENDING
+ * while it runs, VLA_OK with *res filled when done, the request's error if
+ * it failed (*res filled too). */
+vla_status vla_server_poll(vla_server *server, int64_t ticket, double timeout_s, vla_result_t *res);
+
+/* Frees a finished request's outputs (and its mesh, unless resident). */
+vla_status vla_server_release(vla_server *server, int64_t ticket);
+
+/* Fills *stats (host struct). */
+vla_status vla_server_stats(vla_server *server, vla_server_stats_t *stats);
+
+/* Finishes admitted requests, drops queued ones, joins the threads and
+ * frees everything. */
+vla_status vla_server_destroy(vla_server *server);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,7 @@ import torch
 
 __all__ = [
     "VlaError", "lib", "version", "amtam", "astam", "avtam", "amdet", "aminv", "Mesh", "element_pages_static",
-    "Batch", "batch_assemble", "autotune", "tune_get", "tune_set", "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP",
+    "Batch", "batch_assemble", "autotune", "tune_get", "tune_set", "Server", "PENDING", "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP",
 ]
 
 F32, F64 = 0, 1
@@ -64,7 +64,35 @@ class Tune(C.Structure):
     _fields_ = [("tile_budget", C.c_int32), ("ctas_per_sm", C.c_int32), ("us", C.c_double)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("precision", C.c_int32), ("ingest_workers", C.c_int32),
+                ("max_batch", C.c_int32), ("max_inflight", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("key", C.c_int64), ("dim", C.c_int32), ("order", C.c_int32), ("nn", C.c_int64),
+                ("ne", C.c_int64), ("nfb", C.c_int64), ("coords", C.c_void_p), ("elems", C.c_void_p),
+                ("faces", C.c_void_p), ("keep_resident", C.c_int32), ("coeff_kind", C.c_int32),
+                ("ca", C.c_double), ("cb", C.c_double)]
+
+
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("new_mesh", C.c_int32), ("batch_size", C.c_int32),
+                ("reserved", C.c_int32), ("batch_id", C.c_int64), ("nn", C.c_int64), ("ne", C.c_int64),
+                ("nnz", C.c_int64), ("K_vals", C.c_void_p), ("M_vals", C.c_void_p), ("vol", C.c_void_p),
+                ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("t_submit", C.c_double),
+                ("t_admit", C.c_double), ("t_ready", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [(k, C.c_int64) for k in ("budget_bytes", "used_bytes", "peak_bytes", "n_done", "n_failed",
+                                         "n_batches", "n_ingested", "n_reused", "n_evicted", "n_resident",
+                                         "n_queued", "max_batch")] + [("mean_batch", C.c_double),
+                                                                      ("assembly_busy_s", C.c_double)]
+
+
 BATCH_GRAPH = 1
+PENDING = 2
 
 
 def lib():
@@ -105,11 +133,19 @@ def lib():
         L.vla_autotune.argtypes = [i32, i32, i32, i64, i64, vp, vp, i32, vp, C.POINTER(Tune)]
         L.vla_tune_get.argtypes = [i32, i32, i32, C.POINTER(Tune)]
         L.vla_tune_set.argtypes = [i32, i32, i32, C.POINTER(Tune)]
+        L.vla_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(vp)]
+        L.vla_server_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(i64)]
+        L.vla_server_poll.argtypes = [vp, i64, dbl, C.POINTER(Result)]
+        L.vla_server_release.argtypes = [vp, i64]
+        L.vla_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
+        L.vla_server_destroy.argtypes = [vp]
         for name in ("vla_amtam", "vla_astam", "vla_avtam", "vla_amdet", "vla_aminv", "vla_mesh_create",
                      "vla_mesh_info", "vla_mesh_csr", "vla_assemble", "vla_boundary", "vla_simplex_normals",
                      "vla_mesh_destroy", "vla_element_pages_static", "vla_mesh_check", "vla_batch_create",
                      "vla_batch_set_job", "vla_batch_run", "vla_batch_info", "vla_batch_check", "vla_batch_destroy",
-                     "vla_batch_assemble", "vla_autotune", "vla_tune_get", "vla_tune_set"):
+                     "vla_batch_assemble", "vla_autotune", "vla_tune_get", "vla_tune_set", "vla_server_create",
+                     "vla_server_submit", "vla_server_poll", "vla_server_release", "vla_server_stats",
+                     "vla_server_destroy"):
             getattr(L, name).restype = i32
         _lib = L
         return L
@@ -448,3 +484,111 @@ def tune_get(dim, order, precision=PREC_MIXED):
 def tune_set(dim, order, precision=PREC_MIXED, tile_budget=0, ctas_per_sm=0):
     t = Tune(tile_budget, ctas_per_sm, 0.0)
     _check(lib().vla_tune_set(dim, order, precision, C.byref(t)))
+
+
+# ---------------------------------------------------------------------------
+# assembly server
+# ---------------------------------------------------------------------------
+
+class _DevView:
+    """A device array given by pointer, seen by torch through the CUDA array interface."""
+
+    def __init__(self, ptr, n, typestr):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr, "data": (int(ptr or 0), False),
+                                         "version": 2}
+
+
+def _view(ptr, n, typestr, device):
+    if n == 0:
+        return torch.empty(0, dtype=torch.float64 if typestr == "<f8" else torch.int32, device=device)
+    return torch.as_tensor(_DevView(ptr, n, typestr), device=device)
+
+
+class Server:
+    """Continuous-batching assembly server (vla_server_*).
+
+    submit() takes host (numpy) or device (torch) mesh arrays, coords (nn, dim)
+    float64 and elems (ne, nlb) int32, and returns a ticket; poll() returns
+    None while the request runs, else its result record; result() copies K,
+    M, vol (and the CSR pattern) into fresh tensors; release() frees the
+    server's copies."""
+
+    def __init__(self, budget_bytes, precision=PREC_MIXED, ingest_workers=4, max_batch=0, max_inflight=0):
+        cfg = ServerConfig(int(budget_bytes), precision, ingest_workers, max_batch, max_inflight)
+        h = C.c_void_p()
+        _check(lib().vla_server_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._keep = {}
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    @staticmethod
+    def _ptr(a, dtype):
+        if isinstance(a, torch.Tensor):
+            _req(a, dtype)
+            return a, a.data_ptr()
+        import numpy as np
+        a = np.ascontiguousarray(a, dtype={torch.float64: np.float64, torch.int32: np.int32}[dtype])
+        return a, a.ctypes.data
+
+    def submit(self, coords, elems, order=1, key=-1, keep_resident=True, kind=COEFF_POLY, ca=1.0, cb=0.0,
+               faces=None):
+        c, cp = self._ptr(coords, torch.float64)
+        e, ep = self._ptr(elems, torch.int32)
+        f, fp = (None, None) if faces is None else self._ptr(faces, torch.int32)
+        nn, dim = c.shape
+        ne = e.shape[0]
+        nfb = 0 if f is None else f.shape[0]
+        r = Request(int(key), dim, order, nn, ne, nfb, cp, ep, fp, 1 if keep_resident else 0, kind,
+                    float(ca), float(cb))
+        t = C.c_int64()
+        _check(lib().vla_server_submit(self._h, C.byref(r), C.byref(t)))
+        self._keep[t.value] = (c, e, f)
+        return t.value
+
+    def poll(self, ticket, timeout=0.0):
+        res = Result()
+        st = lib().vla_server_poll(self._h, int(ticket), float(timeout), C.byref(res))
+        if st == PENDING:
+            return None
+        self._keep.pop(ticket, None)
+        if st < 0 and res.status == 0:
+            _check(st)
+        return res
+
+    def result(self, ticket, res=None, pattern=False):
+        """K, M, vol (and row_ptr, col_idx) of a finished request as new tensors."""
+        if res is None:
+            res = self.poll(ticket)
+            if res is None:
+                raise RuntimeError("request not finished")
+        if res.status < 0:
+            raise VlaError(res.status, f"request {ticket} failed")
+        dev = self.device
+        out = {"K": _view(res.K_vals, res.nnz, "<f8", dev).clone(),
+               "M": _view(res.M_vals, res.nnz, "<f8", dev).clone(),
+               "vol": _view(res.vol, res.ne, "<f8", dev).clone()}
+        if pattern:
+            out["row_ptr"] = _view(res.row_ptr, res.nn + 1, "<i4", dev).clone()
+            out["col_idx"] = _view(res.col_idx, res.nnz, "<i4", dev).clone()
+        return out
+
+    def release(self, ticket):
+        _check(lib().vla_server_release(self._h, int(ticket)))
+        self._keep.pop(ticket, None)
+
+    def stats(self):
+        st = ServerStats()
+        _check(lib().vla_server_stats(self._h, C.byref(st)))
+        return {k: getattr(st, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().vla_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

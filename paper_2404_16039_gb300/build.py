@@ -56,7 +56,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
         raise RuntimeError(f"nvcc failed:\n{msg}")
     if force or procs or not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs]
+        cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
         subprocess.check_call(cmd)
         os.replace(tmp, LIB)
     return LIB
