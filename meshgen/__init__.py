@@ -245,10 +245,13 @@ def batch_specs(count: int = 256, lo: float = 1e3, hi: float = 1e6, seed: int = 
 
 
 def serving_requests(count: int = 10000, rate_per_s: float = 1000.0, lo: float = 1e3, hi: float = 2e6,
-                     repeat_frac: float = 0.2, seed: int = 0):
+                     repeat_frac: float = 0.2, seed: int = 0, size_levels: int = 0):
     """Poisson arrival stream of assembly requests.  Each request names a mesh
     spec (as in :func:`batch_specs`); a ``repeat_frac`` share repeats an earlier
-    mesh with a new coefficient ``c(x) = a + b |x|^2``, ``a, b ~ U(0.5, 2)``."""
+    mesh with a new coefficient ``c(x) = a + b |x|^2``, ``a, b ~ U(0.5, 2)``.
+    ``size_levels`` > 0 snaps each drawn element count to a geometric ladder of
+    that many levels per decade before choosing n (fewer distinct mesh sizes
+    to generate; the draws themselves are unchanged)."""
     rng = np.random.default_rng(seed)
     t = 0.0
     reqs = []
@@ -262,6 +265,8 @@ def serving_requests(count: int = 10000, rate_per_s: float = 1000.0, lo: float =
         else:
             dim, order = kinds[int(rng.integers(0, 4))]
             target = math.exp(rng.uniform(math.log(lo), math.log(hi)))
+            if size_levels > 0:
+                target = 10.0 ** (round(math.log10(target) * size_levels) / size_levels)
             spec = {"dim": dim, "order": order, "n": _structured_n(dim, order, target),
                     "seed": int(rng.integers(0, 2**31 - 1))}
         reqs.append({"id": q, "t_arrival": t, "mesh": spec, "coeff": (float(a), float(b))})
