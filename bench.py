@@ -293,7 +293,7 @@ def run_batch(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     t0 = time.perf_counter()
-    specs = meshgen.batch_specs(args.batch_count, 1e3, 1e6, seed=0)
+    specs = meshgen.batch_specs(args.batch_count, args.batch_lo, args.batch_hi, seed=0)
     meshes = [meshgen.make_mesh(s["dim"], s["n"], order=s["order"], jitter=0.1, seed=s["seed"]) for s in specs]
     gen_s = time.perf_counter() - t0
     print(f"generated {len(meshes)} meshes in {gen_s:.1f} s", file=sys.stderr, flush=True)
@@ -311,13 +311,20 @@ def run_batch(args):
     build_s = time.perf_counter() - t0
     ne = sum(g.ne for g in gms)
     alg = sum(_alg_bytes_mesh(g.dim, g.order, g.ne, g.nn, g.nnz) for g in gms)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     out_mix = [g.outputs() for g in gms]
     out_64 = [g.outputs() for g in gms]
     bm = vla.Batch([(g, o, vla.COEFF_POLY, 1.0, 1.0) for g, o in zip(gms, out_mix)], precision=vla.PREC_MIXED,
-                   graph=True)
+                   graph=True, tune=True)
     b64 = vla.Batch([(g, o, vla.COEFF_POLY, 1.0, 1.0) for g, o in zip(gms, out_64)], precision=vla.PREC_FP64,
-                    graph=True)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+                    graph=True, tune=True)
+    forms = {}
+    for form in ("fused", "split"):
+        bf = vla.Batch([(g, o, vla.COEFF_POLY, 1.0, 1.0) for g, o in zip(gms, out_mix)], precision=vla.PREC_MIXED,
+                       graph=True, form=form)
+        forms[form] = float(np.median(_time_steps(bf.run, max(3, args.steps // 4), 3, flush,
+                                                  torch.cuda.current_stream())))
+        bf.close()
     stream = torch.cuda.current_stream()
     sampler = ClockSampler(local)
     _barrier(dist)
@@ -374,20 +381,27 @@ def run_batch(args):
     kinds = {}
     for g in gms:
         k = f"{g.dim}d_p{g.order}"
-        kinds.setdefault(k, [0, 0])
-        kinds[k][0] += 1
-        kinds[k][1] += g.ne
+        kinds.setdefault(k, {"meshes": 0, "elements": 0, "max_smem": 0, "min_budget": 1 << 30})
+        kinds[k]["meshes"] += 1
+        kinds[k]["elements"] += g.ne
+        kinds[k]["max_smem"] = max(kinds[k]["max_smem"], g.smem_bytes)
+        kinds[k]["min_budget"] = min(kinds[k]["min_budget"], g.tile_budget)
     line = {"metric": "elements/sec for batched uneven K+M to CSR (one persistent launch)", "value": value,
             "unit": "elements/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"{len(gms)} meshes from seed 0: 2-D unit-square triangles and 3-D Kuhn unit-cube "
-                                   f"tets, half P1 half P2, element counts log-uniform in [1e3, 1e6] rounded to "
-                                   f"the structured n, interior jitter 0.1h, c(x)=1+|x|^2",
+                                   f"tets, half P1 half P2, element counts log-uniform in [{args.batch_lo:g}, "
+                                   f"{args.batch_hi:g}] rounded to the structured n, interior jitter 0.1h, "
+                                   f"c(x)=1+|x|^2",
                        "meshes": len(gms), "elements": ne, "nnz": sum(g.nnz for g in gms), "by_kind": kinds,
                        "precision": "mixed (f32 element matrices, float-float det and CSR sums, f64 outputs)",
-                       "launch": "one persistent kernel over all row tiles, replayed as a CUDA graph",
+                       "launch": ("one persistent kernel per element type" if bm.split else
+                                  "one persistent kernel over the row tiles of every mesh") +
+                                 ", captured in one CUDA graph; form chosen by timing both at creation",
+                       "form_ms": forms,
                        "autotuned": tuned, "grid": bm.grid, "work_items": bm.n_work,
+                       "smem_per_cta": bm.smem_bytes,
                        "l2": "flushed before every timed step (512 MiB write)"},
             "e2e": {"value": ws * ne / e2e_s, "unit": "elements/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
@@ -402,7 +416,8 @@ def run_batch(args):
             "unbatched_loop": {"ms_per_step": float(np.median(ms_loop)),
                                "value": ne / (float(np.median(ms_loop)) * 1e-3),
                                "note": "one vla_assemble launch per mesh, same outputs"},
-            "mesh_build_s": build_s, "gpu_launches": args.steps, "clocks": clocks,
+            "mesh_build_s": build_s, "gpu_launches": args.steps * (sum(1 for k in kinds) if bm.split else 1),
+            "clocks": clocks,
             "p50_ms": float(np.percentile(ms_mix, 50)), "p99_ms": float(np.percentile(ms_mix, 99))}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle
@@ -575,6 +590,8 @@ def main():
     ap.add_argument("--workload", default="p1tet", choices=["p1tet", "pages", "batch", "serve"])
     ap.add_argument("--pages-n", default="100000000")
     ap.add_argument("--batch-count", type=int, default=256)
+    ap.add_argument("--batch-lo", type=float, default=1e3)
+    ap.add_argument("--batch-hi", type=float, default=1e6)
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--calib-requests", type=int, default=1000)
     ap.add_argument("--size-levels", type=int, default=16)

@@ -126,6 +126,9 @@ typedef struct {
     int64_t device_bytes;    /* device memory held by the handle */
     int64_t tile_elems;      /* element computations per assembly (sum over tiles; >= ne) */
     int64_t n_codes;         /* contribution codes streamed per assembly (including padding) */
+    int32_t tile_budget;     /* incidence budget the tiles were cut with */
+    int32_t reserved;
+    int64_t smem_bytes;      /* shared memory per CTA of the mixed-precision assembly launch */
 } vla_mesh_info_t;
 
 /* Ingests a simplicial mesh and builds, on the device, everything the
@@ -258,18 +261,27 @@ typedef struct {
     int64_t elements;          /* sum of ne */
     int64_t tile_elems;        /* element computations per launch (>= elements) */
     int32_t graph;             /* 1 if runs replay a captured CUDA graph */
-    int32_t reserved;
+    int32_t split;             /* 1: one persistent kernel per element type; 0: one kernel for all */
 } vla_batch_info_t;
 
 #define VLA_BATCH_GRAPH 1      /* capture the launch into a CUDA graph at creation */
+#define VLA_BATCH_FUSED 2      /* one persistent kernel for every element type */
+#define VLA_BATCH_SPLIT 4      /* one persistent kernel per element type present, back to back */
+#define VLA_BATCH_AUTOTUNE 8   /* time both forms at creation (runs the batch) and keep the faster */
 
 /* Builds the job table and work list of a batch on the device.
  *   jobs: host array of count >= 1 jobs (copied; meshes must outlive the batch).
  *   precision: VLA_PREC_FP64 or VLA_PREC_MIXED, for every job.
  *   n_singular: device int64[count] receiving, per job, the number of
  *     elements with det == 0 (reset by every run), or NULL.
- *   flags: 0 or VLA_BATCH_GRAPH (the reset and the kernel are captured once
- *     into a CUDA graph; each run is one graph launch).
+ *   flags: VLA_BATCH_GRAPH captures the reset and the kernel(s) once into a
+ *     CUDA graph (each run is one graph launch).  The launch form: one
+ *     persistent kernel whose CTAs take tiles of every element type
+ *     (VLA_BATCH_FUSED: one launch, shared memory sized for the largest tile of
+ *     any type), or one persistent kernel per element type present, each
+ *     sized for its own type (VLA_BATCH_SPLIT); neither flag: split when every
+ *     type has several waves of tiles, else fused; VLA_BATCH_AUTOTUNE: run
+ *     both at creation and keep the faster.  Results do not depend on it.
  * Synchronises `stream`.  Errors: VLA_ERR_INVALID_ARG, VLA_ERR_OOM,
  * VLA_ERR_UNSUPPORTED (a tile larger than shared memory), VLA_ERR_CUDA. */
 vla_status vla_batch_create(const vla_batch_job_t *jobs, int32_t count, int32_t precision, int64_t *n_singular,

@@ -45,7 +45,8 @@ class MeshInfo(C.Structure):
     _fields_ = [("dim", C.c_int32), ("order", C.c_int32), ("nlb", C.c_int32),
                 ("nn", C.c_int64), ("ne", C.c_int64), ("nfb", C.c_int64), ("nnz", C.c_int64),
                 ("max_row_len", C.c_int32), ("n_tiles", C.c_int32), ("device_bytes", C.c_int64),
-                ("tile_elems", C.c_int64), ("n_codes", C.c_int64)]
+                ("tile_elems", C.c_int64), ("n_codes", C.c_int64), ("tile_budget", C.c_int32),
+                ("reserved", C.c_int32), ("smem_bytes", C.c_int64)]
 
 
 class BatchJob(C.Structure):
@@ -57,7 +58,7 @@ class BatchJob(C.Structure):
 class BatchInfo(C.Structure):
     _fields_ = [("count", C.c_int32), ("n_work", C.c_int32), ("grid", C.c_int32), ("ctas_per_sm", C.c_int32),
                 ("smem_bytes", C.c_int64), ("elements", C.c_int64), ("tile_elems", C.c_int64),
-                ("graph", C.c_int32), ("reserved", C.c_int32)]
+                ("graph", C.c_int32), ("split", C.c_int32)]
 
 
 class Tune(C.Structure):
@@ -91,7 +92,7 @@ class ServerStats(C.Structure):
                                                                       ("assembly_busy_s", C.c_double)]
 
 
-BATCH_GRAPH = 1
+BATCH_GRAPH, BATCH_FUSED, BATCH_SPLIT, BATCH_AUTOTUNE = 1, 2, 4, 8
 PENDING = 2
 
 
@@ -299,6 +300,7 @@ class Mesh:
         self.nn, self.ne, self.nfb, self.nnz = info.nn, info.ne, info.nfb, info.nnz
         self.max_row_len, self.n_tiles, self.device_bytes = info.max_row_len, info.n_tiles, info.device_bytes
         self.tile_elems, self.n_codes = info.tile_elems, info.n_codes
+        self.tile_budget, self.smem_bytes = info.tile_budget, info.smem_bytes
         self.device = coords.device
 
     def close(self):
@@ -414,7 +416,8 @@ class Batch:
     Mesh.outputs()).  With ``graph`` the launch is captured into a CUDA graph.
     ``n_singular`` (int64 tensor, one entry per job) is filled by each run."""
 
-    def __init__(self, jobs, precision=PREC_MIXED, graph=False, count_singular=False, stream=None):
+    def __init__(self, jobs, precision=PREC_MIXED, graph=False, count_singular=False, form=None, tune=False,
+                 stream=None):
         if not jobs:
             raise ValueError("a batch needs at least one job")
         self.meshes = [j[0] for j in jobs]
@@ -423,14 +426,17 @@ class Batch:
         dev = self.meshes[0].device
         self.n_singular = torch.zeros(len(jobs), dtype=torch.int64, device=dev) if count_singular else None
         h = C.c_void_p()
-        _check(lib().vla_batch_create(arr, len(jobs), precision, _p(self.n_singular),
-                                      BATCH_GRAPH if graph else 0, _stream(stream), C.byref(h)))
+        flags = (BATCH_GRAPH if graph else 0) | {None: 0, "fused": BATCH_FUSED, "split": BATCH_SPLIT}[form]
+        flags |= BATCH_AUTOTUNE if tune else 0
+        _check(lib().vla_batch_create(arr, len(jobs), precision, _p(self.n_singular), flags, _stream(stream),
+                                      C.byref(h)))
         self._h = h
         info = BatchInfo()
         _check(lib().vla_batch_info(h, C.byref(info)))
         self.count, self.n_work, self.grid = info.count, info.n_work, info.grid
         self.ctas_per_sm, self.smem_bytes = info.ctas_per_sm, info.smem_bytes
         self.elements, self.tile_elems, self.graph = info.elements, info.tile_elems, bool(info.graph)
+        self.split = bool(info.split)
 
     def set_job(self, index, out, kind=COEFF_POLY, ca=1.0, cb=0.0, stream=None):
         job = _job(self.meshes[index], out, kind, ca, cb)

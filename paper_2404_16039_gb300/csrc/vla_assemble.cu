@@ -49,21 +49,117 @@ int packed_index(int p, int q, int n) {  // p <= q
     return p * n - p * (p - 1) / 2 + (q - p);
 }
 
+// P2 stiffness on the reference element, evaluated at compile time:
+// K_pq = sc * sum_t coef[u][t] * Cd[st[u][t]] with u the packed index of
+// p <= q, Cd the packed dot products C_s . C_t of the vertex cofactor vectors
+// and coef the 4-point-rule integral of d(phi_p)/d(lambda_s) d(phi_q)/d(lambda_t)
+// (weights normalised to sum 1).  The kernels unroll over it with every
+// index and coefficient a compile-time constant.
+struct P2Stiff {
+    int nterm[55];
+    int st[55][4];
+    double coef[55][4];
+};
+
+constexpr void p2_edge_c(int dim, int e, int &a, int &b) {
+    if (dim == 2) {
+        const int E[3][2] = {{0, 1}, {1, 2}, {0, 2}};
+        a = E[e][0];
+        b = E[e][1];
+    } else {
+        const int E[6][2] = {{0, 1}, {1, 2}, {0, 2}, {0, 3}, {1, 3}, {2, 3}};
+        a = E[e][0];
+        b = E[e][1];
+    }
+}
+
+// d(phi_p)/d(lambda_s) at barycentric point lam
+constexpr double p2_dphi_c(int dim, int p, int s, const double *lam) {
+    if (p <= dim) return (s == p) ? 4.0 * lam[p] - 1.0 : 0.0;
+    int a = 0, b = 0;
+    p2_edge_c(dim, p - dim - 1, a, b);
+    if (s == a) return 4.0 * lam[b];
+    if (s == b) return 4.0 * lam[a];
+    return 0.0;
+}
+
+constexpr P2Stiff make_p2_stiff(int dim) {
+    P2Stiff T{};
+    const int n = dim == 2 ? 6 : 10, nv = dim + 1;
+    double pts[4][4] = {};
+    double w[4] = {};
+    if (dim == 3) {   // symmetric degree-2 rule: one barycentric coordinate a, the others b
+        for (int i = 0; i < 4; ++i) {
+            for (int j = 0; j < 4; ++j) pts[i][j] = 0.1381966011250105;
+            pts[i][i] = 0.5854101966249685;
+            w[i] = 0.25;
+        }
+    } else {          // degree-3 rule: centroid and three interior points
+        pts[0][0] = pts[0][1] = pts[0][2] = 1.0 / 3;
+        w[0] = -27.0 / 48.0;
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) pts[i + 1][j] = 0.2;
+            pts[i + 1][i] = 0.6;
+            w[i + 1] = 25.0 / 48.0;
+        }
+    }
+    for (int p = 0; p < n; ++p)
+        for (int q = p; q < n; ++q) {
+            const int u = p * n - p * (p - 1) / 2 + (q - p);
+            double acc[16] = {};
+            for (int s = 0; s < nv; ++s)
+                for (int t = 0; t < nv; ++t)
+                    for (int g = 0; g < 4; ++g)
+                        acc[(s < t ? s : t) * nv + (s < t ? t : s)] +=
+                            w[g] * p2_dphi_c(dim, p, s, pts[g]) * p2_dphi_c(dim, q, t, pts[g]);
+            int nt = 0;
+            for (int s = 0; s < nv; ++s)
+                for (int t = s; t < nv; ++t) {
+                    const double v = acc[s * nv + t];
+                    if ((v < 0 ? -v : v) < 1e-14) continue;
+                    T.st[u][nt] = s * nv - s * (s - 1) / 2 + (t - s);
+                    T.coef[u][nt] = v;
+                    ++nt;
+                }
+            T.nterm[u] = nt;
+        }
+    return T;
+}
+
+template <int DIM>
+struct P2S {
+    static constexpr P2Stiff tab = make_p2_stiff(DIM);
+};
+
+template <typename T>
+__device__ __forceinline__ T fma_t(T a, T b, T c) {
+    if constexpr (std::is_same<T, float>::value) return fmaf(a, b, c);
+    else return fma(a, b, c);
+}
+
+// sum over the terms Q.. of entry U (first term a plain product)
+template <int DIM, typename T, int U, int Q>
+__device__ __forceinline__ T p2_k_sum(const T *cd, T acc) {
+    if constexpr (Q < P2S<DIM>::tab.nterm[U]) {
+        constexpr int s = P2S<DIM>::tab.st[U][Q];
+        constexpr T c = (T)P2S<DIM>::tab.coef[U][Q];
+        return p2_k_sum<DIM, T, U, Q + 1>(cd, Q == 0 ? c * cd[s] : fma_t(c, cd[s], acc));
+    } else {
+        return acc;
+    }
+}
+
+// dst[u] = sc * K_ref[u](Cd) for every packed entry u
+template <int DIM, typename T, int... U>
+__device__ __forceinline__ void p2_k_entries(const T *cd, T sc, T *dst, std::integer_sequence<int, U...>) {
+    ((dst[U] = sc * p2_k_sum<DIM, T, U, 0>(cd, T(0))), ...);
+}
+
 void p2_edges(int dim, int e, int &a, int &b) {
     static const int E2[3][2] = {{0, 1}, {1, 2}, {0, 2}};
     static const int E3[6][2] = {{0, 1}, {1, 2}, {0, 2}, {0, 3}, {1, 3}, {2, 3}};
     a = dim == 2 ? E2[e][0] : E3[e][0];
     b = dim == 2 ? E2[e][1] : E3[e][1];
-}
-
-// d(phi_p)/d(lambda_s) at barycentric point lam
-double p2_dphi(int dim, int p, int s, const double *lam) {
-    if (p <= dim) return (s == p) ? 4.0 * lam[p] - 1.0 : 0.0;
-    int a, b;
-    p2_edges(dim, p - dim - 1, a, b);
-    if (s == a) return 4.0 * lam[b];
-    if (s == b) return 4.0 * lam[a];
-    return 0.0;
 }
 
 double p2_phi(int dim, int p, const double *lam) {
@@ -74,50 +170,17 @@ double p2_phi(int dim, int p, const double *lam) {
 }
 
 void build_p2_table(int dim, P2Tab &T) {
-    const int n = dim == 2 ? 6 : 10, nv = dim + 1;
-    // stiffness rule: 4 points, weights normalised to sum 1
-    std::vector<std::vector<double>> pts;
-    std::vector<double> wts;
-    if (dim == 3) {
-        const double a = 0.5854101966249685, b = 0.1381966011250105;
-        for (int i = 0; i < 4; ++i) {
-            std::vector<double> l(4, b);
-            l[i] = a;
-            pts.push_back(l);
-            wts.push_back(0.25);
-        }
-    } else {
-        pts.push_back({1.0 / 3, 1.0 / 3, 1.0 / 3});
-        wts.push_back(-27.0 / 48.0);
-        for (int i = 0; i < 3; ++i) {
-            std::vector<double> l(3, 0.2);
-            l[i] = 0.6;
-            pts.push_back(l);
-            wts.push_back(25.0 / 48.0);
+    const int n = dim == 2 ? 6 : 10;
+    std::memset(&T, 0, sizeof(T));
+    const P2Stiff K = make_p2_stiff(dim);
+    for (int u = 0; u < n * (n + 1) / 2; ++u) {
+        T.nterm[u] = (unsigned char)K.nterm[u];
+        for (int t = 0; t < K.nterm[u]; ++t) {
+            T.st[u][t] = (unsigned char)K.st[u][t];
+            T.coef_d[u][t] = K.coef[u][t];
+            T.coef_f[u][t] = (float)K.coef[u][t];
         }
     }
-    std::memset(&T, 0, sizeof(T));
-    for (int p = 0; p < n; ++p)
-        for (int q = p; q < n; ++q) {
-            int u = packed_index(p, q, n);
-            double acc[16] = {0};
-            for (int s = 0; s < nv; ++s)
-                for (int t = 0; t < nv; ++t)
-                    for (size_t g = 0; g < pts.size(); ++g)
-                        acc[std::min(s, t) * nv + std::max(s, t)] +=
-                            wts[g] * p2_dphi(dim, p, s, pts[g].data()) * p2_dphi(dim, q, t, pts[g].data());
-            int nt = 0;
-            for (int s = 0; s < nv; ++s)
-                for (int t = s; t < nv; ++t) {
-                    double v = acc[s * nv + t];
-                    if (std::fabs(v) < 1e-14) continue;
-                    T.st[u][nt] = (unsigned char)packed_index(s, t, nv);
-                    T.coef_d[u][nt] = v;
-                    T.coef_f[u][nt] = (float)v;
-                    ++nt;
-                }
-            T.nterm[u] = (unsigned char)nt;
-        }
     // mass: collapsed Gauss-Legendre product rule (4 points per direction),
     // exact for the quartic integrand; normalised by the reference measure
     const double gx[4] = {-0.8611363115940526, -0.3399810435848563, 0.3399810435848563, 0.8611363115940526};
@@ -560,6 +623,10 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
     const float4 *s_l = s_h + h.n_nodes;
     const double4 *s_x = reinterpret_cast<const double4 *>(b + mp.xyz);
     const T ca = MIX ? (T)J.caf : (T)J.ca, cb = MIX ? (T)J.cbf : (T)J.cb;
+    // the job's fields once per tile (a batch keeps the job in shared memory)
+    const int kind = J.kind;
+    double *const vol = J.vol, *const Kp = J.Kp, *const Mp = J.Mp;
+    unsigned long long *const n_sing = J.n_sing;
     for (int e = threadIdx.x; e <= h.n_elems; e += kThreads) {
         T *dst = s_k + (size_t)e * C::RS;
         if (e == h.n_elems) {
@@ -574,7 +641,7 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
         } else {
             geo_f64<DIM>(s_x, v, g);
         }
-        const T c = coeff<T>(J.kind, ca, cb, g.xc, DIM);
+        const T c = coeff<T>(kind, ca, cb, g.xc, DIM);
         const T adet = g.det < T(0) ? -g.det : g.det;
         T sc;
         if constexpr (MIX) sc = c * __frcp_rn(T(C::DFACT) * adet);   // K(a,b) = sc * C_a . C_b
@@ -605,27 +672,18 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
             for (int a = 0; a < C::NV; ++a)
 #pragma unroll
                 for (int q = a; q < C::NV; ++q) cd[a * C::NV - a * (a - 1) / 2 + (q - a)] = dot3<T>(g.C[a], g.C[q]);
-            const P2Tab &tb = c_p2[DIM - 2];
-            for (int u = 0; u < C::NU; ++u) {
-                T acc = 0;
-                const int nt = tb.nterm[u];
-                for (int q = 0; q < nt; ++q) {
-                    const T cf = MIX ? (T)tb.coef_f[u][q] : (T)tb.coef_d[u][q];
-                    acc += cf * cd[tb.st[u][q]];
-                }
-                dst[u] = sc * acc;
-            }
+            p2_k_entries<DIM, T>(cd, sc, dst, std::make_integer_sequence<int, C::NU>());
             mscale = c * adet * T(1.0 / C::DFACT);           // c |T|; entries scale the reference mass
             dst[C::NU] = mscale;
         }
         if (e < h.n_own) {
             const int64_t k = s_gid[e];
-            if (g.det == T(0) && J.n_sing) atomicAdd(J.n_sing, 1ull);
-            if (J.vol) {
-                if constexpr (MIX) J.vol[k] = f32_to_f64(adet * (float)(1.0 / C::DFACT));
-                else J.vol[k] = adet / C::DFACT;
+            if (g.det == T(0) && n_sing) atomicAdd(n_sing, 1ull);
+            if (vol) {
+                if constexpr (MIX) vol[k] = f32_to_f64(adet * (float)(1.0 / C::DFACT));
+                else vol[k] = adet / C::DFACT;
             }
-            if (J.Kp || J.Mp) {
+            if (Kp || Mp) {
                 for (int a = 0; a < C::NLB; ++a)
                     for (int q = 0; q < C::NLB; ++q) {
                         const int p0 = a < q ? a : q, p1 = a < q ? q : a;
@@ -636,11 +694,11 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
                         if constexpr (ORDER == 1) mv = mscale * (a == q ? T(2) : T(1));
                         else mv = mscale * mhat[u];
                         if constexpr (MIX) {
-                            if (J.Kp) J.Kp[pos] = f32_to_f64(kv);
-                            if (J.Mp) J.Mp[pos] = f32_to_f64(mv);
+                            if (Kp) Kp[pos] = f32_to_f64(kv);
+                            if (Mp) Mp[pos] = f32_to_f64(mv);
                         } else {
-                            if (J.Kp) J.Kp[pos] = kv;
-                            if (J.Mp) J.Mp[pos] = mv;
+                            if (Kp) Kp[pos] = kv;
+                            if (Mp) Mp[pos] = mv;
                         }
                     }
             }
@@ -781,7 +839,7 @@ constexpr int single_type(int types) { return types == 1 ? 0 : types == 2 ? 1 : 
 // batch, the job of its mesh) and the coordinate gathers (cp.async) of tile
 // j+1 are in flight, and the header of tile j+2 is being fetched.
 template <bool MIX, int TYPES, bool BATCH>
-__global__ void __launch_bounds__(kThreads) k_assemble(const LaunchArgs A) {
+__global__ void __launch_bounds__(kThreads, 3) k_assemble(const LaunchArgs A) {
     using T = typename std::conditional<MIX, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -1145,17 +1203,19 @@ __global__ void k_simplex_normals(int64_t ne, int dim, int nlb, const double *__
 // ---------------------------------------------------------------------------
 // batched launches
 // ---------------------------------------------------------------------------
-// work item w of a batch: the tile w - work_base of the last job whose
-// work_base <= w, with the absolute sources of its staged segments
-__global__ void k_fill_work(const MeshJob *__restrict__ jobs, int count, int n_work, WorkItem *__restrict__ work) {
+// work item w of a batch: the tile w - work_base of the last job (in work
+// order) whose work_base <= w, with the absolute sources of its staged segments
+__global__ void k_fill_work(const MeshJob *__restrict__ jobs, const int32_t *__restrict__ rank, int count,
+                            int n_work, WorkItem *__restrict__ work) {
     for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += gridDim.x * blockDim.x) {
-        int lo = 0, hi = count - 1;
+        int lo = 0, hi = count - 1;   // jobs in work order: rank[0], rank[1], ...
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (jobs[mid].work_base <= w) lo = mid;
+            if (jobs[rank[mid]].work_base <= w) lo = mid;
             else hi = mid - 1;
         }
-        const MeshJob &J = jobs[lo];
+        const int jx = rank[lo];
+        const MeshJob &J = jobs[jx];
         WorkItem it;
         it.h = J.tiles[w - J.work_base];
         it.src[0] = J.tile_nodes + it.h.node_off;
@@ -1164,9 +1224,9 @@ __global__ void k_fill_work(const MeshJob *__restrict__ jobs, int count, int n_w
         it.src[3] = J.tile_chunks + it.h.chunk_off;
         it.src[4] = J.tile_nzpos + it.h.nz_off;
         it.src[5] = reinterpret_cast<const unsigned char *>(J.codes) + (size_t)code_bytes(J.type) * it.h.code_off;
-        it.job = jobs + lo;
+        it.job = jobs + jx;
         it.type = J.type;
-        it.job_index = lo;
+        it.job_index = jx;
         work[w] = it;
     }
 }
@@ -1238,6 +1298,12 @@ struct vla_batch {
     std::vector<const vla_mesh *> meshes;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    bool split = false;                   // one persistent kernel per element type instead of one for all
+    struct Seg {
+        int32_t begin = 0, count = 0, grid = 0, stage_bytes = 0;
+        size_t smem = 0;
+    } seg[4];                             // per element type: its slice of the work list and launch shape
+    int32_t seg_order[4] = {3, 1, 2, 0};  // work order of the types
 };
 
 namespace {
@@ -1271,8 +1337,44 @@ vla_status batch_enqueue(vla_batch *b, cudaStream_t st) {
     a.err = b->d_err;
     a.spin_limit = b->spin_limit;
     a.stage_bytes = b->stage_bytes;
-    if (b->precision == VLA_PREC_MIXED) return launch_kernel<true, 15, true>(a, b->smem, b->grid, st);
-    return launch_kernel<false, 15, true>(a, b->smem, b->grid, st);
+    if (!b->split) {
+        if (b->precision == VLA_PREC_MIXED) return launch_kernel<true, 15, true>(a, b->smem, b->grid, st);
+        return launch_kernel<false, 15, true>(a, b->smem, b->grid, st);
+    }
+    const bool mix = b->precision == VLA_PREC_MIXED;
+    for (int r = 0; r < 4; ++r) {
+        const int t = b->seg_order[r];
+        const vla_batch::Seg &g = b->seg[t];
+        if (g.count == 0) continue;
+        a.work = b->d_work + g.begin;
+        a.n_work = g.count;
+        a.stage_bytes = g.stage_bytes;
+        switch (t * 2 + (mix ? 1 : 0)) {
+        case 0: TRY(launch_kernel<false, 1, true>(a, g.smem, g.grid, st)); break;
+        case 1: TRY(launch_kernel<true, 1, true>(a, g.smem, g.grid, st)); break;
+        case 2: TRY(launch_kernel<false, 2, true>(a, g.smem, g.grid, st)); break;
+        case 3: TRY(launch_kernel<true, 2, true>(a, g.smem, g.grid, st)); break;
+        case 4: TRY(launch_kernel<false, 4, true>(a, g.smem, g.grid, st)); break;
+        case 5: TRY(launch_kernel<true, 4, true>(a, g.smem, g.grid, st)); break;
+        case 6: TRY(launch_kernel<false, 8, true>(a, g.smem, g.grid, st)); break;
+        default: TRY(launch_kernel<true, 8, true>(a, g.smem, g.grid, st)); break;
+        }
+    }
+    return VLA_OK;
+}
+
+// launch shape of the per-type kernel of a split batch
+vla_status seg_shape(int t, bool mix, size_t smem, int cps, int n, int *grid) {
+    switch (t * 2 + (mix ? 1 : 0)) {
+    case 0: return kernel_shape<false, 1, true>(smem, cps, n, grid);
+    case 1: return kernel_shape<true, 1, true>(smem, cps, n, grid);
+    case 2: return kernel_shape<false, 2, true>(smem, cps, n, grid);
+    case 3: return kernel_shape<true, 2, true>(smem, cps, n, grid);
+    case 4: return kernel_shape<false, 4, true>(smem, cps, n, grid);
+    case 5: return kernel_shape<true, 4, true>(smem, cps, n, grid);
+    case 6: return kernel_shape<false, 8, true>(smem, cps, n, grid);
+    default: return kernel_shape<true, 8, true>(smem, cps, n, grid);
+    }
 }
 
 vla_status batch_build(const vla_batch_job_t *jobs, int32_t count, int32_t precision, int64_t *n_singular,
@@ -1282,7 +1384,11 @@ vla_status batch_build(const vla_batch_job_t *jobs, int32_t count, int32_t preci
     if (!jobs || count < 1) return fail(VLA_ERR_INVALID_ARG, "need count >= 1 jobs");
     if (precision != VLA_PREC_FP64 && precision != VLA_PREC_MIXED)
         return fail(VLA_ERR_INVALID_ARG, "precision must be VLA_PREC_FP64 or VLA_PREC_MIXED");
-    if (flags & ~VLA_BATCH_GRAPH) return fail(VLA_ERR_INVALID_ARG, "unknown batch flags");
+    if (flags & ~(VLA_BATCH_GRAPH | VLA_BATCH_FUSED | VLA_BATCH_SPLIT | VLA_BATCH_AUTOTUNE))
+        return fail(VLA_ERR_INVALID_ARG, "unknown batch flags");
+    if ((flags & VLA_BATCH_FUSED) && (flags & VLA_BATCH_SPLIT))
+        return fail(VLA_ERR_INVALID_ARG, "VLA_BATCH_FUSED and VLA_BATCH_SPLIT exclude each other");
+    if (async_mem && (flags & VLA_BATCH_AUTOTUNE)) return fail(VLA_ERR_INVALID_ARG, "a one-shot batch is not tuned");
     if (async_mem && (flags & VLA_BATCH_GRAPH)) return fail(VLA_ERR_INVALID_ARG, "a one-shot batch has no graph");
     const bool mix = precision == VLA_PREC_MIXED;
     int64_t n_work = 0;
@@ -1290,14 +1396,21 @@ vla_status batch_build(const vla_batch_job_t *jobs, int32_t count, int32_t preci
     size_t rec_bytes = 0;
     bool p2 = false;
     int64_t te[4] = {0, 0, 0, 0};   // tile elements per type: the dominant type picks the residency
+    int64_t tn[4] = {0, 0, 0, 0};   // work items per type
+    int tstage[4] = {0, 0, 0, 0};
+    size_t trec[4] = {0, 0, 0, 0};
     for (int i = 0; i < count; ++i) {
         TRY(check_job(jobs[i]));
         const vla_mesh *m = jobs[i].mesh;
+        const int t = type_index(m->dim, m->order);
         n_work += m->n_tiles;
         stage_bytes = std::max(stage_bytes, mesh_stage_bytes(m));
         rec_bytes = std::max(rec_bytes, mesh_record_bytes(m, mix));
         p2 = p2 || m->order == 2;
-        te[type_index(m->dim, m->order)] += m->tile_elems_total;
+        te[t] += m->tile_elems_total;
+        tn[t] += m->n_tiles;
+        tstage[t] = std::max(tstage[t], mesh_stage_bytes(m));
+        trec[t] = std::max(trec[t], mesh_record_bytes(m, mix));
     }
     if (n_work > 0x7fffffffll) return fail(VLA_ERR_UNSUPPORTED, "more than 2^31-1 tiles in one batch");
     if (p2) TRY(ensure_p2_tables());
@@ -1307,8 +1420,11 @@ vla_status batch_build(const vla_batch_job_t *jobs, int32_t count, int32_t preci
         if (te[t] > te[dom]) dom = t;
     const int cps = tuned_ctas(dom, mix);
     int grid = 0;
-    if (mix) TRY(kernel_shape<true, 15, true>(smem, cps, (int)n_work, &grid));
-    else TRY(kernel_shape<false, 15, true>(smem, cps, (int)n_work, &grid));
+    // the fused kernel may not fit (largest stage and largest records of different types): split then
+    const vla_status fs = mix ? kernel_shape<true, 15, true>(smem, cps, (int)n_work, &grid)
+                              : kernel_shape<false, 15, true>(smem, cps, (int)n_work, &grid);
+    if (fs != VLA_OK && (fs != VLA_ERR_UNSUPPORTED || (flags & VLA_BATCH_FUSED))) return fs;
+    const bool fused_fits = fs == VLA_OK;
     vla_batch *b = new (std::nothrow) vla_batch();
     if (!b) return fail(VLA_ERR_OOM, "host allocation failed");
     b->count = count;
@@ -1322,21 +1438,58 @@ vla_status batch_build(const vla_batch_job_t *jobs, int32_t count, int32_t preci
     b->stream = st;
     b->spin_limit = jobs[0].mesh->spin_limit;
     b->n_sing = reinterpret_cast<unsigned long long *>(n_singular);
+    // per-type slices of the work list (types in work order) and their own launch shapes
+    {
+        int32_t begin = 0;
+        bool split_pays = true;   // every present type has work for several waves of its own grid
+        for (int r = 0; r < 4; ++r) {
+            const int t = b->seg_order[r];
+            vla_batch::Seg &g = b->seg[t];
+            g.begin = begin;
+            g.count = (int32_t)tn[t];
+            begin += g.count;
+            if (g.count == 0) continue;
+            g.stage_bytes = tstage[t];
+            g.smem = 2 * (size_t)tstage[t] + trec[t];
+            vla_status ss = seg_shape(t, mix, g.smem, tuned_ctas(t, mix), g.count, &g.grid);
+            if (ss != VLA_OK) {
+                delete b;
+                return ss;
+            }
+            if (g.count < 4 * g.grid) split_pays = false;
+        }
+        b->split = !fused_fits || ((flags & VLA_BATCH_SPLIT) ? true : (flags & VLA_BATCH_FUSED) ? false : split_pays);
+    }
     b->ctas_per_sm = cps;
     b->h_jobs.resize(count);
     b->meshes.resize(count);
-    int32_t base = 0;
     for (int i = 0; i < count; ++i) {
         const vla_batch_job_t &j = jobs[i];
         b->meshes[i] = j.mesh;
         b->h_jobs[i] = make_job(j.mesh, j.coeff_kind, j.ca, j.cb, j.K_vals, j.M_vals, j.vol, j.K_pages, j.M_pages,
                                 b->n_sing ? b->n_sing + i : nullptr);
-        b->h_jobs[i].work_base = base;
-        base += j.mesh->n_tiles;
+    }
+    // work order: element types grouped (the CTAs, which stride through the list
+    // together, then run one type's code at a time), heaviest type first, larger
+    // meshes first within a type (small tiles fill the tail)
+    static const int type_rank[4] = {3, 1, 2, 0};   // rank of each type: P2 tets, P2 triangles, P1 tets, P1 triangles
+    std::vector<int32_t> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+        const int tx = type_rank[b->h_jobs[x].type], ty_ = type_rank[b->h_jobs[y].type];
+        if (tx != ty_) return tx < ty_;
+        return b->h_jobs[x].n_tiles > b->h_jobs[y].n_tiles;
+    });
+    int32_t base = 0;
+    for (int r = 0; r < count; ++r) {
+        b->h_jobs[order[r]].work_base = base;
+        base += b->h_jobs[order[r]].n_tiles;
     }
     const size_t jb = (sizeof(MeshJob) * count + 255) / 256 * 256;
     const size_t wb = (sizeof(WorkItem) * (size_t)n_work + 255) / 256 * 256;
-    cudaError_t e = async_mem ? cudaMallocAsync(&b->block, jb + wb + 256, st) : cudaMalloc(&b->block, jb + wb + 256);
+    const size_t rb = (sizeof(int32_t) * count + 255) / 256 * 256;
+    cudaError_t e = async_mem ? cudaMallocAsync(&b->block, jb + wb + rb + 256, st)
+                              : cudaMalloc(&b->block, jb + wb + rb + 256);
     if (e != cudaSuccess) {
         b->block = nullptr;
         batch_release(b);
@@ -1345,19 +1498,44 @@ vla_status batch_build(const vla_batch_job_t *jobs, int32_t count, int32_t preci
     }
     b->d_jobs = reinterpret_cast<MeshJob *>(b->block);
     b->d_work = reinterpret_cast<WorkItem *>(reinterpret_cast<unsigned char *>(b->block) + jb);
-    b->d_err = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(b->block) + jb + wb);
+    int32_t *d_rank = reinterpret_cast<int32_t *>(reinterpret_cast<unsigned char *>(b->block) + jb + wb);
+    b->d_err = reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(b->block) + jb + wb + rb);
     vla_status s = VLA_OK;
     auto ck = [&](cudaError_t ce, const char *what) {
         if (ce != cudaSuccess && s == VLA_OK) s = cuda_fail(ce, what);
     };
     ck(cudaMemcpyAsync(b->d_jobs, b->h_jobs.data(), sizeof(MeshJob) * count, cudaMemcpyHostToDevice, st), "batch jobs");
+    ck(cudaMemcpyAsync(d_rank, order.data(), sizeof(int32_t) * count, cudaMemcpyHostToDevice, st), "batch order");
     ck(cudaMemsetAsync(b->d_err, 0, sizeof(int), st), "batch error word");
     if (s == VLA_OK) {
-        k_fill_work<<<grid_for(n_work, 256), 256, 0, st>>>(b->d_jobs, count, (int)n_work, b->d_work);
+        k_fill_work<<<grid_for(n_work, 256), 256, 0, st>>>(b->d_jobs, d_rank, count, (int)n_work, b->d_work);
         ck(cudaGetLastError(), "batch work list");
     }
     // the job table is copied from pageable host memory: finish before the vector can go away
     if (s == VLA_OK && !async_mem) ck(cudaStreamSynchronize(st), "batch build");
+    if (s == VLA_OK && (flags & VLA_BATCH_AUTOTUNE)) {
+        // time both launch forms on the batch itself (outputs are overwritten) and keep the faster
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        ck(cudaEventCreate(&e0), "event");
+        ck(cudaEventCreate(&e1), "event");
+        float best[2] = {1e30f, 1e30f};
+        for (int mode = fused_fits ? 0 : 1; mode < 2 && s == VLA_OK; ++mode) {
+            b->split = mode == 1;
+            for (int r = 0; r < 4 && s == VLA_OK; ++r) {
+                ck(cudaEventRecord(e0, st), "event");
+                vla_status es = batch_enqueue(b, st);
+                if (es != VLA_OK) s = es;
+                ck(cudaEventRecord(e1, st), "event");
+                ck(cudaEventSynchronize(e1), "event");
+                float ms = 0.f;
+                ck(cudaEventElapsedTime(&ms, e0, e1), "event");
+                if (r > 0) best[mode] = std::min(best[mode], ms);   // the first run warms up
+            }
+        }
+        b->split = best[1] < best[0];
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
     if (s == VLA_OK && (flags & VLA_BATCH_GRAPH)) {
         cudaStream_t cs = nullptr;
         ck(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking), "capture stream");
@@ -1424,6 +1602,7 @@ extern "C" vla_status vla_batch_info(const vla_batch *b, vla_batch_info_t *info)
     info->ctas_per_sm = b->ctas_per_sm;
     info->smem_bytes = (int64_t)b->smem;
     info->graph = b->exec != nullptr;
+    info->split = b->split ? 1 : 0;
     for (const vla_mesh *m : b->meshes) {
         info->elements += m->ne;
         info->tile_elems += m->tile_elems_total;

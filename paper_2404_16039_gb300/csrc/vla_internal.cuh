@@ -222,6 +222,7 @@ struct vla_mesh {
     int64_t n_codes;
     int64_t tile_elems_total;     // sum over tiles of their element counts (recompute factor * ne)
     size_t tile_stage_bytes;      // largest per-tile staged segment set (ids, records, owned, chunks, pairs, codes)
+    size_t tile_smem;             // shared memory per CTA of the mixed-precision assembly launch
     int32_t spin_limit;           // bounded waits on bulk copies
     int32_t *d_err;               // device error word (bit 0: a bounded wait expired)
     int64_t device_bytes;

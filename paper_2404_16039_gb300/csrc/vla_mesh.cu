@@ -750,6 +750,19 @@ struct Scratch {  // temporary device buffers freed at the end of the build
 };
 
 
+// largest shared-memory footprint of a tile's assembly launch that still lets
+// two CTAs share an SM (VLA_TILE_SMEM_CAP overrides, for experiments)
+size_t tile_smem_cap() {
+    if (const char *c = getenv("VLA_TILE_SMEM_CAP")) return (size_t)std::max(16384ll, atoll(c));
+    int dev = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = 233472;
+    }
+    return (size_t)per_sm / 2 - 4096;
+}
+
 // incidence budget of a tile (sum over its rows of 1 + incident elements)
 int tile_budget(int dim, int order) {
     if (order == 1) return dim == 3 ? 800 : 2048;
@@ -896,159 +909,184 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     int B = m->tile_budget > 0 ? m->tile_budget : tuned_budget((dim - 2) * 2 + (m->order - 1));
     if (B <= 0) B = tile_budget(dim, m->order);
     if (const char *tb = getenv("VLA_TILE_BUDGET")) B = std::max(64, atoi(tb));
-    m->tile_budget = B;
-    int32_t *w, *flag, *tile_begin, *node_tile;
-    long long *fpre;
-    TRY(S.get(&w, nn));
-    TRY(S.get(&flag, nn));
-    TRY(S.get(&fpre, nn + 1));
-    TRY(S.get(&node_tile, nn));
-    k_rank_weights<<<grid_for(nn, TB), TB, 0, st>>>(nn, perm, cnt, w);
-    TRY(excl_scan<int32_t>(w, nn, pre, st, nullptr));
-    k_tile_flags<<<grid_for(nn, TB), TB, 0, st>>>(nn, B, pre, flag);
-    long long n_tiles = 0;
-    TRY(excl_scan<int32_t>(flag, nn, fpre, st, &n_tiles));
-    TRY(S.get(&tile_begin, n_tiles + 1));
-    k_tile_assign<<<grid_for(nn, TB), TB, 0, st>>>(nn, flag, fpre, perm, tile_begin, node_tile);
-    VLA_CUDA(cudaGetLastError());
-    m->n_tiles = (int32_t)n_tiles;
+    const size_t mark_allocs = m->allocs.size();
+    const int64_t mark_bytes = m->device_bytes;
+    const size_t cap = tile_smem_cap();
+    for (int attempt = 0;; ++attempt) {
+        m->tile_budget = B;
+        int32_t *w, *flag, *tile_begin, *node_tile;
+        long long *fpre;
+        TRY(S.get(&w, nn));
+        TRY(S.get(&flag, nn));
+        TRY(S.get(&fpre, nn + 1));
+        TRY(S.get(&node_tile, nn));
+        k_rank_weights<<<grid_for(nn, TB), TB, 0, st>>>(nn, perm, cnt, w);
+        TRY(excl_scan<int32_t>(w, nn, pre, st, nullptr));
+        k_tile_flags<<<grid_for(nn, TB), TB, 0, st>>>(nn, B, pre, flag);
+        long long n_tiles = 0;
+        TRY(excl_scan<int32_t>(flag, nn, fpre, st, &n_tiles));
+        TRY(S.get(&tile_begin, n_tiles + 1));
+        k_tile_assign<<<grid_for(nn, TB), TB, 0, st>>>(nn, flag, fpre, perm, tile_begin, node_tile);
+        VLA_CUDA(cudaGetLastError());
+        m->n_tiles = (int32_t)n_tiles;
 
-    // max incidence of a single node bounds the tile's candidate count: B + max weight
-    std::vector<int32_t> hcnt(nn);
-    VLA_CUDA(cudaMemcpyAsync(hcnt.data(), cnt, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, st));
-    VLA_CUDA(cudaStreamSynchronize(st));
-    int wmax = 0;
-    for (int64_t i = 0; i < nn; ++i) wmax = std::max(wmax, hcnt[i] + 1);
-    if (wmax > B) return fail(VLA_ERR_UNSUPPORTED, "a node belongs to %d elements (tile budget %d)", wmax - 1, B);
-    const int cap_e = next_pow2(B + wmax);
-    const int cap_n = next_pow2((dim + 1) * (B + wmax));
-    int32_t *sc_elems, *sc_nodes;
-    TileCounts *tcnt;
-    TRY(S.get(&sc_elems, (size_t)n_tiles * cap_e));
-    TRY(S.get(&sc_nodes, (size_t)n_tiles * cap_n));
-    TRY(S.get(&tcnt, n_tiles));
-    const size_t smemA = sizeof(int32_t) * (cap_e + cap_n + std::max(cap_e, cap_n));
-    VLA_CUDA(cudaFuncSetAttribute(k_tile_sets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemA));
-    k_tile_sets<<<(int)n_tiles, 256, smemA, st>>>((int)n_tiles, nn, dim, nlb, cap_e, cap_n, tile_begin, perm,
-                                                   m->n2e_ptr, m->n2e, m->elems, m->row_ptr, m->col_idx, node_tile,
-                                                   sc_elems, sc_nodes, tcnt, d_err);
-    VLA_CUDA(cudaGetLastError());
-    std::vector<TileCounts> hc(n_tiles);
-    VLA_CUDA(cudaMemcpyAsync(hc.data(), tcnt, sizeof(TileCounts) * n_tiles, cudaMemcpyDeviceToHost, st));
-    VLA_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    VLA_CUDA(cudaStreamSynchronize(st));
-    if (h_err & 32) return fail(VLA_ERR_UNSUPPORTED, "tile candidate capacity exceeded");
+        // max incidence of a single node bounds the tile's candidate count: B + max weight
+        std::vector<int32_t> hcnt(nn);
+        VLA_CUDA(cudaMemcpyAsync(hcnt.data(), cnt, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, st));
+        VLA_CUDA(cudaStreamSynchronize(st));
+        int wmax = 0;
+        for (int64_t i = 0; i < nn; ++i) wmax = std::max(wmax, hcnt[i] + 1);
+        if (wmax > B) return fail(VLA_ERR_UNSUPPORTED, "a node belongs to %d elements (tile budget %d)", wmax - 1, B);
+        const int cap_e = next_pow2(B + wmax);
+        const int cap_n = next_pow2((dim + 1) * (B + wmax));
+        int32_t *sc_elems, *sc_nodes;
+        TileCounts *tcnt;
+        TRY(S.get(&sc_elems, (size_t)n_tiles * cap_e));
+        TRY(S.get(&sc_nodes, (size_t)n_tiles * cap_n));
+        TRY(S.get(&tcnt, n_tiles));
+        const size_t smemA = sizeof(int32_t) * (cap_e + cap_n + std::max(cap_e, cap_n));
+        VLA_CUDA(cudaFuncSetAttribute(k_tile_sets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemA));
+        k_tile_sets<<<(int)n_tiles, 256, smemA, st>>>((int)n_tiles, nn, dim, nlb, cap_e, cap_n, tile_begin, perm,
+                                                       m->n2e_ptr, m->n2e, m->elems, m->row_ptr, m->col_idx, node_tile,
+                                                       sc_elems, sc_nodes, tcnt, d_err);
+        VLA_CUDA(cudaGetLastError());
+        std::vector<TileCounts> hc(n_tiles);
+        VLA_CUDA(cudaMemcpyAsync(hc.data(), tcnt, sizeof(TileCounts) * n_tiles, cudaMemcpyDeviceToHost, st));
+        VLA_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        VLA_CUDA(cudaStreamSynchronize(st));
+        if (h_err & 32) return fail(VLA_ERR_UNSUPPORTED, "tile candidate capacity exceeded");
 
-    // tile offsets (host scan over a few thousand tiles); every segment padded for bulk copies
-    auto pad = [](int64_t x, int64_t q) { return (x + q - 1) / q * q; };
-    std::vector<TileHdr> hh(n_tiles);
-    int64_t o_node = 0, o_elem = 0, o_own = 0, o_nz = 0, o_chunk = 0, n_own_total = 0, nz_total = 0;
-    m->max_tile_nodes = m->max_tile_elems = m->max_tile_nz = 0;
-    m->tile_elems_total = 0;
-    for (int64_t t = 0; t < n_tiles; ++t) {
-        TileHdr &h = hh[t];
-        std::memset(&h, 0, sizeof(h));
-        const TileCounts &c = hc[t];
-        h.node_off = (int32_t)o_node;
-        h.n_nodes = c.n_nodes;
-        h.elem_off = (int32_t)o_elem;
-        h.n_elems = c.n_elems;
-        h.own_off = (int32_t)o_own;
-        h.n_own = c.n_own;
-        h.nz_off = (int32_t)o_nz;
-        h.n_nz = c.n_up + c.n_diag;
-        h.n_up = c.n_up;
-        h.chunk_off = (int32_t)o_chunk;
-        h.n_chunks = (c.n_up + c.n_diag + 31) / 32;
-        h.rank_begin = c.rank_begin;
-        h.n_rows = c.n_rows;
-        o_node += pad(c.n_nodes, kTilePadNodes);
-        o_elem += pad(c.n_elems, kTilePadElems);
-        o_own += pad(c.n_own, kTilePadOwn);
-        o_nz += pad(h.n_nz, kTilePadNz);
-        o_chunk += pad(h.n_chunks, kTilePadChunks);
-        n_own_total += c.n_own;
-        nz_total += 2LL * c.n_up + c.n_diag;
-        m->tile_elems_total += c.n_elems;
-        m->max_tile_nodes = std::max(m->max_tile_nodes, c.n_nodes);
-        m->max_tile_elems = std::max(m->max_tile_elems, c.n_elems);
-        m->max_tile_nz = std::max(m->max_tile_nz, h.n_nz);
-        if (h.n_chunks > 1024) return fail(VLA_ERR_UNSUPPORTED, "tile has more than 1024 chunks");
+        // tile offsets (host scan over a few thousand tiles); every segment padded for bulk copies
+        auto pad = [](int64_t x, int64_t q) { return (x + q - 1) / q * q; };
+        std::vector<TileHdr> hh(n_tiles);
+        int64_t o_node = 0, o_elem = 0, o_own = 0, o_nz = 0, o_chunk = 0, n_own_total = 0, nz_total = 0;
+        m->max_tile_nodes = m->max_tile_elems = m->max_tile_nz = 0;
+        m->tile_elems_total = 0;
+        for (int64_t t = 0; t < n_tiles; ++t) {
+            TileHdr &h = hh[t];
+            std::memset(&h, 0, sizeof(h));
+            const TileCounts &c = hc[t];
+            h.node_off = (int32_t)o_node;
+            h.n_nodes = c.n_nodes;
+            h.elem_off = (int32_t)o_elem;
+            h.n_elems = c.n_elems;
+            h.own_off = (int32_t)o_own;
+            h.n_own = c.n_own;
+            h.nz_off = (int32_t)o_nz;
+            h.n_nz = c.n_up + c.n_diag;
+            h.n_up = c.n_up;
+            h.chunk_off = (int32_t)o_chunk;
+            h.n_chunks = (c.n_up + c.n_diag + 31) / 32;
+            h.rank_begin = c.rank_begin;
+            h.n_rows = c.n_rows;
+            o_node += pad(c.n_nodes, kTilePadNodes);
+            o_elem += pad(c.n_elems, kTilePadElems);
+            o_own += pad(c.n_own, kTilePadOwn);
+            o_nz += pad(h.n_nz, kTilePadNz);
+            o_chunk += pad(h.n_chunks, kTilePadChunks);
+            n_own_total += c.n_own;
+            nz_total += 2LL * c.n_up + c.n_diag;
+            m->tile_elems_total += c.n_elems;
+            m->max_tile_nodes = std::max(m->max_tile_nodes, c.n_nodes);
+            m->max_tile_elems = std::max(m->max_tile_elems, c.n_elems);
+            m->max_tile_nz = std::max(m->max_tile_nz, h.n_nz);
+            if (h.n_chunks > 1024) return fail(VLA_ERR_UNSUPPORTED, "tile has more than 1024 chunks");
+        }
+        if (n_own_total != ne) return fail(VLA_ERR_CUDA, "internal: tiles own %lld of %lld elements", (long long)n_own_total, (long long)ne);
+        if (nz_total != nnz) return fail(VLA_ERR_CUDA, "internal: tiles cover %lld of %lld nonzeros", (long long)nz_total, nnz);
+        if (m->max_tile_elems >= 0xffff || m->max_tile_nodes > 0xffff)
+            return fail(VLA_ERR_UNSUPPORTED, "tile exceeds 65534 elements or 65535 nodes");
+        if (m->order == 1 && m->max_tile_elems >= 4095)
+            return fail(VLA_ERR_UNSUPPORTED, "P1 tile has %d elements (limit 4094)", m->max_tile_elems);
+        TRY(dalloc(m, &m->tiles, n_tiles, st));
+        VLA_CUDA(cudaMemcpyAsync(m->tiles, hh.data(), sizeof(TileHdr) * n_tiles, cudaMemcpyHostToDevice, st));
+        // +16 bytes of slack: bulk copies round sizes up to 16 bytes
+        TRY(dalloc(m, &m->tile_nodes, o_node + 4, st));
+        TRY(dalloc(m, &m->tile_elem, o_elem + 2, st));
+        TRY(dalloc(m, &m->tile_own, o_own + 4, st));
+        TRY(dalloc(m, &m->tile_nzpos, o_nz + 2, st));
+        TRY(dalloc(m, &m->tile_chunks, o_chunk + 2, st));
+        VLA_CUDA(cudaMemsetAsync(m->tile_nodes, 0, sizeof(int32_t) * (o_node + 4), st));
+        VLA_CUDA(cudaMemsetAsync(m->tile_elem, 0, sizeof(ushort4) * (o_elem + 2), st));
+        VLA_CUDA(cudaMemsetAsync(m->tile_own, 0, sizeof(int32_t) * (o_own + 4), st));
+        VLA_CUDA(cudaMemsetAsync(m->tile_nzpos, 0, sizeof(int2) * (o_nz + 2), st));
+        VLA_CUDA(cudaMemsetAsync(m->tile_chunks, 0, sizeof(int2) * (o_chunk + 2), st));
+        int32_t *nz_count, *tile_ncodes, *nz_order;
+        int2 *row_info, *nzpos_rm;
+        TRY(S.get(&nz_count, o_nz + 2));
+        TRY(S.get(&nz_order, o_nz + 2));
+        TRY(S.get(&nzpos_rm, o_nz + 2));
+        TRY(S.get(&row_info, nn));
+        TRY(S.get(&tile_ncodes, n_tiles));
+        k_tile_fill<<<(int)n_tiles, 256, 0, st>>>((int)n_tiles, dim, nlb, cap_e, cap_n, m->tiles, perm, m->n2e_ptr,
+                                                  m->n2e, m->elems, m->row_ptr, m->col_idx, sc_elems, sc_nodes,
+                                                  m->tile_nodes, m->tile_elem, m->tile_own, nzpos_rm, nz_count,
+                                                  row_info);
+        k_chunk_table<<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, m->tiles, nz_count, nzpos_rm, m->tile_nzpos, nz_order,
+                                                    m->tile_chunks, tile_ncodes);
+        VLA_CUDA(cudaGetLastError());
+        std::vector<int32_t> hnc(n_tiles);
+        VLA_CUDA(cudaMemcpyAsync(hnc.data(), tile_ncodes, sizeof(int32_t) * n_tiles, cudaMemcpyDeviceToHost, st));
+        VLA_CUDA(cudaStreamSynchronize(st));
+        int64_t o_code = 0;
+        const size_t code_bytes = (m->order == 1) ? 2 : 4;
+        size_t stage_max = 0;
+        for (int64_t t = 0; t < n_tiles; ++t) {
+            hh[t].code_off = (int32_t)o_code;
+            hh[t].n_codes = hnc[t];
+            o_code += hnc[t];
+            if (o_code > 0x7fffffffll) return fail(VLA_ERR_UNSUPPORTED, "too many contribution codes");
+            const TileHdr &h = hh[t];
+            size_t stage = 4 * pad(h.n_nodes, kTilePadNodes) + 8 * pad(h.n_elems, kTilePadElems) +
+                           4 * pad(h.n_own, kTilePadOwn) + 8 * pad(h.n_chunks, kTilePadChunks) +
+                           8 * pad(h.n_nz, kTilePadNz) + code_bytes * h.n_codes;
+            stage_max = std::max(stage_max, stage);
+        }
+        m->tile_stage_bytes = stage_max;
+        {
+            // shared-memory footprint of the mixed-precision assembly launch: two input
+            // stages and the element records.  Each part is capped on its own (stage
+            // 30%, records 40% of the two-CTAs-per-SM limit), so a batched launch over
+            // meshes of any types, which sizes each part for its largest tile, keeps
+            // two CTAs per SM too; above a cap the tiles are cut with a smaller budget
+            const int nu = nlb * (nlb + 1) / 2, rs = (nu + 1 + 3) / 4 * 4;
+            const size_t stg = (stage_max + 32 * (size_t)m->max_tile_nodes + 16 + 15) / 16 * 16;
+            const size_t rec = ((size_t)m->max_tile_elems + 1) * rs * 4;
+            m->tile_smem = 2 * stg + rec;
+            const double over = std::max((double)stg / (0.3 * (double)cap), (double)rec / (0.4 * (double)cap));
+            if (over > 1.0 && attempt < 4 && B > wmax) {
+                for (size_t a = mark_allocs; a < m->allocs.size(); ++a) cudaFreeAsync(m->allocs[a], st);
+                m->allocs.resize(mark_allocs);
+                m->device_bytes = mark_bytes;
+                B = std::max(wmax, (int)((double)B / over * 0.95));
+                continue;
+            }
+        }
+        m->n_codes = o_code;
+        VLA_CUDA(cudaMemcpyAsync(m->tiles, hh.data(), sizeof(TileHdr) * n_tiles, cudaMemcpyHostToDevice, st));
+        int32_t *fill;
+        TRY(S.get(&fill, o_nz + 2));
+        VLA_CUDA(cudaMemsetAsync(fill, 0, sizeof(int32_t) * (o_nz + 2), st));
+        if (m->order == 1) {
+            uint16_t *codes;
+            TRY(dalloc(m, &codes, o_code + 64, st));
+            k_tile_codes<uint16_t, 4><<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, m->tiles, perm,
+                                                                     m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
+                                                                     m->col_idx, sc_elems, row_info, nz_order,
+                                                                     m->tile_chunks, fill, codes);
+            m->tile_codes = codes;
+        } else {
+            uint32_t *codes;
+            TRY(dalloc(m, &codes, o_code + 64, st));
+            k_tile_codes<uint32_t, 8><<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, m->tiles, perm,
+                                                                     m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
+                                                                     m->col_idx, sc_elems, row_info, nz_order,
+                                                                     m->tile_chunks, fill, codes);
+            m->tile_codes = codes;
+        }
+        VLA_CUDA(cudaGetLastError());
+        break;
     }
-    if (n_own_total != ne) return fail(VLA_ERR_CUDA, "internal: tiles own %lld of %lld elements", (long long)n_own_total, (long long)ne);
-    if (nz_total != nnz) return fail(VLA_ERR_CUDA, "internal: tiles cover %lld of %lld nonzeros", (long long)nz_total, nnz);
-    if (m->max_tile_elems >= 0xffff || m->max_tile_nodes > 0xffff)
-        return fail(VLA_ERR_UNSUPPORTED, "tile exceeds 65534 elements or 65535 nodes");
-    if (m->order == 1 && m->max_tile_elems >= 4095)
-        return fail(VLA_ERR_UNSUPPORTED, "P1 tile has %d elements (limit 4094)", m->max_tile_elems);
-    TRY(dalloc(m, &m->tiles, n_tiles, st));
-    VLA_CUDA(cudaMemcpyAsync(m->tiles, hh.data(), sizeof(TileHdr) * n_tiles, cudaMemcpyHostToDevice, st));
-    // +16 bytes of slack: bulk copies round sizes up to 16 bytes
-    TRY(dalloc(m, &m->tile_nodes, o_node + 4, st));
-    TRY(dalloc(m, &m->tile_elem, o_elem + 2, st));
-    TRY(dalloc(m, &m->tile_own, o_own + 4, st));
-    TRY(dalloc(m, &m->tile_nzpos, o_nz + 2, st));
-    TRY(dalloc(m, &m->tile_chunks, o_chunk + 2, st));
-    VLA_CUDA(cudaMemsetAsync(m->tile_nodes, 0, sizeof(int32_t) * (o_node + 4), st));
-    VLA_CUDA(cudaMemsetAsync(m->tile_elem, 0, sizeof(ushort4) * (o_elem + 2), st));
-    VLA_CUDA(cudaMemsetAsync(m->tile_own, 0, sizeof(int32_t) * (o_own + 4), st));
-    VLA_CUDA(cudaMemsetAsync(m->tile_nzpos, 0, sizeof(int2) * (o_nz + 2), st));
-    VLA_CUDA(cudaMemsetAsync(m->tile_chunks, 0, sizeof(int2) * (o_chunk + 2), st));
-    int32_t *nz_count, *tile_ncodes, *nz_order;
-    int2 *row_info, *nzpos_rm;
-    TRY(S.get(&nz_count, o_nz + 2));
-    TRY(S.get(&nz_order, o_nz + 2));
-    TRY(S.get(&nzpos_rm, o_nz + 2));
-    TRY(S.get(&row_info, nn));
-    TRY(S.get(&tile_ncodes, n_tiles));
-    k_tile_fill<<<(int)n_tiles, 256, 0, st>>>((int)n_tiles, dim, nlb, cap_e, cap_n, m->tiles, perm, m->n2e_ptr,
-                                              m->n2e, m->elems, m->row_ptr, m->col_idx, sc_elems, sc_nodes,
-                                              m->tile_nodes, m->tile_elem, m->tile_own, nzpos_rm, nz_count,
-                                              row_info);
-    k_chunk_table<<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, m->tiles, nz_count, nzpos_rm, m->tile_nzpos, nz_order,
-                                                m->tile_chunks, tile_ncodes);
-    VLA_CUDA(cudaGetLastError());
-    std::vector<int32_t> hnc(n_tiles);
-    VLA_CUDA(cudaMemcpyAsync(hnc.data(), tile_ncodes, sizeof(int32_t) * n_tiles, cudaMemcpyDeviceToHost, st));
-    VLA_CUDA(cudaStreamSynchronize(st));
-    int64_t o_code = 0;
-    const size_t code_bytes = (m->order == 1) ? 2 : 4;
-    size_t stage_max = 0;
-    for (int64_t t = 0; t < n_tiles; ++t) {
-        hh[t].code_off = (int32_t)o_code;
-        hh[t].n_codes = hnc[t];
-        o_code += hnc[t];
-        if (o_code > 0x7fffffffll) return fail(VLA_ERR_UNSUPPORTED, "too many contribution codes");
-        const TileHdr &h = hh[t];
-        size_t stage = 4 * pad(h.n_nodes, kTilePadNodes) + 8 * pad(h.n_elems, kTilePadElems) +
-                       4 * pad(h.n_own, kTilePadOwn) + 8 * pad(h.n_chunks, kTilePadChunks) +
-                       8 * pad(h.n_nz, kTilePadNz) + code_bytes * h.n_codes;
-        stage_max = std::max(stage_max, stage);
-    }
-    m->tile_stage_bytes = stage_max;
-    m->n_codes = o_code;
-    VLA_CUDA(cudaMemcpyAsync(m->tiles, hh.data(), sizeof(TileHdr) * n_tiles, cudaMemcpyHostToDevice, st));
-    int32_t *fill;
-    TRY(S.get(&fill, o_nz + 2));
-    VLA_CUDA(cudaMemsetAsync(fill, 0, sizeof(int32_t) * (o_nz + 2), st));
-    if (m->order == 1) {
-        uint16_t *codes;
-        TRY(dalloc(m, &codes, o_code + 64, st));
-        k_tile_codes<uint16_t, 4><<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, m->tiles, perm,
-                                                                 m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
-                                                                 m->col_idx, sc_elems, row_info, nz_order,
-                                                                 m->tile_chunks, fill, codes);
-        m->tile_codes = codes;
-    } else {
-        uint32_t *codes;
-        TRY(dalloc(m, &codes, o_code + 64, st));
-        k_tile_codes<uint32_t, 8><<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, m->tiles, perm,
-                                                                 m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
-                                                                 m->col_idx, sc_elems, row_info, nz_order,
-                                                                 m->tile_chunks, fill, codes);
-        m->tile_codes = codes;
-    }
-    VLA_CUDA(cudaGetLastError());
     TRY(dalloc(m, &m->d_err, 1, st));
     VLA_CUDA(cudaMemsetAsync(m->d_err, 0, sizeof(int32_t), st));
     m->spin_limit = 1 << 22;
@@ -1156,6 +1194,9 @@ extern "C" vla_status vla_mesh_info(const vla_mesh *m, vla_mesh_info_t *info) {
     info->device_bytes = m->device_bytes;
     info->tile_elems = m->tile_elems_total;
     info->n_codes = m->n_codes;
+    info->tile_budget = m->tile_budget;
+    info->reserved = 0;
+    info->smem_bytes = (int64_t)m->tile_smem;
     return VLA_OK;
 }
 

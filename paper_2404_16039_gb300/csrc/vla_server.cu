@@ -160,6 +160,7 @@ void admit(vla_server *s) {
         if (mneed + oneed > s->cfg.hbm_budget_bytes) {
             s->queue.pop_front();
             finish(s, q, VLA_ERR_BUDGET);
+            s->done_cv.notify_all();
             continue;
         }
         if (s->cfg.max_inflight > 0 && s->live >= s->cfg.max_inflight) return;

@@ -61,13 +61,17 @@ def _coeffs(q):
 
 @pytest.mark.parametrize("precision", [0, 1])
 @pytest.mark.parametrize("graph", [False, True])
-def test_batch_bit_identical_to_single(vla, precision, graph):
+@pytest.mark.parametrize("form", ["fused", "split", "tuned"])
+def test_batch_bit_identical_to_single(vla, precision, graph, form):
     meshes, gms = _mix(vla, MIX_SPECS)
     jobs = []
     for q, gm in enumerate(gms):
         kind, ca, cb = _coeffs(q)
         jobs.append((gm, gm.outputs(pages=(q % 4 == 1)), kind, ca, cb))
-    b = vla.Batch(jobs, precision=precision, graph=graph, count_singular=True)
+    b = vla.Batch(jobs, precision=precision, graph=graph, count_singular=True,
+                  form=None if form == "tuned" else form, tune=form == "tuned")
+    if form != "tuned":
+        assert b.split == (form == "split")
     assert b.count == len(jobs) and b.graph == graph
     assert b.n_work == sum(gm.n_tiles for gm in gms)
     assert b.elements == sum(m.ne for m in meshes)
