@@ -472,27 +472,35 @@ def run_serve(args):
             cache[k] = meshgen.make_mesh(s["dim"], s["n"], order=s["order"], jitter=0.1, seed=s["n"])
     gen_s = time.perf_counter() - t0
     print(f"generated {len(cache)} distinct meshes for {N} requests in {gen_s:.1f} s", file=sys.stderr, flush=True)
+    # the client's inputs live in pinned host memory
+    pinned = {k: (torch.from_numpy(m.coords).pin_memory(), torch.from_numpy(m.elems).pin_memory(), m.order, m.ne)
+              for k, m in cache.items()}
     keys = {}
     reqs = []
     for r in base:
         s = r["mesh"]
         key = keys.setdefault((s["dim"], s["order"], s["n"], s["seed"]), len(keys))
-        reqs.append((r["t_arrival"], key, cache[(s["dim"], s["order"], s["n"])], r["coeff"]))
-    host = [torch.empty(1 << 20, dtype=torch.float64).pin_memory()]   # grown on demand
+        reqs.append((r["t_arrival"], key, pinned[(s["dim"], s["order"], s["n"])], r["coeff"]))
+    n_poll = args.pollers
+    hosts = [[torch.empty(1 << 20, dtype=torch.float64).pin_memory()] for _ in range(n_poll)]   # grown on demand
 
     def run(precision, rate, count, closed=False):
         srv = vla.Server(args.budget_gb << 30, precision=precision, ingest_workers=args.ingest_workers)
         sub = reqs[:count]
         tickets = [None] * count
         t_arr = [0.0] * count
-        lat, lat_host, els = [], [], []
-        batches = []
+        lat = [None] * count
+        lat_host = [None] * count
+        els = [0] * count
+        bsz = [0] * count
+        fails = {}
         h2d = [0]
-        d2h = [0]
-        done_evt = threading.Event()
+        d2h = [0] * n_poll
+        lock = threading.Lock()
 
-        def poller():
-            for i in range(count):
+        def poller(p):   # requests p, p + n_poll, ...: wait, copy K/M/vol to pinned host memory, release
+            host = hosts[p]
+            for i in range(p, count, n_poll):
                 while tickets[i] is None:
                     time.sleep(0.0002)
                 res = None
@@ -504,40 +512,45 @@ def run_serve(args):
                         host[0] = torch.empty(2 * n, dtype=torch.float64).pin_memory()
                     for ptr, cnt in ((res.K_vals, n), (res.M_vals, n), (res.vol, res.ne)):
                         host[0][:cnt].copy_(vla._view(ptr, cnt, "<f8", dev))
-                        d2h[0] += 8 * cnt
+                        d2h[p] += 8 * cnt
                     th = time.monotonic()
-                    lat.append(res.t_done - t_arr[i])
-                    lat_host.append(th - t_arr[i])
-                    els.append(res.ne)
-                    batches.append(res.batch_size)
+                    lat[i] = res.t_done - t_arr[i]
+                    lat_host[i] = th - t_arr[i]
+                    els[i] = res.ne
+                    bsz[i] = res.batch_size
+                else:
+                    with lock:
+                        fails[int(res.status)] = fails.get(int(res.status), 0) + 1
                 srv.release(tickets[i])
-            done_evt.set()
 
-        th_ = threading.Thread(target=poller)
-        th_.start()
+        ths = [threading.Thread(target=poller, args=(p,)) for p in range(n_poll)]
+        for t_ in ths:
+            t_.start()
         start = time.monotonic() + 0.05
-        for i, (ta, key, m, (a, b)) in enumerate(sub):
+        for i, (ta, key, (c, e, order, ne), (a, b)) in enumerate(sub):
             t_arr[i] = start if closed else start + ta / rate
             d = t_arr[i] - time.monotonic()
             if d > 0:
                 time.sleep(d)
-            tickets[i] = srv.submit(m.coords, m.elems, order=m.order, key=key, keep_resident=True,
-                                    kind=vla.COEFF_POLY, ca=a, cb=b)
-            h2d[0] += m.coords.nbytes + m.elems.nbytes
-        done_evt.wait()
-        th_.join()
+            tickets[i] = srv.submit(c, e, order=order, key=key, keep_resident=True, kind=vla.COEFF_POLY, ca=a, cb=b)
+            h2d[0] += c.numel() * 8 + e.numel() * 4
+        for t_ in ths:
+            t_.join()
         st = srv.stats()
-        wall = max(t_arr[i] + lat_host[i] for i in range(len(lat_host))) - start if lat_host else 1.0
         srv.close()
-        return {"requests": count, "completed": len(lat), "failed": st["n_failed"],
-                "elements": int(sum(els)), "wall_s": wall, "elements_per_s": sum(els) / wall,
-                "requests_per_s": len(lat) / wall,
-                "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
-                "p50_ms_to_host": 1e3 * float(np.percentile(lat_host, 50)),
-                "p99_ms_to_host": 1e3 * float(np.percentile(lat_host, 99)),
-                "mean_batch": float(np.mean(batches)), "max_batch": int(np.max(batches)),
+        ok = [i for i in range(count) if lat[i] is not None]
+        L = np.array([lat[i] for i in ok])
+        LH = np.array([lat_host[i] for i in ok])
+        wall = max(t_arr[i] + lat_host[i] for i in ok) - start
+        ne_ok = int(sum(els[i] for i in ok))
+        return {"requests": count, "completed": len(ok), "failed": st["n_failed"], "fail_status": fails,
+                "elements": ne_ok, "wall_s": wall, "elements_per_s": ne_ok / wall, "requests_per_s": len(ok) / wall,
+                "p50_ms": 1e3 * float(np.percentile(L, 50)), "p99_ms": 1e3 * float(np.percentile(L, 99)),
+                "p50_ms_to_host": 1e3 * float(np.percentile(LH, 50)),
+                "p99_ms_to_host": 1e3 * float(np.percentile(LH, 99)),
+                "mean_batch": float(np.mean([bsz[i] for i in ok])), "max_batch": int(max(bsz[i] for i in ok)),
                 "batches": st["n_batches"], "ingested": st["n_ingested"], "reused": st["n_reused"],
-                "evicted": st["n_evicted"], "peak_bytes": st["peak_bytes"], "h2d_bytes": h2d[0], "d2h_bytes": d2h[0]}
+                "evicted": st["n_evicted"], "peak_bytes": st["peak_bytes"], "h2d_bytes": h2d[0], "d2h_bytes": sum(d2h)}
 
     calib = min(N, args.calib_requests)
     sus = run(vla.PREC_MIXED, 1.0, calib, closed=True)
@@ -560,6 +573,8 @@ def run_serve(args):
                                    f"element counts log-uniform in [1e3, 2e6] (snapped to {args.size_levels} sizes "
                                    f"per decade), 20% repeating a resident mesh with c(x)=a+b|x|^2, a,b~U(0.5,2)",
                        "budget_gb": args.budget_gb, "ingest_workers": args.ingest_workers,
+                       "client": f"inputs in pinned host memory, {n_poll} client threads copying results to pinned "
+                                 f"host memory",
                        "rates": "fractions of the sustained closed-loop rate", "sustained_req_per_s": rate0,
                        "precision": "mixed", "results": "K, M, vol copied to pinned host memory by the client"},
             "latency": {"p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"],
@@ -593,7 +608,8 @@ def main():
     ap.add_argument("--batch-lo", type=float, default=1e3)
     ap.add_argument("--batch-hi", type=float, default=1e6)
     ap.add_argument("--requests", type=int, default=10000)
-    ap.add_argument("--calib-requests", type=int, default=1000)
+    ap.add_argument("--calib-requests", type=int, default=3000)
+    ap.add_argument("--pollers", type=int, default=4)
     ap.add_argument("--size-levels", type=int, default=16)
     ap.add_argument("--budget-gb", type=int, default=100)
     ap.add_argument("--ingest-workers", type=int, default=4)

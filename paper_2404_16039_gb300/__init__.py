@@ -529,8 +529,11 @@ class Server:
 
     @staticmethod
     def _ptr(a, dtype):
-        if isinstance(a, torch.Tensor):
-            _req(a, dtype)
+        if isinstance(a, torch.Tensor):   # device tensor, or host tensor (pinned for full copy speed)
+            if a.is_cuda:
+                _req(a, dtype)
+            elif not a.is_contiguous() or a.dtype != dtype:
+                raise TypeError(f"expected a contiguous {dtype} tensor")
             return a, a.data_ptr()
         import numpy as np
         a = np.ascontiguousarray(a, dtype={torch.float64: np.float64, torch.int32: np.int32}[dtype])

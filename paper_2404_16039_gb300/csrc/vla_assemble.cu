@@ -1294,7 +1294,8 @@ struct vla_batch {
     WorkItem *d_work = nullptr;
     int *d_err = nullptr;
     unsigned long long *n_sing = nullptr;  // caller's per-job singular counts (device), or NULL
-    std::vector<MeshJob> h_jobs;
+    std::vector<MeshJob> h_jobs;          // host sources of the table copies: they live as long as the
+    std::vector<int32_t> order;           // batch (a one-shot batch frees them after its stream passes)
     std::vector<const vla_mesh *> meshes;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -1473,7 +1474,8 @@ vla_status batch_build(const vla_batch_job_t *jobs, int32_t count, int32_t preci
     // together, then run one type's code at a time), heaviest type first, larger
     // meshes first within a type (small tiles fill the tail)
     static const int type_rank[4] = {3, 1, 2, 0};   // rank of each type: P2 tets, P2 triangles, P1 tets, P1 triangles
-    std::vector<int32_t> order(count);
+    std::vector<int32_t> &order = b->order;
+    order.resize(count);
     for (int i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
         const int tx = type_rank[b->h_jobs[x].type], ty_ = type_rank[b->h_jobs[y].type];

@@ -20,6 +20,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 
 #include "vla_internal.cuh"
 
@@ -750,6 +751,25 @@ struct Scratch {  // temporary device buffers freed at the end of the build
 };
 
 
+// k_tile_sets takes a dynamic shared-memory size that depends on the mesh;
+// its limit is raised to the device maximum once per device (meshes built
+// concurrently on several host threads must not change it under each other)
+vla_status allow_max_smem_tile_sets() {
+    static std::mutex mu;
+    static bool done[64] = {};
+    int dev = 0, maxsm = 0;
+    VLA_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && done[dev]) return VLA_OK;
+    VLA_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    VLA_CUDA(cudaFuncGetAttributes(&fa, k_tile_sets));
+    VLA_CUDA(cudaFuncSetAttribute(k_tile_sets, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  maxsm - (int)fa.sharedSizeBytes));
+    if (dev >= 0 && dev < 64) done[dev] = true;
+    return VLA_OK;
+}
+
 // largest shared-memory footprint of a tile's assembly launch that still lets
 // two CTAs share an SM (VLA_TILE_SMEM_CAP overrides, for experiments)
 size_t tile_smem_cap() {
@@ -945,7 +965,14 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         TRY(S.get(&sc_nodes, (size_t)n_tiles * cap_n));
         TRY(S.get(&tcnt, n_tiles));
         const size_t smemA = sizeof(int32_t) * (cap_e + cap_n + std::max(cap_e, cap_n));
-        VLA_CUDA(cudaFuncSetAttribute(k_tile_sets, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smemA));
+        {
+            int dev_ = 0, maxsm_ = 0;
+            VLA_CUDA(cudaGetDevice(&dev_));
+            VLA_CUDA(cudaDeviceGetAttribute(&maxsm_, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_));
+            if (smemA + 1024 > (size_t)maxsm_)
+                return fail(VLA_ERR_UNSUPPORTED, "tile budget %d too large for the tile builder", B);
+        }
+        TRY(allow_max_smem_tile_sets());
         k_tile_sets<<<(int)n_tiles, 256, smemA, st>>>((int)n_tiles, nn, dim, nlb, cap_e, cap_n, tile_begin, perm,
                                                        m->n2e_ptr, m->n2e, m->elems, m->row_ptr, m->col_idx, node_tile,
                                                        sc_elems, sc_nodes, tcnt, d_err);

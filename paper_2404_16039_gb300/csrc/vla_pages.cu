@@ -10,6 +10,8 @@
 //    stores.  Misaligned pointers and the tail chunk take a plain path.
 //  * SoA layout (page index fastest): one page per thread, every load and
 //    store coalesced across the warp.
+#include <mutex>
+
 #include "vla_internal.cuh"
 
 namespace vla {
@@ -288,15 +290,19 @@ vla_status launch_op(int32_t layout, int64_t N, const void *in0, const void *in1
     int64_t staged = 0;
     if (n_chunks > 0 && al16(a) && al16(b) && al16(c) && al16(d)) {
         const size_t smem = (size_t)(2 * (OP::I0 + OP::I1) + OP::O0 + OP::O1) * kPagesPerChunk * sizeof(T);
-        static thread_local bool attr_done = false;
-        if (!attr_done) {
-            VLA_CUDA(cudaFuncSetAttribute(k_page_staged<OP, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)smem));
-            attr_done = true;
-        }
         int dev = 0;
         VLA_CUDA(cudaGetDevice(&dev));
         if (dev < 0 || dev >= 64) return fail(VLA_ERR_INVALID_ARG, "device ordinal %d not supported", dev);
+        {   // the staged kernel's shared-memory size is fixed per operation: set once per device
+            static std::mutex mu;
+            static bool attr_done[64] = {};
+            std::lock_guard<std::mutex> lk(mu);
+            if (!attr_done[dev]) {
+                VLA_CUDA(cudaFuncSetAttribute(k_page_staged<OP, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smem));
+                attr_done[dev] = true;
+            }
+        }
         if (!g_err_flag[dev]) {
             VLA_CUDA(cudaMalloc(&g_err_flag[dev], sizeof(int)));
             VLA_CUDA(cudaMemset(g_err_flag[dev], 0, sizeof(int)));

@@ -68,7 +68,7 @@ struct vla_server {
     vla_server_config_t cfg;
     int device = 0;
     std::mutex mu;
-    std::condition_variable sched_cv, ingest_cv, done_cv;
+    std::condition_variable sched_cv, ingest_cv, done_cv, reap_cv;
     std::unordered_map<int64_t, SReq *> reqs;
     std::deque<SReq *> queue;          // submitted, not admitted (arrival order)
     std::deque<SReq *> ingest_q;       // admitted, their mesh needs a build
@@ -88,7 +88,7 @@ struct vla_server {
     int64_t live = 0;                  // admitted requests not finished yet
     cudaStream_t astream = nullptr;    // assembly launches and output allocations
     cudaStream_t fstream = nullptr;    // frees
-    std::thread sched;
+    std::thread sched, reaper;
     std::vector<std::thread> workers;
 };
 
@@ -164,7 +164,11 @@ void admit(vla_server *s) {
             continue;
         }
         if (s->cfg.max_inflight > 0 && s->live >= s->cfg.max_inflight) return;
-        if (!make_room(s, mneed + oneed)) return;   // head of line waits for memory
+        // the mesh this request reuses must not be the one evicted to make room for it
+        if (m) m->refs++;
+        const bool room = make_room(s, mneed + oneed);
+        if (m) m->refs--;
+        if (!room) return;   // head of line waits for memory
         s->queue.pop_front();
         ++s->live;
         q->t_admit = now_s();
@@ -240,16 +244,7 @@ void scheduler(vla_server *s) {
     cudaSetDevice(s->device);
     std::unique_lock<std::mutex> lk(s->mu);
     while (true) {
-        if (!s->dead.empty() || !s->dead_out.empty()) {
-            std::vector<SMesh *> dead;
-            std::vector<void *> outs;
-            dead.swap(s->dead);
-            outs.swap(s->dead_out);
-            lk.unlock();
-            destroy_dead(s, dead, outs);
-            lk.lock();
-            continue;
-        }
+        if (!s->dead.empty() || !s->dead_out.empty()) s->reap_cv.notify_one();
         if (s->stop && s->queue.empty() && s->ingest_q.empty() && s->ready.empty() && !s->inflight) {
             bool busy = false;
             for (auto &kv : s->reqs)
@@ -257,6 +252,7 @@ void scheduler(vla_server *s) {
             if (!busy) break;
         }
         admit(s);
+        if (!s->dead.empty()) s->reap_cv.notify_one();   // evictions made room
         if (!s->inflight && !s->ready.empty()) {
             std::vector<SReq *> take;
             const size_t cap = s->cfg.max_batch > 0 ? (size_t)s->cfg.max_batch : s->ready.size();
@@ -325,6 +321,23 @@ void scheduler(vla_server *s) {
             continue;
         }
         s->sched_cv.wait(lk);
+    }
+}
+
+// frees evicted or released meshes and outputs off the scheduler's path
+void reaper(vla_server *s) {
+    cudaSetDevice(s->device);
+    std::unique_lock<std::mutex> lk(s->mu);
+    while (true) {
+        while (s->dead.empty() && s->dead_out.empty() && !s->stop) s->reap_cv.wait(lk);
+        if (s->dead.empty() && s->dead_out.empty()) break;   // stopping, nothing left
+        std::vector<SMesh *> dead;
+        std::vector<void *> outs;
+        dead.swap(s->dead);
+        outs.swap(s->dead_out);
+        lk.unlock();
+        destroy_dead(s, dead, outs);
+        lk.lock();
     }
 }
 
@@ -437,6 +450,7 @@ extern "C" vla_status vla_server_create(const vla_server_config_t *cfg, vla_serv
         return cuda_fail(e, "server streams");
     }
     s->sched = std::thread(scheduler, s);
+    s->reaper = std::thread(reaper, s);
     for (int i = 0; i < s->cfg.ingest_workers; ++i) s->workers.emplace_back(ingest_worker, s);
     *out = s;
     return VLA_OK;
@@ -535,6 +549,7 @@ extern "C" vla_status vla_server_release(vla_server *s, int64_t ticket) {
         delete q;
     }
     s->sched_cv.notify_all();
+    s->reap_cv.notify_one();
     return VLA_OK;
 }
 
@@ -576,6 +591,8 @@ extern "C" vla_status vla_server_destroy(vla_server *s) {
     s->done_cv.notify_all();
     for (auto &w : s->workers) w.join();
     if (s->sched.joinable()) s->sched.join();
+    s->reap_cv.notify_all();
+    if (s->reaper.joinable()) s->reaper.join();
     cudaStreamSynchronize(s->astream);
     std::vector<SMesh *> dead = s->meshes;
     dead.insert(dead.end(), s->dead.begin(), s->dead.end());
