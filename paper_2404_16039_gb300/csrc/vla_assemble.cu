@@ -418,9 +418,10 @@ __device__ __forceinline__ T coeff(int kind, T ca, T cb, const T *xc, int dim) {
     return ca + cb * r2;
 }
 
+// a . b with a fixed rounding sequence
 template <typename T>
 __device__ __forceinline__ T dot3(const T *a, const T *b) {
-    return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+    return fma_t(a[2], b[2], fma_t(a[1], b[1], a[0] * b[0]));
 }
 
 // Mixed precision fast path: edge vectors rounded once to float, Kahan 2x2
@@ -627,11 +628,40 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
     const int kind = J.kind;
     double *const vol = J.vol, *const Kp = J.Kp, *const Mp = J.Mp;
     unsigned long long *const n_sing = J.n_sing;
-    for (int e = threadIdx.x; e <= h.n_elems; e += kThreads) {
+    // vol, singular count and optional pages of an element the tile owns
+    auto owned = [&](int e, T det, T adet, T mscale, const T *dst) {
+        const int64_t k = s_gid[e];
+        if (det == T(0) && n_sing) atomicAdd(n_sing, 1ull);
+        if (vol) {
+            if constexpr (MIX) vol[k] = f32_to_f64(adet * (float)(1.0 / C::DFACT));
+            else vol[k] = adet / C::DFACT;
+        }
+        if (Kp || Mp) {
+            for (int a = 0; a < C::NLB; ++a)
+                for (int q = 0; q < C::NLB; ++q) {
+                    const int p0 = a < q ? a : q, p1 = a < q ? q : a;
+                    const int u = p0 * C::NLB - p0 * (p0 - 1) / 2 + (p1 - p0);
+                    const int64_t pos = k * C::NLB * C::NLB + a + (int64_t)q * C::NLB;
+                    const T kv = dst[u];
+                    T mv;
+                    if constexpr (ORDER == 1) mv = mscale * (a == q ? T(2) : T(1));
+                    else mv = mscale * mhat[u];
+                    if constexpr (MIX) {
+                        if (Kp) Kp[pos] = f32_to_f64(kv);
+                        if (Mp) Mp[pos] = f32_to_f64(mv);
+                    } else {
+                        if (Kp) Kp[pos] = kv;
+                        if (Mp) Mp[pos] = mv;
+                    }
+                }
+        }
+    };
+    // one element (index n_elems is the zero record)
+    auto elem = [&](int e) {
         T *dst = s_k + (size_t)e * C::RS;
         if (e == h.n_elems) {
             for (int u = 0; u < C::RS; ++u) dst[u] = T(0);
-            continue;
+            return;
         }
         const ushort4 v = s_rec[e];
         Geo<T> g;
@@ -676,34 +706,9 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
             mscale = c * adet * T(1.0 / C::DFACT);           // c |T|; entries scale the reference mass
             dst[C::NU] = mscale;
         }
-        if (e < h.n_own) {
-            const int64_t k = s_gid[e];
-            if (g.det == T(0) && n_sing) atomicAdd(n_sing, 1ull);
-            if (vol) {
-                if constexpr (MIX) vol[k] = f32_to_f64(adet * (float)(1.0 / C::DFACT));
-                else vol[k] = adet / C::DFACT;
-            }
-            if (Kp || Mp) {
-                for (int a = 0; a < C::NLB; ++a)
-                    for (int q = 0; q < C::NLB; ++q) {
-                        const int p0 = a < q ? a : q, p1 = a < q ? q : a;
-                        const int u = p0 * C::NLB - p0 * (p0 - 1) / 2 + (p1 - p0);
-                        const int64_t pos = k * C::NLB * C::NLB + a + (int64_t)q * C::NLB;
-                        const T kv = dst[u];
-                        T mv;
-                        if constexpr (ORDER == 1) mv = mscale * (a == q ? T(2) : T(1));
-                        else mv = mscale * mhat[u];
-                        if constexpr (MIX) {
-                            if (Kp) Kp[pos] = f32_to_f64(kv);
-                            if (Mp) Mp[pos] = f32_to_f64(mv);
-                        } else {
-                            if (Kp) Kp[pos] = kv;
-                            if (Mp) Mp[pos] = mv;
-                        }
-                    }
-            }
-        }
-    }
+        if (e < h.n_own) owned(e, g.det, adet, mscale, dst);
+    };
+    for (int e = threadIdx.x; e <= h.n_elems; e += kThreads) elem(e);
 }
 
 // Phase 2 of a tile: the pairs {i, j} of its rows, sorted by contribution
