@@ -119,13 +119,17 @@ class ClockSampler:
 
 
 def _dist():
+    """(dist module or None, rank, world size, local rank) from the torchrun
+    environment; NCCL on GPUs, gloo otherwise (the CPU tests of this harness)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
         import torch.distributed as dist
         import torch
         local = int(os.environ.get("LOCAL_RANK", "0"))
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        cuda = torch.cuda.is_available()
+        if cuda:
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if cuda else "gloo")
         return dist, dist.get_rank(), ws, local
     return None, 0, 1, 0
 
@@ -139,9 +143,14 @@ def _max_over_ranks(dist, x):
     if dist is None:
         return x
     import torch
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def _job_value(ws, units_per_rank, ms):
+    """Whole-job throughput: every rank processes units_per_rank in (at most) ms."""
+    return ws * units_per_rank / (ms * 1e-3)
 
 
 def _alg_bytes_per_el(ne, nn, nnz):
@@ -348,7 +357,7 @@ def run_batch(args):
             d = torch.linalg.vector_norm(a[k] - b[k]).item() / max(torch.linalg.vector_norm(b[k]).item(), 1e-300)
             err[k] = max(err[k], d)
     ms = _max_over_ranks(dist, float(np.median(ms_mix)))
-    value = ws * ne / (ms * 1e-3)
+    value = _job_value(ws, ne, ms)
     peaks, src = _peaks()
     achieved = alg / (float(np.median(ms_mix)) * 1e-3) / 1e9
 
@@ -677,7 +686,7 @@ def main():
     asm_ms = [a.elapsed_time(b) for a, b, c in ev]
     ms = _max_over_ranks(dist, sum(step_ms) / len(step_ms))
     asm = sum(asm_ms) / len(asm_ms)
-    value = ws * gm.ne / (ms * 1e-3)
+    value = _job_value(ws, gm.ne, ms)
 
     # end to end through the public API with pinned host buffers
     hc = torch.from_numpy(m.coords).pin_memory()
