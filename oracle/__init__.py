@@ -67,6 +67,13 @@ def _load():
         lib.orc_boundary.restype = _i64
         lib.orc_count_facets.argtypes = [C.c_int, _i64, C.c_int, _i, C.POINTER(_i64), C.POINTER(_i64)]
         lib.orc_count_facets.restype = C.c_int
+        lib.orc_quad_rule.argtypes = [C.c_int, C.c_int, _d, _d]
+        lib.orc_quad_rule.restype = C.c_int
+        lib.orc_quad_points.argtypes = [C.c_int, C.c_int, _i64, C.c_int, _i, _d, C.c_int, _d, _d]
+        lib.orc_gi.argtypes = [_i64, C.c_int, C.c_int, _d, _d, _d, vp, _d]
+        lib.orc_rhs.argtypes = [C.c_int, C.c_int, _i64, _i64, C.c_int, _i, _d, C.c_int, _d, _d, _d, _d, _d]
+        lib.orc_energies.argtypes = [_i64, C.c_int, _i, _d, _d, _d, _d, _d]
+        lib.orc_avtamav.argtypes = [_i64, C.c_int, _d, _d, _d, _d]
         _lib = lib
         return lib
 
@@ -254,3 +261,67 @@ def to_dense(nn, row_ptr, col_idx, vals):
         for q in range(row_ptr[r], row_ptr[r + 1]):
             D[r, col_idx[q]] += vals[q]
     return D
+
+
+# --------------------------------------------------------------------------
+# quadrature, integrals, load vector, energies (Sections 3.4, 3.5)
+# --------------------------------------------------------------------------
+
+def quad_rule(sdim, gqo):
+    """(ip (nip, sdim+1) barycentric points, w (nip,) weights summing to 1)."""
+    ip = np.zeros((8, sdim + 1))
+    w = np.zeros(8)
+    nip = _load().orc_quad_rule(sdim, gqo, ip, w)
+    if nip < 0:
+        raise ValueError(f"no rule for simplex dimension {sdim}, order {gqo}")
+    return ip[:nip].copy(), w[:nip].copy()
+
+
+def quad_points(dim, cells, coords, ip):
+    """X (n, nip, dim): quadrature points of the simplices cells (n, >= nvert)."""
+    cells, coords, ip = _i32(cells), _f64(coords), _f64(ip)
+    n, stride = cells.shape
+    nip, nvert = ip.shape
+    X = np.empty((max(n, 1), nip, dim))
+    _load().orc_quad_points(dim, nvert, n, stride, cells, coords, nip, ip, X)
+    return X[:n]
+
+
+def gi(fip, w, sizes, normals=None):
+    """GI of Section 3.4: fip (n, nip, d).  Returns the d component integrals, or
+    the flux through the simplices (a scalar) when normals (n, d) are given."""
+    fip, w, sizes = _f64(fip), _f64(w), _f64(sizes)
+    n, nip, d = fip.shape
+    out = np.zeros(max(d, 1))
+    nr = None if normals is None else _f64(normals)
+    _load().orc_gi(n, nip, d, fip, w, sizes, None if nr is None else nr.ctypes.data_as(C.c_void_p), out)
+    return out[0] if normals is not None else out
+
+
+def rhs(dim, order, nn, elems, coords, ip, w, fip):
+    """Load vector b (nn,) and element contributions b2D (ne, nlb) for f given at
+    the rule's points (fip (ne, nip))."""
+    elems, coords, ip, w, fip = _i32(elems), _f64(coords), _f64(ip), _f64(w), _f64(fip)
+    ne, nlb = elems.shape
+    b = np.empty(nn)
+    b2D = np.empty((max(ne, 1), nlb))
+    _load().orc_rhs(dim, order, nn, ne, nlb, elems, coords, ip.shape[0], ip, w, fip, b, b2D)
+    return b, b2D[:ne]
+
+
+def energies(elems, u, K3D, M3D, b2D):
+    """Local energies (ne, 3): u_k^T K_k u_k / 2, u_k^T M_k u_k / 2, -b2D_k^T u_k."""
+    elems, u, K3D, M3D, b2D = _i32(elems), _f64(u), _f64(K3D), _f64(M3D), _f64(b2D)
+    ne, nlb = elems.shape
+    J = np.empty((max(ne, 1), 3))
+    _load().orc_energies(ne, nlb, elems, u, K3D, M3D, b2D, J)
+    return J[:ne]
+
+
+def avtamav(v, A, w):
+    """out_k = v_k^T A_k w_k; v, w (N, n); A (N, n, n) pages (N, cols, rows)."""
+    v, A, w = _f64(v), _f64(A), _f64(w)
+    N, n = v.shape
+    out = np.empty(max(N, 1))
+    _load().orc_avtamav(N, n, v, A, w, out)
+    return out[:N]

@@ -599,3 +599,159 @@ int orc_count_facets(int dim, int64_t ne, int nlb, const int32_t *elems, int64_t
     free(f);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* quadrature on simplices (Section 3.4 Gauss_points, Section 3.5 intquad)  */
+/* ------------------------------------------------------------------------ */
+
+/* Symmetric rules in barycentric coordinates, weights summing to 1 (the
+ * "averaged" normalisation of Gauss_points; intquad's weights are these
+ * times 1/dim!).  gqo is the degree of exactness.  sdim is the simplex
+ * dimension (1 segment, 2 triangle, 3 tetrahedron).  Published rules:
+ *   segment   gqo 1: midpoint;  gqo 2-3: Gauss-Legendre, 1/2 +- 1/(2 sqrt 3).
+ *   triangle  gqo 1: centroid;  gqo 2: (2/3,1/6,1/6) and permutations, 1/3 each;
+ *             gqo 3: centroid -27/48, (3/5,1/5,1/5) and permutations 25/48.
+ *   tet       gqo 1: centroid;  gqo 2: (a,b,b,b) and permutations, 1/4 each,
+ *             a = (5 + 3 sqrt 5)/20, b = (5 - sqrt 5)/20;
+ *             gqo 3: centroid -4/5, (1/2,1/6,1/6,1/6) and permutations 9/20.
+ * ip: (sdim+1) x nip column-major (point q at q*(sdim+1)).  Returns nip, or
+ * -1 for an unsupported (sdim, gqo). */
+int orc_quad_rule(int sdim, int gqo, double *ip, double *w) {
+    const int nv = sdim + 1;
+    int nip = 0;
+    if (gqo < 1 || gqo > 3 || sdim < 1 || sdim > 3) return -1;
+    if (gqo == 1) {
+        for (int j = 0; j < nv; ++j) ip[j] = 1.0 / nv;
+        w[0] = 1.0;
+        return 1;
+    }
+    if (sdim == 1) {
+        const double d = 0.5 / sqrt(3.0);
+        ip[0] = 0.5 + d, ip[1] = 0.5 - d;
+        ip[2] = 0.5 - d, ip[3] = 0.5 + d;
+        w[0] = w[1] = 0.5;
+        return 2;
+    }
+    /* centroid (gqo 3) then one orbit of points with one distinguished coordinate */
+    double big, small, wc = 0.0, wo;
+    if (sdim == 2) {
+        if (gqo == 2) big = 2.0 / 3.0, small = 1.0 / 6.0, wo = 1.0 / 3.0;
+        else big = 0.6, small = 0.2, wc = -27.0 / 48.0, wo = 25.0 / 48.0;
+    } else {
+        if (gqo == 2) big = (5.0 + 3.0 * sqrt(5.0)) / 20.0, small = (5.0 - sqrt(5.0)) / 20.0, wo = 0.25;
+        else big = 0.5, small = 1.0 / 6.0, wc = -0.8, wo = 9.0 / 20.0;
+    }
+    if (gqo == 3) {
+        for (int j = 0; j < nv; ++j) ip[nip * nv + j] = 1.0 / nv;
+        w[nip++] = wc;
+    }
+    for (int i = 0; i < nv; ++i) {
+        for (int j = 0; j < nv; ++j) ip[nip * nv + j] = (i == j) ? big : small;
+        w[nip++] = wo;
+    }
+    return nip;
+}
+
+/* Coordinates of the quadrature points of n simplices (elements or facets):
+ * X(:,q,k) = sum_j ip(j,q) x_{cells(k,j)} -- the paper's X_ip =
+ * amsm(coords3D, ip), dim x nip x n.  cells: stride entries per simplex, the
+ * first nvert of which are its vertices. */
+void orc_quad_points(int dim, int nvert, int64_t n, int stride, const int32_t *cells, const double *coords, int nip,
+                     const double *ip, double *X) {
+    for (int64_t k = 0; k < n; ++k)
+        for (int q = 0; q < nip; ++q)
+            for (int d = 0; d < dim; ++d) {
+                double s = 0.0;
+                for (int j = 0; j < nvert; ++j) s += ip[q * nvert + j] * coords[(int64_t)cells[k * stride + j] * dim + d];
+                X[(k * nip + q) * dim + d] = s;
+            }
+}
+
+/* The GI function of Section 3.4: value = sum_k sizes_k sum_q w_q f(:,q,k),
+ * f of d components (fip: d x nip x n).  With normals (d x n) the components
+ * are dotted with the simplex's normal first and out[0] is the scalar
+ * integral; without, out[c] is the integral of component c. */
+void orc_gi(int64_t n, int nip, int d, const double *fip, const double *w, const double *sizes, const double *normals,
+            double *out) {
+    for (int c = 0; c < d; ++c) out[c] = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        double avg[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int c = 0; c < d; ++c)
+            for (int q = 0; q < nip; ++q) avg[c] += w[q] * fip[(k * nip + q) * d + c];
+        if (normals) {
+            double dot = 0.0;
+            for (int c = 0; c < d; ++c) dot += avg[c] * normals[k * d + c];
+            out[0] += sizes[k] * dot;
+        } else {
+            for (int c = 0; c < d; ++c) out[c] += sizes[k] * avg[c];
+        }
+    }
+}
+
+/* local basis function j at barycentric point lam (P1: lambda_j; P2 as in
+ * p2_basis) */
+static double basis_at(int dim, int order, int j, const double *lam) {
+    if (order == 1) return lam[j];
+    poly_t p;
+    p2_basis(dim, j, &p);
+    double v = 0.0;
+    for (int t = 0; t < p.nterm; ++t) {
+        double m = p.coef[t];
+        for (int s = 0; s <= dim; ++s)
+            for (int e = 0; e < p.alpha[t][s]; ++e) m *= lam[s];
+        v += m;
+    }
+    return v;
+}
+
+/* Right-hand side vector of Section 3.5 (rhs_vectorP1, and its P2 analogue):
+ * b2D(j,k) = |T_k| sum_q w_q f(x_q) phi_j(ip_q) with f given at the rule's
+ * points (fip: nip x ne), then b = accumarray(elems(:), b2D(:)). */
+void orc_rhs(int dim, int order, int64_t nn, int64_t ne, int nlb, const int32_t *elems, const double *coords, int nip,
+             const double *ip, const double *w, const double *fip, double *b, double *b2D) {
+    double *vol = (double *)malloc((size_t)(ne > 0 ? ne : 1) * sizeof(double));
+    orc_volumes(dim, ne, nlb, elems, coords, vol, NULL);
+    for (int64_t i = 0; i < nn; ++i) b[i] = 0.0;
+    for (int64_t k = 0; k < ne; ++k)
+        for (int j = 0; j < nlb; ++j) {
+            double s = 0.0;
+            for (int q = 0; q < nip; ++q) s += w[q] * fip[k * nip + q] * basis_at(dim, order, j, ip + q * (dim + 1));
+            b2D[k * nlb + j] = vol[k] * s;
+        }
+    for (int64_t k = 0; k < ne; ++k)
+        for (int j = 0; j < nlb; ++j) b[elems[k * nlb + j]] += b2D[k * nlb + j];
+    free(vol);
+}
+
+/* Local energies of Section 3.5 (eq. Jk_comps): with u_k the element's nodal
+ * values, J(0,k) = u_k^T K_k u_k / 2, J(1,k) = u_k^T M_k u_k / 2,
+ * J(2,k) = -b2D(:,k)^T u_k (b2D the element's own load contributions, so that
+ * the J(.,k) sum to the global forms). */
+void orc_energies(int64_t ne, int nlb, const int32_t *elems, const double *u, const double *K3D, const double *M3D,
+                  const double *b2D, double *J) {
+    for (int64_t k = 0; k < ne; ++k) {
+        double uk[10];
+        for (int j = 0; j < nlb; ++j) uk[j] = u[elems[k * nlb + j]];
+        double a = 0.0, m = 0.0, f = 0.0;
+        for (int i = 0; i < nlb; ++i)
+            for (int j = 0; j < nlb; ++j) {
+                a += uk[i] * K3D[k * nlb * nlb + i + j * nlb] * uk[j];
+                m += uk[i] * M3D[k * nlb * nlb + i + j * nlb] * uk[j];
+            }
+        for (int j = 0; j < nlb; ++j) f += b2D[k * nlb + j] * uk[j];
+        J[k * 3 + 0] = 0.5 * a;
+        J[k * 3 + 1] = 0.5 * m;
+        J[k * 3 + 2] = -f;
+    }
+}
+
+/* out_k = v_k^T A_k w_k (Section 2.4, avtamav), v_k and w_k n-vectors,
+ * A_k n x n column-major. */
+void orc_avtamav(int64_t N, int n, const double *v, const double *A, const double *w, double *out) {
+    for (int64_t k = 0; k < N; ++k) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) s += v[k * n + i] * A[k * n * n + i + j * n] * w[k * n + j];
+        out[k] = s;
+    }
+}
