@@ -231,6 +231,60 @@ vla_status vla_mesh_destroy(vla_mesh *mesh);
 vla_status vla_mesh_check(vla_mesh *mesh, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Quadrature, integrals, load vector, energies (Sections 3.4, 3.5)          */
+/* ------------------------------------------------------------------------ */
+
+/* The quadrature rule of Gauss_points(gqo, sdim) (Section 3.4) on a simplex of
+ * dimension sdim (1 segment, 2 triangle, 3 tetrahedron), degree of exactness
+ * gqo = 1..3: barycentric points ip ((sdim+1) x nip, point q at
+ * q*(sdim+1)) and weights w (nip) summing to 1 (intquad's weights of
+ * Section 3.5 are these times 1/sdim!).  Host arrays of at least 8 points;
+ * any may be NULL.  VLA_ERR_UNSUPPORTED for other degrees. */
+vla_status vla_quad_rule(int32_t sdim, int32_t gqo, int32_t *nip, double *ip, double *w);
+
+/* Quadrature points X_ip = amsm(coords3D, ip) (Section 3.4): for every element
+ * (facets = 0) or every boundary facet (facets = 1) and every point q of the
+ * degree-gqo rule, X(:, q, k) = sum_j ip(j, q) x_j.  X: dim x nip x n FP64
+ * column-major (device), n = ne or nfb.  FP64 arithmetic. */
+vla_status vla_quad_points(const vla_mesh *mesh, int32_t gqo, int32_t facets, double *X, void *stream);
+
+/* The GI function of Section 3.4: value = sum_k sizes_k sum_q w_q f(:, q, k).
+ *   fip: d x nip x n FP64 (device) -- f at the points of n simplices;
+ *   w: nip host weights (nip <= 8); sizes: n FP64 (device) element volumes or
+ *   facet areas; normals: d x n (device) or NULL.
+ * Without normals out[c] (device, d <= 4 values) is the integral of component
+ * c; with normals out[0] is the flux sum_k sizes_k (avg_k f) . n_k.  The sum is
+ * reduced in a fixed order (bit-reproducible).  Allocates stream-ordered
+ * scratch. */
+vla_status vla_gi(int64_t n, int32_t nip, int32_t d, const double *fip, const double *w, const double *sizes,
+                  const double *normals, double *out, void *stream);
+
+/* Load vector of Section 3.5 (rhs_vectorP1; P2 alike):
+ * b2D(j, k) = |T_k| sum_q w_q f(x_q) phi_j(ip_q) for the degree-gqo rule, then
+ * b = accumarray(elems(:), b2D(:)) in a fixed order (each node's incident
+ * elements ascending).  fip: nip x ne FP64 (device) -- f at the points given by
+ * vla_quad_points(mesh, gqo, 0, ...).  b: nn (device) or NULL; b2D: nlb x ne
+ * (device) or NULL (then scratch).  FP64. */
+vla_status vla_rhs(const vla_mesh *mesh, int32_t gqo, const double *fip, double *b, double *b2D, void *stream);
+
+/* Local energies of Section 3.5 (eq. Jk_comps): with u_k the element's nodal
+ * values of u (nn FP64, device),
+ *   J_local(0,k) = u_k^T K_k u_k / 2,  J_local(1,k) = u_k^T M_k u_k / 2,
+ *   J_local(2,k) = -b2D(:,k)^T u_k,
+ * from the element pages of vla_assemble (K_pages, M_pages: nlb x nlb x ne) and
+ * the element loads of vla_rhs (b2D: nlb x ne); any of the three may be NULL
+ * (its energy is then 0).  J_local: 3 x ne (device) or NULL; J_total: 3 values
+ * (device) or NULL -- the sums over elements, i.e. u^T K u / 2, u^T M u / 2 and
+ * -b^T u, reduced in a fixed order.  FP64. */
+vla_status vla_energies(const vla_mesh *mesh, const double *u, const double *K_pages, const double *M_pages,
+                        const double *b2D, double *J_local, double *J_total, void *stream);
+
+/* out_k = v_k^T A_k w_k (Section 2.4, avtamav): v, w n x N, A n x n x N
+ * (VLA_LAYOUT_PAGE, column-major pages) or the SoA layout; out N.  n <= 16. */
+vla_status vla_avtamav(int32_t dtype, int32_t layout, int64_t N, int32_t n, const void *v, const void *A,
+                       const void *w, void *out, void *stream);
+
+/* ------------------------------------------------------------------------ */
 /* Batched assembly (Section 3.5 assembly over many meshes at once)          */
 /* ------------------------------------------------------------------------ */
 /* The paper assembles one mesh per call; a batch runs the same computation

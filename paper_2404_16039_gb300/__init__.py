@@ -21,7 +21,8 @@ import torch
 
 __all__ = [
     "VlaError", "lib", "version", "amtam", "astam", "avtam", "amdet", "aminv", "Mesh", "element_pages_static",
-    "Batch", "batch_assemble", "autotune", "tune_get", "tune_set", "Server", "PENDING", "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP",
+    "Batch", "batch_assemble", "autotune", "tune_get", "tune_set", "Server", "PENDING", "quad_rule", "gi",
+    "avtamav", "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP",
 ]
 
 F32, F64 = 0, 1
@@ -134,6 +135,12 @@ def lib():
         L.vla_autotune.argtypes = [i32, i32, i32, i64, i64, vp, vp, i32, vp, C.POINTER(Tune)]
         L.vla_tune_get.argtypes = [i32, i32, i32, C.POINTER(Tune)]
         L.vla_tune_set.argtypes = [i32, i32, i32, C.POINTER(Tune)]
+        L.vla_quad_rule.argtypes = [i32, i32, C.POINTER(i32), C.POINTER(dbl), C.POINTER(dbl)]
+        L.vla_quad_points.argtypes = [vp, i32, i32, vp, vp]
+        L.vla_gi.argtypes = [i64, i32, i32, vp, C.POINTER(dbl), vp, vp, vp, vp]
+        L.vla_rhs.argtypes = [vp, i32, vp, vp, vp, vp]
+        L.vla_energies.argtypes = [vp, vp, vp, vp, vp, vp, vp, vp]
+        L.vla_avtamav.argtypes = [i32, i32, i64, i32, vp, vp, vp, vp, vp]
         L.vla_server_create.argtypes = [C.POINTER(ServerConfig), C.POINTER(vp)]
         L.vla_server_submit.argtypes = [vp, C.POINTER(Request), C.POINTER(i64)]
         L.vla_server_poll.argtypes = [vp, i64, dbl, C.POINTER(Result)]
@@ -146,7 +153,8 @@ def lib():
                      "vla_batch_set_job", "vla_batch_run", "vla_batch_info", "vla_batch_check", "vla_batch_destroy",
                      "vla_batch_assemble", "vla_autotune", "vla_tune_get", "vla_tune_set", "vla_server_create",
                      "vla_server_submit", "vla_server_poll", "vla_server_release", "vla_server_stats",
-                     "vla_server_destroy"):
+                     "vla_server_destroy", "vla_quad_rule", "vla_quad_points", "vla_gi", "vla_rhs", "vla_energies",
+                     "vla_avtamav"):
             getattr(L, name).restype = i32
         _lib = L
         return L
@@ -354,6 +362,36 @@ class Mesh:
             areas = torch.empty(max(self.nfb, 1), dtype=torch.float64, device=dev)[: self.nfb]
         _check(lib().vla_boundary(self._h, precision, _p(normals), _p(areas), _stream(stream)))
         return normals, areas
+
+    def quad_points(self, gqo, facets=False, stream=None):
+        """Quadrature points (n, nip, dim) of the elements (or boundary facets)
+        for the degree-gqo rule (vla_quad_points)."""
+        nip = quad_rule(self.dim - 1 if facets else self.dim, gqo)[1].shape[0]
+        n = self.nfb if facets else self.ne
+        X = torch.empty((max(n, 1), nip, self.dim), dtype=torch.float64, device=self.device)[:n]
+        _check(lib().vla_quad_points(self._h, gqo, 1 if facets else 0, _p(X), _stream(stream)))
+        return X
+
+    def rhs(self, gqo, fip, b=None, b2D=None, want_b2D=True, stream=None):
+        """Load vector b (nn,) and element loads b2D (ne, nlb) for f at the
+        degree-gqo points (fip (ne, nip)) (vla_rhs)."""
+        _req(fip, torch.float64)
+        dev = self.device
+        if b is None:
+            b = torch.empty(self.nn, dtype=torch.float64, device=dev)
+        if want_b2D and b2D is None:
+            b2D = torch.empty((self.ne, self.nlb), dtype=torch.float64, device=dev)
+        _check(lib().vla_rhs(self._h, gqo, _p(fip), _p(b), _p(b2D) if want_b2D else None, _stream(stream)))
+        return b, (b2D if want_b2D else None)
+
+    def energies(self, u, K3D=None, M3D=None, b2D=None, local=True, stream=None):
+        """Local energies (ne, 3) and their sums (3,) (vla_energies)."""
+        _req(u, torch.float64)
+        dev = self.device
+        J = torch.empty((self.ne, 3), dtype=torch.float64, device=dev) if local else None
+        tot = torch.empty(3, dtype=torch.float64, device=dev)
+        _check(lib().vla_energies(self._h, _p(u), _p(K3D), _p(M3D), _p(b2D), _p(J), _p(tot), _stream(stream)))
+        return J, tot
 
     def check(self, stream=None):
         """Raises VlaError (VLA_ERR_TIMEOUT) if a bounded wait of a kernel on
@@ -601,3 +639,45 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# quadrature and integrals
+# ---------------------------------------------------------------------------
+
+def quad_rule(sdim, gqo):
+    """(ip (nip, sdim+1), w (nip,)) of the degree-gqo rule on an sdim-simplex."""
+    import numpy as np
+    n = C.c_int32()
+    ip = (C.c_double * 32)()
+    w = (C.c_double * 8)()
+    _check(lib().vla_quad_rule(sdim, gqo, C.byref(n), ip, w))
+    k = n.value
+    return (np.array(ip[: k * (sdim + 1)]).reshape(k, sdim + 1), np.array(w[:k]))
+
+
+def gi(fip, w, sizes, normals=None, stream=None):
+    """GI of Section 3.4 on the device: fip (n, nip, d), w (nip,) host weights,
+    sizes (n,), normals (n, d) or None.  Returns a (d,) tensor, or a (1,)
+    tensor holding the flux when normals are given."""
+    _req(fip, torch.float64), _req(sizes, torch.float64)
+    if normals is not None:
+        _req(normals, torch.float64)
+    n, nip, d = fip.shape
+    out = torch.empty(d if normals is None else 1, dtype=torch.float64, device=fip.device)
+    wa = (C.c_double * nip)(*[float(x) for x in w])
+    _check(lib().vla_gi(n, nip, d, _p(fip), wa, _p(sizes), _p(normals), _p(out), _stream(stream)))
+    return out
+
+
+def avtamav(v, A, w, out=None, layout=LAYOUT_PAGE, stream=None):
+    """out_k = v_k^T A_k w_k.  Page layout: v, w (N, n); A (N, n, n) (N, cols, rows)."""
+    _req(v), _req(A), _req(w)
+    if layout == LAYOUT_PAGE:
+        N, n = v.shape
+    else:
+        n, N = v.shape
+    if out is None:
+        out = torch.empty(N, dtype=v.dtype, device=v.device)
+    _check(lib().vla_avtamav(_dtype_code(v), layout, N, n, _p(v), _p(A), _p(w), _p(out), _stream(stream)))
+    return out
