@@ -304,16 +304,54 @@ static void p2_grad(int dim, const poly_t *p, gpoly_t *g) {
 /* Element matrices of element k, P1 or P2, into Kp, Mp (nlb x nlb col-major):
  *   K_k(p,q) = c_k * int_T grad phi_p . grad phi_q,
  *   M_k(p,q) = c_k * int_T phi_p phi_q,
- * with c_k the centroid coefficient.  P1: K_k = c_k vol G^T G,
+ * with c_k the centroid coefficient (kinds 0, 1); kinds 2, 3 (P1 only) take
+ * the coefficient of kind 0, 1 at the points of the degree-2 rule instead.  P1: K_k = c_k vol G^T G,
  * M_k = c_k vol (1 + delta_pq) / ((dim+1)(dim+2)) (Section 3.5 stiffness and
  * mass listings; the integrals are evaluated exactly).  Returns signed det. */
+int orc_quad_rule(int sdim, int gqo, double *ip, double *w);
+
+/* coefficient at a point x: kind 0 a + b |x|^2, kind 1 a exp(b sum x) */
+static double point_coeff(int dim, int kind, double ca, double cb, const double *x) {
+    double r2 = 0.0, sum = 0.0;
+    for (int d = 0; d < dim; ++d) {
+        r2 += x[d] * x[d];
+        sum += x[d];
+    }
+    return kind == 1 ? ca * exp(cb * sum) : ca + cb * r2;
+}
+
 static double element_matrices(int dim, int order, int nlb, const int32_t *elems, const double *coords, int64_t k,
                                int ckind, double ca, double cb, double *Kp, double *Mp, double *c_out) {
     double V[9], glam[12];
     simplex_vectors(dim, nlb, elems, coords, k, V);
     double d = bary_gradients(dim, V, glam);
     double vol = fabs(d) / factorial(dim);
-    double c = centroid_coeff(dim, dim + 1, nlb, elems, coords, k, ckind, ca, cb);
+    if (ckind >= 2 && order == 1) {
+        /* the paper's literal P1 listing (stiffness_matrixP1, Section 3.5): the
+         * degree-2 rule (gqo = 2) with the coefficient evaluated at every point;
+         * the mass matrix the same way: M(p,q) = vol sum_i w_i c(x_i) lambda_p lambda_q */
+        double ip[32], w[8], cq[8];
+        const int nip = orc_quad_rule(dim, 2, ip, w);
+        double cK = 0.0;
+        for (int i = 0; i < nip; ++i) {
+            double x[3] = {0, 0, 0};
+            for (int j = 0; j <= dim; ++j)
+                for (int r = 0; r < dim; ++r) x[r] += ip[i * (dim + 1) + j] * coords[(int64_t)elems[k * nlb + j] * dim + r];
+            cq[i] = point_coeff(dim, ckind - 2, ca, cb, x);
+            cK += w[i] * cq[i];
+        }
+        if (c_out) *c_out = cK;
+        for (int p = 0; p < nlb; ++p)
+            for (int q = 0; q < nlb; ++q) {
+                double s = 0.0, m = 0.0;
+                for (int r = 0; r < dim; ++r) s += glam[r + p * dim] * glam[r + q * dim];
+                for (int i = 0; i < nip; ++i) m += w[i] * cq[i] * ip[i * (dim + 1) + p] * ip[i * (dim + 1) + q];
+                Kp[p + q * nlb] = cK * vol * s;
+                Mp[p + q * nlb] = vol * m;
+            }
+        return d;
+    }
+    double c = centroid_coeff(dim, dim + 1, nlb, elems, coords, k, ckind & 1, ca, cb);
     if (c_out) *c_out = c;
     if (order == 1) {
         for (int p = 0; p < nlb; ++p)

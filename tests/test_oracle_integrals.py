@@ -181,3 +181,61 @@ def test_avtamav_against_numpy():
         A = rng.standard_normal((37, n, n))                 # (N, cols, rows)
         ref = np.einsum("kr,kcr,kc->k", v, A, w)           # v^T A w with A[k][r, c] = A[k, c, r]
         np.testing.assert_allclose(oracle.avtamav(v, A, w), ref, rtol=1e-13, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# the paper's literal P1 listing: degree-2 rule, coefficient at every point
+# --------------------------------------------------------------------------
+
+def _literal(dim, m, ca, cb, kind):
+    return oracle.assemble(dim, 1, m.nn, m.elems, m.coords, ca, cb, want_pages=True, ckind=kind)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_literal_constant_coefficient_is_exact(dim):
+    # c constant: the literal K equals the centroid K, and M the exact P1 mass
+    m = meshgen.make_mesh(dim, 3, jitter=0.1, seed=2)
+    lit = _literal(dim, m, 1.7, 0.0, 2)
+    cen = _literal(dim, m, 1.7, 0.0, 0)
+    np.testing.assert_allclose(lit["K3D"], cen["K3D"], rtol=1e-13, atol=1e-15)
+    vol, _ = oracle.volumes(dim, m.elems, m.coords)
+    Mexact = 1.7 * vol[:, None, None] * (1 + np.eye(dim + 1))[None] / ((dim + 1) * (dim + 2))
+    np.testing.assert_allclose(lit["M3D"], Mexact, rtol=1e-13, atol=0)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_literal_quadratic_coefficient_stiffness_exact(dim):
+    # c = a + b|x|^2 is quadratic, so the degree-2 rule gives K_k = (int_T c) G^T G exactly;
+    # int_T |x|^2 = sum_jk (x_j . x_k) int lambda_j lambda_k, int lambda_j lambda_k = |T| (1 + delta_jk)/((d+1)(d+2))
+    m = meshgen.make_mesh(dim, 2, jitter=0.1, seed=3)
+    a, b = 0.7, 1.3
+    lit = _literal(dim, m, a, b, 2)
+    one = _literal(dim, m, 1.0, 0.0, 0)          # G^T G |T|
+    vol, _ = oracle.volumes(dim, m.elems, m.coords)
+    X = m.coords[m.elems[:, : dim + 1]]          # (ne, d+1, dim)
+    gram = np.einsum("kjd,kld->kjl", X, X)
+    lam2 = (1 + np.eye(dim + 1)) / ((dim + 1) * (dim + 2))
+    intc = a * vol + b * vol * np.einsum("kjl,jl->k", gram, lam2)
+    np.testing.assert_allclose(lit["K3D"], (intc / vol)[:, None, None] * one["K3D"], rtol=1e-12, atol=1e-14)
+
+
+def test_literal_convergence_matches_printed_table_order():
+    # c = e^{x1+x2+x3}, v = cos(pi x1) cos(pi x2) cos(pi x3) on unjittered unit cubes;
+    # printed P1 3-D errors at levels 3-5: e_K 2.70e-1, 6.82e-2, 1.71e-2; e_M 5.04e-2,
+    # 1.31e-2, 3.30e-3.  The cube split differs from the paper's, so the values agree in
+    # order of magnitude (within 15 %) and in the rate (4 per level), not digit for digit.
+    IK, IM = 19.2286024907, 0.6823216700
+    printed = {3: (2.70e-1, 5.04e-2), 4: (6.82e-2, 1.31e-2), 5: (1.71e-2, 3.30e-3)}
+    errs = {}
+    for lev in (3, 4, 5):
+        m = meshgen.kuhn_cube(2 ** lev, jitter=0.0)
+        A = oracle.assemble(3, 1, m.nn, m.elems, m.coords, 1.0, 1.0, ckind=3)
+        v = np.prod(np.cos(np.pi * m.coords), axis=1)
+        rows = np.repeat(np.arange(m.nn), np.diff(A["row_ptr"]))
+        qk = np.sum(v[rows] * A["K"] * v[A["col_idx"]])
+        qm = np.sum(v[rows] * A["M"] * v[A["col_idx"]])
+        errs[lev] = (abs(qk - IK), abs(qm - IM))
+        for e, p in zip(errs[lev], printed[lev]):
+            assert 0.85 < e / p < 1.15, (lev, e, p)
+    for i in (0, 1):
+        assert 3.7 < errs[3][i] / errs[4][i] < 4.3 and 3.7 < errs[4][i] / errs[5][i] < 4.3
