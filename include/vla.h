@@ -65,7 +65,8 @@ enum { VLA_F32 = 0, VLA_F64 = 1 };                      /* dtype */
 enum { VLA_LAYOUT_PAGE = 0, VLA_LAYOUT_SOA = 1 };        /* page-array layout */
 enum { VLA_P1 = 1, VLA_P2 = 2 };                         /* element order */
 enum { VLA_PREC_FP64 = 0, VLA_PREC_MIXED = 1 };          /* assembly precision */
-enum { VLA_COEFF_POLY = 0, VLA_COEFF_EXP = 1 };          /* coefficient kind */
+enum { VLA_COEFF_POLY = 0, VLA_COEFF_EXP = 1,            /* coefficient kind (see vla_assemble) */
+       VLA_COEFF_POLY_IP = 2, VLA_COEFF_EXP_IP = 3 };
 
 /* Library version, 100*major + minor. */
 int32_t vla_version(void);
@@ -162,6 +163,12 @@ vla_status vla_mesh_csr(const vla_mesh *mesh, int32_t *row_ptr, int32_t *col_idx
  *   M_ij = sum_k c_k int_{T_k} phi_i phi_j,
  * where c_k is the coefficient evaluated at the vertex centroid x_c of T_k:
  *   VLA_COEFF_POLY: c = ca + cb |x_c|^2;  VLA_COEFF_EXP: c = ca exp(cb sum_d x_c,d).
+ *   VLA_COEFF_POLY_IP, VLA_COEFF_EXP_IP (P1 only): the paper's literal P1
+ *   listing -- the same functions evaluated at the points of the degree-2
+ *   rule (gqo = 2) of every element: K_k = (sum_i w_i c(x_i)) |T| G^T G and
+ *   M_k(p,q) = |T| sum_i w_i c(x_i) lambda_p(x_i) lambda_q(x_i); P2 meshes get
+ *   VLA_ERR_UNSUPPORTED.  Batches, the server and vla_element_pages_static
+ *   take the centroid kinds only.
  * P1 integrals are exact; P2 stiffness uses the 4-point rule (exact for the
  * quadratic integrand of affine elements) and P2 mass the exact reference
  * mass matrix.  Outputs (device, FP64, any may be NULL):

@@ -22,13 +22,13 @@ import torch
 __all__ = [
     "VlaError", "lib", "version", "amtam", "astam", "avtam", "amdet", "aminv", "Mesh", "element_pages_static",
     "Batch", "batch_assemble", "autotune", "tune_get", "tune_set", "Server", "PENDING", "quad_rule", "gi",
-    "avtamav", "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP",
+    "avtamav", "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP", "COEFF_POLY_IP", "COEFF_EXP_IP",
 ]
 
 F32, F64 = 0, 1
 LAYOUT_PAGE, LAYOUT_SOA = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
-COEFF_POLY, COEFF_EXP = 0, 1
+COEFF_POLY, COEFF_EXP, COEFF_POLY_IP, COEFF_EXP_IP = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvla.so")

@@ -489,12 +489,14 @@ __device__ __forceinline__ void geo_mixed2_fast(const float4 *__restrict__ sh, c
 // ---------------------------------------------------------------------------
 // compile-time configuration
 // ---------------------------------------------------------------------------
-template <int DIM, int ORDER, bool MIX>
+template <int DIM, int ORDER, bool MIX, bool LIT = false>
 struct Cfg {
     static constexpr int NV = DIM + 1;
     static constexpr int NLB = ORDER == 1 ? DIM + 1 : (DIM + 1) * (DIM + 2) / 2;
     static constexpr int NU = NLB * (NLB + 1) / 2;            // packed upper triangle
-    static constexpr int RS = (NU + 1 + 3) / 4 * 4;            // record: NU entries, mass scale, padding
+    // record: NU stiffness entries, then the mass scale (or, for the literal
+    // quadrature, NU mass entries), padded to 16 bytes
+    static constexpr int RS = LIT ? (2 * NU + 3) / 4 * 4 : (NU + 1 + 3) / 4 * 4;
     static constexpr int UB = ORDER == 1 ? 4 : 8;              // code = element << UB | entry
     using T = typename std::conditional<MIX, float, double>::type;
     using CT = typename std::conditional<ORDER == 1, uint16_t, uint32_t>::type;
@@ -612,11 +614,11 @@ __device__ __forceinline__ void cp_async_wait_but1() { asm volatile("cp.async.wa
 // triangle of K_k and the mass scale into the record area (index n_elems is
 // the zero record that padding codes point at), and writes the outputs of
 // the elements the tile owns (vol, optional pages, singular count).
-template <int DIM, int ORDER, bool MIX>
+template <int DIM, int ORDER, bool MIX, bool LIT = false>
 __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileHdr &h, const unsigned char *b,
                                               const StageMap &mp, typename Cfg<DIM, ORDER, MIX>::T *s_k,
                                               const typename Cfg<DIM, ORDER, MIX>::T *mhat) {
-    using C = Cfg<DIM, ORDER, MIX>;
+    using C = Cfg<DIM, ORDER, MIX, LIT>;
     using T = typename C::T;
     const ushort4 *s_rec = reinterpret_cast<const ushort4 *>(b + mp.rec);
     const int32_t *s_gid = reinterpret_cast<const int32_t *>(b + mp.gid);
@@ -644,7 +646,8 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
                     const int64_t pos = k * C::NLB * C::NLB + a + (int64_t)q * C::NLB;
                     const T kv = dst[u];
                     T mv;
-                    if constexpr (ORDER == 1) mv = mscale * (a == q ? T(2) : T(1));
+                    if constexpr (LIT) mv = dst[C::NU + u];
+                    else if constexpr (ORDER == 1) mv = mscale * (a == q ? T(2) : T(1));
                     else mv = mscale * mhat[u];
                     if constexpr (MIX) {
                         if (Kp) Kp[pos] = f32_to_f64(kv);
@@ -671,8 +674,57 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
         } else {
             geo_f64<DIM>(s_x, v, g);
         }
-        const T c = coeff<T>(kind, ca, cb, g.xc, DIM);
         const T adet = g.det < T(0) ? -g.det : g.det;
+        if constexpr (LIT) {
+            // the literal P1 listing: the degree-2 rule (points (a, b, .., b)
+            // and permutations, equal weights) with the coefficient at every
+            // point; K uses the weighted mean of c, M_pq = |T| sum_i w_i c_i l_ip l_iq
+            constexpr T qa = DIM == 3 ? T(0.5854101966249685) : T(2.0 / 3.0);
+            constexpr T qb = DIM == 3 ? T(0.1381966011250105) : T(1.0 / 6.0);
+            constexpr T qw = T(1.0) / T(C::NV);
+            T xv[C::NV][3];
+            const unsigned short vid[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < C::NV; ++j) {
+                if constexpr (MIX) {
+                    const float4 hh = s_h[vid[j]], ll = s_l[vid[j]];
+                    xv[j][0] = hh.x + ll.x, xv[j][1] = hh.y + ll.y, xv[j][2] = hh.z + ll.z;
+                } else {
+                    const double4 xx = s_x[vid[j]];
+                    xv[j][0] = xx.x, xv[j][1] = xx.y, xv[j][2] = xx.z;
+                }
+            }
+            T cq[C::NV], cK = T(0);
+#pragma unroll
+            for (int i = 0; i < C::NV; ++i) {
+                T xq[3] = {T(0), T(0), T(0)};
+#pragma unroll
+                for (int j = 0; j < C::NV; ++j)
+#pragma unroll
+                    for (int r = 0; r < 3; ++r) xq[r] += (i == j ? qa : qb) * xv[j][r];
+                cq[i] = coeff<T>(kind - 2, ca, cb, xq, DIM);
+                cK += qw * cq[i];
+            }
+            T sc;
+            if constexpr (MIX) sc = cK * __frcp_rn(T(C::DFACT) * adet);
+            else sc = cK / (T(C::DFACT) * adet);
+            const T vt = adet / T(C::DFACT);
+#pragma unroll
+            for (int a = 0; a < C::NV; ++a)
+#pragma unroll
+                for (int q = a; q < C::NV; ++q) {
+                    const int u = a * C::NLB - a * (a - 1) / 2 + (q - a);
+                    dst[u] = sc * dot3<T>(g.C[a], g.C[q]);
+                    T m = T(0);
+#pragma unroll
+                    for (int i = 0; i < C::NV; ++i) m += qw * cq[i] * (i == a ? qa : qb) * (i == q ? qa : qb);
+                    dst[C::NU + u] = vt * m;
+                }
+            for (int u = 2 * C::NU; u < C::RS; ++u) dst[u] = T(0);
+            if (e < h.n_own) owned(e, g.det, adet, T(0), dst);
+            return;
+        }
+        const T c = coeff<T>(kind, ca, cb, g.xc, DIM);
         T sc;
         if constexpr (MIX) sc = c * __frcp_rn(T(C::DFACT) * adet);   // K(a,b) = sc * C_a . C_b
         else sc = c / (T(C::DFACT) * adet);
@@ -716,12 +768,13 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
 // round-robin would give the first warps all the long ones); each lane sums
 // its pair's contributions in ascending element order and writes p_ij and
 // p_ji once.
-template <int DIM, int ORDER, bool MIX>
+template <int DIM, int ORDER, bool MIX, bool LIT = false>
 __device__ __forceinline__ void tile_pairs(double *__restrict__ K, double *__restrict__ M, const vla::TileHdr &h,
                                            const unsigned char *b, const StageMap &mp,
                                            const typename Cfg<DIM, ORDER, MIX>::T *s_k,
                                            const typename Cfg<DIM, ORDER, MIX>::T *mhat, int *next_chunk) {
-    using C = Cfg<DIM, ORDER, MIX>;
+    using C = Cfg<DIM, ORDER, MIX, LIT>;
+    constexpr int MO = LIT ? C::NU : 0;   // literal: the mass entry sits NU past the stiffness entry
     using CT = typename C::CT;
     constexpr uint32_t UMASK = (1u << C::UB) - 1;
     const int2 *s_chk = reinterpret_cast<const int2 *>(b + mp.chk);
@@ -739,7 +792,7 @@ __device__ __forceinline__ void tile_pairs(double *__restrict__ K, double *__res
             for (; tt + 1 < ch.y; tt += 2) {
                 const uint32_t c0 = cp[tt * 32], c1 = cp[(tt + 1) * 32];
                 const float *r0 = s_k + (c0 >> C::UB) * C::RS, *r1 = s_k + (c1 >> C::UB) * C::RS;
-                float m0 = r0[C::NU], m1 = r1[C::NU];
+                float m0 = LIT ? r0[MO + (c0 & UMASK)] : r0[C::NU], m1 = LIT ? r1[MO + (c1 & UMASK)] : r1[C::NU];
                 if constexpr (ORDER == 2) {
                     m0 *= mhat[c0 & UMASK];
                     m1 *= mhat[c1 & UMASK];
@@ -750,7 +803,7 @@ __device__ __forceinline__ void tile_pairs(double *__restrict__ K, double *__res
             if (tt < ch.y) {
                 const uint32_t c0 = cp[tt * 32];
                 const float *r0 = s_k + (c0 >> C::UB) * C::RS;
-                float m0 = r0[C::NU];
+                float m0 = LIT ? r0[MO + (c0 & UMASK)] : r0[C::NU];
                 if constexpr (ORDER == 2) m0 *= mhat[c0 & UMASK];
                 ff2_add(h0, l0, pk(r0[c0 & UMASK], m0));
             }
@@ -765,7 +818,7 @@ __device__ __forceinline__ void tile_pairs(double *__restrict__ K, double *__res
                 upk(s2, khi, mhi);
                 upk(e2, klo, mlo);
                 const int2 pos = s_nz[q];
-                if (ORDER == 1 && pos.x == pos.y) {   // P1 diagonal mass: twice the off-diagonal scale
+                if (ORDER == 1 && !LIT && pos.x == pos.y) {   // P1 diagonal mass: twice the off-diagonal scale
                     mhi *= 2.f;
                     mlo *= 2.f;
                 }
@@ -785,12 +838,13 @@ __device__ __forceinline__ void tile_pairs(double *__restrict__ K, double *__res
                 const uint32_t c0 = cp[tt * 32];
                 const double *r0 = s_k + (c0 >> C::UB) * C::RS;
                 ks += r0[c0 & UMASK];
-                if constexpr (ORDER == 2) ms += r0[C::NU] * mhat[c0 & UMASK];
+                if constexpr (LIT) ms += r0[MO + (c0 & UMASK)];
+                else if constexpr (ORDER == 2) ms += r0[C::NU] * mhat[c0 & UMASK];
                 else ms += r0[C::NU];
             }
             if (q < h.n_nz) {
                 const int2 pos = s_nz[q];
-                if (ORDER == 1 && pos.x == pos.y) ms *= 2.0;
+                if (ORDER == 1 && !LIT && pos.x == pos.y) ms *= 2.0;
                 if (K) {
                     K[pos.x] = ks;
                     if (pos.y != pos.x) K[pos.y] = ks;
@@ -843,7 +897,7 @@ constexpr int single_type(int types) { return types == 1 ? 0 : types == 2 ? 1 : 
 // tile j is computed from stage j&1, the bulk copies of tile j+2 (and, in a
 // batch, the job of its mesh) and the coordinate gathers (cp.async) of tile
 // j+1 are in flight, and the header of tile j+2 is being fetched.
-template <bool MIX, int TYPES, bool BATCH>
+template <bool MIX, int TYPES, bool BATCH, bool LIT = false>
 __global__ void __launch_bounds__(kThreads, 3) k_assemble(const LaunchArgs A) {
     using T = typename std::conditional<MIX, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -982,7 +1036,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_assemble(const LaunchArgs A) {
 
         by_type<TYPES>(ty, [&](auto D, auto O) {
             constexpr int DIM = decltype(D)::value, ORDER = decltype(O)::value;
-            tile_elements<DIM, ORDER, MIX>(job_of(s), h, b, mp, s_k, mhat + (DIM == 3 ? 21 : 0));
+            tile_elements<DIM, ORDER, MIX, LIT && ORDER == 1>(job_of(s), h, b, mp, s_k, mhat + (DIM == 3 ? 21 : 0));
         });
         // prefetch: coordinates of the next tile (its bulk copies were issued two tiles ago)
         if (t + G < n) {
@@ -998,7 +1052,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_assemble(const LaunchArgs A) {
         if (J.K || J.M) {
             by_type<TYPES>(ty, [&](auto D, auto O) {
                 constexpr int DIM = decltype(D)::value, ORDER = decltype(O)::value;
-                tile_pairs<DIM, ORDER, MIX>(J.K, J.M, h, b, mp, s_k, mhat + (DIM == 3 ? 21 : 0), &next_chunk[j & 1]);
+                tile_pairs<DIM, ORDER, MIX, LIT && ORDER == 1>(J.K, J.M, h, b, mp, s_k, mhat + (DIM == 3 ? 21 : 0),
+                                                             &next_chunk[j & 1]);
             });
         }
         if (threadIdx.x == 0) next_chunk[(j + 1) & 1] = kThreads / 32;   // reset for the next tile
@@ -1015,8 +1070,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_assemble(const LaunchArgs A) {
 inline int mesh_stage_bytes(const vla_mesh *m) {
     return (int)((m->tile_stage_bytes + 32 * (size_t)m->max_tile_nodes + 16 + 15) / 16 * 16);
 }
-inline size_t mesh_record_bytes(const vla_mesh *m, bool mix) {
-    const int nlb = m->nlb, nu = nlb * (nlb + 1) / 2, rs = (nu + 1 + 3) / 4 * 4;
+inline size_t mesh_record_bytes(const vla_mesh *m, bool mix, bool lit = false) {
+    const int nlb = m->nlb, nu = nlb * (nlb + 1) / 2, rs = lit ? (2 * nu + 3) / 4 * 4 : (nu + 1 + 3) / 4 * 4;
     return ((size_t)m->max_tile_elems + 1) * rs * (mix ? 4 : 8);
 }
 
@@ -1024,7 +1079,7 @@ inline size_t mesh_record_bytes(const vla_mesh *m, bool mix) {
 // the tuned residency and by the work items).  The kernel's dynamic shared
 // memory limit is raised to the device maximum once per device, so launches
 // (and graphs) of any size up to it stay valid.
-template <bool MIX, int TYPES, bool BATCH>
+template <bool MIX, int TYPES, bool BATCH, bool LIT = false>
 vla_status kernel_shape(size_t smem, int ctas_per_sm, int n_work, int *grid) {
     static std::mutex mu;
     static bool ready[64] = {};
@@ -1032,7 +1087,7 @@ vla_status kernel_shape(size_t smem, int ctas_per_sm, int n_work, int *grid) {
     VLA_CUDA(cudaGetDevice(&dev));
     VLA_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     VLA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    auto kern = k_assemble<MIX, TYPES, BATCH>;
+    auto kern = k_assemble<MIX, TYPES, BATCH, LIT>;
     cudaFuncAttributes fa;
     VLA_CUDA(cudaFuncGetAttributes(&fa, kern));
     if (smem + fa.sharedSizeBytes > (size_t)maxsm)
@@ -1056,19 +1111,19 @@ vla_status kernel_shape(size_t smem, int ctas_per_sm, int n_work, int *grid) {
     return VLA_OK;
 }
 
-template <bool MIX, int TYPES, bool BATCH>
+template <bool MIX, int TYPES, bool BATCH, bool LIT = false>
 vla_status launch_kernel(const LaunchArgs &a, size_t smem, int grid, cudaStream_t st) {
     if (grid < 1) return VLA_OK;
-    k_assemble<MIX, TYPES, BATCH><<<grid, kThreads, smem, st>>>(a);
+    k_assemble<MIX, TYPES, BATCH, LIT><<<grid, kThreads, smem, st>>>(a);
     VLA_CUDA(cudaGetLastError());
     return VLA_OK;
 }
 
-template <bool MIX, int TYPES>
+template <bool MIX, int TYPES, bool LIT = false>
 vla_status launch_single(const LaunchArgs &a, size_t smem, int ctas_per_sm, cudaStream_t st) {
     int grid = 0;
-    TRY(kernel_shape<MIX, TYPES, false>(smem, ctas_per_sm, a.n_work, &grid));
-    return launch_kernel<MIX, TYPES, false>(a, smem, grid, st);
+    TRY((kernel_shape<MIX, TYPES, false, LIT>(smem, ctas_per_sm, a.n_work, &grid)));
+    return launch_kernel<MIX, TYPES, false, LIT>(a, smem, grid, st);
 }
 
 MeshJob make_job(const vla_mesh *m, int kind, double ca, double cb, double *K, double *M, double *vol, double *Kp,
@@ -1251,7 +1306,9 @@ extern "C" vla_status vla_assemble(const vla_mesh *m, int32_t kind, double ca, d
                                    double *K_vals, double *M_vals, double *vol, double *K_pages, double *M_pages,
                                    int64_t *n_singular, void *stream) {
     if (!m) return fail(VLA_ERR_INVALID_ARG, "null mesh");
-    if (kind != VLA_COEFF_POLY && kind != VLA_COEFF_EXP) return fail(VLA_ERR_INVALID_ARG, "unknown coefficient kind");
+    if (kind < VLA_COEFF_POLY || kind > VLA_COEFF_EXP_IP) return fail(VLA_ERR_INVALID_ARG, "unknown coefficient kind");
+    if (kind >= VLA_COEFF_POLY_IP && m->order != VLA_P1)
+        return fail(VLA_ERR_UNSUPPORTED, "the literal quadrature coefficient is implemented for P1 elements");
     if (precision != VLA_PREC_FP64 && precision != VLA_PREC_MIXED)
         return fail(VLA_ERR_INVALID_ARG, "precision must be VLA_PREC_FP64 or VLA_PREC_MIXED");
     if (!std::isfinite(ca) || !std::isfinite(cb)) return fail(VLA_ERR_INVALID_ARG, "non-finite coefficient");
@@ -1270,9 +1327,18 @@ extern "C" vla_status vla_assemble(const vla_mesh *m, int32_t kind, double ca, d
     a.err = m->d_err;
     a.spin_limit = m->spin_limit;
     a.stage_bytes = mesh_stage_bytes(m);
-    const size_t smem = 2 * (size_t)a.stage_bytes + mesh_record_bytes(m, mix);
+    const bool lit = kind >= VLA_COEFF_POLY_IP;
+    const size_t smem = 2 * (size_t)a.stage_bytes + mesh_record_bytes(m, mix, lit);
     const int ty = type_index(m->dim, m->order);
     const int cps = tuned_ctas(ty, mix);
+    if (lit) {   // P1 triangles or tetrahedra
+        switch (ty * 2 + (mix ? 1 : 0)) {
+        case 0: return launch_single<false, 1, true>(a, smem, cps, st);
+        case 1: return launch_single<true, 1, true>(a, smem, cps, st);
+        case 4: return launch_single<false, 4, true>(a, smem, cps, st);
+        default: return launch_single<true, 4, true>(a, smem, cps, st);
+        }
+    }
     switch (ty * 2 + (mix ? 1 : 0)) {
     case 0: return launch_single<false, 1>(a, smem, cps, st);
     case 1: return launch_single<true, 1>(a, smem, cps, st);

@@ -385,3 +385,34 @@ def test_invalid_meshes_rejected(vla):
     with pytest.raises(vla.VlaError) as e:
         vla.Mesh(_dev(np.zeros((5, 3))), good, faces=_dev(np.array([[0, 1, 4]], np.int32)))
     assert e.value.status == -7
+
+
+# ---------------------------------------------------------------------------
+# the paper's literal P1 listing: degree-2 rule, coefficient at every point
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,n", [(2, 5), (2, 33), (3, 3), (3, 9)])
+@pytest.mark.parametrize("kind", [2, 3])
+def test_literal_quadrature_fp64_and_mixed(vla, dim, n, kind):
+    m = meshgen.make_mesh(dim, n, order=1, jitter=0.1, seed=7 * n + kind)
+    gm = _gpu_mesh(vla, m)
+    ref = oracle.assemble(dim, 1, m.nn, m.elems, m.coords, 1.2, 0.8, want_pages=True, ckind=kind)
+    out = gm.assemble(1.2, 0.8, kind=kind, precision=vla.PREC_FP64, pages=True)
+    _check_fp64(out["K"].cpu().numpy(), ref["K"], ref["row_ptr"])
+    _check_fp64(out["M"].cpu().numpy(), ref["M"], ref["row_ptr"])
+    for key in ("K3D", "M3D"):
+        P, R = out[key].cpu().numpy(), ref[key]
+        assert (np.abs(P - R).max(axis=(1, 2)) / np.abs(R).max(axis=(1, 2))).max() <= TOL64
+    mixed = gm.assemble(1.2, 0.8, kind=kind, precision=vla.PREC_MIXED, pages=True)
+    for key in ("K", "M", "vol", "K3D", "M3D"):
+        assert _rel_fro(mixed[key].cpu().numpy(), ref[key]) <= TOL_MIX, key
+
+
+def test_literal_quadrature_limits(vla):
+    p2 = _gpu_mesh(vla, meshgen.make_mesh(3, 2, order=2))
+    with pytest.raises(vla.VlaError) as e:
+        p2.assemble(1.0, 1.0, kind=vla.COEFF_EXP_IP)
+    assert e.value.status == -8
+    p1 = _gpu_mesh(vla, meshgen.kuhn_cube(2))
+    with pytest.raises(vla.VlaError):
+        vla.Batch([(p1, p1.outputs(), vla.COEFF_EXP_IP, 1.0, 1.0)])
