@@ -74,6 +74,8 @@ def _load():
         lib.orc_rhs.argtypes = [C.c_int, C.c_int, _i64, _i64, C.c_int, _i, _d, C.c_int, _d, _d, _d, _d, _d]
         lib.orc_energies.argtypes = [_i64, C.c_int, _i, _d, _d, _d, _d, _d]
         lib.orc_avtamav.argtypes = [_i64, C.c_int, _d, _d, _d, _d]
+        lib.orc_facets.argtypes = [C.c_int, _i64, C.c_int, _i, vp, vp, vp, C.POINTER(_i64)]
+        lib.orc_facets.restype = _i64
         _lib = lib
         return lib
 
@@ -325,3 +327,22 @@ def avtamav(v, A, w):
     out = np.empty(max(N, 1))
     _load().orc_avtamav(N, n, v, A, w, out)
     return out[:N]
+
+
+def facets(dim, elems):
+    """(faces (nf, dim), owner (nf, 2) = (element, local facet), neighbor (nf,),
+    n_boundary): every distinct facet once, ordered by first element and local
+    facet index."""
+    elems = _i32(elems)
+    ne, nlb = elems.shape
+    L = _load()
+    nb = _i64(0)
+    nf = L.orc_facets(dim, ne, nlb, elems, None, None, None, C.byref(nb))
+    if nf < 0:
+        raise MemoryError("oracle facets")
+    faces = np.empty((max(nf, 1), dim), np.int32)
+    owner = np.empty((max(nf, 1), 2), np.int32)
+    nbr = np.empty(max(nf, 1), np.int32)
+    L.orc_facets(dim, ne, nlb, elems, faces.ctypes.data_as(C.c_void_p), owner.ctypes.data_as(C.c_void_p),
+                 nbr.ctypes.data_as(C.c_void_p), C.byref(nb))
+    return faces[:nf], owner[:nf], nbr[:nf], int(nb.value)

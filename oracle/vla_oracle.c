@@ -793,3 +793,85 @@ void orc_avtamav(int64_t N, int n, const double *v, const double *A, const doubl
         out[k] = s;
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* facet list (Section 3.2: normals of all faces, boundary faces)            */
+/* ------------------------------------------------------------------------ */
+
+/* Every distinct facet once, in the order of its first element k ascending,
+ * then its local facet j ascending (facet j is opposite local vertex j; its
+ * vertices are the element's other vertices in local order).  A facet shared
+ * by elements k < k' is listed with k.  faces: dim x nf; owner: 2 x nf
+ * (k, j); neighbor: nf, the other element or -1 on the boundary.  Any output
+ * may be NULL.  Returns nf (or -1 on allocation failure); *n_boundary the
+ * number of facets without neighbour.  Brute force: all (sorted triple, k, j)
+ * records sorted, equal triples paired. */
+typedef struct {
+    int32_t v[3];
+    int64_t k;
+    int32_t j;
+} facet_rec;
+
+static int cmp_facet_rec(const void *a, const void *b) {
+    const facet_rec *x = (const facet_rec *)a, *y = (const facet_rec *)b;
+    for (int q = 0; q < 3; ++q)
+        if (x->v[q] != y->v[q]) return (x->v[q] > y->v[q]) - (x->v[q] < y->v[q]);
+    if (x->k != y->k) return (x->k > y->k) - (x->k < y->k);
+    return (x->j > y->j) - (x->j < y->j);
+}
+
+int64_t orc_facets(int dim, int64_t ne, int nlb, const int32_t *elems, int32_t *faces, int32_t *owner,
+                   int32_t *neighbor, int64_t *n_boundary) {
+    const int nv = dim + 1;
+    const int64_t nr = ne * nv;
+    facet_rec *r = (facet_rec *)malloc((size_t)(nr > 0 ? nr : 1) * sizeof(facet_rec));
+    int64_t *partner = (int64_t *)malloc((size_t)(nr > 0 ? nr : 1) * sizeof(int64_t));
+    if (!r || !partner) {
+        free(r);
+        free(partner);
+        return -1;
+    }
+    for (int64_t k = 0; k < ne; ++k)
+        for (int j = 0; j < nv; ++j) {
+            facet_rec *f = r + k * nv + j;
+            int q = 0;
+            f->v[0] = f->v[1] = f->v[2] = -1;
+            for (int i = 0; i < nv; ++i)
+                if (i != j) f->v[q++] = elems[k * nlb + i];
+            for (int a = 1; a < dim; ++a)
+                for (int b = a; b > 0 && f->v[b - 1] > f->v[b]; --b) {
+                    int32_t t = f->v[b];
+                    f->v[b] = f->v[b - 1];
+                    f->v[b - 1] = t;
+                }
+            f->k = k;
+            f->j = j;
+        }
+    qsort(r, (size_t)nr, sizeof(facet_rec), cmp_facet_rec);
+    /* partner element of record (k, j), indexed by k*nv + j */
+    for (int64_t t = 0; t < nr; ++t) partner[r[t].k * nv + r[t].j] = -1;
+    for (int64_t t = 0; t + 1 < nr; ++t)
+        if (r[t].v[0] == r[t + 1].v[0] && r[t].v[1] == r[t + 1].v[1] && r[t].v[2] == r[t + 1].v[2]) {
+            partner[r[t].k * nv + r[t].j] = r[t + 1].k;
+            partner[r[t + 1].k * nv + r[t + 1].j] = r[t].k;
+        }
+    int64_t nf = 0, nb = 0;
+    for (int64_t k = 0; k < ne; ++k)
+        for (int j = 0; j < nv; ++j) {
+            const int64_t p = partner[k * nv + j];
+            if (p >= 0 && p < k) continue;   /* listed with the smaller element */
+            if (faces) {
+                int q = 0;
+                for (int i = 0; i < nv; ++i)
+                    if (i != j) faces[nf * dim + q++] = elems[k * nlb + i];
+            }
+            if (owner) owner[nf * 2] = (int32_t)k, owner[nf * 2 + 1] = j;
+            if (neighbor) neighbor[nf] = (int32_t)p;
+            if (p < 0) ++nb;
+            ++nf;
+        }
+    if (n_boundary) *n_boundary = nb;
+    free(r);
+    free(partner);
+    return nf;
+}

@@ -423,3 +423,38 @@ def test_quadratic_form_convergence(golden_dir, dim, ns):
     for a, b in zip(eM, eM[1:]):
         assert 3.0 < a / b < 5.0
     assert eK[-1] < 0.05 * g["I_K"] and eM[-1] < 0.05 * g["I_M"]
+
+
+# ---------------------------------------------------------------------------
+# facet list: the counts of the paper's normals table (Section 3.2) and
+# brute-force incidence on a tiny mesh
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("level,n_all,n_bnd", [(1, 864, 192), (2, 6528, 768), (3, 50688, 3072)])
+def test_facet_list_counts_match_printed_table(level, n_all, n_bnd):
+    m = meshgen.kuhn_cube(2 ** (level + 1), jitter=0.0)   # level L: (2^(L+1))^3 cubes x 6 tets
+    faces, owner, nbr, nb = oracle.facets(3, m.elems)
+    assert (len(faces), nb) == (n_all, n_bnd)
+    assert np.sum(nbr < 0) == nb
+
+
+def test_facet_list_brute_force_tiny():
+    m = meshgen.kuhn_cube(1)
+    faces, owner, nbr, nb = oracle.facets(3, m.elems)
+    # every facet's vertices are its owner's vertices without the opposite one
+    for f, (k, j), p in zip(faces, owner, nbr):
+        verts = [v for i, v in enumerate(m.elems[k]) if i != j]
+        assert list(f) == verts
+        if p >= 0:
+            assert p > k and set(f) <= set(m.elems[p])
+        else:   # a boundary facet of the unit cube lies in one of its faces
+            X = m.coords[f]
+            assert np.any(np.all(np.isclose(X, 0.0), axis=0) | np.all(np.isclose(X, 1.0), axis=0))
+    # each element's 4 facets appear exactly once overall
+    seen = {}
+    for (k, j), p in zip(owner, nbr):
+        seen[(k, j)] = True
+    assert len(seen) == len(faces)
+    # brute force pairing count: interior facets counted twice across elements
+    triples = [tuple(sorted(v for i, v in enumerate(e) if i != j)) for e in m.elems for j in range(4)]
+    assert len(set(triples)) == len(faces)
