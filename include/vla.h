@@ -226,6 +226,19 @@ vla_status vla_element_pages_static(int32_t dim, int32_t order, int64_t nn, int6
                                     const int32_t *elems, int32_t coeff_kind, double ca, double cb, int32_t precision,
                                     double *K_pages, double *M_pages, double *vol, int64_t *n_singular, void *stream);
 
+/* Every facet of the mesh once (the faces behind the paper's normals of all
+ * faces and its face counts, Section 3.2): facet j of element k is opposite
+ * local vertex j, with the element's other vertex nodes in local order; a
+ * facet shared by elements k < k' is listed with k, and the list is ordered
+ * by (k, j).  Outputs (device, any may be NULL): faces dim x nf int32,
+ * owner 2 x nf int32 (k, j), neighbor nf int32 (k', or -1 for a boundary
+ * facet); *n_faces and *n_boundary (host) receive nf and the number of
+ * boundary facets.  Call with NULL arrays first to learn nf.  Integer work,
+ * deterministic; synchronises `stream`.  Unnormalised normals of all facets:
+ * vla_simplex_normals, column j of element k's page. */
+vla_status vla_mesh_facets(const vla_mesh *mesh, int32_t *faces, int32_t *owner, int32_t *neighbor, int64_t *n_faces,
+                           int64_t *n_boundary, void *stream);
+
 /* Releases the handle and its device memory (stream-ordered on the stream
  * the mesh was created with, which is synchronised first).  NULL is a no-op. */
 vla_status vla_mesh_destroy(vla_mesh *mesh);

@@ -136,6 +136,7 @@ def lib():
         L.vla_tune_get.argtypes = [i32, i32, i32, C.POINTER(Tune)]
         L.vla_tune_set.argtypes = [i32, i32, i32, C.POINTER(Tune)]
         L.vla_quad_rule.argtypes = [i32, i32, C.POINTER(i32), C.POINTER(dbl), C.POINTER(dbl)]
+        L.vla_mesh_facets.argtypes = [vp, vp, vp, vp, C.POINTER(i64), C.POINTER(i64), vp]
         L.vla_quad_points.argtypes = [vp, i32, i32, vp, vp]
         L.vla_gi.argtypes = [i64, i32, i32, vp, C.POINTER(dbl), vp, vp, vp, vp]
         L.vla_rhs.argtypes = [vp, i32, vp, vp, vp, vp]
@@ -154,7 +155,7 @@ def lib():
                      "vla_batch_assemble", "vla_autotune", "vla_tune_get", "vla_tune_set", "vla_server_create",
                      "vla_server_submit", "vla_server_poll", "vla_server_release", "vla_server_stats",
                      "vla_server_destroy", "vla_quad_rule", "vla_quad_points", "vla_gi", "vla_rhs", "vla_energies",
-                     "vla_avtamav"):
+                     "vla_avtamav", "vla_mesh_facets"):
             getattr(L, name).restype = i32
         _lib = L
         return L
@@ -362,6 +363,20 @@ class Mesh:
             areas = torch.empty(max(self.nfb, 1), dtype=torch.float64, device=dev)[: self.nfb]
         _check(lib().vla_boundary(self._h, precision, _p(normals), _p(areas), _stream(stream)))
         return normals, areas
+
+    def facets(self, stream=None):
+        """(faces (nf, dim), owner (nf, 2), neighbor (nf,), n_boundary): every
+        facet once, ordered by owning element and local facet (vla_mesh_facets)."""
+        nf, nb = C.c_int64(), C.c_int64()
+        _check(lib().vla_mesh_facets(self._h, None, None, None, C.byref(nf), C.byref(nb), _stream(stream)))
+        n = nf.value
+        dev = self.device
+        faces = torch.empty((max(n, 1), self.dim), dtype=torch.int32, device=dev)
+        owner = torch.empty((max(n, 1), 2), dtype=torch.int32, device=dev)
+        nbr = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        _check(lib().vla_mesh_facets(self._h, _p(faces), _p(owner), _p(nbr), C.byref(nf), C.byref(nb),
+                                     _stream(stream)))
+        return faces[:n], owner[:n], nbr[:n], nb.value
 
     def quad_points(self, gqo, facets=False, stream=None):
         """Quadrature points (n, nip, dim) of the elements (or boundary facets)

@@ -1128,6 +1128,63 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     return VLA_OK;
 }
 
+// ---------------------------------------------------------------------------
+// facet list: facet j of element k (opposite local vertex j) and the other
+// element holding it, found in the incidence list of the facet's first vertex
+// ---------------------------------------------------------------------------
+__global__ void k_facet_neighbors(int64_t ne, int dim, int nlb, const int32_t *__restrict__ elems,
+                                  const int32_t *__restrict__ n2e_ptr, const int32_t *__restrict__ n2e,
+                                  int32_t *__restrict__ nbr, int32_t *__restrict__ flag) {
+    const int nv = dim + 1;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ne * nv; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / nv;
+        const int j = (int)(t - k * nv);
+        int32_t fv[3];
+        int q = 0;
+        for (int i = 0; i < nv; ++i)
+            if (i != j) fv[q++] = elems[k * nlb + i];
+        int32_t found = -1;
+        for (int32_t p = n2e_ptr[fv[0]]; p < n2e_ptr[fv[0] + 1] && found < 0; ++p) {
+            const int32_t e = n2e[p] >> 4;
+            if (e == k) continue;
+            int hits = 1;   // fv[0] is in e by construction
+            for (int a = 1; a < dim; ++a)
+                for (int i = 0; i < nv; ++i) hits += elems[(int64_t)e * nlb + i] == fv[a];
+            if (hits == dim) found = e;
+        }
+        nbr[t] = found;
+        flag[t] = (found < 0 || found > k) ? 1 : 0;   // listed with the smaller element
+    }
+}
+
+__global__ void k_facet_write(int64_t ne, int dim, int nlb, const int32_t *__restrict__ elems,
+                              const int32_t *__restrict__ nbr, const int32_t *__restrict__ flag,
+                              const long long *__restrict__ pos, int32_t *__restrict__ faces,
+                              int32_t *__restrict__ owner, int32_t *__restrict__ neighbor) {
+    const int nv = dim + 1;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ne * nv; t += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[t]) continue;
+        const int64_t k = t / nv, f = pos[t];
+        const int j = (int)(t - k * nv);
+        if (faces) {
+            int q = 0;
+            for (int i = 0; i < nv; ++i)
+                if (i != j) faces[f * dim + q++] = elems[k * nlb + i];
+        }
+        if (owner) {
+            owner[2 * f] = (int32_t)k;
+            owner[2 * f + 1] = j;
+        }
+        if (neighbor) neighbor[f] = nbr[t];
+    }
+}
+
+__global__ void k_count_boundary(int64_t n, const int32_t *__restrict__ nbr, const int32_t *__restrict__ flag,
+                                 int32_t *__restrict__ bflag) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        bflag[t] = flag[t] && nbr[t] < 0;
+}
+
 }  // namespace
 
 vla_status mesh_build(vla_mesh *m, const double *coords, const int32_t *elems, const int32_t *faces) {
@@ -1234,5 +1291,36 @@ extern "C" vla_status vla_mesh_csr(const vla_mesh *m, int32_t *row_ptr, int32_t 
         VLA_CUDA(cudaMemcpyAsync(row_ptr, m->row_ptr, sizeof(int32_t) * (m->nn + 1), cudaMemcpyDeviceToDevice, st));
     if (col_idx && m->nnz > 0)
         VLA_CUDA(cudaMemcpyAsync(col_idx, m->col_idx, sizeof(int32_t) * m->nnz, cudaMemcpyDeviceToDevice, st));
+    return VLA_OK;
+}
+
+extern "C" vla_status vla_mesh_facets(const vla_mesh *m, int32_t *faces, int32_t *owner, int32_t *neighbor,
+                                      int64_t *n_faces, int64_t *n_boundary, void *stream) {
+    if (!m) return fail(VLA_ERR_INVALID_ARG, "null mesh");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nv = m->dim + 1;
+    const int64_t nt = m->ne * nv;
+    Scratch S;
+    S.st = st;
+    int32_t *nbr, *flag, *bflag;
+    long long *pos;
+    TRY(S.get(&nbr, nt));
+    TRY(S.get(&flag, nt));
+    TRY(S.get(&bflag, nt));
+    TRY(S.get(&pos, nt + 1));
+    k_facet_neighbors<<<grid_for(nt, 256), 256, 0, st>>>(m->ne, m->dim, m->nlb, m->elems, m->n2e_ptr, m->n2e, nbr,
+                                                          flag);
+    VLA_CUDA(cudaGetLastError());
+    long long total = 0, nb = 0;
+    TRY(excl_scan<int32_t>(flag, nt, pos, st, &total));
+    if (faces || owner || neighbor)
+        k_facet_write<<<grid_for(nt, 256), 256, 0, st>>>(m->ne, m->dim, m->nlb, m->elems, nbr, flag, pos, faces,
+                                                          owner, neighbor);
+    k_count_boundary<<<grid_for(nt, 256), 256, 0, st>>>(nt, nbr, flag, bflag);
+    VLA_CUDA(cudaGetLastError());
+    TRY(excl_scan<int32_t>(bflag, nt, pos, st, &nb));
+    VLA_CUDA(cudaStreamSynchronize(st));
+    if (n_faces) *n_faces = total;
+    if (n_boundary) *n_boundary = nb;
     return VLA_OK;
 }

@@ -416,3 +416,31 @@ def test_literal_quadrature_limits(vla):
     p1 = _gpu_mesh(vla, meshgen.kuhn_cube(2))
     with pytest.raises(vla.VlaError):
         vla.Batch([(p1, p1.outputs(), vla.COEFF_EXP_IP, 1.0, 1.0)])
+
+
+# ---------------------------------------------------------------------------
+# facet list (integer work: bit-exact against the oracle)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,order,n", [(2, 1, 6), (2, 2, 4), (3, 1, 4), (3, 2, 3), (3, 1, 16)])
+def test_facet_list_bit_exact(vla, dim, order, n):
+    m = meshgen.make_mesh(dim, n, order=order, jitter=0.1, seed=n)
+    gm = _gpu_mesh(vla, m)
+    faces, owner, nbr, nb = gm.facets()
+    rf, ro, rn, rnb = oracle.facets(dim, m.elems)
+    np.testing.assert_array_equal(faces.cpu().numpy(), rf)
+    np.testing.assert_array_equal(owner.cpu().numpy(), ro)
+    np.testing.assert_array_equal(nbr.cpu().numpy(), rn)
+    assert nb == rnb == m.nfb
+
+
+def test_facet_counts_full_size(vla):
+    # level 5 of the paper's normals table: 1,572,864 tets -> 3,170,304 faces, 49,152 on the boundary
+    m = meshgen.kuhn_cube(64, jitter=0.1, seed=0)
+    gm = _gpu_mesh(vla, m)
+    faces, owner, nbr, nb = gm.facets()
+    assert (faces.shape[0], nb) == (3170304, 49152)
+    # the boundary facets are the mesh's boundary triangles (as vertex sets)
+    bf = np.sort(faces[nbr < 0].cpu().numpy(), axis=1)
+    ref = np.sort(m.faces, axis=1)
+    assert set(map(tuple, bf)) == set(map(tuple, ref))
