@@ -391,23 +391,6 @@ __device__ void bitonic_sort(int32_t *a, int n /* power of two */) {
         }
 }
 
-// compacts the sorted array a[0..n) to its distinct values in place; returns the count
-__device__ int unique_sorted(int32_t *a, int n, int32_t *tmp) {
-    long long base = 0;
-    for (int c0 = 0; c0 < n; c0 += blockDim.x) {
-        int i = c0 + threadIdx.x;
-        int keep = (i < n && (i == 0 || a[i] != a[i - 1])) ? 1 : 0;
-        long long tot;
-        long long pos = block_excl_scan(keep, &tot);
-        if (keep) tmp[base + pos] = a[i];
-        base += tot;
-        __syncthreads();
-    }
-    for (int i = threadIdx.x; i < base; i += blockDim.x) a[i] = tmp[i];
-    __syncthreads();
-    return (int)base;
-}
-
 struct TileCounts {
     int32_t n_nodes, n_elems, n_own, n_up, n_diag, n_rows, rank_begin, pad;
 };
@@ -422,9 +405,53 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int32_t 
     return lo;
 }
 
-// Pass A: distinct elements (owned first, each group ascending) and vertex
-// nodes of every tile, plus counts.  An element is owned by the tile holding
-// the row of its first vertex.
+// insert a non-negative key into an open-addressing set in shared memory
+// (H a power of two, empty slots -1); the probe sequence visits every slot, so
+// it ends once the set holds fewer than H keys
+__device__ __forceinline__ void hset_insert(int32_t *tab, int H, int32_t x) {
+    uint32_t h = ((uint32_t)x * 2654435761u) & (uint32_t)(H - 1);
+    for (int probe = 0; probe < H; ++probe) {
+        const int32_t prev = atomicCAS(&tab[h], -1, x);
+        if (prev == -1 || prev == x) return;
+        h = (h + 1) & (uint32_t)(H - 1);
+    }
+}
+
+// the set's keys, in no particular order, into out[0..count); returns count
+// (warp-aggregated slot claims: one shared atomic per warp and pass)
+__device__ int hset_compact(const int32_t *tab, int H, int32_t *out) {
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int c0 = 0; c0 < H; c0 += blockDim.x) {
+        const int i = c0 + threadIdx.x;
+        const int32_t x = i < H ? tab[i] : -1;
+        const unsigned m = __ballot_sync(0xffffffffu, x >= 0);
+        int base = 0;
+        if (lane == 0 && m) base = atomicAdd(&s_cnt, __popc(m));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (x >= 0) out[base + __popc(m & ((1u << lane) - 1u))] = x;
+    }
+    __syncthreads();
+    const int n = s_cnt;
+    __syncthreads();
+    return n;
+}
+
+// sorts a[0..n) ascending (pads to a power of two with INT_MAX; capacity >= that)
+__device__ void sort_small(int32_t *a, int n) {
+    int p = 1;
+    while (p < n) p <<= 1;
+    for (int i = n + threadIdx.x; i < p; i += blockDim.x) a[i] = 0x7fffffff;
+    __syncthreads();
+    bitonic_sort(a, p);
+}
+
+// Pass A of the tile build: the tile's elements (every element incident to
+// one of its rows: deduplicated in a shared-memory hash set, then sorted;
+// owned elements -- those whose first vertex's row is in the tile -- first),
+// the vertex nodes of those elements (likewise), and the counts of its pairs.
 __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e, int cap_n,
                             const int32_t *__restrict__ tile_begin, const int32_t *__restrict__ perm,
                             const int32_t *__restrict__ n2e_ptr, const int32_t *__restrict__ n2e,
@@ -435,31 +462,35 @@ __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e
     extern __shared__ int32_t sm[];
     const int t = blockIdx.x;
     if (t >= n_tiles) return;
-    int32_t *ce = sm;                 // cap_e (power of two)
-    int32_t *cn = sm + cap_e;         // cap_n (power of two)
-    int32_t *tmp = cn + cap_n;        // max(cap_e, cap_n)
+    int32_t *ce = sm;                 // cap_e: the tile's elements
+    int32_t *hs = sm + cap_e;         // 2 cap_n: hash sets, then scratch of the partition
+    int32_t *cn = hs + 2 * cap_n;     // cap_n: the tile's vertex nodes
+    int32_t *tmp = hs;
     const int rb = tile_begin[t];
     const int re = (t + 1 < n_tiles) ? tile_begin[t + 1] : (int)nn;
+    const int He = 2 * cap_e, Hn = 2 * cap_n;
     __shared__ int s_ne;
     if (threadIdx.x == 0) s_ne = 0;
+    for (int i = threadIdx.x; i < He; i += blockDim.x) hs[i] = -1;
     __syncthreads();
     for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
-        int32_t i = perm[r];
-        int32_t b = n2e_ptr[i], e = n2e_ptr[i + 1];
-        int pos = atomicAdd(&s_ne, e - b);
-        for (int32_t q = b; q < e; ++q)
-            if (pos + (q - b) < cap_e) ce[pos + (q - b)] = n2e[q] >> 4;
+        const int32_t i = perm[r];
+        const int32_t b = n2e_ptr[i], e = n2e_ptr[i + 1];
+        atomicAdd(&s_ne, e - b);
     }
     __syncthreads();
     const int ncand = s_ne;
-    if (ncand > cap_e) {
+    if (ncand > cap_e) {   // more candidates than the tile was sized for
         if (threadIdx.x == 0) atomicOr(err, 32);
         return;
     }
-    for (int i = ncand + threadIdx.x; i < cap_e; i += blockDim.x) ce[i] = 0x7fffffff;
+    for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
+        const int32_t i = perm[r];
+        for (int32_t q = n2e_ptr[i]; q < n2e_ptr[i + 1]; ++q) hset_insert(hs, He, n2e[q] >> 4);
+    }
     __syncthreads();
-    bitonic_sort(ce, cap_e);
-    const int n_el = unique_sorted(ce, ncand, tmp);
+    const int n_el = hset_compact(hs, He, ce);
+    sort_small(ce, n_el);
     // owned elements first (stable partition)
     long long obase = 0, hbase = 0, n_own = 0;
     {
@@ -484,6 +515,7 @@ __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e
     }
     __syncthreads();
     for (int i = threadIdx.x; i < n_el; i += blockDim.x) sc_elems[(int64_t)t * cap_e + i] = tmp[i];
+    __syncthreads();
     // vertex nodes of those elements
     const int nv = dim + 1;
     const int nnc = n_el * nv;
@@ -491,11 +523,12 @@ __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e
         if (threadIdx.x == 0) atomicOr(err, 32);
         return;
     }
-    for (int i = threadIdx.x; i < cap_n; i += blockDim.x)
-        cn[i] = (i < nnc) ? elems[(int64_t)ce[i / nv] * nlb + (i % nv)] : 0x7fffffff;
+    for (int i = threadIdx.x; i < Hn; i += blockDim.x) hs[i] = -1;
     __syncthreads();
-    bitonic_sort(cn, cap_n);
-    const int n_nd = unique_sorted(cn, nnc, tmp);
+    for (int i = threadIdx.x; i < nnc; i += blockDim.x) hset_insert(hs, Hn, elems[(int64_t)ce[i / nv] * nlb + (i % nv)]);
+    __syncthreads();
+    const int n_nd = hset_compact(hs, Hn, cn);
+    sort_small(cn, n_nd);
     for (int i = threadIdx.x; i < n_nd; i += blockDim.x) sc_nodes[(int64_t)t * cap_n + i] = cn[i];
     // upper pairs {i, j > i} and diagonals of the tile's rows
     long long up = 0, dg = 0;
@@ -964,7 +997,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         TRY(S.get(&sc_elems, (size_t)n_tiles * cap_e));
         TRY(S.get(&sc_nodes, (size_t)n_tiles * cap_n));
         TRY(S.get(&tcnt, n_tiles));
-        const size_t smemA = sizeof(int32_t) * (cap_e + cap_n + std::max(cap_e, cap_n));
+        const size_t smemA = sizeof(int32_t) * ((size_t)cap_e + 3 * (size_t)cap_n);
         {
             int dev_ = 0, maxsm_ = 0;
             VLA_CUDA(cudaGetDevice(&dev_));
