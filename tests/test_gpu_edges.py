@@ -1,0 +1,140 @@
+"""GPU edge cases: single-element meshes of every type through every entry
+point, isolated nodes, empty reductions, degenerate elements in batches, and
+the documented size limits (rejected before any work)."""
+import ctypes as C
+
+import numpy as np
+import pytest
+import torch
+
+import meshgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL_MIX = 1e-5
+
+
+@pytest.fixture(scope="module")
+def vla():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2404_16039_gb300 as v
+    v.lib()
+    return v
+
+
+def _dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def _single(dim, order):
+    """One reference simplex (scaled, shifted), P2 mid-edge nodes appended."""
+    if dim == 2:
+        X = np.array([[0.1, 0.2], [1.3, 0.25], [0.4, 1.1]])
+        edges = [(0, 1), (1, 2), (0, 2)]
+    else:
+        X = np.array([[0.1, 0.2, 0.3], [1.3, 0.25, 0.35], [0.4, 1.1, 0.3], [0.2, 0.3, 1.4]])
+        edges = [(0, 1), (1, 2), (0, 2), (0, 3), (1, 3), (2, 3)]
+    el = list(range(dim + 1))
+    if order == 2:
+        for a, b in edges:
+            X = np.vstack([X, 0.5 * (X[a] + X[b])])
+            el.append(len(X) - 1)
+    return X, np.array([el], dtype=np.int32)
+
+
+@pytest.mark.parametrize("dim,order", [(2, 1), (2, 2), (3, 1), (3, 2)])
+def test_single_element_everywhere(vla, dim, order):
+    X, E = _single(dim, order)
+    # an isolated node at the end: an empty CSR row, a zero load
+    X = np.vstack([X, np.full((1, dim), 7.0)])
+    gm = vla.Mesh(_dev(X), _dev(E), order=order)
+    ref = oracle.assemble(dim, order, len(X), E, X, 1.1, 0.3, want_pages=True)
+    for prec, tol in ((vla.PREC_FP64, TOL64), (vla.PREC_MIXED, TOL_MIX)):
+        out = gm.assemble(1.1, 0.3, precision=prec, pages=True)
+        for key in ("K", "M", "vol", "K3D", "M3D"):
+            got = out[key].cpu().numpy()
+            assert np.linalg.norm(got - ref[key]) <= tol * np.linalg.norm(ref[key]), (prec, key)
+    rp, ci = gm.csr()
+    assert rp[-1].item() == rp[-2].item()          # the isolated node's row is empty
+    faces, owner, nbr, nb = gm.facets()
+    assert faces.shape[0] == nb == dim + 1 and bool((nbr < 0).all())
+    ip, w = vla.quad_rule(dim, 2)
+    b, b2D = gm.rhs(2, torch.ones((1, len(w)), dtype=torch.float64, device="cuda"))
+    assert b[-1].item() == 0.0
+    vol = ref["vol"][0]
+    assert b.sum().item() == pytest.approx(vol, rel=1e-13)
+    pg = gm.assemble(1.0, 0.0, precision=vla.PREC_FP64, pages=True)
+    u = torch.from_numpy(X[:, 0].copy()).cuda()
+    _, tot = gm.energies(u, pg["K3D"], pg["M3D"], b2D)
+    Jr = oracle.energies(E, X[:, 0], pg["K3D"].cpu().numpy(), pg["M3D"].cpu().numpy(), b2D.cpu().numpy())
+    np.testing.assert_allclose(tot.cpu().numpy(), Jr.sum(axis=0), rtol=1e-12, atol=1e-15)
+
+
+def test_batch_of_single_elements_and_flat_ones(vla):
+    meshes = []
+    for dim, order in ((2, 1), (2, 2), (3, 1), (3, 2)):
+        X, E = _single(dim, order)
+        meshes.append(vla.Mesh(_dev(X), _dev(E), order=order))
+    # a flat tetrahedron (all four vertices in one plane): det 0, counted per job
+    Xf = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], dtype=np.float64)
+    flat = vla.Mesh(_dev(Xf), _dev(np.array([[0, 1, 2, 3]], np.int32)))
+    jobs = [(g, g.outputs(), vla.COEFF_POLY, 1.0, 0.5) for g in meshes] + [(flat, flat.outputs(), 0, 1.0, 0.0)]
+    for form in ("fused", "split"):
+        b = vla.Batch(jobs, precision=vla.PREC_FP64, count_singular=True, form=form)
+        b.run()
+        torch.cuda.synchronize()
+        assert b.n_singular.cpu().tolist() == [0, 0, 0, 0, 1]
+        for g, o, *_ in jobs[:4]:
+            ref = g.assemble(1.0, 0.5, precision=vla.PREC_FP64)
+            assert torch.equal(o["K"], ref["K"]) and torch.equal(o["M"], ref["M"])
+        assert flat.outputs is not None and b.outs[4]["vol"][0].item() == 0.0
+        b.close()
+
+
+def test_server_single_element_request(vla):
+    X, E = _single(3, 2)
+    srv = vla.Server(1 << 28)
+    try:
+        t = srv.submit(X, E, order=2, key=5, ca=1.0, cb=0.0)
+        res = srv.poll(t, timeout=60.0)
+        assert res is not None and res.status == 0 and res.ne == 1
+        got = srv.result(t, res)
+        ref = oracle.assemble(3, 2, len(X), E, X, 1.0, 0.0)
+        assert np.linalg.norm(got["K"].cpu().numpy() - ref["K"]) <= TOL_MIX * np.linalg.norm(ref["K"])
+        srv.release(t)
+    finally:
+        srv.close()
+
+
+def test_empty_reductions_and_batches(vla):
+    sizes = torch.empty(0, dtype=torch.float64, device="cuda")
+    fip = torch.empty((0, 1, 2), dtype=torch.float64, device="cuda")
+    assert vla.gi(fip, [1.0], sizes).cpu().tolist() == [0.0, 0.0]
+    with pytest.raises(ValueError):
+        vla.Batch([])
+    out = vla.amtam(torch.empty((0, 3, 3), device="cuda"), torch.empty((0, 3, 3), device="cuda"))
+    assert out.shape == (0, 3, 3)
+
+
+def test_row_length_limit(vla):
+    # a fan: one centre node in 300 triangles has a CSR row of 302 entries (> 255)
+    n = 300
+    ang = np.linspace(0.0, 2 * np.pi, n + 1)[:-1]
+    X = np.vstack([[0.0, 0.0], np.stack([np.cos(ang), np.sin(ang)], axis=1)])
+    E = np.array([[0, 1 + i, 1 + (i + 1) % n] for i in range(n)], dtype=np.int32)
+    with pytest.raises(vla.VlaError) as e:
+        vla.Mesh(_dev(X), _dev(E))
+    assert e.value.status == -8
+
+
+def test_element_count_limit_rejected_before_work(vla):
+    # ne >= 2^27 is refused from the sizes alone (the arrays are never read)
+    L = vla.lib()
+    dummy = torch.zeros(16, dtype=torch.float64, device="cuda")
+    h = C.c_void_p()
+    st = L.vla_mesh_create(3, 1, 4, 1 << 27, C.c_void_p(dummy.data_ptr()), C.c_void_p(dummy.data_ptr()), 0, None,
+                           None, C.byref(h))
+    assert st == -8 and not h.value
