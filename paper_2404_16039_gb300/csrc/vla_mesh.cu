@@ -185,31 +185,82 @@ __global__ void k_sort_segments(int64_t n, const int32_t *__restrict__ ptr, int3
 }
 
 // sorted-unique neighbour set of node i, built in scratch (capacity nlb * deg(i))
-__global__ void k_row_count(int64_t nn, int nlb, const int32_t *__restrict__ elems,
-                            const int32_t *__restrict__ n2e_ptr, const int32_t *__restrict__ n2e,
-                            int32_t *__restrict__ scratch, int32_t *__restrict__ rowlen, int *__restrict__ err) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t b = n2e_ptr[i], e = n2e_ptr[i + 1];
-        int32_t *u = scratch + (int64_t)nlb * b;
-        int n = 0;
-        for (int32_t t = b; t < e; ++t) {
-            int64_t k = (int64_t)(n2e[t] >> 4);
-            for (int q = 0; q < nlb; ++q) {
-                int32_t c = elems[k * nlb + q];
-                int lo = 0, hi = n;  // first position with u[pos] >= c
-                while (lo < hi) {
-                    int mid = (lo + hi) >> 1;
-                    if (u[mid] < c) lo = mid + 1;
-                    else hi = mid;
+// CSR row sets, one warp per row: every node of every incident element goes
+// into a 512-slot hash set in shared memory (a row longer than kMaxRow is an
+// error, so a set of more than 256 keys is never needed), then the keys are
+// sorted by a warp bitonic sort and written to the row's scratch slot.
+constexpr int kRowWarps = 8, kRowHash = 512;
+__global__ void __launch_bounds__(kRowWarps * 32) k_row_count(int64_t nn, int nlb, const int32_t *__restrict__ elems,
+                                                              const int32_t *__restrict__ n2e_ptr,
+                                                              const int32_t *__restrict__ n2e,
+                                                              int32_t *__restrict__ scratch,
+                                                              int32_t *__restrict__ rowlen, int *__restrict__ err) {
+    __shared__ int32_t hs[kRowWarps][kRowHash];
+    __shared__ int32_t key[kRowWarps][kRowHash / 2];
+    __shared__ int cnt[kRowWarps];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int32_t *tab = hs[w], *ks = key[w];
+    for (int64_t i = (int64_t)blockIdx.x * kRowWarps + w; i < nn; i += (int64_t)gridDim.x * kRowWarps) {
+        for (int q = lane; q < kRowHash; q += 32) tab[q] = -1;
+        if (lane == 0) cnt[w] = 0;
+        __syncwarp();
+        const int32_t b = n2e_ptr[i], e = n2e_ptr[i + 1];
+        const int ncand = (e - b) * nlb;
+        for (int c = lane; c < ncand; c += 32) {
+            const int64_t k = (int64_t)(n2e[b + c / nlb] >> 4);
+            const int32_t x = elems[k * nlb + (c % nlb)];
+            uint32_t h = ((uint32_t)x * 2654435761u) & (kRowHash - 1);
+            for (int probe = 0; probe < kRowHash; ++probe) {
+                const int32_t prev = atomicCAS(&tab[h], -1, x);
+                if (prev == -1) {
+                    atomicAdd(&cnt[w], 1);
+                    break;
                 }
-                if (lo < n && u[lo] == c) continue;
-                for (int s = n; s > lo; --s) u[s] = u[s - 1];
-                u[lo] = c;
-                ++n;
+                if (prev == x) break;
+                h = (h + 1) & (kRowHash - 1);
             }
         }
-        rowlen[i] = n;
-        if (n > kMaxRow) atomicOr(err, ERR_ROWLEN);
+        __syncwarp();
+        const int n = cnt[w];
+        if (n > kMaxRow) {   // too long: report, skip the row
+            if (lane == 0) {
+                atomicOr(err, ERR_ROWLEN);
+                rowlen[i] = 0;
+            }
+            __syncwarp();
+            continue;
+        }
+        // compact, pad to a power of two, bitonic sort within the warp
+        int base = 0;
+        for (int q0 = 0; q0 < kRowHash; q0 += 32) {
+            const int32_t x = tab[q0 + lane];
+            const unsigned m = __ballot_sync(0xffffffffu, x >= 0);
+            if (x >= 0) ks[base + __popc(m & ((1u << lane) - 1u))] = x;
+            base += __popc(m);
+        }
+        int P = 1;
+        while (P < n) P <<= 1;
+        for (int q = n + lane; q < P; q += 32) ks[q] = 0x7fffffff;
+        __syncwarp();
+        for (int kk = 2; kk <= P; kk <<= 1)
+            for (int j = kk >> 1; j > 0; j >>= 1) {
+                for (int q = lane; q < P; q += 32) {
+                    const int l = q ^ j;
+                    if (l > q) {
+                        const bool up = (q & kk) == 0;
+                        const int32_t x = ks[q], y = ks[l];
+                        if ((x > y) == up) {
+                            ks[q] = y;
+                            ks[l] = x;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        int32_t *u = scratch + (int64_t)nlb * b;
+        for (int q = lane; q < n; q += 32) u[q] = ks[q];
+        if (lane == 0) rowlen[i] = n;
+        __syncwarp();
     }
 }
 
@@ -880,7 +931,8 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     int32_t *scratch, *rowlen;
     TRY(S.get(&scratch, (size_t)n2e_total * nlb));
     TRY(S.get(&rowlen, nn));
-    k_row_count<<<grid_for(nn, 128), 128, 0, st>>>(nn, nlb, m->elems, m->n2e_ptr, m->n2e, scratch, rowlen, d_err);
+    k_row_count<<<grid_for((nn + kRowWarps - 1) / kRowWarps, 1), kRowWarps * 32, 0, st>>>(nn, nlb, m->elems, m->n2e_ptr,
+                                                                                        m->n2e, scratch, rowlen, d_err);
     VLA_CUDA(cudaGetLastError());
     long long nnz = 0;
     TRY(excl_scan<int32_t>(rowlen, nn, pre, st, &nnz));
