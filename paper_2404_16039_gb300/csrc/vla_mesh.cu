@@ -169,22 +169,41 @@ __global__ void k_fill_n2e(int64_t ne, int nlb, const int32_t *__restrict__ elem
 }
 
 // insertion sort of every node's incidence list (ascending element id)
-__global__ void k_sort_segments(int64_t n, const int32_t *__restrict__ ptr, int32_t *__restrict__ v) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t b = ptr[i], e = ptr[i + 1];
-        for (int32_t p = b + 1; p < e; ++p) {
-            int32_t x = v[p];
-            int32_t q = p - 1;
-            while (q >= b && v[q] > x) {
-                v[q + 1] = v[q];
-                --q;
+// sorts every segment [ptr[i], ptr[i+1]) of v ascending, one warp per segment:
+// up to 32 keys by a bitonic sort across the lanes (shuffles), longer ones by
+// insertion on one lane
+constexpr int kSegWarps = 8;
+__global__ void __launch_bounds__(kSegWarps * 32) k_sort_segments(int64_t n, const int32_t *__restrict__ ptr,
+                                                                  int32_t *__restrict__ v) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = (int64_t)blockIdx.x * kSegWarps + (threadIdx.x >> 5); i < n;
+         i += (int64_t)gridDim.x * kSegWarps) {
+        const int32_t b = ptr[i], e = ptr[i + 1], len = e - b;
+        if (len <= 1) continue;
+        if (len <= 32) {
+            int32_t x = lane < len ? v[b + lane] : 0x7fffffff;
+            for (int k = 2; k <= 32; k <<= 1)
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const int32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+                    const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+                    x = keep_min ? min(x, y) : max(x, y);
+                }
+            if (lane < len) v[b + lane] = x;
+        } else if (lane == 0) {
+            for (int32_t p = b + 1; p < e; ++p) {
+                const int32_t x = v[p];
+                int32_t q = p - 1;
+                while (q >= b && v[q] > x) {
+                    v[q + 1] = v[q];
+                    --q;
+                }
+                v[q + 1] = x;
             }
-            v[q + 1] = x;
         }
+        __syncwarp();
     }
 }
 
-// sorted-unique neighbour set of node i, built in scratch (capacity nlb * deg(i))
 // CSR row sets, one warp per row: every node of every incident element goes
 // into a 512-slot hash set in shared memory (a row longer than kMaxRow is an
 // error, so a set of more than 256 keys is never needed), then the keys are
@@ -924,7 +943,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     TRY(S.get(&cursor, nn + 1));
     VLA_CUDA(cudaMemcpyAsync(cursor, m->n2e_ptr, sizeof(int32_t) * (nn + 1), cudaMemcpyDeviceToDevice, st));
     k_fill_n2e<<<grid_for(ne, TB), TB, 0, st>>>(ne, nlb, m->elems, cursor, m->n2e);
-    k_sort_segments<<<grid_for(nn, 128), 128, 0, st>>>(nn, m->n2e_ptr, m->n2e);
+    k_sort_segments<<<grid_for((nn + kSegWarps - 1) / kSegWarps, 1), kSegWarps * 32, 0, st>>>(nn, m->n2e_ptr, m->n2e);
     VLA_CUDA(cudaGetLastError());
 
     // ---- CSR pattern
@@ -1005,7 +1024,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     TRY(S.get(&bcur, nkeys + 1));
     VLA_CUDA(cudaMemcpyAsync(bcur, bptr, sizeof(int32_t) * (nkeys + 1), cudaMemcpyDeviceToDevice, st));
     k_bucket_scatter<<<grid_for(nn, TB), TB, 0, st>>>(nn, key, bcur, perm);
-    k_sort_segments<<<grid_for(nkeys, 128), 128, 0, st>>>(nkeys, bptr, perm);
+    k_sort_segments<<<grid_for((nkeys + kSegWarps - 1) / kSegWarps, 1), kSegWarps * 32, 0, st>>>(nkeys, bptr, perm);
     VLA_CUDA(cudaGetLastError());
 
     // ---- tiles: consecutive ranks, incidence-weight budget B
