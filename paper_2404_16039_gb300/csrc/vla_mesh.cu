@@ -1149,11 +1149,11 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         TRY(S.get(&nzpos_rm, o_nz + 2));
         TRY(S.get(&row_info, nn));
         TRY(S.get(&tile_ncodes, n_tiles));
-        k_tile_fill<<<(int)n_tiles, 256, 0, st>>>((int)n_tiles, dim, nlb, cap_e, cap_n, m->tiles, perm, m->n2e_ptr,
+        k_tile_fill<<<(int)n_tiles, 64, 0, st>>>((int)n_tiles, dim, nlb, cap_e, cap_n, m->tiles, perm, m->n2e_ptr,
                                                   m->n2e, m->elems, m->row_ptr, m->col_idx, sc_elems, sc_nodes,
                                                   m->tile_nodes, m->tile_elem, m->tile_own, nzpos_rm, nz_count,
                                                   row_info);
-        k_chunk_table<<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, m->tiles, nz_count, nzpos_rm, m->tile_nzpos, nz_order,
+        k_chunk_table<<<(int)n_tiles, 64, 0, st>>>((int)n_tiles, m->tiles, nz_count, nzpos_rm, m->tile_nzpos, nz_order,
                                                     m->tile_chunks, tile_ncodes);
         VLA_CUDA(cudaGetLastError());
         std::vector<int32_t> hnc(n_tiles);
@@ -1201,7 +1201,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         if (m->order == 1) {
             uint16_t *codes;
             TRY(dalloc(m, &codes, o_code + 64, st));
-            k_tile_codes<uint16_t, 4><<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, m->tiles, perm,
+            k_tile_codes<uint16_t, 4><<<(int)n_tiles, 64, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, m->tiles, perm,
                                                                      m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
                                                                      m->col_idx, sc_elems, row_info, nz_order,
                                                                      m->tile_chunks, fill, codes);
@@ -1209,7 +1209,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         } else {
             uint32_t *codes;
             TRY(dalloc(m, &codes, o_code + 64, st));
-            k_tile_codes<uint32_t, 8><<<(int)n_tiles, 128, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, m->tiles, perm,
+            k_tile_codes<uint32_t, 8><<<(int)n_tiles, 64, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, m->tiles, perm,
                                                                      m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
                                                                      m->col_idx, sc_elems, row_info, nz_order,
                                                                      m->tile_chunks, fill, codes);
