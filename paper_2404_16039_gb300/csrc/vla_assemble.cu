@@ -362,16 +362,16 @@ __device__ __forceinline__ void geo_mixed2(const float4 *__restrict__ sh, const 
     g.xc[2] = 0.f;
 }
 
-// FP64, 3-D and 2-D (coordinates as double4 in shared memory).
+// FP64, 3-D and 2-D (coordinates as 32-byte double quadruples in shared memory).
 template <int DIM>
-__device__ __forceinline__ void geo_f64(const double4 *__restrict__ sx, ushort4 v, Geo<double> &g) {
+__device__ __forceinline__ void geo_f64(const double4_16a *__restrict__ sx, ushort4 v, Geo<double> &g) {
     const unsigned short vi[4] = {v.x, v.y, v.z, v.w};
-    const double4 xl = sx[vi[DIM]];
+    const double4_16a xl = sx[vi[DIM]];
     double V[3][3];
     double cs[3] = {xl.x, xl.y, xl.z};
 #pragma unroll
     for (int j = 0; j < DIM; ++j) {
-        const double4 xj = sx[vi[j]];
+        const double4_16a xj = sx[vi[j]];
         V[j][0] = xj.x - xl.x;
         V[j][1] = xj.y - xl.y;
         V[j][2] = xj.z - xl.z;
@@ -624,7 +624,7 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
     const int32_t *s_gid = reinterpret_cast<const int32_t *>(b + mp.gid);
     const float4 *s_h = reinterpret_cast<const float4 *>(b + mp.xyz);
     const float4 *s_l = s_h + h.n_nodes;
-    const double4 *s_x = reinterpret_cast<const double4 *>(b + mp.xyz);
+    const double4_16a *s_x = reinterpret_cast<const double4_16a *>(b + mp.xyz);
     const T ca = MIX ? (T)J.caf : (T)J.ca, cb = MIX ? (T)J.cbf : (T)J.cb;
     // the job's fields once per tile (a batch keeps the job in shared memory)
     const int kind = J.kind;
@@ -690,7 +690,7 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
                     const float4 hh = s_h[vid[j]], ll = s_l[vid[j]];
                     xv[j][0] = hh.x + ll.x, xv[j][1] = hh.y + ll.y, xv[j][2] = hh.z + ll.z;
                 } else {
-                    const double4 xx = s_x[vid[j]];
+                    const double4_16a xx = s_x[vid[j]];
                     xv[j][0] = xx.x, xv[j][1] = xx.y, xv[j][2] = xx.z;
                 }
             }
@@ -1827,7 +1827,7 @@ __global__ void __launch_bounds__(256) k_static_pages(int64_t ne, const int32_t 
                 geo_mixed2_fast(h, l, make_ushort4(0, 1, 2, 0), g);
             }
         } else {
-            double4 x[C::NV];
+            double4_16a x[C::NV];
 #pragma unroll
             for (int j = 0; j < C::NV; ++j) {
                 const int32_t v = elems[k * C::NLB + j];
