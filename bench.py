@@ -502,6 +502,7 @@ def run_serve(args):
         lat_host = [None] * count
         els = [0] * count
         bsz = [0] * count
+        phases = [None] * count
         fails = {}
         h2d = [0]
         d2h = [0] * n_poll
@@ -523,6 +524,8 @@ def run_serve(args):
                         host[0][:cnt].copy_(vla._view(ptr, cnt, "<f8", dev))
                         d2h[p] += 8 * cnt
                     th = time.monotonic()
+                    phases[i] = (res.t_admit - res.t_submit, res.t_ready - res.t_admit, res.t_start - res.t_ready,
+                                 res.t_done - res.t_start, th - res.t_done)
                     lat[i] = res.t_done - t_arr[i]
                     lat_host[i] = th - t_arr[i]
                     els[i] = res.ne
@@ -558,6 +561,8 @@ def run_serve(args):
                 "p50_ms_to_host": 1e3 * float(np.percentile(LH, 50)),
                 "p99_ms_to_host": 1e3 * float(np.percentile(LH, 99)),
                 "mean_batch": float(np.mean([bsz[i] for i in ok])), "max_batch": int(max(bsz[i] for i in ok)),
+                "mean_phase_ms": dict(zip(("queued", "ingest", "wait_launch", "assembly", "copy_out"),
+                                          (1e3 * float(np.mean([phases[i][c] for i in ok])) for c in range(5)))),
                 "batches": st["n_batches"], "ingested": st["n_ingested"], "reused": st["n_reused"],
                 "evicted": st["n_evicted"], "peak_bytes": st["peak_bytes"], "h2d_bytes": h2d[0], "d2h_bytes": sum(d2h)}
 

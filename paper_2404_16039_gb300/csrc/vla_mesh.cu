@@ -93,7 +93,45 @@ __global__ void k_scan_add(int64_t n, long long *__restrict__ out, const long lo
     if (i < n) out[i] += block_pre[i / (kScanThreads * kScanItems)];
 }
 
-// out[i] = sum_{j<i} in[j] for i in [0, n]; returns the total on the host.
+__global__ void k_i64_to_i32(int64_t n, const long long *__restrict__ in, int32_t *__restrict__ out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (int32_t)in[i];
+}
+
+// Small pinned host buffer for the scalars a build reads back (one per host
+// thread, allocated on first use): device-to-host copies into pageable memory
+// would each wait for the whole stream.
+long long *pinned_scalars() {
+    static thread_local long long *p = nullptr;
+    if (!p && cudaMallocHost((void **)&p, 64 * sizeof(long long)) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+// out[n] = out[n - 1] + in[n - 1] (the total), on the device
+template <typename TI>
+__global__ void k_scan_total(int64_t n, const TI *__restrict__ in, long long *__restrict__ out) {
+    out[n] = n > 0 ? out[n - 1] + (long long)in[n - 1] : 0;
+}
+
+// out[0] = max_i in[i] + add (one block)
+__global__ void k_max_i32(int64_t n, const int32_t *__restrict__ in, int add, long long *__restrict__ out) {
+    __shared__ int s[32];
+    int v = -0x7fffffff;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v = max(v, in[i] + add);
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = max(v, s[w]);
+        out[0] = v;
+    }
+}
+
+// out[i] = sum_{j<i} in[j] for i in [0, n], all on the device; if total_host
+// is given the total is read back (the only synchronisation).
 template <typename TI>
 vla_status excl_scan(const TI *in, int64_t n, long long *out, cudaStream_t st, long long *total_host) {
     const int64_t per = (int64_t)kScanThreads * kScanItems;
@@ -104,28 +142,24 @@ vla_status excl_scan(const TI *in, int64_t n, long long *out, cudaStream_t st, l
     VLA_CUDA(cudaMallocAsync(&bsp, sizeof(long long) * (nb + 1), st));
     k_scan_blocks<TI><<<(int)nb, kScanThreads, 0, st>>>(n, in, out, bs);
     VLA_CUDA(cudaGetLastError());
-    long long tot = 0;
     if (nb > 1) {
-        vla_status s = excl_scan<long long>(bs, nb, bsp, st, &tot);
+        vla_status s = excl_scan<long long>(bs, nb, bsp, st, nullptr);
         if (s) return s;
         k_scan_add<<<grid_for(n, 256, 1 << 30), 256, 0, st>>>(n, out, bsp);
         VLA_CUDA(cudaGetLastError());
-    } else {
-        VLA_CUDA(cudaMemcpyAsync(&tot, bs, sizeof(long long), cudaMemcpyDeviceToHost, st));
-        VLA_CUDA(cudaStreamSynchronize(st));
     }
-    // out[n] = total
-    VLA_CUDA(cudaMemcpyAsync(out + n, &tot, sizeof(long long), cudaMemcpyHostToDevice, st));
-    VLA_CUDA(cudaStreamSynchronize(st));
+    k_scan_total<TI><<<1, 1, 0, st>>>(n, in, out);
+    VLA_CUDA(cudaGetLastError());
     VLA_CUDA(cudaFreeAsync(bs, st));
     VLA_CUDA(cudaFreeAsync(bsp, st));
-    if (total_host) *total_host = tot;
+    if (total_host) {
+        long long *hp = pinned_scalars();
+        if (!hp) return fail(VLA_ERR_OOM, "pinned host scalars");
+        VLA_CUDA(cudaMemcpyAsync(hp, out + n, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        VLA_CUDA(cudaStreamSynchronize(st));
+        *total_host = hp[0];
+    }
     return VLA_OK;
-}
-
-__global__ void k_i64_to_i32(int64_t n, const long long *__restrict__ in, int32_t *__restrict__ out) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = (int32_t)in[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -346,6 +380,16 @@ __global__ void k_split_coords(int64_t nn, int dim, const double *__restrict__ x
 // ---------------------------------------------------------------------------
 // spatial ordering of the rows
 // ---------------------------------------------------------------------------
+// bounding box from the per-block partials (lo[3], hi[3] each)
+__global__ void k_bbox_final(int nb, const double *__restrict__ part, double *__restrict__ bb) {
+    if (threadIdx.x < 6) {
+        const int c = threadIdx.x;
+        double v = c < 3 ? 1e300 : -1e300;
+        for (int b = 0; b < nb; ++b) v = c < 3 ? fmin(v, part[b * 6 + c]) : fmax(v, part[b * 6 + c]);
+        bb[c] = v;
+    }
+}
+
 __global__ void k_bbox_partial(int64_t nn, int dim, const double *__restrict__ x, double *__restrict__ part) {
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nn; i += (int64_t)gridDim.x * blockDim.x)
@@ -923,11 +967,18 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     VLA_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nn, st));
     k_validate_count<<<grid_for(ne, TB), TB, 0, st>>>(ne, nlb, nn, m->elems, cnt, d_err, d_bad);
     VLA_CUDA(cudaGetLastError());
-    int h_err = 0;
-    long long h_bad = 0;
-    VLA_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    VLA_CUDA(cudaMemcpyAsync(&h_bad, d_bad, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    // scalars read back through pinned memory: [0] scan totals, [1] error word,
+    // [2] bad element, [3] max incidence + 1, [4] max row length
+    long long *hp = pinned_scalars();
+    if (!hp) return fail(VLA_ERR_OOM, "pinned host scalars");
+    long long *dsc;
+    TRY(S.get(&dsc, 8));
+    hp[1] = 0;
+    VLA_CUDA(cudaMemcpyAsync(&hp[1], d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VLA_CUDA(cudaMemcpyAsync(&hp[2], d_bad, sizeof(long long), cudaMemcpyDeviceToHost, st));
     VLA_CUDA(cudaStreamSynchronize(st));
+    int h_err = (int)hp[1];
+    const long long h_bad = hp[2];
     if (h_err & ERR_OOB) return fail(VLA_ERR_INDEX_OOB, "element %lld references a node outside [0, %lld)", h_bad, (long long)nn);
     if (h_err & ERR_DUP) return fail(VLA_ERR_DEGENERATE, "element %lld repeats a node", h_bad);
 
@@ -954,9 +1005,13 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
                                                                                         m->n2e, scratch, rowlen, d_err);
     VLA_CUDA(cudaGetLastError());
     long long nnz = 0;
-    TRY(excl_scan<int32_t>(rowlen, nn, pre, st, &nnz));
-    VLA_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    VLA_CUDA(cudaStreamSynchronize(st));
+    k_max_i32<<<1, 256, 0, st>>>(nn, rowlen, 0, dsc + 1);
+    hp[1] = 0;
+    VLA_CUDA(cudaMemcpyAsync(&hp[1], d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VLA_CUDA(cudaMemcpyAsync(&hp[4], dsc + 1, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    TRY(excl_scan<int32_t>(rowlen, nn, pre, st, &nnz));   // synchronises: the copies above have landed
+    h_err = (int)hp[1];
+    m->max_row_len = (int32_t)hp[4];
     if (h_err & ERR_ROWLEN) return fail(VLA_ERR_UNSUPPORTED, "a CSR row has more than %d entries", kMaxRow);
     if (nnz > 0x7fffffffll) return fail(VLA_ERR_UNSUPPORTED, "nnz %lld exceeds int32", nnz);
     m->nnz = nnz;
@@ -971,10 +1026,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         k_face_owner<<<grid_for(nfb, TB), TB, 0, st>>>(nfb, dim, nlb, nn, m->faces, m->elems, m->n2e_ptr, m->n2e,
                                                         m->face_opp, d_err);
         VLA_CUDA(cudaGetLastError());
-        VLA_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-        VLA_CUDA(cudaStreamSynchronize(st));
-        if (h_err & ERR_FACE_OOB) return fail(VLA_ERR_INDEX_OOB, "a boundary facet references a node outside [0, %lld)", (long long)nn);
-        if (h_err & ERR_FACE_OWNER) return fail(VLA_ERR_DEGENERATE, "a boundary facet is not a facet of any element");
+        // its error bits are read with the tile counts below (nothing before reads the facets)
     }
 
     // ---- float pair coordinates
@@ -989,17 +1041,8 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     TRY(S.get(&bbp, nbb * 6));
     TRY(S.get(&bbf, 6));
     k_bbox_partial<<<nbb, 256, 0, st>>>(nn, dim, m->coords, bbp);
+    k_bbox_final<<<1, 32, 0, st>>>(nbb, bbp, bbf);
     VLA_CUDA(cudaGetLastError());
-    double hbb[nbb * 6];
-    VLA_CUDA(cudaMemcpyAsync(hbb, bbp, sizeof(hbb), cudaMemcpyDeviceToHost, st));
-    VLA_CUDA(cudaStreamSynchronize(st));
-    double bb[6] = {1e300, 1e300, 1e300, -1e300, -1e300, -1e300};
-    for (int b = 0; b < nbb; ++b)
-        for (int d = 0; d < 3; ++d) {
-            bb[d] = std::min(bb[d], hbb[b * 6 + d]);
-            bb[3 + d] = std::max(bb[3 + d], hbb[b * 6 + 3 + d]);
-        }
-    VLA_CUDA(cudaMemcpyAsync(bbf, bb, sizeof(bb), cudaMemcpyHostToDevice, st));
     int bits = 1;
     {
         double cells = (double)nn / 8.0;
@@ -1048,18 +1091,16 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         TRY(excl_scan<int32_t>(w, nn, pre, st, nullptr));
         k_tile_flags<<<grid_for(nn, TB), TB, 0, st>>>(nn, B, pre, flag);
         long long n_tiles = 0;
-        TRY(excl_scan<int32_t>(flag, nn, fpre, st, &n_tiles));
+        k_max_i32<<<1, 256, 0, st>>>(nn, cnt, 1, dsc + 2);   // max incidence + 1
+        VLA_CUDA(cudaMemcpyAsync(&hp[3], dsc + 2, sizeof(long long), cudaMemcpyDeviceToHost, st));
+        TRY(excl_scan<int32_t>(flag, nn, fpre, st, &n_tiles));   // synchronises
         TRY(S.get(&tile_begin, n_tiles + 1));
         k_tile_assign<<<grid_for(nn, TB), TB, 0, st>>>(nn, flag, fpre, perm, tile_begin, node_tile);
         VLA_CUDA(cudaGetLastError());
         m->n_tiles = (int32_t)n_tiles;
 
         // max incidence of a single node bounds the tile's candidate count: B + max weight
-        std::vector<int32_t> hcnt(nn);
-        VLA_CUDA(cudaMemcpyAsync(hcnt.data(), cnt, sizeof(int32_t) * nn, cudaMemcpyDeviceToHost, st));
-        VLA_CUDA(cudaStreamSynchronize(st));
-        int wmax = 0;
-        for (int64_t i = 0; i < nn; ++i) wmax = std::max(wmax, hcnt[i] + 1);
+        const int wmax = (int)hp[3];
         if (wmax > B) return fail(VLA_ERR_UNSUPPORTED, "a node belongs to %d elements (tile budget %d)", wmax - 1, B);
         const int cap_e = next_pow2(B + wmax);
         const int cap_n = next_pow2((dim + 1) * (B + wmax));
@@ -1083,8 +1124,13 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         VLA_CUDA(cudaGetLastError());
         std::vector<TileCounts> hc(n_tiles);
         VLA_CUDA(cudaMemcpyAsync(hc.data(), tcnt, sizeof(TileCounts) * n_tiles, cudaMemcpyDeviceToHost, st));
-        VLA_CUDA(cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        hp[1] = 0;
+        VLA_CUDA(cudaMemcpyAsync(&hp[1], d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         VLA_CUDA(cudaStreamSynchronize(st));
+        h_err = (int)hp[1];
+        if (h_err & ERR_FACE_OOB)
+            return fail(VLA_ERR_INDEX_OOB, "a boundary facet references a node outside [0, %lld)", (long long)nn);
+        if (h_err & ERR_FACE_OWNER) return fail(VLA_ERR_DEGENERATE, "a boundary facet is not a facet of any element");
         if (h_err & 32) return fail(VLA_ERR_UNSUPPORTED, "tile candidate capacity exceeded");
 
         // tile offsets (host scan over a few thousand tiles); every segment padded for bulk copies
@@ -1222,13 +1268,6 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     VLA_CUDA(cudaMemsetAsync(m->d_err, 0, sizeof(int32_t), st));
     m->spin_limit = 1 << 22;
     if (const char *sl = getenv("VLA_DEBUG_SPIN_LIMIT")) m->spin_limit = atoi(sl);
-    // max row length (host, from row_ptr)
-    std::vector<int32_t> hrp(nn + 1);
-    VLA_CUDA(cudaMemcpyAsync(hrp.data(), m->row_ptr, sizeof(int32_t) * (nn + 1), cudaMemcpyDeviceToHost, st));
-    VLA_CUDA(cudaStreamSynchronize(st));
-    int mr = 0;
-    for (int64_t i = 0; i < nn; ++i) mr = std::max(mr, hrp[i + 1] - hrp[i]);
-    m->max_row_len = mr;
     return VLA_OK;
 }
 
