@@ -116,18 +116,14 @@ __global__ void k_scan_total(int64_t n, const TI *__restrict__ in, long long *__
     out[n] = n > 0 ? out[n - 1] + (long long)in[n - 1] : 0;
 }
 
-// out[0] = max_i in[i] + add (one block)
+// out[0] = max(out[0], max_i in[i] + add) for non-negative values (out[0]
+// zeroed beforehand); a max is independent of the order of the atomics
 __global__ void k_max_i32(int64_t n, const int32_t *__restrict__ in, int add, long long *__restrict__ out) {
-    __shared__ int s[32];
-    int v = -0x7fffffff;
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v = max(v, in[i] + add);
+    int v = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v = max(v, in[i] + add);
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_down_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = max(v, s[w]);
-        out[0] = v;
-    }
+    if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(reinterpret_cast<unsigned long long *>(out), (unsigned long long)v);
 }
 
 // out[i] = sum_{j<i} in[j] for i in [0, n], all on the device; if total_host
@@ -380,14 +376,18 @@ __global__ void k_split_coords(int64_t nn, int dim, const double *__restrict__ x
 // ---------------------------------------------------------------------------
 // spatial ordering of the rows
 // ---------------------------------------------------------------------------
-// bounding box from the per-block partials (lo[3], hi[3] each)
+// bounding box from the per-block partials (lo[3], hi[3] each): warp c
+// reduces component c
 __global__ void k_bbox_final(int nb, const double *__restrict__ part, double *__restrict__ bb) {
-    if (threadIdx.x < 6) {
-        const int c = threadIdx.x;
-        double v = c < 3 ? 1e300 : -1e300;
-        for (int b = 0; b < nb; ++b) v = c < 3 ? fmin(v, part[b * 6 + c]) : fmax(v, part[b * 6 + c]);
-        bb[c] = v;
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (c >= 6) return;
+    double v = c < 3 ? 1e300 : -1e300;
+    for (int b = lane; b < nb; b += 32) v = c < 3 ? fmin(v, part[b * 6 + c]) : fmax(v, part[b * 6 + c]);
+    for (int o = 16; o > 0; o >>= 1) {
+        const double y = __shfl_down_sync(0xffffffffu, v, o);
+        v = c < 3 ? fmin(v, y) : fmax(v, y);
     }
+    if (lane == 0) bb[c] = v;
 }
 
 __global__ void k_bbox_partial(int64_t nn, int dim, const double *__restrict__ x, double *__restrict__ part) {
@@ -1005,7 +1005,8 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
                                                                                         m->n2e, scratch, rowlen, d_err);
     VLA_CUDA(cudaGetLastError());
     long long nnz = 0;
-    k_max_i32<<<1, 256, 0, st>>>(nn, rowlen, 0, dsc + 1);
+    VLA_CUDA(cudaMemsetAsync(dsc + 1, 0, sizeof(long long), st));
+    k_max_i32<<<grid_for(nn, 256), 256, 0, st>>>(nn, rowlen, 0, dsc + 1);
     hp[1] = 0;
     VLA_CUDA(cudaMemcpyAsync(&hp[1], d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     VLA_CUDA(cudaMemcpyAsync(&hp[4], dsc + 1, sizeof(long long), cudaMemcpyDeviceToHost, st));
@@ -1041,7 +1042,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     TRY(S.get(&bbp, nbb * 6));
     TRY(S.get(&bbf, 6));
     k_bbox_partial<<<nbb, 256, 0, st>>>(nn, dim, m->coords, bbp);
-    k_bbox_final<<<1, 32, 0, st>>>(nbb, bbp, bbf);
+    k_bbox_final<<<1, 192, 0, st>>>(nbb, bbp, bbf);
     VLA_CUDA(cudaGetLastError());
     int bits = 1;
     {
@@ -1091,7 +1092,8 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         TRY(excl_scan<int32_t>(w, nn, pre, st, nullptr));
         k_tile_flags<<<grid_for(nn, TB), TB, 0, st>>>(nn, B, pre, flag);
         long long n_tiles = 0;
-        k_max_i32<<<1, 256, 0, st>>>(nn, cnt, 1, dsc + 2);   // max incidence + 1
+        VLA_CUDA(cudaMemsetAsync(dsc + 2, 0, sizeof(long long), st));
+        k_max_i32<<<grid_for(nn, 256), 256, 0, st>>>(nn, cnt, 1, dsc + 2);   // max incidence + 1
         VLA_CUDA(cudaMemcpyAsync(&hp[3], dsc + 2, sizeof(long long), cudaMemcpyDeviceToHost, st));
         TRY(excl_scan<int32_t>(flag, nn, fpre, st, &n_tiles));   // synchronises
         TRY(S.get(&tile_begin, n_tiles + 1));
