@@ -324,7 +324,8 @@ def run_batch(args):
     out_mix = [g.outputs() for g in gms]
     out_64 = [g.outputs() for g in gms]
     bm = vla.Batch([(g, o, vla.COEFF_POLY, 1.0, 1.0) for g, o in zip(gms, out_mix)], precision=vla.PREC_MIXED,
-                   graph=True, tune=True)
+                   graph=True, tune=args.batch_form == "auto",
+                   form=None if args.batch_form == "auto" else args.batch_form)
     b64 = vla.Batch([(g, o, vla.COEFF_POLY, 1.0, 1.0) for g, o in zip(gms, out_64)], precision=vla.PREC_FP64,
                     graph=True, tune=True)
     forms = {}
@@ -407,7 +408,8 @@ def run_batch(args):
                        "precision": "mixed (f32 element matrices, float-float det and CSR sums, f64 outputs)",
                        "launch": ("one persistent kernel per element type" if bm.split else
                                   "one persistent kernel over the row tiles of every mesh") +
-                                 ", captured in one CUDA graph; form chosen by timing both at creation",
+                                 ", captured in one CUDA graph" + ("; form chosen by timing both at creation"
+                                                                    if args.batch_form == "auto" else ""),
                        "form_ms": forms,
                        "autotuned": tuned, "grid": bm.grid, "work_items": bm.n_work,
                        "smem_per_cta": bm.smem_bytes,
@@ -621,6 +623,7 @@ def main():
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-lo", type=float, default=1e3)
     ap.add_argument("--batch-hi", type=float, default=1e6)
+    ap.add_argument("--batch-form", default="auto", choices=["auto", "fused", "split"])
     ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--calib-requests", type=int, default=3000)
     ap.add_argument("--pollers", type=int, default=4)
