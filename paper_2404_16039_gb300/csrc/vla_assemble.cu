@@ -495,10 +495,12 @@ struct Cfg {
     static constexpr int NLB = ORDER == 1 ? DIM + 1 : (DIM + 1) * (DIM + 2) / 2;
     static constexpr int NU = NLB * (NLB + 1) / 2;            // packed upper triangle
     // record: NU stiffness entries, then the mass scale (or, for the literal
-    // quadrature, NU mass entries).  P1 records are padded to 16 bytes (float4
-    // stores); mixed-precision P2 records, stored entry by entry, take an odd
-    // stride so that the 32 elements of a warp write 32 different banks
-    static constexpr int RS = LIT ? (2 * NU + 3) / 4 * 4 : (ORDER == 2 && MIX) ? ((NU + 1) | 1) : (NU + 1 + 3) / 4 * 4;
+    // quadrature, NU mass entries).  Mixed-precision records take an odd
+    // stride in words: the 32 elements of a warp store an entry to 32
+    // different banks, and the pair phase's reads of random records spread
+    // over all banks (an even stride folds them onto a few).  FP64 records are
+    // padded to 16 bytes (double2 stores).
+    static constexpr int RS = LIT ? (2 * NU + 3) / 4 * 4 : MIX ? ((NU + 1) | 1) : (NU + 1 + 3) / 4 * 4;
     static constexpr int UB = ORDER == 1 ? 4 : 8;              // code = element << UB | entry
     using T = typename std::conditional<MIX, float, double>::type;
     using CT = typename std::conditional<ORDER == 1, uint16_t, uint32_t>::type;
@@ -743,8 +745,7 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
             rec[C::NU] = mscale;
             if constexpr (MIX) {
 #pragma unroll
-                for (int u = 0; u < C::RS; u += 4)
-                    *reinterpret_cast<float4 *>(dst + u) = make_float4(rec[u], rec[u + 1], rec[u + 2], rec[u + 3]);
+                for (int u = 0; u <= C::NU; ++u) dst[u] = rec[u];
             } else {
 #pragma unroll
                 for (int u = 0; u < C::RS; u += 2)
@@ -1073,8 +1074,7 @@ inline int mesh_stage_bytes(const vla_mesh *m) {
     return (int)((m->tile_stage_bytes + 32 * (size_t)m->max_tile_nodes + 16 + 15) / 16 * 16);
 }
 inline size_t mesh_record_bytes(const vla_mesh *m, bool mix, bool lit = false) {
-    const int nlb = m->nlb, nu = nlb * (nlb + 1) / 2,
-              rs = lit ? (2 * nu + 3) / 4 * 4 : (m->order == 2 && mix) ? ((nu + 1) | 1) : (nu + 1 + 3) / 4 * 4;
+    const int nlb = m->nlb, nu = nlb * (nlb + 1) / 2, rs = lit ? (2 * nu + 3) / 4 * 4 : mix ? ((nu + 1) | 1) : (nu + 1 + 3) / 4 * 4;
     return ((size_t)m->max_tile_elems + 1) * rs * (mix ? 4 : 8);
 }
 

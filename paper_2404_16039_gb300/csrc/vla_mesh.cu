@@ -1228,7 +1228,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
             // 30%, records 40% of the two-CTAs-per-SM limit), so a batched launch over
             // meshes of any types, which sizes each part for its largest tile, keeps
             // two CTAs per SM too; above a cap the tiles are cut with a smaller budget
-            const int nu = nlb * (nlb + 1) / 2, rs = m->order == 2 ? ((nu + 1) | 1) : (nu + 1 + 3) / 4 * 4;
+            const int nu = nlb * (nlb + 1) / 2, rs = (nu + 1) | 1;
             const size_t stg = (stage_max + 32 * (size_t)m->max_tile_nodes + 16 + 15) / 16 * 16;
             const size_t rec = ((size_t)m->max_tile_elems + 1) * rs * 4;
             m->tile_smem = 2 * stg + rec;
