@@ -735,12 +735,31 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
         T mscale;
         if constexpr (ORDER == 1) {
             T rec[C::RS];
+            auto u_of = [](int a, int q) { return a < q ? a * C::NLB - a * (a - 1) / 2 + (q - a)
+                                                        : q * C::NLB - q * (q - 1) / 2 + (a - q); };
+            constexpr int D = C::NV - 1;   // the last vertex
 #pragma unroll
             for (int u = 0; u < C::RS; ++u) rec[u] = T(0);
 #pragma unroll
-            for (int a = 0; a < C::NV; ++a)
+            for (int a = 0; a < D; ++a)
 #pragma unroll
-                for (int q = a; q < C::NV; ++q) rec[a * C::NLB - a * (a - 1) / 2 + (q - a)] = sc * dot3<T>(g.C[a], g.C[q]);
+                for (int q = a; q < D; ++q) rec[u_of(a, q)] = sc * dot3<T>(g.C[a], g.C[q]);
+            // every row of K_k sums to zero (the cofactor vectors sum to zero), so
+            // the last vertex's column and diagonal follow from the others:
+            // K(a,D) = -sum_{b<D} K(a,b), K(D,D) = -sum_{a<D} K(a,D)
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                T r = rec[u_of(a, 0)];
+#pragma unroll
+                for (int b = 1; b < D; ++b) r += rec[u_of(a, b)];
+                rec[u_of(a, D)] = -r;
+            }
+            {
+                T r = rec[u_of(0, D)];
+#pragma unroll
+                for (int a = 1; a < D; ++a) r += rec[u_of(a, D)];
+                rec[u_of(D, D)] = -r;
+            }
             mscale = c * adet * T(C::MOFF / C::DFACT);       // off-diagonal mass entry
             rec[C::NU] = mscale;
             if constexpr (MIX) {
