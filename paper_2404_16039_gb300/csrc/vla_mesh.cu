@@ -774,6 +774,7 @@ __global__ void k_chunk_table(int n_tiles, const TileHdr *__restrict__ hdr, cons
     __shared__ int32_t hist[kMaxCount + 1];
     __shared__ int32_t w[1024];
     for (int i = threadIdx.x; i <= kMaxCount; i += blockDim.x) hist[i] = 0;
+    for (int i = threadIdx.x; i < 1024; i += blockDim.x) w[i] = 0;
     __syncthreads();
     for (int q = threadIdx.x; q < h.n_nz; q += blockDim.x) atomicAdd(&hist[min(nz_count[h.nz_off + q], kMaxCount)], 1);
     __syncthreads();
@@ -786,24 +787,29 @@ __global__ void k_chunk_table(int n_tiles, const TileHdr *__restrict__ hdr, cons
         }
     }
     __syncthreads();
-    // stable placement: one thread walks the pairs in row-major order
-    if (threadIdx.x == 0) {
-        for (int q = 0; q < h.n_nz; ++q) {
-            const int c = min(nz_count[h.nz_off + q], kMaxCount);
-            const int32_t nq = hist[c]++;
-            order[h.nz_off + q] = nq;
-            nzpos[h.nz_off + nq] = nzpos_rowmajor[h.nz_off + q];
+    // stable placement: the first warp walks the pairs in row-major order, 32
+    // at a time; a pair's place is its bucket's next slot plus the number of
+    // earlier lanes of its window with the same count
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (int q0 = 0; q0 < h.n_nz; q0 += 32) {
+            const int q = q0 + lane;
+            const bool valid = q < h.n_nz;
+            const int n = valid ? nz_count[h.nz_off + q] : 0;
+            const int c = valid ? min(n, kMaxCount) : -1 - lane;   // invalid lanes match nobody
+            const unsigned peers = __match_any_sync(0xffffffffu, c);
+            const int rank = __popc(peers & ((1u << lane) - 1u));
+            const int base = valid ? hist[c] : 0;
+            __syncwarp();
+            if (valid) {
+                const int32_t nq = base + rank;
+                order[h.nz_off + q] = nq;
+                nzpos[h.nz_off + nq] = nzpos_rowmajor[h.nz_off + q];
+                if ((nq >> 5) < 1024) atomicMax(&w[nq >> 5], n);   // chunk width: its largest count
+                if (rank == 0) hist[c] = base + __popc(peers);
+            }
+            __syncwarp();
         }
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < h.n_chunks; c += blockDim.x) {
-        const int q0 = c * 32, q1 = min(q0 + 32, h.n_nz);
-        int wd = 0;
-        for (int q = 0; q < h.n_nz; ++q) {
-            const int nq = order[h.nz_off + q];
-            if (nq >= q0 && nq < q1) wd = max(wd, nz_count[h.nz_off + q]);
-        }
-        if (c < 1024) w[c] = wd;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
