@@ -405,8 +405,10 @@ typedef struct {
  * outputs, an L2 flush before every timed run) on the sample mesh for each
  * candidate budget (0.5x to 1.5x the default) and then each residency (1, 2,
  * 3, 4 and the occupancy limit) at the best budget, `reps` timed runs each
- * (median), stores the winner and returns it in *best.  coords/elems as for
- * vla_mesh_create.  Allocates scratch; synchronises `stream`. */
+ * (median), stores the winner and returns it in *best.  The default budget and
+ * the occupancy limit are timed first, and another candidate wins only when it
+ * is at least 3 % faster.  coords/elems as for vla_mesh_create.  Allocates
+ * scratch; synchronises `stream`. */
 vla_status vla_autotune(int32_t dim, int32_t order, int32_t precision, int64_t nn, int64_t ne, const double *coords,
                         const int32_t *elems, int32_t reps, void *stream, vla_tune_t *best);
 

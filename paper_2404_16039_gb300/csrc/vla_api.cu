@@ -37,6 +37,13 @@ static std::mutex g_tune_mu;
 static int g_budget[4] = {0, 0, 0, 0};
 static int g_ctas[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
 
+// default incidence budget of a row tile per element type (measured on
+// GB300: the autotuner's choices on single meshes and on mixed batches)
+int tile_budget(int dim, int order) {
+    if (order == 1) return dim == 3 ? 800 : 1024;
+    return dim == 3 ? 480 : 512;
+}
+
 int tuned_budget(int type) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     return (type >= 0 && type < 4) ? g_budget[type] : 0;

@@ -24,6 +24,7 @@ vla_status cuda_fail(cudaError_t e, const char *what);
 // tile used when a mesh is built, and the resident CTAs per SM of the
 // assembly launch per precision.  0 means the library default.
 int tuned_budget(int type);
+int tile_budget(int dim, int order);   // the default per element type
 int tuned_ctas(int type, bool mix);
 void set_tuned(int type, bool mix, int budget, int ctas);
 

@@ -937,11 +937,6 @@ size_t tile_smem_cap() {
 }
 
 // incidence budget of a tile (sum over its rows of 1 + incident elements)
-int tile_budget(int dim, int order) {
-    if (order == 1) return dim == 3 ? 800 : 2048;
-    return dim == 3 ? 384 : 1024;
-}
-
 vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const int32_t *faces) {
     cudaStream_t st = m->stream;
     const int dim = m->dim, nlb = m->nlb;
