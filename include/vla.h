@@ -139,6 +139,9 @@ typedef struct {
  * tiles of the assembly kernel and the owner of every boundary facet.
  *   dim 2 or 3; order VLA_P1 or VLA_P2; nn, ne >= 1.
  *   coords: dim x nn FP64 (device); elems: nlb x ne int32 (device).
+ *   P2 elements list the vertices, then the edge midpoints in the order
+ *   (0,1), (1,2), (0,2)[, (0,3), (1,3), (2,3)]; the mesh must be conforming
+ *   (every element holding an edge uses the same midpoint node for it).
  *   faces:  dim x nfb int32 (device) boundary facets given by vertex nodes
  *           (triangles in 3-D, edges in 2-D), any orientation; NULL if nfb 0.
  * Validation: node indices outside [0, nn) -> VLA_ERR_INDEX_OOB; an element

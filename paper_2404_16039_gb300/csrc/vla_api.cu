@@ -37,11 +37,14 @@ static std::mutex g_tune_mu;
 static int g_budget[4] = {0, 0, 0, 0};
 static int g_ctas[4][2] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
 
-// default incidence budget of a row tile per element type (measured on
-// GB300: the autotuner's choices on single meshes and on mixed batches)
+// default incidence budget of a row tile per element type.  Smaller tiles
+// assemble a little faster in 2-D (the autotuner picks half these budgets
+// there), and P2 tetrahedra assemble faster in batches at 480, but both cost
+// mesh-build time (more tiles; P2 tiles at 480 often exceed the shared-memory
+// caps and are cut again), which dominates ingest-bound serving.
 int tile_budget(int dim, int order) {
-    if (order == 1) return dim == 3 ? 800 : 1024;
-    return dim == 3 ? 480 : 512;
+    if (order == 1) return dim == 3 ? 800 : 2048;
+    return dim == 3 ? 384 : 1024;
 }
 
 int tuned_budget(int type) {
