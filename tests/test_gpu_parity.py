@@ -1,9 +1,10 @@
 """GPU parity: every CUDA entry point against the CPU FP64 oracle on the same
 seeded inputs.
 
-Tolerances (the design doc derives them):
+Tolerances:
   integer work (CSR pattern): bit-exact;
-  FP64 paths: |gpu - ref| <= 1e-12 * max(|ref|, max over the row of |ref|);
+  FP64 paths: |gpu - ref| <= 1e-12 * max(|ref|, max over the row of |ref|)
+  (an FP64 sum of <= 24 terms of one row's magnitude errs by ~24u ~ 5e-15 of it);
   mixed FP32/compensated paths: relative Frobenius error <= 1e-5 per output;
   FP32 page primitives: relative Frobenius error per page <= 1e-5 (scaled by
   the page condition number for inverses).
