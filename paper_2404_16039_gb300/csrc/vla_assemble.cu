@@ -501,7 +501,11 @@ struct Cfg {
     // over all banks (an even stride folds them onto a few).  FP64 records are
     // padded to 16 bytes (double2 stores).
     static constexpr int RS = LIT ? (2 * NU + 3) / 4 * 4 : MIX ? ((NU + 1) | 1) : (NU + 1 + 3) / 4 * 4;
-    static constexpr int UB = ORDER == 1 ? 4 : 8;              // code = element << UB | entry
+    // contribution code = element * RSC + entry: the word offset of the entry
+    // in a record at the mixed-precision stride; element = code / RSC by one
+    // multiply-high with RINV = ceil(2^32 / RSC) (exact for codes below 2^32 / RSC)
+    static constexpr int RSC = (NU + 1) | 1;
+    static constexpr uint32_t RINV = (uint32_t)((0x100000000ull + RSC - 1) / RSC);
     using T = typename std::conditional<MIX, float, double>::type;
     using CT = typename std::conditional<ORDER == 1, uint16_t, uint32_t>::type;
     static constexpr double DFACT = DIM == 3 ? 6.0 : 2.0;      // dim!
@@ -802,7 +806,8 @@ __device__ __forceinline__ void tile_pairs(double *__restrict__ K, double *__res
     using C = Cfg<DIM, ORDER, MIX, LIT>;
     constexpr int MO = LIT ? C::NU : 0;   // literal: the mass entry sits NU past the stiffness entry
     using CT = typename C::CT;
-    constexpr uint32_t UMASK = (1u << C::UB) - 1;
+    static_assert(LIT || !MIX || C::RS == C::RSC, "mixed records sit at the code stride");
+    auto elem_of = [](uint32_t code) { return __umulhi(code, C::RINV); };
     const int2 *s_chk = reinterpret_cast<const int2 *>(b + mp.chk);
     const int2 *s_nz = reinterpret_cast<const int2 *>(b + mp.nz);
     const CT *s_cod = reinterpret_cast<const CT *>(b + mp.cod);
@@ -817,16 +822,36 @@ __device__ __forceinline__ void tile_pairs(double *__restrict__ K, double *__res
             int tt = 0;
             for (; tt + 1 < ch.y; tt += 2) {
                 const uint32_t c0 = cp[tt * 32], c1 = cp[(tt + 1) * 32];
-                const float *r0 = s_k + (c0 >> C::UB) * C::RS, *r1 = s_k + (c1 >> C::UB) * C::RS;
-                const float m0 = LIT ? r0[MO + (c0 & UMASK)] : r0[C::NU], m1 = LIT ? r1[MO + (c1 & UMASK)] : r1[C::NU];
-                ff2_add(h0, l0, pk(r0[c0 & UMASK], m0));
-                ff2_add(h1, l1, pk(r1[c1 & UMASK], m1));
+                const uint32_t e0 = elem_of(c0), e1 = elem_of(c1);
+                float k0, k1, m0, m1;
+                if constexpr (LIT) {
+                    const uint32_t u0 = c0 - e0 * C::RSC, u1 = c1 - e1 * C::RSC;
+                    k0 = s_k[e0 * C::RS + u0];
+                    k1 = s_k[e1 * C::RS + u1];
+                    m0 = s_k[e0 * C::RS + MO + u0];
+                    m1 = s_k[e1 * C::RS + MO + u1];
+                } else {   // the code is the entry's word offset
+                    k0 = s_k[c0];
+                    k1 = s_k[c1];
+                    m0 = s_k[e0 * C::RS + C::NU];
+                    m1 = s_k[e1 * C::RS + C::NU];
+                }
+                ff2_add(h0, l0, pk(k0, m0));
+                ff2_add(h1, l1, pk(k1, m1));
             }
             if (tt < ch.y) {
                 const uint32_t c0 = cp[tt * 32];
-                const float *r0 = s_k + (c0 >> C::UB) * C::RS;
-                const float m0 = LIT ? r0[MO + (c0 & UMASK)] : r0[C::NU];
-                ff2_add(h0, l0, pk(r0[c0 & UMASK], m0));
+                const uint32_t e0 = elem_of(c0);
+                float k0, m0;
+                if constexpr (LIT) {
+                    const uint32_t u0 = c0 - e0 * C::RSC;
+                    k0 = s_k[e0 * C::RS + u0];
+                    m0 = s_k[e0 * C::RS + MO + u0];
+                } else {
+                    k0 = s_k[c0];
+                    m0 = s_k[e0 * C::RS + C::NU];
+                }
+                ff2_add(h0, l0, pk(k0, m0));
             }
             if (q < h.n_nz) {
                 ff2_add(h0, l0, h1);
@@ -844,7 +869,8 @@ __device__ __forceinline__ void tile_pairs(double *__restrict__ K, double *__res
                     mlo *= 2.f;
                 }
                 if constexpr (ORDER == 2) {   // the pair's reference mass entry times the summed scales
-                    const float mh = mhat[cp[0] & UMASK], p = mhi * mh;
+                    const uint32_t cf = cp[0];
+                    const float mh = mhat[cf - elem_of(cf) * C::RSC], p = mhi * mh;
                     mlo = __fmaf_rn(mlo, mh, __fmaf_rn(mhi, mh, -p));
                     mhi = p;
                 }
@@ -862,12 +888,16 @@ __device__ __forceinline__ void tile_pairs(double *__restrict__ K, double *__res
             double ks = 0.0, ms = 0.0;
             for (int tt = 0; tt < ch.y; ++tt) {
                 const uint32_t c0 = cp[tt * 32];
-                const double *r0 = s_k + (c0 >> C::UB) * C::RS;
-                ks += r0[c0 & UMASK];
-                if constexpr (LIT) ms += r0[MO + (c0 & UMASK)];
+                const uint32_t e0 = elem_of(c0), u0 = c0 - e0 * C::RSC;
+                const double *r0 = s_k + e0 * C::RS;
+                ks += r0[u0];
+                if constexpr (LIT) ms += r0[MO + u0];
                 else ms += r0[C::NU];
             }
-            if constexpr (ORDER == 2) ms *= mhat[cp[0] & UMASK];   // the pair's reference mass entry
+            if constexpr (ORDER == 2) {   // the pair's reference mass entry
+                const uint32_t cf = cp[0];
+                ms *= mhat[cf - elem_of(cf) * C::RSC];
+            }
             if (q < h.n_nz) {
                 const int2 pos = s_nz[q];
                 if (ORDER == 1 && !LIT && pos.x == pos.y) ms *= 2.0;

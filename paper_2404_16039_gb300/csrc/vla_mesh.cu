@@ -822,10 +822,11 @@ __global__ void k_chunk_table(int n_tiles, const TileHdr *__restrict__ hdr, cons
     }
 }
 
-// Pass C: contribution codes (local element, packed (a,b) entry), ascending
-// element order per pair; padding slots point at the tile's zero element.
-template <typename CT, int UBITS>
-__global__ void k_tile_codes(int n_tiles, int nv, int nlb, int cap_e, const TileHdr *__restrict__ hdr,
+// Pass C: contribution codes, element * rsc + packed (a,b) entry (the entry's
+// word offset in a record of stride rsc), ascending element order per pair;
+// padding slots point at the tile's zero element.
+template <typename CT>
+__global__ void k_tile_codes(int n_tiles, int nv, int nlb, int cap_e, int rsc, const TileHdr *__restrict__ hdr,
                              const int32_t *__restrict__ perm, const int32_t *__restrict__ n2e_ptr,
                              const int32_t *__restrict__ n2e, const int32_t *__restrict__ elems,
                              const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
@@ -836,7 +837,7 @@ __global__ void k_tile_codes(int n_tiles, int nv, int nlb, int cap_e, const Tile
     if (t >= n_tiles) return;
     const TileHdr h = hdr[t];
     const int32_t *te = sc_elems + (int64_t)t * cap_e;
-    const CT dummy = (CT)((uint32_t)h.n_elems << UBITS);
+    const CT dummy = (CT)((uint32_t)h.n_elems * (uint32_t)rsc);
     for (int i = threadIdx.x; i < h.n_codes; i += blockDim.x) codes[(int64_t)h.code_off + i] = dummy;
     __syncthreads();
     for (int rr = threadIdx.x; rr < h.n_rows; rr += blockDim.x) {
@@ -859,7 +860,7 @@ __global__ void k_tile_codes(int n_tiles, int nv, int nlb, int cap_e, const Tile
                 const int2 ch = chunks[h.chunk_off + chunk];
                 const int p = a < bb ? a : bb, r = a < bb ? bb : a;
                 const uint32_t u = (uint32_t)(p * nlb - p * (p - 1) / 2 + (r - p));
-                codes[(int64_t)h.code_off + ch.x + tt * 32 + lane] = (CT)(((uint32_t)el << UBITS) | u);
+                codes[(int64_t)h.code_off + ch.x + tt * 32 + lane] = (CT)((uint32_t)el * (uint32_t)rsc + u);
             }
         }
     }
@@ -1244,13 +1245,14 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         }
         m->n_codes = o_code;
         VLA_CUDA(cudaMemcpyAsync(m->tiles, hh.data(), sizeof(TileHdr) * n_tiles, cudaMemcpyHostToDevice, st));
+        const int rsc = (nlb * (nlb + 1) / 2 + 1) | 1;   // code stride: the mixed-precision record stride
         int32_t *fill;
         TRY(S.get(&fill, o_nz + 2));
         VLA_CUDA(cudaMemsetAsync(fill, 0, sizeof(int32_t) * (o_nz + 2), st));
         if (m->order == 1) {
             uint16_t *codes;
             TRY(dalloc(m, &codes, o_code + 64, st));
-            k_tile_codes<uint16_t, 4><<<(int)n_tiles, 64, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, m->tiles, perm,
+            k_tile_codes<uint16_t><<<(int)n_tiles, 64, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, rsc, m->tiles, perm,
                                                                      m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
                                                                      m->col_idx, sc_elems, row_info, nz_order,
                                                                      m->tile_chunks, fill, codes);
@@ -1258,7 +1260,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         } else {
             uint32_t *codes;
             TRY(dalloc(m, &codes, o_code + 64, st));
-            k_tile_codes<uint32_t, 8><<<(int)n_tiles, 64, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, m->tiles, perm,
+            k_tile_codes<uint32_t><<<(int)n_tiles, 64, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, rsc, m->tiles, perm,
                                                                      m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
                                                                      m->col_idx, sc_elems, row_info, nz_order,
                                                                      m->tile_chunks, fill, codes);
