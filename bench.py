@@ -19,6 +19,11 @@ resident mesh.
           16 nnz/ne B, volume 8 B).
   cpu_baseline  the FP64 oracle (plain C, one thread) on the same mesh.
 
+Other workloads (--workload): pages (page primitives at N = 1e8), batch (256
+meshes of all four element types in one persistent launch), serve (a Poisson
+request stream through the server), next (the rows beyond the assembly core,
+one timed call each on the bench mesh).
+
 Multi-GPU (torchrun): every rank assembles its own copy of the workload on its
 own GPU (independent problems, no collective on the data path); the reported
 time is the max over ranks.
@@ -607,6 +612,121 @@ def run_serve(args):
     return 0
 
 
+def run_next(args):
+    """The rows beyond the assembly core, each timed on the bench mesh (CUDA
+    events around one call, L2 flushed before each, median of 20 after 3
+    warm-ups): literal-quadrature assembly, facet list, quadrature points, GI
+    integrals, load vector, local energies and avtamav.  Algorithmic bytes:
+    what each call must read and write once (stated per row); achieved =
+    bytes / time against the measured HBM copy bandwidth."""
+    import torch
+    import meshgen
+    import paper_2404_16039_gb300 as vla
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    m = meshgen.kuhn_cube(args.n, jitter=0.1, seed=0)
+    gm = vla.Mesh(torch.from_numpy(m.coords).to(dev), torch.from_numpy(m.elems).to(dev),
+                  torch.from_numpy(m.faces).to(dev))
+    ne, nn, nnz, nfb = gm.ne, gm.nn, gm.nnz, gm.nfb
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peaks, src = _peaks()
+    hbm = peaks["hbm_gbs"]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            flush.zero_()
+            fn()
+        ts = []
+        for _ in range(20):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+
+    fp64_peak = 1250.0   # GFLOP/s, the GB300's nominal dense FP64 rate (a probe measured ~1,000)
+
+    def row(ms, units, unit, nbytes, what, fp64_flops=None, flops_what=None):
+        g = nbytes / (ms * 1e-3) / 1e9
+        r = {"ms": ms, "throughput": units / (ms * 1e-3), "unit": unit, "alg_bytes": int(nbytes),
+             "achieved_gbs": g, "frac_of_measured_hbm": g / hbm, "bytes": what, "bound": "hbm"}
+        if fp64_flops is not None:
+            f = fp64_flops / (ms * 1e-3) / 1e9
+            r.update({"fp64_gflops": f, "frac_of_nominal_fp64": f / fp64_peak, "flops": flops_what})
+            if f / fp64_peak > g / hbm:
+                r["bound"] = "fp64"
+        return r
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    rows = {}
+    K = torch.empty(nnz, dtype=torch.float64, device=dev)
+    M = torch.empty_like(K)
+    vol = torch.empty(ne, dtype=torch.float64, device=dev)
+    bpe = _alg_bytes_per_el(ne, nn, nnz)
+    for name, kind in (("assembly_centroid_coefficient", vla.COEFF_POLY),
+                       ("f1_literal_quadrature_assembly", vla.COEFF_POLY_IP)):
+        ms = timed(lambda: gm.assemble(1.0, 1.0, kind=kind, precision=vla.PREC_MIXED, K=K, M=M, vol=vol))
+        rows[name] = row(ms, ne, "elements/s", bpe * ne, "as the main bench line (elements, coordinates, "
+                         "element-to-nonzero map, K and M, volumes)")
+    faces, owner, nbr, nb = gm.facets()
+    nf = faces.shape[0]
+    ms = timed(lambda: gm.facets())
+    rows["f2_facet_list"] = row(ms, nf, "facets/s", 16 * ne + 8 * 4 * ne + nf * (12 + 8 + 4),
+                                "elements 16 B and their incidence lists (4 x 8 B) per element; per facet "
+                                "3 vertices, owner pair and neighbour")
+    rows["f2_facet_list"]["bound"] = "latency (integer search of incidence lists; two calls: count, then fill)"
+    ip, w = vla.quad_rule(3, 3)
+    nip = len(w)
+    X = gm.quad_points(3)
+    ms = timed(lambda: gm.quad_points(3))
+    rows["f4_quadrature_points_degree3"] = row(ms, ne * nip, "points/s", 16 * ne + 24 * nn + 24 * ne * nip,
+                                               "elements 16 B, coordinates 24 B per node, 3 doubles per point",
+                                               2.0 * ne * nip * 4 * 3, "4 vertices x 3 coordinates FMA per point")
+    rho = (1.0 + X[..., 0] ** 2)[..., None].contiguous()
+    gm.assemble(1.0, 1.0, precision=vla.PREC_FP64, K=K, M=M, vol=vol)
+    ms = timed(lambda: vla.gi(rho, w, vol))
+    rows["f4_gi_integral_degree3"] = row(ms, ne * nip, "points/s", 8 * ne * nip + 8 * ne,
+                                         "one double per point and the element measure",
+                                         2.0 * ne * nip + 2.0 * ne, "weight FMA per point, measure per element")
+    ip2, w2 = vla.quad_rule(3, 2)
+    f = torch.ones((ne, len(w2)), dtype=torch.float64, device=dev)
+    b = torch.empty(nn, dtype=torch.float64, device=dev)
+    b2D = torch.empty((ne, 4), dtype=torch.float64, device=dev)
+    ms = timed(lambda: gm.rhs(2, f, b=b, b2D=b2D))
+    rows["f3_load_vector_degree2"] = row(ms, ne, "elements/s", 8 * ne * len(w2) + 16 * ne + 24 * nn + 32 * ne
+                                         + 8 * nn + 64 * ne,
+                                         "f at the points, elements, coordinates, b2D, b, and the node "
+                                         "gather's incidence lists (4 x 16 B per element)",
+                                         (35.0 + 4 * len(w2) * 3 + 4 + 4) * ne,
+                                         "measure ~35, 3 per point and basis function, scaling, gather adds")
+    pg = gm.assemble(1.0, 1.0, precision=vla.PREC_FP64, pages=True)
+    u = torch.from_numpy(m.coords[:, 0].copy()).to(dev)
+    J = torch.empty((ne, 3), dtype=torch.float64, device=dev)
+    ms = timed(lambda: gm.energies(u, pg["K3D"], pg["M3D"], b2D))
+    rows["f3_local_energies"] = row(ms, ne, "elements/s", 2 * 128 * ne + 32 * ne + 16 * ne + 8 * nn + 24 * ne,
+                                    "K3D and M3D pages (2 x 128 B), b2D, elements, u, J (3 doubles)",
+                                    88.0 * ne, "K u and M u (2 x 16 FMA), two dots and b.u per element")
+    v4 = torch.randn((ne, 4), dtype=torch.float64, device=dev)
+    A4 = pg["K3D"]
+    ms = timed(lambda: vla.avtamav(v4, A4, v4))
+    rows["f3_avtamav_4x4_fp64"] = row(ms, ne, "pages/s", ne * 8 * (4 + 16 + 4 + 1), "v, A, w and the result",
+                                      40.0 * ne, "A w (16 FMA) and v.(A w) (4 FMA) per page")
+    clocks = sampler.stop()
+    line = {"metric": "rows beyond the assembly core, timed on the bench mesh", "unit": "per row",
+            "n_gpus": 1, "workload": "unit cube %d^3 cubes x 6 Kuhn tets (%d tets, %d nodes, %d nonzeros, %d boundary "
+            "facets), interior jitter 0.1h seed 0" % (args.n, ne, nn, nnz, nfb), "peak_gbs": hbm,
+            "peak_source": src, "l2": "flushed before every timed call (512 MiB write)", "rows": rows,
+            "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    gm.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -618,7 +738,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="p1tet", choices=["p1tet", "pages", "batch", "serve"])
+    ap.add_argument("--workload", default="p1tet", choices=["p1tet", "pages", "batch", "serve", "next"])
     ap.add_argument("--pages-n", default="100000000")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-lo", type=float, default=1e3)
@@ -642,6 +762,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "next":
+        return run_next(args)
 
     import torch
     import meshgen

@@ -1280,25 +1280,42 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
 // facet list: facet j of element k (opposite local vertex j) and the other
 // element holding it, found in the incidence list of the facet's first vertex
 // ---------------------------------------------------------------------------
-__global__ void k_facet_neighbors(int64_t ne, int dim, int nlb, const int32_t *__restrict__ elems,
+template <int DIM>
+__global__ void k_facet_neighbors(int64_t ne, int nlb, const int32_t *__restrict__ elems,
                                   const int32_t *__restrict__ n2e_ptr, const int32_t *__restrict__ n2e,
                                   int32_t *__restrict__ nbr, int32_t *__restrict__ flag) {
-    const int nv = dim + 1;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ne * nv; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = t / nv;
-        const int j = (int)(t - k * nv);
-        int32_t fv[3];
+    constexpr int NV = DIM + 1;
+    // vertex ids of element e: one 16-byte load for P1 tetrahedra
+    auto verts = [&](int64_t e, int32_t (&v)[NV]) {
+        if (DIM == 3 && nlb == 4) {
+            const int4 q = __ldg(reinterpret_cast<const int4 *>(elems) + e);
+            v[0] = q.x, v[1] = q.y, v[2] = q.z, v[NV - 1] = q.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) v[i] = __ldg(elems + e * nlb + i);
+        }
+    };
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < ne * NV; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / NV;
+        const int j = (int)(t - k * NV);
+        int32_t kv[NV], fv[DIM];
+        verts(k, kv);
         int q = 0;
-        for (int i = 0; i < nv; ++i)
-            if (i != j) fv[q++] = elems[k * nlb + i];
+#pragma unroll
+        for (int i = 0; i < NV; ++i)
+            if (i != j) fv[q++] = kv[i];
         int32_t found = -1;
         for (int32_t p = n2e_ptr[fv[0]]; p < n2e_ptr[fv[0] + 1] && found < 0; ++p) {
             const int32_t e = n2e[p] >> 4;
             if (e == k) continue;
+            int32_t ev[NV];
+            verts(e, ev);
             int hits = 1;   // fv[0] is in e by construction
-            for (int a = 1; a < dim; ++a)
-                for (int i = 0; i < nv; ++i) hits += elems[(int64_t)e * nlb + i] == fv[a];
-            if (hits == dim) found = e;
+#pragma unroll
+            for (int a = 1; a < DIM; ++a)
+#pragma unroll
+                for (int i = 0; i < NV; ++i) hits += ev[i] == fv[a];
+            if (hits == DIM) found = e;
         }
         nbr[t] = found;
         flag[t] = (found < 0 || found > k) ? 1 : 0;   // listed with the smaller element
@@ -1456,8 +1473,10 @@ extern "C" vla_status vla_mesh_facets(const vla_mesh *m, int32_t *faces, int32_t
     TRY(S.get(&flag, nt));
     TRY(S.get(&bflag, nt));
     TRY(S.get(&pos, nt + 1));
-    k_facet_neighbors<<<grid_for(nt, 256), 256, 0, st>>>(m->ne, m->dim, m->nlb, m->elems, m->n2e_ptr, m->n2e, nbr,
-                                                          flag);
+    if (m->dim == 3)
+        k_facet_neighbors<3><<<grid_for(nt, 256), 256, 0, st>>>(m->ne, m->nlb, m->elems, m->n2e_ptr, m->n2e, nbr, flag);
+    else
+        k_facet_neighbors<2><<<grid_for(nt, 256), 256, 0, st>>>(m->ne, m->nlb, m->elems, m->n2e_ptr, m->n2e, nbr, flag);
     VLA_CUDA(cudaGetLastError());
     long long total = 0, nb = 0;
     TRY(excl_scan<int32_t>(flag, nt, pos, st, &total));
