@@ -616,7 +616,8 @@ def run_next(args):
     """The rows beyond the assembly core, each timed on the bench mesh (CUDA
     events around one call, L2 flushed before each, median of 20 after 3
     warm-ups): literal-quadrature assembly, facet list, quadrature points, GI
-    integrals, load vector, local energies and avtamav.  Algorithmic bytes:
+    integrals, load vector, local energies and avtamav; then the remaining
+    page functions of Section 2.4 on 1e7 FP32 pages.  Algorithmic bytes:
     what each call must read and write once (stated per row); achieved =
     bytes / time against the measured HBM copy bandwidth."""
     import torch
@@ -717,6 +718,26 @@ def run_next(args):
     ms = timed(lambda: vla.avtamav(v4, A4, v4))
     rows["f3_avtamav_4x4_fp64"] = row(ms, ne, "pages/s", ne * 8 * (4 + 16 + 4 + 1), "v, A, w and the result",
                                       40.0 * ne, "A w (16 FMA) and v.(A w) (4 FMA) per page")
+    # the remaining page functions of Section 2.4, FP32 page layout, 1e7 pages
+    NP = 10_000_000
+    g = torch.Generator(device=dev).manual_seed(0)
+    A33 = torch.randn((NP, 3, 3), generator=g, device=dev)
+    A45 = torch.randn((NP, 4, 3), generator=g, device=dev)        # pages 3 x 4
+    B45 = torch.randn((NP, 4, 5), generator=g, device=dev)        # pages 5 x 4
+    v3 = torch.randn((NP, 3), generator=g, device=dev)
+    S = torch.randn((5, 4), generator=g, device=dev)              # 4 x 5
+    Sp = torch.randn((4, 3), generator=g, device=dev)             # 3 x 4
+    s4 = torch.randn(4, generator=g, device=dev)
+    for name, fn, nbytes, what in (
+            ("pages_amt_3x3_f32", lambda: vla.amt(A33), NP * 72, "read 9 and write 9 floats"),
+            ("pages_avtav_3_f32", lambda: vla.avtav(v3, v3), NP * 28, "read 2 x 3 floats (the same array), write 1"),
+            ("pages_amsm_3x4_by_4x5_f32", lambda: vla.amsm(A45, S), NP * 108, "read 12, write 15 floats"),
+            ("pages_amsv_3x4_f32", lambda: vla.amsv(A45, s4), NP * 60, "read 12, write 3 floats"),
+            ("pages_smamt_3x4_by_5x4_f32", lambda: vla.smamt(Sp, B45), NP * 140, "read 20, write 15 floats"),
+            ("pages_svamt_3x4_f32", lambda: vla.svamt(s4, A45), NP * 60, "read 12, write 3 floats")):
+        ms = timed(fn)
+        rows[name] = row(ms, NP, "pages/s", nbytes, what)
+    del A33, A45, B45, v3
     clocks = sampler.stop()
     line = {"metric": "rows beyond the assembly core, timed on the bench mesh", "unit": "per row",
             "n_gpus": 1, "workload": "unit cube %d^3 cubes x 6 Kuhn tets (%d tets, %d nodes, %d nonzeros, %d boundary "

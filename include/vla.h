@@ -113,6 +113,38 @@ vla_status vla_amdet(int32_t dtype, int32_t layout, int64_t N, int32_t n, const 
 vla_status vla_aminv(int32_t dtype, int32_t layout, int64_t N, int32_t n, const void *A, void *Ainv, void *det,
                      int64_t *n_singular, void *stream);
 
+/* amt: C_k = A_k^T (page-wise transpose, pagemtranspose, Section 2.4 and the
+ * transpose map of Section 2.2; the X3D = amt(Y3D) index pages of the
+ * Section 3.5 listings).  A: m x n x N, C: n x m x N, m and n in {2, 3}. */
+vla_status vla_amt(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t n, const void *A, void *C,
+                   void *stream);
+
+/* avtav: out_k = a_k^T b_k (page-wise dot product of two vector arrays,
+ * Section 2.4).  a, b: n x N with n in {2, 3}; out: N values. */
+vla_status vla_avtav(int32_t dtype, int32_t layout, int64_t N, int32_t n, const void *a, const void *b, void *out,
+                     void *stream);
+
+/* Products with one single matrix or vector (Section 2.4: the single object
+ * is copied to every page and multiplied page-wise).  Page arrays as above
+ * (column-major pages, page or SoA layout); the single object S (column-major)
+ * or s is one DEVICE array of the same dtype shared by all pages; every
+ * dimension in [1, 16].
+ *   amsm:  C_k = A_k S,       A: m x p x N, S: p x n, C: m x n x N
+ *          (X_ip = amsm(coords3D, ip) of Section 3.4; dphi = amsm(tjacinv, dshape) of Section 3.5)
+ *   amsv:  y_k = A_k s,       A: m x n x N, s: n, y: m x N
+ *          (f_elems = amsv(fip, w) of Section 3.4)
+ *   smamt: C_k = S A_k^T,     S: m x p, A: n x p x N, C: m x n x N
+ *          (tjac = smamt(dshape, coords3D), the transposed Jacobian of Section 3.5)
+ *   svamt: y_k = s^T A_k^T,   s: n, A: m x n x N, y: 1 x m x N (the values of amsv as rows) */
+vla_status vla_amsm(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t p, int32_t n, const void *A,
+                    const void *S, void *C, void *stream);
+vla_status vla_amsv(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t n, const void *A, const void *s,
+                    void *y, void *stream);
+vla_status vla_smamt(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t p, int32_t n, const void *S,
+                     const void *A, void *C, void *stream);
+vla_status vla_svamt(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t n, const void *s, const void *A,
+                     void *y, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Meshes and assembly (Sections 3.1-3.5)                                    */
 /* ------------------------------------------------------------------------ */

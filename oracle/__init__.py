@@ -49,6 +49,12 @@ def _load():
         lib.orc_astam.argtypes = [_i64, C.c_int, C.c_int, _d, _d, _d]
         lib.orc_avtam.argtypes = [_i64, C.c_int, C.c_int, _d, _d, _d]
         lib.orc_amdet.argtypes = [_i64, C.c_int, _d, _d]
+        lib.orc_amt.argtypes = [_i64, C.c_int, C.c_int, _d, _d]
+        lib.orc_avtav.argtypes = [_i64, C.c_int, _d, _d, _d]
+        lib.orc_amsm.argtypes = [_i64, C.c_int, C.c_int, C.c_int, _d, _d, _d]
+        lib.orc_amsv.argtypes = [_i64, C.c_int, C.c_int, _d, _d, _d]
+        lib.orc_smamt.argtypes = [_i64, C.c_int, C.c_int, C.c_int, _d, _d, _d]
+        lib.orc_svamt.argtypes = [_i64, C.c_int, C.c_int, _d, _d, _d]
         lib.orc_aminv.argtypes = [_i64, C.c_int, _d, _d, vp]
         lib.orc_aminv.restype = _i64
         lib.orc_vectors.argtypes = [C.c_int, _i64, C.c_int, _i, _d, _d]
@@ -119,6 +125,65 @@ def avtam(v, A):
     y = np.empty((N, n))
     _load().orc_avtam(N, p, n, v, A, y)
     return y
+
+
+def amt(A):
+    """C_k = A_k^T (Section 2.4 amt).  A: (N, n, m) = N pages m x n; C: (N, m, n)."""
+    A = _f64(A)
+    N, n, m = A.shape
+    out = np.empty((N, m, n))
+    _load().orc_amt(N, m, n, A, out)
+    return out
+
+
+def avtav(a, b):
+    """out_k = a_k^T b_k (Section 2.4 avtav).  a, b: (N, n)."""
+    a, b = _f64(a), _f64(b)
+    N, n = a.shape
+    out = np.empty(max(N, 1))
+    _load().orc_avtav(N, n, a, b, out)
+    return out[:N]
+
+
+def amsm(A, S):
+    """C_k = A_k S (Section 2.4 amsm).  A: (N, p, m) = pages m x p; S: (n, p) =
+    the p x n matrix; C: (N, n, m)."""
+    A, S = _f64(A), _f64(S)
+    N, p, m = A.shape
+    n = S.shape[0]
+    out = np.empty((N, n, m))
+    _load().orc_amsm(N, m, p, n, A, S, out)
+    return out
+
+
+def amsv(A, s):
+    """y_k = A_k s (Section 2.4 amsv).  A: (N, n, m) = pages m x n; s: (n,); y: (N, m)."""
+    A, s = _f64(A), _f64(s)
+    N, n, m = A.shape
+    out = np.empty((N, m))
+    _load().orc_amsv(N, m, n, A, s, out)
+    return out
+
+
+def smamt(S, A):
+    """C_k = S A_k^T (Section 2.4 smamt).  S: (p, m) = the m x p matrix; A: (N, p, n)
+    = pages n x p; C: (N, n, m)."""
+    S, A = _f64(S), _f64(A)
+    p, m = S.shape
+    N, _, n = A.shape
+    out = np.empty((N, n, m))
+    _load().orc_smamt(N, m, p, n, S, A, out)
+    return out
+
+
+def svamt(s, A):
+    """y_k = s^T A_k^T (Section 2.4 svamt), a 1 x m page.  s: (n,); A: (N, n, m) =
+    pages m x n; y: (N, m)."""
+    s, A = _f64(s), _f64(A)
+    N, n, m = A.shape
+    out = np.empty((N, m))
+    _load().orc_svamt(N, m, n, s, A, out)
+    return out
 
 
 def amdet(A):

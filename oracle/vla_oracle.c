@@ -115,6 +115,69 @@ void orc_avtam(int64_t N, int p, int n, const double *v, const double *A, double
         }
 }
 
+/* C_k = A_k^T (page-wise transpose, pagemtranspose; Section 2.4).
+ * A: m x n pages, C: n x m pages (column-major pages, page-major arrays). */
+void orc_amt(int64_t N, int m, int n, const double *A, double *C) {
+    for (int64_t k = 0; k < N; ++k)
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < n; ++j) C[k * m * n + j + i * n] = A[k * m * n + i + j * m];
+}
+
+/* out_k = a_k^T b_k (page-wise dot product of vector arrays; Section 2.4). */
+void orc_avtav(int64_t N, int n, const double *a, const double *b, double *out) {
+    for (int64_t k = 0; k < N; ++k) {
+        double s = 0.0;
+        for (int r = 0; r < n; ++r) s += a[k * n + r] * b[k * n + r];
+        out[k] = s;
+    }
+}
+
+/* C_k = A_k S: the single matrix S (p x n) copied to every page and
+ * multiplied (amsm, Section 2.4).  A: m x p pages, C: m x n pages. */
+void orc_amsm(int64_t N, int m, int p, int n, const double *A, const double *S, double *C) {
+    for (int64_t k = 0; k < N; ++k)
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < n; ++j) {
+                double s = 0.0;
+                for (int r = 0; r < p; ++r) s += A[k * m * p + i + r * m] * S[r + j * p];
+                C[k * m * n + i + j * m] = s;
+            }
+}
+
+/* y_k = A_k s for the single vector s (amsv, Section 2.4).  A: m x n pages,
+ * y: m values per page. */
+void orc_amsv(int64_t N, int m, int n, const double *A, const double *sv, double *y) {
+    for (int64_t k = 0; k < N; ++k)
+        for (int i = 0; i < m; ++i) {
+            double s = 0.0;
+            for (int r = 0; r < n; ++r) s += A[k * m * n + i + r * m] * sv[r];
+            y[k * m + i] = s;
+        }
+}
+
+/* C_k = S A_k^T for the single matrix S (m x p) (smamt, Section 2.4).
+ * A: n x p pages, C: m x n pages. */
+void orc_smamt(int64_t N, int m, int p, int n, const double *S, const double *A, double *C) {
+    for (int64_t k = 0; k < N; ++k)
+        for (int i = 0; i < m; ++i)
+            for (int j = 0; j < n; ++j) {
+                double s = 0.0;
+                for (int r = 0; r < p; ++r) s += S[i + r * m] * A[k * n * p + j + r * n];
+                C[k * m * n + i + j * m] = s;
+            }
+}
+
+/* y_k = s^T A_k^T for the single vector s (svamt, Section 2.4): a 1 x m page.
+ * A: m x n pages. */
+void orc_svamt(int64_t N, int m, int n, const double *sv, const double *A, double *y) {
+    for (int64_t k = 0; k < N; ++k)
+        for (int j = 0; j < m; ++j) {
+            double s = 0.0;
+            for (int r = 0; r < n; ++r) s += sv[r] * A[k * m * n + j + r * m];
+            y[k * m + j] = s;
+        }
+}
+
 /* det_k = det(A_k), signed (Section 2.3 eq. of det_W; Section 3.2 example). */
 void orc_amdet(int64_t N, int n, const double *A, double *det) {
     for (int64_t k = 0; k < N; ++k) det[k] = det_small(n, A + k * n * n);

@@ -20,7 +20,8 @@ import threading
 import torch
 
 __all__ = [
-    "VlaError", "lib", "version", "amtam", "astam", "avtam", "amdet", "aminv", "Mesh", "element_pages_static",
+    "VlaError", "lib", "version", "amtam", "astam", "avtam", "amdet", "aminv", "amt", "avtav", "amsm", "amsv",
+    "smamt", "svamt", "Mesh", "element_pages_static",
     "Batch", "batch_assemble", "autotune", "tune_get", "tune_set", "Server", "PENDING", "quad_rule", "gi",
     "avtamav", "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP", "COEFF_POLY_IP", "COEFF_EXP_IP",
 ]
@@ -116,6 +117,12 @@ def lib():
         L.vla_avtam.argtypes = [i32, i32, i64, i32, i32, vp, vp, vp, vp]
         L.vla_amdet.argtypes = [i32, i32, i64, i32, vp, vp, vp]
         L.vla_aminv.argtypes = [i32, i32, i64, i32, vp, vp, vp, vp, vp]
+        L.vla_amt.argtypes = [i32, i32, i64, i32, i32, vp, vp, vp]
+        L.vla_avtav.argtypes = [i32, i32, i64, i32, vp, vp, vp, vp]
+        L.vla_amsm.argtypes = [i32, i32, i64, i32, i32, i32, vp, vp, vp, vp]
+        L.vla_amsv.argtypes = [i32, i32, i64, i32, i32, vp, vp, vp, vp]
+        L.vla_smamt.argtypes = [i32, i32, i64, i32, i32, i32, vp, vp, vp, vp]
+        L.vla_svamt.argtypes = [i32, i32, i64, i32, i32, vp, vp, vp, vp]
         L.vla_mesh_create.argtypes = [i32, i32, i64, i64, vp, vp, i64, vp, vp, C.POINTER(vp)]
         L.vla_mesh_info.argtypes = [vp, C.POINTER(MeshInfo)]
         L.vla_mesh_csr.argtypes = [vp, vp, vp, vp]
@@ -281,6 +288,75 @@ def aminv(A, out=None, det=None, want_det=True, count_singular=True, layout=LAYO
     _check(lib().vla_aminv(_dtype_code(A), layout, N, n, _p(A), _p(out), _p(det) if want_det else None, _p(ns),
                            _stream(stream)))
     return out, (det if want_det else None), ns
+
+
+def amt(A, out=None, layout=LAYOUT_PAGE, stream=None):
+    """C_k = A_k^T (amt).  A: m x n pages -> n x m pages."""
+    _req(A)
+    N, m, n = _page_dims(A, layout)
+    out = _new_pages(N, n, m, layout, A) if out is None else _req(out, A.dtype)
+    _check(lib().vla_amt(_dtype_code(A), layout, N, m, n, _p(A), _p(out), _stream(stream)))
+    return out
+
+
+def avtav(a, b, out=None, layout=LAYOUT_PAGE, stream=None):
+    """out_k = a_k^T b_k (avtav).  a, b: (N, n) page layout or (n, N) SoA."""
+    _req(a), _req(b, a.dtype)
+    N, n = a.shape if layout == LAYOUT_PAGE else a.shape[::-1]
+    if b.shape != a.shape:
+        raise ValueError("avtav: a and b must have the same shape")
+    out = torch.empty(N, dtype=a.dtype, device=a.device) if out is None else _req(out, a.dtype)
+    _check(lib().vla_avtav(_dtype_code(a), layout, N, n, _p(a), _p(b), _p(out), _stream(stream)))
+    return out
+
+
+def amsm(A, S, out=None, layout=LAYOUT_PAGE, stream=None):
+    """C_k = A_k S (amsm).  A: m x p pages; S: one p x n matrix as a (n, p)
+    tensor (its columns, column-major like a page) -> m x n pages."""
+    _req(A), _req(S, A.dtype)
+    N, m, p = _page_dims(A, layout)
+    n, p2 = S.shape
+    if p2 != p:
+        raise ValueError("amsm: S must have p rows")
+    out = _new_pages(N, m, n, layout, A) if out is None else _req(out, A.dtype)
+    _check(lib().vla_amsm(_dtype_code(A), layout, N, m, p, n, _p(A), _p(S), _p(out), _stream(stream)))
+    return out
+
+
+def amsv(A, s, out=None, layout=LAYOUT_PAGE, stream=None):
+    """y_k = A_k s (amsv).  A: m x n pages; s: (n,) -> (N, m) page layout or (m, N) SoA."""
+    _req(A), _req(s, A.dtype)
+    N, m, n = _page_dims(A, layout)
+    if s.numel() != n:
+        raise ValueError("amsv: s must hold n values")
+    out = _new_vec(N, m, layout, A) if out is None else _req(out, A.dtype)
+    _check(lib().vla_amsv(_dtype_code(A), layout, N, m, n, _p(A), _p(s), _p(out), _stream(stream)))
+    return out
+
+
+def smamt(S, A, out=None, layout=LAYOUT_PAGE, stream=None):
+    """C_k = S A_k^T (smamt).  S: one m x p matrix as a (p, m) tensor; A: n x p
+    pages -> m x n pages."""
+    _req(A), _req(S, A.dtype)
+    N, n, p = _page_dims(A, layout)
+    p2, m = S.shape
+    if p2 != p:
+        raise ValueError("smamt: S must have p columns")
+    out = _new_pages(N, m, n, layout, A) if out is None else _req(out, A.dtype)
+    _check(lib().vla_smamt(_dtype_code(A), layout, N, m, p, n, _p(S), _p(A), _p(out), _stream(stream)))
+    return out
+
+
+def svamt(s, A, out=None, layout=LAYOUT_PAGE, stream=None):
+    """y_k = s^T A_k^T (svamt), a 1 x m page per k.  s: (n,); A: m x n pages ->
+    (N, m) page layout or (m, N) SoA."""
+    _req(A), _req(s, A.dtype)
+    N, m, n = _page_dims(A, layout)
+    if s.numel() != n:
+        raise ValueError("svamt: s must hold n values")
+    out = _new_vec(N, m, layout, A) if out is None else _req(out, A.dtype)
+    _check(lib().vla_svamt(_dtype_code(A), layout, N, m, n, _p(s), _p(A), _p(out), _stream(stream)))
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -10,6 +10,7 @@
 //    stores.  Misaligned pointers and the tail chunk take a plain path.
 //  * SoA layout (page index fastest): one page per thread, every load and
 //    store coalesced across the warp.
+#include <algorithm>
 #include <mutex>
 
 #include "vla_internal.cuh"
@@ -72,6 +73,30 @@ struct OpAvtam {  // y (1 x N) = v^T A, A: P x N
             for (int r = 0; r < P; ++r) s += v[r] * a[r + j * P];
             y[j] = s;
         }
+        return false;
+    }
+};
+
+template <typename T, int M, int N>
+struct OpAmt {  // C (N x M) = A^T, A: M x N (pagemtranspose)
+    static constexpr int I0 = M * N, I1 = 0, O0 = M * N, O1 = 0;
+    __device__ static bool apply(const T *a, const T *, T *c, T *) {
+#pragma unroll
+        for (int j = 0; j < N; ++j)
+#pragma unroll
+            for (int i = 0; i < M; ++i) c[j + i * N] = a[i + j * M];
+        return false;
+    }
+};
+
+template <typename T, int N>
+struct OpAvtav {  // s = a^T b, a and b: N-vectors
+    static constexpr int I0 = N, I1 = N, O0 = 1, O1 = 0;
+    __device__ static bool apply(const T *a, const T *b, T *c, T *) {
+        T s = 0;
+#pragma unroll
+        for (int r = 0; r < N; ++r) s += a[r] * b[r];
+        c[0] = s;
         return false;
     }
 };
@@ -259,6 +284,48 @@ __global__ void k_page_soa(int64_t N, const T *__restrict__ in0, const T *__rest
     if (n_sing && local_sing) atomicAdd(n_sing, local_sing);
 }
 
+// ---------------------------------------------------------------------------
+// products with one single matrix or vector (shapes chosen at run time, up to
+// kBcastMax per side): one page per thread, the single object read through
+// the read-only cache from device memory.  Page entry (i, j) of an r x c page
+// k sits at k r c + i + j r (page layout) or (i + j r) N + k (SoA).
+// ---------------------------------------------------------------------------
+constexpr int kBcastMax = 16;
+enum BcastOp { kAmsm, kAmsv, kSmamt, kSvamt };
+
+template <typename T>
+__global__ void k_page_bcast(int op, int64_t N, int soa, int m, int p, int n, const T *__restrict__ A,
+                             const T *__restrict__ S, T *__restrict__ C) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        if (op == kAmsm) {   // A: m x p, S: p x n, C: m x n
+            auto a = [&](int i, int r) { return soa ? A[(int64_t)(i + r * m) * N + k] : A[k * m * p + i + r * m]; };
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < m; ++i) {
+                    T acc = 0;
+                    for (int r = 0; r < p; ++r) acc += a(i, r) * __ldg(S + r + j * p);
+                    const int64_t o = soa ? (int64_t)(i + j * m) * N + k : k * m * n + i + j * m;
+                    C[o] = acc;
+                }
+        } else if (op == kSmamt) {   // S: m x p, A: n x p, C = S A^T: m x n
+            auto a = [&](int j, int r) { return soa ? A[(int64_t)(j + r * n) * N + k] : A[k * n * p + j + r * n]; };
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < m; ++i) {
+                    T acc = 0;
+                    for (int r = 0; r < p; ++r) acc += __ldg(S + i + r * m) * a(j, r);
+                    const int64_t o = soa ? (int64_t)(i + j * m) * N + k : k * m * n + i + j * m;
+                    C[o] = acc;
+                }
+        } else {   // amsv / svamt: A: m x p, s: p, y_i = sum_r A(i, r) s_r (an m x 1 or 1 x m page)
+            auto a = [&](int i, int r) { return soa ? A[(int64_t)(i + r * m) * N + k] : A[k * m * p + i + r * m]; };
+            for (int i = 0; i < m; ++i) {
+                T acc = 0;
+                for (int r = 0; r < p; ++r) acc += a(i, r) * __ldg(S + r);
+                C[soa ? (int64_t)i * N + k : k * m + i] = acc;
+            }
+        }
+    }
+}
+
 int g_num_sms = 0;
 int *g_err_flag[64] = {nullptr};
 
@@ -437,4 +504,76 @@ extern "C" vla_status vla_aminv(int32_t dtype, int32_t layout, int64_t N, int32_
         return n == 2 ? launch_op<OpAminv<T, 2, false>, T>(layout, N, A, nullptr, Ainv, nullptr, ns, s)
                       : launch_op<OpAminv<T, 3, false>, T>(layout, N, A, nullptr, Ainv, nullptr, ns, s);
     }()));
+}
+
+extern "C" vla_status vla_amt(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t n, const void *A, void *C,
+                              void *stream) {
+    vla_status st = check_common(dtype, layout, N);
+    if (st) return st;
+    if (!dim_ok(m) || !dim_ok(n)) return fail(VLA_ERR_INVALID_ARG, "amt: m, n must be 2 or 3");
+    if (N > 0 && (!A || !C)) return fail(VLA_ERR_INVALID_ARG, "amt: null array");
+    cudaStream_t s = (cudaStream_t)stream;
+    int code = (m - 2) * 2 + (n - 2);
+    return DISPATCH_T(dtype, ([&]() -> vla_status {
+        switch (code) {
+        case 0: return launch_op<OpAmt<T, 2, 2>, T>(layout, N, A, nullptr, C, nullptr, nullptr, s);
+        case 1: return launch_op<OpAmt<T, 2, 3>, T>(layout, N, A, nullptr, C, nullptr, nullptr, s);
+        case 2: return launch_op<OpAmt<T, 3, 2>, T>(layout, N, A, nullptr, C, nullptr, nullptr, s);
+        default: return launch_op<OpAmt<T, 3, 3>, T>(layout, N, A, nullptr, C, nullptr, nullptr, s);
+        }
+    }()));
+}
+
+extern "C" vla_status vla_avtav(int32_t dtype, int32_t layout, int64_t N, int32_t n, const void *a, const void *b,
+                                void *out, void *stream) {
+    vla_status st = check_common(dtype, layout, N);
+    if (st) return st;
+    if (!dim_ok(n)) return fail(VLA_ERR_INVALID_ARG, "avtav: n must be 2 or 3");
+    if (N > 0 && (!a || !b || !out)) return fail(VLA_ERR_INVALID_ARG, "avtav: null array");
+    cudaStream_t s = (cudaStream_t)stream;
+    return DISPATCH_T(dtype, ([&]() -> vla_status {
+        return n == 2 ? launch_op<OpAvtav<T, 2>, T>(layout, N, a, b, out, nullptr, nullptr, s)
+                      : launch_op<OpAvtav<T, 3>, T>(layout, N, a, b, out, nullptr, nullptr, s);
+    }()));
+}
+
+namespace {
+vla_status launch_bcast(const char *name, int op, int32_t dtype, int32_t layout, int64_t N, int m, int p, int n,
+                        const void *A, const void *S, void *C, void *stream) {
+    vla_status st = check_common(dtype, layout, N);
+    if (st) return st;
+    if (m < 1 || p < 1 || n < 1 || m > kBcastMax || p > kBcastMax || n > kBcastMax)
+        return fail(VLA_ERR_INVALID_ARG, "%s: dimensions must be in [1, %d]", name, kBcastMax);
+    if (N > 0 && (!A || !S || !C)) return fail(VLA_ERR_INVALID_ARG, "%s: null array", name);
+    if (N == 0) return VLA_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int soa = layout == VLA_LAYOUT_SOA;
+    const int g = grid_for(N, 256, (int64_t)num_sms() * 16);
+    if (dtype == VLA_F32)
+        k_page_bcast<float><<<g, 256, 0, s>>>(op, N, soa, m, p, n, (const float *)A, (const float *)S, (float *)C);
+    else
+        k_page_bcast<double><<<g, 256, 0, s>>>(op, N, soa, m, p, n, (const double *)A, (const double *)S, (double *)C);
+    VLA_CUDA(cudaGetLastError());
+    return VLA_OK;
+}
+}  // namespace
+
+extern "C" vla_status vla_amsm(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t p, int32_t n,
+                               const void *A, const void *S, void *C, void *stream) {
+    return launch_bcast("amsm", kAmsm, dtype, layout, N, m, p, n, A, S, C, stream);
+}
+
+extern "C" vla_status vla_amsv(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t n, const void *A,
+                               const void *sv, void *y, void *stream) {
+    return launch_bcast("amsv", kAmsv, dtype, layout, N, m, n, 1, A, sv, y, stream);
+}
+
+extern "C" vla_status vla_smamt(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t p, int32_t n,
+                                const void *S, const void *A, void *C, void *stream) {
+    return launch_bcast("smamt", kSmamt, dtype, layout, N, m, p, n, A, S, C, stream);
+}
+
+extern "C" vla_status vla_svamt(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t n, const void *sv,
+                                const void *A, void *y, void *stream) {
+    return launch_bcast("svamt", kSvamt, dtype, layout, N, m, n, 1, A, sv, y, stream);
 }
