@@ -723,7 +723,6 @@ def run_next(args):
     g = torch.Generator(device=dev).manual_seed(0)
     A33 = torch.randn((NP, 3, 3), generator=g, device=dev)
     A45 = torch.randn((NP, 4, 3), generator=g, device=dev)        # pages 3 x 4
-    B45 = torch.randn((NP, 4, 5), generator=g, device=dev)        # pages 5 x 4
     v3 = torch.randn((NP, 3), generator=g, device=dev)
     S = torch.randn((5, 4), generator=g, device=dev)              # 4 x 5
     Sp = torch.randn((4, 3), generator=g, device=dev)             # 3 x 4
@@ -733,11 +732,12 @@ def run_next(args):
             ("pages_avtav_3_f32", lambda: vla.avtav(v3, v3), NP * 28, "read 2 x 3 floats (the same array), write 1"),
             ("pages_amsm_3x4_by_4x5_f32", lambda: vla.amsm(A45, S), NP * 108, "read 12, write 15 floats"),
             ("pages_amsv_3x4_f32", lambda: vla.amsv(A45, s4), NP * 60, "read 12, write 3 floats"),
-            ("pages_smamt_3x4_by_5x4_f32", lambda: vla.smamt(Sp, B45), NP * 140, "read 20, write 15 floats"),
+            ("pages_smamt_3x4_by_3x4_f32", lambda: vla.smamt(Sp, A45), NP * 84,
+             "read 12, write 9 floats (tjac = smamt(dshape, coords3D))"),
             ("pages_svamt_3x4_f32", lambda: vla.svamt(s4, A45), NP * 60, "read 12, write 3 floats")):
         ms = timed(fn)
         rows[name] = row(ms, NP, "pages/s", nbytes, what)
-    del A33, A45, B45, v3
+    del A33, A45, v3
     clocks = sampler.stop()
     line = {"metric": "rows beyond the assembly core, timed on the bench mesh", "unit": "per row",
             "n_gpus": 1, "workload": "unit cube %d^3 cubes x 6 Kuhn tets (%d tets, %d nodes, %d nonzeros, %d boundary "

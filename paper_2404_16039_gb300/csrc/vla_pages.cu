@@ -326,6 +326,67 @@ __global__ void k_page_bcast(int op, int64_t N, int soa, int m, int p, int n, co
     }
 }
 
+// The same products for a page of compile-time shape R x CC held in
+// registers; the single object's other dimension (`other`) stays a run-time
+// loop.  amsm/amsv: page A (R x CC) times S (CC x other) -> R x other.
+// smamt: S (other x CC) times the transposed page (R x CC) -> other x R.
+template <typename T, int R, int CC>
+__global__ void k_page_bcast_rc(int op, int64_t N, int soa, int other, const T *__restrict__ A,
+                                const T *__restrict__ S, T *__restrict__ C) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < N; k += (int64_t)gridDim.x * blockDim.x) {
+        T a[R * CC];
+#pragma unroll
+        for (int e = 0; e < R * CC; ++e) a[e] = soa ? A[(int64_t)e * N + k] : A[k * (R * CC) + e];
+        if (op == kSmamt) {
+            for (int i = 0; i < other; ++i) {
+                T srow[CC];
+#pragma unroll
+                for (int r = 0; r < CC; ++r) srow[r] = __ldg(S + i + r * other);
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    T acc = 0;
+#pragma unroll
+                    for (int r = 0; r < CC; ++r) acc += srow[r] * a[j + r * R];
+                    const int e = i + j * other;
+                    C[soa ? (int64_t)e * N + k : k * (other * R) + e] = acc;
+                }
+            }
+        } else {
+            for (int j = 0; j < other; ++j) {
+                T scol[CC];
+#pragma unroll
+                for (int r = 0; r < CC; ++r) scol[r] = __ldg(S + r + j * CC);
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    T acc = 0;
+#pragma unroll
+                    for (int r = 0; r < CC; ++r) acc += a[i + r * R] * scol[r];
+                    const int e = i + j * R;
+                    C[soa ? (int64_t)e * N + k : k * (R * other) + e] = acc;
+                }
+            }
+        }
+    }
+}
+
+// launches the register-page kernel when the page shape is one of the
+// instantiated ones (rows 1-3; columns 2, 3, 4, 6, 10: vertices, P2 nodes and
+// the quadrature points of the Section 3.4/3.5 uses); false otherwise
+template <typename T>
+bool launch_bcast_rc(int op, int64_t N, int soa, int R, int CC, int other, const T *A, const T *S, T *C, int g,
+                     cudaStream_t st) {
+#define VLA_RC(r_, c_)                                                                            \
+    if (R == r_ && CC == c_) {                                                                    \
+        k_page_bcast_rc<T, r_, c_><<<g, 256, 0, st>>>(op, N, soa, other, A, S, C);                \
+        return true;                                                                              \
+    }
+#define VLA_RC_ROW(r_) VLA_RC(r_, 2) VLA_RC(r_, 3) VLA_RC(r_, 4) VLA_RC(r_, 6) VLA_RC(r_, 10)
+    VLA_RC_ROW(1) VLA_RC_ROW(2) VLA_RC_ROW(3)
+#undef VLA_RC_ROW
+#undef VLA_RC
+    return false;
+}
+
 int g_num_sms = 0;
 int *g_err_flag[64] = {nullptr};
 
@@ -549,6 +610,17 @@ vla_status launch_bcast(const char *name, int op, int32_t dtype, int32_t layout,
     cudaStream_t s = (cudaStream_t)stream;
     const int soa = layout == VLA_LAYOUT_SOA;
     const int g = grid_for(N, 256, (int64_t)num_sms() * 16);
+    // page shape and the single object's other dimension
+    const int R = op == kSmamt ? n : m, CC = p, other = op == kSmamt ? m : n;
+    const bool fast = dtype == VLA_F32
+                          ? launch_bcast_rc<float>(op, N, soa, R, CC, other, (const float *)A, (const float *)S,
+                                                   (float *)C, g, s)
+                          : launch_bcast_rc<double>(op, N, soa, R, CC, other, (const double *)A, (const double *)S,
+                                                    (double *)C, g, s);
+    if (fast) {
+        VLA_CUDA(cudaGetLastError());
+        return VLA_OK;
+    }
     if (dtype == VLA_F32)
         k_page_bcast<float><<<g, 256, 0, s>>>(op, N, soa, m, p, n, (const float *)A, (const float *)S, (float *)C);
     else
