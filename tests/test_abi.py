@@ -63,6 +63,30 @@ def test_argument_validation_without_gpu(libpath):
     assert lib.vla_mesh_create(3, 1, 10, 1 << 27, None, None, 0, None, None, ctypes.byref(h)) == -8
 
 
+def test_page_function_argument_validation_without_gpu(libpath):
+    # the Section 2.4 page functions beyond the core: shape, dtype and pointer
+    # checks run before any CUDA call; zero pages are a no-op
+    lib = ctypes.CDLL(libpath)
+    i32, i64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    lib.vla_amt.argtypes = [i32, i32, i64, i32, i32, vp, vp, vp]
+    lib.vla_avtav.argtypes = [i32, i32, i64, i32, vp, vp, vp, vp]
+    for name in ("vla_amsm", "vla_smamt"):
+        getattr(lib, name).argtypes = [i32, i32, i64, i32, i32, i32, vp, vp, vp, vp]
+    for name in ("vla_amsv", "vla_svamt"):
+        getattr(lib, name).argtypes = [i32, i32, i64, i32, i32, vp, vp, vp, vp]
+    fake = 16   # never dereferenced: every call below fails its checks or has N = 0
+    assert lib.vla_amt(1, 0, 10, 4, 3, fake, fake, None) == -1           # m = 4 unsupported
+    assert lib.vla_amt(1, 2, 10, 3, 3, fake, fake, None) == -1           # unknown layout
+    assert lib.vla_avtav(3, 0, 10, 3, fake, fake, fake, None) == -1      # unknown dtype
+    assert lib.vla_avtav(1, 0, 10, 3, None, fake, fake, None) == -1      # null array
+    assert lib.vla_amsm(1, 0, 10, 3, 17, 2, fake, fake, fake, None) == -1  # p > 16
+    assert lib.vla_amsm(1, 0, 10, 0, 4, 2, fake, fake, fake, None) == -1   # m < 1
+    assert lib.vla_smamt(0, 0, 10, 3, 4, 3, fake, None, fake, None) == -1  # null pages
+    assert lib.vla_amsv(1, 0, -1, 3, 4, fake, fake, fake, None) == -1     # negative page count
+    assert lib.vla_svamt(1, 1, 0, 3, 4, None, None, None, None) == 0      # N = 0: nothing to do
+    assert lib.vla_amt(0, 0, 0, 2, 3, None, None, None) == 0
+
+
 def test_binding_refuses_to_run_without_library(tmp_path, monkeypatch):
     import paper_2404_16039_gb300 as vla
     monkeypatch.setattr(vla, "LIB_PATH", str(tmp_path / "missing.so"))
