@@ -118,25 +118,41 @@ struct GIArgs {
 };
 
 // partial[b][c] over simplices k = b*T + t, stride grid*T of
-// sizes_k * sum_q w_q f(c, q, k)  (or the flux: sum_c ... * n(c, k))
+// sizes_k * sum_q w_q f(c, q, k)  (FLUX: the one sum of sizes_k *
+// sum_c (sum_q w_q f(c, q, k)) n(c, k)); D components, compile-time, so the
+// per-simplex averages stay in registers
+template <int D, bool FLUX>
 __global__ void k_gi_partial(int64_t n, GIArgs ga, const double *__restrict__ fip, const double *__restrict__ sizes,
                              const double *__restrict__ normals, double *__restrict__ partial) {
     __shared__ double sh[32];
-    double acc[kRedMaxComp] = {0.0, 0.0, 0.0, 0.0};
-    const int ncomp = normals ? 1 : ga.d;
+    constexpr int NC = FLUX ? 1 : D;
+    double acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = 0.0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        double avg[kRedMaxComp] = {0.0, 0.0, 0.0, 0.0};
-        for (int c = 0; c < ga.d; ++c)
-            for (int q = 0; q < ga.nip; ++q) avg[c] = fma(ga.w[q], fip[(k * ga.nip + q) * ga.d + c], avg[c]);
-        if (normals) {
+        const double *fk = fip + k * ga.nip * D;
+        double avg[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) avg[c] = 0.0;
+#pragma unroll
+        for (int q = 0; q < kMaxIp; ++q) {
+            if (q >= ga.nip) break;
+#pragma unroll
+            for (int c = 0; c < D; ++c) avg[c] = fma(ga.w[q], fk[q * D + c], avg[c]);
+        }
+        const double sk = sizes[k];
+        if constexpr (FLUX) {
             double dot = 0.0;
-            for (int c = 0; c < ga.d; ++c) dot = fma(avg[c], normals[k * ga.d + c], dot);
-            acc[0] = fma(sizes[k], dot, acc[0]);
+#pragma unroll
+            for (int c = 0; c < D; ++c) dot = fma(avg[c], normals[k * D + c], dot);
+            acc[0] = fma(sk, dot, acc[0]);
         } else {
-            for (int c = 0; c < ga.d; ++c) acc[c] = fma(sizes[k], avg[c], acc[c]);
+#pragma unroll
+            for (int c = 0; c < D; ++c) acc[c] = fma(sk, avg[c], acc[c]);
         }
     }
-    for (int c = 0; c < ncomp; ++c) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
         const double s = block_sum(acc[c], sh);
         if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * kRedMaxComp + c] = s;
     }
@@ -213,35 +229,42 @@ __global__ void k_rhs_gather(int64_t nn, int nlb, const int32_t *__restrict__ n2
 }
 
 // J(0,k) = u_k^T K_k u_k / 2, J(1,k) = u_k^T M_k u_k / 2, J(2,k) = -b2D(:,k)^T u_k,
-// plus block partials of the three sums
-__global__ void k_energies(int64_t ne, int nlb, const int32_t *__restrict__ elems, const double *__restrict__ u,
+// plus block partials of the three sums; NLB nodes per element, compile-time
+template <int NLB>
+__global__ void k_energies(int64_t ne, const int32_t *__restrict__ elems, const double *__restrict__ u,
                            const double *__restrict__ Kp, const double *__restrict__ Mp, const double *__restrict__ b2D,
                            double *__restrict__ J, double *__restrict__ partial) {
     __shared__ double sh[32];
     double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += (int64_t)gridDim.x * blockDim.x) {
-        double uk[10];
-        for (int j = 0; j < nlb; ++j) uk[j] = u[elems[k * nlb + j]];
+        double uk[NLB];
+#pragma unroll
+        for (int j = 0; j < NLB; ++j) uk[j] = u[elems[k * NLB + j]];
         double e[3] = {0.0, 0.0, 0.0};
-        const int64_t pg = k * nlb * nlb;
-        for (int c = 0; c < nlb; ++c) {
-            double kc = 0.0, mc = 0.0;   // (K_k u_k)_c and (M_k u_k)_c over rows r: A(r,c) at r + c nlb
-            for (int r = 0; r < nlb; ++r) {
-                if (Kp) kc = fma(Kp[pg + r + c * nlb], uk[r], kc);
-                if (Mp) mc = fma(Mp[pg + r + c * nlb], uk[r], mc);
+        const int64_t pg = k * NLB * NLB;
+#pragma unroll
+        for (int c = 0; c < NLB; ++c) {
+            double kc = 0.0, mc = 0.0;   // (K_k u_k)_c and (M_k u_k)_c over rows r: A(r,c) at r + c NLB
+#pragma unroll
+            for (int r = 0; r < NLB; ++r) {
+                if (Kp) kc = fma(Kp[pg + r + c * NLB], uk[r], kc);
+                if (Mp) mc = fma(Mp[pg + r + c * NLB], uk[r], mc);
             }
             e[0] = fma(kc, uk[c], e[0]);
             e[1] = fma(mc, uk[c], e[1]);
-            if (b2D) e[2] = fma(b2D[k * nlb + c], uk[c], e[2]);
+            if (b2D) e[2] = fma(b2D[k * NLB + c], uk[c], e[2]);
         }
         e[0] *= 0.5;
         e[1] *= 0.5;
         e[2] = -e[2];
         if (J)
+#pragma unroll
             for (int c = 0; c < 3; ++c) J[k * 3 + c] = e[c];
+#pragma unroll
         for (int c = 0; c < 3; ++c) acc[c] += e[c];
     }
     if (partial)
+#pragma unroll
         for (int c = 0; c < 3; ++c) {
             const double s = block_sum(acc[c], sh);
             if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * kRedMaxComp + c] = s;
@@ -266,6 +289,13 @@ __global__ void k_avtamav(int64_t N, int n, int soa, const T *__restrict__ v, co
         }
         out[k] = s;
     }
+}
+
+template <int D>
+void launch_gi(int nb, cudaStream_t st, int64_t n, const GIArgs &ga, const double *fip, const double *sizes,
+               const double *normals, double *partial) {
+    if (normals) k_gi_partial<D, true><<<nb, kRedThreads, 0, st>>>(n, ga, fip, sizes, normals, partial);
+    else k_gi_partial<D, false><<<nb, kRedThreads, 0, st>>>(n, ga, fip, sizes, normals, partial);
 }
 
 template <typename T>
@@ -329,7 +359,12 @@ extern "C" vla_status vla_gi(int64_t n, int32_t nip, int32_t d, const double *fi
     const int nb = red_blocks(n);
     double *partial = nullptr;
     TRY(scratch_alloc(&partial, (size_t)nb * kRedMaxComp, st));
-    k_gi_partial<<<nb, kRedThreads, 0, st>>>(n, ga, fip, sizes, normals, partial);
+    switch (d) {
+    case 1: launch_gi<1>(nb, st, n, ga, fip, sizes, normals, partial); break;
+    case 2: launch_gi<2>(nb, st, n, ga, fip, sizes, normals, partial); break;
+    case 3: launch_gi<3>(nb, st, n, ga, fip, sizes, normals, partial); break;
+    default: launch_gi<4>(nb, st, n, ga, fip, sizes, normals, partial); break;
+    }
     k_sum_partials<<<1, kRedThreads, 0, st>>>(nb, normals ? 1 : d, partial, out);
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(partial, st);
@@ -368,7 +403,15 @@ extern "C" vla_status vla_energies(const vla_mesh *m, const double *u, const dou
     const int nb = red_blocks(m->ne);
     double *partial = nullptr;
     if (J_total) TRY(scratch_alloc(&partial, (size_t)nb * kRedMaxComp, st));
-    k_energies<<<nb, kRedThreads, 0, st>>>(m->ne, m->nlb, m->elems, u, K_pages, M_pages, b2D, J_local, partial);
+#define VLA_ENERGIES(NLB) \
+    k_energies<NLB><<<nb, kRedThreads, 0, st>>>(m->ne, m->elems, u, K_pages, M_pages, b2D, J_local, partial)
+    switch (m->nlb) {
+    case 3: VLA_ENERGIES(3); break;
+    case 4: VLA_ENERGIES(4); break;
+    case 6: VLA_ENERGIES(6); break;
+    default: VLA_ENERGIES(10); break;
+    }
+#undef VLA_ENERGIES
     if (J_total) k_sum_partials<<<1, kRedThreads, 0, st>>>(nb, 3, partial, J_total);
     cudaError_t e = cudaGetLastError();
     if (partial) cudaFreeAsync(partial, st);
