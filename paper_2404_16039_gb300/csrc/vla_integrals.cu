@@ -76,19 +76,27 @@ struct QuadArgs {
     int nip, nvert, stride, dim;
 };
 
-// X(:, q, k) = sum_j ip(j, q) x_{cells(k, j)}  (the paper's amsm(coords3D, ip))
-__global__ void k_quad_points(int64_t n, QuadArgs qa, const int32_t *__restrict__ cells,
-                              const double *__restrict__ x, double *__restrict__ X) {
+// X(:, q, k) = sum_j ip(j, q) x_{cells(k, j)}  (the paper's amsm(coords3D, ip));
+// one point per thread, DIM coordinates and NV vertices compile-time
+template <int DIM, int NV>
+__global__ void __launch_bounds__(256, 8) k_quad_points(int64_t n, QuadArgs qa, const int32_t *__restrict__ cells,
+                                                        const double *__restrict__ x, double *__restrict__ X) {
     const int64_t total = n * qa.nip;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = t / qa.nip;
         const int q = (int)(t - k * qa.nip);
-        double s[3] = {0.0, 0.0, 0.0};
-        for (int j = 0; j < qa.nvert; ++j) {
+        double s[DIM];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) s[d] = 0.0;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
             const int64_t node = cells[k * qa.stride + j];
-            for (int d = 0; d < qa.dim; ++d) s[d] = fma(qa.ip[q][j], x[node * qa.dim + d], s[d]);
+            const double c = qa.ip[q][j];
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) s[d] = fma(c, x[node * DIM + d], s[d]);
         }
-        for (int d = 0; d < qa.dim; ++d) X[t * qa.dim + d] = s[d];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) X[t * DIM + d] = s[d];
     }
 }
 
@@ -185,32 +193,38 @@ struct RhsArgs {
 };
 
 // simplex measure |det V| / dim! from FP64 coordinates (vectors to the last vertex)
-__device__ __forceinline__ double simplex_measure(int dim, int nlb, const int32_t *__restrict__ elems, int64_t k,
+template <int DIM, int NLB>
+__device__ __forceinline__ double simplex_measure(const int32_t *__restrict__ elems, int64_t k,
                                                   const double *__restrict__ x) {
-    const int64_t last = elems[k * nlb + dim];
-    double V[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    for (int j = 0; j < dim; ++j) {
-        const int64_t vj = elems[k * nlb + j];
-        for (int d = 0; d < dim; ++d) V[j][d] = x[vj * dim + d] - x[last * dim + d];
+    const int64_t last = elems[k * NLB + DIM];
+    double V[DIM][DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+        const int64_t vj = elems[k * NLB + j];
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) V[j][d] = x[vj * DIM + d] - x[last * DIM + d];
     }
     double det;
-    if (dim == 3)
+    if constexpr (DIM == 3)
         det = V[0][0] * (V[1][1] * V[2][2] - V[1][2] * V[2][1]) - V[0][1] * (V[1][0] * V[2][2] - V[1][2] * V[2][0]) +
               V[0][2] * (V[1][0] * V[2][1] - V[1][1] * V[2][0]);
     else
         det = V[0][0] * V[1][1] - V[0][1] * V[1][0];
-    return fabs(det) / (dim == 3 ? 6.0 : 2.0);
+    return fabs(det) / (DIM == 3 ? 6.0 : 2.0);
 }
 
-// b2D(j, k) = |T_k| sum_q w_q f(q, k) phi_j(ip_q)
-__global__ void k_rhs_local(int64_t ne, RhsArgs ra, const int32_t *__restrict__ elems, const double *__restrict__ x,
-                            const double *__restrict__ fip, double *__restrict__ b2D) {
+// b2D(j, k) = |T_k| sum_q w_q f(q, k) phi_j(ip_q); DIM and NLB compile-time
+template <int DIM, int NLB>
+__global__ void __launch_bounds__(256, 8) k_rhs_local(int64_t ne, RhsArgs ra, const int32_t *__restrict__ elems,
+                                                      const double *__restrict__ x, const double *__restrict__ fip,
+                                                      double *__restrict__ b2D) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += (int64_t)gridDim.x * blockDim.x) {
-        const double vol = simplex_measure(ra.dim, ra.nlb, elems, k, x);
-        for (int j = 0; j < ra.nlb; ++j) {
+        const double vol = simplex_measure<DIM, NLB>(elems, k, x);
+#pragma unroll
+        for (int j = 0; j < NLB; ++j) {
             double s = 0.0;
             for (int q = 0; q < ra.nip; ++q) s = fma(ra.w[q] * fip[k * ra.nip + q], ra.phi[q][j], s);
-            b2D[k * ra.nlb + j] = vol * s;
+            b2D[k * NLB + j] = vol * s;
         }
     }
 }
@@ -339,8 +353,16 @@ extern "C" vla_status vla_quad_points(const vla_mesh *m, int32_t gqo, int32_t fa
     qa.dim = m->dim;
     const int64_t n = facets ? m->nfb : m->ne;
     if (n == 0) return VLA_OK;
-    k_quad_points<<<grid_for(n * r.nip, 256), 256, 0, (cudaStream_t)stream>>>(n, qa, facets ? m->faces : m->elems,
-                                                                             m->coords, X);
+    const int grid = grid_for(n * r.nip, 256);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t *cells = facets ? m->faces : m->elems;
+    if (m->dim == 2) {
+        if (qa.nvert == 2) k_quad_points<2, 2><<<grid, 256, 0, st>>>(n, qa, cells, m->coords, X);
+        else k_quad_points<2, 3><<<grid, 256, 0, st>>>(n, qa, cells, m->coords, X);
+    } else {
+        if (qa.nvert == 3) k_quad_points<3, 3><<<grid, 256, 0, st>>>(n, qa, cells, m->coords, X);
+        else k_quad_points<3, 4><<<grid, 256, 0, st>>>(n, qa, cells, m->coords, X);
+    }
     VLA_CUDA(cudaGetLastError());
     return VLA_OK;
 }
@@ -388,7 +410,13 @@ extern "C" vla_status vla_rhs(const vla_mesh *m, int32_t gqo, const double *fip,
     }
     double *loc = b2D;
     if (!loc) TRY(scratch_alloc(&loc, (size_t)m->ne * m->nlb, st));
-    k_rhs_local<<<grid_for(m->ne, 256), 256, 0, st>>>(m->ne, ra, m->elems, m->coords, fip, loc);
+    const int grid = grid_for(m->ne, 256);
+    switch (m->nlb) {
+    case 3: k_rhs_local<2, 3><<<grid, 256, 0, st>>>(m->ne, ra, m->elems, m->coords, fip, loc); break;
+    case 4: k_rhs_local<3, 4><<<grid, 256, 0, st>>>(m->ne, ra, m->elems, m->coords, fip, loc); break;
+    case 6: k_rhs_local<2, 6><<<grid, 256, 0, st>>>(m->ne, ra, m->elems, m->coords, fip, loc); break;
+    default: k_rhs_local<3, 10><<<grid, 256, 0, st>>>(m->ne, ra, m->elems, m->coords, fip, loc); break;
+    }
     if (b) k_rhs_gather<<<grid_for(m->nn, 256), 256, 0, st>>>(m->nn, m->nlb, m->n2e_ptr, m->n2e, loc, b);
     cudaError_t e = cudaGetLastError();
     if (!b2D) cudaFreeAsync(loc, st);
