@@ -135,3 +135,22 @@ def test_full_size_closed_forms(vla):
     ipb, wb = vla.quad_rule(2, 2)
     Y = gm.quad_points(2, facets=True)
     assert vla.gi((Y ** 2).contiguous(), wb, ar, normals=nrm).item() == pytest.approx(3.0, abs=1e-12)
+
+
+@pytest.mark.parametrize("flux", [False, True])
+@pytest.mark.parametrize("d", [1, 2, 3, 4])
+def test_gi_every_component_count(vla, d, flux):
+    # every compiled component count, volume integrals and fluxes, on random
+    # signed data over more simplices than one pass of the reduction grid
+    # (1024 blocks of 256) covers; bound: 1e-12 of the sum of absolute terms
+    rng = np.random.default_rng(100 * d + flux)
+    n, nip = 1024 * 256 + 12345, 5
+    fip = rng.standard_normal((n, nip, d))
+    w = rng.standard_normal(nip)
+    sizes = rng.random(n)
+    normals = rng.standard_normal((n, d)) if flux else None
+    ref = oracle.gi(fip, w, sizes, normals)
+    scale = oracle.gi(np.abs(fip), np.abs(w), sizes, None if normals is None else np.abs(normals))
+    got = vla.gi(_dev(fip), w, _dev(sizes), None if normals is None else _dev(normals)).cpu().numpy()
+    assert got.shape == ((1,) if flux else (d,))
+    assert np.all(np.abs(got - ref) <= 1e-12 * scale)
