@@ -76,7 +76,7 @@ int32_t vla_version(void);
 size_t vla_last_error(char *buf, size_t len);
 
 /* ------------------------------------------------------------------------ */
-/* Page primitives (Section 2.4, "A vectorization library")                  */
+/* Page primitives (the vectorization library of Section 2.4)               */
 /* dtype: VLA_F32 or VLA_F64 (all arrays of the call share it).  Shapes      */
 /* p, m, n in {2, 3}.  N >= 0; N == 0 is a no-op.  Arrays must not overlap.  */
 /* ------------------------------------------------------------------------ */

@@ -34,8 +34,8 @@
 /* small dense helpers (column-major)                                        */
 /* ------------------------------------------------------------------------ */
 
-/* determinant by cofactor expansion along the first row (Section 2.3,
- * "Page-wise determinants"); n in {1,2,3}. */
+/* determinant by cofactor expansion along the first row (page-wise
+ * determinants, Section 2.3); n in {1,2,3}. */
 static double det_small(int n, const double *a /* n x n col-major */) {
 #define A(r, c) a[(r) + (c) * n]
     if (n == 1) return A(0, 0);
@@ -48,7 +48,7 @@ static double det_small(int n, const double *a /* n x n col-major */) {
 #undef A
 }
 
-/* inverse = adjugate / det (Section 2.3, "Inverses and page-wise inverses").
+/* inverse = adjugate / det (page-wise inverses, Section 2.3).
  * Returns det.  A singular matrix yields IEEE inf/nan entries. */
 static double inv_small(int n, const double *a, double *inv) {
 #define A(r, c) a[(r) + (c) * n]
@@ -83,7 +83,7 @@ static double inv_small(int n, const double *a, double *inv) {
 /* ------------------------------------------------------------------------ */
 
 /* C_k = A_k^T B_k with A_k p x m, B_k p x n, C_k m x n.  Reading of the
- * amtam operand order: the page-wise product "transpose(first) * second", as
+ * amtam operand order: the transposed first operand times the second, as
  * the pagemtimes override in Section 2.4 and the call amtam(dphi,dphi) of the
  * P1 stiffness listing (Section 3.5) require. */
 void orc_amtam(int64_t N, int p, int m, int n, const double *A, const double *B, double *C) {
@@ -279,8 +279,8 @@ static double bary_gradients(int dim, const double *V, double *glam) {
 }
 
 /* Coefficient evaluated once per element at the vertex centroid x_c
- * (reading of "a coefficient at one quadrature point", Section 3.5 remark on
- * gqo = 1):
+ * (reading of the Section 3.5 remark on gqo = 1: the coefficient taken at a
+ * single quadrature point):
  *   kind 0:  c = a + b |x_c|^2
  *   kind 1:  c = a * exp(b * sum_d x_c[d])   (the benchmark coefficient
  *            e^{x1+x2(+x3)} of Section 3.5.1 with a = b = 1). */
