@@ -150,7 +150,7 @@ def test_load_vector_closed_forms(dim, order):
     np.testing.assert_allclose(b, M0 @ fx(m.coords), rtol=0, atol=1e-13)
 
 
-@pytest.mark.parametrize("dim,order", [(2, 1), (3, 1), (3, 2)])
+@pytest.mark.parametrize("dim,order", [(2, 1), (3, 1), (2, 2), (3, 2)])
 def test_energies_closed_forms_and_sums(dim, order):
     # u = x1 (reproduced exactly), c = 1: J1 = |Omega|/2 = 1/2, J2 = int x1^2 / 2 = 1/6;
     # f = 1: J3 = -int u = -1/2.  Local energies sum to the global quadratic forms.
