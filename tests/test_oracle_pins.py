@@ -167,25 +167,33 @@ def test_boundary_orientation_independent_of_listing():
     np.testing.assert_allclose(ar2, ar, rtol=1e-15)
 
 
-def test_boundary_matches_paper_normal_transform():
+@pytest.mark.parametrize("dim", [2, 3])
+def test_boundary_matches_paper_normal_transform(dim):
     # the boundary normal equals the normalised facet normal V^{-T} normalsRef of the
-    # owning tet (Section 3.2 route), and |det V| |n_j| / 2 is the facet area
-    m = meshgen.kuhn_cube(2, jitter=0.1, seed=2)
-    # make the boundary geometry non-trivial: move the whole mesh by an affine map
-    Aff = np.array([[1.0, 0.2, -0.1], [0.1, 0.9, 0.3], [-0.2, 0.1, 1.1]])
-    coords = m.coords @ Aff.T + np.array([0.3, -0.2, 0.5])
-    nrm, ar, _ = oracle.boundary(3, m.nn, m.elems, coords, m.faces)
-    tn = oracle.simplex_normals(3, m.elems, coords)
-    _, det = oracle.volumes(3, m.elems, coords)
+    # owning simplex (Section 3.2 route), is orthogonal to the facet's edges, and
+    # |det V| |n_j| / (dim-1)! is the facet measure; the mesh is moved by an affine
+    # map so that no boundary facet is axis-aligned
+    if dim == 3:
+        m = meshgen.kuhn_cube(2, jitter=0.1, seed=2)
+        Aff, shift = np.array([[1.0, 0.2, -0.1], [0.1, 0.9, 0.3], [-0.2, 0.1, 1.1]]), np.array([0.3, -0.2, 0.5])
+    else:
+        m = meshgen.make_mesh(2, 4, jitter=0.1, seed=2)
+        Aff, shift = np.array([[1.0, 0.3], [-0.2, 0.8]]), np.array([0.3, -0.2])
+    coords = m.coords @ Aff.T + shift
+    nrm, ar, _ = oracle.boundary(dim, m.nn, m.elems, coords, m.faces)
+    tn = oracle.simplex_normals(dim, m.elems, coords)
+    _, det = oracle.volumes(dim, m.elems, coords)
     for f in range(m.nfb):
         fs = set(m.faces[f].tolist())
         owners = [k for k in range(m.ne) if fs <= set(m.elems[k].tolist())]
         assert len(owners) == 1
         k = owners[0]
-        j = [q for q in range(4) if m.elems[k, q] not in fs][0]
+        j = [q for q in range(dim + 1) if m.elems[k, q] not in fs][0]
         nj = tn[k, j]
         np.testing.assert_allclose(nj / np.linalg.norm(nj), nrm[f], atol=1e-13)
-        assert abs(det[k]) * np.linalg.norm(nj) / 2 == pytest.approx(ar[f], rel=1e-13)
+        assert abs(det[k]) * np.linalg.norm(nj) / math.factorial(dim - 1) == pytest.approx(ar[f], rel=1e-13)
+        X = coords[m.faces[f]]
+        assert np.all(np.abs((X[1:] - X[0]) @ nrm[f]) < 1e-13)
 
 
 # ---------------------------------------------------------------------------
