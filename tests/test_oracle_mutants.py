@@ -111,6 +111,30 @@ MUTANTS = [
     ("energy_load_sign", "J[k * 3 + 2] = -f;", "J[k * 3 + 2] = f;"),
     ("energy_mass_operand", "m += uk[i] * M3D[k * nlb * nlb + i + j * nlb] * uk[j];",
      "m += uk[i] * K3D[k * nlb * nlb + i + j * nlb] * uk[j];"),
+    # second batch: operands, dropped factors and indices elsewhere in the same functions
+    ("amsm_output_transposed", "C[k * m * n + i + j * m] = s;\n            }\n}\n\n/* y_k = A_k s",
+     "C[k * m * n + j + i * n] = s;\n            }\n}\n\n/* y_k = A_k s"),
+    ("aminv_singular_count", "if (d == 0.0) ++nsing;", "if (d != 0.0) ++nsing;"),
+    ("vectors_from_first_vertex", "const double *xl = coords + (int64_t)e[dim] * dim;",
+     "const double *xl = coords + (int64_t)e[0] * dim;"),
+    ("poly_coefficient_uses_sum", "return ca + cb * r2;\n}", "return ca + cb * sum;\n}"),
+    ("exp_coefficient_dropped_factor", "if (kind == 1) return ca * exp(cb * sum);", "if (kind == 1) return exp(cb * sum);"),
+    ("centroid_vertex_index", "xc[d] += coords[(int64_t)elems[k * nlb + j] * dim + d];",
+     "xc[d] += coords[(int64_t)elems[k * nlb] * dim + d];"),
+    ("p2_stiffness_dropped_coefficient", "sk += G[p].coef[u] * G[q].coef[v] * gg[",
+     "sk += G[p].coef[u] * gg["),
+    ("p2_stiffness_exponent_operand", "al[j] = G[p].alpha[u][j] + G[q].alpha[v][j];",
+     "al[j] = G[p].alpha[u][j] + G[p].alpha[u][j];"),
+    ("literal_stiffness_dropped_coefficient", "Kp[p + q * nlb] = cK * vol * s;", "Kp[p + q * nlb] = vol * s;"),
+    ("assemble_mass_from_stiffness_pages", "rc = orc_csr_scatter(ne, nlb, elems, M3D, row_ptr, col_idx, Mv);",
+     "rc = orc_csr_scatter(ne, nlb, elems, K3D, row_ptr, col_idx, Mv);"),
+    ("csr_column_from_row_bits", "col_idx[nnz] = (int32_t)(keys[q] & 0xffffffffu);", "col_idx[nnz] = (int32_t)(keys[q] >> 32);"),
+    ("boundary_owner_test", "if (hits != dim) continue;", "if (hits < dim - 1) continue;"),
+    ("rule_degree1_weight", "w[0] = 1.0;\n        return 1;", "w[0] = 0.5;\n        return 1;"),
+    ("gi_flux_dropped_size", "out[0] += sizes[k] * dot;", "out[0] += dot;"),
+    ("rhs_value_index", "s += w[q] * fip[k * nip + q] * basis_at", "s += w[q] * fip[k * nip] * basis_at"),
+    ("energy_load_node_index", "f += b2D[k * nlb + j] * uk[j];", "f += b2D[k * nlb + j] * uk[0];"),
+    ("facet_list_owner_facet", "owner[nf * 2 + 1] = j;", "owner[nf * 2 + 1] = 0;"),
 ]
 
 

@@ -207,6 +207,22 @@ def _assembled_dense(m, ca=1.0, cb=0.0, ckind=0):
     return K, M, out
 
 
+@pytest.mark.parametrize("dim,order", [(2, 1), (3, 1), (2, 2), (3, 2)])
+def test_coefficient_kinds_closed_forms(dim, order):
+    # the element coefficient is taken once at the vertex centroid x_c: kind 0
+    # c = a + b |x_c|^2, kind 1 c = a exp(b sum_d x_c[d]) (Section 3.5.1's
+    # e^{x1+x2+x3} with a = b = 1); each element page is c times the c = 1 page,
+    # with x_c computed here from the vertex coordinates
+    m = meshgen.make_mesh(dim, 3, order=order, jitter=0.1, seed=21)
+    xc = m.coords[m.elems[:, :dim + 1]].mean(axis=1)
+    one = oracle.assemble(dim, order, m.nn, m.elems, m.coords, 1.0, 0.0, want_pages=True)
+    a, b = 2.5, -0.7
+    for kind, c in ((0, a + b * np.sum(xc ** 2, axis=1)), (1, a * np.exp(b * xc.sum(axis=1)))):
+        out = oracle.assemble(dim, order, m.nn, m.elems, m.coords, a, b, want_pages=True, ckind=kind)
+        np.testing.assert_allclose(out["K3D"], c[:, None, None] * one["K3D"], rtol=1e-13, atol=1e-13)
+        np.testing.assert_allclose(out["M3D"], c[:, None, None] * one["M3D"], rtol=1e-13, atol=1e-16)
+
+
 @pytest.mark.parametrize("dim,order,n", [(2, 1, 6), (3, 1, 3), (2, 2, 4), (3, 2, 2)])
 @pytest.mark.parametrize("cb", [0.0, 1.0])
 def test_K_M_invariants(dim, order, n, cb):
