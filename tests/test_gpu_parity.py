@@ -206,7 +206,7 @@ def test_pattern_bit_exact(vla, dim, order, n):
 
 
 @pytest.mark.parametrize("dim,order,n", CASES)
-@pytest.mark.parametrize("kind,ca,cb", [(0, 1.0, 0.0), (0, 1.0, 1.0), (1, 1.0, 1.0)])
+@pytest.mark.parametrize("kind,ca,cb", [(0, 1.0, 0.0), (0, 1.0, 1.0), (1, 1.0, 1.0), (1, 2.5, -0.7)])
 def test_assembly_fp64(vla, dim, order, n, kind, ca, cb):
     m = meshgen.make_mesh(dim, n, order=order, jitter=0.1, seed=3 * n + order)
     gm = _gpu_mesh(vla, m)
