@@ -200,7 +200,10 @@ def run_reference(args):
     line = {"metric": "elements/sec for P1 tet K+M to CSR", "value": val, "unit": "elements/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": _config(m, "fp64 oracle"),
+            "config": dict(_config(m, "fp64 oracle"),
+                           l2=f"host run, no flush: each step reads and writes over "
+                              f"{int(_alg_bytes_per_el(m.ne, m.nn, len(pat[1])) * m.ne / 1e6)} MB of mesh "
+                              f"arrays and CSR values, more than the host caches hold"),
             "cpu_baseline": {"value": val, "unit": "elements/s", "cores": 1, "kind": "oracle",
                              "sample": f"each step one full oracle pass over the {m.ne}-tet mesh, 1 host thread"},
             "e2e": {"value": val, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
