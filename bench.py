@@ -22,7 +22,8 @@ resident mesh.
 Other workloads (--workload): pages (page primitives at N = 1e8), batch (256
 meshes of all four element types in one persistent launch), serve (a Poisson
 request stream through the server), next (the rows beyond the assembly core,
-one timed call each on the bench mesh).
+one timed call each on the bench mesh), small (p50/p99 latency of the FP64
+call with element pages on the 3,072-tet mesh).
 
 Multi-GPU (torchrun): every rank assembles its own copy of the workload on its
 own GPU (independent problems, no collective on the data path); the reported
@@ -615,6 +616,76 @@ def run_serve(args):
     return 0
 
 
+def run_small(args):
+    """The small FP64 case with element pages: Kuhn 8^3 x 6 (3,072 tets, 729
+    nodes), c = 1, K, M, volumes and both page arrays in FP64 from one call,
+    a latency-bound call.  Reports p50/p99 over --small-reps calls of the
+    device time between CUDA events around the call with the L2 flushed
+    before each (cold), the same back to back (warm), and the host wall time
+    of the call plus a synchronize."""
+    import torch
+    import meshgen
+    import paper_2404_16039_gb300 as vla
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    m = meshgen.kuhn_cube(8, jitter=0.1, seed=0)
+    gm = vla.Mesh(torch.from_numpy(m.coords).to(dev), torch.from_numpy(m.elems).to(dev),
+                  torch.from_numpy(m.faces).to(dev))
+    K = torch.empty(gm.nnz, dtype=torch.float64, device=dev)
+    M = torch.empty_like(K)
+    vol = torch.empty(gm.ne, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def call():
+        gm.assemble(1.0, 0.0, precision=vla.PREC_FP64, K=K, M=M, vol=vol, pages=True)
+
+    warmup = max(args.warmup, 3)
+    for _ in range(warmup):
+        call()
+    torch.cuda.synchronize()
+
+    def device_ms(flushed):
+        ts = []
+        for _ in range(args.small_reps):
+            if flushed:
+                flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            call()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+
+    sampler = ClockSampler(0)
+    sampler.start()
+    cold = device_ms(True)
+    warm = device_ms(False)
+    host = []
+    for _ in range(args.small_reps):
+        t0 = time.perf_counter()
+        call()
+        torch.cuda.synchronize()
+        host.append((time.perf_counter() - t0) * 1e3)
+    clocks = sampler.stop()
+
+    def pct(x):
+        return {"p50_ms": float(np.percentile(x, 50)), "p99_ms": float(np.percentile(x, 99))}
+
+    line = {"metric": "latency of one FP64 P1 tet K+M call with element pages", "value": pct(cold)["p50_ms"],
+            "unit": "ms", "higher_is_better": False, "n_gpus": 1, "steps": args.small_reps, "warmup": warmup,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"P1 tet K+M -> CSR with K3D/M3D pages, FP64, unit cube 8^3 cubes x 6 Kuhn "
+                                   f"tets ({gm.ne} tets, {gm.nn} nodes, {gm.nnz} nonzeros), interior jitter "
+                                   f"U(-0.1h,0.1h) seed 0, c = 1",
+                       "l2": "cold: flushed before every call (512 MiB write); warm: back to back"},
+            "cold_l2": pct(cold), "warm_l2": pct(warm), "host_call_and_sync": pct(host), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_next(args):
     """The rows beyond the assembly core, each timed on the bench mesh (CUDA
     events around one call, L2 flushed before each, median of 20 after 3
@@ -762,7 +833,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="p1tet", choices=["p1tet", "pages", "batch", "serve", "next"])
+    ap.add_argument("--workload", default="p1tet", choices=["p1tet", "pages", "batch", "serve", "next", "small"])
+    ap.add_argument("--small-reps", type=int, default=1000)
     ap.add_argument("--pages-n", default="100000000")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-lo", type=float, default=1e3)
@@ -788,6 +860,8 @@ def main():
         return run_serve(args)
     if args.workload == "next":
         return run_next(args)
+    if args.workload == "small":
+        return run_small(args)
 
     import torch
     import meshgen
