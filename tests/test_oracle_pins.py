@@ -84,6 +84,25 @@ def test_facet_counts(golden_dir, level):
     assert m.nfb == row["boundary_faces"]
 
 
+def _p1_nnz_closed_form(dim, n):
+    # a P1 pattern holds the diagonal and both directions of every mesh edge.
+    # Unit square, n x n squares each cut by one diagonal: 2n(n+1) axis edges
+    # and n^2 diagonals.  Unit cube, n^3 cubes x 6 Kuhn tets: 3n(n+1)^2 axis
+    # edges, 3n^2(n+1) face diagonals and n^3 body diagonals.
+    if dim == 2:
+        return (n + 1) ** 2 + 2 * (2 * n * (n + 1) + n * n)
+    return (n + 1) ** 3 + 2 * (3 * n * (n + 1) ** 2 + 3 * n * n * (n + 1) + n ** 3)
+
+
+@pytest.mark.parametrize("dim,n", [(2, 1), (2, 4), (2, 9), (3, 1), (3, 2), (3, 5), (3, 8)])
+def test_p1_pattern_size_closed_form(dim, n):
+    m = meshgen.make_mesh(dim, n, jitter=0.1, seed=n)
+    rp, ci = oracle.csr_pattern(m.nn, m.elems)
+    assert len(ci) == rp[-1] == _p1_nnz_closed_form(dim, n)
+    # the sizes of the 8^3 and 64^3 benchmark meshes
+    assert _p1_nnz_closed_form(3, 8) == 9097 and _p1_nnz_closed_form(3, 64) == 4018753
+
+
 # ---------------------------------------------------------------------------
 # page primitives (Section 2.4) against closed forms and numpy.linalg
 # ---------------------------------------------------------------------------
