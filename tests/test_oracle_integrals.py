@@ -219,6 +219,31 @@ def test_literal_quadratic_coefficient_stiffness_exact(dim):
     np.testing.assert_allclose(lit["K3D"], (intc / vol)[:, None, None] * one["K3D"], rtol=1e-12, atol=1e-14)
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("kind", [2, 3])
+def test_literal_pages_follow_the_degree2_rule(dim, kind):
+    # the literal P1 listing evaluates c at the points of the degree-2 rule (gqo = 2):
+    # K_k = (sum_i w_i c(x_i)) |T| G^T G and M_k(p,q) = |T| sum_i w_i c(x_i) lam_p lam_q,
+    # rebuilt here element by element with numpy (gradients from numpy.linalg.inv);
+    # the rule itself is pinned to its degree of exactness above
+    m = meshgen.make_mesh(dim, 2, jitter=0.1, seed=4)
+    a, b = 1.2, 0.8
+    lit = _literal(dim, m, a, b, kind)
+    ip, w = oracle.quad_rule(dim, 2)                 # (nip, dim+1) barycentric, weights sum to 1
+    for k in range(m.ne):
+        X = m.coords[m.elems[k, : dim + 1]]          # (dim+1, dim)
+        V = (X[:dim] - X[dim]).T                     # columns: vectors to the last vertex
+        vol = abs(np.linalg.det(V)) / math.factorial(dim)
+        Vi = np.linalg.inv(V)
+        G = np.vstack([Vi, -Vi.sum(axis=0)])         # (dim+1, dim): row j = grad lambda_j
+        xq = ip @ X                                  # (nip, dim) points
+        c = a + b * np.sum(xq ** 2, axis=1) if kind == 2 else a * np.exp(b * xq.sum(axis=1))
+        K = (w @ c) * vol * G @ G.T
+        M = vol * np.einsum("i,ip,iq->pq", w * c, ip, ip)
+        np.testing.assert_allclose(lit["K3D"][k], K, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(lit["M3D"][k], M, rtol=1e-12, atol=1e-16)
+
+
 def test_literal_convergence_matches_printed_table_order():
     # c = e^{x1+x2+x3}, v = cos(pi x1) cos(pi x2) cos(pi x3) on unjittered unit cubes;
     # printed P1 3-D errors at levels 3-5: e_K 2.70e-1, 6.82e-2, 1.71e-2; e_M 5.04e-2,

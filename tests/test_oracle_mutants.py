@@ -135,6 +135,25 @@ MUTANTS = [
     ("rhs_value_index", "s += w[q] * fip[k * nip + q] * basis_at", "s += w[q] * fip[k * nip] * basis_at"),
     ("energy_load_node_index", "f += b2D[k * nlb + j] * uk[j];", "f += b2D[k * nlb + j] * uk[0];"),
     ("facet_list_owner_facet", "owner[nf * 2 + 1] = j;", "owner[nf * 2 + 1] = 0;"),
+    # third batch: more indices, factors and the literal variant's rule
+    ("boundary_2d_length_sqrt", "meas = sqrt(n[0] * n[0] + n[1] * n[1]);", "meas = n[0] * n[0] + n[1] * n[1];"),
+    ("boundary_2d_tangent_index", "n[0] = x2[1] - x1[1];", "n[0] = x2[0] - x1[0];"),
+    ("energy_stiffness_right_node", "a += uk[i] * K3D[k * nlb * nlb + i + j * nlb] * uk[j];", "a += uk[i] * K3D[k * nlb * nlb + i + j * nlb] * uk[i];"),
+    ("inv2_diagonal", "I(1, 1) = A(0, 0) / d;", "I(1, 1) = A(1, 1) / d;"),
+    ("p2_vertex_basis_leading", "out->coef[0] = 2.0;", "out->coef[0] = 1.0;"),
+    ("p2_derivative_exponent_kept", "g->alpha[i][j] -= 1;", "g->alpha[i][j] -= 0;"),
+    ("monomial_integral_dropped_alpha_factorial", "num *= factorial(alpha[j]);", "num *= 1.0;"),
+    ("centroid_radius_unsquared", "r2 += xc[d] * xc[d];", "r2 += xc[d];"),
+    ("literal_rule_degree", "const int nip = orc_quad_rule(dim, 2, ip, w);", "const int nip = orc_quad_rule(dim, 3, ip, w);"),
+    ("literal_point_coefficient_kind", "cq[i] = point_coeff(dim, ckind - 2, ca, cb, x);", "cq[i] = point_coeff(dim, 0, ca, cb, x);"),
+    ("point_coeff_radius", "r2 += x[d] * x[d];\n        sum += x[d];\n    }\n    return kind == 1", "r2 += x[d];\n        sum += x[d];\n    }\n    return kind == 1"),
+    ("quad_points_weight_index", "s += ip[q * nvert + j] * coords", "s += ip[j] * coords"),
+    ("rhs_basis_order", "if (order == 1) return lam[j];", "if (order == 1) return lam[0];"),
+    ("gi_component_index", "avg[c] += w[q] * fip[(k * nip + q) * d + c];", "avg[c] += w[q] * fip[(k * nip + q) * d];"),
+    ("facet_count_drop_index", "if (j != drop) v[q++] = elems[k * nlb + j];", "if (j != drop) v[q++] = elems[k * nlb + drop];"),
+    ("normals_last_reference_column", "(c == dim) ? 1.0 :", "(c == dim) ? -1.0 :"),
+    ("volume_signed", "det_signed[k] = d;\n        vol[k] = fabs(d) / factorial(dim);", "det_signed[k] = d;\n        vol[k] = d / factorial(dim);"),
+    ("p1_mass_dropped_coefficient", "Mp[p + q * nlb] = c * vol * (p == q", "Mp[p + q * nlb] = vol * (p == q"),
 ]
 
 
