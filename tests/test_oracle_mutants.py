@@ -154,6 +154,26 @@ MUTANTS = [
     ("normals_last_reference_column", "(c == dim) ? 1.0 :", "(c == dim) ? -1.0 :"),
     ("volume_signed", "det_signed[k] = d;\n        vol[k] = fabs(d) / factorial(dim);", "det_signed[k] = d;\n        vol[k] = d / factorial(dim);"),
     ("p1_mass_dropped_coefficient", "Mp[p + q * nlb] = c * vol * (p == q", "Mp[p + q * nlb] = vol * (p == q"),
+    # fourth batch: cofactor indices, outputs, P2 coefficients, search and facet outputs
+    ("det3_minor_index", "double c1 = A(1, 0) * A(2, 2) - A(1, 2) * A(2, 0);", "double c1 = A(1, 0) * A(2, 2) - A(1, 2) * A(2, 1);"),
+    ("det3_minor_sign", "double c2 = A(1, 0) * A(2, 1) - A(1, 1) * A(2, 0);", "double c2 = A(1, 1) * A(2, 0) - A(1, 0) * A(2, 1);"),
+    ("inv3_row_cycle_swapped", "int r0 = (r + 1) % 3, r1 = (r + 2) % 3;", "int r0 = (r + 2) % 3, r1 = (r + 1) % 3;"),
+    ("inv3_column_cycle", "int c0 = (c + 1) % 3, c1 = (c + 2) % 3;", "int c0 = (c + 1) % 3, c1 = (c + 1) % 3;"),
+    ("smamt_output_transposed", "C[k * m * n + i + j * m] = s;\n            }\n}\n\n/* y_k = s^T", "C[k * m * n + j + i * n] = s;\n            }\n}\n\n/* y_k = s^T"),
+    ("element_pages_volume_factorial", "if (vol) vol[k] = fabs(d) / factorial(dim);", "if (vol) vol[k] = fabs(d);"),
+    ("p2_gradient_gram_operand", "s += glam[r + i * dim] * glam[r + j * dim];\n            gg", "s += glam[r + i * dim] * glam[r + i * dim];\n            gg"),
+    ("rule_segment_weights", "w[0] = w[1] = 0.5;", "w[0] = w[1] = 1.0;"),
+    ("rule_triangle_degree3_points", "else big = 0.6, small = 0.2,", "else big = 0.6, small = 0.25,"),
+    ("csr_search_direction", "if (col_idx[mid] < c) lo = mid + 1;", "if (col_idx[mid] > c) lo = mid + 1;"),
+    ("facet_list_neighbor_output", "if (neighbor) neighbor[nf] = (int32_t)p;", "if (neighbor) neighbor[nf] = (int32_t)k;"),
+    ("rhs_p2_basis_index", "    p2_basis(dim, j, &p);\n    double v = 0.0;", "    p2_basis(dim, 0, &p);\n    double v = 0.0;"),
+    ("energy_mass_uses_stiffness_sum", "J[k * 3 + 1] = 0.5 * m;", "J[k * 3 + 1] = 0.5 * a;"),
+    ("literal_mass_coefficient_twice", "Mp[p + q * nlb] = vol * m;", "Mp[p + q * nlb] = cK * vol * m;"),
+    ("p2_stiffness_dropped_coefficient_c", "Kp[p + q * nlb] = c * sk;", "Kp[p + q * nlb] = sk;"),
+    ("p2_mass_dropped_coefficient_c", "Mp[p + q * nlb] = c * sm;", "Mp[p + q * nlb] = sm;"),
+    ("avtamav_right_vector_index", "* w[k * n + j];\n        out[k] = s;", "* w[k * n + i];\n        out[k] = s;"),
+    ("boundary_opposite_vertex", "if (!in) opp = v;", "if (in) opp = v;"),
+    ("simplex_normals_inverse_operand", "        inv_small(dim, V, Vi);\n        double *out", "        inv_small(dim, V, Vi);\n        for (int q = 0; q < dim * dim; ++q) Vi[q] = V[q];\n        double *out"),
 ]
 
 
