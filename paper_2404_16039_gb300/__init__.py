@@ -207,6 +207,43 @@ def _req(t, dtype=None):
     return t
 
 
+def _buf(t, numel, dtype, device, name):
+    """A caller-supplied tensor of which the library reads or writes exactly
+    ``numel`` entries: checked here, since the C entry points see only a
+    pointer."""
+    _req(t, dtype)
+    if t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {t.numel()}")
+    if t.device != device:
+        raise ValueError(f"{name}: expected a tensor on {device}, got {t.device}")
+    return t
+
+
+def _same_device(first, *rest):
+    for t in rest:
+        if t is not None and t.device != first.device:
+            raise ValueError(f"all tensors must be on {first.device}, got {t.device}")
+
+
+def _nlb(dim, order):
+    return dim + 1 if order == 1 else (dim + 1) * (dim + 2) // 2
+
+
+def _mesh_arrays(coords, elems, faces, order):
+    """Shapes of mesh arrays against the element order: the library reads
+    ne x nlb element indices and nfb x dim facet indices."""
+    if coords.dim() != 2 or coords.shape[1] not in (2, 3):
+        raise ValueError("coords must be (nn, dim) with dim 2 or 3")
+    dim = coords.shape[1]
+    if order not in (1, 2):
+        raise ValueError("order must be 1 or 2")
+    if elems.dim() != 2 or elems.shape[1] != _nlb(dim, order):
+        raise ValueError(f"elems must be (ne, {_nlb(dim, order)}) for dim {dim}, order {order}")
+    if faces is not None and (faces.dim() != 2 or faces.shape[1] != dim):
+        raise ValueError(f"faces must be (nfb, {dim})")
+    return dim
+
+
 def _page_dims(A, layout):
     # returns (N, rows, cols)
     if layout == LAYOUT_PAGE:
@@ -233,11 +270,12 @@ def _new_vec(N, n, layout, like):
 def amtam(A, B, out=None, layout=LAYOUT_PAGE, stream=None):
     """C_k = A_k^T B_k (amtam).  A: p x m pages, B: p x n pages -> m x n pages."""
     _req(A), _req(B)
+    _same_device(A, B)
     N, p, m = _page_dims(A, layout)
     N2, p2, n = _page_dims(B, layout)
     if N2 != N or p2 != p or A.dtype != B.dtype:
         raise ValueError("amtam: page counts, row counts and dtypes must match")
-    out = _new_pages(N, m, n, layout, A) if out is None else _req(out, A.dtype)
+    out = _new_pages(N, m, n, layout, A) if out is None else _buf(out, N * m * n, A.dtype, A.device, "out")
     _check(lib().vla_amtam(_dtype_code(A), layout, N, p, m, n, _p(A), _p(B), _p(out), _stream(stream)))
     return out
 
@@ -245,10 +283,11 @@ def amtam(A, B, out=None, layout=LAYOUT_PAGE, stream=None):
 def astam(s, A, out=None, layout=LAYOUT_PAGE, stream=None):
     """C_k = s_k A_k (astam)."""
     _req(s, A.dtype), _req(A)
+    _same_device(A, s)
     N, m, n = _page_dims(A, layout)
     if s.numel() != N:
         raise ValueError("astam: one scalar per page")
-    out = _new_pages(N, m, n, layout, A) if out is None else _req(out, A.dtype)
+    out = _new_pages(N, m, n, layout, A) if out is None else _buf(out, N * m * n, A.dtype, A.device, "out")
     _check(lib().vla_astam(_dtype_code(A), layout, N, m, n, _p(s), _p(A), _p(out), _stream(stream)))
     return out
 
@@ -256,10 +295,11 @@ def astam(s, A, out=None, layout=LAYOUT_PAGE, stream=None):
 def avtam(v, A, out=None, layout=LAYOUT_PAGE, stream=None):
     """y_k = v_k^T A_k (avtam).  v: (N, p) page layout or (p, N) SoA."""
     _req(v, A.dtype), _req(A)
+    _same_device(A, v)
     N, p, n = _page_dims(A, layout)
     if v.numel() != N * p:
         raise ValueError("avtam: v must hold p values per page")
-    out = _new_vec(N, n, layout, A) if out is None else _req(out, A.dtype)
+    out = _new_vec(N, n, layout, A) if out is None else _buf(out, N * n, A.dtype, A.device, "out")
     _check(lib().vla_avtam(_dtype_code(A), layout, N, p, n, _p(v), _p(A), _p(out), _stream(stream)))
     return out
 
@@ -270,7 +310,7 @@ def amdet(A, out=None, layout=LAYOUT_PAGE, stream=None):
     N, n, n2 = _page_dims(A, layout)
     if n != n2:
         raise ValueError("amdet: square pages required")
-    out = torch.empty(N, dtype=A.dtype, device=A.device) if out is None else _req(out, A.dtype)
+    out = torch.empty(N, dtype=A.dtype, device=A.device) if out is None else _buf(out, N, A.dtype, A.device, "out")
     _check(lib().vla_amdet(_dtype_code(A), layout, N, n, _p(A), _p(out), _stream(stream)))
     return out
 
@@ -281,9 +321,11 @@ def aminv(A, out=None, det=None, want_det=True, count_singular=True, layout=LAYO
     N, n, n2 = _page_dims(A, layout)
     if n != n2:
         raise ValueError("aminv: square pages required")
-    out = torch.empty_like(A) if out is None else _req(out, A.dtype)
+    out = torch.empty_like(A) if out is None else _buf(out, N * n * n, A.dtype, A.device, "out")
     if want_det and det is None:
         det = torch.empty(N, dtype=A.dtype, device=A.device)
+    elif want_det:
+        _buf(det, N, A.dtype, A.device, "det")
     ns = torch.zeros(1, dtype=torch.int64, device=A.device) if count_singular else None
     _check(lib().vla_aminv(_dtype_code(A), layout, N, n, _p(A), _p(out), _p(det) if want_det else None, _p(ns),
                            _stream(stream)))
@@ -294,7 +336,7 @@ def amt(A, out=None, layout=LAYOUT_PAGE, stream=None):
     """C_k = A_k^T (amt).  A: m x n pages -> n x m pages."""
     _req(A)
     N, m, n = _page_dims(A, layout)
-    out = _new_pages(N, n, m, layout, A) if out is None else _req(out, A.dtype)
+    out = _new_pages(N, n, m, layout, A) if out is None else _buf(out, N * m * n, A.dtype, A.device, "out")
     _check(lib().vla_amt(_dtype_code(A), layout, N, m, n, _p(A), _p(out), _stream(stream)))
     return out
 
@@ -302,10 +344,11 @@ def amt(A, out=None, layout=LAYOUT_PAGE, stream=None):
 def avtav(a, b, out=None, layout=LAYOUT_PAGE, stream=None):
     """out_k = a_k^T b_k (avtav).  a, b: (N, n) page layout or (n, N) SoA."""
     _req(a), _req(b, a.dtype)
+    _same_device(a, b)
     N, n = a.shape if layout == LAYOUT_PAGE else a.shape[::-1]
     if b.shape != a.shape:
         raise ValueError("avtav: a and b must have the same shape")
-    out = torch.empty(N, dtype=a.dtype, device=a.device) if out is None else _req(out, a.dtype)
+    out = torch.empty(N, dtype=a.dtype, device=a.device) if out is None else _buf(out, N, a.dtype, a.device, "out")
     _check(lib().vla_avtav(_dtype_code(a), layout, N, n, _p(a), _p(b), _p(out), _stream(stream)))
     return out
 
@@ -314,11 +357,12 @@ def amsm(A, S, out=None, layout=LAYOUT_PAGE, stream=None):
     """C_k = A_k S (amsm).  A: m x p pages; S: one p x n matrix as a (n, p)
     tensor (its columns, column-major like a page) -> m x n pages."""
     _req(A), _req(S, A.dtype)
+    _same_device(A, S)
     N, m, p = _page_dims(A, layout)
     n, p2 = S.shape
     if p2 != p:
         raise ValueError("amsm: S must have p rows")
-    out = _new_pages(N, m, n, layout, A) if out is None else _req(out, A.dtype)
+    out = _new_pages(N, m, n, layout, A) if out is None else _buf(out, N * m * n, A.dtype, A.device, "out")
     _check(lib().vla_amsm(_dtype_code(A), layout, N, m, p, n, _p(A), _p(S), _p(out), _stream(stream)))
     return out
 
@@ -326,10 +370,11 @@ def amsm(A, S, out=None, layout=LAYOUT_PAGE, stream=None):
 def amsv(A, s, out=None, layout=LAYOUT_PAGE, stream=None):
     """y_k = A_k s (amsv).  A: m x n pages; s: (n,) -> (N, m) page layout or (m, N) SoA."""
     _req(A), _req(s, A.dtype)
+    _same_device(A, s)
     N, m, n = _page_dims(A, layout)
     if s.numel() != n:
         raise ValueError("amsv: s must hold n values")
-    out = _new_vec(N, m, layout, A) if out is None else _req(out, A.dtype)
+    out = _new_vec(N, m, layout, A) if out is None else _buf(out, N * m, A.dtype, A.device, "out")
     _check(lib().vla_amsv(_dtype_code(A), layout, N, m, n, _p(A), _p(s), _p(out), _stream(stream)))
     return out
 
@@ -338,11 +383,12 @@ def smamt(S, A, out=None, layout=LAYOUT_PAGE, stream=None):
     """C_k = S A_k^T (smamt).  S: one m x p matrix as a (p, m) tensor; A: n x p
     pages -> m x n pages."""
     _req(A), _req(S, A.dtype)
+    _same_device(A, S)
     N, n, p = _page_dims(A, layout)
     p2, m = S.shape
     if p2 != p:
         raise ValueError("smamt: S must have p columns")
-    out = _new_pages(N, m, n, layout, A) if out is None else _req(out, A.dtype)
+    out = _new_pages(N, m, n, layout, A) if out is None else _buf(out, N * m * n, A.dtype, A.device, "out")
     _check(lib().vla_smamt(_dtype_code(A), layout, N, m, p, n, _p(S), _p(A), _p(out), _stream(stream)))
     return out
 
@@ -351,10 +397,11 @@ def svamt(s, A, out=None, layout=LAYOUT_PAGE, stream=None):
     """y_k = s^T A_k^T (svamt), a 1 x m page per k.  s: (n,); A: m x n pages ->
     (N, m) page layout or (m, N) SoA."""
     _req(A), _req(s, A.dtype)
+    _same_device(A, s)
     N, m, n = _page_dims(A, layout)
     if s.numel() != n:
         raise ValueError("svamt: s must hold n values")
-    out = _new_vec(N, m, layout, A) if out is None else _req(out, A.dtype)
+    out = _new_vec(N, m, layout, A) if out is None else _buf(out, N * m, A.dtype, A.device, "out")
     _check(lib().vla_svamt(_dtype_code(A), layout, N, m, n, _p(s), _p(A), _p(out), _stream(stream)))
     return out
 
@@ -372,6 +419,8 @@ class Mesh:
         _req(coords, torch.float64), _req(elems, torch.int32)
         if faces is not None:
             _req(faces, torch.int32)
+        _same_device(coords, elems, faces)
+        _mesh_arrays(coords, elems, faces, order)
         nn, dim = coords.shape
         ne = elems.shape[0]
         nfb = 0 if faces is None else faces.shape[0]
@@ -411,12 +460,12 @@ class Mesh:
         element pages (ne, nlb, nlb).  Returns a dict of tensors."""
         dev = self.device
         f64 = torch.float64
-        if want_K and K is None:
-            K = torch.empty(self.nnz, dtype=f64, device=dev)
-        if want_M and M is None:
-            M = torch.empty(self.nnz, dtype=f64, device=dev)
-        if want_vol and vol is None:
-            vol = torch.empty(self.ne, dtype=f64, device=dev)
+        if want_K:
+            K = torch.empty(self.nnz, dtype=f64, device=dev) if K is None else _buf(K, self.nnz, f64, dev, "K")
+        if want_M:
+            M = torch.empty(self.nnz, dtype=f64, device=dev) if M is None else _buf(M, self.nnz, f64, dev, "M")
+        if want_vol:
+            vol = torch.empty(self.ne, dtype=f64, device=dev) if vol is None else _buf(vol, self.ne, f64, dev, "vol")
         Kp = torch.empty((self.ne, self.nlb, self.nlb), dtype=f64, device=dev) if pages else None
         Mp = torch.empty((self.ne, self.nlb, self.nlb), dtype=f64, device=dev) if pages else None
         ns = torch.zeros(1, dtype=torch.int64, device=dev) if count_singular else None
@@ -435,8 +484,12 @@ class Mesh:
         dev = self.device
         if normals is None:
             normals = torch.empty((max(self.nfb, 1), self.dim), dtype=torch.float64, device=dev)[: self.nfb]
+        else:
+            _buf(normals, self.nfb * self.dim, torch.float64, dev, "normals")
         if areas is None:
             areas = torch.empty(max(self.nfb, 1), dtype=torch.float64, device=dev)[: self.nfb]
+        else:
+            _buf(areas, self.nfb, torch.float64, dev, "areas")
         _check(lib().vla_boundary(self._h, precision, _p(normals), _p(areas), _stream(stream)))
         return normals, areas
 
@@ -466,19 +519,24 @@ class Mesh:
     def rhs(self, gqo, fip, b=None, b2D=None, want_b2D=True, stream=None):
         """Load vector b (nn,) and element loads b2D (ne, nlb) for f at the
         degree-gqo points (fip (ne, nip)) (vla_rhs)."""
-        _req(fip, torch.float64)
-        dev = self.device
-        if b is None:
-            b = torch.empty(self.nn, dtype=torch.float64, device=dev)
-        if want_b2D and b2D is None:
-            b2D = torch.empty((self.ne, self.nlb), dtype=torch.float64, device=dev)
+        dev, f64 = self.device, torch.float64
+        nip = quad_rule(self.dim, gqo)[1].shape[0]
+        _buf(fip, self.ne * nip, f64, dev, "fip")
+        b = torch.empty(self.nn, dtype=f64, device=dev) if b is None else _buf(b, self.nn, f64, dev, "b")
+        if want_b2D:
+            b2D = (torch.empty((self.ne, self.nlb), dtype=f64, device=dev) if b2D is None
+                   else _buf(b2D, self.ne * self.nlb, f64, dev, "b2D"))
         _check(lib().vla_rhs(self._h, gqo, _p(fip), _p(b), _p(b2D) if want_b2D else None, _stream(stream)))
         return b, (b2D if want_b2D else None)
 
     def energies(self, u, K3D=None, M3D=None, b2D=None, local=True, stream=None):
         """Local energies (ne, 3) and their sums (3,) (vla_energies)."""
-        _req(u, torch.float64)
-        dev = self.device
+        dev, f64 = self.device, torch.float64
+        _buf(u, self.nn, f64, dev, "u")
+        for name, t, n in (("K3D", K3D, self.ne * self.nlb * self.nlb), ("M3D", M3D, self.ne * self.nlb * self.nlb),
+                           ("b2D", b2D, self.ne * self.nlb)):
+            if t is not None:
+                _buf(t, n, f64, dev, name)
         J = torch.empty((self.ne, 3), dtype=torch.float64, device=dev) if local else None
         tot = torch.empty(3, dtype=torch.float64, device=dev)
         _check(lib().vla_energies(self._h, _p(u), _p(K3D), _p(M3D), _p(b2D), _p(J), _p(tot), _stream(stream)))
@@ -511,8 +569,12 @@ def element_pages_static(coords, elems, order=1, ca=1.0, cb=0.0, kind=COEFF_POLY
     count from raw mesh arrays, without a mesh handle and without any device
     allocation inside the library (vla_element_pages_static; at most 262,144
     nodes).  The output tensors are allocated here by PyTorch; callers that
-    cannot allocate pass the C entry point their own buffers."""
+    cannot allocate pass the C entry point their own buffers.  The element
+    indices must lie in [0, nn): this entry point reads them as given (use
+    Mesh, which validates them, for untrusted meshes)."""
     _req(coords, torch.float64), _req(elems, torch.int32)
+    _same_device(coords, elems)
+    _mesh_arrays(coords, elems, None, order)
     nn, dim = coords.shape
     ne, nlb = elems.shape
     dev = coords.device
@@ -533,6 +595,11 @@ def element_pages_static(coords, elems, order=1, ca=1.0, cb=0.0, kind=COEFF_POLY
 # ---------------------------------------------------------------------------
 
 def _job(mesh, out, kind, ca, cb):
+    sizes = {"K": mesh.nnz, "M": mesh.nnz, "vol": mesh.ne, "K3D": mesh.ne * mesh.nlb * mesh.nlb,
+             "M3D": mesh.ne * mesh.nlb * mesh.nlb}
+    for name, n in sizes.items():
+        if out.get(name) is not None:
+            _buf(out[name], n, torch.float64, mesh.device, name)
     return BatchJob(mesh._h, kind, 0, float(ca), float(cb), _p(out.get("K")), _p(out.get("M")),
                     _p(out.get("vol")), _p(out.get("K3D")), _p(out.get("M3D")))
 
@@ -594,6 +661,8 @@ class Batch:
 def batch_assemble(jobs, precision=PREC_MIXED, n_singular=None, stream=None):
     """One-shot batch (vla_batch_assemble): jobs as for Batch; stream-ordered."""
     arr = (BatchJob * len(jobs))(*[_job(m, o, k, a, b) for (m, o, k, a, b) in jobs])
+    if n_singular is not None:
+        _buf(n_singular, len(jobs), torch.int64, jobs[0][0].device, "n_singular")
     _check(lib().vla_batch_assemble(arr, len(jobs), precision, _p(n_singular), _stream(stream)))
     return [j[1] for j in jobs]
 
@@ -603,6 +672,8 @@ def autotune(coords, elems, order=1, precision=PREC_MIXED, reps=5, stream=None):
     stores the fastest for its element type and precision, and returns
     (tile_budget, ctas_per_sm, microseconds)."""
     _req(coords, torch.float64), _req(elems, torch.int32)
+    _same_device(coords, elems)
+    _mesh_arrays(coords, elems, None, order)
     nn, dim = coords.shape
     t = Tune()
     _check(lib().vla_autotune(dim, order, precision, nn, elems.shape[0], _p(coords), _p(elems), reps,
@@ -673,7 +744,13 @@ class Server:
         c, cp = self._ptr(coords, torch.float64)
         e, ep = self._ptr(elems, torch.int32)
         f, fp = (None, None) if faces is None else self._ptr(faces, torch.int32)
+        if len(c.shape) != 2 or c.shape[1] not in (2, 3):
+            raise ValueError("coords must be (nn, dim) with dim 2 or 3")
         nn, dim = c.shape
+        if order not in (1, 2) or len(e.shape) != 2 or e.shape[1] != _nlb(dim, order):
+            raise ValueError(f"elems must be (ne, {_nlb(dim, order) if order in (1, 2) else 'nlb'}) for order {order}")
+        if f is not None and (len(f.shape) != 2 or f.shape[1] != dim):
+            raise ValueError(f"faces must be (nfb, {dim})")
         ne = e.shape[0]
         nfb = 0 if f is None else f.shape[0]
         r = Request(int(key), dim, order, nn, ne, nfb, cp, ep, fp, 1 if keep_resident else 0, kind,
@@ -751,10 +828,13 @@ def gi(fip, w, sizes, normals=None, stream=None):
     """GI of Section 3.4 on the device: fip (n, nip, d), w (nip,) host weights,
     sizes (n,), normals (n, d) or None.  Returns a (d,) tensor, or a (1,)
     tensor holding the flux when normals are given."""
-    _req(fip, torch.float64), _req(sizes, torch.float64)
-    if normals is not None:
-        _req(normals, torch.float64)
+    _req(fip, torch.float64)
     n, nip, d = fip.shape
+    _buf(sizes, n, torch.float64, fip.device, "sizes")
+    if normals is not None:
+        _buf(normals, n * d, torch.float64, fip.device, "normals")
+    if len(w) != nip:
+        raise ValueError(f"gi: {nip} points in fip but {len(w)} weights")
     out = torch.empty(d if normals is None else 1, dtype=torch.float64, device=fip.device)
     wa = (C.c_double * nip)(*[float(x) for x in w])
     _check(lib().vla_gi(n, nip, d, _p(fip), wa, _p(sizes), _p(normals), _p(out), _stream(stream)))
@@ -763,12 +843,14 @@ def gi(fip, w, sizes, normals=None, stream=None):
 
 def avtamav(v, A, w, out=None, layout=LAYOUT_PAGE, stream=None):
     """out_k = v_k^T A_k w_k.  Page layout: v, w (N, n); A (N, n, n) (N, cols, rows)."""
-    _req(v), _req(A), _req(w)
+    _req(v), _req(A, v.dtype), _req(w, v.dtype)
+    _same_device(v, A, w)
     if layout == LAYOUT_PAGE:
         N, n = v.shape
     else:
         n, N = v.shape
-    if out is None:
-        out = torch.empty(N, dtype=v.dtype, device=v.device)
+    if w.shape != v.shape or A.numel() != N * n * n:
+        raise ValueError("avtamav: v and w must have the same shape and A n x n pages, one per vector")
+    out = torch.empty(N, dtype=v.dtype, device=v.device) if out is None else _buf(out, N, v.dtype, v.device, "out")
     _check(lib().vla_avtamav(_dtype_code(v), layout, N, n, _p(v), _p(A), _p(w), _p(out), _stream(stream)))
     return out
