@@ -165,8 +165,8 @@ typedef struct {
 } vla_mesh_info_t;
 
 /* Ingests a simplicial mesh and builds, on the device, everything the
- * assembly needs: the CSR pattern of sparse(X3D(:),Y3D(:),.,nn,nn) of
- * Section 3.5 (every (elems(k,i), elems(k,j)) pair, duplicates merged,
+ * assembly needs: the CSR pattern of the sparse assembly of Section 3.5
+ * (every (elems(k,i), elems(k,j)) pair, duplicates merged,
  * explicit zeros kept, columns ascending), node->element incidence, the row
  * tiles of the assembly kernel and the owner of every boundary facet.
  *   dim 2 or 3; order VLA_P1 or VLA_P2; nn, ne >= 1.

@@ -475,8 +475,9 @@ void orc_element_pages(int dim, int order, int64_t ne, int nlb, const int32_t *e
 }
 
 /* ------------------------------------------------------------------------ */
-/* sparse assembly: the semantics of sparse(X3D(:),Y3D(:),K3D(:),nn,nn)      */
-/* (Section 3.5): all (row, col) pairs of all elements, duplicates summed.   */
+/* sparse assembly with the semantics of MATLAB's sparse() on the row and    */
+/* column index pages and the element pages (Section 3.5): all (row, col)   */
+/* pairs of all elements, duplicates summed.                                */
 /* Structural zeros are kept: the pattern depends on connectivity only.     */
 /* ------------------------------------------------------------------------ */
 

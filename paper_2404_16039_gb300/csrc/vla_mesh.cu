@@ -1,5 +1,5 @@
 // vla_mesh.cu -- mesh ingest on the device: validation, node->element
-// incidence, the CSR pattern of sparse(X3D(:),Y3D(:),.,nn,nn) (Section 3.5),
+// incidence, the CSR pattern of the sparse assembly of Section 3.5,
 // boundary-facet owners, the float-pair split of the coordinates, and the row
 // tiles used by the assembly kernel.
 //
