@@ -174,6 +174,17 @@ MUTANTS = [
     ("avtamav_right_vector_index", "* w[k * n + j];\n        out[k] = s;", "* w[k * n + i];\n        out[k] = s;"),
     ("boundary_opposite_vertex", "if (!in) opp = v;", "if (in) opp = v;"),
     ("simplex_normals_inverse_operand", "        inv_small(dim, V, Vi);\n        double *out", "        inv_small(dim, V, Vi);\n        for (int q = 0; q < dim * dim; ++q) Vi[q] = V[q];\n        double *out"),
+    # fifth batch: 2-D rules and facets, P2 basis, gradients and node values
+    ("rule_segment_points_equal", "ip[2] = 0.5 - d, ip[3] = 0.5 + d;", "ip[2] = 0.5 + d, ip[3] = 0.5 - d;"),
+    ("rule_centroid_not_barycentric", "for (int j = 0; j < nv; ++j) ip[j] = 1.0 / nv;", "for (int j = 0; j < nv; ++j) ip[j] = 1.0 / (nv + 1);"),
+    ("p2_vertex_basis_exponent", "out->alpha[1][q] = 1;", "out->alpha[1][q] = 2;"),
+    ("p2_edge_basis_node", "out->alpha[0][e[0]] += 1;", "out->alpha[0][e[1]] += 1;"),
+    ("basis_value_power_index", "for (int e = 0; e < p.alpha[t][s]; ++e) m *= lam[s];", "for (int e = 0; e < p.alpha[t][s]; ++e) m *= lam[0];"),
+    ("boundary_second_node", "*x2 = coords + (int64_t)fn[1] * dim;", "*x2 = coords + (int64_t)fn[2 % dim] * dim;"),
+    ("quad_points_dropped_vertex", "for (int j = 0; j < nvert; ++j) s += ip", "for (int j = 0; j < nvert - 1; ++j) s += ip"),
+    ("last_gradient_partial_sum", "for (int j = 0; j < dim; ++j) s += glam[r + j * dim];", "for (int j = 0; j < dim - 1; ++j) s += glam[r + j * dim];"),
+    ("energy_node_values_index", "for (int j = 0; j < nlb; ++j) uk[j] = u[elems[k * nlb + j]];", "for (int j = 0; j < nlb; ++j) uk[j] = u[elems[k * nlb]];"),
+    ("centroid_vertex_argument", "double c = centroid_coeff(dim, dim + 1, nlb,", "double c = centroid_coeff(dim, dim, nlb,"),
 ]
 
 
