@@ -198,7 +198,7 @@ def run_reference(args):
             per_step.append(time.perf_counter() - t0)
     dt = sum(per_step) / len(per_step)
     val = m.ne / dt
-    line = {"metric": "elements/sec for P1 tet K+M to CSR", "value": val, "unit": "elements/s", "n_gpus": 1,
+    line = {"metric": "elements/sec for P1 tet K+M to CSR", "value": val, "unit": "elements/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": dict(_config(m, "fp64 oracle"),

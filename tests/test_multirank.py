@@ -78,6 +78,6 @@ def test_reference_arm_rank0_only(tmp_path):
     assert rc0 == "0" and rc1 == "0"
     assert out1.strip() == ""                      # rank 1 prints nothing
     line = json.loads(out0.strip().splitlines()[-1])
-    assert line["impl"] == "reference" and line["n_gpus"] == 1
+    assert line["impl"] == "reference" and line["n_gpus"] == 2   # the launch it was given; rank 0 does the work
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["value"] > 0 and line["unit"] == "elements/s"
