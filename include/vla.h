@@ -68,7 +68,8 @@ enum { VLA_PREC_FP64 = 0, VLA_PREC_MIXED = 1 };          /* assembly precision *
 enum { VLA_COEFF_POLY = 0, VLA_COEFF_EXP = 1,            /* coefficient kind (see vla_assemble) */
        VLA_COEFF_POLY_IP = 2, VLA_COEFF_EXP_IP = 3 };
 
-/* Library version, 100*major + minor. */
+/* Library version, 100*major + minor (housekeeping; no counterpart in the
+ * paper). */
 int32_t vla_version(void);
 
 /* Copies the last error message of the calling thread into buf (NUL
@@ -185,11 +186,12 @@ typedef struct {
 vla_status vla_mesh_create(int32_t dim, int32_t order, int64_t nn, int64_t ne, const double *coords,
                            const int32_t *elems, int64_t nfb, const int32_t *faces, void *stream, vla_mesh **out);
 
-/* Fills *info (host struct). */
+/* Fills *info (host struct): the sizes of the mesh and of the CSR pattern of
+ * the Section 3.5 assembly, and the tiling (no counterpart in the paper). */
 vla_status vla_mesh_info(const vla_mesh *mesh, vla_mesh_info_t *info);
 
-/* Copies the CSR pattern to caller buffers (device): row_ptr nn+1 int32,
- * col_idx nnz int32.  Either may be NULL. */
+/* Copies the CSR pattern of the Section 3.5 sparse assembly to caller buffers
+ * (device): row_ptr nn+1 int32, col_idx nnz int32.  Either may be NULL. */
 vla_status vla_mesh_csr(const vla_mesh *mesh, int32_t *row_ptr, int32_t *col_idx, void *stream);
 
 /* Assembles K and M (Section 3.5 stiffness and mass listings) into the
@@ -274,11 +276,13 @@ vla_status vla_element_pages_static(int32_t dim, int32_t order, int64_t nn, int6
 vla_status vla_mesh_facets(const vla_mesh *mesh, int32_t *faces, int32_t *owner, int32_t *neighbor, int64_t *n_faces,
                            int64_t *n_boundary, void *stream);
 
-/* Releases the handle and its device memory (stream-ordered on the stream
+/* Housekeeping (no counterpart in the paper): releases the handle and its
+ * device memory (stream-ordered on the stream
  * the mesh was created with, which is synchronised first).  NULL is a no-op. */
 vla_status vla_mesh_destroy(vla_mesh *mesh);
 
-/* Reads and clears the mesh's device error word, synchronising `stream`:
+/* Failure detection (no counterpart in the paper): reads and clears the
+ * mesh's device error word, synchronising `stream`:
  * VLA_ERR_TIMEOUT if a bounded wait of a kernel on this mesh expired since
  * the last check (its outputs are then incomplete), else VLA_OK.  Kernels
  * never spin without a limit; an expired wait ends the kernel early and is
@@ -378,7 +382,8 @@ typedef struct {
 #define VLA_BATCH_SPLIT 4      /* one persistent kernel per element type present, back to back */
 #define VLA_BATCH_AUTOTUNE 8   /* time both forms at creation (runs the batch) and keep the faster */
 
-/* Builds the job table and work list of a batch on the device.
+/* Builds the job table and work list of a batch on the device (batching of
+ * the Section 3.5 assembly; no counterpart in the paper).
  *   jobs: host array of count >= 1 jobs (copied; meshes must outlive the batch).
  *   precision: VLA_PREC_FP64 or VLA_PREC_MIXED, for every job.
  *   n_singular: device int64[count] receiving, per job, the number of
@@ -396,24 +401,27 @@ typedef struct {
 vla_status vla_batch_create(const vla_batch_job_t *jobs, int32_t count, int32_t precision, int64_t *n_singular,
                             int32_t flags, void *stream, vla_batch **out);
 
-/* Replaces job `index`'s coefficient and output pointers (same mesh), stream
- * ordered: runs enqueued on `stream` afterwards see the new job. */
+/* Replaces job `index`'s coefficient (Section 3.5.1 coefficients) and output
+ * pointers (same mesh), stream ordered: runs enqueued on `stream` afterwards see the new job. */
 vla_status vla_batch_set_job(vla_batch *batch, int32_t index, const vla_batch_job_t *job, void *stream);
 
-/* Enqueues one assembly of every job on `stream` (one persistent launch, or
+/* Enqueues one Section 3.5 assembly of every job on `stream` (one persistent launch, or
  * one graph launch with VLA_BATCH_GRAPH). */
 vla_status vla_batch_run(vla_batch *batch, void *stream);
 
-/* Fills *info (host struct). */
+/* Fills *info (host struct): the batch's launch shape (no counterpart in the
+ * paper). */
 vla_status vla_batch_info(const vla_batch *batch, vla_batch_info_t *info);
 
-/* As vla_mesh_check, for the batch's own error word. */
+/* As vla_mesh_check, for the batch's own error word (no counterpart in the
+ * paper). */
 vla_status vla_batch_check(vla_batch *batch, void *stream);
 
-/* Frees the batch.  No run of it may still be in flight. */
+/* Frees the batch (housekeeping; no counterpart in the paper).  No run of it
+ * may still be in flight. */
 vla_status vla_batch_destroy(vla_batch *batch);
 
-/* One-shot batch: create, run once and free, all stream-ordered on `stream`
+/* One-shot batch of Section 3.5 assemblies: create, run once and free, all stream-ordered on `stream`
  * (no host synchronisation); the error word is not kept. */
 vla_status vla_batch_assemble(const vla_batch_job_t *jobs, int32_t count, int32_t precision, int64_t *n_singular,
                               void *stream);
@@ -436,7 +444,8 @@ typedef struct {
     double us;                 /* median time of one assembly of the sample mesh, microseconds (tuner output) */
 } vla_tune_t;
 
-/* Times vla_assemble (precision as given, coefficient 1 + |x|^2, K, M and vol
+/* Autotuner (no counterpart in the paper): times the Section 3.5 assembly of
+ * vla_assemble (precision as given, coefficient 1 + |x|^2, K, M and vol
  * outputs, an L2 flush before every timed run) on the sample mesh for each
  * candidate budget (0.5x to 1.5x the default) and then each residency (1, 2,
  * 3, 4 and the occupancy limit) at the best budget, `reps` timed runs each
@@ -447,7 +456,8 @@ typedef struct {
 vla_status vla_autotune(int32_t dim, int32_t order, int32_t precision, int64_t nn, int64_t ne, const double *coords,
                         const int32_t *elems, int32_t reps, void *stream, vla_tune_t *best);
 
-/* Reads or sets the stored parameters for an element type and precision
+/* Autotuner state (no counterpart in the paper): reads or sets the stored
+ * parameters for an element type and precision
  * (us is ignored by vla_tune_set and 0 from vla_tune_get). */
 vla_status vla_tune_get(int32_t dim, int32_t order, int32_t precision, vla_tune_t *out);
 vla_status vla_tune_set(int32_t dim, int32_t order, int32_t precision, const vla_tune_t *in);
@@ -511,25 +521,30 @@ typedef struct {
     double assembly_busy_s;    /* time with a launch in flight */
 } vla_server_stats_t;
 
-/* Starts the scheduler and ingest threads on the current device. */
+/* Starts the scheduler and ingest threads on the current device (serving of
+ * the Section 3.5 assembly; no counterpart in the paper). */
 vla_status vla_server_create(const vla_server_config_t *cfg, vla_server **out);
 
-/* Queues a request; *ticket identifies it.  Never blocks on the GPU. */
+/* Queues a request (a mesh and a Section 3.5.1 coefficient); *ticket
+ * identifies it.  Never blocks on the GPU. */
 vla_status vla_server_submit(vla_server *server, const vla_request_t *req, int64_t *ticket);
 
-/* Waits up to timeout_s seconds (0: no wait) for the request: VLA_PENDING
+/* Serving (no counterpart in the paper): waits up to timeout_s seconds (0: no
+ * wait) for the request: VLA_PENDING
  * while it runs, VLA_OK with *res filled when done, the request's error if
  * it failed (*res filled too). */
 vla_status vla_server_poll(vla_server *server, int64_t ticket, double timeout_s, vla_result_t *res);
 
-/* Frees a finished request's outputs (and its mesh, unless resident). */
+/* Frees a finished request's outputs (and its mesh, unless resident); no
+ * counterpart in the paper. */
 vla_status vla_server_release(vla_server *server, int64_t ticket);
 
-/* Fills *stats (host struct). */
+/* Fills *stats (host struct): the server's counters (no counterpart in the
+ * paper). */
 vla_status vla_server_stats(vla_server *server, vla_server_stats_t *stats);
 
 /* Finishes admitted requests, drops queued ones, joins the threads and
- * frees everything. */
+ * frees everything (housekeeping; no counterpart in the paper). */
 vla_status vla_server_destroy(vla_server *server);
 
 #ifdef __cplusplus
