@@ -93,3 +93,85 @@ def test_binding_refuses_to_run_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(vla, "_lib", None)
     with pytest.raises(ImportError):
         vla.lib()
+
+
+def test_remaining_entry_points_validate_without_gpu(libpath):
+    # every other entry point: arguments rejected before any CUDA call (null
+    # handles, unknown shapes, kinds, precisions, flags, limits), destroy of
+    # NULL is a no-op, and the quadrature rules are pure host code
+    lib = ctypes.CDLL(libpath)
+    i32, i64, f64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+    fake = 16   # never dereferenced
+    INVALID, BUDGET, UNSUPPORTED = -1, -6, -8
+
+    lib.vla_quad_rule.argtypes = [i32, i32, ctypes.POINTER(i32), vp, vp]
+    nip = i32()
+    ip = (f64 * 32)()
+    w = (f64 * 8)()
+    assert lib.vla_quad_rule(3, 3, ctypes.byref(nip), ip, w) == 0
+    assert nip.value == 5 and abs(sum(w[: nip.value]) - 1.0) < 1e-15
+    assert lib.vla_quad_rule(2, 2, ctypes.byref(nip), ip, w) == 0 and nip.value == 3
+    assert lib.vla_quad_rule(3, 4, ctypes.byref(nip), ip, w) == UNSUPPORTED
+    assert lib.vla_quad_rule(0, 1, ctypes.byref(nip), ip, w) == UNSUPPORTED
+
+    lib.vla_gi.argtypes = [i64, i32, i32, vp, vp, vp, vp, vp, vp]
+    assert lib.vla_gi(10, 9, 1, fake, w, fake, None, fake, None) == INVALID      # more than 8 points
+    assert lib.vla_gi(10, 4, 5, fake, w, fake, None, fake, None) == INVALID      # more than 4 components
+    assert lib.vla_gi(-1, 4, 1, fake, w, fake, None, fake, None) == INVALID
+    assert lib.vla_gi(10, 4, 1, fake, None, fake, None, fake, None) == INVALID   # no weights
+
+    lib.vla_avtamav.argtypes = [i32, i32, i64, i32, vp, vp, vp, vp, vp]
+    assert lib.vla_avtamav(1, 0, 10, 17, fake, fake, fake, fake, None) == INVALID
+    assert lib.vla_avtamav(3, 0, 10, 3, fake, fake, fake, fake, None) == INVALID
+    assert lib.vla_avtamav(1, 0, 0, 3, None, None, None, None, None) == 0
+
+    lib.vla_element_pages_static.argtypes = [i32, i32, i64, i64, vp, vp, i32, f64, f64, i32, vp, vp, vp, vp, vp]
+    assert lib.vla_element_pages_static(4, 1, 10, 10, fake, fake, 0, 1.0, 0.0, 1, None, None, None, None, None) == INVALID
+    assert lib.vla_element_pages_static(3, 3, 10, 10, fake, fake, 0, 1.0, 0.0, 1, None, None, None, None, None) == INVALID
+    assert lib.vla_element_pages_static(3, 1, 1 << 20, 10, fake, fake, 0, 1.0, 0.0, 1,
+                                        None, None, None, None, None) == BUDGET
+
+    lib.vla_batch_create.argtypes = [vp, i32, i32, vp, i32, vp, ctypes.POINTER(vp)]
+    lib.vla_batch_assemble.argtypes = [vp, i32, i32, vp, vp]
+    h = vp()
+    jobs = ctypes.create_string_buffer(1024)
+    assert lib.vla_batch_create(None, 0, 1, None, 0, None, ctypes.byref(h)) == INVALID
+    assert lib.vla_batch_create(jobs, 1, 7, None, 0, None, ctypes.byref(h)) == INVALID     # precision
+    assert lib.vla_batch_create(jobs, 1, 1, None, 1 << 10, None, ctypes.byref(h)) == INVALID   # unknown flag
+    assert lib.vla_batch_assemble(None, 0, 1, None, None) == INVALID
+
+    class Tune(ctypes.Structure):
+        _fields_ = [("tile_budget", i32), ("ctas_per_sm", i32), ("us", f64)]
+
+    lib.vla_tune_get.argtypes = [i32, i32, i32, ctypes.POINTER(Tune)]
+    lib.vla_tune_set.argtypes = [i32, i32, i32, ctypes.POINTER(Tune)]
+    t = Tune(-1, 0, 0.0)
+    assert lib.vla_tune_get(4, 1, 1, ctypes.byref(t)) == INVALID
+    assert lib.vla_tune_set(3, 1, 1, ctypes.byref(t)) == INVALID                          # negative budget
+    lib.vla_autotune.argtypes = [i32, i32, i32, i64, i64, vp, vp, i32, vp, ctypes.POINTER(Tune)]
+    assert lib.vla_autotune(4, 1, 1, 10, 10, fake, fake, 3, None, ctypes.byref(t)) == INVALID
+
+    class ServerConfig(ctypes.Structure):
+        _fields_ = [("hbm_budget_bytes", i64), ("precision", i32), ("ingest_workers", i32),
+                    ("max_batch", i32), ("max_inflight", i32)]
+
+    lib.vla_server_create.argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+    for cfg in (ServerConfig(0, 1, 4, 0, 0), ServerConfig(1 << 30, 5, 4, 0, 0), ServerConfig(1 << 30, 1, 65, 0, 0)):
+        assert lib.vla_server_create(ctypes.byref(cfg), ctypes.byref(h)) == INVALID
+    lib.vla_server_poll.argtypes = [vp, i64, f64, vp]
+    assert lib.vla_server_submit(None, None, None) == INVALID
+    assert lib.vla_server_poll(None, 0, 0.0, None) == INVALID
+    assert lib.vla_server_release(None, ctypes.c_int64(0)) == INVALID
+    assert lib.vla_server_stats(None, None) == INVALID
+
+    lib.vla_assemble.argtypes = [vp, i32, f64, f64, i32, vp, vp, vp, vp, vp, vp, vp]
+    assert lib.vla_assemble(None, 0, 1.0, 0.0, 1, None, None, None, None, None, None, None) == INVALID
+    for name, nargs in (("vla_boundary", 5), ("vla_simplex_normals", 3), ("vla_mesh_csr", 4), ("vla_mesh_check", 2),
+                        ("vla_mesh_info", 2), ("vla_quad_points", 5), ("vla_rhs", 6), ("vla_energies", 8),
+                        ("vla_mesh_facets", 7)):
+        args = [None] * nargs
+        if name in ("vla_boundary", "vla_quad_points", "vla_rhs"):
+            args[1] = 1
+        assert getattr(lib, name)(*args) == INVALID, name
+    for name in ("vla_mesh_destroy", "vla_batch_destroy", "vla_server_destroy"):
+        assert getattr(lib, name)(None) == 0, name
