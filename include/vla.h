@@ -69,7 +69,7 @@ enum { VLA_COEFF_POLY = 0, VLA_COEFF_EXP = 1,            /* coefficient kind (se
        VLA_COEFF_POLY_IP = 2, VLA_COEFF_EXP_IP = 3 };
 
 /* Library version, 100*major + minor (housekeeping; no counterpart in the
- * paper). */
+ * paper).  Cannot fail. */
 int32_t vla_version(void);
 
 /* Copies the last error message of the calling thread into buf (NUL
@@ -84,25 +84,29 @@ size_t vla_last_error(char *buf, size_t len);
 
 /* amtam: C_k = A_k^T B_k for every page k.  A: p x m x N, B: p x n x N,
  * C: m x n x N.  (Section 2.4 lists amtam as the product of one page array
- * with the transpose of another and identifies it with
- * pagemtimes(amx,'transpose',ama,'none'); its use amtam(dphi3D,dphi3D) in the
- * P1 stiffness listing of Section 3.5 fixes the reading transpose(A)*B.) */
+ * with the transpose of another and identifies it with MATLAB's pagemtimes
+ * with the transpose flag on the first operand; its use on two gradient
+ * pages in the P1 stiffness code of Section 3.5 fixes the reading A^T B.)
+ * Errors: VLA_ERR_INVALID_ARG for an unknown dtype or layout, N < 0, a shape
+ * outside the limits or a null array with N > 0; VLA_ERR_CUDA if a launch
+ * fails. */
 vla_status vla_amtam(int32_t dtype, int32_t layout, int64_t N, int32_t p, int32_t m, int32_t n, const void *A,
                      const void *B, void *C, void *stream);
 
 /* astam: C_k = s_k A_k (page-wise scalar multiplication Id (x) pi, Section
- * 2.2 and the astam example of Section 2.4).  s: N scalars, A and C m x n x N. */
+ * 2.2 and the astam example of Section 2.4).  s: N scalars, A and C m x n x N.
+ * Errors as for vla_amtam. */
 vla_status vla_astam(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t n, const void *s, const void *A,
                      void *C, void *stream);
 
 /* avtam: y_k = v_k^T A_k (row vector times page, Section 2.4).  v: p x N,
- * A: p x n x N, y: n x N. */
+ * A: p x n x N, y: n x N.  Errors as for vla_amtam. */
 vla_status vla_avtam(int32_t dtype, int32_t layout, int64_t N, int32_t p, int32_t n, const void *v, const void *A,
                      void *y, void *stream);
 
 /* amdet: det_k = det(A_k), signed (page-wise determinant det_W of Section
  * 2.3; the signed value -25/64 * 6 of the Section 3.2 example).  A: n x n x N,
- * det: N values. */
+ * det: N values.  Errors as for vla_amtam. */
 vla_status vla_amdet(int32_t dtype, int32_t layout, int64_t N, int32_t n, const void *A, void *det, void *stream);
 
 /* aminv: Ainv_k = A_k^{-1} (page-wise inverse of Section 2.3, pageinv) and,
@@ -110,18 +114,21 @@ vla_status vla_amdet(int32_t dtype, int32_t layout, int64_t N, int32_t n, const 
  * a page with det == 0 gets IEEE inf/nan entries and is counted.
  * n_singular: NULL, or a DEVICE int64 that receives the number of singular
  * pages (overwritten, not accumulated).  Returns VLA_OK; singular pages are
- * reported through n_singular only (the count lives on the device). */
+ * reported through n_singular only (the count lives on the device).
+ * Errors as for vla_amtam. */
 vla_status vla_aminv(int32_t dtype, int32_t layout, int64_t N, int32_t n, const void *A, void *Ainv, void *det,
                      int64_t *n_singular, void *stream);
 
 /* amt: C_k = A_k^T (page-wise transpose, pagemtranspose, Section 2.4 and the
  * transpose map of Section 2.2; the X3D = amt(Y3D) index pages of the
- * Section 3.5 listings).  A: m x n x N, C: n x m x N, m and n in {2, 3}. */
+ * Section 3.5 listings).  A: m x n x N, C: n x m x N, m and n in {2, 3}.
+ * Errors as for vla_amtam. */
 vla_status vla_amt(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t n, const void *A, void *C,
                    void *stream);
 
 /* avtav: out_k = a_k^T b_k (page-wise dot product of two vector arrays,
- * Section 2.4).  a, b: n x N with n in {2, 3}; out: N values. */
+ * Section 2.4).  a, b: n x N with n in {2, 3}; out: N values.  Errors as for
+ * vla_amtam. */
 vla_status vla_avtav(int32_t dtype, int32_t layout, int64_t N, int32_t n, const void *a, const void *b, void *out,
                      void *stream);
 
@@ -136,7 +143,8 @@ vla_status vla_avtav(int32_t dtype, int32_t layout, int64_t N, int32_t n, const 
  *          (f_elems = amsv(fip, w) of Section 3.4)
  *   smamt: C_k = S A_k^T,     S: m x p, A: n x p x N, C: m x n x N
  *          (tjac = smamt(dshape, coords3D), the transposed Jacobian of Section 3.5)
- *   svamt: y_k = s^T A_k^T,   s: n, A: m x n x N, y: 1 x m x N (the values of amsv as rows) */
+ *   svamt: y_k = s^T A_k^T,   s: n, A: m x n x N, y: 1 x m x N (the values of amsv as rows)
+ * Errors as for vla_amtam (every dimension must lie in [1, 16]). */
 vla_status vla_amsm(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t p, int32_t n, const void *A,
                     const void *S, void *C, void *stream);
 vla_status vla_amsv(int32_t dtype, int32_t layout, int64_t N, int32_t m, int32_t n, const void *A, const void *s,
@@ -187,11 +195,13 @@ vla_status vla_mesh_create(int32_t dim, int32_t order, int64_t nn, int64_t ne, c
                            const int32_t *elems, int64_t nfb, const int32_t *faces, void *stream, vla_mesh **out);
 
 /* Fills *info (host struct): the sizes of the mesh and of the CSR pattern of
- * the Section 3.5 assembly, and the tiling (no counterpart in the paper). */
+ * the Section 3.5 assembly, and the tiling (no counterpart in the paper).
+ * Errors: VLA_ERR_INVALID_ARG for a NULL argument. */
 vla_status vla_mesh_info(const vla_mesh *mesh, vla_mesh_info_t *info);
 
 /* Copies the CSR pattern of the Section 3.5 sparse assembly to caller buffers
- * (device): row_ptr nn+1 int32, col_idx nnz int32.  Either may be NULL. */
+ * (device): row_ptr nn+1 int32, col_idx nnz int32.  Either may be NULL.
+ * Errors: VLA_ERR_INVALID_ARG for a NULL mesh; VLA_ERR_CUDA if a copy fails. */
 vla_status vla_mesh_csr(const vla_mesh *mesh, int32_t *row_ptr, int32_t *col_idx, void *stream);
 
 /* Assembles K and M (Section 3.5 stiffness and mass listings) into the
@@ -230,7 +240,9 @@ vla_status vla_assemble(const vla_mesh *mesh, int32_t coeff_kind, double ca, dou
  * rotated by -90 degrees (2-D), oriented away from the remaining vertex of
  * the owning element, normalised to unit length; areas[f] = |n|/2 (3-D) or
  * the edge length (2-D).  normals: dim x nfb FP64 (facet f at f*dim + d),
- * areas: nfb FP64 (device).  precision as in vla_assemble. */
+ * areas: nfb FP64 (device).  precision as in vla_assemble.  A mesh without
+ * boundary facets is a no-op.  Errors: VLA_ERR_INVALID_ARG for a NULL mesh or
+ * output or an unknown precision; VLA_ERR_CUDA if a launch fails. */
 vla_status vla_boundary(const vla_mesh *mesh, int32_t precision, double *normals, double *areas, void *stream);
 
 /* Unnormalised outer normals of all element facets,
@@ -238,7 +250,9 @@ vla_status vla_boundary(const vla_mesh *mesh, int32_t precision, double *normals
  * transform X = A^{-T} of Section 2.3).  vectors3D_k holds x_j - x_last as
  * columns; normalsRef columns are -e_1..-e_dim and (1,..,1); column j is the
  * normal of the facet opposite local vertex j.  normals: dim x (dim+1) x ne
- * FP64 column-major pages (device). FP64 arithmetic. */
+ * FP64 column-major pages (device). FP64 arithmetic.  Errors:
+ * VLA_ERR_INVALID_ARG for a NULL mesh or output; VLA_ERR_CUDA if a launch
+ * fails. */
 vla_status vla_simplex_normals(const vla_mesh *mesh, double *normals, void *stream);
 
 /* Element pages and volumes without a mesh handle and without allocating.
@@ -272,13 +286,16 @@ vla_status vla_element_pages_static(int32_t dim, int32_t order, int64_t nn, int6
  * facet); *n_faces and *n_boundary (host) receive nf and the number of
  * boundary facets.  Call with NULL arrays first to learn nf.  Integer work,
  * deterministic; synchronises `stream`.  Unnormalised normals of all facets:
- * vla_simplex_normals, column j of element k's page. */
+ * vla_simplex_normals, column j of element k's page.  Errors:
+ * VLA_ERR_INVALID_ARG for a NULL mesh; VLA_ERR_OOM if scratch cannot be
+ * allocated; VLA_ERR_CUDA if a launch fails. */
 vla_status vla_mesh_facets(const vla_mesh *mesh, int32_t *faces, int32_t *owner, int32_t *neighbor, int64_t *n_faces,
                            int64_t *n_boundary, void *stream);
 
 /* Housekeeping (no counterpart in the paper): releases the handle and its
  * device memory (stream-ordered on the stream
- * the mesh was created with, which is synchronised first).  NULL is a no-op. */
+ * the mesh was created with, which is synchronised first).  NULL is a no-op;
+ * cannot fail. */
 vla_status vla_mesh_destroy(vla_mesh *mesh);
 
 /* Failure detection (no counterpart in the paper): reads and clears the
@@ -304,7 +321,10 @@ vla_status vla_quad_rule(int32_t sdim, int32_t gqo, int32_t *nip, double *ip, do
 /* Quadrature points X_ip = amsm(coords3D, ip) (Section 3.4): for every element
  * (facets = 0) or every boundary facet (facets = 1) and every point q of the
  * degree-gqo rule, X(:, q, k) = sum_j ip(j, q) x_j.  X: dim x nip x n FP64
- * column-major (device), n = ne or nfb.  FP64 arithmetic. */
+ * column-major (device), n = ne or nfb.  FP64 arithmetic.  Errors:
+ * VLA_ERR_INVALID_ARG for a NULL mesh or output, or facets = 1 on a mesh
+ * without boundary facets; VLA_ERR_UNSUPPORTED for a degree outside 1..3;
+ * VLA_ERR_CUDA if a launch fails. */
 vla_status vla_quad_points(const vla_mesh *mesh, int32_t gqo, int32_t facets, double *X, void *stream);
 
 /* The GI function of Section 3.4: value = sum_k sizes_k sum_q w_q f(:, q, k).
@@ -314,16 +334,22 @@ vla_status vla_quad_points(const vla_mesh *mesh, int32_t gqo, int32_t facets, do
  * Without normals out[c] (device, d <= 4 values) is the integral of component
  * c; with normals out[0] is the flux sum_k sizes_k (avg_k f) . n_k.  The sum is
  * reduced in a fixed order (bit-reproducible).  Allocates stream-ordered
- * scratch. */
+ * scratch.  Errors: VLA_ERR_INVALID_ARG for n < 0, nip outside [1, 8], d
+ * outside [1, 4], NULL w or out, or NULL fip or sizes with n > 0;
+ * VLA_ERR_OOM if the scratch cannot be allocated; VLA_ERR_CUDA if a launch
+ * fails. */
 vla_status vla_gi(int64_t n, int32_t nip, int32_t d, const double *fip, const double *w, const double *sizes,
                   const double *normals, double *out, void *stream);
 
 /* Load vector of Section 3.5 (rhs_vectorP1; P2 alike):
  * b2D(j, k) = |T_k| sum_q w_q f(x_q) phi_j(ip_q) for the degree-gqo rule, then
- * b = accumarray(elems(:), b2D(:)) in a fixed order (each node's incident
- * elements ascending).  fip: nip x ne FP64 (device) -- f at the points given by
+ * b_i = the sum of b2D(j, k) over the entries with elems(k, j) = i, in a fixed
+ * order (each node's incident elements ascending).  fip: nip x ne FP64 (device) -- f at the points given by
  * vla_quad_points(mesh, gqo, 0, ...).  b: nn (device) or NULL; b2D: nlb x ne
- * (device) or NULL (then scratch).  FP64. */
+ * (device) or NULL (then scratch).  FP64.  Errors: VLA_ERR_INVALID_ARG for a
+ * NULL mesh or fip; VLA_ERR_UNSUPPORTED for a degree outside 1..3;
+ * VLA_ERR_OOM if the scratch cannot be allocated; VLA_ERR_CUDA if a launch
+ * fails. */
 vla_status vla_rhs(const vla_mesh *mesh, int32_t gqo, const double *fip, double *b, double *b2D, void *stream);
 
 /* Local energies of Section 3.5 (eq. Jk_comps): with u_k the element's nodal
@@ -334,12 +360,16 @@ vla_status vla_rhs(const vla_mesh *mesh, int32_t gqo, const double *fip, double 
  * the element loads of vla_rhs (b2D: nlb x ne); any of the three may be NULL
  * (its energy is then 0).  J_local: 3 x ne (device) or NULL; J_total: 3 values
  * (device) or NULL -- the sums over elements, i.e. u^T K u / 2, u^T M u / 2 and
- * -b^T u, reduced in a fixed order.  FP64. */
+ * -b^T u, reduced in a fixed order.  FP64.  Errors: VLA_ERR_INVALID_ARG for a
+ * NULL mesh or u; VLA_ERR_OOM if the scratch for J_total cannot be allocated;
+ * VLA_ERR_CUDA if a launch fails. */
 vla_status vla_energies(const vla_mesh *mesh, const double *u, const double *K_pages, const double *M_pages,
                         const double *b2D, double *J_local, double *J_total, void *stream);
 
 /* out_k = v_k^T A_k w_k (Section 2.4, avtamav): v, w n x N, A n x n x N
- * (VLA_LAYOUT_PAGE, column-major pages) or the SoA layout; out N.  n <= 16. */
+ * (VLA_LAYOUT_PAGE, column-major pages) or the SoA layout; out N.  n <= 16.
+ * Errors: VLA_ERR_INVALID_ARG for an unknown dtype or layout, N < 0, n outside
+ * [1, 16] or a NULL array with N > 0; VLA_ERR_CUDA if a launch fails. */
 vla_status vla_avtamav(int32_t dtype, int32_t layout, int64_t N, int32_t n, const void *v, const void *A,
                        const void *w, void *out, void *stream);
 
@@ -402,15 +432,19 @@ vla_status vla_batch_create(const vla_batch_job_t *jobs, int32_t count, int32_t 
                             int32_t flags, void *stream, vla_batch **out);
 
 /* Replaces job `index`'s coefficient (Section 3.5.1 coefficients) and output
- * pointers (same mesh), stream ordered: runs enqueued on `stream` afterwards see the new job. */
+ * pointers (same mesh), stream ordered: runs enqueued on `stream` afterwards see the new job.
+ * Errors: VLA_ERR_INVALID_ARG for a NULL batch or job, an index outside
+ * [0, count), another mesh or an unknown coefficient kind; VLA_ERR_CUDA if
+ * the launch that updates the device job table fails. */
 vla_status vla_batch_set_job(vla_batch *batch, int32_t index, const vla_batch_job_t *job, void *stream);
 
 /* Enqueues one Section 3.5 assembly of every job on `stream` (one persistent launch, or
- * one graph launch with VLA_BATCH_GRAPH). */
+ * one graph launch with VLA_BATCH_GRAPH).  Errors: VLA_ERR_INVALID_ARG for a
+ * NULL batch; VLA_ERR_CUDA if the launch fails. */
 vla_status vla_batch_run(vla_batch *batch, void *stream);
 
 /* Fills *info (host struct): the batch's launch shape (no counterpart in the
- * paper). */
+ * paper).  Errors: VLA_ERR_INVALID_ARG for a NULL argument. */
 vla_status vla_batch_info(const vla_batch *batch, vla_batch_info_t *info);
 
 /* As vla_mesh_check, for the batch's own error word (no counterpart in the
@@ -418,7 +452,7 @@ vla_status vla_batch_info(const vla_batch *batch, vla_batch_info_t *info);
 vla_status vla_batch_check(vla_batch *batch, void *stream);
 
 /* Frees the batch (housekeeping; no counterpart in the paper).  No run of it
- * may still be in flight. */
+ * may still be in flight.  NULL is a no-op; cannot fail. */
 vla_status vla_batch_destroy(vla_batch *batch);
 
 /* One-shot batch of Section 3.5 assemblies: create, run once and free, all stream-ordered on `stream`
@@ -452,13 +486,18 @@ typedef struct {
  * (median), stores the winner and returns it in *best.  The default budget and
  * the occupancy limit are timed first, and another candidate wins only when it
  * is at least 3 % faster.  coords/elems as for vla_mesh_create.  Allocates
- * scratch; synchronises `stream`. */
+ * scratch; synchronises `stream`.  Errors: VLA_ERR_INVALID_ARG for a NULL
+ * best, an unknown element type or precision; the errors of vla_mesh_create
+ * for the sample mesh; VLA_ERR_OOM, VLA_ERR_CUDA. */
 vla_status vla_autotune(int32_t dim, int32_t order, int32_t precision, int64_t nn, int64_t ne, const double *coords,
                         const int32_t *elems, int32_t reps, void *stream, vla_tune_t *best);
 
 /* Autotuner state (no counterpart in the paper): reads or sets the stored
  * parameters for an element type and precision
- * (us is ignored by vla_tune_set and 0 from vla_tune_get). */
+ * (us is ignored by vla_tune_set and 0 from vla_tune_get).  Errors:
+ * VLA_ERR_INVALID_ARG for a NULL struct, an unknown element type or
+ * precision, or (set) a budget outside [0, 65536] or residency outside
+ * [0, 32]. */
 vla_status vla_tune_get(int32_t dim, int32_t order, int32_t precision, vla_tune_t *out);
 vla_status vla_tune_set(int32_t dim, int32_t order, int32_t precision, const vla_tune_t *in);
 
@@ -522,29 +561,39 @@ typedef struct {
 } vla_server_stats_t;
 
 /* Starts the scheduler and ingest threads on the current device (serving of
- * the Section 3.5 assembly; no counterpart in the paper). */
+ * the Section 3.5 assembly; no counterpart in the paper).  Errors:
+ * VLA_ERR_INVALID_ARG for a NULL argument, a budget <= 0, an unknown
+ * precision, ingest_workers outside [0, 64] or a negative limit; VLA_ERR_OOM;
+ * VLA_ERR_CUDA if the streams cannot be created. */
 vla_status vla_server_create(const vla_server_config_t *cfg, vla_server **out);
 
 /* Queues a request (a mesh and a Section 3.5.1 coefficient); *ticket
- * identifies it.  Never blocks on the GPU. */
+ * identifies it.  Never blocks on the GPU.  Errors: VLA_ERR_INVALID_ARG for a
+ * NULL argument, an unknown dim, order or coefficient kind, bad sizes or
+ * arrays, or a server that is shutting down.  A request that fails later
+ * (its mesh is invalid or can never fit the budget) reports its error
+ * through vla_server_poll. */
 vla_status vla_server_submit(vla_server *server, const vla_request_t *req, int64_t *ticket);
 
 /* Serving (no counterpart in the paper): waits up to timeout_s seconds (0: no
  * wait) for the request: VLA_PENDING
  * while it runs, VLA_OK with *res filled when done, the request's error if
- * it failed (*res filled too). */
+ * it failed (*res filled too).  Errors: VLA_ERR_INVALID_ARG for a NULL
+ * server or an unknown ticket. */
 vla_status vla_server_poll(vla_server *server, int64_t ticket, double timeout_s, vla_result_t *res);
 
 /* Frees a finished request's outputs (and its mesh, unless resident); no
- * counterpart in the paper. */
+ * counterpart in the paper.  Errors: VLA_ERR_INVALID_ARG for a NULL server,
+ * an unknown ticket or a request that has not finished. */
 vla_status vla_server_release(vla_server *server, int64_t ticket);
 
 /* Fills *stats (host struct): the server's counters (no counterpart in the
- * paper). */
+ * paper).  Errors: VLA_ERR_INVALID_ARG for a NULL argument. */
 vla_status vla_server_stats(vla_server *server, vla_server_stats_t *stats);
 
 /* Finishes admitted requests, drops queued ones, joins the threads and
- * frees everything (housekeeping; no counterpart in the paper). */
+ * frees everything (housekeeping; no counterpart in the paper).  NULL is a
+ * no-op; cannot fail. */
 vla_status vla_server_destroy(vla_server *server);
 
 #ifdef __cplusplus
