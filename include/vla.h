@@ -448,7 +448,8 @@ vla_status vla_batch_run(vla_batch *batch, void *stream);
 vla_status vla_batch_info(const vla_batch *batch, vla_batch_info_t *info);
 
 /* As vla_mesh_check, for the batch's own error word (no counterpart in the
- * paper). */
+ * paper).  Errors: VLA_ERR_TIMEOUT as described there; VLA_ERR_INVALID_ARG
+ * for a NULL batch; VLA_ERR_CUDA if the read fails. */
 vla_status vla_batch_check(vla_batch *batch, void *stream);
 
 /* Frees the batch (housekeeping; no counterpart in the paper).  No run of it
@@ -456,7 +457,8 @@ vla_status vla_batch_check(vla_batch *batch, void *stream);
 vla_status vla_batch_destroy(vla_batch *batch);
 
 /* One-shot batch of Section 3.5 assemblies: create, run once and free, all stream-ordered on `stream`
- * (no host synchronisation); the error word is not kept. */
+ * (no host synchronisation); the error word is not kept.  Errors: those of
+ * vla_batch_create (flags 0), and VLA_ERR_CUDA if the launch fails. */
 vla_status vla_batch_assemble(const vla_batch_job_t *jobs, int32_t count, int32_t precision, int64_t *n_singular,
                               void *stream);
 

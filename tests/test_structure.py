@@ -1,8 +1,8 @@
 """Structural rules of the repository, checked on the source text.
 
 * Every entry point declared in include/vla.h is documented by a comment that
-  cites the paper passage defining its operation, or states that the paper
-  has no counterpart.
+  cites the paper passage defining its operation (or states that the paper
+  has no counterpart) and states its error behaviour.
 * The oracle and the library share no code: the package and its CUDA sources
   never import, include or load anything under oracle/, and the oracle never
   imports the package.
@@ -27,12 +27,17 @@ def test_every_entry_point_cites_its_passage():
              re.finditer(r"^(?:vla_status|int32_t|const char \*)\s*(vla_\w+)\(", s, re.M)]
     assert len(decls) > 40
     cite = re.compile(r"Section \d|no counterpart in the paper|paper has no counterpart")
-    uncited = []
+    errors = re.compile(r"VLA_ERR_|errors|cannot fail", re.I)
+    uncited, silent = [], []
     for pos, name in decls:
         before = [text for end, text in comments if end <= pos]
-        if not before or not cite.search(before[-1]):
+        doc = before[-1] if before else ""
+        if not cite.search(doc):
             uncited.append(name)
+        if name not in ("vla_last_error",) and not errors.search(doc):
+            silent.append(name)
     assert not uncited, uncited
+    assert not silent, silent          # every entry point states its error behaviour
 
 
 def test_oracle_and_library_share_no_code():
