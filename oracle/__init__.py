@@ -100,7 +100,8 @@ def _i32(x):
 # --------------------------------------------------------------------------
 
 def amtam(A, B):
-    """C_k = A_k^T B_k.  A: (N, m, p) = N pages p x m; B: (N, n, p); C: (N, n, m)."""
+    """C_k = A_k^T B_k.  A: (N, m, p) = N pages p x m; B: (N, n, p); C: (N, n, m).  Follows amtam of Section
+    2.4, read as A^T B."""
     A, B = _f64(A), _f64(B)
     N, m, p = A.shape
     n = B.shape[1]
@@ -110,7 +111,7 @@ def amtam(A, B):
 
 
 def astam(s, A):
-    """C_k = s_k A_k."""
+    """C_k = s_k A_k.  Follows astam of Sections 2.2 and 2.4."""
     s, A = _f64(s), _f64(A)
     N, n, m = A.shape
     out = np.empty_like(A)
@@ -119,7 +120,7 @@ def astam(s, A):
 
 
 def avtam(v, A):
-    """y_k = v_k^T A_k.  v: (N, p); A: (N, n, p) = pages p x n; y: (N, n)."""
+    """y_k = v_k^T A_k.  v: (N, p); A: (N, n, p) = pages p x n; y: (N, n).  Follows avtam of Section 2.4."""
     v, A = _f64(v), _f64(A)
     N, n, p = A.shape
     y = np.empty((N, n))
@@ -187,6 +188,7 @@ def svamt(s, A):
 
 
 def amdet(A):
+    """Signed page determinants (N,) of (N, n, n) pages.  Follows amdet of Sections 2.3 and 3.2."""
     A = _f64(A)
     N, n, _ = A.shape
     out = np.empty(N)
@@ -195,7 +197,7 @@ def amdet(A):
 
 
 def aminv(A):
-    """Returns (Ainv, det, n_singular)."""
+    """Returns (Ainv, det, n_singular).  Follows aminv of Section 2.3."""
     A = _f64(A)
     N, n, _ = A.shape
     inv = np.empty_like(A)
@@ -209,7 +211,8 @@ def aminv(A):
 # --------------------------------------------------------------------------
 
 def vectors(dim, elems, coords):
-    """vectors3D pages: (ne, dim, dim) with [k, j, :] = x_{e_k[j]} - x_{e_k[dim]}."""
+    """vectors3D pages: (ne, dim, dim) with [k, j, :] = x_{e_k[j]} - x_{e_k[dim]}.  Follows vectors3D of
+    Sections 3.1 and 3.2."""
     elems, coords = _i32(elems), _f64(coords)
     ne, nlb = elems.shape
     V = np.empty((ne, dim, dim))
@@ -218,7 +221,7 @@ def vectors(dim, elems, coords):
 
 
 def volumes(dim, elems, coords):
-    """Returns (vol = |det|/dim!, signed det)."""
+    """Returns (vol = |det|/dim!, signed det).  Follows the volume script of Section 3.2."""
     elems, coords = _i32(elems), _f64(coords)
     ne, nlb = elems.shape
     vol, det = np.empty(ne), np.empty(ne)
@@ -227,7 +230,8 @@ def volumes(dim, elems, coords):
 
 
 def simplex_normals(dim, elems, coords):
-    """Unnormalised facet normals (V^{-T} normalsRef): (ne, dim+1, dim); [k, j] is column j."""
+    """Unnormalised facet normals (V^{-T} normalsRef): (ne, dim+1, dim); [k, j] is column j.  Follows
+    normals3D of Section 3.2, with the normal transform of Section 2.3."""
     elems, coords = _i32(elems), _f64(coords)
     ne, nlb = elems.shape
     out = np.empty((ne, dim + 1, dim))
@@ -237,7 +241,8 @@ def simplex_normals(dim, elems, coords):
 
 def element_pages(dim, order, elems, coords, ca=1.0, cb=0.0, ckind=0):
     """Returns (K3D, M3D, vol, coef); pages as (ne, nlb, nlb) with [k, q, p] = P_k(p, q).
-    Coefficient at the element's vertex centroid: ckind 0: a + b|x|^2; 1: a exp(b sum x)."""
+    Coefficient at the element's vertex centroid: ckind 0: a + b|x|^2; 1: a exp(b sum x).
+    Follows the stiffness and mass listings of Section 3.5."""
     elems, coords = _i32(elems), _f64(coords)
     ne, nlb = elems.shape
     K = np.empty((ne, nlb, nlb))
@@ -248,7 +253,8 @@ def element_pages(dim, order, elems, coords, ca=1.0, cb=0.0, ckind=0):
 
 
 def csr_pattern(nn, elems):
-    """Sorted-unique (row, col) pattern of all element pairs: (row_ptr, col_idx)."""
+    """Sorted-unique (row, col) pattern of all element pairs: (row_ptr, col_idx).  Follows the sparse assembly
+    of Section 3.5."""
     elems = _i32(elems)
     ne, nlb = elems.shape
     lib = _load()
@@ -262,6 +268,8 @@ def csr_pattern(nn, elems):
 
 
 def csr_scatter(elems, pages, row_ptr, col_idx):
+    """CSR values of element pages (ne, nlb, nlb) summed into the pattern (row_ptr,
+    col_idx).  Follows the sparse assembly of Section 3.5."""
     elems = _i32(elems)
     ne, nlb = elems.shape
     vals = np.zeros(len(col_idx))
@@ -274,7 +282,7 @@ def csr_scatter(elems, pages, row_ptr, col_idx):
 
 def assemble(dim, order, nn, elems, coords, ca=1.0, cb=0.0, pattern=None, want_pages=False, ckind=0):
     """K and M in CSR (values FP64) plus volumes.  Returns a dict with
-    row_ptr, col_idx, K, M, vol and (optionally) K3D, M3D."""
+    row_ptr, col_idx, K, M, vol and (optionally) K3D, M3D.  Follows Section 3.5."""
     elems, coords = _i32(elems), _f64(coords)
     ne, nlb = elems.shape
     rp, ci = pattern if pattern is not None else csr_pattern(nn, elems)
@@ -300,7 +308,7 @@ def assemble(dim, order, nn, elems, coords, ca=1.0, cb=0.0, pattern=None, want_p
 
 def boundary(dim, nn, elems, coords, faces):
     """Outward unit normals (nfb, dim) and facet measures (nfb,).  Returns
-    (normals, areas, n_missing_owner)."""
+    (normals, areas, n_missing_owner).  Follows the boundary normals and areas of Sections 3.2 and 3.4."""
     elems, coords, faces = _i32(elems), _f64(coords), _i32(faces)
     ne, nlb = elems.shape
     nfb = faces.shape[0]
@@ -312,7 +320,7 @@ def boundary(dim, nn, elems, coords, faces):
 
 
 def count_facets(dim, elems):
-    """(number of distinct facets, number of boundary facets)."""
+    """(number of distinct facets, number of boundary facets).  Follows the face counts of Section 3.2."""
     elems = _i32(elems)
     ne, nlb = elems.shape
     a, b = _i64(0), _i64(0)
@@ -335,7 +343,7 @@ def to_dense(nn, row_ptr, col_idx, vals):
 # --------------------------------------------------------------------------
 
 def quad_rule(sdim, gqo):
-    """(ip (nip, sdim+1) barycentric points, w (nip,) weights summing to 1)."""
+    """(ip (nip, sdim+1) barycentric points, w (nip,) weights summing to 1).  Follows Gauss_points of Section 3.4."""
     ip = np.zeros((8, sdim + 1))
     w = np.zeros(8)
     nip = _load().orc_quad_rule(sdim, gqo, ip, w)
@@ -345,7 +353,7 @@ def quad_rule(sdim, gqo):
 
 
 def quad_points(dim, cells, coords, ip):
-    """X (n, nip, dim): quadrature points of the simplices cells (n, >= nvert)."""
+    """X (n, nip, dim): quadrature points of the simplices cells (n, >= nvert).  Follows X_ip of Section 3.4."""
     cells, coords, ip = _i32(cells), _f64(coords), _f64(ip)
     n, stride = cells.shape
     nip, nvert = ip.shape
@@ -367,7 +375,7 @@ def gi(fip, w, sizes, normals=None):
 
 def rhs(dim, order, nn, elems, coords, ip, w, fip):
     """Load vector b (nn,) and element contributions b2D (ne, nlb) for f given at
-    the rule's points (fip (ne, nip))."""
+    the rule's points (fip (ne, nip)).  Follows rhs_vectorP1 of Section 3.5."""
     elems, coords, ip, w, fip = _i32(elems), _f64(coords), _f64(ip), _f64(w), _f64(fip)
     ne, nlb = elems.shape
     b = np.empty(nn)
@@ -377,7 +385,8 @@ def rhs(dim, order, nn, elems, coords, ip, w, fip):
 
 
 def energies(elems, u, K3D, M3D, b2D):
-    """Local energies (ne, 3): u_k^T K_k u_k / 2, u_k^T M_k u_k / 2, -b2D_k^T u_k."""
+    """Local energies (ne, 3): u_k^T K_k u_k / 2, u_k^T M_k u_k / 2, -b2D_k^T u_k.  Follows the local energies
+    of Section 3.5."""
     elems, u, K3D, M3D, b2D = _i32(elems), _f64(u), _f64(K3D), _f64(M3D), _f64(b2D)
     ne, nlb = elems.shape
     J = np.empty((max(ne, 1), 3))
@@ -386,7 +395,7 @@ def energies(elems, u, K3D, M3D, b2D):
 
 
 def avtamav(v, A, w):
-    """out_k = v_k^T A_k w_k; v, w (N, n); A (N, n, n) pages (N, cols, rows)."""
+    """out_k = v_k^T A_k w_k; v, w (N, n); A (N, n, n) pages (N, cols, rows).  Follows avtamav of Section 2.4."""
     v, A, w = _f64(v), _f64(A), _f64(w)
     N, n = v.shape
     out = np.empty(max(N, 1))
@@ -397,7 +406,7 @@ def avtamav(v, A, w):
 def facets(dim, elems):
     """(faces (nf, dim), owner (nf, 2) = (element, local facet), neighbor (nf,),
     n_boundary): every distinct facet once, ordered by first element and local
-    facet index."""
+    facet index.  Follows the normals of all faces, Section 3.2."""
     elems = _i32(elems)
     ne, nlb = elems.shape
     L = _load()
