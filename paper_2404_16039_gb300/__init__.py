@@ -23,7 +23,8 @@ __all__ = [
     "VlaError", "lib", "version", "amtam", "astam", "avtam", "amdet", "aminv", "amt", "avtav", "amsm", "amsv",
     "smamt", "svamt", "Mesh", "element_pages_static",
     "Batch", "batch_assemble", "autotune", "tune_get", "tune_set", "Server", "PENDING", "quad_rule", "gi",
-    "avtamav", "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP", "COEFF_POLY_IP", "COEFF_EXP_IP",
+    "avtamav", "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP",
+    "COEFF_POLY_IP", "COEFF_EXP_IP",
 ]
 
 F32, F64 = 0, 1
@@ -268,7 +269,7 @@ def _new_vec(N, n, layout, like):
 # ---------------------------------------------------------------------------
 
 def amtam(A, B, out=None, layout=LAYOUT_PAGE, stream=None):
-    """C_k = A_k^T B_k (amtam).  A: p x m pages, B: p x n pages -> m x n pages."""
+    """C_k = A_k^T B_k (amtam).  A: p x m pages, B: p x n pages -> m x n pages.  Section 2.4."""
     _req(A), _req(B)
     _same_device(A, B)
     N, p, m = _page_dims(A, layout)
@@ -281,7 +282,7 @@ def amtam(A, B, out=None, layout=LAYOUT_PAGE, stream=None):
 
 
 def astam(s, A, out=None, layout=LAYOUT_PAGE, stream=None):
-    """C_k = s_k A_k (astam)."""
+    """C_k = s_k A_k (astam).  Sections 2.2, 2.4."""
     _req(s, A.dtype), _req(A)
     _same_device(A, s)
     N, m, n = _page_dims(A, layout)
@@ -293,7 +294,7 @@ def astam(s, A, out=None, layout=LAYOUT_PAGE, stream=None):
 
 
 def avtam(v, A, out=None, layout=LAYOUT_PAGE, stream=None):
-    """y_k = v_k^T A_k (avtam).  v: (N, p) page layout or (p, N) SoA."""
+    """y_k = v_k^T A_k (avtam).  v: (N, p) page layout or (p, N) SoA.  Section 2.4."""
     _req(v, A.dtype), _req(A)
     _same_device(A, v)
     N, p, n = _page_dims(A, layout)
@@ -305,7 +306,7 @@ def avtam(v, A, out=None, layout=LAYOUT_PAGE, stream=None):
 
 
 def amdet(A, out=None, layout=LAYOUT_PAGE, stream=None):
-    """Signed page determinants (amdet)."""
+    """Signed page determinants (amdet).  Sections 2.3, 3.2."""
     _req(A)
     N, n, n2 = _page_dims(A, layout)
     if n != n2:
@@ -316,7 +317,7 @@ def amdet(A, out=None, layout=LAYOUT_PAGE, stream=None):
 
 
 def aminv(A, out=None, det=None, want_det=True, count_singular=True, layout=LAYOUT_PAGE, stream=None):
-    """Page inverses (aminv).  Returns (Ainv, det or None, n_singular device tensor or None)."""
+    """Page inverses (aminv).  Returns (Ainv, det or None, n_singular device tensor or None).  Section 2.3."""
     _req(A)
     N, n, n2 = _page_dims(A, layout)
     if n != n2:
@@ -333,7 +334,7 @@ def aminv(A, out=None, det=None, want_det=True, count_singular=True, layout=LAYO
 
 
 def amt(A, out=None, layout=LAYOUT_PAGE, stream=None):
-    """C_k = A_k^T (amt).  A: m x n pages -> n x m pages."""
+    """C_k = A_k^T (amt).  A: m x n pages -> n x m pages.  Section 2.4."""
     _req(A)
     N, m, n = _page_dims(A, layout)
     out = _new_pages(N, n, m, layout, A) if out is None else _buf(out, N * m * n, A.dtype, A.device, "out")
@@ -342,7 +343,7 @@ def amt(A, out=None, layout=LAYOUT_PAGE, stream=None):
 
 
 def avtav(a, b, out=None, layout=LAYOUT_PAGE, stream=None):
-    """out_k = a_k^T b_k (avtav).  a, b: (N, n) page layout or (n, N) SoA."""
+    """out_k = a_k^T b_k (avtav).  a, b: (N, n) page layout or (n, N) SoA.  Section 2.4."""
     _req(a), _req(b, a.dtype)
     _same_device(a, b)
     N, n = a.shape if layout == LAYOUT_PAGE else a.shape[::-1]
@@ -355,7 +356,7 @@ def avtav(a, b, out=None, layout=LAYOUT_PAGE, stream=None):
 
 def amsm(A, S, out=None, layout=LAYOUT_PAGE, stream=None):
     """C_k = A_k S (amsm).  A: m x p pages; S: one p x n matrix as a (n, p)
-    tensor (its columns, column-major like a page) -> m x n pages."""
+    tensor (its columns, column-major like a page) -> m x n pages.  Section 2.4."""
     _req(A), _req(S, A.dtype)
     _same_device(A, S)
     N, m, p = _page_dims(A, layout)
@@ -368,7 +369,7 @@ def amsm(A, S, out=None, layout=LAYOUT_PAGE, stream=None):
 
 
 def amsv(A, s, out=None, layout=LAYOUT_PAGE, stream=None):
-    """y_k = A_k s (amsv).  A: m x n pages; s: (n,) -> (N, m) page layout or (m, N) SoA."""
+    """y_k = A_k s (amsv).  A: m x n pages; s: (n,) -> (N, m) page layout or (m, N) SoA.  Section 2.4."""
     _req(A), _req(s, A.dtype)
     _same_device(A, s)
     N, m, n = _page_dims(A, layout)
@@ -381,7 +382,7 @@ def amsv(A, s, out=None, layout=LAYOUT_PAGE, stream=None):
 
 def smamt(S, A, out=None, layout=LAYOUT_PAGE, stream=None):
     """C_k = S A_k^T (smamt).  S: one m x p matrix as a (p, m) tensor; A: n x p
-    pages -> m x n pages."""
+    pages -> m x n pages.  Section 2.4."""
     _req(A), _req(S, A.dtype)
     _same_device(A, S)
     N, n, p = _page_dims(A, layout)
@@ -395,7 +396,7 @@ def smamt(S, A, out=None, layout=LAYOUT_PAGE, stream=None):
 
 def svamt(s, A, out=None, layout=LAYOUT_PAGE, stream=None):
     """y_k = s^T A_k^T (svamt), a 1 x m page per k.  s: (n,); A: m x n pages ->
-    (N, m) page layout or (m, N) SoA."""
+    (N, m) page layout or (m, N) SoA.  Section 2.4."""
     _req(A), _req(s, A.dtype)
     _same_device(A, s)
     N, m, n = _page_dims(A, layout)
@@ -457,7 +458,7 @@ class Mesh:
     def assemble(self, ca=1.0, cb=0.0, kind=COEFF_POLY, precision=PREC_MIXED, K=None, M=None, vol=None,
                  want_K=True, want_M=True, want_vol=True, pages=False, count_singular=False, stream=None):
         """K and M values in CSR order (FP64), element volumes and optionally the
-        element pages (ne, nlb, nlb).  Returns a dict of tensors."""
+        element pages (ne, nlb, nlb).  Returns a dict of tensors.  Section 3.5."""
         dev = self.device
         f64 = torch.float64
         if want_K:
@@ -480,7 +481,7 @@ class Mesh:
         return out
 
     def boundary(self, precision=PREC_MIXED, normals=None, areas=None, stream=None):
-        """Outward unit normals (nfb, dim) and facet measures (nfb,)."""
+        """Outward unit normals (nfb, dim) and facet measures (nfb,).  Sections 3.2, 3.4."""
         dev = self.device
         if normals is None:
             normals = torch.empty((max(self.nfb, 1), self.dim), dtype=torch.float64, device=dev)[: self.nfb]
@@ -495,7 +496,7 @@ class Mesh:
 
     def facets(self, stream=None):
         """(faces (nf, dim), owner (nf, 2), neighbor (nf,), n_boundary): every
-        facet once, ordered by owning element and local facet (vla_mesh_facets)."""
+        facet once, ordered by owning element and local facet (vla_mesh_facets).  Section 3.2."""
         nf, nb = C.c_int64(), C.c_int64()
         _check(lib().vla_mesh_facets(self._h, None, None, None, C.byref(nf), C.byref(nb), _stream(stream)))
         n = nf.value
@@ -509,7 +510,7 @@ class Mesh:
 
     def quad_points(self, gqo, facets=False, stream=None):
         """Quadrature points (n, nip, dim) of the elements (or boundary facets)
-        for the degree-gqo rule (vla_quad_points)."""
+        for the degree-gqo rule (vla_quad_points).  Section 3.4."""
         nip = quad_rule(self.dim - 1 if facets else self.dim, gqo)[1].shape[0]
         n = self.nfb if facets else self.ne
         X = torch.empty((max(n, 1), nip, self.dim), dtype=torch.float64, device=self.device)[:n]
@@ -518,7 +519,7 @@ class Mesh:
 
     def rhs(self, gqo, fip, b=None, b2D=None, want_b2D=True, stream=None):
         """Load vector b (nn,) and element loads b2D (ne, nlb) for f at the
-        degree-gqo points (fip (ne, nip)) (vla_rhs)."""
+        degree-gqo points (fip (ne, nip)) (vla_rhs).  Section 3.5."""
         dev, f64 = self.device, torch.float64
         nip = quad_rule(self.dim, gqo)[1].shape[0]
         _buf(fip, self.ne * nip, f64, dev, "fip")
@@ -530,7 +531,7 @@ class Mesh:
         return b, (b2D if want_b2D else None)
 
     def energies(self, u, K3D=None, M3D=None, b2D=None, local=True, stream=None):
-        """Local energies (ne, 3) and their sums (3,) (vla_energies)."""
+        """Local energies (ne, 3) and their sums (3,) (vla_energies).  Section 3.5."""
         dev, f64 = self.device, torch.float64
         _buf(u, self.nn, f64, dev, "u")
         for name, t, n in (("K3D", K3D, self.ne * self.nlb * self.nlb), ("M3D", M3D, self.ne * self.nlb * self.nlb),
@@ -557,7 +558,7 @@ class Mesh:
                 "M3D": torch.empty((self.ne, self.nlb, self.nlb), dtype=f64, device=dev) if pages else None}
 
     def simplex_normals(self, stream=None):
-        """Unnormalised facet normals of every element: (ne, dim+1, dim), [k, j] = column j."""
+        """Unnormalised facet normals of every element: (ne, dim+1, dim), [k, j] = column j.  Section 3.2."""
         out = torch.empty((self.ne, self.dim + 1, self.dim), dtype=torch.float64, device=self.device)
         _check(lib().vla_simplex_normals(self._h, _p(out), _stream(stream)))
         return out
@@ -571,7 +572,7 @@ def element_pages_static(coords, elems, order=1, ca=1.0, cb=0.0, kind=COEFF_POLY
     nodes).  The output tensors are allocated here by PyTorch; callers that
     cannot allocate pass the C entry point their own buffers.  The element
     indices must lie in [0, nn): this entry point reads them as given (use
-    Mesh, which validates them, for untrusted meshes)."""
+    Mesh, which validates them, for untrusted meshes).  Section 3.5."""
     _req(coords, torch.float64), _req(elems, torch.int32)
     _same_device(coords, elems)
     _mesh_arrays(coords, elems, None, order)
@@ -748,7 +749,8 @@ class Server:
             raise ValueError("coords must be (nn, dim) with dim 2 or 3")
         nn, dim = c.shape
         if order not in (1, 2) or len(e.shape) != 2 or e.shape[1] != _nlb(dim, order):
-            raise ValueError(f"elems must be (ne, {_nlb(dim, order) if order in (1, 2) else 'nlb'}) for order {order}")
+            nlb = _nlb(dim, order) if order in (1, 2) else "nlb"
+            raise ValueError(f"elems must be (ne, {nlb}) for order {order}")
         if f is not None and (len(f.shape) != 2 or f.shape[1] != dim):
             raise ValueError(f"faces must be (nfb, {dim})")
         ne = e.shape[0]
@@ -814,7 +816,7 @@ class Server:
 # ---------------------------------------------------------------------------
 
 def quad_rule(sdim, gqo):
-    """(ip (nip, sdim+1), w (nip,)) of the degree-gqo rule on an sdim-simplex."""
+    """(ip (nip, sdim+1), w (nip,)) of the degree-gqo rule on an sdim-simplex.  Section 3.4."""
     import numpy as np
     n = C.c_int32()
     ip = (C.c_double * 32)()
@@ -842,7 +844,7 @@ def gi(fip, w, sizes, normals=None, stream=None):
 
 
 def avtamav(v, A, w, out=None, layout=LAYOUT_PAGE, stream=None):
-    """out_k = v_k^T A_k w_k.  Page layout: v, w (N, n); A (N, n, n) (N, cols, rows)."""
+    """out_k = v_k^T A_k w_k.  Page layout: v, w (N, n); A (N, n, n) (N, cols, rows).  Section 2.4."""
     _req(v), _req(A, v.dtype), _req(w, v.dtype)
     _same_device(v, A, w)
     if layout == LAYOUT_PAGE:
