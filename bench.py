@@ -17,7 +17,14 @@ resident mesh.
           the algorithmic bytes per element of the method (elements 16 B,
           coordinates 24 nn/ne B, element-to-nonzero map 64 B, K and M values
           16 nnz/ne B, volume 8 B).
-  cpu_baseline  the FP64 oracle (plain C, one thread) on the same mesh.
+  cpu_baseline  the FP64 oracle (plain C) on the same mesh, one host thread
+          and all host cores (core count read at run time).
+  errors  every output (K, M, volumes, normals, areas) against the FP64
+          oracle of the cpu_baseline leg.
+  latency p50/p99 of the step over --latency-reps calls: L2 flushed, warm,
+          and host call plus synchronize.
+  --precision fp64: the plain FP64 form, its roofline against the FP64 pipe
+          (cuBLAS DGEMM measured in the same run) beside HBM.
 
 Other workloads (--workload): pages (page primitives at N = 1e8), batch (256
 meshes of all four element types in one persistent launch), serve (a Poisson
@@ -163,22 +170,107 @@ def _alg_bytes_per_el(ne, nn, nnz):
     return 16.0 + 24.0 * nn / ne + 64.0 + 16.0 * nnz / ne + 8.0
 
 
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(m, seconds=10.0):
-    """The oracle as it stands (single thread) on the same mesh; pattern built once."""
+    """The oracle as it stands on the same mesh, CSR pattern built once: one
+    host thread (orc_assemble), then every host core (the same pinned element
+    and scatter steps over element ranges and row blocks, bit-identical
+    results).  Also returns the oracle's outputs of the first pass, which the
+    error report compares against."""
     import oracle
     pat = oracle.csr_pattern(m.nn, m.elems)
+    ref = None
     t0 = time.perf_counter()
     reps = 0
     while True:
-        oracle.assemble(3, 1, m.nn, m.elems, m.coords, 1.0, 1.0, pattern=pat)
-        oracle.boundary(3, m.nn, m.elems, m.coords, m.faces)
+        r = oracle.assemble(3, 1, m.nn, m.elems, m.coords, 1.0, 1.0, pattern=pat)
+        b = oracle.boundary(3, m.nn, m.elems, m.coords, m.faces)
+        if ref is None:
+            ref = dict(r, normals=b[0], areas=b[1])
         reps += 1
         if time.perf_counter() - t0 >= seconds:
             break
-    dt = (time.perf_counter() - t0) / reps
-    return {"value": m.ne / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+    dt1 = (time.perf_counter() - t0) / reps
+    cores = _host_cores()
+    t0 = time.perf_counter()
+    reps_n = 0
+    while True:
+        oracle.assemble_threads(3, 1, m.nn, m.elems, m.coords, 1.0, 1.0, pattern=pat, nthreads=cores)
+        oracle.boundary(3, m.nn, m.elems, m.coords, m.faces)
+        reps_n += 1
+        if time.perf_counter() - t0 >= seconds / 2:
+            break
+    dtn = (time.perf_counter() - t0) / reps_n
+    base = {"value": m.ne / dt1, "unit": "elements/s", "cores": 1, "kind": "oracle",
             "sample": f"{reps} full passes of the oracle assembly (K, M, volumes, CSR scatter) plus boundary "
-                      f"facets on the same {m.ne}-tet mesh, CSR pattern precomputed, 1 host thread"}
+                      f"facets on the same {m.ne}-tet mesh, CSR pattern precomputed, 1 host thread",
+            "all_cores": {"value": m.ne / dtn, "unit": "elements/s", "cores": cores,
+                          "sample": f"{reps_n} passes, element pages over element ranges and the CSR scatter over "
+                                    f"row blocks on {cores} host threads (same results bit for bit), boundary "
+                                    f"facets on one"}}
+    return base, ref
+
+
+def _errors(ref, got):
+    """Error of every output against the FP64 oracle: K and M entrywise, each
+    entry scaled by max(|ref|, max over its row of |ref|), and by relative
+    Frobenius norm; volumes and areas relative per entry; unit normals
+    absolute per component."""
+    rp = ref["row_ptr"]
+    rows = np.repeat(np.arange(len(rp) - 1), np.diff(rp))
+    out = {}
+    for k in ("K", "M"):
+        r, g = ref[k], got[k]
+        rowmax = np.zeros(len(rp) - 1)
+        np.maximum.at(rowmax, rows, np.abs(r))
+        scale = np.maximum(np.abs(r), rowmax[rows])
+        out[k] = {"max_entry_rel_rowscale": float((np.abs(g - r) / scale).max()),
+                  "rel_fro": float(np.linalg.norm(g - r) / np.linalg.norm(r))}
+    for k in ("vol", "areas"):
+        r, g = ref[k], got[k]
+        out[k] = {"max_rel": float((np.abs(g - r) / np.abs(r)).max()),
+                  "rel_fro": float(np.linalg.norm(g - r) / np.linalg.norm(r))}
+    r, g = ref["normals"].reshape(-1), got["normals"].reshape(-1)
+    out["normals"] = {"max_abs": float(np.abs(g - r).max()), "rel_fro": float(np.linalg.norm(g - r) /
+                                                                             np.linalg.norm(r))}
+    return out
+
+
+def _fp64_peak(dev):
+    """FP64 throughput of this GPU measured with cuBLAS DGEMM (torch.matmul,
+    4096^3, best of 5, CUDA events), GFLOP/s."""
+    import torch
+    n = 4096
+    a = torch.randn((n, n), dtype=torch.float64, device=dev)
+    b = torch.randn((n, n), dtype=torch.float64, device=dev)
+    c = a @ b
+    best = 1e30
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b, c
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e9
+
+
+# FP64 flops one P1 tetrahedron needs in the FP64 form (add, sub, mul, div 1; FMA 2): edge vectors 9,
+# centroid 12, cofactors 27, det 5, coefficient 7, scale 2, six stiffness dot products and scalings 36,
+# zero-row-sum column and diagonal 8, mass scale 2, volume 1, and 20 CSR additions (10 entries of K and M).
+MIXED_LABEL = ("mixed: f32 element matrices; det and inverse in plain f32 where |det| >= perm(|V|)/4 (error <= "
+               "11u perm), from error-free float-pair edge vectors with a compensated det below; compensated "
+               "float-float CSR sums; f64 outputs")
+
+FP64_FLOPS_PER_TET = 129
+FP64_FLOPS_PER_TET_EVAL = 108   # the per-evaluation part, repeated by every row tile an element touches
 
 
 def run_reference(args):
@@ -189,10 +281,11 @@ def run_reference(args):
     m = meshgen.kuhn_cube(args.n, jitter=0.1, seed=0)
     import oracle
     pat = oracle.csr_pattern(m.nn, m.elems)
+    cores = _host_cores()
     per_step = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.assemble(3, 1, m.nn, m.elems, m.coords, 1.0, 1.0, pattern=pat)
+        oracle.assemble_threads(3, 1, m.nn, m.elems, m.coords, 1.0, 1.0, pattern=pat, nthreads=cores)
         oracle.boundary(3, m.nn, m.elems, m.coords, m.faces)
         if i >= args.warmup:
             per_step.append(time.perf_counter() - t0)
@@ -205,8 +298,10 @@ def run_reference(args):
                            l2=f"host run, no flush: each step reads and writes over "
                               f"{int(_alg_bytes_per_el(m.ne, m.nn, len(pat[1])) * m.ne / 1e6)} MB of mesh "
                               f"arrays and CSR values, more than the host caches hold"),
-            "cpu_baseline": {"value": val, "unit": "elements/s", "cores": 1, "kind": "oracle",
-                             "sample": f"each step one full oracle pass over the {m.ne}-tet mesh, 1 host thread"},
+            "cpu_baseline": {"value": val, "unit": "elements/s", "cores": cores, "kind": "oracle",
+                             "sample": f"each step one full oracle pass over the {m.ne}-tet mesh: element pages "
+                                       f"over element ranges and the CSR scatter over row blocks on {cores} host "
+                                       f"threads, boundary facets on one"},
             "e2e": {"value": val, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -414,7 +509,7 @@ def run_batch(args):
                                    f"{args.batch_hi:g}] rounded to the structured n, interior jitter 0.1h, "
                                    f"c(x)=1+|x|^2",
                        "meshes": len(gms), "elements": ne, "nnz": sum(g.nnz for g in gms), "by_kind": kinds,
-                       "precision": "mixed (f32 element matrices, float-float det and CSR sums, f64 outputs)",
+                       "precision": MIXED_LABEL,
                        "launch": ("one persistent kernel per element type" if bm.split else
                                   "one persistent kernel over the row tiles of every mesh") +
                                  ", captured in one CUDA graph" + ("; form chosen by timing both at creation"
@@ -835,6 +930,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="p1tet", choices=["p1tet", "pages", "batch", "serve", "next", "small"])
     ap.add_argument("--small-reps", type=int, default=1000)
+    ap.add_argument("--latency-reps", type=int, default=1000)
     ap.add_argument("--pages-n", default="100000000")
     ap.add_argument("--batch-count", type=int, default=256)
     ap.add_argument("--batch-lo", type=float, default=1e3)
@@ -916,6 +1012,37 @@ def main():
     asm = sum(asm_ms) / len(asm_ms)
     value = _job_value(ws, gm.ne, ms)
 
+    # latency of the hot step over --latency-reps calls: device time with the L2
+    # flushed before each (cold) and back to back (warm), and the host time of
+    # the call plus a synchronize
+    def _lat(flushed):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.latency_reps)]
+        for a, b in evs:
+            if flushed:
+                flush.zero_()
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    def _pct(x):
+        return {"p50_ms": float(np.percentile(x, 50)), "p99_ms": float(np.percentile(x, 99)), "reps": len(x)}
+
+    lat_cold = _lat(True)
+    lat_warm = _lat(False)
+    host = []
+    for _ in range(args.latency_reps):
+        t0 = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        host.append((time.perf_counter() - t0) * 1e3)
+    latency = {"cold_l2": _pct(lat_cold), "warm_l2": _pct(lat_warm), "host_call_and_sync": _pct(host),
+               "what": "one step (assemble + boundary) on the resident mesh; cold = 512 MiB L2 flush before each"}
+    got = {"K": K.cpu().numpy(), "M": M.cpu().numpy(), "vol": vol.cpu().numpy(), "normals": nrm.cpu().numpy(),
+           "areas": ar.cpu().numpy()}
+
     # end to end through the public API with pinned host buffers
     hc = torch.from_numpy(m.coords).pin_memory()
     he = torch.from_numpy(m.elems).pin_memory()
@@ -972,17 +1099,34 @@ def main():
             "frac": achieved / peaks["hbm_gbs"], "peak_source": src,
             "traffic": _traffic_from_profile(khash) if prec == vla.PREC_MIXED else None,
             "alg_bytes_per_element": bpe, "kernel_ms": asm, "kernel_source_hash": khash}
+    if prec == vla.PREC_FP64:
+        # the plain FP64 form against the FP64 pipe: min(HBM, FP64) and which one binds
+        fp64 = _fp64_peak(dev)
+        recompute = gm.tile_elems / gm.ne
+        fl = FP64_FLOPS_PER_TET * gm.ne / (asm * 1e-3) / 1e9
+        fl_exec = (FP64_FLOPS_PER_TET_EVAL * recompute + FP64_FLOPS_PER_TET - FP64_FLOPS_PER_TET_EVAL) * gm.ne \
+            / (asm * 1e-3) / 1e9
+        hbm_roof = dict(roof)
+        roof = {"bound": "fp64", "kernel": roof["kernel"], "achieved": fl, "peak": fp64, "unit": "GFLOP/s",
+                "frac": fl / fp64, "peak_source": "measured in this run: cuBLAS DGEMM 4096^3 (torch.matmul, "
+                                                   "best of 5)",
+                "flops_per_element": FP64_FLOPS_PER_TET,
+                "executed_gflops": fl_exec, "executed_frac": fl_exec / fp64, "element_recompute": recompute,
+                "traffic": None, "kernel_ms": asm, "kernel_source_hash": khash, "hbm": hbm_roof}
+        if hbm_roof["frac"] > roof["executed_frac"]:
+            roof["bound"] = "hbm"
 
     line = {"metric": "elements/sec for P1 tet K+M to CSR", "value": value, "unit": "elements/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == vla.PREC_MIXED else "f64", "data": "synthetic",
-            "config": _config(m, "mixed: f32 element matrices, float-float det and CSR sums, f64 outputs"
-                              if prec else "fp64"),
+            "config": _config(m, MIXED_LABEL if prec else "fp64"),
             "e2e": e2e, "roofline": roof, "gpu_launches": 2 * args.steps, "clocks": clocks,
-            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99))}
+            "p50_ms": latency["cold_l2"]["p50_ms"], "p99_ms": latency["cold_l2"]["p99_ms"], "latency": latency}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(m, args.cpu_seconds)
+        base, ref = cpu_baseline(m, args.cpu_seconds)
+        line["cpu_baseline"] = base
+        line["errors"] = dict(_errors(ref, got), against="the FP64 oracle on the same mesh and coefficient")
     if rank == 0:
         print(json.dumps(line), flush=True)
     gm.close()

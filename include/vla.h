@@ -224,10 +224,16 @@ vla_status vla_mesh_csr(const vla_mesh *mesh, int32_t *row_ptr, int32_t *col_idx
  *   K_pages, M_pages: the element matrices K3D, M3D as nlb x nlb x ne
  *   column-major pages (second output of the Section 3.5 listings).
  * precision: VLA_PREC_FP64 computes everything in FP64.  VLA_PREC_MIXED
- *   forms element matrices in FP32 from coordinates stored as float pairs;
- *   the edge vectors are exact to float rounding, the 2x2 cofactors use
- *   Kahan's FMA determinant, det uses a compensated dot product, and every CSR
- *   value is a compensated (float-float) sum converted to FP64 once.
+ *   forms element matrices in FP32 from coordinates stored as float pairs.
+ *   The geometry of an element is first computed in plain FP32 (edge vectors
+ *   rounded once, one FMA per cofactor, det as an FMA dot product), whose
+ *   det is within 11u perm(|V|) of the exact one (u = 2^-24, perm the
+ *   permanent of the absolute Jacobian).  Where |det| < perm(|V|)/4 (flat
+ *   or sliver elements, where that bound exceeds 44u relative) the element
+ *   is recomputed from error-free float-pair edge vectors with a compensated
+ *   determinant (error about 2u relative plus O(u^2 perm)) and Kahan's FMA
+ *   algorithm for the remaining cofactors.  Every CSR value is a compensated
+ *   (float-float) sum converted to FP64 once.
  * If n_singular != NULL (device int64), it receives the number of elements
  * with det == 0.  Deterministic: the same inputs give bit-identical outputs. */
 vla_status vla_assemble(const vla_mesh *mesh, int32_t coeff_kind, double ca, double cb, int32_t precision,
@@ -259,23 +265,42 @@ vla_status vla_simplex_normals(const vla_mesh *mesh, double *normals, void *stre
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory where they need element matrices (a heap
  * owned by another framework, allocator-free real-time loops, code that must
- * not create a persistent handle).  It computes exactly what vla_assemble
- * writes to K_pages, M_pages and vol (same geometry and precision paths), but
- * from the raw arrays: coords dim x nn FP64 and elems nlb x ne int32 (device,
- * layouts as for vla_mesh_create; indices are not validated here).
+ * not create a persistent handle).  It computes what vla_assemble writes to
+ * K_pages, M_pages and vol, bit for bit (the same element arithmetic, in
+ * both precisions), for the centroid coefficient kinds VLA_COEFF_POLY and
+ * VLA_COEFF_EXP (the literal-quadrature kinds are rejected with
+ * VLA_ERR_INVALID_ARG), from the raw arrays: coords dim x nn FP64 and elems
+ * nlb x ne int32 (device, layouts as for vla_mesh_create).  Element indices
+ * are checked on the device before any coordinate is read: an element with
+ * a node index outside [0, nn) is skipped, its pages and volume are set to
+ * NaN, and it is counted; vla_element_pages_static_check reports the count
+ * of the last call.
  * Scratch: the float-pair split of the coordinates used by VLA_PREC_MIXED is
  * kept in a fixed device array built into the library (8 MiB per GPU that
  * loads it, held until the process exits); nn above 262,144 is rejected with
  * VLA_ERR_BUDGET.  No cudaMalloc/cudaFree or allocating library call is made.
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call shares the one array: calls that overlap on the GPU (different
- * streams, or different host threads) race and must be serialised by the
- * caller.  Outputs (device, any may be NULL): K_pages, M_pages nlb x nlb x ne
- * column-major, vol ne, n_singular (device int64, overwritten). */
+ * Every call shares the one array and the skip counter (cleared at the start
+ * of each call): calls that overlap on the GPU (different streams, or
+ * different host threads) race and must be serialised by the caller.
+ * Outputs (device, any may be NULL): K_pages, M_pages nlb x nlb x ne
+ * column-major, vol ne, n_singular (device int64, overwritten).
+ * Errors (before any work): VLA_ERR_INVALID_ARG for an unknown dim, order,
+ * coefficient kind or precision, nn < 1, ne < 0, too many elements, NULL
+ * mesh arrays with ne > 0 or a non-finite coefficient; VLA_ERR_BUDGET for
+ * nn > 262,144; VLA_ERR_CUDA if a launch fails. */
 vla_status vla_element_pages_static(int32_t dim, int32_t order, int64_t nn, int64_t ne, const double *coords,
                                     const int32_t *elems, int32_t coeff_kind, double ca, double cb, int32_t precision,
                                     double *K_pages, double *M_pages, double *vol, int64_t *n_singular, void *stream);
+
+/* Reports how many elements the last vla_element_pages_static call on the
+ * current device skipped for a node index outside [0, nn) (the paper has no
+ * counterpart; index validation of the allocation-free path).  Copies the
+ * device counter to *n_skipped (host, may be NULL) on `stream` and
+ * synchronises it.  Returns VLA_ERR_INDEX_OOB if the count is nonzero,
+ * VLA_ERR_CUDA if the copy fails, VLA_OK otherwise. */
+vla_status vla_element_pages_static_check(int64_t *n_skipped, void *stream);
 
 /* Every facet of the mesh once (the faces behind the paper's normals of all
  * faces and its face counts, Section 3.2): facet j of element k is opposite

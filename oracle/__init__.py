@@ -33,7 +33,8 @@ def build(force: bool = False) -> str:
     """Compile ``vla_oracle.c`` into ``liboracle.so`` (gcc, -O2, portable flags)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_POSIX_C_SOURCE=200809L", "-pthread", "-fPIC", "-shared",
+                               "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -69,6 +70,9 @@ def _load():
         lib.orc_assemble.argtypes = [C.c_int, C.c_int, _i64, _i64, C.c_int, _i, _d, C.c_int, C.c_double, C.c_double,
                                      _i, _i, _d, _d, _d, vp, vp]
         lib.orc_assemble.restype = C.c_int
+        lib.orc_assemble_threads.argtypes = [C.c_int, C.c_int, _i64, _i64, C.c_int, _i, _d, C.c_int, C.c_double,
+                                             C.c_double, _i, _i, _d, _d, _d, C.c_int]
+        lib.orc_assemble_threads.restype = C.c_int
         lib.orc_boundary.argtypes = [C.c_int, _i64, _i64, C.c_int, _i, _d, _i64, _i, _d, _d]
         lib.orc_boundary.restype = _i64
         lib.orc_count_facets.argtypes = [C.c_int, _i64, C.c_int, _i, C.POINTER(_i64), C.POINTER(_i64)]
@@ -304,6 +308,22 @@ def assemble(dim, order, nn, elems, coords, ca=1.0, cb=0.0, pattern=None, want_p
     if want_pages:
         out["K3D"], out["M3D"] = K3D, M3D
     return out
+
+
+def assemble_threads(dim, order, nn, elems, coords, ca=1.0, cb=0.0, pattern=None, ckind=0, nthreads=1):
+    """The same K, M and volumes as ``assemble`` (bit for bit) on ``nthreads``
+    host threads: a timing entry for the CPU baseline, which runs the pinned
+    element-page and scatter steps over element ranges and row blocks."""
+    elems, coords = _i32(elems), _f64(coords)
+    ne, nlb = elems.shape
+    rp, ci = pattern if pattern is not None else csr_pattern(nn, elems)
+    nnz = len(ci)
+    Kv, Mv, vol = np.zeros(max(nnz, 1)), np.zeros(max(nnz, 1)), np.zeros(max(ne, 1))
+    rc = _load().orc_assemble_threads(dim, order, nn, ne, nlb, elems, coords, ckind, ca, cb, _i32(rp),
+                                      _i32(ci) if nnz else np.zeros(1, np.int32), Kv, Mv, vol, int(nthreads))
+    if rc != 0:
+        raise ValueError("oracle assembly failed")
+    return {"row_ptr": rp, "col_idx": ci, "K": Kv[:nnz], "M": Mv[:nnz], "vol": vol[:ne]}
 
 
 def boundary(dim, nn, elems, coords, faces):

@@ -939,3 +939,107 @@ int64_t orc_facets(int dim, int64_t ne, int nlb, const int32_t *elems, int32_t *
     free(partner);
     return nf;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Timing entry for the CPU baseline only (not pinned separately: it runs   */
+/* the pinned functions above and gives their results bit for bit).  The    */
+/* same assembly as orc_assemble on nthreads host threads: element pages    */
+/* by orc_element_pages over contiguous element ranges, then each thread     */
+/* scatters the entries whose row falls in its own block of rows, visiting  */
+/* elements in ascending order, so every CSR value receives its terms in    */
+/* the same order as the sequential scatter.                                */
+/* ------------------------------------------------------------------------ */
+#include <pthread.h>
+
+typedef struct {
+    int dim, order, nlb, ckind;
+    int64_t ne, k0, k1;          /* element range of the page phase */
+    int32_t r0, r1;              /* row block of the scatter phase */
+    const int32_t *elems, *row_ptr, *col_idx;
+    const double *coords;
+    double ca, cb;
+    double *K3D, *M3D, *vol, *Kv, *Mv;
+    int phase, rc;
+} orc_task;
+
+static void *orc_task_run(void *p) {
+    orc_task *t = (orc_task *)p;
+    const int nlb = t->nlb;
+    if (t->phase == 0) {
+        orc_element_pages(t->dim, t->order, t->k1 - t->k0, nlb, t->elems + t->k0 * nlb, t->coords, t->ckind, t->ca,
+                          t->cb, t->K3D + t->k0 * nlb * nlb, t->M3D + t->k0 * nlb * nlb, t->vol + t->k0, NULL);
+        return NULL;
+    }
+    for (int64_t q = t->row_ptr[t->r0]; q < t->row_ptr[t->r1]; ++q) t->Kv[q] = t->Mv[q] = 0.0;
+    for (int64_t k = 0; k < t->ne; ++k)
+        for (int j = 0; j < nlb; ++j) {
+            const int32_t r = t->elems[k * nlb + j];
+            if (r < t->r0 || r >= t->r1) continue;
+            for (int i = 0; i < nlb; ++i) {
+                int64_t pos = csr_find(t->row_ptr, t->col_idx, r, t->elems[k * nlb + i]);
+                if (pos < 0) {
+                    t->rc = -1;
+                    return NULL;
+                }
+                t->Kv[pos] += t->K3D[k * nlb * nlb + i + j * nlb];
+                t->Mv[pos] += t->M3D[k * nlb * nlb + i + j * nlb];
+            }
+        }
+    return NULL;
+}
+
+int orc_assemble_threads(int dim, int order, int64_t nn, int64_t ne, int nlb, const int32_t *elems,
+                         const double *coords, int ckind, double ca, double cb, const int32_t *row_ptr,
+                         const int32_t *col_idx, double *Kv, double *Mv, double *vol, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    double *K3D = (double *)malloc((size_t)(ne > 0 ? ne : 1) * nlb * nlb * sizeof(double));
+    double *M3D = (double *)malloc((size_t)(ne > 0 ? ne : 1) * nlb * nlb * sizeof(double));
+    orc_task *T = (orc_task *)calloc((size_t)nthreads, sizeof(orc_task));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    char *started = (char *)calloc((size_t)nthreads, 1);
+    int rc = 0;
+    if (!K3D || !M3D || !T || !th || !started) rc = -1;
+    for (int phase = 0; phase < 2 && rc == 0; ++phase) {
+        for (int t = 0; t < nthreads; ++t) {
+            orc_task *x = &T[t];
+            x->dim = dim;
+            x->order = order;
+            x->nlb = nlb;
+            x->ckind = ckind;
+            x->ne = ne;
+            x->k0 = ne * t / nthreads;
+            x->k1 = ne * (t + 1) / nthreads;
+            x->r0 = (int32_t)(nn * t / nthreads);
+            x->r1 = (int32_t)(nn * (t + 1) / nthreads);
+            x->elems = elems;
+            x->row_ptr = row_ptr;
+            x->col_idx = col_idx;
+            x->coords = coords;
+            x->ca = ca;
+            x->cb = cb;
+            x->K3D = K3D;
+            x->M3D = M3D;
+            x->vol = vol;
+            x->Kv = Kv;
+            x->Mv = Mv;
+            x->phase = phase;
+            x->rc = 0;
+        }
+        for (int t = 1; t < nthreads; ++t) {
+            started[t] = pthread_create(&th[t], NULL, orc_task_run, &T[t]) == 0;
+            if (!started[t]) orc_task_run(&T[t]);   /* no thread to be had: run the task here */
+        }
+        orc_task_run(&T[0]);
+        for (int t = 1; t < nthreads; ++t)
+            if (started[t]) pthread_join(th[t], NULL);
+        for (int t = 0; t < nthreads; ++t)
+            if (T[t].rc) rc = T[t].rc;
+    }
+    free(K3D);
+    free(M3D);
+    free(T);
+    free(th);
+    free(started);
+    return rc;
+}

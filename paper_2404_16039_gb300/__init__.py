@@ -21,7 +21,7 @@ import torch
 
 __all__ = [
     "VlaError", "lib", "version", "amtam", "astam", "avtam", "amdet", "aminv", "amt", "avtav", "amsm", "amsv",
-    "smamt", "svamt", "Mesh", "element_pages_static",
+    "smamt", "svamt", "Mesh", "element_pages_static", "static_skipped",
     "Batch", "batch_assemble", "autotune", "tune_get", "tune_set", "Server", "PENDING", "quad_rule", "gi",
     "avtamav", "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP",
     "COEFF_POLY_IP", "COEFF_EXP_IP",
@@ -31,6 +31,7 @@ F32, F64 = 0, 1
 LAYOUT_PAGE, LAYOUT_SOA = 0, 1
 PREC_FP64, PREC_MIXED = 0, 1
 COEFF_POLY, COEFF_EXP, COEFF_POLY_IP, COEFF_EXP_IP = 0, 1, 2, 3
+VLA_ERR_INDEX_OOB = -2
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvla.so")
@@ -132,6 +133,7 @@ def lib():
         L.vla_simplex_normals.argtypes = [vp, vp, vp]
         L.vla_mesh_destroy.argtypes = [vp]
         L.vla_element_pages_static.argtypes = [i32, i32, i64, i64, vp, vp, i32, dbl, dbl, i32, vp, vp, vp, vp, vp]
+        L.vla_element_pages_static_check.argtypes = [C.POINTER(i64), vp]
         L.vla_mesh_check.argtypes = [vp, vp]
         L.vla_batch_create.argtypes = [C.POINTER(BatchJob), i32, i32, vp, i32, vp, C.POINTER(vp)]
         L.vla_batch_set_job.argtypes = [vp, i32, C.POINTER(BatchJob), vp]
@@ -158,7 +160,7 @@ def lib():
         L.vla_server_destroy.argtypes = [vp]
         for name in ("vla_amtam", "vla_astam", "vla_avtam", "vla_amdet", "vla_aminv", "vla_mesh_create",
                      "vla_mesh_info", "vla_mesh_csr", "vla_assemble", "vla_boundary", "vla_simplex_normals",
-                     "vla_mesh_destroy", "vla_element_pages_static", "vla_mesh_check", "vla_batch_create",
+                     "vla_mesh_destroy", "vla_element_pages_static", "vla_element_pages_static_check", "vla_mesh_check", "vla_batch_create",
                      "vla_batch_set_job", "vla_batch_run", "vla_batch_info", "vla_batch_check", "vla_batch_destroy",
                      "vla_batch_assemble", "vla_autotune", "vla_tune_get", "vla_tune_set", "vla_server_create",
                      "vla_server_submit", "vla_server_poll", "vla_server_release", "vla_server_stats",
@@ -569,15 +571,20 @@ def element_pages_static(coords, elems, order=1, ca=1.0, cb=0.0, kind=COEFF_POLY
     """Element pages (ne, nlb, nlb), volumes (ne,) and optionally the singular
     count from raw mesh arrays, without a mesh handle and without any device
     allocation inside the library (vla_element_pages_static; at most 262,144
-    nodes).  The output tensors are allocated here by PyTorch; callers that
-    cannot allocate pass the C entry point their own buffers.  The element
-    indices must lie in [0, nn): this entry point reads them as given (use
-    Mesh, which validates them, for untrusted meshes).  Section 3.5."""
+    nodes; the centroid coefficient kinds).  The output tensors are allocated
+    here by PyTorch; callers that cannot allocate pass the C entry point their
+    own buffers.  The element indices are checked here against [0, nn) before
+    the call (the library also skips and counts out-of-range elements on the
+    device, see static_skipped).  Section 3.5."""
     _req(coords, torch.float64), _req(elems, torch.int32)
     _same_device(coords, elems)
     _mesh_arrays(coords, elems, None, order)
     nn, dim = coords.shape
     ne, nlb = elems.shape
+    if ne > 0:
+        lo, hi = int(elems.min().item()), int(elems.max().item())
+        if lo < 0 or hi >= nn:
+            raise VlaError(VLA_ERR_INDEX_OOB, f"element node index outside [0, {nn}) (min {lo}, max {hi})")
     dev = coords.device
     Kp = torch.empty((ne, nlb, nlb), dtype=torch.float64, device=dev)
     Mp = torch.empty((ne, nlb, nlb), dtype=torch.float64, device=dev)
@@ -589,6 +596,17 @@ def element_pages_static(coords, elems, order=1, ca=1.0, cb=0.0, kind=COEFF_POLY
     if count_singular:
         out["n_singular"] = ns
     return out
+
+
+def static_skipped(stream=None) -> int:
+    """Number of elements the last element_pages_static call on the current
+    device skipped for an index outside [0, nn) (synchronises the stream;
+    vla_element_pages_static_check).  No counterpart in the paper."""
+    n = C.c_int64(0)
+    st = lib().vla_element_pages_static_check(C.byref(n), _stream(stream))
+    if st < 0 and st != VLA_ERR_INDEX_OOB:
+        _check(st)
+    return int(n.value)
 
 
 # ---------------------------------------------------------------------------

@@ -424,10 +424,14 @@ __device__ __forceinline__ T dot3(const T *a, const T *b) {
     return fma_t(a[2], b[2], fma_t(a[1], b[1], a[0] * b[0]));
 }
 
-// Mixed precision fast path: edge vectors rounded once to float, Kahan 2x2
-// cofactors, plain dot for det.  The det error is below ~8u perm(|V|); if
-// |det| < perm(|V|)/32 (a flat or sliver element) the exact float-pair path
-// recomputes the geometry.
+// Mixed precision fast path, in plain FP32: edge vectors rounded once to
+// float (relative error <= 2u per component, u = 2^-24), each cofactor as one
+// FMA against a rounded product, det as an FMA dot product.  To first order
+// |det_computed - det| <= u (2 Q + 5 perm) <= 11 u perm, where perm is the
+// permanent of |V| and Q = sum_jc |V_jc| |C_jc| <= 3 perm.  Elements with
+// |det| < perm/4 (flat or sliver elements, where that bound exceeds 44u
+// relative) are recomputed by the float-pair path above, whose det is
+// accurate to about 2u relative plus O(u^2 perm).
 __device__ __forceinline__ void geo_mixed3_fast(const float4 *__restrict__ sh, const float4 *__restrict__ sl,
                                                 ushort4 v, Geo<float> &g) {
     const float4 h3 = sh[v.w], l3 = sl[v.w];
@@ -461,9 +465,12 @@ __device__ __forceinline__ void geo_mixed3_fast(const float4 *__restrict__ sh, c
     g.xc[0] = sx * 0.25f;
     g.xc[1] = sy * 0.25f;
     g.xc[2] = sz * 0.25f;
-    if (fabsf(g.det) < 0.03125f * perm) geo_mixed3(sh, sl, v, g);
+    if (fabsf(g.det) < 0.25f * perm) geo_mixed3(sh, sl, v, g);
 }
 
+// 2-D fast path: V rounded once, det by Kahan's FMA 2x2 algorithm, so
+// |det_computed - det| <= 4u perm2 + 2u |det| with perm2 = |V00 V11| + |V01 V10|;
+// elements with |det| < perm2/4 take the float-pair path.
 __device__ __forceinline__ void geo_mixed2_fast(const float4 *__restrict__ sh, const float4 *__restrict__ sl,
                                                 ushort4 v, Geo<float> &g) {
     const float4 h2 = sh[v.z], l2 = sl[v.z];
@@ -483,7 +490,34 @@ __device__ __forceinline__ void geo_mixed2_fast(const float4 *__restrict__ sh, c
     g.xc[0] = (h0.x + h1.x + h2.x) * (1.0f / 3.0f);
     g.xc[1] = (h0.y + h1.y + h2.y) * (1.0f / 3.0f);
     g.xc[2] = 0.f;
-    if (fabsf(g.det) < 0.03125f * (fabsf(V00 * V11) + fabsf(V01 * V10))) geo_mixed2(sh, sl, v, g);
+    if (fabsf(g.det) < 0.25f * (fabsf(V00 * V11) + fabsf(V01 * V10))) geo_mixed2(sh, sl, v, g);
+}
+
+// P1 stiffness record: the packed upper triangle (NLB = dim + 1) of
+// K_k(a,b) = sc (C_a . C_b).  Every row of K_k sums to zero (the cofactor
+// vectors sum to zero), so only the entries among the first dim vertices are
+// dot products; the last vertex's column and diagonal follow from them:
+// K(a,D) = -sum_{b<D} K(a,b), K(D,D) = -sum_{a<D} K(a,D).
+template <int DIM, typename T>
+__device__ __forceinline__ void p1_stiffness(const Geo<T> &g, T sc, T *rec) {
+    constexpr int NLB = DIM + 1, D = DIM;   // D: the last vertex
+    auto u_of = [](int a, int q) { return a < q ? a * NLB - a * (a - 1) / 2 + (q - a)
+                                                : q * NLB - q * (q - 1) / 2 + (a - q); };
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int q = a; q < D; ++q) rec[u_of(a, q)] = sc * dot3<T>(g.C[a], g.C[q]);
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        T r = rec[u_of(a, 0)];
+#pragma unroll
+        for (int b = 1; b < D; ++b) r += rec[u_of(a, b)];
+        rec[u_of(a, D)] = -r;
+    }
+    T r = rec[u_of(0, D)];
+#pragma unroll
+    for (int a = 1; a < D; ++a) r += rec[u_of(a, D)];
+    rec[u_of(D, D)] = -r;
 }
 
 // ---------------------------------------------------------------------------
@@ -739,31 +773,9 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
         T mscale;
         if constexpr (ORDER == 1) {
             T rec[C::RS];
-            auto u_of = [](int a, int q) { return a < q ? a * C::NLB - a * (a - 1) / 2 + (q - a)
-                                                        : q * C::NLB - q * (q - 1) / 2 + (a - q); };
-            constexpr int D = C::NV - 1;   // the last vertex
 #pragma unroll
             for (int u = 0; u < C::RS; ++u) rec[u] = T(0);
-#pragma unroll
-            for (int a = 0; a < D; ++a)
-#pragma unroll
-                for (int q = a; q < D; ++q) rec[u_of(a, q)] = sc * dot3<T>(g.C[a], g.C[q]);
-            // every row of K_k sums to zero (the cofactor vectors sum to zero), so
-            // the last vertex's column and diagonal follow from the others:
-            // K(a,D) = -sum_{b<D} K(a,b), K(D,D) = -sum_{a<D} K(a,D)
-#pragma unroll
-            for (int a = 0; a < D; ++a) {
-                T r = rec[u_of(a, 0)];
-#pragma unroll
-                for (int b = 1; b < D; ++b) r += rec[u_of(a, b)];
-                rec[u_of(a, D)] = -r;
-            }
-            {
-                T r = rec[u_of(0, D)];
-#pragma unroll
-                for (int a = 1; a < D; ++a) r += rec[u_of(a, D)];
-                rec[u_of(D, D)] = -r;
-            }
+            p1_stiffness<DIM, T>(g, sc, rec);
             mscale = c * adet * T(C::MOFF / C::DFACT);       // off-diagonal mass entry
             rec[C::NU] = mscale;
             if constexpr (MIX) {
@@ -1819,25 +1831,32 @@ namespace {
 
 constexpr int64_t kStaticMaxNodes = int64_t(1) << 18;    // 262,144 nodes: 8 MiB of float pairs
 static __device__ __align__(256) float4 g_static_xhl[2 * kStaticMaxNodes];
+// elements the last call skipped because an index lay outside [0, nn)
+static __device__ unsigned long long g_static_bad;
 
 std::mutex g_static_mu;
 void *g_static_ptr[64] = {nullptr};
+void *g_static_bad_ptr[64] = {nullptr};
 
-// Device address of the scratch array for the current device (set up once
-// per device with that device current; host code must not use the symbol's
-// name as an address).
-vla_status static_scratch(float4 **out) {
+// Device addresses of the scratch array and of the skip counter for the
+// current device (set up once per device with that device current; host code
+// must not use the symbols' names as addresses).
+vla_status static_scratch(float4 **out, unsigned long long **bad) {
     int dev = 0;
     VLA_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return fail(VLA_ERR_INVALID_ARG, "device ordinal %d not supported", dev);
     std::lock_guard<std::mutex> lk(g_static_mu);
     if (!g_static_ptr[dev]) {
-        void *p = nullptr;
+        void *p = nullptr, *q = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_xhl);
         if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+        e = cudaGetSymbolAddress(&q, g_static_bad);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static skip counter)");
+        g_static_bad_ptr[dev] = q;
         g_static_ptr[dev] = p;
     }
     *out = reinterpret_cast<float4 *>(g_static_ptr[dev]);
+    *bad = reinterpret_cast<unsigned long long *>(g_static_bad_ptr[dev]);
     return VLA_OK;
 }
 
@@ -1855,41 +1874,62 @@ __global__ void k_static_split(int64_t nn, int dim, const double *__restrict__ x
     }
 }
 
-// element pages and volumes straight from the mesh arrays, one thread per element
+// Element pages and volumes straight from the mesh arrays, one thread per
+// element, with the arithmetic of the tiled assembly's element phase (same
+// geometry, coefficient, stiffness record and mass scale), so the pages equal
+// vla_assemble's bit for bit.  An element with an index outside [0, nn) is
+// skipped before any coordinate is read: its pages and volume become NaN and
+// it is counted in g_static_bad.
 template <int DIM, int ORDER, bool MIX>
-__global__ void __launch_bounds__(256) k_static_pages(int64_t ne, const int32_t *__restrict__ elems,
+__global__ void __launch_bounds__(256) k_static_pages(int64_t ne, int64_t nn, const int32_t *__restrict__ elems,
                                                       const float4 *__restrict__ xh, const float4 *__restrict__ xl,
                                                       const double *__restrict__ coords, int kind, double ca,
                                                       double cb, double *__restrict__ Kp, double *__restrict__ Mp,
-                                                      double *__restrict__ vol, unsigned long long *__restrict__ n_sing) {
+                                                      double *__restrict__ vol, unsigned long long *__restrict__ n_sing,
+                                                      unsigned long long *__restrict__ n_bad) {
     using C = Cfg<DIM, ORDER, MIX>;
     using T = typename C::T;
-    const T cat = (T)ca, cbt = (T)cb;
-    unsigned long long sing = 0;
+    const T cat = MIX ? (T)(float)ca : (T)ca, cbt = MIX ? (T)(float)cb : (T)cb;
+    unsigned long long sing = 0, bad = 0;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < ne; k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t vid[C::NV];
+        bool ok = true;
+#pragma unroll
+        for (int j = 0; j < C::NV; ++j) {
+            vid[j] = elems[k * C::NLB + j];
+            ok = ok && vid[j] >= 0 && (int64_t)vid[j] < nn;
+        }
+        for (int j = C::NV; j < C::NLB; ++j) {   // P2 mid-edge nodes: checked, never read
+            const int32_t v = elems[k * C::NLB + j];
+            ok = ok && v >= 0 && (int64_t)v < nn;
+        }
+        if (!ok) {
+            ++bad;
+            const double nan = __longlong_as_double(0x7ff8000000000000ll);
+            for (int q = 0; q < C::NLB * C::NLB; ++q) {
+                if (Kp) Kp[k * C::NLB * C::NLB + q] = nan;
+                if (Mp) Mp[k * C::NLB * C::NLB + q] = nan;
+            }
+            if (vol) vol[k] = nan;
+            continue;
+        }
         Geo<T> g;
         if constexpr (MIX) {
             float4 h[C::NV], l[C::NV];
 #pragma unroll
             for (int j = 0; j < C::NV; ++j) {
-                const int32_t v = elems[k * C::NLB + j];
-                h[j] = xh[v];
-                l[j] = xl[v];
+                h[j] = xh[vid[j]];
+                l[j] = xl[vid[j]];
             }
-            // same geometry as the tiled assembly, from vertex arrays
-            if constexpr (DIM == 3) {
-                geo_mixed3_fast(h, l, make_ushort4(0, 1, 2, 3), g);
-            } else {
-                geo_mixed2_fast(h, l, make_ushort4(0, 1, 2, 0), g);
-            }
+            if constexpr (DIM == 3) geo_mixed3_fast(h, l, make_ushort4(0, 1, 2, 3), g);
+            else geo_mixed2_fast(h, l, make_ushort4(0, 1, 2, 0), g);
         } else {
             double4_16a x[C::NV];
 #pragma unroll
             for (int j = 0; j < C::NV; ++j) {
-                const int32_t v = elems[k * C::NLB + j];
-                x[j].x = coords[(int64_t)v * DIM];
-                x[j].y = coords[(int64_t)v * DIM + 1];
-                x[j].z = DIM == 3 ? coords[(int64_t)v * DIM + 2] : 0.0;
+                x[j].x = coords[(int64_t)vid[j] * DIM];
+                x[j].y = coords[(int64_t)vid[j] * DIM + 1];
+                x[j].z = DIM == 3 ? coords[(int64_t)vid[j] * DIM + 2] : 0.0;
                 x[j].w = 0.0;
             }
             geo_f64<DIM>(x, make_ushort4(0, 1, 2, DIM == 3 ? 3 : 0), g);
@@ -1899,27 +1939,28 @@ __global__ void __launch_bounds__(256) k_static_pages(int64_t ne, const int32_t 
         T sc;
         if constexpr (MIX) sc = c * __frcp_rn(T(C::DFACT) * adet);
         else sc = c / (T(C::DFACT) * adet);
-        T cd[10];
+        T rec[C::NU];
+        T mscale;
+        if constexpr (ORDER == 1) {
+            p1_stiffness<DIM, T>(g, sc, rec);
+            mscale = c * adet * T(C::MOFF / C::DFACT);
+        } else {
+            T cd[10];
 #pragma unroll
-        for (int a = 0; a < C::NV; ++a)
+            for (int a = 0; a < C::NV; ++a)
 #pragma unroll
-            for (int q = a; q < C::NV; ++q) cd[a * C::NV - a * (a - 1) / 2 + (q - a)] = dot3<T>(g.C[a], g.C[q]);
-        const T mscale = ORDER == 1 ? c * adet * T(C::MOFF / C::DFACT) : c * adet * T(1.0 / C::DFACT);
+                for (int q = a; q < C::NV; ++q) cd[a * C::NV - a * (a - 1) / 2 + (q - a)] = dot3<T>(g.C[a], g.C[q]);
+            p2_k_entries<DIM, T>(cd, sc, rec, std::make_integer_sequence<int, C::NU>());
+            mscale = c * adet * T(1.0 / C::DFACT);
+        }
         for (int a = 0; a < C::NLB; ++a)
             for (int q = 0; q < C::NLB; ++q) {
                 const int p0 = a < q ? a : q, p1 = a < q ? q : a;
-                T kv, mv;
-                if constexpr (ORDER == 1) {
-                    kv = sc * cd[p0 * C::NV - p0 * (p0 - 1) / 2 + (p1 - p0)];
-                    mv = mscale * (a == q ? T(2) : T(1));
-                } else {
-                    const int u = p0 * C::NLB - p0 * (p0 - 1) / 2 + (p1 - p0);
-                    const P2Tab &tb = c_p2[DIM - 2];
-                    T acc = 0;
-                    for (int t = 0; t < tb.nterm[u]; ++t) acc += (MIX ? (T)tb.coef_f[u][t] : (T)tb.coef_d[u][t]) * cd[tb.st[u][t]];
-                    kv = sc * acc;
-                    mv = mscale * (MIX ? (T)tb.mhat_f[u] : (T)tb.mhat_d[u]);
-                }
+                const int u = p0 * C::NLB - p0 * (p0 - 1) / 2 + (p1 - p0);
+                const T kv = rec[u];
+                T mv;
+                if constexpr (ORDER == 1) mv = mscale * (a == q ? T(2) : T(1));
+                else mv = mscale * (MIX ? (T)c_p2[DIM - 2].mhat_f[u] : (T)c_p2[DIM - 2].mhat_d[u]);
                 const int64_t pos = k * C::NLB * C::NLB + a + (int64_t)q * C::NLB;
                 if constexpr (MIX) {
                     if (Kp) Kp[pos] = f32_to_f64(kv);
@@ -1936,14 +1977,15 @@ __global__ void __launch_bounds__(256) k_static_pages(int64_t ne, const int32_t 
         }
     }
     if (n_sing && sing) atomicAdd(n_sing, sing);
+    if (bad) atomicAdd(n_bad, bad);
 }
 
 template <int DIM, int ORDER, bool MIX>
-void launch_static_pages(int64_t ne, const int32_t *elems, const float4 *xh, const float4 *xl, const double *coords,
-                         int kind, double ca, double cb, double *Kp, double *Mp, double *vol,
-                         unsigned long long *ns, cudaStream_t st) {
-    k_static_pages<DIM, ORDER, MIX><<<grid_for(ne, 256, 152 * 16), 256, 0, st>>>(ne, elems, xh, xl, coords, kind, ca,
-                                                                                   cb, Kp, Mp, vol, ns);
+void launch_static_pages(int64_t ne, int64_t nn, const int32_t *elems, const float4 *xh, const float4 *xl,
+                         const double *coords, int kind, double ca, double cb, double *Kp, double *Mp, double *vol,
+                         unsigned long long *ns, unsigned long long *bad, cudaStream_t st) {
+    k_static_pages<DIM, ORDER, MIX><<<grid_for(ne, 256, 152 * 16), 256, 0, st>>>(ne, nn, elems, xh, xl, coords, kind,
+                                                                                   ca, cb, Kp, Mp, vol, ns, bad);
 }
 
 }  // namespace
@@ -1967,7 +2009,8 @@ extern "C" vla_status vla_element_pages_static(int32_t dim, int32_t order, int64
     if (!std::isfinite(ca) || !std::isfinite(cb)) return fail(VLA_ERR_INVALID_ARG, "non-finite coefficient");
     cudaStream_t st = (cudaStream_t)stream;
     float4 *scratch = nullptr;
-    vla_status s = static_scratch(&scratch);
+    unsigned long long *bad = nullptr;
+    vla_status s = static_scratch(&scratch, &bad);
     if (s) return s;
     if (order == 2) {
         s = ensure_p2_tables();
@@ -1975,6 +2018,7 @@ extern "C" vla_status vla_element_pages_static(int32_t dim, int32_t order, int64
     }
     unsigned long long *ns = reinterpret_cast<unsigned long long *>(n_singular);
     if (ns) VLA_CUDA(cudaMemsetAsync(ns, 0, sizeof(unsigned long long), st));
+    VLA_CUDA(cudaMemsetAsync(bad, 0, sizeof(unsigned long long), st));
     if (ne == 0) return VLA_OK;
     const bool mix = precision == VLA_PREC_MIXED;
     float4 *xh = scratch, *xl = scratch + kStaticMaxNodes;
@@ -1983,17 +2027,33 @@ extern "C" vla_status vla_element_pages_static(int32_t dim, int32_t order, int64
         VLA_CUDA(cudaGetLastError());
     }
     const int key = (dim == 3 ? 4 : 0) + (order == 2 ? 2 : 0) + (mix ? 1 : 0);
+#define VLA_STATIC(D, O, X) \
+    launch_static_pages<D, O, X>(ne, nn, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, bad, st)
     switch (key) {
-    case 0: launch_static_pages<2, 1, false>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
-    case 1: launch_static_pages<2, 1, true>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
-    case 2: launch_static_pages<2, 2, false>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
-    case 3: launch_static_pages<2, 2, true>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
-    case 4: launch_static_pages<3, 1, false>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
-    case 5: launch_static_pages<3, 1, true>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
-    case 6: launch_static_pages<3, 2, false>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
-    default: launch_static_pages<3, 2, true>(ne, elems, xh, xl, coords, kind, ca, cb, K_pages, M_pages, vol, ns, st); break;
+    case 0: VLA_STATIC(2, 1, false); break;
+    case 1: VLA_STATIC(2, 1, true); break;
+    case 2: VLA_STATIC(2, 2, false); break;
+    case 3: VLA_STATIC(2, 2, true); break;
+    case 4: VLA_STATIC(3, 1, false); break;
+    case 5: VLA_STATIC(3, 1, true); break;
+    case 6: VLA_STATIC(3, 2, false); break;
+    default: VLA_STATIC(3, 2, true); break;
     }
+#undef VLA_STATIC
     VLA_CUDA(cudaGetLastError());
+    return VLA_OK;
+}
+
+extern "C" vla_status vla_element_pages_static_check(int64_t *n_skipped, void *stream) {
+    float4 *scratch = nullptr;
+    unsigned long long *bad = nullptr;
+    TRY(static_scratch(&scratch, &bad));
+    unsigned long long h = 0;
+    VLA_CUDA(cudaMemcpyAsync(&h, bad, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    VLA_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+    if (n_skipped) *n_skipped = (int64_t)h;
+    if (h) return fail(VLA_ERR_INDEX_OOB, "vla_element_pages_static skipped %llu element(s) with a node index outside "
+                                          "[0, nn)", h);
     return VLA_OK;
 }
 

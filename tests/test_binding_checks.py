@@ -77,6 +77,15 @@ def test_mesh_arrays_must_match_the_element_order(b):
         b.Mesh(coords, torch.zeros((2, 4), dtype=I32), faces=torch.zeros((4, 2), dtype=I32))
     with pytest.raises(ValueError):
         b.element_pages_static(coords, torch.zeros((2, 3), dtype=I32))
+    # the allocation-free path reads its indices as given: the binding checks them first
+    for bad in (5, -1):
+        el = torch.zeros((2, 4), dtype=I32)
+        el[1, 2] = bad
+        with pytest.raises(vla.VlaError) as ei:
+            b.element_pages_static(coords, el)
+        assert ei.value.status == vla.VLA_ERR_INDEX_OOB
+    with pytest.raises(_LibraryReached):
+        b.element_pages_static(coords, torch.tensor([[0, 1, 2, 4], [1, 2, 3, 4]], dtype=I32))
     with pytest.raises(ValueError):
         b.autotune(torch.zeros((5, 2), dtype=F64), torch.zeros((2, 4), dtype=I32))
     with pytest.raises(_LibraryReached):

@@ -501,3 +501,16 @@ def test_facet_list_brute_force_tiny():
     # brute force pairing count: interior facets counted twice across elements
     triples = [tuple(sorted(v for i, v in enumerate(e) if i != j)) for e in m.elems for j in range(4)]
     assert len(set(triples)) == len(faces)
+
+
+@pytest.mark.parametrize("dim,order,n", [(3, 1, 5), (3, 2, 3), (2, 1, 9), (2, 2, 6)])
+def test_threaded_timing_entry_is_bit_identical(dim, order, n):
+    # the CPU baseline's all-cores entry runs the pinned steps over element
+    # ranges and row blocks; every value must equal the sequential assembly's
+    m = meshgen.make_mesh(dim, n, order=order, jitter=0.1, seed=4)
+    pat = oracle.csr_pattern(m.nn, m.elems)
+    a = oracle.assemble(dim, order, m.nn, m.elems, m.coords, 0.7, 1.3, pattern=pat)
+    for nt in (1, 3, 7):
+        b = oracle.assemble_threads(dim, order, m.nn, m.elems, m.coords, 0.7, 1.3, pattern=pat, nthreads=nt)
+        for k in ("K", "M", "vol"):
+            assert np.array_equal(a[k], b[k]), (k, nt)
