@@ -883,10 +883,12 @@ __device__ __forceinline__ void tile_pairs(double *__restrict__ K, double *__res
                 if constexpr (ORDER == 2) {   // the pair's reference mass entry times the summed scales
                     const uint32_t cf = cp[0];
                     const float mh = mhat[cf - elem_of(cf) * C::RSC], p = mhi * mh;
-                    mlo = __fmaf_rn(mlo, mh, __fmaf_rn(mhi, mh, -p));
-                    mhi = p;
+                    const float t = __fmaf_rn(mlo, mh, __fmaf_rn(mhi, mh, -p));
+                    mhi = __fadd_rn(p, t);                        // renormalise (Fast2Sum, |p| >= |t|)
+                    mlo = __fsub_rn(t, __fsub_rn(mhi, p));
                 }
-                const double kd = ff_to_f64(khi, klo), md = ff_to_f64(mhi, mlo);
+                // the FP64 pipe runs at a small fraction of the FP32 rate: build the doubles with integer ops
+                const double kd = ff_to_f64_int(khi, klo), md = ff_to_f64_int(mhi, mlo);
                 if (K) {
                     K[pos.x] = kd;
                     if (pos.y != pos.x) K[pos.y] = kd;
