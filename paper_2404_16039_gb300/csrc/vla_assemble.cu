@@ -830,28 +830,8 @@ __device__ __forceinline__ void tile_pairs(double *__restrict__ K, double *__res
         const int2 ch = s_chk[c];
         const CT *cp = s_cod + ch.x + lane;
         if constexpr (MIX) {
-            unsigned long long h0 = 0ull, l0 = 0ull, h1 = 0ull, l1 = 0ull;   // (K, M) pairs, 2 chains
-            int tt = 0;
-            for (; tt + 1 < ch.y; tt += 2) {
-                const uint32_t c0 = cp[tt * 32], c1 = cp[(tt + 1) * 32];
-                const uint32_t e0 = elem_of(c0), e1 = elem_of(c1);
-                float k0, k1, m0, m1;
-                if constexpr (LIT) {
-                    const uint32_t u0 = c0 - e0 * C::RSC, u1 = c1 - e1 * C::RSC;
-                    k0 = s_k[e0 * C::RS + u0];
-                    k1 = s_k[e1 * C::RS + u1];
-                    m0 = s_k[e0 * C::RS + MO + u0];
-                    m1 = s_k[e1 * C::RS + MO + u1];
-                } else {   // the code is the entry's word offset
-                    k0 = s_k[c0];
-                    k1 = s_k[c1];
-                    m0 = s_k[e0 * C::RS + C::NU];
-                    m1 = s_k[e1 * C::RS + C::NU];
-                }
-                ff2_add(h0, l0, pk(k0, m0));
-                ff2_add(h1, l1, pk(k1, m1));
-            }
-            if (tt < ch.y) {
+            unsigned long long h0 = 0ull, l0 = 0ull;   // the (K, M) float-pair sums, packed
+            for (int tt = 0; tt < ch.y; ++tt) {
                 const uint32_t c0 = cp[tt * 32];
                 const uint32_t e0 = elem_of(c0);
                 float k0, m0;
@@ -859,15 +839,13 @@ __device__ __forceinline__ void tile_pairs(double *__restrict__ K, double *__res
                     const uint32_t u0 = c0 - e0 * C::RSC;
                     k0 = s_k[e0 * C::RS + u0];
                     m0 = s_k[e0 * C::RS + MO + u0];
-                } else {
+                } else {   // the code is the entry's word offset
                     k0 = s_k[c0];
                     m0 = s_k[e0 * C::RS + C::NU];
                 }
                 ff2_add(h0, l0, pk(k0, m0));
             }
             if (q < h.n_nz) {
-                ff2_add(h0, l0, h1);
-                ff2_add(h0, l0, l1);
                 // renormalise both sums at once: (hi, lo) <- TwoSum(hi, lo)
                 const unsigned long long s2 = add2(h0, l0);
                 const unsigned long long bb = sub2(s2, h0);

@@ -140,30 +140,24 @@ __device__ __forceinline__ double f32_to_f64_w(float x) {
 // integer significand construction).
 __device__ __forceinline__ double ff_to_f64(float hi, float lo) { return f32_to_f64_w(hi) + f32_to_f64_w(lo); }
 
-// hi + lo of a normalised float pair (|lo| <= ulp(hi)/2) as a double with
-// integer instructions only: hi is widened exactly, and lo's significand is
-// added to the widened bit pattern in units of the double ulp of hi,
-// d = m_lo * 2^(e_lo - e_hi + 29) (bits of lo below that ulp are dropped, so
-// the result is within one double ulp of hi + lo, and exact when lo's
-// exponent is within 29 of hi's).  Normalisation keeps d below 2^28, so the
-// addition never carries out of hi's significand; a subtraction borrows only
-// when hi is a power of two, where the result lies one binade lower and d
-// counts twice.  Zero or subnormal hi or lo and inf/nan take the FP64 path.
+// hi + lo of a normalised float pair (|lo| <= ulp(hi)/2) as a double without
+// the FP64 pipe: hi is widened exactly with integer instructions, and lo is
+// counted in units of the double ulp of hi, d = trunc(lo * 2^(52 - E_hi)) (one
+// exact power-of-two multiply carrying hi's sign, one float-to-int conversion;
+// |d| <= 2^28, so adding d to the widened bit pattern never carries out of
+// hi's significand).  When hi is a power of two and lo lowers it, the result
+// lies one binade down, where the ulp halves and d counts twice.  Bits of lo
+// below the double ulp of hi are dropped: the result is within one double ulp
+// of hi + lo.  hi below 2^-75, zero, subnormal, inf or nan takes the FP64 path.
 __device__ __forceinline__ double ff_to_f64_int(float hi, float lo) {
-    const uint32_t uh = __float_as_uint(hi), ul = __float_as_uint(lo);
-    const uint32_t eh = (uh >> 23) & 0xffu, el = (ul >> 23) & 0xffu, mh = uh & 0x7fffffu;
-    if (eh == 0u || eh == 0xffu || el == 0xffu || (el == 0u && (ul & 0x7fffffu) != 0u)) return ff_to_f64(hi, lo);
-    unsigned long long bits = ((unsigned long long)(uh >> 31) << 63) | ((unsigned long long)(eh + 896u) << 52) |
-                              ((unsigned long long)mh << 29);
-    if (el != 0u) {
-        const unsigned long long ml = (ul & 0x7fffffu) | 0x800000u;
-        const int s = (int)el - (int)eh + 29;
-        unsigned long long d = s >= 0 ? ml << s : (s > -32 ? ml >> (-s) : 0ull);
-        const bool opp = ((uh ^ ul) >> 31) != 0u;
-        if (opp && mh == 0u) d <<= 1;
-        bits = opp ? bits - d : bits + d;
-    }
-    return __longlong_as_double((long long)bits);
+    const uint32_t uh = __float_as_uint(hi), eh = (uh >> 23) & 0xffu;
+    if (eh < 52u || eh == 0xffu) return ff_to_f64(hi, lo);
+    const float scale = __uint_as_float((uh & 0x80000000u) | ((306u - eh) << 23));   // +-2^(52 - E_hi)
+    int d = __float2int_rz(__fmul_rn(lo, scale));
+    if ((uh & 0x7fffffu) == 0u && d < 0) d *= 2;
+    const unsigned long long bits = ((unsigned long long)(uh & 0x80000000u) << 32) |
+                                    (((unsigned long long)(uh & 0x7fffffffu) << 29) + (896ull << 52));
+    return __longlong_as_double((long long)(bits + (unsigned long long)(long long)d));
 }
 
 // ---------------------------------------------------------------------------
