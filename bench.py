@@ -32,9 +32,12 @@ request stream through the server), next (the rows beyond the assembly core,
 one timed call each on the bench mesh), small (p50/p99 latency of the FP64
 call with element pages on the 3,072-tet mesh).
 
-Multi-GPU (torchrun): every rank assembles its own copy of the workload on its
-own GPU (independent problems, no collective on the data path); the reported
-time is the max over ranks.
+Multi-GPU (torchrun): the one mesh is split by rows -- rank r of N owns the
+contiguous node rows [nn r / N, nn (r+1) / N) and assembles the sub-mesh of
+the elements touching them (halo elements duplicated), which gives it those
+rows of K and M complete; no collective on the data path (strong scaling,
+value = elements of the whole mesh / slowest rank's step time).  The
+reference arm runs on rank 0 alone.
 """
 from __future__ import annotations
 
@@ -141,8 +144,10 @@ def _dist():
         local = int(os.environ.get("LOCAL_RANK", "0"))
         cuda = torch.cuda.is_available()
         if cuda:
+            local %= torch.cuda.device_count()   # more ranks than GPUs only in a gloo check of this harness
             torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if cuda else "gloo")
+        # BENCH_DIST_BACKEND=gloo runs the harness without NCCL (a check of the multi-rank path on fewer GPUs)
+        dist.init_process_group(os.environ.get("BENCH_DIST_BACKEND") or ("nccl" if cuda else "gloo"))
         return dist, dist.get_rank(), ws, local
     return None, 0, 1, 0
 
@@ -164,6 +169,11 @@ def _max_over_ranks(dist, x):
 def _job_value(ws, units_per_rank, ms):
     """Whole-job throughput: every rank processes units_per_rank in (at most) ms."""
     return ws * units_per_rank / (ms * 1e-3)
+
+
+def _row_block(nn, rank, ws):
+    """The contiguous rows [r0, r1) rank `rank` of `ws` owns."""
+    return nn * rank // ws, nn * (rank + 1) // ws
 
 
 def _alg_bytes_per_el(ne, nn, nnz):
@@ -971,7 +981,10 @@ def main():
     coords = torch.from_numpy(m.coords).to(dev)
     elems = torch.from_numpy(m.elems).to(dev)
     faces = torch.from_numpy(m.faces).to(dev)
-    gm = vla.Mesh(coords, elems, faces)
+    # one row block per rank (strong scaling: the one mesh split by rows, halo elements duplicated,
+    # complete rows per rank, no collective on the data path); one rank takes every row
+    blk = _row_block(m.nn, rank, ws)
+    gm = vla.Mesh(coords, elems, faces, rows=None if ws == 1 else blk)
     K = torch.empty(gm.nnz, dtype=torch.float64, device=dev)
     M = torch.empty(gm.nnz, dtype=torch.float64, device=dev)
     vol = torch.empty(gm.ne, dtype=torch.float64, device=dev)
@@ -1010,7 +1023,7 @@ def main():
     asm_ms = [a.elapsed_time(b) for a, b, c in ev]
     ms = _max_over_ranks(dist, sum(step_ms) / len(step_ms))
     asm = sum(asm_ms) / len(asm_ms)
-    value = _job_value(ws, gm.ne, ms)
+    value = m.ne / (ms * 1e-3)   # every element of the one mesh, over the slowest rank's time
 
     # latency of the hot step over --latency-reps calls: device time with the L2
     # flushed before each (cold) and back to back (warm), and the host time of
@@ -1057,23 +1070,24 @@ def main():
         "ci": torch.empty(gm.nnz, dtype=torch.int32).pin_memory(),
     }
     h2d = hc.numel() * 8 + he.numel() * 4 + hf.numel() * 4
-    d2h = sum(t.numel() * t.element_size() for t in out_host.values())
+    rp_b, ci_b = gm.block()
+    d2h = rp_b.numel() * 4 + ci_b.numel() * (4 + 8 + 8) + gm.ne * 8 + gm.nfb * (3 * 8 + 8)   # what one rank copies
 
     def e2e_step():
         dc = hc.to(dev, non_blocking=True)
         de = he.to(dev, non_blocking=True)
         df = hf.to(dev, non_blocking=True)
-        g2 = vla.Mesh(dc, de, df)
+        g2 = vla.Mesh(dc, de, df, rows=None if ws == 1 else blk)
         o = g2.assemble(1.0, 1.0, precision=prec)
         n2, a2 = g2.boundary(precision=prec)
-        rp, ci = g2.csr()
-        out_host["K"].copy_(o["K"], non_blocking=True)
-        out_host["M"].copy_(o["M"], non_blocking=True)
-        out_host["vol"].copy_(o["vol"], non_blocking=True)
-        out_host["nrm"].copy_(n2, non_blocking=True)
-        out_host["ar"].copy_(a2, non_blocking=True)
-        out_host["rp"].copy_(rp, non_blocking=True)
-        out_host["ci"].copy_(ci, non_blocking=True)
+        rp, ci, kb, mb = g2.block((o["K"], o["M"]))
+        out_host["K"][: kb.numel()].copy_(kb, non_blocking=True)
+        out_host["M"][: mb.numel()].copy_(mb, non_blocking=True)
+        out_host["vol"][: g2.ne].copy_(o["vol"], non_blocking=True)
+        out_host["nrm"][: g2.nfb].copy_(n2, non_blocking=True)
+        out_host["ar"][: g2.nfb].copy_(a2, non_blocking=True)
+        out_host["rp"][: rp.numel()].copy_(rp, non_blocking=True)
+        out_host["ci"][: ci.numel()].copy_(ci, non_blocking=True)
         torch.cuda.synchronize()
         g2.close()
 
@@ -1085,7 +1099,7 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = _max_over_ranks(dist, (time.perf_counter() - t0) / args.e2e_steps)
-    e2e = {"value": ws * gm.ne / e2e_s, "unit": "elements/s", "h2d_bytes_per_step": int(h2d),
+    e2e = {"value": m.ne / e2e_s, "unit": "elements/s", "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
            "includes": "H2D of coords/elems/faces, mesh build (CSR pattern, tiles), assembly, boundary, "
                        "D2H of row_ptr/col_idx/K/M/vol/normals/areas"}
@@ -1118,9 +1132,12 @@ def main():
 
     line = {"metric": "elements/sec for P1 tet K+M to CSR", "value": value, "unit": "elements/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
             "dtype": "f32" if prec == vla.PREC_MIXED else "f64", "data": "synthetic",
-            "config": _config(m, MIXED_LABEL if prec else "fp64"),
+            "config": dict(_config(m, MIXED_LABEL if prec else "fp64"),
+                           parallelism=f"rows split in {ws} contiguous blocks, one per rank (halo elements "
+                                       f"duplicated, complete rows per rank, no collective on the data path)"
+                           if ws > 1 else "one GPU, every row"),
             "e2e": e2e, "roofline": roof, "gpu_launches": 2 * args.steps, "clocks": clocks,
             "p50_ms": latency["cold_l2"]["p50_ms"], "p99_ms": latency["cold_l2"]["p99_ms"], "latency": latency}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

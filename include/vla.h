@@ -302,6 +302,38 @@ vla_status vla_element_pages_static(int32_t dim, int32_t order, int64_t nn, int6
  * VLA_ERR_CUDA if the copy fails, VLA_OK otherwise. */
 vla_status vla_element_pages_static_check(int64_t *n_skipped, void *stream);
 
+/* Row-block partition for assembly on several GPUs (the data-parallel
+ * sharding of the Section 3.5 assembly: every element is independent, the
+ * CSR sum is the one exchange step).  A GPU that owns the contiguous rows
+ * [row_begin, row_end) needs every element with a node in that range; the
+ * elements shared with neighbouring blocks (the halo) are duplicated, so each
+ * GPU assembles complete rows and no reduction across GPUs is needed.
+ * vla_partition_rows writes the ascending ids of those elements (any node,
+ * P2 mid-edge nodes included, in the range) to elem_ids (device int32,
+ * capacity ne, may be NULL to count only) and their number to *n_elems
+ * (host).  elems: nlb x ne int32 as for vla_mesh_create (device); indices
+ * are compared, never dereferenced.  Synchronises `stream`.  Errors:
+ * VLA_ERR_INVALID_ARG for a NULL n_elems or elems, nlb outside [3, 10], ne
+ * outside [0, 2^31-1] or a range with row_begin < 0 or row_end < row_begin
+ * (an empty range gives 0 elements); VLA_ERR_CUDA if a launch or copy fails. */
+vla_status vla_partition_rows(int32_t nlb, int64_t ne, const int32_t *elems, int32_t row_begin, int32_t row_end,
+                              int32_t *elem_ids, int64_t *n_elems, void *stream);
+
+/* A mesh handle for one row block (Section 3.5 assembly split by rows, see
+ * vla_partition_rows): the sub-mesh of the elements with a node in
+ * [row_begin, row_end) and of the boundary facets whose smallest node lies in
+ * that range, with the global node numbering (coords and nn are the whole
+ * mesh's).  Rows [row_begin, row_end) of its CSR pattern and of the K and M
+ * values vla_assemble writes are exactly those rows of the whole mesh's
+ * (same columns, same summation order, same bits); its other rows are
+ * partial and belong to other blocks.  Arguments as vla_mesh_create plus the
+ * block.  Synchronises `stream`.  Errors: those of vla_mesh_create, and
+ * VLA_ERR_INVALID_ARG for a block that is empty, reaches outside [0, nn) or
+ * holds no element's node. */
+vla_status vla_mesh_create_rows(int32_t dim, int32_t order, int64_t nn, int64_t ne, const double *coords,
+                                const int32_t *elems, int64_t nfb, const int32_t *faces, int32_t row_begin,
+                                int32_t row_end, void *stream, vla_mesh **out);
+
 /* Every facet of the mesh once (the faces behind the paper's normals of all
  * faces and its face counts, Section 3.2): facet j of element k is opposite
  * local vertex j, with the element's other vertex nodes in local order; a

@@ -21,7 +21,7 @@ import torch
 
 __all__ = [
     "VlaError", "lib", "version", "amtam", "astam", "avtam", "amdet", "aminv", "amt", "avtav", "amsm", "amsv",
-    "smamt", "svamt", "Mesh", "element_pages_static", "static_skipped",
+    "smamt", "svamt", "Mesh", "element_pages_static", "static_skipped", "partition_rows",
     "Batch", "batch_assemble", "autotune", "tune_get", "tune_set", "Server", "PENDING", "quad_rule", "gi",
     "avtamav", "F32", "F64", "LAYOUT_PAGE", "LAYOUT_SOA", "PREC_FP64", "PREC_MIXED", "COEFF_POLY", "COEFF_EXP",
     "COEFF_POLY_IP", "COEFF_EXP_IP",
@@ -135,6 +135,8 @@ def lib():
         L.vla_element_pages_static.argtypes = [i32, i32, i64, i64, vp, vp, i32, dbl, dbl, i32, vp, vp, vp, vp, vp]
         L.vla_element_pages_static_check.argtypes = [C.POINTER(i64), vp]
         L.vla_mesh_check.argtypes = [vp, vp]
+        L.vla_partition_rows.argtypes = [i32, i64, vp, i32, i32, vp, C.POINTER(i64), vp]
+        L.vla_mesh_create_rows.argtypes = [i32, i32, i64, i64, vp, vp, i64, vp, i32, i32, vp, C.POINTER(vp)]
         L.vla_batch_create.argtypes = [C.POINTER(BatchJob), i32, i32, vp, i32, vp, C.POINTER(vp)]
         L.vla_batch_set_job.argtypes = [vp, i32, C.POINTER(BatchJob), vp]
         L.vla_batch_run.argtypes = [vp, vp]
@@ -160,7 +162,8 @@ def lib():
         L.vla_server_destroy.argtypes = [vp]
         for name in ("vla_amtam", "vla_astam", "vla_avtam", "vla_amdet", "vla_aminv", "vla_mesh_create",
                      "vla_mesh_info", "vla_mesh_csr", "vla_assemble", "vla_boundary", "vla_simplex_normals",
-                     "vla_mesh_destroy", "vla_element_pages_static", "vla_element_pages_static_check", "vla_mesh_check", "vla_batch_create",
+                     "vla_mesh_destroy", "vla_element_pages_static", "vla_element_pages_static_check", "vla_mesh_check",
+                     "vla_partition_rows", "vla_mesh_create_rows", "vla_batch_create",
                      "vla_batch_set_job", "vla_batch_run", "vla_batch_info", "vla_batch_check", "vla_batch_destroy",
                      "vla_batch_assemble", "vla_autotune", "vla_tune_get", "vla_tune_set", "vla_server_create",
                      "vla_server_submit", "vla_server_poll", "vla_server_release", "vla_server_stats",
@@ -418,7 +421,12 @@ class Mesh:
     (vla_mesh_create).  ``coords`` (nn, dim) float64 and ``elems`` (ne, nlb)
     int32 are CUDA tensors; ``faces`` (nfb, dim) int32 or None."""
 
-    def __init__(self, coords, elems, faces=None, order=1, stream=None):
+    def __init__(self, coords, elems, faces=None, order=1, stream=None, rows=None):
+        """``rows=(r0, r1)`` builds the sub-mesh of one row block instead
+        (vla_mesh_create_rows): the elements with a node in [r0, r1) and the
+        facets whose smallest node lies there, global node numbering; rows
+        [r0, r1) of its CSR and values are those of the whole mesh (see
+        ``block``).  Section 3.5 assembly split by rows."""
         _req(coords, torch.float64), _req(elems, torch.int32)
         if faces is not None:
             _req(faces, torch.int32)
@@ -428,8 +436,15 @@ class Mesh:
         ne = elems.shape[0]
         nfb = 0 if faces is None else faces.shape[0]
         h = C.c_void_p()
-        _check(lib().vla_mesh_create(dim, order, nn, ne, _p(coords), _p(elems), nfb, _p(faces), _stream(stream),
-                                     C.byref(h)))
+        if rows is None:
+            _check(lib().vla_mesh_create(dim, order, nn, ne, _p(coords), _p(elems), nfb, _p(faces), _stream(stream),
+                                         C.byref(h)))
+            self.rows = (0, nn)
+        else:
+            r0, r1 = int(rows[0]), int(rows[1])
+            _check(lib().vla_mesh_create_rows(dim, order, nn, ne, _p(coords), _p(elems), nfb, _p(faces), r0, r1,
+                                              _stream(stream), C.byref(h)))
+            self.rows = (r0, r1)
         self._h = h
         info = MeshInfo()
         _check(lib().vla_mesh_info(h, C.byref(info)))
@@ -456,6 +471,18 @@ class Mesh:
         ci = torch.empty(max(self.nnz, 1), dtype=torch.int32, device=self.device)
         _check(lib().vla_mesh_csr(self._h, _p(rp), _p(ci), _stream(stream)))
         return rp, ci[: self.nnz]
+
+    def block(self, values=(), stream=None):
+        """The CSR rows [r0, r1) this mesh owns (all rows for a whole mesh):
+        (row_ptr (r1 - r0 + 1, starting at 0), col_idx, and the same slice of
+        each tensor in ``values``, e.g. the K and M values of ``assemble``).
+        Views of the device tensors, no copy."""
+        r0, r1 = self.rows
+        rp, ci = self.csr(stream=stream)
+        a, b = int(rp[r0].item()), int(rp[r1].item())
+        for v in values:
+            _buf(v, self.nnz, torch.float64, self.device, "values")
+        return (rp[r0:r1 + 1] - a, ci[a:b]) + tuple(v[a:b] for v in values)
 
     def assemble(self, ca=1.0, cb=0.0, kind=COEFF_POLY, precision=PREC_MIXED, K=None, M=None, vol=None,
                  want_K=True, want_M=True, want_vol=True, pages=False, count_singular=False, stream=None):
@@ -564,6 +591,20 @@ class Mesh:
         out = torch.empty((self.ne, self.dim + 1, self.dim), dtype=torch.float64, device=self.device)
         _check(lib().vla_simplex_normals(self._h, _p(out), _stream(stream)))
         return out
+
+
+def partition_rows(elems, row_begin, row_end, stream=None):
+    """Ascending ids (int32 tensor) of the elements with a node in rows
+    [row_begin, row_end): the elements a GPU owning those rows assembles,
+    halo included (vla_partition_rows; synchronises).  Section 3.5 assembly
+    split by rows."""
+    _req(elems, torch.int32)
+    ne, nlb = elems.shape
+    ids = torch.empty(max(ne, 1), dtype=torch.int32, device=elems.device)
+    n = C.c_int64(0)
+    _check(lib().vla_partition_rows(nlb, ne, _p(elems), int(row_begin), int(row_end), _p(ids), C.byref(n),
+                                     _stream(stream)))
+    return ids[: n.value]
 
 
 def element_pages_static(coords, elems, order=1, ca=1.0, cb=0.0, kind=COEFF_POLY, precision=PREC_MIXED,

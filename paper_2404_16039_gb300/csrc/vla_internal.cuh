@@ -247,6 +247,7 @@ struct vla_mesh {
     int32_t spin_limit;           // bounded waits on bulk copies
     int32_t *d_err;               // device error word (bit 0: a bounded wait expired)
     int64_t device_bytes;
+    int32_t row_begin = 0, row_end = -1;   // a row-block sub-mesh (vla_mesh_create_rows): its complete rows
     cudaStream_t stream;
 
     double *coords;        // nn x dim

@@ -1491,3 +1491,162 @@ extern "C" vla_status vla_mesh_facets(const vla_mesh *m, int32_t *faces, int32_t
     if (n_boundary) *n_boundary = nb;
     return VLA_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Row-block partition (assembly on several GPUs by blocks of rows).  Every
+// element and every page is independent; the one exchange step is the CSR
+// sum.  A GPU that owns the contiguous rows [r0, r1) takes every element with
+// a node in that range -- the elements it shares with its neighbours (the
+// halo) are duplicated -- and so holds every contribution to its rows: it
+// assembles complete rows and no reduction across GPUs is needed.  Node
+// numbering stays global, so the rows [r0, r1) of the sub-mesh's CSR are the
+// rows [r0, r1) of the whole mesh's CSR, with the same summation order
+// (ascending element id) and therefore the same bits.
+// ---------------------------------------------------------------------------
+namespace vla {
+namespace {
+
+// flag[k] = 1 if element k has a node (vertex or P2 mid-edge node) in [r0, r1)
+__global__ void k_block_elem_flags(int64_t ne, int nlb, const int32_t *__restrict__ elems, int32_t r0, int32_t r1,
+                                   int32_t *__restrict__ flag) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t f = 0;
+        for (int j = 0; j < nlb; ++j) {
+            const int32_t v = elems[k * nlb + j];
+            f |= (v >= r0 && v < r1) ? 1 : 0;
+        }
+        flag[k] = f;
+    }
+}
+
+// flag[f] = 1 if the smallest node of facet f lies in [r0, r1): the facets are split among the blocks
+__global__ void k_block_facet_flags(int64_t nf, int dim, const int32_t *__restrict__ faces, int32_t r0, int32_t r1,
+                                    int32_t *__restrict__ flag) {
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nf; f += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = faces[f * dim];
+        for (int j = 1; j < dim; ++j) v = min(v, faces[f * dim + j]);
+        flag[f] = (v >= r0 && v < r1) ? 1 : 0;
+    }
+}
+
+__global__ void k_compact_flags(int64_t n, const int32_t *__restrict__ flag, const long long *__restrict__ pre,
+                                int32_t *__restrict__ ids) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        if (flag[k]) ids[pre[k]] = (int32_t)k;
+}
+
+// dst row i = src row ids[i] (rows of w int32)
+__global__ void k_gather_rows(int64_t n, int w, const int32_t *__restrict__ ids, const int32_t *__restrict__ src,
+                              int32_t *__restrict__ dst) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n * w; q += (int64_t)gridDim.x * blockDim.x)
+        dst[q] = src[(int64_t)ids[q / w] * w + q % w];
+}
+
+// ascending ids of the flagged items into a stream-ordered allocation; synchronises for the count
+vla_status select_flagged(int64_t n, const int32_t *flag, int32_t **ids, int64_t *count, cudaStream_t st) {
+    *ids = nullptr;
+    *count = 0;
+    long long *pre = nullptr;
+    VLA_CUDA(cudaMallocAsync(&pre, sizeof(long long) * (n + 1), st));
+    long long total = 0;
+    vla_status s = excl_scan<int32_t>(flag, n, pre, st, &total);
+    if (s == VLA_OK && total > 0) {
+        cudaError_t e = cudaMallocAsync(ids, sizeof(int32_t) * total, st);
+        if (e != cudaSuccess) s = cuda_fail(e, "partition ids");
+        else k_compact_flags<<<grid_for(n, 256), 256, 0, st>>>(n, flag, pre, *ids);
+    }
+    cudaFreeAsync(pre, st);
+    if (s == VLA_OK) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) s = cuda_fail(e, "partition compaction");
+    }
+    *count = total;
+    return s;
+}
+
+vla_status check_block(int64_t nn, int32_t row_begin, int32_t row_end) {
+    if (row_begin < 0 || row_end <= row_begin || (int64_t)row_end > nn)
+        return fail(VLA_ERR_INVALID_ARG, "row block [%d, %d) must be a non-empty range inside [0, %lld)", row_begin,
+                    row_end, (long long)nn);
+    return VLA_OK;
+}
+
+}  // namespace
+}  // namespace vla
+
+extern "C" vla_status vla_partition_rows(int32_t nlb, int64_t ne, const int32_t *elems, int32_t row_begin,
+                                         int32_t row_end, int32_t *elem_ids, int64_t *n_elems, void *stream) {
+    if (!n_elems) return fail(VLA_ERR_INVALID_ARG, "n_elems is NULL");
+    *n_elems = 0;
+    if (nlb < 3 || nlb > 10) return fail(VLA_ERR_INVALID_ARG, "nlb must be in [3, 10]");
+    if (ne < 0 || ne > 0x7fffffffll) return fail(VLA_ERR_INVALID_ARG, "ne must be in [0, 2^31-1]");
+    if (row_begin < 0 || row_end < row_begin) return fail(VLA_ERR_INVALID_ARG, "need 0 <= row_begin <= row_end");
+    if (ne == 0 || row_end == row_begin) return VLA_OK;
+    if (!elems) return fail(VLA_ERR_INVALID_ARG, "elems is NULL");
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *flag = nullptr, *ids = nullptr;
+    VLA_CUDA(cudaMallocAsync(&flag, sizeof(int32_t) * ne, st));
+    k_block_elem_flags<<<grid_for(ne, 256), 256, 0, st>>>(ne, nlb, elems, row_begin, row_end, flag);
+    int64_t cnt = 0;
+    vla_status s = select_flagged(ne, flag, &ids, &cnt, st);
+    if (s == VLA_OK && elem_ids && cnt > 0) {
+        cudaError_t e = cudaMemcpyAsync(elem_ids, ids, sizeof(int32_t) * cnt, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) s = cuda_fail(e, "partition copy");
+    }
+    cudaFreeAsync(flag, st);
+    if (ids) cudaFreeAsync(ids, st);
+    if (s == VLA_OK) *n_elems = cnt;
+    return s;
+}
+
+extern "C" vla_status vla_mesh_create_rows(int32_t dim, int32_t order, int64_t nn, int64_t ne, const double *coords,
+                                           const int32_t *elems, int64_t nfb, const int32_t *faces, int32_t row_begin,
+                                           int32_t row_end, void *stream, vla_mesh **out) {
+    if (!out) return fail(VLA_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (dim != 2 && dim != 3) return fail(VLA_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (order != VLA_P1 && order != VLA_P2) return fail(VLA_ERR_INVALID_ARG, "order must be VLA_P1 or VLA_P2");
+    if (nn < 1 || nn > 0x7fffffffll || ne < 1 || ne > 0x7fffffffll || nfb < 0 || nfb > 0x7fffffffll)
+        return fail(VLA_ERR_INVALID_ARG, "need 1 <= nn, ne < 2^31 and 0 <= nfb < 2^31");
+    TRY(check_block(nn, row_begin, row_end));
+    if (!coords || !elems || (nfb > 0 && !faces)) return fail(VLA_ERR_INVALID_ARG, "null mesh array");
+    const int nlb = order == VLA_P1 ? dim + 1 : (dim + 1) * (dim + 2) / 2;
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t *flag = nullptr, *ids = nullptr, *sub = nullptr, *fflag = nullptr, *fids = nullptr, *fsub = nullptr;
+    int64_t nes = 0, nfs = 0;
+    vla_status s = VLA_OK;
+    auto ck = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && s == VLA_OK) s = cuda_fail(e, what);
+    };
+    ck(cudaMallocAsync(&flag, sizeof(int32_t) * ne, st), "partition flags");
+    if (s == VLA_OK) {
+        k_block_elem_flags<<<grid_for(ne, 256), 256, 0, st>>>(ne, nlb, elems, row_begin, row_end, flag);
+        s = select_flagged(ne, flag, &ids, &nes, st);
+    }
+    if (s == VLA_OK && nes == 0)
+        s = fail(VLA_ERR_INVALID_ARG, "no element has a node in rows [%d, %d)", row_begin, row_end);
+    if (s == VLA_OK) {
+        ck(cudaMallocAsync(&sub, sizeof(int32_t) * nes * nlb, st), "sub-mesh elements");
+        if (s == VLA_OK) k_gather_rows<<<grid_for(nes * nlb, 256), 256, 0, st>>>(nes, nlb, ids, elems, sub);
+    }
+    if (s == VLA_OK && nfb > 0) {
+        ck(cudaMallocAsync(&fflag, sizeof(int32_t) * nfb, st), "partition facet flags");
+        if (s == VLA_OK) {
+            k_block_facet_flags<<<grid_for(nfb, 256), 256, 0, st>>>(nfb, dim, faces, row_begin, row_end, fflag);
+            s = select_flagged(nfb, fflag, &fids, &nfs, st);
+        }
+        if (s == VLA_OK && nfs > 0) {
+            ck(cudaMallocAsync(&fsub, sizeof(int32_t) * nfs * dim, st), "sub-mesh facets");
+            if (s == VLA_OK) k_gather_rows<<<grid_for(nfs * dim, 256), 256, 0, st>>>(nfs, dim, fids, faces, fsub);
+        }
+    }
+    if (s == VLA_OK) ck(cudaGetLastError(), "partition gather");
+    if (s == VLA_OK) s = mesh_create_budget(dim, order, nn, nes, coords, sub, nfs, fsub, stream, 0, out);
+    for (int32_t *p : {flag, ids, sub, fflag, fids, fsub})
+        if (p) cudaFreeAsync(p, st);
+    if (s == VLA_OK) {
+        (*out)->row_begin = row_begin;
+        (*out)->row_end = row_end;
+    }
+    return s;
+}

@@ -131,6 +131,20 @@ def test_remaining_entry_points_validate_without_gpu(libpath):
     assert lib.vla_element_pages_static(3, 1, 1 << 20, 10, fake, fake, 0, 1.0, 0.0, 1,
                                         None, None, None, None, None) == BUDGET
 
+    lib.vla_partition_rows.argtypes = [i32, i64, vp, i32, i32, vp, ctypes.POINTER(i64), vp]
+    n = i64(-1)
+    assert lib.vla_partition_rows(4, 10, fake, 0, 5, None, None, None) == INVALID          # no count output
+    assert lib.vla_partition_rows(11, 10, fake, 0, 5, None, ctypes.byref(n), None) == INVALID
+    assert lib.vla_partition_rows(4, 10, fake, 5, 2, None, ctypes.byref(n), None) == INVALID
+    assert lib.vla_partition_rows(4, 10, fake, 3, 3, None, ctypes.byref(n), None) == 0 and n.value == 0
+    lib.vla_mesh_create_rows.argtypes = [i32, i32, i64, i64, vp, vp, i64, vp, i32, i32, vp, ctypes.POINTER(vp)]
+    hm = vp()
+    for r0, r1 in ((-1, 3), (3, 3), (0, 11)):
+        assert lib.vla_mesh_create_rows(3, 1, 10, 4, fake, fake, 0, None, r0, r1, None, ctypes.byref(hm)) == INVALID
+    assert lib.vla_mesh_create_rows(4, 1, 10, 4, fake, fake, 0, None, 0, 5, None, ctypes.byref(hm)) == INVALID
+    assert lib.vla_mesh_create_rows(3, 1, 10, 4, None, fake, 0, None, 0, 5, None, ctypes.byref(hm)) == INVALID
+    lib.vla_element_pages_static_check.argtypes = [ctypes.POINTER(i64), vp]
+
     lib.vla_batch_create.argtypes = [vp, i32, i32, vp, i32, vp, ctypes.POINTER(vp)]
     lib.vla_batch_assemble.argtypes = [vp, i32, i32, vp, vp]
     h = vp()
