@@ -619,6 +619,7 @@ def run_serve(args):
         els = [0] * count
         bsz = [0] * count
         phases = [None] * count
+        ingest = [None] * count
         fails = {}
         h2d = [0]
         d2h = [0] * n_poll
@@ -642,6 +643,9 @@ def run_serve(args):
                     th = time.monotonic()
                     phases[i] = (res.t_admit - res.t_submit, res.t_ready - res.t_admit, res.t_start - res.t_ready,
                                  res.t_done - res.t_start, th - res.t_done)
+                    if res.new_mesh:
+                        ingest[i] = (res.t_ingest - res.t_admit, res.h2d_ms * 1e-3, res.build_ms * 1e-3,
+                                     res.t_ready - res.t_ingest - (res.h2d_ms + res.build_ms) * 1e-3)
                     lat[i] = res.t_done - t_arr[i]
                     lat_host[i] = th - t_arr[i]
                     els[i] = res.ne
@@ -679,6 +683,10 @@ def run_serve(args):
                 "mean_batch": float(np.mean([bsz[i] for i in ok])), "max_batch": int(max(bsz[i] for i in ok)),
                 "mean_phase_ms": dict(zip(("queued", "ingest", "wait_launch", "assembly", "copy_out"),
                                           (1e3 * float(np.mean([phases[i][c] for i in ok])) for c in range(5)))),
+                "ingest_split_ms": dict(zip(("wait_for_ingest_thread", "h2d_device", "build_device",
+                                             "build_host_rest"),
+                                            (1e3 * float(np.mean([ingest[i][c] for i in ok if ingest[i]]))
+                                             for c in range(4)))) if any(ingest[i] for i in ok) else None,
                 "batches": st["n_batches"], "ingested": st["n_ingested"], "reused": st["n_reused"],
                 "evicted": st["n_evicted"], "peak_bytes": st["peak_bytes"], "h2d_bytes": h2d[0], "d2h_bytes": sum(d2h)}
 
@@ -1073,14 +1081,28 @@ def main():
     rp_b, ci_b = gm.block()
     d2h = rp_b.numel() * 4 + ci_b.numel() * (4 + 8 + 8) + gm.ne * 8 + gm.nfb * (3 * 8 + 8)   # what one rank copies
 
+    split = []
+
     def e2e_step():
+        # CUDA events between the phases and the host clock around each, to itemise the step
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+        th = [time.perf_counter()]
+        ev[0].record(stream)
         dc = hc.to(dev, non_blocking=True)
         de = he.to(dev, non_blocking=True)
         df = hf.to(dev, non_blocking=True)
-        g2 = vla.Mesh(dc, de, df, rows=None if ws == 1 else blk)
+        ev[1].record(stream)
+        th.append(time.perf_counter())
+        g2 = vla.Mesh(dc, de, df, rows=None if ws == 1 else blk)   # the build synchronises the stream
+        ev[2].record(stream)
+        th.append(time.perf_counter())
         o = g2.assemble(1.0, 1.0, precision=prec)
+        ev[3].record(stream)
         n2, a2 = g2.boundary(precision=prec)
+        ev[4].record(stream)
         rp, ci, kb, mb = g2.block((o["K"], o["M"]))
+        ev[5].record(stream)
+        th.append(time.perf_counter())
         out_host["K"][: kb.numel()].copy_(kb, non_blocking=True)
         out_host["M"][: mb.numel()].copy_(mb, non_blocking=True)
         out_host["vol"][: g2.ne].copy_(o["vol"], non_blocking=True)
@@ -1088,21 +1110,31 @@ def main():
         out_host["ar"][: g2.nfb].copy_(a2, non_blocking=True)
         out_host["rp"][: rp.numel()].copy_(rp, non_blocking=True)
         out_host["ci"][: ci.numel()].copy_(ci, non_blocking=True)
+        ev[6].record(stream)
         torch.cuda.synchronize()
+        th.append(time.perf_counter())
         g2.close()
+        names = ("h2d", "mesh_build", "assemble", "boundary", "csr_pattern_out", "d2h")
+        split.append({"device_ms": {n: ev[i].elapsed_time(ev[i + 1]) for i, n in enumerate(names)},
+                      "host_ms": {"h2d_enqueue": (th[1] - th[0]) * 1e3, "mesh_build_call": (th[2] - th[1]) * 1e3,
+                                  "assemble_boundary_csr_enqueue": (th[3] - th[2]) * 1e3,
+                                  "d2h_and_sync": (th[4] - th[3]) * 1e3}})
 
     e2e_step()
     _barrier(dist)
     torch.cuda.synchronize()
+    split.clear()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         e2e_step()
     torch.cuda.synchronize()
     e2e_s = _max_over_ranks(dist, (time.perf_counter() - t0) / args.e2e_steps)
+    e2e_split = {kind: {n: float(np.median([d[kind][n] for d in split])) for n in split[0][kind]}
+                 for kind in ("device_ms", "host_ms")}
     e2e = {"value": m.ne / e2e_s, "unit": "elements/s", "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
            "includes": "H2D of coords/elems/faces, mesh build (CSR pattern, tiles), assembly, boundary, "
-                       "D2H of row_ptr/col_idx/K/M/vol/normals/areas"}
+                       "D2H of row_ptr/col_idx/K/M/vol/normals/areas", "split": e2e_split}
 
     peaks, src = _peaks()
     bpe = _alg_bytes_per_el(gm.ne, gm.nn, gm.nnz)

@@ -610,6 +610,8 @@ typedef struct {
     const double *K_vals, *M_vals, *vol;   /* device; valid until vla_server_release */
     const int32_t *row_ptr, *col_idx;      /* device CSR pattern of the mesh; same lifetime */
     double t_submit, t_admit, t_ready, t_start, t_done;   /* CLOCK_MONOTONIC seconds */
+    double t_ingest;           /* when an ingest thread took the request (0 if it reused a mesh) */
+    double h2d_ms, build_ms;   /* device time of its input copy and of its mesh build (0 if reused) */
 } vla_result_t;
 
 typedef struct {

@@ -86,7 +86,8 @@ class Result(C.Structure):
                 ("reserved", C.c_int32), ("batch_id", C.c_int64), ("nn", C.c_int64), ("ne", C.c_int64),
                 ("nnz", C.c_int64), ("K_vals", C.c_void_p), ("M_vals", C.c_void_p), ("vol", C.c_void_p),
                 ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p), ("t_submit", C.c_double),
-                ("t_admit", C.c_double), ("t_ready", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double)]
+                ("t_admit", C.c_double), ("t_ready", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
+                ("t_ingest", C.c_double), ("h2d_ms", C.c_double), ("build_ms", C.c_double)]
 
 
 class ServerStats(C.Structure):

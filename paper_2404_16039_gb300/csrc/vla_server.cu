@@ -54,6 +54,7 @@ struct SReq {
     int64_t out_charged = 0;
     vla_status status = VLA_OK;
     double t_submit = 0, t_admit = 0, t_ready = 0, t_start = 0, t_done = 0;
+    double t_ingest = 0, h2d_ms = 0, build_ms = 0;   // ingest split: pickup time, device copy and build
     int32_t batch_size = 0;
     int64_t batch_id = -1;
     bool holds_mesh = false;   // counted in m->refs
@@ -353,6 +354,7 @@ void ingest_worker(vla_server *s) {
         s->ingest_q.pop_front();
         SMesh *sm = q->m;
         const vla_request_t r = q->r;
+        q->t_ingest = now_s();
         lk.unlock();
         // H2D of the request's arrays into stream-ordered staging, then the device build
         const size_t cb = sizeof(double) * r.dim * r.nn, eb = sizeof(int32_t) * nlb_of(r.dim, r.order) * r.ne,
@@ -365,6 +367,13 @@ void ingest_worker(vla_server *s) {
             stage = nullptr;
             st = fail(VLA_ERR_OOM, "server staging: out of device memory");
         }
+        cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+        for (auto &e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                e = nullptr;
+            }
+        if (ev[0]) cudaEventRecord(ev[0], ws);
         if (st == VLA_OK) {
             unsigned char *p = static_cast<unsigned char *>(stage);
             double *dc = reinterpret_cast<double *>(p);
@@ -375,13 +384,27 @@ void ingest_worker(vla_server *s) {
                 (fb && cudaMemcpyAsync(df, r.faces, fb, cudaMemcpyDefault, ws) != cudaSuccess)) {
                 st = cuda_fail(cudaGetLastError(), "server input copy");
             } else {
+                if (ev[1]) cudaEventRecord(ev[1], ws);
                 st = vla_mesh_create(r.dim, r.order, r.nn, r.ne, dc, de, r.nfb, fb ? df : nullptr, ws, &mesh);
+                if (ev[2]) cudaEventRecord(ev[2], ws);
             }
         }
         if (stage) cudaFreeAsync(stage, ws);
         cudaStreamSynchronize(ws);
+        float h2d_ms = 0.f, build_ms = 0.f;
+        if (st == VLA_OK && ev[0] && ev[1] && ev[2]) {
+            if (cudaEventElapsedTime(&h2d_ms, ev[0], ev[1]) != cudaSuccess ||
+                cudaEventElapsedTime(&build_ms, ev[1], ev[2]) != cudaSuccess) {
+                cudaGetLastError();
+                h2d_ms = build_ms = 0.f;
+            }
+        }
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
         lk.lock();
         ++s->n_ingested;
+        q->h2d_ms = h2d_ms;
+        q->build_ms = build_ms;
         sm->building = false;
         s->used -= sm->charged;
         if (st == VLA_OK) {
@@ -506,6 +529,9 @@ extern "C" vla_status vla_server_poll(vla_server *s, int64_t ticket, double time
         res->t_ready = q->t_ready;
         res->t_start = q->t_start;
         res->t_done = q->t_done;
+        res->t_ingest = q->t_ingest;
+        res->h2d_ms = q->h2d_ms;
+        res->build_ms = q->build_ms;
         if (q->state == DONE) {
             const vla_mesh *m = q->m->mesh;
             res->nn = m->nn;
