@@ -1129,29 +1129,52 @@ inline size_t mesh_record_bytes(const vla_mesh *m, bool mix, bool lit = false) {
 // (and graphs) of any size up to it stay valid.
 template <bool MIX, int TYPES, bool BATCH, bool LIT = false>
 vla_status kernel_shape(size_t smem, int ctas_per_sm, int n_work, int *grid) {
+    // the occupancy answer per (device, shared memory) is cached: the host
+    // latency of a call on a small mesh is otherwise dominated by the queries
+    struct Shape {
+        int dev;
+        size_t smem;
+        int per_sm, nsm;
+    };
     static std::mutex mu;
     static bool ready[64] = {};
-    int dev = 0, maxsm = 0, nsm = 0;
+    static std::vector<Shape> cache;
+    int dev = 0;
     VLA_CUDA(cudaGetDevice(&dev));
-    VLA_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    VLA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-    auto kern = k_assemble<MIX, TYPES, BATCH, LIT>;
-    cudaFuncAttributes fa;
-    VLA_CUDA(cudaFuncGetAttributes(&fa, kern));
-    if (smem + fa.sharedSizeBytes > (size_t)maxsm)
-        return fail(VLA_ERR_UNSUPPORTED, "assembly tile needs %zu bytes of shared memory (limit %d)",
-                    smem + fa.sharedSizeBytes, maxsm);
+    int per_sm = -1, nsm = 0;
     {
         std::lock_guard<std::mutex> lk(mu);
-        if (dev < 0 || dev >= 64 || !ready[dev]) {
-            VLA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          maxsm - (int)fa.sharedSizeBytes));
-            if (dev >= 0 && dev < 64) ready[dev] = true;
-        }
+        for (const Shape &c : cache)
+            if (c.dev == dev && c.smem == smem) {
+                per_sm = c.per_sm;
+                nsm = c.nsm;
+                break;
+            }
     }
-    int per_sm = 0;
-    VLA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-    if (per_sm < 1) per_sm = 1;
+    if (per_sm < 0) {
+        int maxsm = 0;
+        VLA_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        VLA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        auto kern = k_assemble<MIX, TYPES, BATCH, LIT>;
+        cudaFuncAttributes fa;
+        VLA_CUDA(cudaFuncGetAttributes(&fa, kern));
+        if (smem + fa.sharedSizeBytes > (size_t)maxsm)
+            return fail(VLA_ERR_UNSUPPORTED, "assembly tile needs %zu bytes of shared memory (limit %d)",
+                        smem + fa.sharedSizeBytes, maxsm);
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (dev < 0 || dev >= 64 || !ready[dev]) {
+                VLA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              maxsm - (int)fa.sharedSizeBytes));
+                if (dev >= 0 && dev < 64) ready[dev] = true;
+            }
+        }
+        per_sm = 0;
+        VLA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+        if (per_sm < 1) per_sm = 1;
+        std::lock_guard<std::mutex> lk(mu);
+        if (cache.size() < 4096) cache.push_back(Shape{dev, smem, per_sm, nsm});
+    }
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     int g = nsm * per_sm;
     if (g > n_work) g = n_work;
