@@ -598,9 +598,12 @@ __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e
         if (threadIdx.x == 0) atomicOr(err, 32);
         return;
     }
-    for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
-        const int32_t i = perm[r];
-        for (int32_t q = n2e_ptr[i]; q < n2e_ptr[i + 1]; ++q) hset_insert(hs, He, n2e[q] >> 4);
+    {   // one warp per row, its lanes over the row's incidence list (a set: the order does not matter)
+        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int r = rb + (threadIdx.x >> 5); r < re; r += nw) {
+            const int32_t i = perm[r];
+            for (int32_t q = n2e_ptr[i] + lane; q < n2e_ptr[i + 1]; q += 32) hset_insert(hs, He, n2e[q] >> 4);
+        }
     }
     __syncthreads();
     const int n_el = hset_compact(hs, He, ce);
@@ -987,8 +990,9 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     // ---- node -> element incidence (sorted by element)
     long long *pre;
     TRY(S.get(&pre, nn + 1));
-    long long n2e_total = 0;
-    TRY(excl_scan<int32_t>(cnt, nn, pre, st, &n2e_total));
+    // every element of a validated mesh puts each of its nlb nodes in one incidence list: no count to read back
+    const long long n2e_total = (long long)ne * nlb;
+    TRY(excl_scan<int32_t>(cnt, nn, pre, st, nullptr));
     TRY(dalloc(m, &m->n2e_ptr, nn + 1, st));
     TRY(dalloc(m, &m->n2e, n2e_total, st));
     k_i64_to_i32<<<grid_for(nn + 1, TB, 1 << 30), TB, 0, st>>>(nn + 1, pre, m->n2e_ptr);
