@@ -369,16 +369,100 @@ __global__ void k_page_bcast_rc(int op, int64_t N, int soa, int other, const T *
     }
 }
 
+int num_sms();
+
+// Page-major pages of compile-time shape R x CC through shared memory.  A
+// page-major page is R*CC contiguous words, so one page per thread reads and
+// writes with a stride of a whole page per lane (one cache line per page per
+// warp access, L1-wavefront bound).  Here the block reads its PB pages with
+// consecutive threads on consecutive words, keeps them at a per-page stride of
+// R*CC + 1 words (odd: the page reads of a warp fall on distinct banks), each
+// thread forms its result page from there into a second area (stride
+// OUT + 1), and the block writes the result pages back with consecutive words.
+// `div_in`/`div_out` are ceil(2^32 / size) for the page index of a word by one
+// multiply-high (exact for words below 2^32 / size).
+template <typename T, int R, int CC>
+__global__ void __launch_bounds__(512 / sizeof(T)) k_page_bcast_staged(int op, int64_t N, int other,
+                                                                      const T *__restrict__ A,
+                                                                      const T *__restrict__ S, T *__restrict__ C,
+                                                                      uint32_t div_out) {
+    constexpr int PB = 512 / sizeof(T), IN = R * CC, INS = IN + 1;
+    constexpr uint32_t DIV_IN = (uint32_t)((0x100000000ull + IN - 1) / IN);
+    const int OUT = R * other, OUTS = OUT + 1;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sa = reinterpret_cast<T *>(smraw);
+    T *sc = sa + PB * INS;
+    const int t = threadIdx.x;
+    for (int64_t k0 = (int64_t)blockIdx.x * PB; k0 < N; k0 += (int64_t)gridDim.x * PB) {
+        const int np = (int)(N - k0 < PB ? N - k0 : PB);
+        const T *src = A + k0 * IN;
+        for (int f = t; f < np * IN; f += PB) {
+            const int pg = (int)__umulhi((uint32_t)f, DIV_IN);
+            sa[pg * INS + (f - pg * IN)] = src[f];
+        }
+        __syncthreads();
+        if (t < np) {
+            T a[IN];
+#pragma unroll
+            for (int e = 0; e < IN; ++e) a[e] = sa[t * INS + e];
+            T *out = sc + t * OUTS;
+            if (op == kSmamt) {   // S (other x CC) times the transposed page: other x R
+                for (int i = 0; i < other; ++i) {
+                    T srow[CC];
+#pragma unroll
+                    for (int r = 0; r < CC; ++r) srow[r] = __ldg(S + i + r * other);
+#pragma unroll
+                    for (int j = 0; j < R; ++j) {
+                        T acc = 0;
+#pragma unroll
+                        for (int r = 0; r < CC; ++r) acc += srow[r] * a[j + r * R];
+                        out[i + j * other] = acc;
+                    }
+                }
+            } else {   // amsm / amsv: the page (R x CC) times S (CC x other): R x other
+                for (int j = 0; j < other; ++j) {
+                    T scol[CC];
+#pragma unroll
+                    for (int r = 0; r < CC; ++r) scol[r] = __ldg(S + r + j * CC);
+#pragma unroll
+                    for (int i = 0; i < R; ++i) {
+                        T acc = 0;
+#pragma unroll
+                        for (int r = 0; r < CC; ++r) acc += a[i + r * R] * scol[r];
+                        out[i + j * R] = acc;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        T *dst = C + k0 * OUT;
+        for (int f = t; f < np * OUT; f += PB) {
+            const int pg = (int)__umulhi((uint32_t)f, div_out);
+            dst[f] = sc[pg * OUTS + (f - pg * OUT)];
+        }
+        __syncthreads();   // the next pages overwrite both areas
+    }
+}
+
 // launches the register-page kernel when the page shape is one of the
 // instantiated ones (rows 1-3; columns 2, 3, 4, 6, 10: vertices, P2 nodes and
 // the quadrature points of the Section 3.4/3.5 uses); false otherwise
 template <typename T>
 bool launch_bcast_rc(int op, int64_t N, int soa, int R, int CC, int other, const T *A, const T *S, T *C, int g,
                      cudaStream_t st) {
-#define VLA_RC(r_, c_)                                                                            \
-    if (R == r_ && CC == c_) {                                                                    \
-        k_page_bcast_rc<T, r_, c_><<<g, 256, 0, st>>>(op, N, soa, other, A, S, C);                \
-        return true;                                                                              \
+    // page-major pages go through shared memory (see k_page_bcast_staged); SoA pages are coalesced as they are
+    constexpr int PB = 512 / sizeof(T);
+    const int OUT = R * other;
+    const uint32_t div_out = (uint32_t)((0x100000000ull + OUT - 1) / OUT);
+    const size_t smem = (size_t)PB * ((size_t)R * CC + 1 + OUT + 1) * sizeof(T);
+    const int gs = grid_for(N, PB, (int64_t)num_sms() * 16);
+#define VLA_RC(r_, c_)                                                                               \
+    if (R == r_ && CC == c_) {                                                                       \
+        if (soa)                                                                                     \
+            k_page_bcast_rc<T, r_, c_><<<g, 256, 0, st>>>(op, N, soa, other, A, S, C);               \
+        else                                                                                         \
+            k_page_bcast_staged<T, r_, c_><<<gs, PB, smem, st>>>(op, N, other, A, S, C, div_out);    \
+        return true;                                                                                 \
     }
 #define VLA_RC_ROW(r_) VLA_RC(r_, 2) VLA_RC(r_, 3) VLA_RC(r_, 4) VLA_RC(r_, 6) VLA_RC(r_, 10)
     VLA_RC_ROW(1) VLA_RC_ROW(2) VLA_RC_ROW(3)
