@@ -488,10 +488,12 @@ __global__ void k_tile_assign(int64_t nn, const int32_t *__restrict__ flag, cons
 // per-tile sets (one CTA per tile)
 // ---------------------------------------------------------------------------
 // Thread t handles the indices t, t + blockDim.x, ...; a stage of distance
-// j < 32 pairs index i with i ^ j, handled by thread t ^ j of the same warp,
-// so the stages that follow one another at distances below 32 need only a
-// warp barrier (blockDim.x is a multiple of 32); a block barrier precedes
-// every stage of distance 32 and more, and ends the sort.
+// j < 32 pairs index i with i ^ j, handled by thread t ^ j of the same warp.
+// Between two consecutive stages that both have distances below 32 every
+// element is written and read within one warp, so a warp barrier suffices
+// (blockDim.x is a multiple of 32); after a stage of distance 32 or more, and
+// before one, elements cross warps and the block synchronises.  A block
+// barrier also ends the sort.
 __device__ void bitonic_sort(int32_t *a, int n /* power of two */) {
     for (int k = 2; k <= n; k <<= 1)
         for (int j = k >> 1; j > 0; j >>= 1) {
@@ -507,7 +509,7 @@ __device__ void bitonic_sort(int32_t *a, int n /* power of two */) {
                 }
             }
             const int next = j > 1 ? j >> 1 : k;   // distance of the next stage (the next k's first is k)
-            if (next < 32) __syncwarp();
+            if (j < 32 && next < 32) __syncwarp();
             else __syncthreads();
         }
     __syncthreads();
