@@ -396,9 +396,19 @@ __global__ void __launch_bounds__(512 / sizeof(T)) k_page_bcast_staged(int op, i
     for (int64_t k0 = (int64_t)blockIdx.x * PB; k0 < N; k0 += (int64_t)gridDim.x * PB) {
         const int np = (int)(N - k0 < PB ? N - k0 : PB);
         const T *src = A + k0 * IN;
-        for (int f = t; f < np * IN; f += PB) {
-            const int pg = (int)__umulhi((uint32_t)f, DIV_IN);
-            sa[pg * INS + (f - pg * IN)] = src[f];
+        {   // IN words per thread, all loads in flight before the first store
+            T v[IN];
+#pragma unroll
+            for (int q = 0; q < IN; ++q) {
+                const int f = t + q * PB;
+                v[q] = f < np * IN ? src[f] : T(0);
+            }
+#pragma unroll
+            for (int q = 0; q < IN; ++q) {
+                const int f = t + q * PB;
+                const int pg = (int)__umulhi((uint32_t)f, DIV_IN);
+                if (f < np * IN) sa[pg * INS + (f - pg * IN)] = v[q];
+            }
         }
         __syncthreads();
         if (t < np) {
@@ -450,7 +460,10 @@ __global__ void __launch_bounds__(512 / sizeof(T)) k_page_bcast_staged(int op, i
 template <typename T>
 bool launch_bcast_rc(int op, int64_t N, int soa, int R, int CC, int other, const T *A, const T *S, T *C, int g,
                      cudaStream_t st) {
-    // page-major pages go through shared memory (see k_page_bcast_staged); SoA pages are coalesced as they are
+    // page-major pages of the matrix products go through shared memory (see k_page_bcast_staged;
+    // amsm 0.28 -> 0.40, smamt 0.37 -> 0.68 of HBM on 1e7 3x4 pages); SoA pages are coalesced as they are, and
+    // the matrix-vector forms (other == 1: amsv, svamt) read a page's few outputs faster one page per thread
+    // (0.79 against 0.62 staged)
     constexpr int PB = 512 / sizeof(T);
     const int OUT = R * other;
     const uint32_t div_out = (uint32_t)((0x100000000ull + OUT - 1) / OUT);
@@ -458,7 +471,7 @@ bool launch_bcast_rc(int op, int64_t N, int soa, int R, int CC, int other, const
     const int gs = grid_for(N, PB, (int64_t)num_sms() * 16);
 #define VLA_RC(r_, c_)                                                                               \
     if (R == r_ && CC == c_) {                                                                       \
-        if (soa)                                                                                     \
+        if (soa || other == 1)                                                                       \
             k_page_bcast_rc<T, r_, c_><<<g, 256, 0, st>>>(op, N, soa, other, A, S, C);               \
         else                                                                                         \
             k_page_bcast_staged<T, r_, c_><<<gs, PB, smem, st>>>(op, N, other, A, S, C, div_out);    \
