@@ -235,9 +235,10 @@ __global__ void __launch_bounds__(kSegWarps * 32) k_sort_segments(int64_t n, con
 }
 
 // CSR row sets, one warp per row: every node of every incident element goes
-// into a 512-slot hash set in shared memory (a row longer than kMaxRow is an
-// error, so a set of more than 256 keys is never needed), then the keys are
-// sorted by a warp bitonic sort and written to the row's scratch slot.
+// into a hash set in shared memory of at least twice as many slots as
+// candidates, up to 512 (a row longer than kMaxRow is an error, so a set of
+// more than 256 keys is never needed), then the keys are sorted by a warp
+// bitonic sort and written to the row's scratch slot.
 constexpr int kRowWarps = 8, kRowHash = 512;
 __global__ void __launch_bounds__(kRowWarps * 32) k_row_count(int64_t nn, int nlb, const int32_t *__restrict__ elems,
                                                               const int32_t *__restrict__ n2e_ptr,
@@ -250,23 +251,26 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_row_count(int64_t nn, int nl
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int32_t *tab = hs[w], *ks = key[w];
     for (int64_t i = (int64_t)blockIdx.x * kRowWarps + w; i < nn; i += (int64_t)gridDim.x * kRowWarps) {
-        for (int q = lane; q < kRowHash; q += 32) tab[q] = -1;
-        if (lane == 0) cnt[w] = 0;
-        __syncwarp();
         const int32_t b = n2e_ptr[i], e = n2e_ptr[i + 1];
         const int ncand = (e - b) * nlb;
+        // a table of at least twice the candidates (at most kRowHash): the set never fills past half
+        int H = 32;
+        while (H < 2 * ncand && H < kRowHash) H <<= 1;
+        for (int q = lane; q < H; q += 32) tab[q] = -1;
+        if (lane == 0) cnt[w] = 0;
+        __syncwarp();
         for (int c = lane; c < ncand; c += 32) {
             const int64_t k = (int64_t)(n2e[b + c / nlb] >> 4);
             const int32_t x = elems[k * nlb + (c % nlb)];
-            uint32_t h = ((uint32_t)x * 2654435761u) & (kRowHash - 1);
-            for (int probe = 0; probe < kRowHash; ++probe) {
+            uint32_t h = ((uint32_t)x * 2654435761u) & (uint32_t)(H - 1);
+            for (int probe = 0; probe < H; ++probe) {
                 const int32_t prev = atomicCAS(&tab[h], -1, x);
                 if (prev == -1) {
                     atomicAdd(&cnt[w], 1);
                     break;
                 }
                 if (prev == x) break;
-                h = (h + 1) & (kRowHash - 1);
+                h = (h + 1) & (uint32_t)(H - 1);
             }
         }
         __syncwarp();
@@ -281,7 +285,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_row_count(int64_t nn, int nl
         }
         // compact, pad to a power of two, bitonic sort within the warp
         int base = 0;
-        for (int q0 = 0; q0 < kRowHash; q0 += 32) {
+        for (int q0 = 0; q0 < H; q0 += 32) {
             const int32_t x = tab[q0 + lane];
             const unsigned m = __ballot_sync(0xffffffffu, x >= 0);
             if (x >= 0) ks[base + __popc(m & ((1u << lane) - 1u))] = x;
