@@ -189,8 +189,11 @@ __global__ void k_validate_count(int64_t ne, int nlb, int64_t nn, const int32_t 
     }
 }
 
+// does nothing when validation found a bad element (the build reads the error
+// word at its next synchronisation and fails there)
 __global__ void k_fill_n2e(int64_t ne, int nlb, const int32_t *__restrict__ elems, int32_t *__restrict__ cursor,
-                           int32_t *__restrict__ n2e) {
+                           int32_t *__restrict__ n2e, const int *__restrict__ err) {
+    if (*err & (ERR_OOB | ERR_DUP)) return;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += (int64_t)gridDim.x * blockDim.x)
         for (int j = 0; j < nlb; ++j) {
             int32_t pos = atomicAdd(&cursor[elems[k * nlb + j]], 1);
@@ -248,6 +251,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_row_count(int64_t nn, int nl
     __shared__ int32_t hs[kRowWarps][kRowHash];
     __shared__ int32_t key[kRowWarps][kRowHash / 2];
     __shared__ int cnt[kRowWarps];
+    if (*err & (ERR_OOB | ERR_DUP)) return;   // validation failed: the incidence lists were not filled
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     int32_t *tab = hs[w], *ks = key[w];
     for (int64_t i = (int64_t)blockIdx.x * kRowWarps + w; i < nn; i += (int64_t)gridDim.x * kRowWarps) {
@@ -654,11 +658,15 @@ __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e
         if (threadIdx.x == 0) atomicOr(err, 32);
         return;
     }
-    for (int i = threadIdx.x; i < Hn; i += blockDim.x) hs[i] = -1;
+    // a table of at least twice the candidates (the tile's elements share most
+    // vertices: a few thousand slots where the capacity allows 2 cap_n)
+    int Hu = Hn < 64 ? Hn : 64;
+    while (Hu < 2 * nnc && Hu < Hn) Hu <<= 1;
+    for (int i = threadIdx.x; i < Hu; i += blockDim.x) hs[i] = -1;
     __syncthreads();
-    for (int i = threadIdx.x; i < nnc; i += blockDim.x) hset_insert(hs, Hn, elems[(int64_t)ce[i / nv] * nlb + (i % nv)]);
+    for (int i = threadIdx.x; i < nnc; i += blockDim.x) hset_insert(hs, Hu, elems[(int64_t)ce[i / nv] * nlb + (i % nv)]);
     __syncthreads();
-    const int n_nd = hset_compact(hs, Hn, cn);
+    const int n_nd = hset_compact(hs, Hu, cn);
     sort_small(cn, n_nd);
     for (int i = threadIdx.x; i < n_nd; i += blockDim.x) sc_nodes[(int64_t)t * cap_n + i] = cn[i];
     // upper pairs {i, j > i} and diagonals of the tile's rows
@@ -992,14 +1000,10 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     if (!hp) return fail(VLA_ERR_OOM, "pinned host scalars");
     long long *dsc;
     TRY(S.get(&dsc, 8));
-    hp[1] = 0;
-    VLA_CUDA(cudaMemcpyAsync(&hp[1], d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    VLA_CUDA(cudaMemcpyAsync(&hp[2], d_bad, sizeof(long long), cudaMemcpyDeviceToHost, st));
-    VLA_CUDA(cudaStreamSynchronize(st));
-    int h_err = (int)hp[1];
-    const long long h_bad = hp[2];
-    if (h_err & ERR_OOB) return fail(VLA_ERR_INDEX_OOB, "element %lld references a node outside [0, %lld)", h_bad, (long long)nn);
-    if (h_err & ERR_DUP) return fail(VLA_ERR_DEGENERATE, "element %lld repeats a node", h_bad);
+    // the validation result is read at the next synchronisation (after the CSR row
+    // counts); until then the kernels that follow index through the elements only
+    // when the error word is clear
+    int h_err = 0;
 
     // ---- node -> element incidence (sorted by element)
     long long *pre;
@@ -1013,7 +1017,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     int32_t *cursor;
     TRY(S.get(&cursor, nn + 1));
     VLA_CUDA(cudaMemcpyAsync(cursor, m->n2e_ptr, sizeof(int32_t) * (nn + 1), cudaMemcpyDeviceToDevice, st));
-    k_fill_n2e<<<grid_for(ne, TB), TB, 0, st>>>(ne, nlb, m->elems, cursor, m->n2e);
+    k_fill_n2e<<<grid_for(ne, TB), TB, 0, st>>>(ne, nlb, m->elems, cursor, m->n2e, d_err);
     k_sort_segments<<<grid_for((nn + kSegWarps - 1) / kSegWarps, 1), kSegWarps * 32, 0, st>>>(nn, m->n2e_ptr, m->n2e);
     VLA_CUDA(cudaGetLastError());
 
@@ -1029,9 +1033,13 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     k_max_i32<<<grid_for(nn, 256), 256, 0, st>>>(nn, rowlen, 0, dsc + 1);
     hp[1] = 0;
     VLA_CUDA(cudaMemcpyAsync(&hp[1], d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VLA_CUDA(cudaMemcpyAsync(&hp[2], d_bad, sizeof(long long), cudaMemcpyDeviceToHost, st));
     VLA_CUDA(cudaMemcpyAsync(&hp[4], dsc + 1, sizeof(long long), cudaMemcpyDeviceToHost, st));
     TRY(excl_scan<int32_t>(rowlen, nn, pre, st, &nnz));   // synchronises: the copies above have landed
     h_err = (int)hp[1];
+    const long long h_bad = hp[2];
+    if (h_err & ERR_OOB) return fail(VLA_ERR_INDEX_OOB, "element %lld references a node outside [0, %lld)", h_bad, (long long)nn);
+    if (h_err & ERR_DUP) return fail(VLA_ERR_DEGENERATE, "element %lld repeats a node", h_bad);
     m->max_row_len = (int32_t)hp[4];
     if (h_err & ERR_ROWLEN) return fail(VLA_ERR_UNSUPPORTED, "a CSR row has more than %d entries", kMaxRow);
     if (nnz > 0x7fffffffll) return fail(VLA_ERR_UNSUPPORTED, "nnz %lld exceeds int32", nnz);
