@@ -37,7 +37,9 @@ contiguous node rows [nn r / N, nn (r+1) / N) and assembles the sub-mesh of
 the elements touching them (halo elements duplicated), which gives it those
 rows of K and M complete; no collective on the data path (strong scaling,
 value = elements of the whole mesh / slowest rank's step time).  The
-reference arm runs on rank 0 alone.
+reference arm runs on rank 0 alone.  BENCH_DIST_BACKEND=gloo runs the
+multi-rank harness without NCCL (ranks may then share a GPU: a functional
+check of the row-block path, not a timing).
 """
 from __future__ import annotations
 
