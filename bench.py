@@ -5,8 +5,8 @@ nodes, 4,018,753 CSR nonzeros, interior nodes jittered by U(-0.1h, 0.1h)
 (seed 0), coefficient c(x) = 1 + |x|^2 at the element centroid, mixed
 precision (FP32 element matrices, compensated determinant and CSR sums, FP64
 outputs), plus outward unit normals and areas of the 49,152 boundary
-triangles.  One step = vla_assemble (K, M, volumes) + vla_boundary on a
-resident mesh.
+triangles.  One step = vla_assemble_with_boundary (K, M, volumes, and the
+boundary facets in the same persistent launch) on a resident mesh.
 
   value   elements/s over all ranks, inputs resident in HBM, CUDA events
           around each step, L2 flushed (512 MiB write) before every step.
@@ -16,7 +16,8 @@ resident mesh.
   roofline  the assembly kernel against the measured HBM copy bandwidth, with
           the algorithmic bytes per element of the method (elements 16 B,
           coordinates 24 nn/ne B, element-to-nonzero map 64 B, K and M values
-          16 nnz/ne B, volume 8 B).
+          16 nnz/ne B, volume 8 B) plus 48 B per boundary facet (three node
+          indices, the opposite node, normal and area).
   cpu_baseline  the FP64 oracle (plain C) on the same mesh, one host thread
           and all host cores (core count read at run time).
   errors  every output (K, M, volumes, normals, areas) against the FP64
@@ -180,6 +181,9 @@ def _row_block(nn, rank, ws):
 
 def _alg_bytes_per_el(ne, nn, nnz):
     return 16.0 + 24.0 * nn / ne + 64.0 + 16.0 * nnz / ne + 8.0
+
+
+FACET_BYTES = 48.0   # a P1 tet boundary facet: 3 node indices + opposite node (16 B), normal + area (32 B)
 
 
 def _host_cores():
@@ -1004,15 +1008,14 @@ def main():
     stream = torch.cuda.current_stream()
 
     def step():
-        gm.assemble(1.0, 1.0, precision=prec, K=K, M=M, vol=vol)
-        gm.boundary(precision=prec, normals=nrm, areas=ar)
+        gm.assemble(1.0, 1.0, precision=prec, K=K, M=M, vol=vol, boundary=True, normals=nrm, areas=ar)
 
     for _ in range(args.warmup):
         flush.zero_()
         step()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
     sampler = ClockSampler(local)
     _barrier(dist)
     torch.cuda.synchronize()
@@ -1020,19 +1023,16 @@ def main():
     time.sleep(0.3)
     for i in range(args.steps):
         flush.zero_()
-        e0, e1, e2 = ev[i]
+        e0, e1 = ev[i]
         e0.record(stream)
-        gm.assemble(1.0, 1.0, precision=prec, K=K, M=M, vol=vol)
+        step()   # one launch: the assembly kernel with the boundary facets after its tiles
         e1.record(stream)
-        gm.boundary(precision=prec, normals=nrm, areas=ar)
-        e2.record(stream)
     torch.cuda.synchronize()
     _barrier(dist)
     clocks = sampler.stop()
-    step_ms = [a.elapsed_time(c) for a, b, c in ev]
-    asm_ms = [a.elapsed_time(b) for a, b, c in ev]
+    step_ms = [a.elapsed_time(b) for a, b in ev]
     ms = _max_over_ranks(dist, sum(step_ms) / len(step_ms))
-    asm = sum(asm_ms) / len(asm_ms)
+    asm = sum(step_ms) / len(step_ms)   # this rank's kernel time (the step is that one launch)
     value = m.ne / (ms * 1e-3)   # every element of the one mesh, over the slowest rank's time
 
     # latency of the hot step over --latency-reps calls: device time with the L2
@@ -1062,7 +1062,8 @@ def main():
         torch.cuda.synchronize()
         host.append((time.perf_counter() - t0) * 1e3)
     latency = {"cold_l2": _pct(lat_cold), "warm_l2": _pct(lat_warm), "host_call_and_sync": _pct(host),
-               "what": "one step (assemble + boundary) on the resident mesh; cold = 512 MiB L2 flush before each"}
+               "what": "one step (assembly with boundary facets, one launch) on the resident mesh; cold = 512 MiB "
+                       "L2 flush before each"}
     got = {"K": K.cpu().numpy(), "M": M.cpu().numpy(), "vol": vol.cpu().numpy(), "normals": nrm.cpu().numpy(),
            "areas": ar.cpu().numpy()}
 
@@ -1087,7 +1088,7 @@ def main():
 
     def e2e_step():
         # CUDA events between the phases and the host clock around each, to itemise the step
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         th = [time.perf_counter()]
         ev[0].record(stream)
         dc = hc.to(dev, non_blocking=True)
@@ -1098,12 +1099,11 @@ def main():
         g2 = vla.Mesh(dc, de, df, rows=None if ws == 1 else blk)   # the build synchronises the stream
         ev[2].record(stream)
         th.append(time.perf_counter())
-        o = g2.assemble(1.0, 1.0, precision=prec)
+        o = g2.assemble(1.0, 1.0, precision=prec, boundary=True)
+        n2, a2 = o["normals"], o["areas"]
         ev[3].record(stream)
-        n2, a2 = g2.boundary(precision=prec)
-        ev[4].record(stream)
         rp, ci, kb, mb = g2.block((o["K"], o["M"]))
-        ev[5].record(stream)
+        ev[4].record(stream)
         th.append(time.perf_counter())
         out_host["K"][: kb.numel()].copy_(kb, non_blocking=True)
         out_host["M"][: mb.numel()].copy_(mb, non_blocking=True)
@@ -1112,11 +1112,11 @@ def main():
         out_host["ar"][: g2.nfb].copy_(a2, non_blocking=True)
         out_host["rp"][: rp.numel()].copy_(rp, non_blocking=True)
         out_host["ci"][: ci.numel()].copy_(ci, non_blocking=True)
-        ev[6].record(stream)
+        ev[5].record(stream)
         torch.cuda.synchronize()
         th.append(time.perf_counter())
         g2.close()
-        names = ("h2d", "mesh_build", "assemble", "boundary", "csr_pattern_out", "d2h")
+        names = ("h2d", "mesh_build", "assemble_with_boundary", "csr_pattern_out", "d2h")
         split.append({"device_ms": {n: ev[i].elapsed_time(ev[i + 1]) for i, n in enumerate(names)},
                       "host_ms": {"h2d_enqueue": (th[1] - th[0]) * 1e3, "mesh_build_call": (th[2] - th[1]) * 1e3,
                                   "assemble_boundary_csr_enqueue": (th[3] - th[2]) * 1e3,
@@ -1139,7 +1139,7 @@ def main():
                        "D2H of row_ptr/col_idx/K/M/vol/normals/areas", "split": e2e_split}
 
     peaks, src = _peaks()
-    bpe = _alg_bytes_per_el(gm.ne, gm.nn, gm.nnz)
+    bpe = _alg_bytes_per_el(gm.ne, gm.nn, gm.nnz) + FACET_BYTES * gm.nfb / gm.ne
     achieved = bpe * gm.ne / (asm * 1e-3) / 1e9
     khash = _src_hash()
     roof = {"bound": "hbm", "kernel": "k_assemble<3,1,%s>" % ("mixed" if prec else "fp64"),
@@ -1172,7 +1172,7 @@ def main():
                            parallelism=f"rows split in {ws} contiguous blocks, one per rank (halo elements "
                                        f"duplicated, complete rows per rank, no collective on the data path)"
                            if ws > 1 else "one GPU, every row"),
-            "e2e": e2e, "roofline": roof, "gpu_launches": 2 * args.steps, "clocks": clocks,
+            "e2e": e2e, "roofline": roof, "gpu_launches": args.steps, "clocks": clocks,
             "p50_ms": latency["cold_l2"]["p50_ms"], "p99_ms": latency["cold_l2"]["p99_ms"], "latency": latency}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         base, ref = cpu_baseline(m, args.cpu_seconds)

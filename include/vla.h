@@ -240,6 +240,21 @@ vla_status vla_assemble(const vla_mesh *mesh, int32_t coeff_kind, double ca, dou
                         double *K_vals, double *M_vals, double *vol, double *K_pages, double *M_pages,
                         int64_t *n_singular, void *stream);
 
+/* vla_assemble and vla_boundary of the same mesh in one launch (the Section
+ * 3.5 assembly and the Section 3.2/3.4 boundary normals and areas): the
+ * persistent assembly CTAs compute the mesh's boundary facets after their
+ * row tiles, in the precision given, instead of a second kernel after the
+ * assembly.  The outputs equal those of the two separate calls bit for bit.
+ * normals (dim x nfb) and areas (nfb) as for vla_boundary; every other
+ * argument as for vla_assemble.  A mesh without boundary facets is assembled
+ * as by vla_assemble (normals and areas may then be NULL).  Errors: those of
+ * vla_assemble, and VLA_ERR_INVALID_ARG for a NULL normals or areas on a mesh
+ * with boundary facets. */
+vla_status vla_assemble_with_boundary(const vla_mesh *mesh, int32_t coeff_kind, double ca, double cb,
+                                      int32_t precision, double *K_vals, double *M_vals, double *vol,
+                                      double *K_pages, double *M_pages, int64_t *n_singular, double *normals,
+                                      double *areas, void *stream);
+
 /* Boundary facets (Section 3.2 normals of boundary faces; the areas used by
  * the surface integrals of Section 3.4): for facet f with vertex nodes
  * (x1, x2[, x3]) the normal n = (x2-x1) x (x3-x1) (3-D) or the edge vector

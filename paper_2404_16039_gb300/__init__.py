@@ -130,6 +130,7 @@ def lib():
         L.vla_mesh_info.argtypes = [vp, C.POINTER(MeshInfo)]
         L.vla_mesh_csr.argtypes = [vp, vp, vp, vp]
         L.vla_assemble.argtypes = [vp, i32, dbl, dbl, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.vla_assemble_with_boundary.argtypes = [vp, i32, dbl, dbl, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.vla_boundary.argtypes = [vp, i32, vp, vp, vp]
         L.vla_simplex_normals.argtypes = [vp, vp, vp]
         L.vla_mesh_destroy.argtypes = [vp]
@@ -162,7 +163,7 @@ def lib():
         L.vla_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
         L.vla_server_destroy.argtypes = [vp]
         for name in ("vla_amtam", "vla_astam", "vla_avtam", "vla_amdet", "vla_aminv", "vla_mesh_create",
-                     "vla_mesh_info", "vla_mesh_csr", "vla_assemble", "vla_boundary", "vla_simplex_normals",
+                     "vla_mesh_info", "vla_mesh_csr", "vla_assemble", "vla_assemble_with_boundary", "vla_boundary", "vla_simplex_normals",
                      "vla_mesh_destroy", "vla_element_pages_static", "vla_element_pages_static_check", "vla_mesh_check",
                      "vla_partition_rows", "vla_mesh_create_rows", "vla_batch_create",
                      "vla_batch_set_job", "vla_batch_run", "vla_batch_info", "vla_batch_check", "vla_batch_destroy",
@@ -486,9 +487,13 @@ class Mesh:
         return (rp[r0:r1 + 1] - a, ci[a:b]) + tuple(v[a:b] for v in values)
 
     def assemble(self, ca=1.0, cb=0.0, kind=COEFF_POLY, precision=PREC_MIXED, K=None, M=None, vol=None,
-                 want_K=True, want_M=True, want_vol=True, pages=False, count_singular=False, stream=None):
+                 want_K=True, want_M=True, want_vol=True, pages=False, count_singular=False, stream=None,
+                 boundary=False, normals=None, areas=None):
         """K and M values in CSR order (FP64), element volumes and optionally the
-        element pages (ne, nlb, nlb).  Returns a dict of tensors.  Section 3.5."""
+        element pages (ne, nlb, nlb).  Returns a dict of tensors.  Section 3.5.
+        ``boundary=True`` also computes the boundary facets' normals and areas
+        in the same launch (vla_assemble_with_boundary; "normals", "areas" in
+        the dict, as from ``boundary``).  Sections 3.2, 3.4."""
         dev = self.device
         f64 = torch.float64
         if want_K:
@@ -500,10 +505,26 @@ class Mesh:
         Kp = torch.empty((self.ne, self.nlb, self.nlb), dtype=f64, device=dev) if pages else None
         Mp = torch.empty((self.ne, self.nlb, self.nlb), dtype=f64, device=dev) if pages else None
         ns = torch.zeros(1, dtype=torch.int64, device=dev) if count_singular else None
-        _check(lib().vla_assemble(self._h, kind, float(ca), float(cb), precision,
-                                  _p(K) if want_K else None, _p(M) if want_M else None,
-                                  _p(vol) if want_vol else None, _p(Kp), _p(Mp), _p(ns), _stream(stream)))
+        if boundary:
+            if normals is None:
+                normals = torch.empty((max(self.nfb, 1), self.dim), dtype=f64, device=dev)[: self.nfb]
+            else:
+                _buf(normals, self.nfb * self.dim, f64, dev, "normals")
+            if areas is None:
+                areas = torch.empty(max(self.nfb, 1), dtype=f64, device=dev)[: self.nfb]
+            else:
+                _buf(areas, self.nfb, f64, dev, "areas")
+            _check(lib().vla_assemble_with_boundary(self._h, kind, float(ca), float(cb), precision,
+                                                    _p(K) if want_K else None, _p(M) if want_M else None,
+                                                    _p(vol) if want_vol else None, _p(Kp), _p(Mp), _p(ns),
+                                                    _p(normals), _p(areas), _stream(stream)))
+        else:
+            _check(lib().vla_assemble(self._h, kind, float(ca), float(cb), precision,
+                                      _p(K) if want_K else None, _p(M) if want_M else None,
+                                      _p(vol) if want_vol else None, _p(Kp), _p(Mp), _p(ns), _stream(stream)))
         out = {"K": K if want_K else None, "M": M if want_M else None, "vol": vol if want_vol else None}
+        if boundary:
+            out["normals"], out["areas"] = normals, areas
         if pages:
             out["K3D"], out["M3D"] = Kp, Mp
         if count_singular:

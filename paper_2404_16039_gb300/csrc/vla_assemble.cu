@@ -546,6 +546,77 @@ struct Cfg {
     static constexpr double MOFF = 1.0 / ((DIM + 1) * (DIM + 2));   // P1 off-diagonal mass / (c |T|)
 };
 
+// Boundary facet f (Section 3.2 normals of boundary faces, Section 3.4 areas):
+// n = (x2 - x1) x (x3 - x1) in 3-D or the edge rotated by -90 degrees in 2-D,
+// oriented away from the owning element's remaining vertex, normalised; the
+// measure |n|/2 (3-D) or |n| (2-D).  Used by the boundary kernels and by the
+// single-mesh assembly launch that computes the facets after its tiles.
+__device__ __forceinline__ void boundary_facet_f64(int64_t f, int dim, const double *__restrict__ x,
+                                                   const int32_t *__restrict__ faces, const int32_t *__restrict__ opp,
+                                                   double *__restrict__ nrm, double *__restrict__ area) {
+    const int32_t a = faces[f * dim], b = faces[f * dim + 1];
+    const int32_t o = opp[f];
+    double n[3] = {0, 0, 0}, meas;
+    const double *x1 = x + (int64_t)a * dim, *x2 = x + (int64_t)b * dim, *xo = x + (int64_t)o * dim;
+    if (dim == 3) {
+        const double *x3 = x + (int64_t)faces[f * dim + 2] * dim;
+        double u[3], w[3];
+        for (int d = 0; d < 3; ++d) {
+            u[d] = x2[d] - x1[d];
+            w[d] = x3[d] - x1[d];
+        }
+        n[0] = u[1] * w[2] - u[2] * w[1];
+        n[1] = u[2] * w[0] - u[0] * w[2];
+        n[2] = u[0] * w[1] - u[1] * w[0];
+    } else {
+        n[0] = x2[1] - x1[1];
+        n[1] = -(x2[0] - x1[0]);
+    }
+    const double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    meas = dim == 3 ? 0.5 * len : len;
+    double side = 0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        if (d < dim) side += n[d] * (xo[d] - x1[d]);
+    const double sg = side > 0 ? -1.0 : 1.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        if (d < dim) nrm[f * dim + d] = sg * n[d] / len;
+    area[f] = meas;
+}
+
+// the same from the float-pair coordinates (mixed precision)
+__device__ __forceinline__ void boundary_facet_mixed(int64_t f, int dim, const float4 *__restrict__ xh,
+                                                     const float4 *__restrict__ xl, const int32_t *__restrict__ faces,
+                                                     const int32_t *__restrict__ opp, double *__restrict__ nrm,
+                                                     double *__restrict__ area) {
+    const int32_t ia = faces[f * dim], ib = faces[f * dim + 1], io = opp[f];
+    const float4 ha = xh[ia], la = xl[ia], hb = xh[ib], lb = xl[ib], ho = xh[io], lo = xl[io];
+    auto dif = [](float h1, float l1, float h0, float l0) { return __fadd_rn(__fsub_rn(h1, h0), __fsub_rn(l1, l0)); };
+    float u[3] = {dif(hb.x, lb.x, ha.x, la.x), dif(hb.y, lb.y, ha.y, la.y), dif(hb.z, lb.z, ha.z, la.z)};
+    float r[3] = {dif(ho.x, lo.x, ha.x, la.x), dif(ho.y, lo.y, ha.y, la.y), dif(ho.z, lo.z, ha.z, la.z)};
+    float n[3];
+    if (dim == 3) {
+        const int32_t ic = faces[f * dim + 2];
+        const float4 hc = xh[ic], lc = xl[ic];
+        float w[3] = {dif(hc.x, lc.x, ha.x, la.x), dif(hc.y, lc.y, ha.y, la.y), dif(hc.z, lc.z, ha.z, la.z)};
+        n[0] = det2_kahan(u[1], u[2], w[1], w[2]);
+        n[1] = det2_kahan(u[2], u[0], w[2], w[0]);
+        n[2] = det2_kahan(u[0], u[1], w[0], w[1]);
+    } else {
+        n[0] = u[1];
+        n[1] = -u[0];
+        n[2] = 0.f;
+    }
+    const float len = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    const float side = n[0] * r[0] + n[1] * r[1] + n[2] * r[2];
+    const float inv = (side > 0.f ? -1.f : 1.f) / len;
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+        if (d < dim) nrm[f * dim + d] = f32_to_f64(n[d] * inv);
+    area[f] = f32_to_f64(dim == 3 ? 0.5f * len : len);
+}
+
 // One mesh of an assembly launch: its tile streams, coordinates, coefficient
 // and outputs.  A single-mesh launch passes it as a kernel parameter; a
 // batched launch keeps a table of them in device memory and bulk-copies the
@@ -591,6 +662,11 @@ struct LaunchArgs {
     int *err;                 // device error word (bit 0: a bounded wait expired)
     int spin_limit;
     int stage_bytes;          // bytes of one input stage (segments + coordinates), 16-byte multiple
+    // boundary facets a single-mesh launch computes after its tiles (nfb 0: none)
+    const int32_t *faces, *face_opp;
+    double *nrm, *area;
+    int64_t nfb;
+    int dim;
 };
 
 __host__ __device__ constexpr int padq(int x, int q) { return (x + q - 1) / q * q; }
@@ -1112,6 +1188,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_assemble(const LaunchArgs A) {
             issue(s);
         }
     }
+    // a single-mesh launch may also compute the mesh's boundary facets: each CTA
+    // takes its share once its tiles are done (the tail of the persistent launch)
+    if constexpr (!BATCH) {
+        for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < A.nfb;
+             f += (int64_t)gridDim.x * blockDim.x) {
+            if constexpr (MIX) boundary_facet_mixed(f, A.dim, A.one.xh, A.one.xl, A.faces, A.face_opp, A.nrm, A.area);
+            else boundary_facet_f64(f, A.dim, A.one.coords, A.faces, A.face_opp, A.nrm, A.area);
+        }
+    }
 }
 
 // stage and record-area sizes of a mesh under a launch of precision MIX
@@ -1232,65 +1317,15 @@ MeshJob make_job(const vla_mesh *m, int kind, double ca, double cb, double *K, d
 // ---------------------------------------------------------------------------
 __global__ void k_boundary_f64(int64_t nfb, int dim, const double *__restrict__ x, const int32_t *__restrict__ faces,
                                const int32_t *__restrict__ opp, double *__restrict__ nrm, double *__restrict__ area) {
-    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nfb; f += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t a = faces[f * dim], b = faces[f * dim + 1];
-        const int32_t o = opp[f];
-        double n[3] = {0, 0, 0}, meas;
-        const double *x1 = x + (int64_t)a * dim, *x2 = x + (int64_t)b * dim, *xo = x + (int64_t)o * dim;
-        if (dim == 3) {
-            const double *x3 = x + (int64_t)faces[f * dim + 2] * dim;
-            double u[3], w[3];
-            for (int d = 0; d < 3; ++d) {
-                u[d] = x2[d] - x1[d];
-                w[d] = x3[d] - x1[d];
-            }
-            n[0] = u[1] * w[2] - u[2] * w[1];
-            n[1] = u[2] * w[0] - u[0] * w[2];
-            n[2] = u[0] * w[1] - u[1] * w[0];
-        } else {
-            n[0] = x2[1] - x1[1];
-            n[1] = -(x2[0] - x1[0]);
-        }
-        const double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-        meas = dim == 3 ? 0.5 * len : len;
-        double side = 0;
-        for (int d = 0; d < dim; ++d) side += n[d] * (xo[d] - x1[d]);
-        const double sg = side > 0 ? -1.0 : 1.0;
-        for (int d = 0; d < dim; ++d) nrm[f * dim + d] = sg * n[d] / len;
-        area[f] = meas;
-    }
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nfb; f += (int64_t)gridDim.x * blockDim.x)
+        boundary_facet_f64(f, dim, x, faces, opp, nrm, area);
 }
 
 __global__ void k_boundary_mixed(int64_t nfb, int dim, const float4 *__restrict__ xh, const float4 *__restrict__ xl,
                                  const int32_t *__restrict__ faces, const int32_t *__restrict__ opp,
                                  double *__restrict__ nrm, double *__restrict__ area) {
-    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nfb; f += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t ia = faces[f * dim], ib = faces[f * dim + 1], io = opp[f];
-        const float4 ha = xh[ia], la = xl[ia], hb = xh[ib], lb = xl[ib], ho = xh[io], lo = xl[io];
-        auto dif = [](float h1, float l1, float h0, float l0) {
-            return __fadd_rn(__fsub_rn(h1, h0), __fsub_rn(l1, l0));
-        };
-        float u[3] = {dif(hb.x, lb.x, ha.x, la.x), dif(hb.y, lb.y, ha.y, la.y), dif(hb.z, lb.z, ha.z, la.z)};
-        float r[3] = {dif(ho.x, lo.x, ha.x, la.x), dif(ho.y, lo.y, ha.y, la.y), dif(ho.z, lo.z, ha.z, la.z)};
-        float n[3];
-        if (dim == 3) {
-            const int32_t ic = faces[f * dim + 2];
-            const float4 hc = xh[ic], lc = xl[ic];
-            float w[3] = {dif(hc.x, lc.x, ha.x, la.x), dif(hc.y, lc.y, ha.y, la.y), dif(hc.z, lc.z, ha.z, la.z)};
-            n[0] = det2_kahan(u[1], u[2], w[1], w[2]);
-            n[1] = det2_kahan(u[2], u[0], w[2], w[0]);
-            n[2] = det2_kahan(u[0], u[1], w[0], w[1]);
-        } else {
-            n[0] = u[1];
-            n[1] = -u[0];
-            n[2] = 0.f;
-        }
-        const float len = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-        const float side = n[0] * r[0] + n[1] * r[1] + n[2] * r[2];
-        const float inv = (side > 0.f ? -1.f : 1.f) / len;
-        for (int d = 0; d < dim; ++d) nrm[f * dim + d] = f32_to_f64(n[d] * inv);
-        area[f] = f32_to_f64(dim == 3 ? 0.5f * len : len);
-    }
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < nfb; f += (int64_t)gridDim.x * blockDim.x)
+        boundary_facet_mixed(f, dim, xh, xl, faces, opp, nrm, area);
 }
 
 // all-facet normals V^{-T} normalsRef = -grad lambda_j = -C_j / det (FP64)
@@ -1373,9 +1408,11 @@ __global__ void k_set_job(MeshJob *dst, MeshJob j) {
 
 using namespace vla;
 
-extern "C" vla_status vla_assemble(const vla_mesh *m, int32_t kind, double ca, double cb, int32_t precision,
-                                   double *K_vals, double *M_vals, double *vol, double *K_pages, double *M_pages,
-                                   int64_t *n_singular, void *stream) {
+namespace vla {
+namespace {
+vla_status assemble_impl(const vla_mesh *m, int32_t kind, double ca, double cb, int32_t precision, double *K_vals,
+                         double *M_vals, double *vol, double *K_pages, double *M_pages, int64_t *n_singular,
+                         double *normals, double *areas, void *stream) {
     if (!m) return fail(VLA_ERR_INVALID_ARG, "null mesh");
     if (kind < VLA_COEFF_POLY || kind > VLA_COEFF_EXP_IP) return fail(VLA_ERR_INVALID_ARG, "unknown coefficient kind");
     if (kind >= VLA_COEFF_POLY_IP && m->order != VLA_P1)
@@ -1398,6 +1435,14 @@ extern "C" vla_status vla_assemble(const vla_mesh *m, int32_t kind, double ca, d
     a.err = m->d_err;
     a.spin_limit = m->spin_limit;
     a.stage_bytes = mesh_stage_bytes(m);
+    if (normals && areas && m->nfb > 0) {
+        a.faces = m->faces;
+        a.face_opp = m->face_opp;
+        a.nrm = normals;
+        a.area = areas;
+        a.nfb = m->nfb;
+        a.dim = m->dim;
+    }
     const bool lit = kind >= VLA_COEFF_POLY_IP;
     const size_t smem = 2 * (size_t)a.stage_bytes + mesh_record_bytes(m, mix, lit);
     const int ty = type_index(m->dim, m->order);
@@ -1420,6 +1465,24 @@ extern "C" vla_status vla_assemble(const vla_mesh *m, int32_t kind, double ca, d
     case 6: return launch_single<false, 8>(a, smem, cps, st);
     default: return launch_single<true, 8>(a, smem, cps, st);
     }
+}
+}  // namespace
+}  // namespace vla
+
+extern "C" vla_status vla_assemble(const vla_mesh *m, int32_t kind, double ca, double cb, int32_t precision,
+                                   double *K_vals, double *M_vals, double *vol, double *K_pages, double *M_pages,
+                                   int64_t *n_singular, void *stream) {
+    return assemble_impl(m, kind, ca, cb, precision, K_vals, M_vals, vol, K_pages, M_pages, n_singular, nullptr,
+                         nullptr, stream);
+}
+
+extern "C" vla_status vla_assemble_with_boundary(const vla_mesh *m, int32_t kind, double ca, double cb,
+                                                 int32_t precision, double *K_vals, double *M_vals, double *vol,
+                                                 double *K_pages, double *M_pages, int64_t *n_singular,
+                                                 double *normals, double *areas, void *stream) {
+    if (m && m->nfb > 0 && (!normals || !areas)) return fail(VLA_ERR_INVALID_ARG, "null boundary output");
+    return assemble_impl(m, kind, ca, cb, precision, K_vals, M_vals, vol, K_pages, M_pages, n_singular, normals,
+                         areas, stream);
 }
 
 // ---------------------------------------------------------------------------

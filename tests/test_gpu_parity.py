@@ -257,8 +257,11 @@ def test_config2_full_size_mixed(vla):
     m = meshgen.kuhn_cube(64, jitter=0.1, seed=0)
     gm = _gpu_mesh(vla, m)
     assert (gm.ne, gm.nn, gm.nnz, gm.nfb) == (1572864, 274625, 4018753, 49152)
-    out = gm.assemble(1.0, 1.0, precision=vla.PREC_MIXED)
-    nrm, ar = gm.boundary(precision=vla.PREC_MIXED)
+    # the benchmark's launch: assembly and boundary facets in one launch
+    out = gm.assemble(1.0, 1.0, precision=vla.PREC_MIXED, boundary=True)
+    nrm, ar = out["normals"], out["areas"]
+    n2, a2 = gm.boundary(precision=vla.PREC_MIXED)
+    assert torch.equal(nrm, n2) and torch.equal(ar, a2)
     ref = oracle.assemble(3, 1, m.nn, m.elems, m.coords, 1.0, 1.0)
     rn, ra, _ = oracle.boundary(3, m.nn, m.elems, m.coords, m.faces)
     rp, ci = gm.csr()
@@ -293,6 +296,29 @@ def test_boundary_and_facet_normals(vla, dim, order, n):
     snr = oracle.simplex_normals(dim, m.elems, m.coords)
     err = np.abs(sn - snr).max(axis=(1, 2)) / np.abs(snr).max(axis=(1, 2))
     assert err.max() <= TOL64
+
+
+@pytest.mark.parametrize("dim,order,n", [(2, 1, 5), (3, 1, 4), (2, 2, 6), (3, 2, 3), (3, 1, 17)])
+def test_assembly_with_boundary_one_launch(vla, dim, order, n):
+    # vla_assemble_with_boundary equals vla_assemble followed by vla_boundary, bit for bit
+    m = meshgen.make_mesh(dim, n, order=order, jitter=0.1, seed=7 * n)
+    gm = _gpu_mesh(vla, m)
+    rn, ra, _ = oracle.boundary(dim, m.nn, m.elems, m.coords, m.faces)
+    for prec in (vla.PREC_FP64, vla.PREC_MIXED):
+        one = gm.assemble(0.7, 1.3, precision=prec, pages=True, count_singular=True, boundary=True)
+        two = gm.assemble(0.7, 1.3, precision=prec, pages=True, count_singular=True)
+        nrm, ar = gm.boundary(precision=prec)
+        for key in ("K", "M", "vol", "K3D", "M3D", "n_singular"):
+            assert torch.equal(one[key], two[key]), key
+        assert torch.equal(one["normals"], nrm) and torch.equal(one["areas"], ar)
+        tol = 1e-13 if prec == vla.PREC_FP64 else TOL_MIX
+        assert _rel_fro(one["normals"].cpu().numpy(), rn) <= tol
+        assert _rel_fro(one["areas"].cpu().numpy(), ra) <= tol
+    # a mesh given without boundary facets: the fused call is the plain assembly
+    bare = vla.Mesh(_dev(m.coords), _dev(m.elems), None, order=m.order)
+    one = bare.assemble(1.0, 0.0, precision=vla.PREC_MIXED, boundary=True)
+    assert one["normals"].numel() == 0 and one["areas"].numel() == 0
+    assert torch.equal(one["K"], bare.assemble(1.0, 0.0, precision=vla.PREC_MIXED)["K"])
 
 
 def test_worked_tetrahedron_normals(vla):
