@@ -1,6 +1,8 @@
 // vla_api.cu -- library-wide entry points: version, error reporting, and the
 // device error word polled after bounded waits.
+#include <algorithm>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -62,6 +64,52 @@ void set_tuned(int type, bool mix, int budget, int ctas) {
     if (type < 0 || type >= 4) return;
     g_budget[type] = budget;
     g_ctas[type][mix ? 1 : 0] = ctas;
+}
+
+// Device memory of mesh builds, batches, servers and integral scratch comes
+// from one memory pool per device that keeps up to min(8 GiB, 1/16 of the
+// device) of freed memory mapped between calls.  The device's default pool
+// keeps none: every synchronisation returns what was freed to the driver, and
+// the next build maps it again (a few hundred MB of scratch per million
+// elements).  VLA_POOL_KEEP (bytes) sets the amount kept; 0 keeps none.
+cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t st) {
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, st);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps pp;
+            std::memset(&pp, 0, sizeof(pp));
+            pp.allocType = cudaMemAllocationTypePinned;
+            pp.handleTypes = cudaMemHandleTypeNone;
+            pp.location.type = cudaMemLocationTypeDevice;
+            pp.location.id = dev;
+            cudaMemPool_t np;
+            e = cudaMemPoolCreate(&np, &pp);
+            if (e != cudaSuccess) return e;
+            size_t fr = 0, total = 0;
+            e = cudaMemGetInfo(&fr, &total);
+            if (e != cudaSuccess) {
+                cudaMemPoolDestroy(np);
+                return e;
+            }
+            unsigned long long keep = std::min<unsigned long long>(8ull << 30, total / 16);
+            if (const char *k = getenv("VLA_POOL_KEEP")) keep = strtoull(k, nullptr, 10);
+            e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+            if (e != cudaSuccess) {
+                cudaMemPoolDestroy(np);
+                return e;
+            }
+            pools[dev] = np;
+        }
+        pool = pools[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, st);
 }
 
 }  // namespace vla

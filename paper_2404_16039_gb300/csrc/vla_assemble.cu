@@ -1695,7 +1695,7 @@ vla_status batch_build(const vla_batch_job_t *jobs, int32_t count, int32_t preci
     const size_t jb = (sizeof(MeshJob) * count + 255) / 256 * 256;
     const size_t wb = (sizeof(WorkItem) * (size_t)n_work + 255) / 256 * 256;
     const size_t rb = (sizeof(int32_t) * count + 255) / 256 * 256;
-    cudaError_t e = async_mem ? cudaMallocAsync(&b->block, jb + wb + rb + 256, st)
+    cudaError_t e = async_mem ? pool_malloc((void **)&b->block, jb + wb + rb + 256, st)
                               : cudaMalloc(&b->block, jb + wb + rb + 256);
     if (e != cudaSuccess) {
         b->block = nullptr;

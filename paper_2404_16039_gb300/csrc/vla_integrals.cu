@@ -314,7 +314,7 @@ void launch_gi(int nb, cudaStream_t st, int64_t n, const GIArgs &ga, const doubl
 
 template <typename T>
 vla_status scratch_alloc(T **p, size_t count, cudaStream_t st) {
-    if (cudaMallocAsync((void **)p, sizeof(T) * (count ? count : 1), st) != cudaSuccess) {
+    if (pool_malloc((void **)p, sizeof(T) * (count ? count : 1), st) != cudaSuccess) {
         cudaGetLastError();
         return fail(VLA_ERR_OOM, "scratch allocation of %zu bytes failed", sizeof(T) * count);
     }

@@ -25,6 +25,9 @@ vla_status cuda_fail(cudaError_t e, const char *what);
 // assembly launch per precision.  0 means the library default.
 int tuned_budget(int type);
 int tile_budget(int dim, int order);   // the default per element type
+// stream-ordered device allocation from the library's pool of this device,
+// which keeps freed memory mapped for the next mesh build (up to a limit)
+cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t st);
 int tuned_ctas(int type, bool mix);
 void set_tuned(int type, bool mix, int budget, int ctas);
 

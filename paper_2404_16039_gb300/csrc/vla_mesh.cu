@@ -101,6 +101,27 @@ __global__ void k_i64_to_i32(int64_t n, const long long *__restrict__ in, int32_
 // Small pinned host buffer for the scalars a build reads back (one per host
 // thread, allocated on first use): device-to-host copies into pageable memory
 // would each wait for the whole stream.
+// a growable pinned host buffer per host thread for the tile tables a build
+// reads back and sends down (pageable copies of a few hundred KB go through a
+// driver staging buffer); every build ends with a synchronisation before the
+// thread's next build reuses it
+void *pinned_tables(size_t bytes) {
+    static thread_local void *p = nullptr;
+    static thread_local size_t cap = 0;
+    if (bytes > cap) {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        const size_t want = bytes > ((size_t)1 << 20) ? bytes + bytes / 4 : ((size_t)1 << 20);
+        if (cudaMallocHost(&p, want) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        cap = want;
+    }
+    return p;
+}
+
 long long *pinned_scalars() {
     static thread_local long long *p = nullptr;
     if (!p && cudaMallocHost((void **)&p, 64 * sizeof(long long)) != cudaSuccess) {
@@ -134,8 +155,8 @@ vla_status excl_scan(const TI *in, int64_t n, long long *out, cudaStream_t st, l
     int64_t nb = (n + per - 1) / per;
     if (nb < 1) nb = 1;
     long long *bs = nullptr, *bsp = nullptr;
-    VLA_CUDA(cudaMallocAsync(&bs, sizeof(long long) * (nb + 1), st));
-    VLA_CUDA(cudaMallocAsync(&bsp, sizeof(long long) * (nb + 1), st));
+    VLA_CUDA(pool_malloc((void **)&bs, sizeof(long long) * (nb + 1), st));
+    VLA_CUDA(pool_malloc((void **)&bsp, sizeof(long long) * (nb + 1), st));
     k_scan_blocks<TI><<<(int)nb, kScanThreads, 0, st>>>(n, in, out, bs);
     VLA_CUDA(cudaGetLastError());
     if (nb > 1) {
@@ -900,7 +921,7 @@ int next_pow2(int x) {
 template <typename T>
 vla_status dalloc(vla_mesh *m, T **p, size_t count, cudaStream_t st) {
     size_t bytes = sizeof(T) * (count > 0 ? count : 1);
-    cudaError_t e = cudaMallocAsync((void **)p, bytes, st);
+    cudaError_t e = pool_malloc((void **)p, bytes, st);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(VLA_ERR_OOM, "device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
@@ -916,7 +937,7 @@ struct Scratch {  // temporary device buffers freed at the end of the build
     template <typename T>
     vla_status get(T **p, size_t count) {
         size_t bytes = sizeof(T) * (count > 0 ? count : 1);
-        cudaError_t e = cudaMallocAsync((void **)p, bytes, st);
+        cudaError_t e = pool_malloc((void **)p, bytes, st);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(VLA_ERR_OOM, "device scratch allocation of %zu bytes failed", bytes);
@@ -1152,8 +1173,14 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
                                                        m->n2e_ptr, m->n2e, m->elems, m->row_ptr, m->col_idx, node_tile,
                                                        sc_elems, sc_nodes, tcnt, d_err);
         VLA_CUDA(cudaGetLastError());
-        std::vector<TileCounts> hc(n_tiles);
-        VLA_CUDA(cudaMemcpyAsync(hc.data(), tcnt, sizeof(TileCounts) * n_tiles, cudaMemcpyDeviceToHost, st));
+        // pinned tables: the tile counts (read back), the headers (sent down), the code counts (read back)
+        unsigned char *tb = static_cast<unsigned char *>(
+            pinned_tables((sizeof(TileCounts) + sizeof(TileHdr) + sizeof(int32_t)) * (size_t)n_tiles));
+        if (!tb) return fail(VLA_ERR_OOM, "pinned host tile tables");
+        TileCounts *hc = reinterpret_cast<TileCounts *>(tb);
+        TileHdr *hh = reinterpret_cast<TileHdr *>(tb + sizeof(TileCounts) * (size_t)n_tiles);
+        int32_t *hnc = reinterpret_cast<int32_t *>(tb + (sizeof(TileCounts) + sizeof(TileHdr)) * (size_t)n_tiles);
+        VLA_CUDA(cudaMemcpyAsync(hc, tcnt, sizeof(TileCounts) * n_tiles, cudaMemcpyDeviceToHost, st));
         hp[1] = 0;
         VLA_CUDA(cudaMemcpyAsync(&hp[1], d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         VLA_CUDA(cudaStreamSynchronize(st));
@@ -1165,7 +1192,6 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
 
         // tile offsets (host scan over a few thousand tiles); every segment padded for bulk copies
         auto pad = [](int64_t x, int64_t q) { return (x + q - 1) / q * q; };
-        std::vector<TileHdr> hh(n_tiles);
         int64_t o_node = 0, o_elem = 0, o_own = 0, o_nz = 0, o_chunk = 0, n_own_total = 0, nz_total = 0;
         m->max_tile_nodes = m->max_tile_elems = m->max_tile_nz = 0;
         m->tile_elems_total = 0;
@@ -1206,7 +1232,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         if (m->order == 1 && m->max_tile_elems >= 4095)
             return fail(VLA_ERR_UNSUPPORTED, "P1 tile has %d elements (limit 4094)", m->max_tile_elems);
         TRY(dalloc(m, &m->tiles, n_tiles, st));
-        VLA_CUDA(cudaMemcpyAsync(m->tiles, hh.data(), sizeof(TileHdr) * n_tiles, cudaMemcpyHostToDevice, st));
+        VLA_CUDA(cudaMemcpyAsync(m->tiles, hh, sizeof(TileHdr) * n_tiles, cudaMemcpyHostToDevice, st));
         // +16 bytes of slack: bulk copies round sizes up to 16 bytes
         TRY(dalloc(m, &m->tile_nodes, o_node + 4, st));
         TRY(dalloc(m, &m->tile_elem, o_elem + 2, st));
@@ -1232,8 +1258,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         k_chunk_table<<<(int)n_tiles, 64, 0, st>>>((int)n_tiles, m->tiles, nz_count, nzpos_rm, m->tile_nzpos, nz_order,
                                                     m->tile_chunks, tile_ncodes);
         VLA_CUDA(cudaGetLastError());
-        std::vector<int32_t> hnc(n_tiles);
-        VLA_CUDA(cudaMemcpyAsync(hnc.data(), tile_ncodes, sizeof(int32_t) * n_tiles, cudaMemcpyDeviceToHost, st));
+        VLA_CUDA(cudaMemcpyAsync(hnc, tile_ncodes, sizeof(int32_t) * n_tiles, cudaMemcpyDeviceToHost, st));
         VLA_CUDA(cudaStreamSynchronize(st));
         int64_t o_code = 0;
         const size_t code_bytes = (m->order == 1) ? 2 : 4;
@@ -1270,7 +1295,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
             }
         }
         m->n_codes = o_code;
-        VLA_CUDA(cudaMemcpyAsync(m->tiles, hh.data(), sizeof(TileHdr) * n_tiles, cudaMemcpyHostToDevice, st));
+        VLA_CUDA(cudaMemcpyAsync(m->tiles, hh, sizeof(TileHdr) * n_tiles, cudaMemcpyHostToDevice, st));
         const int rsc = (nlb * (nlb + 1) / 2 + 1) | 1;   // code stride: the mixed-precision record stride
         int32_t *fill;
         TRY(S.get(&fill, o_nz + 2));
@@ -1412,6 +1437,8 @@ vla_status mesh_create_budget(int32_t dim, int32_t order, int64_t nn, int64_t ne
     if (s != VLA_OK) {
         char keep[512];
         vla_last_error(keep, sizeof(keep));
+        cudaStreamSynchronize(m->stream);   // no copy from this thread's pinned tables left in flight
+        cudaGetLastError();
         vla_mesh_destroy(m);
         set_error("%s", keep);
         return s;
@@ -1573,11 +1600,11 @@ vla_status select_flagged(int64_t n, const int32_t *flag, int32_t **ids, int64_t
     *ids = nullptr;
     *count = 0;
     long long *pre = nullptr;
-    VLA_CUDA(cudaMallocAsync(&pre, sizeof(long long) * (n + 1), st));
+    VLA_CUDA(pool_malloc((void **)&pre, sizeof(long long) * (n + 1), st));
     long long total = 0;
     vla_status s = excl_scan<int32_t>(flag, n, pre, st, &total);
     if (s == VLA_OK && total > 0) {
-        cudaError_t e = cudaMallocAsync(ids, sizeof(int32_t) * total, st);
+        cudaError_t e = pool_malloc((void **)ids, sizeof(int32_t) * total, st);
         if (e != cudaSuccess) s = cuda_fail(e, "partition ids");
         else k_compact_flags<<<grid_for(n, 256), 256, 0, st>>>(n, flag, pre, *ids);
     }
@@ -1611,7 +1638,7 @@ extern "C" vla_status vla_partition_rows(int32_t nlb, int64_t ne, const int32_t 
     if (!elems) return fail(VLA_ERR_INVALID_ARG, "elems is NULL");
     cudaStream_t st = (cudaStream_t)stream;
     int32_t *flag = nullptr, *ids = nullptr;
-    VLA_CUDA(cudaMallocAsync(&flag, sizeof(int32_t) * ne, st));
+    VLA_CUDA(pool_malloc((void **)&flag, sizeof(int32_t) * ne, st));
     k_block_elem_flags<<<grid_for(ne, 256), 256, 0, st>>>(ne, nlb, elems, row_begin, row_end, flag);
     int64_t cnt = 0;
     vla_status s = select_flagged(ne, flag, &ids, &cnt, st);
@@ -1644,7 +1671,7 @@ extern "C" vla_status vla_mesh_create_rows(int32_t dim, int32_t order, int64_t n
     auto ck = [&](cudaError_t e, const char *what) {
         if (e != cudaSuccess && s == VLA_OK) s = cuda_fail(e, what);
     };
-    ck(cudaMallocAsync(&flag, sizeof(int32_t) * ne, st), "partition flags");
+    ck(pool_malloc((void **)&flag, sizeof(int32_t) * ne, st), "partition flags");
     if (s == VLA_OK) {
         k_block_elem_flags<<<grid_for(ne, 256), 256, 0, st>>>(ne, nlb, elems, row_begin, row_end, flag);
         s = select_flagged(ne, flag, &ids, &nes, st);
@@ -1652,17 +1679,17 @@ extern "C" vla_status vla_mesh_create_rows(int32_t dim, int32_t order, int64_t n
     if (s == VLA_OK && nes == 0)
         s = fail(VLA_ERR_INVALID_ARG, "no element has a node in rows [%d, %d)", row_begin, row_end);
     if (s == VLA_OK) {
-        ck(cudaMallocAsync(&sub, sizeof(int32_t) * nes * nlb, st), "sub-mesh elements");
+        ck(pool_malloc((void **)&sub, sizeof(int32_t) * nes * nlb, st), "sub-mesh elements");
         if (s == VLA_OK) k_gather_rows<<<grid_for(nes * nlb, 256), 256, 0, st>>>(nes, nlb, ids, elems, sub);
     }
     if (s == VLA_OK && nfb > 0) {
-        ck(cudaMallocAsync(&fflag, sizeof(int32_t) * nfb, st), "partition facet flags");
+        ck(pool_malloc((void **)&fflag, sizeof(int32_t) * nfb, st), "partition facet flags");
         if (s == VLA_OK) {
             k_block_facet_flags<<<grid_for(nfb, 256), 256, 0, st>>>(nfb, dim, faces, row_begin, row_end, fflag);
             s = select_flagged(nfb, fflag, &fids, &nfs, st);
         }
         if (s == VLA_OK && nfs > 0) {
-            ck(cudaMallocAsync(&fsub, sizeof(int32_t) * nfs * dim, st), "sub-mesh facets");
+            ck(pool_malloc((void **)&fsub, sizeof(int32_t) * nfs * dim, st), "sub-mesh facets");
             if (s == VLA_OK) k_gather_rows<<<grid_for(nfs * dim, 256), 256, 0, st>>>(nfs, dim, fids, faces, fsub);
         }
     }

@@ -270,7 +270,7 @@ void scheduler(vla_server *s) {
                 SReq *q = take[i];
                 const vla_mesh *m = q->m->mesh;
                 const size_t ob = (size_t)out_bytes(m->nnz, m->ne);
-                if (cudaMallocAsync(&q->out, ob, s->astream) != cudaSuccess) {
+                if (pool_malloc((void **)&q->out, ob, s->astream) != cudaSuccess) {
                     cudaGetLastError();
                     q->out = nullptr;
                     st = fail(VLA_ERR_OOM, "server outputs: out of device memory");
@@ -362,7 +362,7 @@ void ingest_worker(vla_server *s) {
         void *stage = nullptr;
         vla_status st = VLA_OK;
         vla_mesh *mesh = nullptr;
-        if (cudaMallocAsync(&stage, cb + eb + fb + 512, ws) != cudaSuccess) {
+        if (pool_malloc((void **)&stage, cb + eb + fb + 512, ws) != cudaSuccess) {
             cudaGetLastError();
             stage = nullptr;
             st = fail(VLA_ERR_OOM, "server staging: out of device memory");
