@@ -21,6 +21,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <set>
 
 #include "vla_internal.cuh"
 
@@ -516,31 +517,58 @@ __global__ void k_tile_assign(int64_t nn, const int32_t *__restrict__ flag, cons
 // ---------------------------------------------------------------------------
 // per-tile sets (one CTA per tile)
 // ---------------------------------------------------------------------------
-// Thread t handles the indices t, t + blockDim.x, ...; a stage of distance
-// j < 32 pairs index i with i ^ j, handled by thread t ^ j of the same warp.
-// Between two consecutive stages that both have distances below 32 every
-// element is written and read within one warp, so a warp barrier suffices
-// (blockDim.x is a multiple of 32); after a stage of distance 32 or more, and
-// before one, elements cross warps and the block synchronises.  A block
-// barrier also ends the sort.
-__device__ void bitonic_sort(int32_t *a, int n /* power of two */) {
-    for (int k = 2; k <= n; k <<= 1)
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                int l = i ^ j;
-                if (l > i) {
-                    bool up = ((i & k) == 0);
-                    int32_t x = a[i], y = a[l];
-                    if ((x > y) == up) {
-                        a[i] = y;
-                        a[l] = x;
-                    }
+// Sorts n distinct keys (n <= capacity of a, which is a multiple of 64)
+// ascending from a into out.  Each warp sorts runs of 64 keys in registers (a
+// bitonic network over its lanes, two keys per lane, shuffles for the
+// distances below 32), the runs go back to a, padded with INT_MAX; then every
+// key's place is its index in its run plus the number of smaller keys in each
+// other run (a binary search per run).  The keys are distinct, so the places
+// are a permutation.  Ends with a block barrier.
+__device__ void sort_distinct(int32_t *a, int n, int32_t *out) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int nruns = (n + 63) >> 6;
+    for (int r = threadIdx.x >> 5; r < nruns; r += nw) {
+        int32_t *run = a + r * 64;
+        int32_t x0 = r * 64 + lane < n ? run[lane] : 0x7fffffff;
+        int32_t x1 = r * 64 + 32 + lane < n ? run[32 + lane] : 0x7fffffff;
+        // key q = lane + 32 h sits in register h; stage (k, j) pairs q with q ^ j
+        // and keeps the smaller key at the lower index where (q & k) == 0
+#pragma unroll
+        for (int k = 2; k <= 64; k <<= 1)
+#pragma unroll
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                if (j == 32) {   // only with k == 64: the two registers of a lane, ascending
+                    const int32_t lo = min(x0, x1), hi = max(x0, x1);
+                    x0 = lo;
+                    x1 = hi;
+                } else {
+                    const int32_t y0 = __shfl_xor_sync(0xffffffffu, x0, j);
+                    const int32_t y1 = __shfl_xor_sync(0xffffffffu, x1, j);
+                    const bool low = (lane & j) == 0;
+                    const bool up0 = (lane & k) == 0, up1 = ((lane + 32) & k) == 0;
+                    x0 = (low == up0) ? min(x0, y0) : max(x0, y0);
+                    x1 = (low == up1) ? min(x1, y1) : max(x1, y1);
                 }
             }
-            const int next = j > 1 ? j >> 1 : k;   // distance of the next stage (the next k's first is k)
-            if (j < 32 && next < 32) __syncwarp();
-            else __syncthreads();
+        run[lane] = x0;
+        run[32 + lane] = x1;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int32_t x = a[i];
+        const int r = i >> 6;
+        int pos = i & 63;
+        for (int s2 = 0; s2 < nruns; ++s2) {
+            if (s2 == r) continue;
+            const int32_t *run = a + s2 * 64;
+            int lo = 0;   // keys of run s2 below x
+#pragma unroll
+            for (int step = 64; step > 0; step >>= 1)
+                if (lo + step <= 64 && run[lo + step - 1] < x) lo += step;
+            pos += lo;
         }
+        out[pos] = x;
+    }
     __syncthreads();
 }
 
@@ -592,19 +620,23 @@ __device__ int hset_compact(const int32_t *tab, int H, int32_t *out) {
     return n;
 }
 
-// sorts a[0..n) ascending (pads to a power of two with INT_MAX; capacity >= that)
-__device__ void sort_small(int32_t *a, int n) {
-    int p = 1;
-    while (p < n) p <<= 1;
-    for (int i = n + threadIdx.x; i < p; i += blockDim.x) a[i] = 0x7fffffff;
-    __syncthreads();
-    bitonic_sort(a, p);
+// number of entries of the ascending array a[0..n) that are <= x
+__device__ __forceinline__ int upper_bound_i32(const int32_t *a, int n, int32_t x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (a[mid] <= x) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
 }
 
 // Pass A of the tile build: the tile's elements (every element incident to
 // one of its rows: deduplicated in a shared-memory hash set, then sorted;
 // owned elements -- those whose first vertex's row is in the tile -- first),
 // the vertex nodes of those elements (likewise), and the counts of its pairs.
+// The global loads of each step are issued in batches ahead of the set
+// insertions, so a CTA waits for one memory round trip per batch.
 __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e, int cap_n,
                             const int32_t *__restrict__ tile_begin, const int32_t *__restrict__ perm,
                             const int32_t *__restrict__ n2e_ptr, const int32_t *__restrict__ n2e,
@@ -615,56 +647,100 @@ __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e
     extern __shared__ int32_t sm[];
     const int t = blockIdx.x;
     if (t >= n_tiles) return;
+    // cap_e >= B + wmax >= the tile's weight >= its rows and its candidates, and
+    // 2 cap_n >= (dim + 1) cap_e >= 3 cap_e
     int32_t *ce = sm;                 // cap_e: the tile's elements
     int32_t *hs = sm + cap_e;         // 2 cap_n: hash sets, then scratch of the partition
     int32_t *cn = hs + 2 * cap_n;     // cap_n: the tile's vertex nodes
     int32_t *tmp = hs;
     const int rb = tile_begin[t];
     const int re = (t + 1 < n_tiles) ? tile_begin[t + 1] : (int)nn;
+    const int nr = re - rb;
     const int He = 2 * cap_e, Hn = 2 * cap_n;
-    __shared__ int s_ne;
-    if (threadIdx.x == 0) s_ne = 0;
+    // the rows' incidence-list starts (past the element table) and the prefix
+    // of their lengths (in the node list's space, unused until the node phase)
+    int32_t *r_start = hs + He, *r_pre = cn;
     for (int i = threadIdx.x; i < He; i += blockDim.x) hs[i] = -1;
-    __syncthreads();
-    for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
-        const int32_t i = perm[r];
-        const int32_t b = n2e_ptr[i], e = n2e_ptr[i + 1];
-        atomicAdd(&s_ne, e - b);
+    long long ncand_l = 0;
+    for (int c0 = 0; c0 < nr; c0 += blockDim.x) {
+        const int rr = c0 + threadIdx.x;
+        long long len = 0;
+        int32_t st = 0;
+        if (rr < nr) {
+            const int32_t i = perm[rb + rr];
+            st = n2e_ptr[i];
+            len = n2e_ptr[i + 1] - st;
+        }
+        long long tot;
+        const long long pre = block_excl_scan(len, &tot);
+        if (rr < nr) {
+            r_pre[rr] = (int32_t)(ncand_l + pre);
+            r_start[rr] = st;
+        }
+        ncand_l += tot;
     }
-    __syncthreads();
-    const int ncand = s_ne;
-    if (ncand > cap_e) {   // more candidates than the tile was sized for
+    if (ncand_l > cap_e) {   // more candidates than the tile was sized for
         if (threadIdx.x == 0) atomicOr(err, 32);
         return;
     }
-    {   // one warp per row, its lanes over the row's incidence list (a set: the order does not matter)
-        const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        for (int r = rb + (threadIdx.x >> 5); r < re; r += nw) {
-            const int32_t i = perm[r];
-            for (int32_t q = n2e_ptr[i] + lane; q < n2e_ptr[i + 1]; q += 32) hset_insert(hs, He, n2e[q] >> 4);
+    const int ncand = (int)ncand_l;
+    if (threadIdx.x == 0) r_pre[nr] = ncand;
+    __syncthreads();
+    // the rows' incidences as one flat list, four per thread per batch
+    for (int x0 = threadIdx.x; x0 < ncand; x0 += 4 * blockDim.x) {
+        int32_t kk[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int x = x0 + u * blockDim.x;
+            kk[u] = -1;
+            if (x < ncand) {
+                const int rr = upper_bound_i32(r_pre, nr + 1, x) - 1;   // the row whose range holds x
+                kk[u] = n2e[r_start[rr] + (x - r_pre[rr])] >> 4;
+            }
         }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (kk[u] >= 0) hset_insert(hs, He, kk[u]);
     }
     __syncthreads();
-    const int n_el = hset_compact(hs, He, ce);
-    sort_small(ce, n_el);
-    // owned elements first (stable partition)
-    long long obase = 0, hbase = 0, n_own = 0;
-    {
-        long long own = 0;
-        for (int i = threadIdx.x; i < n_el; i += blockDim.x) own += (node_tile[elems[(int64_t)ce[i] * nlb]] == t);
-        block_excl_scan(own, &n_own);
+    // the set's keys past the table, sorted into ce
+    const int n_el = hset_compact(hs, He, hs + He);
+    sort_distinct(hs + He, n_el, ce);
+    // owner flags (past the partition's output in the scratch region)
+    int32_t *oflag = hs + cap_e;
+    long long own = 0;
+    for (int i0 = threadIdx.x; i0 < n_el; i0 += 4 * blockDim.x) {
+        int32_t f[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            f[u] = i < n_el ? elems[(int64_t)ce[i] * nlb] : 0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < n_el) {
+                const int o = node_tile[f[u]] == t;
+                oflag[i] = o;
+                own += o;
+            }
+        }
     }
+    long long n_own = 0;
+    block_excl_scan(own, &n_own);   // synchronises: the flags are visible below
+    // owned elements first (stable partition)
+    long long obase = 0, hbase = 0;
     for (int c0 = 0; c0 < n_el; c0 += blockDim.x) {
         const int i = c0 + threadIdx.x;
-        int own = 0, halo = 0;
+        int o = 0, halo = 0;
         if (i < n_el) {
-            own = node_tile[elems[(int64_t)ce[i] * nlb]] == t;
-            halo = !own;
+            o = oflag[i];
+            halo = !o;
         }
         long long tot_o, tot_h;
-        long long po = block_excl_scan(own, &tot_o);
+        long long po = block_excl_scan(o, &tot_o);
         long long ph = block_excl_scan(halo, &tot_h);
-        if (own) tmp[obase + po] = ce[i];
+        if (o) tmp[obase + po] = ce[i];
         if (halo) tmp[n_own + hbase + ph] = ce[i];
         obase += tot_o;
         hbase += tot_h;
@@ -685,11 +761,21 @@ __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e
     while (Hu < 2 * nnc && Hu < Hn) Hu <<= 1;
     for (int i = threadIdx.x; i < Hu; i += blockDim.x) hs[i] = -1;
     __syncthreads();
-    for (int i = threadIdx.x; i < nnc; i += blockDim.x) hset_insert(hs, Hu, elems[(int64_t)ce[i / nv] * nlb + (i % nv)]);
+    for (int x0 = threadIdx.x; x0 < nnc; x0 += 8 * blockDim.x) {
+        int32_t vv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int x = x0 + u * blockDim.x;
+            vv[u] = x < nnc ? elems[(int64_t)ce[x / nv] * nlb + (x % nv)] : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (vv[u] >= 0) hset_insert(hs, Hu, vv[u]);
+    }
     __syncthreads();
     const int n_nd = hset_compact(hs, Hu, cn);
-    sort_small(cn, n_nd);
-    for (int i = threadIdx.x; i < n_nd; i += blockDim.x) sc_nodes[(int64_t)t * cap_n + i] = cn[i];
+    sort_distinct(cn, n_nd, hs);   // the table is dead after the compaction
+    for (int i = threadIdx.x; i < n_nd; i += blockDim.x) sc_nodes[(int64_t)t * cap_n + i] = hs[i];
     // upper pairs {i, j > i} and diagonals of the tile's rows
     long long up = 0, dg = 0;
     for (int r = rb + threadIdx.x; r < re; r += blockDim.x) {
@@ -724,26 +810,58 @@ __device__ __forceinline__ int tile_local_elem(const int32_t *te, int n_own, int
     return n_own + lower_bound_i32(te + n_own, n_el - n_own, k);
 }
 
+// number of a row's columns below i (the diagonal's offset in the row), by a warp
+__device__ __forceinline__ int warp_count_below(const int32_t *__restrict__ col, int len, int32_t i) {
+    const int lane = threadIdx.x & 31;
+    int n = 0;
+    for (int s0 = 0; s0 < len; s0 += 32) {
+        const int s = s0 + lane;
+        n += __popc(__ballot_sync(0xffffffffu, s < len && col[s] < i));
+    }
+    return n;
+}
+
+// The rows of a tile are visited by warps, one row at a time.  A row's pairs
+// (its upper pairs {i, c > i} in column order, then the diagonal {i, i}) are
+// held one per lane, 32 at a time; its incidences (ascending element order)
+// one per lane, 32 at a time.  For each pair, the ballot of the incidences
+// whose element holds the pair's other node counts the pair's contributions
+// and ranks each contributing incidence among them (incidence order, which is
+// element order): the count pass and the code pass see the contributions in
+// the same order a single thread walking the row would.
+
 // Pass B: node lists, element records, owned ids, pair positions and the
-// contribution count of every pair.
-__global__ void k_tile_fill(int n_tiles, int dim, int nlb, int cap_e, int cap_n, const TileHdr *__restrict__ hdr,
-                            const int32_t *__restrict__ perm, const int32_t *__restrict__ n2e_ptr,
-                            const int32_t *__restrict__ n2e, const int32_t *__restrict__ elems,
-                            const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
-                            const int32_t *__restrict__ sc_elems, const int32_t *__restrict__ sc_nodes,
-                            int32_t *__restrict__ tile_nodes, ushort4 *__restrict__ tile_elem,
-                            int32_t *__restrict__ tile_own, int2 *__restrict__ tile_nzpos,
-                            int32_t *__restrict__ nz_count, int2 *__restrict__ row_info) {
+// contribution count of every pair.  Dynamic shared memory: the tile's node
+// list (n_nodes ints), searched for the elements' local vertex indices.
+template <int NLB>
+__global__ void __launch_bounds__(256) k_tile_fill(int n_tiles, int dim, int cap_e, int cap_n,
+                                                   const TileHdr *__restrict__ hdr, const int32_t *__restrict__ perm,
+                                                   const int32_t *__restrict__ n2e_ptr, const int32_t *__restrict__ n2e,
+                                                   const int32_t *__restrict__ elems, const int32_t *__restrict__ row_ptr,
+                                                   const int32_t *__restrict__ col_idx,
+                                                   const int32_t *__restrict__ sc_elems,
+                                                   const int32_t *__restrict__ sc_nodes, int32_t *__restrict__ tile_nodes,
+                                                   ushort4 *__restrict__ tile_elem, int32_t *__restrict__ tile_own,
+                                                   int2 *__restrict__ tile_nzpos, int32_t *__restrict__ nz_count,
+                                                   int2 *__restrict__ row_info) {
+    extern __shared__ int32_t s_tn[];
     const int t = blockIdx.x;
     if (t >= n_tiles) return;
     const TileHdr h = hdr[t];
     const int32_t *te = sc_elems + (int64_t)t * cap_e;
     const int32_t *tn = sc_nodes + (int64_t)t * cap_n;
-    for (int i = threadIdx.x; i < h.n_nodes; i += blockDim.x) tile_nodes[h.node_off + i] = tn[i];
+    for (int i = threadIdx.x; i < h.n_nodes; i += blockDim.x) {
+        const int32_t v = tn[i];
+        s_tn[i] = v;
+        tile_nodes[h.node_off + i] = v;
+    }
+    __syncthreads();
     for (int e = threadIdx.x; e < h.n_elems; e += blockDim.x) {
         const int64_t k = te[e];
         unsigned short v[4] = {0, 0, 0, 0};
-        for (int j = 0; j <= dim; ++j) v[j] = (unsigned short)lower_bound_i32(tn, h.n_nodes, elems[k * nlb + j]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+            if (j <= dim) v[j] = (unsigned short)lower_bound_i32(s_tn, h.n_nodes, elems[k * NLB + j]);
         tile_elem[h.elem_off + e] = make_ushort4(v[0], v[1], v[2], v[3]);
         if (e < h.n_own) tile_own[h.own_off + e] = (int32_t)k;
     }
@@ -774,33 +892,44 @@ __global__ void k_tile_fill(int n_tiles, int dim, int nlb, int cap_e, int cap_n,
                 const int32_t bj = row_ptr[j], lj = row_ptr[j + 1] - bj;
                 const int32_t pji = bj + lower_bound_i32(col_idx + bj, lj, i);
                 tile_nzpos[h.nz_off + qu + (s - ds - 1)] = make_int2(b + s, pji);
-                nz_count[h.nz_off + qu + (s - ds - 1)] = 0;
             }
-            if (hasd) {
-                tile_nzpos[h.nz_off + qd] = make_int2(b + ds, b + ds);
-                nz_count[h.nz_off + qd] = 0;
-            }
+            if (hasd) tile_nzpos[h.nz_off + qd] = make_int2(b + ds, b + ds);
             row_info[h.rank_begin + rr] = make_int2(qu, qd);
         }
         ubase += tot_u;
         dbase += tot_d;
     }
     __syncthreads();
-    // contribution counts: one thread per row, every pair it owns is private to it
-    for (int rr = threadIdx.x; rr < h.n_rows; rr += blockDim.x) {
+    // contribution counts (every pair of the tile written once)
+    const int lane = threadIdx.x & 31;
+    for (int rr = threadIdx.x >> 5; rr < h.n_rows; rr += blockDim.x >> 5) {
         const int32_t i = perm[h.rank_begin + rr];
         const int32_t b = row_ptr[i], len = row_ptr[i + 1] - b;
         if (len == 0) continue;
         const int2 ri = row_info[h.rank_begin + rr];
-        const int ds = lower_bound_i32(col_idx + b, len, i);
-        for (int32_t q = n2e_ptr[i]; q < n2e_ptr[i + 1]; ++q) {
-            const int64_t k = n2e[q] >> 4;
-            for (int bb = 0; bb < nlb; ++bb) {
-                const int32_t c = elems[k * nlb + bb];
-                if (c < i) continue;
-                const int32_t qq = (c == i) ? ri.y : ri.x + lower_bound_i32(col_idx + b, len, c) - ds - 1;
-                nz_count[h.nz_off + qq] += 1;
+        const int ds = warp_count_below(col_idx + b, len, i);
+        const int np = len - ds;
+        const int32_t q0 = n2e_ptr[i], nq = n2e_ptr[i + 1] - q0;
+        for (int p0 = 0; p0 < np; p0 += 32) {
+            const int pp = p0 + lane, npq = min(32, np - p0);
+            const int32_t c_pp = pp < np - 1 ? col_idx[b + ds + 1 + pp] : i;
+            int cnt = 0;
+            for (int j0 = 0; j0 < nq; j0 += 32) {
+                const bool valid = j0 + lane < nq;
+                const int64_t k = valid ? (int64_t)(n2e[q0 + j0 + lane] >> 4) : 0;
+                int32_t v[NLB];
+#pragma unroll
+                for (int bb = 0; bb < NLB; ++bb) v[bb] = valid ? elems[k * NLB + bb] : -1;
+                for (int q = 0; q < npq; ++q) {
+                    const int32_t c = __shfl_sync(0xffffffffu, c_pp, q);
+                    bool hit = false;
+#pragma unroll
+                    for (int bb = 0; bb < NLB; ++bb) hit |= v[bb] == c;
+                    const int n = __popc(__ballot_sync(0xffffffffu, hit));
+                    if (lane == q) cnt += n;
+                }
             }
+            if (pp < np) nz_count[h.nz_off + (pp == np - 1 ? ri.y : ri.x + pp)] = cnt;
         }
     }
 }
@@ -870,43 +999,73 @@ __global__ void k_chunk_table(int n_tiles, const TileHdr *__restrict__ hdr, cons
 
 // Pass C: contribution codes, element * rsc + packed (a,b) entry (the entry's
 // word offset in a record of stride rsc), ascending element order per pair;
-// padding slots point at the tile's zero element.
-template <typename CT>
-__global__ void k_tile_codes(int n_tiles, int nv, int nlb, int cap_e, int rsc, const TileHdr *__restrict__ hdr,
-                             const int32_t *__restrict__ perm, const int32_t *__restrict__ n2e_ptr,
-                             const int32_t *__restrict__ n2e, const int32_t *__restrict__ elems,
-                             const int32_t *__restrict__ row_ptr, const int32_t *__restrict__ col_idx,
-                             const int32_t *__restrict__ sc_elems, const int2 *__restrict__ row_info,
-                             const int32_t *__restrict__ order, const int2 *__restrict__ chunks,
-                             int32_t *__restrict__ fill, CT *__restrict__ codes) {
+// padding slots point at the tile's zero element.  Dynamic shared memory:
+// the tile's element list (n_elems ints), searched for local element indices.
+template <int NLB, typename CT>
+__global__ void __launch_bounds__(256) k_tile_codes(int n_tiles, int cap_e, int rsc, const TileHdr *__restrict__ hdr,
+                                                    const int32_t *__restrict__ perm,
+                                                    const int32_t *__restrict__ n2e_ptr,
+                                                    const int32_t *__restrict__ n2e, const int32_t *__restrict__ elems,
+                                                    const int32_t *__restrict__ row_ptr,
+                                                    const int32_t *__restrict__ col_idx,
+                                                    const int32_t *__restrict__ sc_elems,
+                                                    const int2 *__restrict__ row_info,
+                                                    const int32_t *__restrict__ order, const int2 *__restrict__ chunks,
+                                                    CT *__restrict__ codes) {
+    extern __shared__ int32_t s_te[];
     const int t = blockIdx.x;
     if (t >= n_tiles) return;
     const TileHdr h = hdr[t];
     const int32_t *te = sc_elems + (int64_t)t * cap_e;
+    for (int i = threadIdx.x; i < h.n_elems; i += blockDim.x) s_te[i] = te[i];
     const CT dummy = (CT)((uint32_t)h.n_elems * (uint32_t)rsc);
     for (int i = threadIdx.x; i < h.n_codes; i += blockDim.x) codes[(int64_t)h.code_off + i] = dummy;
     __syncthreads();
-    for (int rr = threadIdx.x; rr < h.n_rows; rr += blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const unsigned below = (1u << lane) - 1u;
+    for (int rr = threadIdx.x >> 5; rr < h.n_rows; rr += blockDim.x >> 5) {
         const int32_t i = perm[h.rank_begin + rr];
         const int32_t b = row_ptr[i], len = row_ptr[i + 1] - b;
         if (len == 0) continue;
         const int2 ri = row_info[h.rank_begin + rr];
-        const int ds = lower_bound_i32(col_idx + b, len, i);
-        for (int32_t q = n2e_ptr[i]; q < n2e_ptr[i + 1]; ++q) {
-            const int64_t k = n2e[q] >> 4;
-            const int a = n2e[q] & 15;
-            const int el = tile_local_elem(te, h.n_own, h.n_elems, (int32_t)k);
-            for (int bb = 0; bb < nlb; ++bb) {
-                const int32_t c = elems[k * nlb + bb];
-                if (c < i) continue;
-                const int32_t qq = (c == i) ? ri.y : ri.x + lower_bound_i32(col_idx + b, len, c) - ds - 1;
-                const int nq = order[h.nz_off + qq];
-                const int chunk = nq >> 5, lane = nq & 31;
-                const int tt = fill[h.nz_off + qq]++;
-                const int2 ch = chunks[h.chunk_off + chunk];
-                const int p = a < bb ? a : bb, r = a < bb ? bb : a;
-                const uint32_t u = (uint32_t)(p * nlb - p * (p - 1) / 2 + (r - p));
-                codes[(int64_t)h.code_off + ch.x + tt * 32 + lane] = (CT)((uint32_t)el * (uint32_t)rsc + u);
+        const int ds = warp_count_below(col_idx + b, len, i);
+        const int np = len - ds;
+        const int32_t q0 = n2e_ptr[i], nq = n2e_ptr[i + 1] - q0;
+        for (int p0 = 0; p0 < np; p0 += 32) {
+            const int pp = p0 + lane, npq = min(32, np - p0);
+            const int32_t c_pp = pp < np - 1 ? col_idx[b + ds + 1 + pp] : i;
+            int base_pp = 0;   // the pair's first slot: its chunk's code offset plus its lane in the chunk
+            if (pp < np) {
+                const int nqo = order[h.nz_off + (pp == np - 1 ? ri.y : ri.x + pp)];
+                base_pp = chunks[h.chunk_off + (nqo >> 5)].x + (nqo & 31);
+            }
+            int cnt = 0;
+            for (int j0 = 0; j0 < nq; j0 += 32) {
+                const bool valid = j0 + lane < nq;
+                const int32_t word = valid ? n2e[q0 + j0 + lane] : 0;
+                const int64_t k = word >> 4;
+                const int a = word & 15;
+                int32_t v[NLB];
+#pragma unroll
+                for (int bb = 0; bb < NLB; ++bb) v[bb] = valid ? elems[k * NLB + bb] : -1;
+                const int el = valid ? tile_local_elem(s_te, h.n_own, h.n_elems, (int32_t)k) : 0;
+                for (int q = 0; q < npq; ++q) {
+                    const int32_t c = __shfl_sync(0xffffffffu, c_pp, q);
+                    const int bs = __shfl_sync(0xffffffffu, base_pp, q);
+                    const int cb = __shfl_sync(0xffffffffu, cnt, q);
+                    int hb = -1;
+#pragma unroll
+                    for (int bb = 0; bb < NLB; ++bb)
+                        if (v[bb] == c) hb = bb;
+                    const unsigned m = __ballot_sync(0xffffffffu, hb >= 0);
+                    if (hb >= 0) {
+                        const int tt = cb + __popc(m & below);
+                        const int p = a < hb ? a : hb, r = a < hb ? hb : a;
+                        const uint32_t u = (uint32_t)(p * NLB - p * (p - 1) / 2 + (r - p));
+                        codes[(int64_t)h.code_off + bs + tt * 32] = (CT)((uint32_t)el * (uint32_t)rsc + u);
+                    }
+                    if (lane == q) cnt += __popc(m);
+                }
             }
         }
     }
@@ -951,22 +1110,22 @@ struct Scratch {  // temporary device buffers freed at the end of the build
 };
 
 
-// k_tile_sets takes a dynamic shared-memory size that depends on the mesh;
-// its limit is raised to the device maximum once per device (meshes built
-// concurrently on several host threads must not change it under each other)
-vla_status allow_max_smem_tile_sets() {
+// the tile kernels take dynamic shared-memory sizes that depend on the mesh;
+// a kernel's limit is raised to the device maximum once per device (meshes
+// built concurrently on several host threads must not change it under each
+// other)
+vla_status allow_max_smem(const void *fn) {
     static std::mutex mu;
-    static bool done[64] = {};
+    static std::set<std::pair<int, const void *>> done;
     int dev = 0, maxsm = 0;
     VLA_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lk(mu);
-    if (dev >= 0 && dev < 64 && done[dev]) return VLA_OK;
+    if (done.count({dev, fn})) return VLA_OK;
     VLA_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     cudaFuncAttributes fa;
-    VLA_CUDA(cudaFuncGetAttributes(&fa, k_tile_sets));
-    VLA_CUDA(cudaFuncSetAttribute(k_tile_sets, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  maxsm - (int)fa.sharedSizeBytes));
-    if (dev >= 0 && dev < 64) done[dev] = true;
+    VLA_CUDA(cudaFuncGetAttributes(&fa, fn));
+    VLA_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, maxsm - (int)fa.sharedSizeBytes));
+    done.insert({dev, fn});
     return VLA_OK;
 }
 
@@ -1168,7 +1327,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
             if (smemA + 1024 > (size_t)maxsm_)
                 return fail(VLA_ERR_UNSUPPORTED, "tile budget %d too large for the tile builder", B);
         }
-        TRY(allow_max_smem_tile_sets());
+        TRY(allow_max_smem((const void *)k_tile_sets));
         k_tile_sets<<<(int)n_tiles, 256, smemA, st>>>((int)n_tiles, nn, dim, nlb, cap_e, cap_n, tile_begin, perm,
                                                        m->n2e_ptr, m->n2e, m->elems, m->row_ptr, m->col_idx, node_tile,
                                                        sc_elems, sc_nodes, tcnt, d_err);
@@ -1251,10 +1410,14 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         TRY(S.get(&nzpos_rm, o_nz + 2));
         TRY(S.get(&row_info, nn));
         TRY(S.get(&tile_ncodes, n_tiles));
-        k_tile_fill<<<(int)n_tiles, 64, 0, st>>>((int)n_tiles, dim, nlb, cap_e, cap_n, m->tiles, perm, m->n2e_ptr,
-                                                  m->n2e, m->elems, m->row_ptr, m->col_idx, sc_elems, sc_nodes,
-                                                  m->tile_nodes, m->tile_elem, m->tile_own, nzpos_rm, nz_count,
-                                                  row_info);
+        {
+            auto kf = nlb == 3 ? k_tile_fill<3> : nlb == 4 ? k_tile_fill<4> : nlb == 6 ? k_tile_fill<6> : k_tile_fill<10>;
+            TRY(allow_max_smem((const void *)kf));
+            kf<<<(int)n_tiles, 256, sizeof(int32_t) * (size_t)std::max(1, m->max_tile_nodes), st>>>(
+                (int)n_tiles, dim, cap_e, cap_n, m->tiles, perm, m->n2e_ptr, m->n2e, m->elems, m->row_ptr, m->col_idx,
+                sc_elems, sc_nodes, m->tile_nodes, m->tile_elem, m->tile_own, nzpos_rm, nz_count, row_info);
+            VLA_CUDA(cudaGetLastError());
+        }
         k_chunk_table<<<(int)n_tiles, 64, 0, st>>>((int)n_tiles, m->tiles, nz_count, nzpos_rm, m->tile_nzpos, nz_order,
                                                     m->tile_chunks, tile_ncodes);
         VLA_CUDA(cudaGetLastError());
@@ -1297,24 +1460,24 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         m->n_codes = o_code;
         VLA_CUDA(cudaMemcpyAsync(m->tiles, hh, sizeof(TileHdr) * n_tiles, cudaMemcpyHostToDevice, st));
         const int rsc = (nlb * (nlb + 1) / 2 + 1) | 1;   // code stride: the mixed-precision record stride
-        int32_t *fill;
-        TRY(S.get(&fill, o_nz + 2));
-        VLA_CUDA(cudaMemsetAsync(fill, 0, sizeof(int32_t) * (o_nz + 2), st));
+        const size_t smem_codes = sizeof(int32_t) * (size_t)std::max(1, m->max_tile_elems);
         if (m->order == 1) {
             uint16_t *codes;
             TRY(dalloc(m, &codes, o_code + 64, st));
-            k_tile_codes<uint16_t><<<(int)n_tiles, 64, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, rsc, m->tiles, perm,
-                                                                     m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
-                                                                     m->col_idx, sc_elems, row_info, nz_order,
-                                                                     m->tile_chunks, fill, codes);
+            auto kc = nlb == 3 ? k_tile_codes<3, uint16_t> : k_tile_codes<4, uint16_t>;
+            TRY(allow_max_smem((const void *)kc));
+            kc<<<(int)n_tiles, 256, smem_codes, st>>>((int)n_tiles, cap_e, rsc, m->tiles, perm, m->n2e_ptr, m->n2e,
+                                                      m->elems, m->row_ptr, m->col_idx, sc_elems, row_info, nz_order,
+                                                      m->tile_chunks, codes);
             m->tile_codes = codes;
         } else {
             uint32_t *codes;
             TRY(dalloc(m, &codes, o_code + 64, st));
-            k_tile_codes<uint32_t><<<(int)n_tiles, 64, 0, st>>>((int)n_tiles, dim + 1, nlb, cap_e, rsc, m->tiles, perm,
-                                                                     m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
-                                                                     m->col_idx, sc_elems, row_info, nz_order,
-                                                                     m->tile_chunks, fill, codes);
+            auto kc = nlb == 6 ? k_tile_codes<6, uint32_t> : k_tile_codes<10, uint32_t>;
+            TRY(allow_max_smem((const void *)kc));
+            kc<<<(int)n_tiles, 256, smem_codes, st>>>((int)n_tiles, cap_e, rsc, m->tiles, perm, m->n2e_ptr, m->n2e,
+                                                      m->elems, m->row_ptr, m->col_idx, sc_elems, row_info, nz_order,
+                                                      m->tile_chunks, codes);
             m->tile_codes = codes;
         }
         VLA_CUDA(cudaGetLastError());
