@@ -259,13 +259,16 @@ __global__ void __launch_bounds__(kSegWarps * 32) k_sort_segments(int64_t n, con
     }
 }
 
-// CSR row sets, one warp per row: every node of every incident element goes
-// into a hash set in shared memory of at least twice as many slots as
-// candidates, up to 512 (a row longer than kMaxRow is an error, so a set of
-// more than 256 keys is never needed), then the keys are sorted by a warp
-// bitonic sort and written to the row's scratch slot.
+// CSR row sets, one warp per row: the nodes of the row's incident elements
+// (one incidence per lane, its element's nodes loaded together) go into a
+// hash set in shared memory of at least twice as many slots as candidates,
+// up to 512 (a row longer than kMaxRow is an error, so a set of more than 256
+// keys is never needed); the keys are sorted (up to 32 by a bitonic network
+// across the lanes, more by a bitonic sort in shared memory) and written to
+// the row's scratch slot.
 constexpr int kRowWarps = 8, kRowHash = 512;
-__global__ void __launch_bounds__(kRowWarps * 32) k_row_count(int64_t nn, int nlb, const int32_t *__restrict__ elems,
+template <int NLB>
+__global__ void __launch_bounds__(kRowWarps * 32) k_row_count(int64_t nn, const int32_t *__restrict__ elems,
                                                               const int32_t *__restrict__ n2e_ptr,
                                                               const int32_t *__restrict__ n2e,
                                                               int32_t *__restrict__ scratch,
@@ -278,25 +281,34 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_row_count(int64_t nn, int nl
     int32_t *tab = hs[w], *ks = key[w];
     for (int64_t i = (int64_t)blockIdx.x * kRowWarps + w; i < nn; i += (int64_t)gridDim.x * kRowWarps) {
         const int32_t b = n2e_ptr[i], e = n2e_ptr[i + 1];
-        const int ncand = (e - b) * nlb;
+        const int nq = e - b, ncand = nq * NLB;
         // a table of at least twice the candidates (at most kRowHash): the set never fills past half
         int H = 32;
         while (H < 2 * ncand && H < kRowHash) H <<= 1;
         for (int q = lane; q < H; q += 32) tab[q] = -1;
         if (lane == 0) cnt[w] = 0;
         __syncwarp();
-        for (int c = lane; c < ncand; c += 32) {
-            const int64_t k = (int64_t)(n2e[b + c / nlb] >> 4);
-            const int32_t x = elems[k * nlb + (c % nlb)];
-            uint32_t h = ((uint32_t)x * 2654435761u) & (uint32_t)(H - 1);
-            for (int probe = 0; probe < H; ++probe) {
-                const int32_t prev = atomicCAS(&tab[h], -1, x);
-                if (prev == -1) {
-                    atomicAdd(&cnt[w], 1);
-                    break;
+        for (int q0 = 0; q0 < nq; q0 += 32) {
+            const int q = q0 + lane;
+            int32_t v[NLB];
+            if (q < nq) {
+                const int64_t k = (int64_t)(n2e[b + q] >> 4);
+#pragma unroll
+                for (int bb = 0; bb < NLB; ++bb) v[bb] = elems[k * NLB + bb];
+#pragma unroll
+                for (int bb = 0; bb < NLB; ++bb) {
+                    const int32_t x = v[bb];
+                    uint32_t h = ((uint32_t)x * 2654435761u) & (uint32_t)(H - 1);
+                    for (int probe = 0; probe < H; ++probe) {
+                        const int32_t prev = atomicCAS(&tab[h], -1, x);
+                        if (prev == -1) {
+                            atomicAdd(&cnt[w], 1);
+                            break;
+                        }
+                        if (prev == x) break;
+                        h = (h + 1) & (uint32_t)(H - 1);
+                    }
                 }
-                if (prev == x) break;
-                h = (h + 1) & (uint32_t)(H - 1);
             }
         }
         __syncwarp();
@@ -309,7 +321,7 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_row_count(int64_t nn, int nl
             __syncwarp();
             continue;
         }
-        // compact, pad to a power of two, bitonic sort within the warp
+        // compact
         int base = 0;
         for (int q0 = 0; q0 < H; q0 += 32) {
             const int32_t x = tab[q0 + lane];
@@ -317,27 +329,40 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_row_count(int64_t nn, int nl
             if (x >= 0) ks[base + __popc(m & ((1u << lane) - 1u))] = x;
             base += __popc(m);
         }
-        int P = 1;
-        while (P < n) P <<= 1;
-        for (int q = n + lane; q < P; q += 32) ks[q] = 0x7fffffff;
         __syncwarp();
-        for (int kk = 2; kk <= P; kk <<= 1)
-            for (int j = kk >> 1; j > 0; j >>= 1) {
-                for (int q = lane; q < P; q += 32) {
-                    const int l = q ^ j;
-                    if (l > q) {
-                        const bool up = (q & kk) == 0;
-                        const int32_t x = ks[q], y = ks[l];
-                        if ((x > y) == up) {
-                            ks[q] = y;
-                            ks[l] = x;
+        int32_t *u = scratch + (int64_t)NLB * b;
+        if (n <= 32) {   // one key per lane, bitonic network over the lanes
+            int32_t x = lane < n ? ks[lane] : 0x7fffffff;
+#pragma unroll
+            for (int k = 2; k <= 32; k <<= 1)
+#pragma unroll
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    const int32_t y = __shfl_xor_sync(0xffffffffu, x, j);
+                    x = (((lane & j) == 0) == ((lane & k) == 0)) ? min(x, y) : max(x, y);
+                }
+            if (lane < n) u[lane] = x;
+        } else {   // pad to a power of two, bitonic sort in shared memory
+            int P = 1;
+            while (P < n) P <<= 1;
+            for (int q = n + lane; q < P; q += 32) ks[q] = 0x7fffffff;
+            __syncwarp();
+            for (int kk = 2; kk <= P; kk <<= 1)
+                for (int j = kk >> 1; j > 0; j >>= 1) {
+                    for (int q = lane; q < P; q += 32) {
+                        const int l = q ^ j;
+                        if (l > q) {
+                            const bool up = (q & kk) == 0;
+                            const int32_t x = ks[q], y = ks[l];
+                            if ((x > y) == up) {
+                                ks[q] = y;
+                                ks[l] = x;
+                            }
                         }
                     }
+                    __syncwarp();
                 }
-                __syncwarp();
-            }
-        int32_t *u = scratch + (int64_t)nlb * b;
-        for (int q = lane; q < n; q += 32) u[q] = ks[q];
+            for (int q = lane; q < n; q += 32) u[q] = ks[q];
+        }
         if (lane == 0) rowlen[i] = n;
         __syncwarp();
     }
@@ -887,12 +912,6 @@ __global__ void __launch_bounds__(256) k_tile_fill(int n_tiles, int dim, int cap
         if (rr < h.n_rows) {
             const int32_t qu = (int32_t)(ubase + pu);
             const int32_t qd = hasd ? h.n_up + (int32_t)(dbase + pd) : -1;
-            for (int s = ds + 1; s < len; ++s) {
-                const int32_t j = col_idx[b + s];
-                const int32_t bj = row_ptr[j], lj = row_ptr[j + 1] - bj;
-                const int32_t pji = bj + lower_bound_i32(col_idx + bj, lj, i);
-                tile_nzpos[h.nz_off + qu + (s - ds - 1)] = make_int2(b + s, pji);
-            }
             if (hasd) tile_nzpos[h.nz_off + qd] = make_int2(b + ds, b + ds);
             row_info[h.rank_begin + rr] = make_int2(qu, qd);
         }
@@ -900,7 +919,8 @@ __global__ void __launch_bounds__(256) k_tile_fill(int n_tiles, int dim, int cap
         dbase += tot_d;
     }
     __syncthreads();
-    // contribution counts (every pair of the tile written once)
+    // CSR positions (p_ij, p_ji) of the upper pairs and contribution counts of
+    // every pair (each written once)
     const int lane = threadIdx.x & 31;
     for (int rr = threadIdx.x >> 5; rr < h.n_rows; rr += blockDim.x >> 5) {
         const int32_t i = perm[h.rank_begin + rr];
@@ -913,6 +933,10 @@ __global__ void __launch_bounds__(256) k_tile_fill(int n_tiles, int dim, int cap
         for (int p0 = 0; p0 < np; p0 += 32) {
             const int pp = p0 + lane, npq = min(32, np - p0);
             const int32_t c_pp = pp < np - 1 ? col_idx[b + ds + 1 + pp] : i;
+            if (pp < np - 1) {   // upper pair {i, c}: its place in row c by a search of that row
+                const int32_t bj = row_ptr[c_pp], lj = row_ptr[c_pp + 1] - bj;
+                tile_nzpos[h.nz_off + ri.x + pp] = make_int2(b + ds + 1 + pp, bj + lower_bound_i32(col_idx + bj, lj, i));
+            }
             int cnt = 0;
             for (int j0 = 0; j0 < nq; j0 += 32) {
                 const bool valid = j0 + lane < nq;
@@ -1205,8 +1229,11 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     int32_t *scratch, *rowlen;
     TRY(S.get(&scratch, (size_t)n2e_total * nlb));
     TRY(S.get(&rowlen, nn));
-    k_row_count<<<grid_for((nn + kRowWarps - 1) / kRowWarps, 1), kRowWarps * 32, 0, st>>>(nn, nlb, m->elems, m->n2e_ptr,
-                                                                                        m->n2e, scratch, rowlen, d_err);
+    {
+        auto kr = nlb == 3 ? k_row_count<3> : nlb == 4 ? k_row_count<4> : nlb == 6 ? k_row_count<6> : k_row_count<10>;
+        kr<<<grid_for((nn + kRowWarps - 1) / kRowWarps, 1), kRowWarps * 32, 0, st>>>(nn, m->elems, m->n2e_ptr, m->n2e,
+                                                                                     scratch, rowlen, d_err);
+    }
     VLA_CUDA(cudaGetLastError());
     long long nnz = 0;
     VLA_CUDA(cudaMemsetAsync(dsc + 1, 0, sizeof(long long), st));
