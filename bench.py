@@ -31,7 +31,8 @@ Other workloads (--workload): pages (page primitives at N = 1e8), batch (256
 meshes of all four element types in one persistent launch), serve (a Poisson
 request stream through the server), next (the rows beyond the assembly core,
 one timed call each on the bench mesh), small (p50/p99 latency of the FP64
-call with element pages on the 3,072-tet mesh).
+call with element pages on the 3,072-tet mesh), build (mesh build latency by
+size).
 
 Multi-GPU (torchrun): the one mesh is split by rows -- rank r of N owns the
 contiguous node rows [nn r / N, nn (r+1) / N) and assembles the sub-mesh of
@@ -735,6 +736,52 @@ def run_serve(args):
     return 0
 
 
+def run_build(args):
+    """Mesh build latency by size: `vla_mesh_create` (validation, CSR pattern,
+    row tiles; synchronous) on device-resident inputs, for P1/P2 triangles and
+    tetrahedra from hundreds to 1.57 M elements.  Per size one untimed build,
+    then the median and maximum of --build-reps builds by the host clock
+    around the call (the call synchronises).  `value` is the median for the
+    bench mesh (64^3 x 6 Kuhn tets).  VLA_POOL_KEEP (bytes of freed device
+    memory the library keeps mapped between calls) is reported as set."""
+    import torch
+    import meshgen
+    import paper_2404_16039_gb300 as vla
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    cases = [(3, 1, 5), (3, 1, 12), (3, 1, 25), (3, 1, 50), (3, 1, 64), (3, 2, 6), (3, 2, 20), (2, 1, 30),
+             (2, 1, 300), (2, 2, 100)]
+    rows, value = [], None
+    for dim, order, n in cases:
+        m = meshgen.kuhn_cube(n, jitter=0.1, seed=0) if (dim, order) == (3, 1) else \
+            meshgen.make_mesh(dim, n, order=order, jitter=0.1, seed=1)
+        c, e = torch.from_numpy(m.coords).to(dev), torch.from_numpy(m.elems).to(dev)
+        f = torch.from_numpy(m.faces).to(dev) if m.nfb else None
+        ts = []
+        for r in range(args.build_reps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = vla.Mesh(c, e, f, order=order)
+            ts.append((time.perf_counter() - t0) * 1e3)
+            g.close()
+        ts = ts[1:]
+        row = {"dim": dim, "order": order, "ne": int(m.ne), "nn": int(m.nn), "median_ms": float(np.median(ts)),
+               "max_ms": float(np.max(ts))}
+        rows.append(row)
+        if (dim, order, n) == (3, 1, 64):
+            value = row["median_ms"]
+        print(json.dumps(row), file=sys.stderr, flush=True)
+    line = {"metric": "mesh build latency (vla_mesh_create) of the 64^3 x 6 Kuhn cube", "value": value, "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": args.build_reps, "warmup": 1, "data": "synthetic",
+            "config": {"workload": "vla_mesh_create on device-resident inputs, sizes " +
+                                   ", ".join(f"{r['ne']} {'tets' if r['dim'] == 3 else 'triangles'} P{r['order']}"
+                                             for r in rows),
+                       "pool_keep_bytes": os.environ.get("VLA_POOL_KEEP", "default (min(8 GiB, HBM/16))")},
+            "sizes": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_small(args):
     """The small FP64 case with element pages: Kuhn 8^3 x 6 (3,072 tets, 729
     nodes), c = 1, K, M, volumes and both page arrays in FP64 from one call,
@@ -952,7 +999,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="p1tet", choices=["p1tet", "pages", "batch", "serve", "next", "small"])
+    ap.add_argument("--workload", default="p1tet", choices=["p1tet", "pages", "batch", "serve", "next", "small", "build"])
+    ap.add_argument("--build-reps", type=int, default=5)
     ap.add_argument("--small-reps", type=int, default=1000)
     ap.add_argument("--latency-reps", type=int, default=1000)
     ap.add_argument("--pages-n", default="100000000")
@@ -982,6 +1030,8 @@ def main():
         return run_next(args)
     if args.workload == "small":
         return run_small(args)
+    if args.workload == "build":
+        return run_build(args)
 
     import torch
     import meshgen
