@@ -686,7 +686,10 @@ __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e
     // of their lengths (in the node list's space, unused until the node phase)
     int32_t *r_start = hs + He, *r_pre = cn;
     for (int i = threadIdx.x; i < He; i += blockDim.x) hs[i] = -1;
-    long long ncand_l = 0;
+    // one scan carries both the incidence counts (low word) and the CSR row
+    // lengths (high word); the row lengths bound the tile's vertex nodes, all
+    // of which are columns of the tile's rows
+    long long ncand_l = 0, cols_l = 0;
     for (int c0 = 0; c0 < nr; c0 += blockDim.x) {
         const int rr = c0 + threadIdx.x;
         long long len = 0;
@@ -694,15 +697,16 @@ __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e
         if (rr < nr) {
             const int32_t i = perm[rb + rr];
             st = n2e_ptr[i];
-            len = n2e_ptr[i + 1] - st;
+            len = (long long)(n2e_ptr[i + 1] - st) | ((long long)(row_ptr[i + 1] - row_ptr[i]) << 32);
         }
         long long tot;
         const long long pre = block_excl_scan(len, &tot);
         if (rr < nr) {
-            r_pre[rr] = (int32_t)(ncand_l + pre);
+            r_pre[rr] = (int32_t)(ncand_l + (pre & 0xffffffffll));
             r_start[rr] = st;
         }
-        ncand_l += tot;
+        ncand_l += tot & 0xffffffffll;
+        cols_l += tot >> 32;
     }
     if (ncand_l > cap_e) {   // more candidates than the tile was sized for
         if (threadIdx.x == 0) atomicOr(err, 32);
@@ -780,10 +784,11 @@ __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e
         if (threadIdx.x == 0) atomicOr(err, 32);
         return;
     }
-    // a table of at least twice the candidates (the tile's elements share most
-    // vertices: a few thousand slots where the capacity allows 2 cap_n)
+    // a table of at least twice the distinct nodes the tile can have (the
+    // candidates, or the columns of its rows if fewer)
+    const int nnb = nnc < cols_l ? nnc : (int)cols_l;   // at most this many distinct nodes
     int Hu = Hn < 64 ? Hn : 64;
-    while (Hu < 2 * nnc && Hu < Hn) Hu <<= 1;
+    while (Hu < 2 * nnb && Hu < Hn) Hu <<= 1;
     for (int i = threadIdx.x; i < Hu; i += blockDim.x) hs[i] = -1;
     __syncthreads();
     for (int x0 = threadIdx.x; x0 < nnc; x0 += 8 * blockDim.x) {
@@ -1310,8 +1315,27 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
     // budget: the caller's (autotuner candidates), else the tuned one, else the default;
     // VLA_TILE_BUDGET overrides all three (experiments)
     int B = m->tile_budget > 0 ? m->tile_budget : tuned_budget((dim - 2) * 2 + (m->order - 1));
-    if (B <= 0) B = tile_budget(dim, m->order);
-    if (const char *tb = getenv("VLA_TILE_BUDGET")) B = std::max(64, atoi(tb));
+    const int B_default = tile_budget(dim, m->order);
+    bool adaptive = false;
+    if (B <= 0) {
+        B = B_default;
+        adaptive = true;
+    }
+    if (const char *tb = getenv("VLA_TILE_BUDGET")) {
+        B = std::max(64, atoi(tb));
+        adaptive = false;
+    }
+    if (adaptive) {
+        // under the default budget a small mesh is cut into about two tiles per
+        // SM, where tiles of at least 128 incidences allow it: its per-tile
+        // build passes and its assembly then spread over the GPU instead of
+        // running on a few CTAs (the results do not depend on the tiling)
+        int dev_ = 0, nsm = 0;
+        VLA_CUDA(cudaGetDevice(&dev_));
+        VLA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev_));
+        const int64_t total_w = nn + n2e_total, per = (total_w + 2 * (int64_t)nsm - 1) / (2 * (int64_t)std::max(nsm, 1));
+        B = (int)std::min<int64_t>(B, std::max<int64_t>(128, per));
+    }
     const size_t mark_allocs = m->allocs.size();
     const int64_t mark_bytes = m->device_bytes;
     const size_t cap = tile_smem_cap();
@@ -1338,6 +1362,10 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
 
         // max incidence of a single node bounds the tile's candidate count: B + max weight
         const int wmax = (int)hp[3];
+        if (wmax > B && adaptive && B < B_default) {   // a small-mesh budget below a node's weight: cut again
+            B = std::min(B_default, std::max(wmax, 2 * B));
+            continue;
+        }
         if (wmax > B) return fail(VLA_ERR_UNSUPPORTED, "a node belongs to %d elements (tile budget %d)", wmax - 1, B);
         const int cap_e = next_pow2(B + wmax);
         const int cap_n = next_pow2((dim + 1) * (B + wmax));
