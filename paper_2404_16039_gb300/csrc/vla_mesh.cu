@@ -259,13 +259,59 @@ __global__ void __launch_bounds__(kSegWarps * 32) k_sort_segments(int64_t n, con
     }
 }
 
+// Sorts the 32 R keys x[h] of lane l (key index l + 32 h) ascending across
+// the warp: a bitonic network, shuffles for the distances below 32 and
+// register pairs of a lane for the others (all indices fixed at compile time).
+template <int R>
+__device__ __forceinline__ void warp_sort_regs(int32_t (&x)[R]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 2; k <= 32 * R; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32) {
+                const int hj = j >> 5;
+#pragma unroll
+                for (int h = 0; h < R; ++h)
+                    if ((h & hj) == 0) {
+                        const int h2 = h | hj;
+                        const bool up = ((lane + 32 * h) & k) == 0;
+                        const int32_t a = x[h], b = x[h2];
+                        x[h] = up ? min(a, b) : max(a, b);
+                        x[h2] = up ? max(a, b) : min(a, b);
+                    }
+            } else {
+                const bool low = (lane & j) == 0;
+#pragma unroll
+                for (int h = 0; h < R; ++h) {
+                    const int32_t y = __shfl_xor_sync(0xffffffffu, x[h], j);
+                    const bool up = ((lane + 32 * h) & k) == 0;
+                    x[h] = (low == up) ? min(x[h], y) : max(x[h], y);
+                }
+            }
+        }
+}
+
+// the n keys ks[0..n) (n <= 32 R) sorted across the warp into u[0..n)
+template <int R>
+__device__ __forceinline__ void warp_sort_out(const int32_t *ks, int n, int32_t *u) {
+    const int lane = threadIdx.x & 31;
+    int32_t x[R];
+#pragma unroll
+    for (int h = 0; h < R; ++h) x[h] = lane + 32 * h < n ? ks[lane + 32 * h] : 0x7fffffff;
+    warp_sort_regs<R>(x);
+#pragma unroll
+    for (int h = 0; h < R; ++h)
+        if (lane + 32 * h < n) u[lane + 32 * h] = x[h];
+}
+
 // CSR row sets, one warp per row: the nodes of the row's incident elements
 // (one incidence per lane, its element's nodes loaded together) go into a
 // hash set in shared memory of at least twice as many slots as candidates,
 // up to 512 (a row longer than kMaxRow is an error, so a set of more than 256
-// keys is never needed); the keys are sorted (up to 32 by a bitonic network
-// across the lanes, more by a bitonic sort in shared memory) and written to
-// the row's scratch slot.
+// keys is never needed); the keys are sorted (up to 128 by a bitonic network
+// over the lanes' registers, more by a bitonic sort in shared memory) and
+// written to the row's scratch slot.
 constexpr int kRowWarps = 8, kRowHash = 512;
 template <int NLB>
 __global__ void __launch_bounds__(kRowWarps * 32) k_row_count(int64_t nn, const int32_t *__restrict__ elems,
@@ -331,16 +377,12 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_row_count(int64_t nn, const 
         }
         __syncwarp();
         int32_t *u = scratch + (int64_t)NLB * b;
-        if (n <= 32) {   // one key per lane, bitonic network over the lanes
-            int32_t x = lane < n ? ks[lane] : 0x7fffffff;
-#pragma unroll
-            for (int k = 2; k <= 32; k <<= 1)
-#pragma unroll
-                for (int j = k >> 1; j > 0; j >>= 1) {
-                    const int32_t y = __shfl_xor_sync(0xffffffffu, x, j);
-                    x = (((lane & j) == 0) == ((lane & k) == 0)) ? min(x, y) : max(x, y);
-                }
-            if (lane < n) u[lane] = x;
+        if (n <= 32) {   // up to 128 keys: a bitonic network over the lanes' registers
+            warp_sort_out<1>(ks, n, u);
+        } else if (n <= 64) {
+            warp_sort_out<2>(ks, n, u);
+        } else if (n <= 128) {
+            warp_sort_out<4>(ks, n, u);
         } else {   // pad to a power of two, bitonic sort in shared memory
             int P = 1;
             while (P < n) P <<= 1;
@@ -966,64 +1008,84 @@ __global__ void __launch_bounds__(256) k_tile_fill(int n_tiles, int dim, int cap
 // Orders every tile's pairs by contribution count (descending, stable), so
 // that the 32 pairs of a chunk need nearly the same number of iterations, then
 // writes the chunk table (tile-relative code offset, width) and the permuted
-// pair positions.  order[nz_off + q] = new index of row-major pair q.
-__global__ void k_chunk_table(int n_tiles, const TileHdr *__restrict__ hdr, const int32_t *__restrict__ nz_count,
-                              const int2 *__restrict__ nzpos_rowmajor, int2 *__restrict__ nzpos,
-                              int32_t *__restrict__ order, int2 *__restrict__ chunks,
-                              int32_t *__restrict__ tile_codes_n) {
+// pair positions.  order[nz_off + q] = new index of row-major pair q.  Each
+// warp places a contiguous range of the row-major pairs (whole 32-pair
+// windows): per-warp count histograms give every (count, warp) its first slot
+// (counts descending, then warps in range order, which keeps the order
+// stable), and within a window a pair's slot is its bucket's next slot plus
+// the number of earlier lanes with the same count.
+constexpr int kChunkWarps = 8, kMaxCount = 512;
+__global__ void __launch_bounds__(kChunkWarps * 32) k_chunk_table(int n_tiles, const TileHdr *__restrict__ hdr,
+                                                                  const int32_t *__restrict__ nz_count,
+                                                                  const int2 *__restrict__ nzpos_rowmajor,
+                                                                  int2 *__restrict__ nzpos, int32_t *__restrict__ order,
+                                                                  int2 *__restrict__ chunks,
+                                                                  int32_t *__restrict__ tile_codes_n) {
     const int t = blockIdx.x;
     if (t >= n_tiles) return;
     const TileHdr h = hdr[t];
-    constexpr int kMaxCount = 512;
-    __shared__ int32_t hist[kMaxCount + 1];
+    __shared__ int32_t hist[kChunkWarps][kMaxCount + 1];
     __shared__ int32_t w[1024];
-    for (int i = threadIdx.x; i <= kMaxCount; i += blockDim.x) hist[i] = 0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < kChunkWarps * (kMaxCount + 1); i += blockDim.x) (&hist[0][0])[i] = 0;
     for (int i = threadIdx.x; i < 1024; i += blockDim.x) w[i] = 0;
     __syncthreads();
-    for (int q = threadIdx.x; q < h.n_nz; q += blockDim.x) atomicAdd(&hist[min(nz_count[h.nz_off + q], kMaxCount)], 1);
+    const int nwin = (h.n_nz + 31) >> 5, per = (nwin + kChunkWarps - 1) / kChunkWarps;
+    const int q_begin = min(wid * per, nwin) * 32, q_end = min(min((wid + 1) * per, nwin) * 32, h.n_nz);
+    for (int q = q_begin + lane; q < q_end; q += 32) atomicAdd(&hist[wid][min(nz_count[h.nz_off + q], kMaxCount)], 1);
     __syncthreads();
-    if (threadIdx.x == 0) {   // descending counts: start offset of each count value
-        int32_t run = 0;
-        for (int c = kMaxCount; c >= 0; --c) {
-            const int32_t n = hist[c];
-            hist[c] = run;
-            run += n;
-        }
-    }
-    __syncthreads();
-    // stable placement: the first warp walks the pairs in row-major order, 32
-    // at a time; a pair's place is its bucket's next slot plus the number of
-    // earlier lanes of its window with the same count
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        for (int q0 = 0; q0 < h.n_nz; q0 += 32) {
-            const int q = q0 + lane;
-            const bool valid = q < h.n_nz;
-            const int n = valid ? nz_count[h.nz_off + q] : 0;
-            const int c = valid ? min(n, kMaxCount) : -1 - lane;   // invalid lanes match nobody
-            const unsigned peers = __match_any_sync(0xffffffffu, c);
-            const int rank = __popc(peers & ((1u << lane) - 1u));
-            const int base = valid ? hist[c] : 0;
-            __syncwarp();
-            if (valid) {
-                const int32_t nq = base + rank;
-                order[h.nz_off + q] = nq;
-                nzpos[h.nz_off + nq] = nzpos_rowmajor[h.nz_off + q];
-                if ((nq >> 5) < 1024) atomicMax(&w[nq >> 5], n);   // chunk width: its largest count
-                if (rank == 0) hist[c] = base + __popc(peers);
+    // first slot of every (count, warp): a block scan over the counts in
+    // descending order of the per-count totals, then the warps in order
+    long long base = 0;
+    for (int r0 = 0; r0 <= kMaxCount; r0 += blockDim.x) {
+        const int r = r0 + threadIdx.x, c = kMaxCount - r;
+        int tot = 0;
+        if (r <= kMaxCount)
+            for (int ww = 0; ww < kChunkWarps; ++ww) tot += hist[ww][c];
+        long long all;
+        const long long pre = block_excl_scan(tot, &all);
+        if (r <= kMaxCount) {
+            int run = (int)(base + pre);
+            for (int ww = 0; ww < kChunkWarps; ++ww) {
+                const int n = hist[ww][c];
+                hist[ww][c] = run;
+                run += n;
             }
-            __syncwarp();
         }
+        base += all;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int32_t off = 0;
-        for (int c = 0; c < h.n_chunks && c < 1024; ++c) {
-            chunks[h.chunk_off + c] = make_int2(off, w[c]);
-            off += 32 * w[c];
+    for (int q0 = q_begin; q0 < q_end; q0 += 32) {
+        const int q = q0 + lane;
+        const bool valid = q < q_end;
+        const int n = valid ? nz_count[h.nz_off + q] : 0;
+        const int c = valid ? min(n, kMaxCount) : -1 - lane;   // invalid lanes match nobody
+        const unsigned peers = __match_any_sync(0xffffffffu, c);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        const int bs = valid ? hist[wid][c] : 0;
+        __syncwarp();
+        if (valid) {
+            const int32_t nq = bs + rank;
+            order[h.nz_off + q] = nq;
+            nzpos[h.nz_off + nq] = nzpos_rowmajor[h.nz_off + q];
+            if ((nq >> 5) < 1024) atomicMax(&w[nq >> 5], n);   // chunk width: its largest count
+            if (rank == 0) hist[wid][c] = bs + __popc(peers);
         }
-        tile_codes_n[t] = off;
+        __syncwarp();
     }
+    __syncthreads();
+    // chunk table: code offsets by a block scan of 32 x width
+    const int nch = min(h.n_chunks, 1024);
+    long long off = 0;
+    for (int c0 = 0; c0 < nch; c0 += blockDim.x) {
+        const int c = c0 + threadIdx.x;
+        const long long v = c < nch ? 32LL * w[c] : 0;
+        long long all;
+        const long long pre = block_excl_scan(v, &all);
+        if (c < nch) chunks[h.chunk_off + c] = make_int2((int)(off + pre), w[c]);
+        off += all;
+    }
+    if (threadIdx.x == 0) tile_codes_n[t] = (int32_t)off;
 }
 
 // Pass C: contribution codes, element * rsc + packed (a,b) entry (the entry's
@@ -1473,7 +1535,7 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
                 sc_elems, sc_nodes, m->tile_nodes, m->tile_elem, m->tile_own, nzpos_rm, nz_count, row_info);
             VLA_CUDA(cudaGetLastError());
         }
-        k_chunk_table<<<(int)n_tiles, 64, 0, st>>>((int)n_tiles, m->tiles, nz_count, nzpos_rm, m->tile_nzpos, nz_order,
+        k_chunk_table<<<(int)n_tiles, kChunkWarps * 32, 0, st>>>((int)n_tiles, m->tiles, nz_count, nzpos_rm, m->tile_nzpos, nz_order,
                                                     m->tile_chunks, tile_ncodes);
         VLA_CUDA(cudaGetLastError());
         VLA_CUDA(cudaMemcpyAsync(hnc, tile_ncodes, sizeof(int32_t) * n_tiles, cudaMemcpyDeviceToHost, st));
