@@ -375,10 +375,11 @@ int num_sms();
 // page-major page is R*CC contiguous words, so one page per thread reads and
 // writes with a stride of a whole page per lane (one cache line per page per
 // warp access, L1-wavefront bound).  Here the block reads its PB pages with
-// consecutive threads on consecutive words, keeps them at a per-page stride of
-// R*CC + 1 words (odd: the page reads of a warp fall on distinct banks), each
-// thread forms its result page from there into a second area (stride
-// OUT + 1), and the block writes the result pages back with consecutive words.
+// consecutive threads on consecutive words, keeps them at an odd per-page
+// stride (R*CC, or R*CC + 1 when that is even: the page reads of a warp fall
+// on distinct banks), each thread forms its result page from there into a
+// second area (odd stride likewise from OUT), and the block writes the result
+// pages back with consecutive words.
 // `div_in`/`div_out` are ceil(2^32 / size) for the page index of a word by one
 // multiply-high (exact for words below 2^32 / size).
 template <typename T, int R, int CC>
@@ -386,13 +387,17 @@ __global__ void __launch_bounds__(512 / sizeof(T)) k_page_bcast_staged(int op, i
                                                                       const T *__restrict__ A,
                                                                       const T *__restrict__ S, T *__restrict__ C,
                                                                       uint32_t div_out) {
-    constexpr int PB = 512 / sizeof(T), IN = R * CC, INS = IN + 1;
+    constexpr int PB = 512 / sizeof(T), IN = R * CC, INS = IN | 1;
     constexpr uint32_t DIV_IN = (uint32_t)((0x100000000ull + IN - 1) / IN);
-    const int OUT = R * other, OUTS = OUT + 1;
+    const int OUT = R * other, OUTS = OUT | 1;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sa = reinterpret_cast<T *>(smraw);
     T *sc = sa + PB * INS;
+    // the single matrix, read once per block (its uses below are broadcast
+    // shared-memory reads instead of a global load per entry and page)
+    T *ss = sc + ((PB * OUTS + 15) & ~15);
     const int t = threadIdx.x;
+    for (int i = t; i < CC * other; i += PB) ss[i] = S[i];   // visible after the loop's first barrier
     for (int64_t k0 = (int64_t)blockIdx.x * PB; k0 < N; k0 += (int64_t)gridDim.x * PB) {
         const int np = (int)(N - k0 < PB ? N - k0 : PB);
         const T *src = A + k0 * IN;
@@ -420,7 +425,7 @@ __global__ void __launch_bounds__(512 / sizeof(T)) k_page_bcast_staged(int op, i
                 for (int i = 0; i < other; ++i) {
                     T srow[CC];
 #pragma unroll
-                    for (int r = 0; r < CC; ++r) srow[r] = __ldg(S + i + r * other);
+                    for (int r = 0; r < CC; ++r) srow[r] = ss[i + r * other];
 #pragma unroll
                     for (int j = 0; j < R; ++j) {
                         T acc = 0;
@@ -433,7 +438,7 @@ __global__ void __launch_bounds__(512 / sizeof(T)) k_page_bcast_staged(int op, i
                 for (int j = 0; j < other; ++j) {
                     T scol[CC];
 #pragma unroll
-                    for (int r = 0; r < CC; ++r) scol[r] = __ldg(S + r + j * CC);
+                    for (int r = 0; r < CC; ++r) scol[r] = ss[r + j * CC];
 #pragma unroll
                     for (int i = 0; i < R; ++i) {
                         T acc = 0;
@@ -467,7 +472,9 @@ bool launch_bcast_rc(int op, int64_t N, int soa, int R, int CC, int other, const
     constexpr int PB = 512 / sizeof(T);
     const int OUT = R * other;
     const uint32_t div_out = (uint32_t)((0x100000000ull + OUT - 1) / OUT);
-    const size_t smem = (size_t)PB * ((size_t)R * CC + 1 + OUT + 1) * sizeof(T);
+    // pages (odd stride R CC | 1), results (odd stride OUT | 1, area padded to 16 words), the single matrix
+    const size_t smem = ((size_t)PB * (size_t)((R * CC) | 1) + (((size_t)PB * (size_t)(OUT | 1) + 15) & ~(size_t)15) +
+                         (size_t)CC * other) * sizeof(T);
     const int gs = grid_for(N, PB, (int64_t)num_sms() * 16);
 #define VLA_RC(r_, c_)                                                                               \
     if (R == r_ && CC == c_) {                                                                       \
