@@ -306,7 +306,7 @@ __device__ __forceinline__ void warp_sort_out(const int32_t *ks, int n, int32_t 
 }
 
 // CSR row sets, one warp per row: the nodes of the row's incident elements
-// (one incidence per lane, its element's nodes loaded together) go into a
+// (one candidate node per lane, four rounds of loads at a time) go into a
 // hash set in shared memory of at least twice as many slots as candidates,
 // up to 512 (a row longer than kMaxRow is an error, so a set of more than 256
 // keys is never needed); the keys are sorted (up to 128 by a bitonic network
@@ -334,26 +334,28 @@ __global__ void __launch_bounds__(kRowWarps * 32) k_row_count(int64_t nn, const 
         for (int q = lane; q < H; q += 32) tab[q] = -1;
         if (lane == 0) cnt[w] = 0;
         __syncwarp();
-        for (int q0 = 0; q0 < nq; q0 += 32) {
-            const int q = q0 + lane;
-            int32_t v[NLB];
-            if (q < nq) {
-                const int64_t k = (int64_t)(n2e[b + q] >> 4);
+        // candidate c = node c % NLB of incidence c / NLB, one per lane, four
+        // rounds of loads in flight before their insertions
+        for (int c0 = 0; c0 < ncand; c0 += 128) {
+            int32_t xs[4];
 #pragma unroll
-                for (int bb = 0; bb < NLB; ++bb) v[bb] = elems[k * NLB + bb];
+            for (int u = 0; u < 4; ++u) {
+                const int c = c0 + 32 * u + lane;
+                xs[u] = c < ncand ? elems[(int64_t)(n2e[b + c / NLB] >> 4) * NLB + c % NLB] : -1;
+            }
 #pragma unroll
-                for (int bb = 0; bb < NLB; ++bb) {
-                    const int32_t x = v[bb];
-                    uint32_t h = ((uint32_t)x * 2654435761u) & (uint32_t)(H - 1);
-                    for (int probe = 0; probe < H; ++probe) {
-                        const int32_t prev = atomicCAS(&tab[h], -1, x);
-                        if (prev == -1) {
-                            atomicAdd(&cnt[w], 1);
-                            break;
-                        }
-                        if (prev == x) break;
-                        h = (h + 1) & (uint32_t)(H - 1);
+            for (int u = 0; u < 4; ++u) {
+                const int32_t x = xs[u];
+                if (x < 0) continue;
+                uint32_t h = ((uint32_t)x * 2654435761u) & (uint32_t)(H - 1);
+                for (int probe = 0; probe < H; ++probe) {
+                    const int32_t prev = atomicCAS(&tab[h], -1, x);
+                    if (prev == -1) {
+                        atomicAdd(&cnt[w], 1);
+                        break;
                     }
+                    if (prev == x) break;
+                    h = (h + 1) & (uint32_t)(H - 1);
                 }
             }
         }

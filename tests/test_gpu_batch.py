@@ -180,6 +180,29 @@ def test_tile_budget_does_not_change_results(vla):
         vla.tune_set(3, 1, 1, tile_budget=0, ctas_per_sm=0)
 
 
+@pytest.mark.parametrize("dim,order,n", [(3, 1, 8), (2, 1, 30), (3, 2, 4), (2, 2, 12)])
+def test_small_mesh_tiling_does_not_change_results(vla, dim, order, n):
+    # under the default budget a small mesh is cut into about two tiles per SM;
+    # its outputs equal those of the same mesh cut at the full budget, bit for bit
+    m = meshgen.kuhn_cube(n, jitter=0.1, seed=0) if (dim, order) == (3, 1) else \
+        meshgen.make_mesh(dim, n, order=order, jitter=0.1, seed=3)
+    fine = _gpu_mesh(vla, m)
+    full_budget = {(2, 1): 2048, (2, 2): 1024, (3, 1): 800, (3, 2): 384}[(dim, order)]
+    try:
+        vla.tune_set(dim, order, 1, tile_budget=full_budget, ctas_per_sm=0)
+        coarse = _gpu_mesh(vla, m)
+    finally:
+        vla.tune_set(dim, order, 1, tile_budget=0, ctas_per_sm=0)
+    assert fine.n_tiles > coarse.n_tiles
+    for prec in (0, 1):
+        a = fine.assemble(1.0, 1.0, precision=prec, pages=True)
+        b = coarse.assemble(1.0, 1.0, precision=prec, pages=True)
+        for key in ("K", "M", "vol", "K3D", "M3D"):
+            assert torch.equal(a[key], b[key]), (prec, key)
+    fine.close()
+    coarse.close()
+
+
 def test_autotune_picks_a_candidate(vla):
     m = meshgen.kuhn_cube(16, seed=0)
     try:
