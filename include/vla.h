@@ -204,6 +204,11 @@ vla_status vla_mesh_info(const vla_mesh *mesh, vla_mesh_info_t *info);
  * Errors: VLA_ERR_INVALID_ARG for a NULL mesh; VLA_ERR_CUDA if a copy fails. */
 vla_status vla_mesh_csr(const vla_mesh *mesh, int32_t *row_ptr, int32_t *col_idx, void *stream);
 
+/* The CSR pattern of the Section 3.5 sparse assembly without a copy: device
+ * pointers to the mesh's own row_ptr (nn+1 int32) and col_idx (nnz int32).  They stay valid, read-only,
+ * until vla_mesh_destroy.  Errors: VLA_ERR_INVALID_ARG for a NULL argument. */
+vla_status vla_mesh_csr_view(const vla_mesh *mesh, const int32_t **row_ptr, const int32_t **col_idx);
+
 /* Assembles K and M (Section 3.5 stiffness and mass listings) into the
  * mesh's CSR pattern:
  *   K_ij = sum_k c_k int_{T_k} grad phi_i . grad phi_j,

@@ -45,6 +45,17 @@ class VlaError(RuntimeError):
         self.status = status
 
 
+class _DeviceArray:
+    """An int32 device array owned by the library, exposed through the CUDA
+    array interface so that torch.as_tensor makes a view of it without a copy;
+    the view keeps this object, and through it the owning handle, alive."""
+
+    def __init__(self, ptr, n, owner):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<i4", "data": (int(ptr or 0), False),
+                                         "version": 3, "strides": None}
+        self._owner = owner
+
+
 class MeshInfo(C.Structure):
     _fields_ = [("dim", C.c_int32), ("order", C.c_int32), ("nlb", C.c_int32),
                 ("nn", C.c_int64), ("ne", C.c_int64), ("nfb", C.c_int64), ("nnz", C.c_int64),
@@ -129,6 +140,7 @@ def lib():
         L.vla_mesh_create.argtypes = [i32, i32, i64, i64, vp, vp, i64, vp, vp, C.POINTER(vp)]
         L.vla_mesh_info.argtypes = [vp, C.POINTER(MeshInfo)]
         L.vla_mesh_csr.argtypes = [vp, vp, vp, vp]
+        L.vla_mesh_csr_view.argtypes = [vp, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p)]
         L.vla_assemble.argtypes = [vp, i32, dbl, dbl, i32, vp, vp, vp, vp, vp, vp, vp]
         L.vla_assemble_with_boundary.argtypes = [vp, i32, dbl, dbl, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.vla_boundary.argtypes = [vp, i32, vp, vp, vp]
@@ -163,7 +175,7 @@ def lib():
         L.vla_server_stats.argtypes = [vp, C.POINTER(ServerStats)]
         L.vla_server_destroy.argtypes = [vp]
         for name in ("vla_amtam", "vla_astam", "vla_avtam", "vla_amdet", "vla_aminv", "vla_mesh_create",
-                     "vla_mesh_info", "vla_mesh_csr", "vla_assemble", "vla_assemble_with_boundary", "vla_boundary", "vla_simplex_normals",
+                     "vla_mesh_info", "vla_mesh_csr", "vla_mesh_csr_view", "vla_assemble", "vla_assemble_with_boundary", "vla_boundary", "vla_simplex_normals",
                      "vla_mesh_destroy", "vla_element_pages_static", "vla_element_pages_static_check", "vla_mesh_check",
                      "vla_partition_rows", "vla_mesh_create_rows", "vla_batch_create",
                      "vla_batch_set_job", "vla_batch_run", "vla_batch_info", "vla_batch_check", "vla_batch_destroy",
@@ -474,17 +486,30 @@ class Mesh:
         _check(lib().vla_mesh_csr(self._h, _p(rp), _p(ci), _stream(stream)))
         return rp, ci[: self.nnz]
 
+    def csr_view(self):
+        """row_ptr (nn+1) and col_idx (nnz) of the mesh's own CSR pattern as
+        int32 device tensors without a copy (vla_mesh_csr_view).  Read-only,
+        valid until ``close()``."""
+        rp, ci = C.c_void_p(), C.c_void_p()
+        _check(lib().vla_mesh_csr_view(self._h, C.byref(rp), C.byref(ci)))
+        return (torch.as_tensor(_DeviceArray(rp.value, self.nn + 1, self), device=self.device),
+                torch.as_tensor(_DeviceArray(ci.value, self.nnz, self), device=self.device))
+
     def block(self, values=(), stream=None):
         """The CSR rows [r0, r1) this mesh owns (all rows for a whole mesh):
         (row_ptr (r1 - r0 + 1, starting at 0), col_idx, and the same slice of
         each tensor in ``values``, e.g. the K and M values of ``assemble``).
-        Views of the device tensors, no copy."""
+        col_idx and the values are views without a copy (col_idx of the
+        mesh's own pattern, valid until ``close()``)."""
         r0, r1 = self.rows
-        rp, ci = self.csr(stream=stream)
-        a, b = int(rp[r0].item()), int(rp[r1].item())
+        rp, ci = self.csr_view()
+        if r0 == 0 and r1 == self.nn:   # the whole pattern: its bounds are known on the host
+            a, b = 0, self.nnz
+        else:
+            a, b = int(rp[r0].item()), int(rp[r1].item())
         for v in values:
             _buf(v, self.nnz, torch.float64, self.device, "values")
-        return (rp[r0:r1 + 1] - a, ci[a:b]) + tuple(v[a:b] for v in values)
+        return (rp[r0:r1 + 1] - a if a else rp[r0:r1 + 1], ci[a:b]) + tuple(v[a:b] for v in values)
 
     def assemble(self, ca=1.0, cb=0.0, kind=COEFF_POLY, precision=PREC_MIXED, K=None, M=None, vol=None,
                  want_K=True, want_M=True, want_vol=True, pages=False, count_singular=False, stream=None,

@@ -1784,6 +1784,13 @@ extern "C" vla_status vla_mesh_info(const vla_mesh *m, vla_mesh_info_t *info) {
     return VLA_OK;
 }
 
+extern "C" vla_status vla_mesh_csr_view(const vla_mesh *m, const int32_t **row_ptr, const int32_t **col_idx) {
+    if (!m || !row_ptr || !col_idx) return fail(VLA_ERR_INVALID_ARG, "vla_mesh_csr_view: NULL argument");
+    *row_ptr = m->row_ptr;
+    *col_idx = m->col_idx;
+    return VLA_OK;
+}
+
 extern "C" vla_status vla_mesh_csr(const vla_mesh *m, int32_t *row_ptr, int32_t *col_idx, void *stream) {
     if (!m) return fail(VLA_ERR_INVALID_ARG, "null mesh");
     cudaStream_t st = (cudaStream_t)stream;

@@ -180,6 +180,8 @@ def test_remaining_entry_points_validate_without_gpu(libpath):
 
     lib.vla_assemble.argtypes = [vp, i32, f64, f64, i32, vp, vp, vp, vp, vp, vp, vp]
     assert lib.vla_assemble(None, 0, 1.0, 0.0, 1, None, None, None, None, None, None, None) == INVALID
+    lib.vla_mesh_csr_view.argtypes = [vp, vp, vp]
+    assert lib.vla_mesh_csr_view(None, None, None) == INVALID
     lib.vla_assemble_with_boundary.argtypes = [vp, i32, f64, f64, i32] + [vp] * 9
     assert lib.vla_assemble_with_boundary(None, 0, 1.0, 0.0, 1, *([None] * 9)) == INVALID
     for name, nargs in (("vla_boundary", 5), ("vla_simplex_normals", 3), ("vla_mesh_csr", 4), ("vla_mesh_check", 2),

@@ -161,6 +161,46 @@ def test_batch_uneven_config_scaled(vla):
     b.check()
 
 
+def test_batch_uneven_full_size(vla):
+    # the batched workload at full size, in the launch the benchmark times: 256
+    # meshes (2-D/3-D x P1/P2, 1e3..1e6 elements, 45 M elements), c = 1 + |x|^2,
+    # mixed precision, one graph-captured launch per element type.  Every job
+    # equals its single-mesh assembly bit for bit; every mesh's K rows sum to
+    # zero and its volumes to the domain's; the smallest mesh of each type is
+    # checked against the FP64 oracle
+    specs = meshgen.batch_specs(256, 1e3, 1e6, seed=0)
+    meshes = [meshgen.make_mesh(s["dim"], s["n"], order=s["order"], jitter=0.1, seed=s["seed"]) for s in specs]
+    assert sum(m.ne for m in meshes) == 45000030
+    gms = [_gpu_mesh(vla, m) for m in meshes]
+    jobs = [(gm, gm.outputs(), 0, 1.0, 1.0) for gm in gms]
+    b = vla.Batch(jobs, precision=1, graph=True, form="split")
+    b.run()
+    torch.cuda.synchronize()
+    b.check()
+    smallest = {}
+    for q, (m, gm, (_, out, *_)) in enumerate(zip(meshes, gms, jobs)):
+        ref = gm.assemble(1.0, 1.0, precision=1)
+        for key in ("K", "M", "vol"):
+            assert torch.equal(out[key], ref[key]), (q, key)
+        rp, _ = gm.csr()
+        rows = torch.repeat_interleave(torch.arange(gm.nn, device=rp.device), rp[1:] - rp[:-1])
+        rsum = torch.zeros(gm.nn, dtype=torch.float64, device=rp.device).index_add_(0, rows, out["K"])
+        rmax = torch.zeros(gm.nn, dtype=torch.float64, device=rp.device).scatter_reduce_(
+            0, rows, out["K"].abs(), "amax", include_self=False)
+        assert (rsum.abs() <= 1e-5 * rmax).all(), q
+        assert abs(out["vol"].sum().item() - 1.0) <= 1e-6, q
+        key = (m.dim, m.order)
+        if key not in smallest or m.ne < smallest[key][0].ne:
+            smallest[key] = (m, out)
+    for m, out in smallest.values():
+        ref = oracle.assemble(m.dim, m.order, m.nn, m.elems, m.coords, 1.0, 1.0)
+        for key in ("K", "M", "vol"):
+            assert _rel_fro(out[key].cpu().numpy(), ref[key]) <= TOL_MIX, (m.dim, m.order, key)
+    b.close()
+    for gm in gms:
+        gm.close()
+
+
 def test_tile_budget_does_not_change_results(vla):
     m = meshgen.kuhn_cube(10, seed=2)
     ref = None

@@ -203,6 +203,10 @@ def test_pattern_bit_exact(vla, dim, order, n):
     np.testing.assert_array_equal(rp.cpu().numpy(), rpr)
     np.testing.assert_array_equal(ci.cpu().numpy(), cir)
     assert gm.nnz == len(cir)
+    rpv, civ = gm.csr_view()   # the mesh's own arrays, no copy
+    assert torch.equal(rpv, rp) and torch.equal(civ, ci)
+    rpb, cib = gm.block()
+    assert torch.equal(rpb, rp) and torch.equal(cib, ci)
 
 
 @pytest.mark.parametrize("dim,order,n", CASES)
