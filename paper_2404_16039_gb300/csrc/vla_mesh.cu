@@ -102,34 +102,43 @@ __global__ void k_i64_to_i32(int64_t n, const long long *__restrict__ in, int32_
 // Small pinned host buffer for the scalars a build reads back (one per host
 // thread, allocated on first use): device-to-host copies into pageable memory
 // would each wait for the whole stream.
-// a growable pinned host buffer per host thread for the tile tables a build
-// reads back and sends down (pageable copies of a few hundred KB go through a
-// driver staging buffer); every build ends with a synchronisation before the
-// thread's next build reuses it
-void *pinned_tables(size_t bytes) {
-    static thread_local void *p = nullptr;
-    static thread_local size_t cap = 0;
-    if (bytes > cap) {
+// Pinned host buffers per host thread, freed when the thread ends (server
+// ingest threads come and go with their servers)
+struct PinnedBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    ~PinnedBuf() {
         if (p) cudaFreeHost(p);
-        p = nullptr;
-        cap = 0;
-        const size_t want = bytes > ((size_t)1 << 20) ? bytes + bytes / 4 : ((size_t)1 << 20);
-        if (cudaMallocHost(&p, want) != cudaSuccess) {
-            cudaGetLastError();
-            return nullptr;
-        }
-        cap = want;
     }
-    return p;
+    void *get(size_t bytes, size_t min_bytes) {
+        if (bytes > cap) {
+            if (p) cudaFreeHost(p);
+            p = nullptr;
+            cap = 0;
+            const size_t want = bytes > min_bytes ? bytes + bytes / 4 : min_bytes;
+            if (cudaMallocHost(&p, want) != cudaSuccess) {
+                cudaGetLastError();
+                return nullptr;
+            }
+            cap = want;
+        }
+        return p;
+    }
+};
+
+// a growable buffer for the tile tables a build reads back and sends down
+// (pageable copies of a few hundred KB go through a driver staging buffer);
+// every build ends with a synchronisation before the thread's next build
+// reuses it
+void *pinned_tables(size_t bytes) {
+    static thread_local PinnedBuf b;
+    return b.get(bytes, (size_t)1 << 20);
 }
 
+// scalars read back through pinned memory (scan totals, error word, maxima)
 long long *pinned_scalars() {
-    static thread_local long long *p = nullptr;
-    if (!p && cudaMallocHost((void **)&p, 64 * sizeof(long long)) != cudaSuccess) {
-        cudaGetLastError();
-        p = nullptr;
-    }
-    return p;
+    static thread_local PinnedBuf b;
+    return static_cast<long long *>(b.get(64 * sizeof(long long), 64 * sizeof(long long)));
 }
 
 // out[n] = out[n - 1] + in[n - 1] (the total), on the device
