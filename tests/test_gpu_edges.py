@@ -138,3 +138,48 @@ def test_element_count_limit_rejected_before_work(vla):
     st = L.vla_mesh_create(3, 1, 4, 1 << 27, C.c_void_p(dummy.data_ptr()), C.c_void_p(dummy.data_ptr()), 0, None,
                            None, C.byref(h))
     assert st == -8 and not h.value
+
+
+@pytest.mark.parametrize("dim,order,n", [(3, 1, 4), (2, 1, 7), (3, 2, 2), (2, 2, 4)])
+def test_vertex_order_and_node_labels_do_not_matter(vla, dim, order, n):
+    # every element's vertices in a random order (about half of them with a
+    # negative determinant; P2 mid-edge nodes moved with their edges), the
+    # global node labels permuted at random, the boundary facets listed in
+    # reverse order: the outputs still match the oracle on the same arrays
+    m = meshgen.make_mesh(dim, n, order=order, jitter=0.1, seed=n)
+    rng = np.random.default_rng(5)
+    nv = dim + 1
+    edges = [(0, 1), (1, 2), (0, 2)] if dim == 2 else [(0, 1), (1, 2), (0, 2), (0, 3), (1, 3), (2, 3)]
+    E = np.empty_like(m.elems)
+    flipped = 0
+    for k in range(m.ne):
+        s = rng.permutation(nv)
+        flipped += int(np.sum([s[a] > s[b] for a in range(nv) for b in range(a + 1, nv)]) % 2)
+        row = list(m.elems[k, s])
+        if order == 2:
+            edge_node = {frozenset(e): m.elems[k, nv + t] for t, e in enumerate(edges)}
+            row += [edge_node[frozenset((s[p], s[q]))] for p, q in edges]
+        E[k] = row
+    assert 0 < flipped < m.ne
+    lab = rng.permutation(m.nn).astype(np.int32)
+    E2 = lab[E].astype(np.int32)
+    X2 = np.empty_like(m.coords)
+    X2[lab] = m.coords
+    F2 = np.ascontiguousarray(lab[m.faces][:, ::-1]).astype(np.int32)
+    gm = vla.Mesh(_dev(X2), _dev(E2), _dev(F2), order=order)
+    ref = oracle.assemble(dim, order, m.nn, E2, X2, 1.0, 1.0)
+    rp, ci = gm.csr()
+    np.testing.assert_array_equal(rp.cpu().numpy(), ref["row_ptr"])
+    np.testing.assert_array_equal(ci.cpu().numpy(), ref["col_idx"])
+    o64 = gm.assemble(1.0, 1.0, precision=vla.PREC_FP64, boundary=True)
+    omx = gm.assemble(1.0, 1.0, precision=vla.PREC_MIXED, boundary=True)
+    for key in ("K", "M", "vol"):
+        r = ref[key]
+        assert np.abs(o64[key].cpu().numpy() - r).max() <= TOL64 * np.abs(r).max(), key
+        assert np.linalg.norm(omx[key].cpu().numpy() - r) <= TOL_MIX * np.linalg.norm(r), key
+    assert (o64["vol"] > 0).all()
+    rn, ra, miss = oracle.boundary(dim, m.nn, E2, X2, F2)
+    assert miss == 0
+    np.testing.assert_allclose(o64["normals"].cpu().numpy(), rn, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(o64["areas"].cpu().numpy(), ra, rtol=1e-13)
+    gm.close()
