@@ -205,8 +205,9 @@ vla_status vla_mesh_info(const vla_mesh *mesh, vla_mesh_info_t *info);
 vla_status vla_mesh_csr(const vla_mesh *mesh, int32_t *row_ptr, int32_t *col_idx, void *stream);
 
 /* The CSR pattern of the Section 3.5 sparse assembly without a copy: device
- * pointers to the mesh's own row_ptr (nn+1 int32) and col_idx (nnz int32).  They stay valid, read-only,
- * until vla_mesh_destroy.  Errors: VLA_ERR_INVALID_ARG for a NULL argument. */
+ * pointers to the mesh's own row_ptr (nn+1 int32) and col_idx (nnz int32).
+ * They stay valid, read-only, until vla_mesh_destroy.
+ * Errors: VLA_ERR_INVALID_ARG for a NULL argument. */
 vla_status vla_mesh_csr_view(const vla_mesh *mesh, const int32_t **row_ptr, const int32_t **col_idx);
 
 /* Assembles K and M (Section 3.5 stiffness and mass listings) into the
@@ -370,9 +371,12 @@ vla_status vla_mesh_facets(const vla_mesh *mesh, int32_t *faces, int32_t *owner,
                            int64_t *n_boundary, void *stream);
 
 /* Housekeeping (no counterpart in the paper): releases the handle and its
- * device memory (stream-ordered on the stream
- * the mesh was created with, which is synchronised first).  NULL is a no-op;
- * cannot fail. */
+ * device memory (stream-ordered on the stream the mesh was created with,
+ * which is synchronised first).  The memory returns to the library's device
+ * memory pool, which keeps up to min(8 GiB, 1/16 of the device) of freed
+ * memory mapped for later builds (the environment variable VLA_POOL_KEEP, in
+ * bytes, sets that amount when the pool is first used; 0 keeps none).  NULL
+ * is a no-op; cannot fail. */
 vla_status vla_mesh_destroy(vla_mesh *mesh);
 
 /* Failure detection (no counterpart in the paper): reads and clears the
