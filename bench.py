@@ -1060,17 +1060,20 @@ def main():
     def step():
         gm.assemble(1.0, 1.0, precision=prec, K=K, M=M, vol=vol, boundary=True, normals=nrm, areas=ar)
 
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    # the clock sampler starts first; the warm-up steps then run right before
+    # the timed ones (a GPU left idle while the sampler starts slows the first
+    # timed step by up to 70 us)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
     for _ in range(args.warmup):
         flush.zero_()
         step()
     torch.cuda.synchronize()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-          for _ in range(args.steps)]
-    sampler = ClockSampler(local)
     _barrier(dist)
     torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.3)
     for i in range(args.steps):
         flush.zero_()
         e0, e1 = ev[i]
@@ -1223,7 +1226,9 @@ def main():
                                        f"duplicated, complete rows per rank, no collective on the data path)"
                            if ws > 1 else "one GPU, every row"),
             "e2e": e2e, "roofline": roof, "gpu_launches": args.steps, "clocks": clocks,
-            "p50_ms": latency["cold_l2"]["p50_ms"], "p99_ms": latency["cold_l2"]["p99_ms"], "latency": latency}
+            "p50_ms": latency["cold_l2"]["p50_ms"], "p99_ms": latency["cold_l2"]["p99_ms"], "latency": latency,
+            "timed_steps_ms": {"min": min(step_ms), "median": float(np.median(step_ms)), "max": max(step_ms),
+                               "all": [round(x, 5) for x in step_ms]}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         base, ref = cpu_baseline(m, args.cpu_seconds)
         line["cpu_baseline"] = base
