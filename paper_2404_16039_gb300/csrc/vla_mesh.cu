@@ -232,10 +232,10 @@ __global__ void k_fill_n2e(int64_t ne, int nlb, const int32_t *__restrict__ elem
         }
 }
 
-// insertion sort of every node's incidence list (ascending element id)
-// sorts every segment [ptr[i], ptr[i+1]) of v ascending, one warp per segment:
-// up to 32 keys by a bitonic sort across the lanes (shuffles), longer ones by
-// insertion on one lane
+// Sorts every segment [ptr[i], ptr[i+1]) of v ascending (the nodes'
+// incidence lists by element id, the Morton buckets by node id), one warp per
+// segment: up to 32 keys by a bitonic sort across the lanes (shuffles), longer
+// ones by insertion on one lane
 constexpr int kSegWarps = 8;
 __global__ void __launch_bounds__(kSegWarps * 32) k_sort_segments(int64_t n, const int32_t *__restrict__ ptr,
                                                                   int32_t *__restrict__ v) {
