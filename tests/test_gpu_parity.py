@@ -144,7 +144,7 @@ def test_page_primitives_misaligned_pointer(vla):
     np.testing.assert_allclose(D, oracle.amdet(P["A"]), rtol=1e-13, atol=1e-12)
 
 
-@pytest.mark.parametrize("op", ["amtam", "aminv"])
+@pytest.mark.parametrize("op", ["amtam", "aminv", "astam", "avtam", "amdet", "amtam_f32"])
 def test_page_primitives_full_size_sampled(vla, op):
     # N = 1e8 pages of 3x3 FP64 (the largest sweep point), generated on the device;
     # a seeded sample of 1e5 pages is checked against the oracle
@@ -154,16 +154,44 @@ def test_page_primitives_full_size_sampled(vla, op):
     A[:, [0, 1, 2], [0, 1, 2]] += 3.0
     idx = np.random.default_rng(0).choice(N, 100_000, replace=False)
     Ai = A[torch.from_numpy(idx).cuda()].cpu().numpy()
+    sel = torch.from_numpy(idx).cuda()
     if op == "amtam":
         B = torch.randn((N, 3, 3), generator=g, dtype=torch.float64, device="cuda")
         C = vla.amtam(A, B)
-        Bi = B[torch.from_numpy(idx).cuda()].cpu().numpy()
-        Ci = C[torch.from_numpy(idx).cuda()].cpu().numpy()
+        Bi = B[sel].cpu().numpy()
+        Ci = C[sel].cpu().numpy()
         np.testing.assert_allclose(Ci, oracle.amtam(Ai, Bi), rtol=0, atol=1e-12 * np.abs(Ci).max())
         del B, C
+    elif op == "amtam_f32":   # the FP32 sweep point: the same pages rounded to float
+        A32 = A.float()
+        del A
+        B32 = torch.randn((N, 3, 3), generator=g, dtype=torch.float32, device="cuda")
+        C = vla.amtam(A32, B32)
+        Ai, Bi, Ci = (x[sel].double().cpu().numpy() for x in (A32, B32, C))
+        ref = oracle.amtam(Ai, Bi)   # FP64 of the FP32 inputs: only the float products' rounding differs
+        assert np.abs(Ci - ref).max() <= 1e-5 * np.abs(ref).max()
+        del A32, B32, C
+        torch.cuda.empty_cache()
+        return
+    elif op == "astam":
+        sc = 0.5 + 1.5 * torch.rand(N, generator=g, dtype=torch.float64, device="cuda")
+        C = vla.astam(sc, A)
+        np.testing.assert_allclose(C[sel].cpu().numpy(), oracle.astam(sc[sel].cpu().numpy(), Ai), rtol=1e-15, atol=0)
+        del sc, C
+    elif op == "avtam":
+        v = torch.randn((N, 3), generator=g, dtype=torch.float64, device="cuda")
+        y = vla.avtam(v, A)
+        yr = oracle.avtam(v[sel].cpu().numpy(), Ai)
+        np.testing.assert_allclose(y[sel].cpu().numpy(), yr, rtol=0, atol=1e-12 * np.abs(yr).max())
+        del v, y
+    elif op == "amdet":
+        d = vla.amdet(A)
+        dr = oracle.amdet(Ai)
+        np.testing.assert_allclose(d[sel].cpu().numpy(), dr, rtol=0, atol=1e-12 * np.abs(dr).max())
+        del d
     else:
         inv, det, ns = vla.aminv(A)
-        Ii = inv[torch.from_numpy(idx).cuda()].cpu().numpy()
+        Ii = inv[sel].cpu().numpy()
         Ir, Dr, _ = oracle.aminv(Ai)
         cond = np.linalg.cond(np.transpose(Ai, (0, 2, 1)))
         err = np.abs(Ii - Ir).max(axis=(1, 2)) / np.abs(Ir).max(axis=(1, 2))
