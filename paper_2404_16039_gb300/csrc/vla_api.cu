@@ -71,18 +71,21 @@ void set_tuned(int type, bool mix, int budget, int ctas) {
 // device) of freed memory mapped between calls.  The device's default pool
 // keeps none: every synchronisation returns what was freed to the driver, and
 // the next build maps it again (a few hundred MB of scratch per million
-// elements).  VLA_POOL_KEEP (bytes) sets the amount kept; 0 keeps none.
+// elements).  VLA_POOL_KEEP (bytes) sets the amount kept; 0 keeps none.  If
+// the pool cannot be made, the device's default pool serves the allocations.
 cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t st) {
     static std::mutex mu;
     static cudaMemPool_t pools[64] = {};
+    static bool tried[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaMallocAsync(p, bytes, st);
-    cudaMemPool_t pool;
+    cudaMemPool_t pool = nullptr;
     {
         std::lock_guard<std::mutex> lk(mu);
-        if (!pools[dev]) {
+        if (!tried[dev]) {   // one attempt per device; without a pool the device's default one serves
+            tried[dev] = true;
             cudaMemPoolProps pp;
             std::memset(&pp, 0, sizeof(pp));
             pp.allocType = cudaMemAllocationTypePinned;
@@ -90,26 +93,19 @@ cudaError_t pool_malloc(void **p, size_t bytes, cudaStream_t st) {
             pp.location.type = cudaMemLocationTypeDevice;
             pp.location.id = dev;
             cudaMemPool_t np;
-            e = cudaMemPoolCreate(&np, &pp);
-            if (e != cudaSuccess) return e;
             size_t fr = 0, total = 0;
-            e = cudaMemGetInfo(&fr, &total);
-            if (e != cudaSuccess) {
-                cudaMemPoolDestroy(np);
-                return e;
+            if (cudaMemPoolCreate(&np, &pp) == cudaSuccess) {
+                unsigned long long keep = 0;
+                if (cudaMemGetInfo(&fr, &total) == cudaSuccess) keep = std::min<unsigned long long>(8ull << 30, total / 16);
+                if (const char *k = getenv("VLA_POOL_KEEP")) keep = strtoull(k, nullptr, 10);
+                if (cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess) pools[dev] = np;
+                else cudaMemPoolDestroy(np);
             }
-            unsigned long long keep = std::min<unsigned long long>(8ull << 30, total / 16);
-            if (const char *k = getenv("VLA_POOL_KEEP")) keep = strtoull(k, nullptr, 10);
-            e = cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
-            if (e != cudaSuccess) {
-                cudaMemPoolDestroy(np);
-                return e;
-            }
-            pools[dev] = np;
+            cudaGetLastError();   // a failed attempt leaves no sticky error behind
         }
         pool = pools[dev];
     }
-    return cudaMallocFromPoolAsync(p, bytes, pool, st);
+    return pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMallocAsync(p, bytes, st);
 }
 
 }  // namespace vla
