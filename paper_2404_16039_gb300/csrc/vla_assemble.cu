@@ -22,6 +22,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <set>
 #include <type_traits>
 
 #include "vla_internal.cuh"
@@ -30,6 +31,12 @@ namespace vla {
 namespace {
 
 constexpr int kThreads = 256;
+// FP64 single-mesh calls on tetrahedral meshes of at least this many elements
+// take the two-pass form (records once per element, then the tiles): 1.6-1.7x
+// faster on 64^3 P1 and 36^3 P2 tets.  Smaller meshes keep the one-launch
+// form, whose latency is lower, and so do triangles, whose tiles recompute
+// fewer elements (two passes measured 6-21 % slower there)
+constexpr int64_t kTwoPassMinElems = 20000;
 
 // ---------------------------------------------------------------------------
 // P2 reference tables (built on the host once per device)
@@ -639,7 +646,7 @@ struct MeshJob {
     int32_t type;          // element type index (dim - 2) * 2 + (order - 1)
     int32_t n_tiles;
     int32_t work_base;     // first work item of the mesh in a batched launch
-    int64_t pad;
+    const int32_t *tile_eid;   // global ids of every tile element (records computed beforehand)
 };
 static_assert(sizeof(MeshJob) == 176, "MeshJob is bulk-copied in 16-byte units");
 static_assert(sizeof(vla::TileHdr) == 64, "TileHdr is fetched in 16-byte units");
@@ -667,6 +674,9 @@ struct LaunchArgs {
     double *nrm, *area;
     int64_t nfb;
     int dim;
+    // records computed beforehand, one per element at the record stride (FP64
+    // single-mesh launch; null: the tiles compute their elements)
+    const double *recs;
 };
 
 __host__ __device__ constexpr int padq(int x, int q) { return (x + q - 1) / q * q; }
@@ -732,6 +742,52 @@ __device__ __forceinline__ void cp_async_wait_but1() { asm volatile("cp.async.wa
 // triangle of K_k and the mass scale into the record area (index n_elems is
 // the zero record that padding codes point at), and writes the outputs of
 // the elements the tile owns (vol, optional pages, singular count).
+// The record of one element (centroid coefficient): the packed upper triangle
+// of K_k = c/(d!|det|) (C_a . C_b) (P1: the last vertex's column from the
+// zero row sums) and the mass scale after it; returns the mass scale (P1 the
+// off-diagonal mass entry, P2 c|T|).  FP64 records are written in pairs of
+// words up to the record stride.
+template <int DIM, int ORDER, bool MIX>
+__device__ __forceinline__ typename Cfg<DIM, ORDER, MIX>::T element_record(const Geo<typename Cfg<DIM, ORDER, MIX>::T> &g,
+                                                                          typename Cfg<DIM, ORDER, MIX>::T adet, int kind,
+                                                                          typename Cfg<DIM, ORDER, MIX>::T ca,
+                                                                          typename Cfg<DIM, ORDER, MIX>::T cb,
+                                                                          typename Cfg<DIM, ORDER, MIX>::T *dst) {
+    using C = Cfg<DIM, ORDER, MIX>;
+    using T = typename C::T;
+    const T c = coeff<T>(kind, ca, cb, g.xc, DIM);
+    T sc;
+    if constexpr (MIX) sc = c * __frcp_rn(T(C::DFACT) * adet);   // K(a,b) = sc * C_a . C_b
+    else sc = c / (T(C::DFACT) * adet);
+    T mscale;
+    if constexpr (ORDER == 1) {
+        T rec[C::RS];
+#pragma unroll
+        for (int u = 0; u < C::RS; ++u) rec[u] = T(0);
+        p1_stiffness<DIM, T>(g, sc, rec);
+        mscale = c * adet * T(C::MOFF / C::DFACT);       // off-diagonal mass entry
+        rec[C::NU] = mscale;
+        if constexpr (MIX) {
+#pragma unroll
+            for (int u = 0; u <= C::NU; ++u) dst[u] = rec[u];
+        } else {
+#pragma unroll
+            for (int u = 0; u < C::RS; u += 2)
+                *reinterpret_cast<double2 *>(dst + u) = make_double2(rec[u], rec[u + 1]);
+        }
+    } else {
+        T cd[10];
+#pragma unroll
+        for (int a = 0; a < C::NV; ++a)
+#pragma unroll
+            for (int q = a; q < C::NV; ++q) cd[a * C::NV - a * (a - 1) / 2 + (q - a)] = dot3<T>(g.C[a], g.C[q]);
+        p2_k_entries<DIM, T>(cd, sc, dst, std::make_integer_sequence<int, C::NU>());
+        mscale = c * adet * T(1.0 / C::DFACT);           // c |T|; entries scale the reference mass
+        dst[C::NU] = mscale;
+    }
+    return mscale;
+}
+
 template <int DIM, int ORDER, bool MIX, bool LIT = false>
 __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileHdr &h, const unsigned char *b,
                                               const StageMap &mp, typename Cfg<DIM, ORDER, MIX>::T *s_k,
@@ -842,36 +898,7 @@ __device__ __forceinline__ void tile_elements(const MeshJob &J, const vla::TileH
             if (e < h.n_own) owned(e, g.det, adet, T(0), dst);
             return;
         }
-        const T c = coeff<T>(kind, ca, cb, g.xc, DIM);
-        T sc;
-        if constexpr (MIX) sc = c * __frcp_rn(T(C::DFACT) * adet);   // K(a,b) = sc * C_a . C_b
-        else sc = c / (T(C::DFACT) * adet);
-        T mscale;
-        if constexpr (ORDER == 1) {
-            T rec[C::RS];
-#pragma unroll
-            for (int u = 0; u < C::RS; ++u) rec[u] = T(0);
-            p1_stiffness<DIM, T>(g, sc, rec);
-            mscale = c * adet * T(C::MOFF / C::DFACT);       // off-diagonal mass entry
-            rec[C::NU] = mscale;
-            if constexpr (MIX) {
-#pragma unroll
-                for (int u = 0; u <= C::NU; ++u) dst[u] = rec[u];
-            } else {
-#pragma unroll
-                for (int u = 0; u < C::RS; u += 2)
-                    *reinterpret_cast<double2 *>(dst + u) = make_double2(rec[u], rec[u + 1]);
-            }
-        } else {
-            T cd[10];
-#pragma unroll
-            for (int a = 0; a < C::NV; ++a)
-#pragma unroll
-                for (int q = a; q < C::NV; ++q) cd[a * C::NV - a * (a - 1) / 2 + (q - a)] = dot3<T>(g.C[a], g.C[q]);
-            p2_k_entries<DIM, T>(cd, sc, dst, std::make_integer_sequence<int, C::NU>());
-            mscale = c * adet * T(1.0 / C::DFACT);           // c |T|; entries scale the reference mass
-            dst[C::NU] = mscale;
-        }
+        const T mscale = element_record<DIM, ORDER, MIX>(g, adet, kind, ca, cb, dst);
         if (e < h.n_own) owned(e, g.det, adet, mscale, dst);
     };
     for (int e = threadIdx.x; e <= h.n_elems; e += kThreads) elem(e);
@@ -1021,7 +1048,7 @@ constexpr int single_type(int types) { return types == 1 ? 0 : types == 2 ? 1 : 
 // tile j is computed from stage j&1, the bulk copies of tile j+2 (and, in a
 // batch, the job of its mesh) and the coordinate gathers (cp.async) of tile
 // j+1 are in flight, and the header of tile j+2 is being fetched.
-template <bool MIX, int TYPES, bool BATCH, bool LIT = false>
+template <bool MIX, int TYPES, bool BATCH, bool LIT = false, bool PRE = false>
 __global__ void __launch_bounds__(kThreads, 3) k_assemble(const LaunchArgs A) {
     using T = typename std::conditional<MIX, float, double>::type;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1092,6 +1119,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_assemble(const LaunchArgs A) {
     };
     // coordinate gathers of the tile of stage s (all threads, asynchronous)
     auto gather = [&](int s) {
+        if constexpr (PRE) {   // records computed beforehand: no coordinates (an empty group keeps the count)
+            cp_async_commit();
+            return;
+        }
         const vla::TileHdr &h = s_item[s].h;
         const StageMap &mp = s_map[s];
         const MeshJob &J = job_of(s);
@@ -1158,10 +1189,30 @@ __global__ void __launch_bounds__(kThreads, 3) k_assemble(const LaunchArgs A) {
         const unsigned char *b = stage(s);
         const int ty = type_of(s);
 
-        by_type<TYPES>(ty, [&](auto D, auto O) {
-            constexpr int DIM = decltype(D)::value, ORDER = decltype(O)::value;
-            tile_elements<DIM, ORDER, MIX, LIT && ORDER == 1>(job_of(s), h, b, mp, s_k, mhat + (DIM == 3 ? 21 : 0));
-        });
+        if constexpr (PRE) {   // the tile's records, computed beforehand, gathered by element id
+            by_type<TYPES>(ty, [&](auto D, auto O) {
+                constexpr int DIM = decltype(D)::value, ORDER = decltype(O)::value;
+                constexpr int RS = Cfg<DIM, ORDER, false>::RS;
+                const int32_t *eid = job_of(s).tile_eid + h.elem_off;
+                for (int e = threadIdx.x; e <= h.n_elems; e += kThreads) {
+                    double2 *dst = reinterpret_cast<double2 *>(s_k + (size_t)e * RS);
+                    if (e == h.n_elems) {
+#pragma unroll
+                        for (int u = 0; u < RS / 2; ++u) dst[u] = make_double2(0.0, 0.0);
+                    } else {
+                        const double2 *src = reinterpret_cast<const double2 *>(A.recs + (size_t)eid[e] * RS);
+#pragma unroll
+                        for (int u = 0; u < RS / 2; ++u) dst[u] = src[u];
+                    }
+                }
+            });
+        } else {
+            by_type<TYPES>(ty, [&](auto D, auto O) {
+                constexpr int DIM = decltype(D)::value, ORDER = decltype(O)::value;
+                tile_elements<DIM, ORDER, MIX, LIT && ORDER == 1>(job_of(s), h, b, mp, s_k,
+                                                                  mhat + (DIM == 3 ? 21 : 0));
+            });
+        }
         // prefetch: coordinates of the next tile (its bulk copies were issued two tiles ago)
         if (t + G < n) {
             if (__syncthreads_or(!mbar_wait_bounded(&bar[s ^ 1], (uint32_t)(((j + 1) >> 1) & 1), A.spin_limit))) {
@@ -1199,6 +1250,54 @@ __global__ void __launch_bounds__(kThreads, 3) k_assemble(const LaunchArgs A) {
     }
 }
 
+// The first pass of the FP64 single-mesh form: every element's record once
+// (the tile kernel's geometry and record code on the element's own vertex
+// coordinates), at the FP64 record stride, with its volume, singular count
+// and pages.  The FP64 pipe runs at a small fraction of the FP32 rate, and the
+// tile kernel would evaluate every element once per tile touching it (2.5
+// times on a 3-D P1 mesh); the second pass gathers these records per tile.
+template <int DIM, int ORDER>
+__global__ void __launch_bounds__(256) k_records_f64(int64_t ne, const int32_t *__restrict__ elems,
+                                                     const double *__restrict__ x, int kind, double ca, double cb,
+                                                     double *__restrict__ recs, double *__restrict__ vol,
+                                                     double *__restrict__ Kp, double *__restrict__ Mp,
+                                                     unsigned long long *__restrict__ n_sing) {
+    using C = Cfg<DIM, ORDER, false>;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < ne; k += (int64_t)gridDim.x * blockDim.x) {
+        double4_16a lx[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            lx[j].x = lx[j].y = lx[j].z = lx[j].w = 0.0;
+            if (j < C::NV) {
+                const int64_t v = elems[k * C::NLB + j];
+                lx[j].x = x[v * DIM];
+                lx[j].y = x[v * DIM + 1];
+                if (DIM == 3) lx[j].z = x[v * DIM + 2];
+            }
+        }
+        Geo<double> g;
+        geo_f64<DIM>(lx, make_ushort4(0, 1, 2, DIM == 3 ? 3 : 0), g);
+        const double adet = g.det < 0.0 ? -g.det : g.det;
+        double *dst = recs + (size_t)k * C::RS;
+        const double mscale = element_record<DIM, ORDER, false>(g, adet, kind, ca, cb, dst);
+        if (g.det == 0.0 && n_sing) atomicAdd(n_sing, 1ull);
+        if (vol) vol[k] = adet / C::DFACT;
+        if (Kp || Mp) {
+            for (int a = 0; a < C::NLB; ++a)
+                for (int q = 0; q < C::NLB; ++q) {
+                    const int p0 = a < q ? a : q, p1 = a < q ? q : a;
+                    const int u = p0 * C::NLB - p0 * (p0 - 1) / 2 + (p1 - p0);
+                    const int64_t pos = k * C::NLB * C::NLB + a + (int64_t)q * C::NLB;
+                    double mv;
+                    if constexpr (ORDER == 1) mv = mscale * (a == q ? 2.0 : 1.0);
+                    else mv = mscale * c_p2[DIM == 3 ? 1 : 0].mhat_d[u];
+                    if (Kp) Kp[pos] = dst[u];
+                    if (Mp) Mp[pos] = mv;
+                }
+        }
+    }
+}
+
 // stage and record-area sizes of a mesh under a launch of precision MIX
 inline int mesh_stage_bytes(const vla_mesh *m) {
     return (int)((m->tile_stage_bytes + 32 * (size_t)m->max_tile_nodes + 16 + 15) / 16 * 16);
@@ -1213,16 +1312,18 @@ inline size_t mesh_record_bytes(const vla_mesh *m, bool mix, bool lit = false) {
 // memory limit is raised to the device maximum once per device, so launches
 // (and graphs) of any size up to it stay valid.
 template <bool MIX, int TYPES, bool BATCH, bool LIT = false>
-vla_status kernel_shape(size_t smem, int ctas_per_sm, int n_work, int *grid) {
+vla_status kernel_shape(size_t smem, int ctas_per_sm, int n_work, int *grid,
+                        const void *kern_ptr = (const void *)k_assemble<MIX, TYPES, BATCH, LIT>) {
     // the occupancy answer per (device, shared memory) is cached: the host
     // latency of a call on a small mesh is otherwise dominated by the queries
     struct Shape {
         int dev;
+        const void *kern;
         size_t smem;
         int per_sm, nsm;
     };
     static std::mutex mu;
-    static bool ready[64] = {};
+    static std::set<std::pair<int, const void *>> ready;
     static std::vector<Shape> cache;
     int dev = 0;
     VLA_CUDA(cudaGetDevice(&dev));
@@ -1230,7 +1331,7 @@ vla_status kernel_shape(size_t smem, int ctas_per_sm, int n_work, int *grid) {
     {
         std::lock_guard<std::mutex> lk(mu);
         for (const Shape &c : cache)
-            if (c.dev == dev && c.smem == smem) {
+            if (c.dev == dev && c.kern == kern_ptr && c.smem == smem) {
                 per_sm = c.per_sm;
                 nsm = c.nsm;
                 break;
@@ -1240,7 +1341,7 @@ vla_status kernel_shape(size_t smem, int ctas_per_sm, int n_work, int *grid) {
         int maxsm = 0;
         VLA_CUDA(cudaDeviceGetAttribute(&maxsm, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         VLA_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        auto kern = k_assemble<MIX, TYPES, BATCH, LIT>;
+        const void *kern = kern_ptr;
         cudaFuncAttributes fa;
         VLA_CUDA(cudaFuncGetAttributes(&fa, kern));
         if (smem + fa.sharedSizeBytes > (size_t)maxsm)
@@ -1248,17 +1349,17 @@ vla_status kernel_shape(size_t smem, int ctas_per_sm, int n_work, int *grid) {
                         smem + fa.sharedSizeBytes, maxsm);
         {
             std::lock_guard<std::mutex> lk(mu);
-            if (dev < 0 || dev >= 64 || !ready[dev]) {
+            if (!ready.count({dev, kern})) {
                 VLA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               maxsm - (int)fa.sharedSizeBytes));
-                if (dev >= 0 && dev < 64) ready[dev] = true;
+                ready.insert({dev, kern});
             }
         }
         per_sm = 0;
         VLA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
         if (per_sm < 1) per_sm = 1;
         std::lock_guard<std::mutex> lk(mu);
-        if (cache.size() < 4096) cache.push_back(Shape{dev, smem, per_sm, nsm});
+        if (cache.size() < 4096) cache.push_back(Shape{dev, kern, smem, per_sm, nsm});
     }
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     int g = nsm * per_sm;
@@ -1282,6 +1383,18 @@ vla_status launch_single(const LaunchArgs &a, size_t smem, int ctas_per_sm, cuda
     return launch_kernel<MIX, TYPES, false, LIT>(a, smem, grid, st);
 }
 
+// the second pass of the FP64 single-mesh form: the tile kernel on records computed beforehand
+template <int TYPES>
+vla_status launch_pre(const LaunchArgs &a, size_t smem, int ctas_per_sm, cudaStream_t st) {
+    int grid = 0;
+    TRY((kernel_shape<false, TYPES, false, false>(smem, ctas_per_sm, a.n_work, &grid,
+                                                  (const void *)k_assemble<false, TYPES, false, false, true>)));
+    if (grid < 1) return VLA_OK;
+    k_assemble<false, TYPES, false, false, true><<<grid, kThreads, smem, st>>>(a);
+    VLA_CUDA(cudaGetLastError());
+    return VLA_OK;
+}
+
 MeshJob make_job(const vla_mesh *m, int kind, double ca, double cb, double *K, double *M, double *vol, double *Kp,
                  double *Mp, unsigned long long *ns) {
     MeshJob j;
@@ -1290,6 +1403,7 @@ MeshJob make_job(const vla_mesh *m, int kind, double ca, double cb, double *K, d
     j.tile_nodes = m->tile_nodes;
     j.tile_elem = m->tile_elem;
     j.tile_own = m->tile_own;
+    j.tile_eid = m->tile_eid;
     j.tile_nzpos = m->tile_nzpos;
     j.tile_chunks = m->tile_chunks;
     j.codes = m->tile_codes;
@@ -1454,6 +1568,33 @@ vla_status assemble_impl(const vla_mesh *m, int32_t kind, double ca, double cb, 
         case 4: return launch_single<false, 4, true>(a, smem, cps, st);
         default: return launch_single<true, 4, true>(a, smem, cps, st);
         }
+    }
+    if (!mix && m->dim == 3 && m->ne >= kTwoPassMinElems) {   // FP64 tets: records once, then the tiles
+        const int nu = m->nlb * (m->nlb + 1) / 2, rs = (nu + 1 + 3) / 4 * 4;
+        double *recs = nullptr;
+        VLA_CUDA(pool_malloc((void **)&recs, sizeof(double) * (size_t)rs * (size_t)m->ne, st));
+        const int g = grid_for(m->ne, 256, (int64_t)152 * 16);
+        switch (ty) {
+        case 0: k_records_f64<2, 1><<<g, 256, 0, st>>>(m->ne, m->elems, m->coords, kind, ca, cb, recs, vol, K_pages, M_pages, ns); break;
+        case 1: k_records_f64<2, 2><<<g, 256, 0, st>>>(m->ne, m->elems, m->coords, kind, ca, cb, recs, vol, K_pages, M_pages, ns); break;
+        case 2: k_records_f64<3, 1><<<g, 256, 0, st>>>(m->ne, m->elems, m->coords, kind, ca, cb, recs, vol, K_pages, M_pages, ns); break;
+        default: k_records_f64<3, 2><<<g, 256, 0, st>>>(m->ne, m->elems, m->coords, kind, ca, cb, recs, vol, K_pages, M_pages, ns); break;
+        }
+        vla_status s = VLA_OK;
+        if (cudaGetLastError() != cudaSuccess) s = fail(VLA_ERR_CUDA, "FP64 element records launch failed");
+        if (s == VLA_OK) {
+            a.recs = recs;
+            a.one.vol = a.one.Kp = a.one.Mp = nullptr;   // written by the first pass
+            a.one.n_sing = nullptr;
+            switch (ty) {
+            case 0: s = launch_pre<1>(a, smem, cps, st); break;
+            case 1: s = launch_pre<2>(a, smem, cps, st); break;
+            case 2: s = launch_pre<4>(a, smem, cps, st); break;
+            default: s = launch_pre<8>(a, smem, cps, st); break;
+            }
+        }
+        cudaFreeAsync(recs, st);
+        return s;
     }
     switch (ty * 2 + (mix ? 1 : 0)) {
     case 0: return launch_single<false, 1>(a, smem, cps, st);

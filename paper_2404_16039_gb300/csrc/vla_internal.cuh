@@ -265,6 +265,7 @@ struct vla_mesh {
     int32_t *tile_nodes;   // global node ids per tile
     ushort4 *tile_elem;    // local vertex indices per tile element
     int32_t *tile_own;     // global ids of owned elements
+    int32_t *tile_eid;     // global ids of every tile element (owned first), as tile_elem
     int2 *tile_nzpos;      // (p_ij, p_ji) CSR positions of each tile pair
     int2 *tile_chunks;     // (code offset within the tile segment, width) per 32-pair chunk
     void *tile_codes;      // uint16 (P1) or uint32 (P2) contribution codes, chunk-interleaved

@@ -925,6 +925,7 @@ __global__ void __launch_bounds__(256) k_tile_fill(int n_tiles, int dim, int cap
                                                    const int32_t *__restrict__ sc_elems,
                                                    const int32_t *__restrict__ sc_nodes, int32_t *__restrict__ tile_nodes,
                                                    ushort4 *__restrict__ tile_elem, int32_t *__restrict__ tile_own,
+                                                   int32_t *__restrict__ tile_eid,
                                                    int2 *__restrict__ tile_nzpos, int32_t *__restrict__ nz_count,
                                                    int2 *__restrict__ row_info) {
     extern __shared__ int32_t s_tn[];
@@ -947,6 +948,7 @@ __global__ void __launch_bounds__(256) k_tile_fill(int n_tiles, int dim, int cap
             if (j <= dim) v[j] = (unsigned short)lower_bound_i32(s_tn, h.n_nodes, elems[k * NLB + j]);
         tile_elem[h.elem_off + e] = make_ushort4(v[0], v[1], v[2], v[3]);
         if (e < h.n_own) tile_own[h.own_off + e] = (int32_t)k;
+        tile_eid[h.elem_off + e] = (int32_t)k;
     }
     // per-row base of its upper pairs and index of its diagonal (rank order)
     long long ubase = 0, dbase = 0;
@@ -1524,11 +1526,13 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         TRY(dalloc(m, &m->tile_nodes, o_node + 4, st));
         TRY(dalloc(m, &m->tile_elem, o_elem + 2, st));
         TRY(dalloc(m, &m->tile_own, o_own + 4, st));
+        TRY(dalloc(m, &m->tile_eid, o_elem + 4, st));
         TRY(dalloc(m, &m->tile_nzpos, o_nz + 2, st));
         TRY(dalloc(m, &m->tile_chunks, o_chunk + 2, st));
         VLA_CUDA(cudaMemsetAsync(m->tile_nodes, 0, sizeof(int32_t) * (o_node + 4), st));
         VLA_CUDA(cudaMemsetAsync(m->tile_elem, 0, sizeof(ushort4) * (o_elem + 2), st));
         VLA_CUDA(cudaMemsetAsync(m->tile_own, 0, sizeof(int32_t) * (o_own + 4), st));
+        VLA_CUDA(cudaMemsetAsync(m->tile_eid, 0, sizeof(int32_t) * (o_elem + 4), st));
         VLA_CUDA(cudaMemsetAsync(m->tile_nzpos, 0, sizeof(int2) * (o_nz + 2), st));
         VLA_CUDA(cudaMemsetAsync(m->tile_chunks, 0, sizeof(int2) * (o_chunk + 2), st));
         int32_t *nz_count, *tile_ncodes, *nz_order;
@@ -1543,7 +1547,8 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
             TRY(allow_max_smem((const void *)kf));
             kf<<<(int)n_tiles, 256, sizeof(int32_t) * (size_t)std::max(1, m->max_tile_nodes), st>>>(
                 (int)n_tiles, dim, cap_e, cap_n, m->tiles, perm, m->n2e_ptr, m->n2e, m->elems, m->row_ptr, m->col_idx,
-                sc_elems, sc_nodes, m->tile_nodes, m->tile_elem, m->tile_own, nzpos_rm, nz_count, row_info);
+                sc_elems, sc_nodes, m->tile_nodes, m->tile_elem, m->tile_own, m->tile_eid, nzpos_rm, nz_count,
+                row_info);
             VLA_CUDA(cudaGetLastError());
         }
         k_chunk_table<<<(int)n_tiles, kChunkWarps * 32, 0, st>>>((int)n_tiles, m->tiles, nz_count, nzpos_rm, m->tile_nzpos, nz_order,

@@ -201,6 +201,35 @@ def test_batch_uneven_full_size(vla):
         gm.close()
 
 
+@pytest.mark.parametrize("dim,order,n", [(3, 1, 16), (3, 2, 16)])
+def test_fp64_two_pass_equals_one_launch(vla, dim, order, n):
+    # an FP64 call on a tetrahedral mesh of >= 20,000 elements computes every
+    # element's record once and then the tiles (two passes); a batch of that
+    # mesh runs the one-launch form: the same bits, pages, volumes and
+    # singular count too
+    m = meshgen.kuhn_cube(n, jitter=0.1, seed=4) if (dim, order) == (3, 1) else \
+        meshgen.make_mesh(dim, n, order=order, jitter=0.1, seed=4)
+    assert m.ne >= 20000
+    gm = _gpu_mesh(vla, m)
+    for kind, ca, cb in ((0, 1.0, 1.0), (1, 0.7, 0.3)):
+        two = gm.assemble(ca, cb, kind=kind, precision=0, pages=True, count_singular=True)
+        jobs = [(gm, gm.outputs(pages=True), kind, ca, cb)]
+        b = vla.Batch(jobs, precision=0, count_singular=True)
+        b.run()
+        torch.cuda.synchronize()
+        one = jobs[0][1]
+        for key in ("K", "M", "vol", "K3D", "M3D"):
+            assert torch.equal(two[key], one[key]), (kind, key)
+        assert int(two["n_singular"].item()) == int(b.n_singular.abs().sum().item()) == 0
+        b.close()
+    ref = oracle.assemble(dim, order, m.nn, m.elems, m.coords, 1.0, 1.0)
+    two = gm.assemble(1.0, 1.0, precision=0)
+    for key in ("K", "M", "vol"):
+        r = ref[key]
+        assert np.abs(two[key].cpu().numpy() - r).max() <= TOL64 * np.abs(r).max(), key
+    gm.close()
+
+
 def test_tile_budget_does_not_change_results(vla):
     m = meshgen.kuhn_cube(10, seed=2)
     ref = None
