@@ -893,6 +893,14 @@ __device__ __forceinline__ int tile_local_elem(const int32_t *te, int n_own, int
     return n_own + lower_bound_i32(te + n_own, n_el - n_own, k);
 }
 
+// What the warp passes need of a tile row, written once by the row pass of
+// k_tile_fill: its node, CSR start and length, the diagonal's offset, its
+// incidence list, and the indices of its first upper pair and its diagonal
+// among the tile's pairs (one 32-byte load instead of a chain of dependent ones)
+struct __align__(16) RowInfo {
+    int32_t qu, qd, i, b, len, ds, q0, nq;
+};
+
 // number of a row's columns below i (the diagonal's offset in the row), by a warp
 __device__ __forceinline__ int warp_count_below(const int32_t *__restrict__ col, int len, int32_t i) {
     const int lane = threadIdx.x & 31;
@@ -927,7 +935,7 @@ __global__ void __launch_bounds__(256) k_tile_fill(int n_tiles, int dim, int cap
                                                    ushort4 *__restrict__ tile_elem, int32_t *__restrict__ tile_own,
                                                    int32_t *__restrict__ tile_eid,
                                                    int2 *__restrict__ tile_nzpos, int32_t *__restrict__ nz_count,
-                                                   int2 *__restrict__ row_info) {
+                                                   RowInfo *__restrict__ row_info) {
     extern __shared__ int32_t s_tn[];
     const int t = blockIdx.x;
     if (t >= n_tiles) return;
@@ -973,7 +981,8 @@ __global__ void __launch_bounds__(256) k_tile_fill(int n_tiles, int dim, int cap
             const int32_t qu = (int32_t)(ubase + pu);
             const int32_t qd = hasd ? h.n_up + (int32_t)(dbase + pd) : -1;
             if (hasd) tile_nzpos[h.nz_off + qd] = make_int2(b + ds, b + ds);
-            row_info[h.rank_begin + rr] = make_int2(qu, qd);
+            const int32_t q0 = n2e_ptr[i];
+            row_info[h.rank_begin + rr] = RowInfo{qu, qd, i, b, len, ds, q0, n2e_ptr[i + 1] - q0};
         }
         ubase += tot_u;
         dbase += tot_d;
@@ -983,19 +992,16 @@ __global__ void __launch_bounds__(256) k_tile_fill(int n_tiles, int dim, int cap
     // every pair (each written once)
     const int lane = threadIdx.x & 31;
     for (int rr = threadIdx.x >> 5; rr < h.n_rows; rr += blockDim.x >> 5) {
-        const int32_t i = perm[h.rank_begin + rr];
-        const int32_t b = row_ptr[i], len = row_ptr[i + 1] - b;
+        const RowInfo ri = row_info[h.rank_begin + rr];
+        const int32_t i = ri.i, b = ri.b, len = ri.len, ds = ri.ds, q0 = ri.q0, nq = ri.nq;
         if (len == 0) continue;
-        const int2 ri = row_info[h.rank_begin + rr];
-        const int ds = warp_count_below(col_idx + b, len, i);
         const int np = len - ds;
-        const int32_t q0 = n2e_ptr[i], nq = n2e_ptr[i + 1] - q0;
         for (int p0 = 0; p0 < np; p0 += 32) {
             const int pp = p0 + lane, npq = min(32, np - p0);
             const int32_t c_pp = pp < np - 1 ? col_idx[b + ds + 1 + pp] : i;
             if (pp < np - 1) {   // upper pair {i, c}: its place in row c by a search of that row
                 const int32_t bj = row_ptr[c_pp], lj = row_ptr[c_pp + 1] - bj;
-                tile_nzpos[h.nz_off + ri.x + pp] = make_int2(b + ds + 1 + pp, bj + lower_bound_i32(col_idx + bj, lj, i));
+                tile_nzpos[h.nz_off + ri.qu + pp] = make_int2(b + ds + 1 + pp, bj + lower_bound_i32(col_idx + bj, lj, i));
             }
             int cnt = 0;
             for (int j0 = 0; j0 < nq; j0 += 32) {
@@ -1013,7 +1019,7 @@ __global__ void __launch_bounds__(256) k_tile_fill(int n_tiles, int dim, int cap
                     if (lane == q) cnt += n;
                 }
             }
-            if (pp < np) nz_count[h.nz_off + (pp == np - 1 ? ri.y : ri.x + pp)] = cnt;
+            if (pp < np) nz_count[h.nz_off + (pp == np - 1 ? ri.qd : ri.qu + pp)] = cnt;
         }
     }
 }
@@ -1113,7 +1119,7 @@ __global__ void __launch_bounds__(256) k_tile_codes(int n_tiles, int cap_e, int 
                                                     const int32_t *__restrict__ row_ptr,
                                                     const int32_t *__restrict__ col_idx,
                                                     const int32_t *__restrict__ sc_elems,
-                                                    const int2 *__restrict__ row_info,
+                                                    const RowInfo *__restrict__ row_info,
                                                     const int32_t *__restrict__ order, const int2 *__restrict__ chunks,
                                                     CT *__restrict__ codes) {
     extern __shared__ int32_t s_te[];
@@ -1128,19 +1134,16 @@ __global__ void __launch_bounds__(256) k_tile_codes(int n_tiles, int cap_e, int 
     const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
     for (int rr = threadIdx.x >> 5; rr < h.n_rows; rr += blockDim.x >> 5) {
-        const int32_t i = perm[h.rank_begin + rr];
-        const int32_t b = row_ptr[i], len = row_ptr[i + 1] - b;
+        const RowInfo ri = row_info[h.rank_begin + rr];
+        const int32_t i = ri.i, b = ri.b, len = ri.len, ds = ri.ds, q0 = ri.q0, nq = ri.nq;
         if (len == 0) continue;
-        const int2 ri = row_info[h.rank_begin + rr];
-        const int ds = warp_count_below(col_idx + b, len, i);
         const int np = len - ds;
-        const int32_t q0 = n2e_ptr[i], nq = n2e_ptr[i + 1] - q0;
         for (int p0 = 0; p0 < np; p0 += 32) {
             const int pp = p0 + lane, npq = min(32, np - p0);
             const int32_t c_pp = pp < np - 1 ? col_idx[b + ds + 1 + pp] : i;
             int base_pp = 0;   // the pair's first slot: its chunk's code offset plus its lane in the chunk
             if (pp < np) {
-                const int nqo = order[h.nz_off + (pp == np - 1 ? ri.y : ri.x + pp)];
+                const int nqo = order[h.nz_off + (pp == np - 1 ? ri.qd : ri.qu + pp)];
                 base_pp = chunks[h.chunk_off + (nqo >> 5)].x + (nqo & 31);
             }
             int cnt = 0;
@@ -1536,7 +1539,8 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         VLA_CUDA(cudaMemsetAsync(m->tile_nzpos, 0, sizeof(int2) * (o_nz + 2), st));
         VLA_CUDA(cudaMemsetAsync(m->tile_chunks, 0, sizeof(int2) * (o_chunk + 2), st));
         int32_t *nz_count, *tile_ncodes, *nz_order;
-        int2 *row_info, *nzpos_rm;
+        RowInfo *row_info;
+        int2 *nzpos_rm;
         TRY(S.get(&nz_count, o_nz + 2));
         TRY(S.get(&nz_order, o_nz + 2));
         TRY(S.get(&nzpos_rm, o_nz + 2));
