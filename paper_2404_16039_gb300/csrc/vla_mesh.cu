@@ -1109,70 +1109,91 @@ __global__ void __launch_bounds__(kChunkWarps * 32) k_chunk_table(int n_tiles, c
 
 // Pass C: contribution codes, element * rsc + packed (a,b) entry (the entry's
 // word offset in a record of stride rsc), ascending element order per pair;
-// padding slots point at the tile's zero element.  Dynamic shared memory:
-// the tile's element list (n_elems ints), searched for local element indices.
+// padding slots point at the tile's zero element.  A warp takes a row and
+// walks its incidence list as (incidence, local node) items, 32 at a time:
+// an item whose node c is at or above the row's node is a contribution to
+// pair (i, c), found by a binary search of the row's upper columns staged in
+// shared memory; the items of a batch that hit the same pair are ranked by
+// lane (match), which keeps the ascending element order, and the pair's
+// running count sits in shared memory.  Dynamic shared memory: per warp the
+// row's upper columns, pair slot bases and counts (kMaxRow + 1 each), then the
+// tile's element list (n_elems ints), searched for local element indices.
+constexpr int kCodeWarps = 8;
 template <int NLB, typename CT>
-__global__ void __launch_bounds__(256) k_tile_codes(int n_tiles, int cap_e, int rsc, const TileHdr *__restrict__ hdr,
-                                                    const int32_t *__restrict__ perm,
-                                                    const int32_t *__restrict__ n2e_ptr,
-                                                    const int32_t *__restrict__ n2e, const int32_t *__restrict__ elems,
-                                                    const int32_t *__restrict__ row_ptr,
-                                                    const int32_t *__restrict__ col_idx,
-                                                    const int32_t *__restrict__ sc_elems,
-                                                    const RowInfo *__restrict__ row_info,
-                                                    const int32_t *__restrict__ order, const int2 *__restrict__ chunks,
-                                                    CT *__restrict__ codes) {
-    extern __shared__ int32_t s_te[];
+__global__ void __launch_bounds__(kCodeWarps * 32, 4) k_tile_codes(int n_tiles, int cap_e, int rsc,
+                                                                const TileHdr *__restrict__ hdr,
+                                                                const int32_t *__restrict__ n2e,
+                                                                const int32_t *__restrict__ elems,
+                                                                const int32_t *__restrict__ col_idx,
+                                                                const int32_t *__restrict__ sc_elems,
+                                                                const RowInfo *__restrict__ row_info,
+                                                                const int32_t *__restrict__ order,
+                                                                const int2 *__restrict__ chunks,
+                                                                CT *__restrict__ codes) {
+    extern __shared__ int32_t s_dyn[];
+    constexpr int W = kMaxRow + 1;
     const int t = blockIdx.x;
     if (t >= n_tiles) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int32_t *s_col = s_dyn + warp * 3 * W, *s_base = s_col + W, *s_cnt = s_base + W;
+    int32_t *s_te = s_dyn + kCodeWarps * 3 * W;
     const TileHdr h = hdr[t];
     const int32_t *te = sc_elems + (int64_t)t * cap_e;
     for (int i = threadIdx.x; i < h.n_elems; i += blockDim.x) s_te[i] = te[i];
     const CT dummy = (CT)((uint32_t)h.n_elems * (uint32_t)rsc);
     for (int i = threadIdx.x; i < h.n_codes; i += blockDim.x) codes[(int64_t)h.code_off + i] = dummy;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
     const unsigned below = (1u << lane) - 1u;
-    for (int rr = threadIdx.x >> 5; rr < h.n_rows; rr += blockDim.x >> 5) {
+    CT *out = codes + h.code_off;
+    for (int rr = warp; rr < h.n_rows; rr += kCodeWarps) {
         const RowInfo ri = row_info[h.rank_begin + rr];
-        const int32_t i = ri.i, b = ri.b, len = ri.len, ds = ri.ds, q0 = ri.q0, nq = ri.nq;
+        const int32_t i = ri.i, len = ri.len, q0 = ri.q0, nq = ri.nq;
         if (len == 0) continue;
-        const int np = len - ds;
-        for (int p0 = 0; p0 < np; p0 += 32) {
-            const int pp = p0 + lane, npq = min(32, np - p0);
-            const int32_t c_pp = pp < np - 1 ? col_idx[b + ds + 1 + pp] : i;
-            int base_pp = 0;   // the pair's first slot: its chunk's code offset plus its lane in the chunk
-            if (pp < np) {
-                const int nqo = order[h.nz_off + (pp == np - 1 ? ri.qd : ri.qu + pp)];
-                base_pp = chunks[h.chunk_off + (nqo >> 5)].x + (nqo & 31);
+        const int np = len - ri.ds, nu = np - 1;   // pairs: the nu upper columns, then the diagonal
+        for (int pp = lane; pp < np; pp += 32) {
+            if (pp < nu) s_col[pp] = col_idx[ri.b + ri.ds + 1 + pp];
+            const int nqo = order[h.nz_off + (pp == nu ? ri.qd : ri.qu + pp)];
+            s_base[pp] = chunks[h.chunk_off + (nqo >> 5)].x + (nqo & 31);
+            s_cnt[pp] = 0;
+        }
+        __syncwarp();
+        const int top = nu > 0 ? 1 << (31 - __clz(nu)) : 0;
+        for (int j0 = 0; j0 < nq; j0 += 32) {
+            const int nj = min(32, nq - j0);
+            int32_t kl = 0, ea = 0;   // this lane's incidence: element, (local element << 4 | local node)
+            if (lane < nj) {
+                const int32_t word = n2e[q0 + j0 + lane];
+                kl = word >> 4;
+                ea = (tile_local_elem(s_te, h.n_own, h.n_elems, kl) << 4) | (word & 15);
             }
-            int cnt = 0;
-            for (int j0 = 0; j0 < nq; j0 += 32) {
-                const bool valid = j0 + lane < nq;
-                const int32_t word = valid ? n2e[q0 + j0 + lane] : 0;
-                const int64_t k = word >> 4;
-                const int a = word & 15;
-                int32_t v[NLB];
-#pragma unroll
-                for (int bb = 0; bb < NLB; ++bb) v[bb] = valid ? elems[k * NLB + bb] : -1;
-                const int el = valid ? tile_local_elem(s_te, h.n_own, h.n_elems, (int32_t)k) : 0;
-                for (int q = 0; q < npq; ++q) {
-                    const int32_t c = __shfl_sync(0xffffffffu, c_pp, q);
-                    const int bs = __shfl_sync(0xffffffffu, base_pp, q);
-                    const int cb = __shfl_sync(0xffffffffu, cnt, q);
-                    int hb = -1;
-#pragma unroll
-                    for (int bb = 0; bb < NLB; ++bb)
-                        if (v[bb] == c) hb = bb;
-                    const unsigned m = __ballot_sync(0xffffffffu, hb >= 0);
-                    if (hb >= 0) {
-                        const int tt = cb + __popc(m & below);
-                        const int p = a < hb ? a : hb, r = a < hb ? hb : a;
-                        const uint32_t u = (uint32_t)(p * NLB - p * (p - 1) / 2 + (r - p));
-                        codes[(int64_t)h.code_off + bs + tt * 32] = (CT)((uint32_t)el * (uint32_t)rsc + u);
+            const int nit = nj * NLB;
+            for (int it0 = 0; it0 < nit; it0 += 32) {
+                const int it = it0 + lane, jj = it / NLB, bb = it - jj * NLB;
+                const int32_t k = __shfl_sync(0xffffffffu, kl, jj & 31);
+                const int32_t e = __shfl_sync(0xffffffffu, ea, jj & 31);
+                int pp = -1;
+                if (it < nit) {
+                    const int32_t c = elems[(int64_t)k * NLB + bb];
+                    if (c == i) {
+                        pp = nu;
+                    } else if (c > i) {
+                        int pos = 0;   // upper columns below c
+                        for (int s = top; s > 0; s >>= 1)
+                            if (pos + s <= nu && s_col[pos + s - 1] < c) pos += s;
+                        pp = pos;
                     }
-                    if (lane == q) cnt += __popc(m);
                 }
+                const unsigned grp = __match_any_sync(0xffffffffu, pp);
+                const int rank = __popc(grp & below), gsz = __popc(grp);
+                const int cnt = pp >= 0 ? s_cnt[pp] : 0;
+                __syncwarp();
+                if (pp >= 0) {
+                    const int a = e & 15, p = a < bb ? a : bb, r = a < bb ? bb : a;
+                    const uint32_t u = (uint32_t)(p * NLB - p * (p - 1) / 2 + (r - p));
+                    out[s_base[pp] + (cnt + rank) * 32] = (CT)((uint32_t)(e >> 4) * (uint32_t)rsc + u);
+                    if (rank == gsz - 1) s_cnt[pp] = cnt + gsz;
+                }
+                __syncwarp();
             }
         }
     }
@@ -1597,24 +1618,24 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         m->n_codes = o_code;
         VLA_CUDA(cudaMemcpyAsync(m->tiles, hh, sizeof(TileHdr) * n_tiles, cudaMemcpyHostToDevice, st));
         const int rsc = (nlb * (nlb + 1) / 2 + 1) | 1;   // code stride: the mixed-precision record stride
-        const size_t smem_codes = sizeof(int32_t) * (size_t)std::max(1, m->max_tile_elems);
+        const size_t smem_codes = sizeof(int32_t) * ((size_t)kCodeWarps * 3 * (kMaxRow + 1) + std::max(1, m->max_tile_elems));
         if (m->order == 1) {
             uint16_t *codes;
             TRY(dalloc(m, &codes, o_code + 64, st));
             auto kc = nlb == 3 ? k_tile_codes<3, uint16_t> : k_tile_codes<4, uint16_t>;
             TRY(allow_max_smem((const void *)kc));
-            kc<<<(int)n_tiles, 256, smem_codes, st>>>((int)n_tiles, cap_e, rsc, m->tiles, perm, m->n2e_ptr, m->n2e,
-                                                      m->elems, m->row_ptr, m->col_idx, sc_elems, row_info, nz_order,
-                                                      m->tile_chunks, codes);
+            kc<<<(int)n_tiles, kCodeWarps * 32, smem_codes, st>>>((int)n_tiles, cap_e, rsc, m->tiles, m->n2e, m->elems,
+                                                                  m->col_idx, sc_elems, row_info, nz_order,
+                                                                  m->tile_chunks, codes);
             m->tile_codes = codes;
         } else {
             uint32_t *codes;
             TRY(dalloc(m, &codes, o_code + 64, st));
             auto kc = nlb == 6 ? k_tile_codes<6, uint32_t> : k_tile_codes<10, uint32_t>;
             TRY(allow_max_smem((const void *)kc));
-            kc<<<(int)n_tiles, 256, smem_codes, st>>>((int)n_tiles, cap_e, rsc, m->tiles, perm, m->n2e_ptr, m->n2e,
-                                                      m->elems, m->row_ptr, m->col_idx, sc_elems, row_info, nz_order,
-                                                      m->tile_chunks, codes);
+            kc<<<(int)n_tiles, kCodeWarps * 32, smem_codes, st>>>((int)n_tiles, cap_e, rsc, m->tiles, m->n2e, m->elems,
+                                                                  m->col_idx, sc_elems, row_info, nz_order,
+                                                                  m->tile_chunks, codes);
             m->tile_codes = codes;
         }
         VLA_CUDA(cudaGetLastError());
