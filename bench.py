@@ -1138,6 +1138,8 @@ def main():
     d2h = rp_b.numel() * 4 + ci_b.numel() * (4 + 8 + 8) + gm.ne * 8 + gm.nfb * (3 * 8 + 8)   # what one rank copies
 
     split = []
+    copy_stream = torch.cuda.Stream()
+    ready = torch.cuda.Event()
 
     def e2e_step():
         # CUDA events between the phases and the host clock around each, to itemise the step
@@ -1152,10 +1154,18 @@ def main():
         g2 = vla.Mesh(dc, de, df, rows=None if ws == 1 else blk)   # the build synchronises the stream
         ev[2].record(stream)
         th.append(time.perf_counter())
+        # the CSR pattern is final once the mesh is built: its copy to the host
+        # runs on a second stream while the assembly runs
+        rp, ci = g2.block()
+        ready.record(stream)
         o = g2.assemble(1.0, 1.0, precision=prec, boundary=True)
         n2, a2 = o["normals"], o["areas"]
+        copy_stream.wait_event(ready)
+        with torch.cuda.stream(copy_stream):
+            out_host["rp"][: rp.numel()].copy_(rp, non_blocking=True)
+            out_host["ci"][: ci.numel()].copy_(ci, non_blocking=True)
         ev[3].record(stream)
-        rp, ci, kb, mb = g2.block((o["K"], o["M"]))
+        _, _, kb, mb = g2.block((o["K"], o["M"]))
         ev[4].record(stream)
         th.append(time.perf_counter())
         out_host["K"][: kb.numel()].copy_(kb, non_blocking=True)
@@ -1163,13 +1173,12 @@ def main():
         out_host["vol"][: g2.ne].copy_(o["vol"], non_blocking=True)
         out_host["nrm"][: g2.nfb].copy_(n2, non_blocking=True)
         out_host["ar"][: g2.nfb].copy_(a2, non_blocking=True)
-        out_host["rp"][: rp.numel()].copy_(rp, non_blocking=True)
-        out_host["ci"][: ci.numel()].copy_(ci, non_blocking=True)
+        stream.wait_stream(copy_stream)
         ev[5].record(stream)
         torch.cuda.synchronize()
         th.append(time.perf_counter())
         g2.close()
-        names = ("h2d", "mesh_build", "assemble_with_boundary", "csr_pattern_out", "d2h")
+        names = ("h2d", "mesh_build", "assemble_with_boundary", "csr_views", "d2h")
         split.append({"device_ms": {n: ev[i].elapsed_time(ev[i + 1]) for i, n in enumerate(names)},
                       "host_ms": {"h2d_enqueue": (th[1] - th[0]) * 1e3, "mesh_build_call": (th[2] - th[1]) * 1e3,
                                   "assemble_boundary_csr_enqueue": (th[3] - th[2]) * 1e3,
@@ -1189,7 +1198,8 @@ def main():
     e2e = {"value": m.ne / e2e_s, "unit": "elements/s", "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
            "includes": "H2D of coords/elems/faces, mesh build (CSR pattern, tiles), assembly, boundary, "
-                       "D2H of row_ptr/col_idx/K/M/vol/normals/areas", "split": e2e_split}
+                       "D2H of row_ptr/col_idx/K/M/vol/normals/areas (row_ptr/col_idx on a second stream, "
+                       "during the assembly)", "split": e2e_split}
 
     peaks, src = _peaks()
     bpe = _alg_bytes_per_el(gm.ne, gm.nn, gm.nnz) + FACET_BYTES * gm.nfb / gm.ne
