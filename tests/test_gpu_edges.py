@@ -183,3 +183,60 @@ def test_vertex_order_and_node_labels_do_not_matter(vla, dim, order, n):
     np.testing.assert_allclose(o64["normals"].cpu().numpy(), rn, rtol=0, atol=1e-13)
     np.testing.assert_allclose(o64["areas"].cpu().numpy(), ra, rtol=1e-13)
     gm.close()
+
+
+def _p2_nodes(X, E, dim):
+    """Mid-edge nodes appended for every element edge (one node per edge,
+    shared by the elements around it), in the element's local edge order."""
+    edges = [(0, 1), (1, 2), (0, 2)] if dim == 2 else [(0, 1), (1, 2), (0, 2), (0, 3), (1, 3), (2, 3)]
+    pts = [np.asarray(x, dtype=np.float64) for x in X]
+    mid, rows = {}, []
+    for el in E:
+        row = [int(v) for v in el]
+        for a, b in edges:
+            key = (min(el[a], el[b]), max(el[a], el[b]))
+            if key not in mid:
+                mid[key] = len(pts)
+                pts.append(0.5 * (pts[key[0]] + pts[key[1]]))
+            row.append(mid[key])
+        rows.append(row)
+    return np.array(pts), np.array(rows, dtype=np.int32)
+
+
+def _high_valence_mesh(dim, order, n):
+    # 2-D: a fan of n triangles around node 0; 3-D: a book of n tetrahedra
+    # around the edge (0, 1).  Node 0 (and 1) lies in n elements
+    rng = np.random.default_rng(n)
+    ang = np.linspace(0.0, 2 * np.pi, n + 1)[:-1] + rng.uniform(-0.2, 0.2, n) * np.pi / n
+    rad = 1.0 + 0.1 * rng.uniform(-1.0, 1.0, n)
+    if dim == 2:
+        X = np.vstack([[0.05, -0.03], np.stack([rad * np.cos(ang), rad * np.sin(ang)], axis=1)])
+        E = np.array([[0, 1 + i, 1 + (i + 1) % n] for i in range(n)], dtype=np.int32)
+    else:
+        ring = np.stack([rad * np.cos(ang), rad * np.sin(ang), 0.05 * rng.uniform(-1.0, 1.0, n)], axis=1)
+        X = np.vstack([[0.02, 0.01, -1.0], [-0.03, 0.02, 1.1], ring])
+        E = np.array([[0, 1, 2 + i, 2 + (i + 1) % n] for i in range(n)], dtype=np.int32)
+    if order == 2:
+        X, E = _p2_nodes(X, E, dim)
+    return X, E
+
+
+@pytest.mark.parametrize("dim,order,n", [(2, 1, 100), (2, 2, 60), (3, 1, 80), (3, 2, 40)])
+def test_high_valence_rows(vla, dim, order, n):
+    # incidence lists longer than a warp (the build walks them 32 at a time)
+    # and pairs with n contributions (node 0 with its neighbours on the fan's
+    # centre or the book's spine): pattern bit-exact, values as everywhere
+    X, E = _high_valence_mesh(dim, order, n)
+    gm = vla.Mesh(_dev(X), _dev(E), order=order)
+    ref = oracle.assemble(dim, order, len(X), E, X, 1.0, 0.5)
+    rp, ci = gm.csr()
+    np.testing.assert_array_equal(rp.cpu().numpy(), ref["row_ptr"])
+    np.testing.assert_array_equal(ci.cpu().numpy(), ref["col_idx"])
+    assert np.diff(ref["row_ptr"]).max() > 32
+    o64 = gm.assemble(1.0, 0.5, precision=vla.PREC_FP64)
+    omx = gm.assemble(1.0, 0.5, precision=vla.PREC_MIXED)
+    for key in ("K", "M", "vol"):
+        r = ref[key]
+        assert np.abs(o64[key].cpu().numpy() - r).max() <= TOL64 * np.abs(r).max(), key
+        assert np.linalg.norm(omx[key].cpu().numpy() - r) <= TOL_MIX * np.linalg.norm(r), key
+    gm.close()
