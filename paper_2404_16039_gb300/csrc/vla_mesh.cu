@@ -192,7 +192,8 @@ vla_status excl_scan(const TI *in, int64_t n, long long *out, cudaStream_t st, l
 // ---------------------------------------------------------------------------
 // validation and incidence
 // ---------------------------------------------------------------------------
-enum { ERR_OOB = 1, ERR_DUP = 2, ERR_ROWLEN = 4, ERR_FACE_OOB = 8, ERR_FACE_OWNER = 16 };
+enum { ERR_OOB = 1, ERR_DUP = 2, ERR_ROWLEN = 4, ERR_FACE_OOB = 8, ERR_FACE_OWNER = 16, ERR_TILE_CAP = 32,
+       ERR_NODE_CAP = 64 };
 
 __global__ void k_validate_count(int64_t ne, int nlb, int64_t nn, const int32_t *__restrict__ elems,
                                  int32_t *__restrict__ cnt, int *__restrict__ err, long long *__restrict__ bad) {
@@ -666,14 +667,16 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int n, int32_t 
 
 // insert a non-negative key into an open-addressing set in shared memory
 // (H a power of two, empty slots -1); the probe sequence visits every slot, so
-// it ends once the set holds fewer than H keys
-__device__ __forceinline__ void hset_insert(int32_t *tab, int H, int32_t x) {
+// it ends once the set holds fewer than H keys.  Returns false when the key
+// found no slot (the set was full)
+__device__ __forceinline__ bool hset_insert(int32_t *tab, int H, int32_t x) {
     uint32_t h = ((uint32_t)x * 2654435761u) & (uint32_t)(H - 1);
     for (int probe = 0; probe < H; ++probe) {
         const int32_t prev = atomicCAS(&tab[h], -1, x);
-        if (prev == -1 || prev == x) return;
+        if (prev == -1 || prev == x) return true;
         h = (h + 1) & (uint32_t)(H - 1);
     }
+    return false;
 }
 
 // the set's keys, in no particular order, into out[0..count); returns count
@@ -725,16 +728,18 @@ __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e
     extern __shared__ int32_t sm[];
     const int t = blockIdx.x;
     if (t >= n_tiles) return;
-    // cap_e >= B + wmax >= the tile's weight >= its rows and its candidates, and
-    // 2 cap_n >= (dim + 1) cap_e >= 3 cap_e
+    // cap_e >= B + wmax >= the tile's weight >= its rows and its candidates;
+    // cap_n bounds the tile's distinct vertex nodes (a tile with more reports
+    // ERR_NODE_CAP, and the host runs the pass again with a larger cap_n)
+    const int hs_len = 3 * cap_e > 2 * cap_n ? 3 * cap_e : 2 * cap_n;
     int32_t *ce = sm;                 // cap_e: the tile's elements
-    int32_t *hs = sm + cap_e;         // 2 cap_n: hash sets, then scratch of the partition
-    int32_t *cn = hs + 2 * cap_n;     // cap_n: the tile's vertex nodes
+    int32_t *hs = sm + cap_e;         // hs_len: hash sets, then scratch of the partition
+    int32_t *cn = hs + hs_len;        // max(cap_e, cap_n) + 64: the rows' prefix, then the tile's vertex nodes
     int32_t *tmp = hs;
     const int rb = tile_begin[t];
     const int re = (t + 1 < n_tiles) ? tile_begin[t + 1] : (int)nn;
     const int nr = re - rb;
-    const int He = 2 * cap_e, Hn = 2 * cap_n;
+    const int He = 2 * cap_e;
     // the rows' incidence-list starts (past the element table) and the prefix
     // of their lengths (in the node list's space, unused until the node phase)
     int32_t *r_start = hs + He, *r_pre = cn;
@@ -762,7 +767,7 @@ __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e
         cols_l += tot >> 32;
     }
     if (ncand_l > cap_e) {   // more candidates than the tile was sized for
-        if (threadIdx.x == 0) atomicOr(err, 32);
+        if (threadIdx.x == 0) atomicOr(err, ERR_TILE_CAP);
         return;
     }
     const int ncand = (int)ncand_l;
@@ -833,17 +838,15 @@ __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e
     // vertex nodes of those elements
     const int nv = dim + 1;
     const int nnc = n_el * nv;
-    if (nnc > cap_n) {
-        if (threadIdx.x == 0) atomicOr(err, 32);
-        return;
-    }
     // a table of at least twice the distinct nodes the tile can have (the
-    // candidates, or the columns of its rows if fewer)
+    // candidates, or the columns of its rows if fewer), at most cap_n slots, so
+    // that the keys it holds fit the node list
     const int nnb = nnc < cols_l ? nnc : (int)cols_l;   // at most this many distinct nodes
-    int Hu = Hn < 64 ? Hn : 64;
-    while (Hu < 2 * nnb && Hu < Hn) Hu <<= 1;
+    int Hu = cap_n < 64 ? cap_n : 64;
+    while (Hu < 2 * nnb && Hu < cap_n) Hu <<= 1;
     for (int i = threadIdx.x; i < Hu; i += blockDim.x) hs[i] = -1;
     __syncthreads();
+    bool fits = true;
     for (int x0 = threadIdx.x; x0 < nnc; x0 += 8 * blockDim.x) {
         int32_t vv[8];
 #pragma unroll
@@ -853,9 +856,12 @@ __global__ void k_tile_sets(int n_tiles, int64_t nn, int dim, int nlb, int cap_e
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u)
-            if (vv[u] >= 0) hset_insert(hs, Hu, vv[u]);
+            if (vv[u] >= 0) fits &= hset_insert(hs, Hu, vv[u]);
     }
-    __syncthreads();
+    if (__syncthreads_or(!fits)) {   // more distinct nodes than cap_n: the host sizes the pass again
+        if (threadIdx.x == 0) atomicOr(err, ERR_NODE_CAP);
+        return;
+    }
     const int n_nd = hset_compact(hs, Hu, cn);
     sort_distinct(cn, n_nd, hs);   // the table is dead after the compaction
     for (int i = threadIdx.x; i < n_nd; i += blockDim.x) sc_nodes[(int64_t)t * cap_n + i] = hs[i];
@@ -1466,26 +1472,35 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
             continue;
         }
         if (wmax > B) return fail(VLA_ERR_UNSUPPORTED, "a node belongs to %d elements (tile budget %d)", wmax - 1, B);
+        // cap_n bounds a tile's distinct vertex nodes: first the element bound
+        // cap_e (a few times what Kuhn-like meshes need), and only if some tile
+        // has more, the bound no tile can exceed, (dim + 1) (B + wmax).
+        // VLA_TILE_NODE_CAP sets the first bound instead (experiments, tests)
         const int cap_e = next_pow2(B + wmax);
-        const int cap_n = next_pow2((dim + 1) * (B + wmax));
+        const int cap_n_max = next_pow2((dim + 1) * (B + wmax));
+        int cap_n = cap_e;
+        if (const char *nc = getenv("VLA_TILE_NODE_CAP")) cap_n = std::min(cap_n_max, next_pow2(std::max(64, atoi(nc))));
         int32_t *sc_elems, *sc_nodes;
         TileCounts *tcnt;
         TRY(S.get(&sc_elems, (size_t)n_tiles * cap_e));
-        TRY(S.get(&sc_nodes, (size_t)n_tiles * cap_n));
         TRY(S.get(&tcnt, n_tiles));
-        const size_t smemA = sizeof(int32_t) * ((size_t)cap_e + 3 * (size_t)cap_n);
-        {
+        auto launch_sets = [&]() -> vla_status {
+            TRY(S.get(&sc_nodes, (size_t)n_tiles * cap_n));
+            const size_t hs_len = std::max(3 * (size_t)cap_e, 2 * (size_t)cap_n);
+            const size_t smemA = sizeof(int32_t) * ((size_t)cap_e + hs_len + (size_t)std::max(cap_e, cap_n) + 64);
             int dev_ = 0, maxsm_ = 0;
             VLA_CUDA(cudaGetDevice(&dev_));
             VLA_CUDA(cudaDeviceGetAttribute(&maxsm_, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev_));
             if (smemA + 1024 > (size_t)maxsm_)
                 return fail(VLA_ERR_UNSUPPORTED, "tile budget %d too large for the tile builder", B);
-        }
-        TRY(allow_max_smem((const void *)k_tile_sets));
-        k_tile_sets<<<(int)n_tiles, 256, smemA, st>>>((int)n_tiles, nn, dim, nlb, cap_e, cap_n, tile_begin, perm,
-                                                       m->n2e_ptr, m->n2e, m->elems, m->row_ptr, m->col_idx, node_tile,
-                                                       sc_elems, sc_nodes, tcnt, d_err);
-        VLA_CUDA(cudaGetLastError());
+            TRY(allow_max_smem((const void *)k_tile_sets));
+            k_tile_sets<<<(int)n_tiles, 256, smemA, st>>>((int)n_tiles, nn, dim, nlb, cap_e, cap_n, tile_begin,
+                                                           perm, m->n2e_ptr, m->n2e, m->elems, m->row_ptr,
+                                                           m->col_idx, node_tile, sc_elems, sc_nodes, tcnt, d_err);
+            VLA_CUDA(cudaGetLastError());
+            return VLA_OK;
+        };
+        TRY(launch_sets());
         // pinned tables: the tile counts (read back), the headers (sent down), the code counts (read back)
         unsigned char *tb = static_cast<unsigned char *>(
             pinned_tables((sizeof(TileCounts) + sizeof(TileHdr) + sizeof(int32_t)) * (size_t)n_tiles));
@@ -1498,10 +1513,20 @@ vla_status build(vla_mesh *m, const double *coords, const int32_t *elems, const 
         VLA_CUDA(cudaMemcpyAsync(&hp[1], d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
         VLA_CUDA(cudaStreamSynchronize(st));
         h_err = (int)hp[1];
+        if (h_err == ERR_NODE_CAP && cap_n < cap_n_max) {   // a tile with more vertex nodes than cap_n: size up once
+            cap_n = cap_n_max;
+            VLA_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int32_t), st));
+            TRY(launch_sets());
+            VLA_CUDA(cudaMemcpyAsync(hc, tcnt, sizeof(TileCounts) * n_tiles, cudaMemcpyDeviceToHost, st));
+            hp[1] = 0;
+            VLA_CUDA(cudaMemcpyAsync(&hp[1], d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            VLA_CUDA(cudaStreamSynchronize(st));
+            h_err = (int)hp[1];
+        }
         if (h_err & ERR_FACE_OOB)
             return fail(VLA_ERR_INDEX_OOB, "a boundary facet references a node outside [0, %lld)", (long long)nn);
         if (h_err & ERR_FACE_OWNER) return fail(VLA_ERR_DEGENERATE, "a boundary facet is not a facet of any element");
-        if (h_err & 32) return fail(VLA_ERR_UNSUPPORTED, "tile candidate capacity exceeded");
+        if (h_err & (ERR_TILE_CAP | ERR_NODE_CAP)) return fail(VLA_ERR_UNSUPPORTED, "tile candidate capacity exceeded");
 
         // tile offsets (host scan over a few thousand tiles); every segment padded for bulk copies
         auto pad = [](int64_t x, int64_t q) { return (x + q - 1) / q * q; };

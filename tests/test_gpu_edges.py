@@ -240,3 +240,35 @@ def test_high_valence_rows(vla, dim, order, n):
         assert np.abs(o64[key].cpu().numpy() - r).max() <= TOL64 * np.abs(r).max(), key
         assert np.linalg.norm(omx[key].cpu().numpy() - r) <= TOL_MIX * np.linalg.norm(r), key
     gm.close()
+
+
+@pytest.mark.parametrize("dim,order,n", [(3, 1, 22), (3, 2, 12), (2, 1, 120), (2, 2, 60)])
+def test_tile_node_capacity_second_pass(vla, monkeypatch, dim, order, n):
+    # the tile builder first bounds a tile's distinct vertex nodes tightly and,
+    # when a tile has more, runs its pass again under the bound no tile can
+    # exceed; VLA_TILE_NODE_CAP=64 forces the tight bound down so that every
+    # larger tile takes the second pass: the pattern, the tiles and every
+    # output stay the same bit for bit
+    m = meshgen.make_mesh(dim, n, order=order, jitter=0.1, seed=n)
+    X, E = _dev(m.coords), _dev(m.elems)
+    runs = []
+    for cap in (None, "64"):
+        if cap is not None:
+            monkeypatch.setenv("VLA_TILE_NODE_CAP", cap)
+        g = vla.Mesh(X, E, order=order)
+        rp, ci = g.csr()
+        omx = g.assemble(1.0, 1.0, precision=vla.PREC_MIXED)
+        o64 = g.assemble(1.0, 1.0, precision=vla.PREC_FP64)
+        runs.append(([rp.cpu(), ci.cpu(), omx["K"].cpu(), omx["M"].cpu(), o64["K"].cpu(), o64["M"].cpu()],
+                     (g.n_tiles, g.tile_elems, g.n_codes, g.smem_bytes)))
+        g.close()
+    monkeypatch.delenv("VLA_TILE_NODE_CAP")
+    (a, ia), (b, ib) = runs
+    assert ia == ib
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    if (dim, order) == (3, 1):
+        # every vertex of this mesh is in at most 24 tetrahedra, so a tile of
+        # more than 6 x 64 elements has more than 64 vertex nodes: the second
+        # pass did run
+        assert ia[1] / ia[0] > 6 * 64
