@@ -324,7 +324,7 @@ __device__ __forceinline__ void warp_sort_out(const int32_t *ks, int n, int32_t 
 // written to the row's scratch slot.
 constexpr int kRowWarps = 8, kRowHash = 512;
 template <int NLB>
-__global__ void __launch_bounds__(kRowWarps * 32) k_row_count(int64_t nn, const int32_t *__restrict__ elems,
+__global__ void __launch_bounds__(kRowWarps * 32, 8) k_row_count(int64_t nn, const int32_t *__restrict__ elems,
                                                               const int32_t *__restrict__ n2e_ptr,
                                                               const int32_t *__restrict__ n2e,
                                                               int32_t *__restrict__ scratch,
@@ -1126,7 +1126,7 @@ __global__ void __launch_bounds__(kChunkWarps * 32) k_chunk_table(int n_tiles, c
 // tile's element list (n_elems ints), searched for local element indices.
 constexpr int kCodeWarps = 8;
 template <int NLB, typename CT>
-__global__ void __launch_bounds__(kCodeWarps * 32, 4) k_tile_codes(int n_tiles, int cap_e, int rsc,
+__global__ void __launch_bounds__(kCodeWarps * 32, NLB == 4 ? 8 : 4) k_tile_codes(int n_tiles, int cap_e, int rsc,
                                                                 const TileHdr *__restrict__ hdr,
                                                                 const int32_t *__restrict__ n2e,
                                                                 const int32_t *__restrict__ elems,
