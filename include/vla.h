@@ -375,7 +375,10 @@ vla_status vla_mesh_facets(const vla_mesh *mesh, int32_t *faces, int32_t *owner,
  * which is synchronised first).  The memory returns to the library's device
  * memory pool, which keeps up to min(8 GiB, 1/16 of the device) of freed
  * memory mapped for later builds (the environment variable VLA_POOL_KEEP, in
- * bytes, sets that amount when the pool is first used; 0 keeps none).  NULL
+ * bytes, sets that amount when the pool is first used; 0 keeps none).  The
+ * temporary buffers of mesh builds are not the mesh's: each host thread that
+ * builds meshes keeps up to 512 MiB of them per device for its next build
+ * (more is returned when a build ends), freed when the thread ends.  NULL
  * is a no-op; cannot fail. */
 vla_status vla_mesh_destroy(vla_mesh *mesh);
 

@@ -157,6 +157,117 @@ __global__ void k_max_i32(int64_t n, const int32_t *__restrict__ in, int add, lo
     if ((threadIdx.x & 31) == 0 && v > 0) atomicMax(reinterpret_cast<unsigned long long *>(out), (unsigned long long)v);
 }
 
+// Device scratch of the mesh passes, per host thread and device, kept from
+// one call to the next: a call's temporary buffers are carved in order from
+// chunks of device memory the thread holds (a new chunk comes from the
+// library pool only when the held ones are full) and given back in reverse
+// order when the call's Scratch ends, instead of one pool allocation and one
+// free per buffer.  The end of a thread's outermost Scratch is recorded as an
+// event on its stream, and the thread's next call waits for it on its own
+// stream (a call on the same stream is ordered anyway).  More than
+// kScratchKeep bytes held are returned to the pool when the thread's
+// outermost Scratch ends; the rest is freed when the thread ends.
+constexpr size_t kScratchKeep = (size_t)512 << 20, kScratchChunk = (size_t)32 << 20, kScratchAlign = 256;
+struct ScratchArena {
+    struct Chunk {
+        char *p;
+        size_t cap, used;
+    };
+    std::vector<Chunk> chunks;
+    size_t cur = 0, held = 0;
+    int depth = 0, dev = -1;
+    cudaEvent_t done = nullptr;   // recorded where the last outermost Scratch ended
+    cudaStream_t done_st = nullptr;
+    bool pending = false;
+    void release(cudaStream_t st) {
+        for (const Chunk &c : chunks) cudaFreeAsync(c.p, st);
+        chunks.clear();
+        cur = 0;
+        held = 0;
+    }
+    ~ScratchArena() {
+        if (chunks.empty() && !done) return;
+        int old = 0;
+        if (cudaGetDevice(&old) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess) return;
+        for (const Chunk &c : chunks) cudaFree(c.p);
+        if (done) cudaEventDestroy(done);
+        cudaSetDevice(old);
+        cudaGetLastError();
+    }
+};
+ScratchArena &scratch_arena(int dev) {
+    static thread_local std::vector<ScratchArena> a;
+    if ((int)a.size() <= dev) a.resize(dev + 1);
+    a[dev].dev = dev;
+    return a[dev];
+}
+
+struct Scratch {  // temporary device buffers of one call, given back when it ends
+    cudaStream_t st = nullptr;
+    ScratchArena *A = nullptr;
+    size_t mark_cur = 0, mark_used = 0;
+    template <typename T>
+    vla_status get(T **p, size_t count) {
+        void *q = nullptr;
+        vla_status s = get_bytes(&q, sizeof(T) * (count > 0 ? count : 1));
+        *p = static_cast<T *>(q);
+        return s;
+    }
+    vla_status get_bytes(void **p, size_t bytes) {
+        if (!A) {
+            int dev = 0;
+            VLA_CUDA(cudaGetDevice(&dev));
+            A = &scratch_arena(dev);
+            if (A->depth == 0 && A->pending && A->done_st != st) VLA_CUDA(cudaStreamWaitEvent(st, A->done, 0));
+            A->depth += 1;
+            mark_cur = A->cur;
+            mark_used = A->chunks.empty() ? 0 : A->chunks[A->cur].used;
+        }
+        bytes = (bytes + kScratchAlign - 1) / kScratchAlign * kScratchAlign;
+        while (!A->chunks.empty() && A->chunks[A->cur].cap - A->chunks[A->cur].used < bytes &&
+               A->cur + 1 < A->chunks.size() && A->chunks[A->cur + 1].cap >= bytes)
+            A->cur += 1;   // chunks past cur hold nothing
+        if (A->chunks.empty() || A->chunks[A->cur].cap - A->chunks[A->cur].used < bytes) {
+            const size_t last = A->chunks.empty() ? 0 : A->chunks.back().cap;
+            const size_t cap = std::max(bytes, std::max(kScratchChunk, 2 * last));
+            void *q = nullptr;
+            cudaError_t e = pool_malloc(&q, cap, st);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(VLA_ERR_OOM, "device scratch allocation of %zu bytes failed", cap);
+            }
+            // the new chunk goes right after cur, so that chunks past cur stay empty
+            A->chunks.insert(A->chunks.begin() + (A->chunks.empty() ? 0 : A->cur + 1),
+                             ScratchArena::Chunk{static_cast<char *>(q), cap, 0});
+            if (A->chunks.size() > 1) A->cur += 1;
+            A->held += cap;
+        }
+        ScratchArena::Chunk &c = A->chunks[A->cur];
+        *p = c.p + c.used;
+        c.used += bytes;
+        return VLA_OK;
+    }
+    ~Scratch() {
+        if (!A) return;
+        for (size_t i = mark_cur + 1; i < A->chunks.size(); ++i) A->chunks[i].used = 0;
+        if (!A->chunks.empty()) A->chunks[mark_cur].used = mark_used;
+        A->cur = mark_cur;
+        A->depth -= 1;
+        if (A->depth > 0) return;
+        if (A->held > kScratchKeep) A->release(st);
+        if (!A->done && cudaEventCreateWithFlags(&A->done, cudaEventDisableTiming) != cudaSuccess) {
+            A->done = nullptr;
+            cudaGetLastError();
+            cudaStreamSynchronize(st);   // no event: leave nothing in flight on the memory
+            A->pending = false;
+            return;
+        }
+        cudaEventRecord(A->done, st);
+        A->done_st = st;
+        A->pending = true;
+    }
+};
+
 // out[i] = sum_{j<i} in[j] for i in [0, n], all on the device; if total_host
 // is given the total is read back (the only synchronisation).
 template <typename TI>
@@ -164,9 +275,11 @@ vla_status excl_scan(const TI *in, int64_t n, long long *out, cudaStream_t st, l
     const int64_t per = (int64_t)kScanThreads * kScanItems;
     int64_t nb = (n + per - 1) / per;
     if (nb < 1) nb = 1;
+    Scratch S;   // the block sums
+    S.st = st;
     long long *bs = nullptr, *bsp = nullptr;
-    VLA_CUDA(pool_malloc((void **)&bs, sizeof(long long) * (nb + 1), st));
-    VLA_CUDA(pool_malloc((void **)&bsp, sizeof(long long) * (nb + 1), st));
+    TRY(S.get(&bs, nb + 1));
+    TRY(S.get(&bsp, nb + 1));
     k_scan_blocks<TI><<<(int)nb, kScanThreads, 0, st>>>(n, in, out, bs);
     VLA_CUDA(cudaGetLastError());
     if (nb > 1) {
@@ -177,8 +290,6 @@ vla_status excl_scan(const TI *in, int64_t n, long long *out, cudaStream_t st, l
     }
     k_scan_total<TI><<<1, 1, 0, st>>>(n, in, out);
     VLA_CUDA(cudaGetLastError());
-    VLA_CUDA(cudaFreeAsync(bs, st));
-    VLA_CUDA(cudaFreeAsync(bsp, st));
     if (total_host) {
         long long *hp = pinned_scalars();
         if (!hp) return fail(VLA_ERR_OOM, "pinned host scalars");
@@ -1224,24 +1335,6 @@ vla_status dalloc(vla_mesh *m, T **p, size_t count, cudaStream_t st) {
     return VLA_OK;
 }
 
-struct Scratch {  // temporary device buffers freed at the end of the build
-    std::vector<void *> bufs;
-    cudaStream_t st;
-    template <typename T>
-    vla_status get(T **p, size_t count) {
-        size_t bytes = sizeof(T) * (count > 0 ? count : 1);
-        cudaError_t e = pool_malloc((void **)p, bytes, st);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return fail(VLA_ERR_OOM, "device scratch allocation of %zu bytes failed", bytes);
-        }
-        bufs.push_back((void *)*p);
-        return VLA_OK;
-    }
-    ~Scratch() {
-        for (void *b : bufs) cudaFreeAsync(b, st);
-    }
-};
 
 
 // the tile kernels take dynamic shared-memory sizes that depend on the mesh;
