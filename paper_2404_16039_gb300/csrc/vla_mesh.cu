@@ -1018,17 +1018,6 @@ struct __align__(16) RowInfo {
     int32_t qu, qd, i, b, len, ds, q0, nq;
 };
 
-// number of a row's columns below i (the diagonal's offset in the row), by a warp
-__device__ __forceinline__ int warp_count_below(const int32_t *__restrict__ col, int len, int32_t i) {
-    const int lane = threadIdx.x & 31;
-    int n = 0;
-    for (int s0 = 0; s0 < len; s0 += 32) {
-        const int s = s0 + lane;
-        n += __popc(__ballot_sync(0xffffffffu, s < len && col[s] < i));
-    }
-    return n;
-}
-
 // The rows of a tile are visited by warps, one row at a time.  A row's pairs
 // (its upper pairs {i, c > i} in column order, then the diagonal {i, i}) are
 // held one per lane, 32 at a time; its incidences (ascending element order)
