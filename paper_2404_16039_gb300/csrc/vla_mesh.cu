@@ -1019,13 +1019,14 @@ struct __align__(16) RowInfo {
 };
 
 // The rows of a tile are visited by warps, one row at a time.  A row's pairs
-// (its upper pairs {i, c > i} in column order, then the diagonal {i, i}) are
-// held one per lane, 32 at a time; its incidences (ascending element order)
-// one per lane, 32 at a time.  For each pair, the ballot of the incidences
-// whose element holds the pair's other node counts the pair's contributions
-// and ranks each contributing incidence among them (incidence order, which is
-// element order): the count pass and the code pass see the contributions in
-// the same order a single thread walking the row would.
+// are its upper pairs {i, c > i} in column order, then the diagonal {i, i};
+// its incidences come in ascending element order.  The count pass holds the
+// pairs one per lane and the incidences one per lane, 32 at a time: for each
+// pair, the ballot of the incidences whose element holds the pair's other
+// node counts its contributions.  The code pass (below) walks the incidences
+// as (incidence, local node) items instead and ranks the items that hit the
+// same pair by lane; both see the contributions in the order a single thread
+// walking the row would (element order).
 
 // Pass B: node lists, element records, owned ids, pair positions and the
 // contribution count of every pair.  Dynamic shared memory: the tile's node
