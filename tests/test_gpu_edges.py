@@ -272,3 +272,62 @@ def test_tile_node_capacity_second_pass(vla, monkeypatch, dim, order, n):
         # more than 6 x 64 elements has more than 64 vertex nodes: the second
         # pass did run
         assert ia[1] / ia[0] > 6 * 64
+
+
+def test_builds_on_several_streams_and_threads(vla):
+    # a host thread's builds share its kept scratch memory; builds on
+    # alternating streams of one thread, a facet query between them, and
+    # builds on two threads at once must give the same meshes as one build
+    # on the current stream
+    import threading
+    specs = [(3, 1, 12), (2, 2, 20), (3, 2, 5), (2, 1, 60)]
+    meshes = [meshgen.make_mesh(d, n, order=o, jitter=0.1, seed=n) for d, o, n in specs]
+    args = [(_dev(m.coords), _dev(m.elems), o) for m, (_, o, _) in zip(meshes, specs)]
+
+    def summary(g):
+        rp, ci = g.csr()
+        o = g.assemble(1.0, 1.0, precision=vla.PREC_MIXED)
+        return [rp.cpu(), ci.cpu(), o["K"].cpu(), o["M"].cpu(), o["vol"].cpu()]
+
+    ref = []
+    for X, E, o in args:
+        g = vla.Mesh(X, E, order=o)
+        ref.append(summary(g))
+        g.close()
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for rep in range(2):
+        for k, (X, E, o) in enumerate(args):
+            s = streams[(k + rep) % 2]
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                g = vla.Mesh(X, E, order=o, stream=s)
+                g.facets(stream=s)
+                got = summary(g)
+            torch.cuda.synchronize()
+            for a, b in zip(got, ref[k]):
+                assert torch.equal(a, b)
+            g.close()
+    out, errors = {}, []
+
+    def worker(t):
+        try:
+            s = torch.cuda.Stream()
+            for k in range(t, len(args), 2):
+                X, E, o = args[k]
+                with torch.cuda.stream(s):
+                    g = vla.Mesh(X, E, order=o, stream=s)
+                    out[k] = summary(g)
+                    torch.cuda.synchronize()
+                    g.close()
+        except Exception as e:   # reported by the main thread
+            errors.append(e)
+
+    th = [threading.Thread(target=worker, args=(t,)) for t in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors
+    for k in range(len(args)):
+        for a, b in zip(out[k], ref[k]):
+            assert torch.equal(a, b)
