@@ -736,7 +736,6 @@ __device__ __forceinline__ void cp_async8(void *dst, const void *src) {
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_but1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // Phase 1 of a tile: one thread per tile element computes the packed upper
 // triangle of K_k and the mass scale into the record area (index n_elems is
@@ -1054,7 +1053,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_assemble(const LaunchArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
     __shared__ int next_chunk[2];                   // dynamic chunk counters, one per tile parity
-    __shared__ __align__(16) WorkItem s_item[3];    // the tiles of the two stages, and the next one
+    __shared__ __align__(16) WorkItem s_item[4];    // the tiles of the two stages, and the next one (two slots)
     __shared__ __align__(16) MeshJob s_job[BATCH ? 2 : 1];
     __shared__ StageMap s_map[2];
     __shared__ T mhat[(TYPES & 10) ? 76 : 1];        // P2 reference mass: triangles at 0, tetrahedra at 21
@@ -1081,8 +1080,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_assemble(const LaunchArgs A) {
         if constexpr (BATCH) s_item[slot] = A.work[w];
         else s_item[slot].h = A.one.tiles[w];
     };
-    auto prefetch = [&](int w) {   // work item w into s_item[2], asynchronously (one cp.async group)
-        unsigned char *d = reinterpret_cast<unsigned char *>(&s_item[2]);
+    auto prefetch = [&](int w, int slot) {   // work item w into s_item[slot], asynchronously (one cp.async group)
+        unsigned char *d = reinterpret_cast<unsigned char *>(&s_item[slot]);
         if constexpr (BATCH) {
             if (threadIdx.x < 8) cp_async16(d + 16 * threadIdx.x, reinterpret_cast<const unsigned char *>(A.work + w) + 16 * threadIdx.x);
         } else {
@@ -1180,10 +1179,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_assemble(const LaunchArgs A) {
         const int t = t0 + j * G;
         if (t >= n) break;
         const int s = j & 1;
-        cp_async_wait_all();   // this thread's coordinate copies of tile t
-        __syncthreads();       // everyone's
+        if (j == 0) {   // later tiles: the previous iteration's closing barrier covers this
+            cp_async_wait_all();   // this thread's coordinate copies of tile t
+            __syncthreads();       // everyone's
+        }
         const bool more = t + 2 * G < n;
-        if (more) prefetch(t + 2 * G);
+        // the next header goes to the slot the previous iteration did not use:
+        // thread 0 may still be copying that one out after the closing barrier
+        const int pslot = 2 + s;
+        if (more) prefetch(t + 2 * G, pslot);
         const vla::TileHdr h = s_item[s].h;
         const StageMap mp = s_map[s];
         const unsigned char *b = stage(s);
@@ -1232,10 +1236,12 @@ __global__ void __launch_bounds__(kThreads, 3) k_assemble(const LaunchArgs A) {
             });
         }
         if (threadIdx.x == 0) next_chunk[(j + 1) & 1] = kThreads / 32;   // reset for the next tile
-        if (more) cp_async_wait_but1();   // the header fetch (the gather group may still be in flight)
-        __syncthreads();   // stage s, its job and the element records are free; the next header has landed
+        // this thread's header fetch and its coordinate copies of the next tile
+        // (issued before the pair phase) have landed
+        cp_async_wait_all();
+        __syncthreads();   // stage s, its job and the element records are free; the next header and tile are in
         if (threadIdx.x == 0 && more) {
-            s_item[s] = s_item[2];
+            s_item[s] = s_item[pslot];
             issue(s);
         }
     }
