@@ -195,11 +195,12 @@ struct ScratchArena {
         cudaGetLastError();
     }
 };
-ScratchArena &scratch_arena(int dev) {
-    static thread_local std::vector<ScratchArena> a;
-    if ((int)a.size() <= dev) a.resize(dev + 1);
+constexpr int kScratchDevices = 64;
+ScratchArena *scratch_arena(int dev) {   // a fixed table: arenas never move while a Scratch points at one
+    static thread_local ScratchArena a[kScratchDevices];
+    if (dev < 0 || dev >= kScratchDevices) return nullptr;
     a[dev].dev = dev;
-    return a[dev];
+    return &a[dev];
 }
 
 struct Scratch {  // temporary device buffers of one call, given back when it ends
@@ -217,7 +218,8 @@ struct Scratch {  // temporary device buffers of one call, given back when it en
         if (!A) {
             int dev = 0;
             VLA_CUDA(cudaGetDevice(&dev));
-            A = &scratch_arena(dev);
+            A = scratch_arena(dev);
+            if (!A) return fail(VLA_ERR_UNSUPPORTED, "device ordinal %d beyond the scratch table", dev);
             if (A->depth == 0 && A->pending && A->done_st != st) VLA_CUDA(cudaStreamWaitEvent(st, A->done, 0));
             A->depth += 1;
             mark_cur = A->cur;
